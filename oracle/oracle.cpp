@@ -1,0 +1,648 @@
+// CPU oracle for round-synchronous contraction-hierarchy construction and
+// CH s-t queries.
+//
+// TEST INFRASTRUCTURE. This file is the reference the CUDA path is checked
+// against. Only the test suite, the smoke check and the benchmark's CPU
+// baseline leg load it; the library's product path never does. It shares no
+// code, header, table or helper with the CUDA path.
+//
+// It is deliberately plain: single-threaded, ordered std::map adjacency,
+// every step applied literally in the order the paper gives it, no blocking,
+// no fusion, no pruning of searches. Where the paper leaves a detail open the
+// reading taken is stated next to the code.
+//
+// Paper passages followed (arXiv 2412.18008):
+//   Sec. 2 notation: N_in, N_out, N over the overlay graph G_O.
+//   Alg. 2  round loop: LocalSearch -> Score -> Select -> Contract, then the
+//           affected set becomes N(V_F); Postprocess at the end.
+//   Alg. 3  LocalSearch: searches batched per source s, with target set
+//           V_n = union of N_out(u) over u in N_out(s) and u in the affected set.
+//   Alg. 4  Score: P[u] = -(edges of u) + #{(v1, v2) : a shortcut is needed}.
+//   Alg. 5  Select: u is chosen iff its score is below every neighbour's,
+//           ties broken by a per-vertex label.
+//   Alg. 6  Contract: in-edges of u go to the downward set, out-edges to the
+//           upward set, surviving in x out pairs become shortcuts, u and its
+//           edges leave the overlay.
+//   Sec. 4  duplicate shortcuts (u-c1-v and u-c2-v) keep the smallest weight.
+//   Sec. 4  Postprocess: vertices ordered by level, then by score.
+//   Sec. 5  Query: upward search from s on the upward edges, upward search
+//           from t on the reversed downward edges, answer = min over meeting
+//           vertices of d_s(v) + d_t(v).
+//
+// Readings of points the paper leaves open:
+//   * Witness search: the paper bounds each Dijkstra by a settled-vertex cap
+//     whose value it never gives. Here the witness distance is the hop-limited
+//     distance d_H(a, b) = least weight of a walk a -> b with at most H edges
+//     in the current overlay graph (INF if none), which is exact and does not
+//     depend on any visiting order. The contracted vertex itself is not
+//     excluded from the search.
+//   * Shortcut predicate: a candidate (v1, u, v2) with v1 != v2 is kept iff
+//     w(v1,u) + w(u,v2) <= d_H(v1, v2). For H >= 2 this is the paper's
+//     "equals the witness distance" test; for H < 2 it is its natural
+//     extension (the pair's distance is not known, so the shortcut stays).
+//   * Edge term of the score: the prose defines edge difference with the
+//     number of edges incident to u, so P[u] subtracts |N_in(u)| + |N_out(u)|.
+//   * Tie-break label: either the vertex id itself, or the MurmurHash3 32-bit
+//     finaliser of (id XOR seed), a bijection on 32-bit words, so that a chain
+//     or a row-major grid does not get a single local minimum per round.
+//   * Rescoring: only the affected set A_r = N(V_F of round r-1) is rescored,
+//     other scores stay as they were. Contraction decisions use fresh
+//     witness distances on the overlay of the current round.
+//   * Merge: among kept candidates with the same (v1, v2), the smallest
+//     weight wins, ties to the smallest contracted vertex id; it is inserted
+//     when (v1, v2) is not an overlay edge or its weight is strictly smaller
+//     than the existing edge's, which it then replaces. Each such insertion
+//     is one shortcut.
+//   * Saturation: sums are computed exactly and any sum >= 2^32 - 1 is INF. A
+//     candidate whose via-weight is INF is never kept: it cannot lie on a
+//     path shorter than INF, so no representable distance needs it.
+//   * Rank: by (level, score at contraction, id), all ascending.
+//
+// Why the result preserves every distance, for any H, tie-break or score:
+// take a shortest path in the round-r overlay between two vertices that
+// survive the round. Each contracted vertex u on it has its predecessor a and
+// successor b outside V_F (V_F is independent) and a != b (weights are >= 1),
+// and w(a,u) + w(u,b) = dist(a, b) <= d_H(a, b), so (a, b) is kept, and the
+// edge (a, b) of the next overlay weighs at most that. Every shortcut weighs
+// as much as a real walk, so no distance can drop below the true one.
+
+#include <algorithm>
+#include <array>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <queue>
+#include <tuple>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+namespace {
+
+constexpr uint32_t INF = 0xFFFFFFFFu;
+
+constexpr int ORC_OK = 0;
+constexpr int ORC_EINVAL = -1;
+
+enum StatField {
+    ST_AFFECTED = 0,      // |A_r|
+    ST_SCORE_SOURCES,     // |N_in(A_r)|
+    ST_SELECTED,          // |V_F|
+    ST_CONTRACT_SOURCES,  // |N_in(V_F)|
+    ST_CANDIDATES,        // in x out pairs of V_F with v1 != v2
+    ST_KEPT,              // candidates passing the witness test
+    ST_MERGED,            // distinct (v1, v2) among kept
+    ST_INSERTED,          // shortcuts written into the overlay
+    ST_VO_AFTER,          // live vertices after the round
+    ST_EO_AFTER,          // live directed edges after the round
+    NSTAT
+};
+
+uint32_t sat_add(uint32_t a, uint32_t b) {
+    uint64_t s = uint64_t(a) + uint64_t(b);
+    return s >= INF ? INF : uint32_t(s);
+}
+
+// MurmurHash3 fmix32 (Appleby): a bijection on 32-bit words.
+uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+using Adj = std::map<uint32_t, uint32_t>;  // neighbour -> weight
+
+struct Overlay {
+    std::vector<Adj> out, in;
+    std::vector<char> alive;
+};
+
+bool validate(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
+              const uint32_t* w) {
+    if (n == 0) return m == 0;
+    if (!off || off[0] != 0 || off[n] != m) return false;
+    for (uint32_t u = 0; u < n; ++u)
+        if (off[u] > off[u + 1]) return false;
+    for (uint64_t e = 0; e < m; ++e) {
+        if (tgt[e] >= n) return false;
+        if (w[e] == 0 || w[e] == INF) return false;
+    }
+    return true;
+}
+
+// Input normalisation: drop self-loops, merge parallel edges by min weight.
+void load(Overlay& g, uint32_t n, const uint64_t* off, const uint32_t* tgt,
+          const uint32_t* w) {
+    g.out.assign(n, Adj());
+    g.in.assign(n, Adj());
+    g.alive.assign(n, 1);
+    for (uint32_t u = 0; u < n; ++u) {
+        for (uint64_t e = off[u]; e < off[u + 1]; ++e) {
+            uint32_t v = tgt[e];
+            if (v == u) continue;
+            auto it = g.out[u].find(v);
+            if (it == g.out[u].end() || w[e] < it->second) {
+                g.out[u][v] = w[e];
+                g.in[v][u] = w[e];
+            }
+        }
+    }
+}
+
+// Hop-limited distances from one source: d_k(y) = min(d_{k-1}(y),
+// min_x d_{k-1}(x) + w(x, y)), k = 1..H, starting from d_0 = {s: 0}. Every
+// level re-relaxes all edges out of every vertex reached so far using the
+// previous level's values, exactly as the recurrence reads.
+struct HopSearch {
+    std::vector<uint32_t> prev, cur;
+    std::vector<char> seen;
+    std::vector<uint32_t> reached;
+
+    explicit HopSearch(uint32_t n) : prev(n, INF), cur(n, INF), seen(n, 0) {}
+
+    void run(const std::vector<Adj>& out, uint32_t s, uint32_t H) {
+        for (uint32_t x : reached) {
+            prev[x] = cur[x] = INF;
+            seen[x] = 0;
+        }
+        reached.clear();
+        prev[s] = cur[s] = 0;
+        seen[s] = 1;
+        reached.push_back(s);
+        for (uint32_t k = 1; k <= H; ++k) {
+            size_t R = reached.size();
+            for (size_t i = 0; i < R; ++i) {
+                uint32_t x = reached[i];
+                uint32_t dx = prev[x];
+                for (const auto& [y, wy] : out[x]) {
+                    uint32_t nd = sat_add(dx, wy);
+                    if (nd < cur[y]) {
+                        cur[y] = nd;
+                        if (!seen[y]) {
+                            seen[y] = 1;
+                            reached.push_back(y);
+                        }
+                    }
+                }
+            }
+            for (uint32_t x : reached) prev[x] = cur[x];
+        }
+    }
+    uint32_t dist(uint32_t v) const { return seen[v] ? cur[v] : INF; }
+};
+
+bool keep(uint32_t via, uint32_t dh) { return via != INF && via <= dh; }
+
+uint64_t pair_key(uint32_t a, uint32_t b) { return (uint64_t(a) << 32) | b; }
+
+// Alg. 3 with the d_H reading: for every source s with an out-neighbour u in
+// `middle`, compute d_H from s and record it for every target v in N_out(u),
+// v != s. Returns the number of sources searched.
+uint64_t local_search(const Overlay& g, const std::vector<char>& middle,
+                      const std::vector<uint32_t>& middle_list, uint32_t H,
+                      HopSearch& hs, std::unordered_map<uint64_t, uint32_t>& dist) {
+    std::vector<uint32_t> sources;
+    for (uint32_t u : middle_list)
+        for (const auto& [v1, w1] : g.in[u]) sources.push_back(v1);
+    std::sort(sources.begin(), sources.end());
+    sources.erase(std::unique(sources.begin(), sources.end()), sources.end());
+    dist.clear();
+    for (uint32_t s : sources) {
+        hs.run(g.out, s, H);
+        for (const auto& [u, w1] : g.out[s]) {
+            if (!middle[u]) continue;
+            for (const auto& [v, w2] : g.out[u]) {
+                if (v == s) continue;
+                dist[pair_key(s, v)] = hs.dist(v);
+            }
+        }
+    }
+    return sources.size();
+}
+
+struct Shortcut {
+    uint32_t round, v1, v2, w, via;
+};
+
+struct CH {
+    uint32_t n = 0;
+    uint32_t H = 0;
+    std::vector<uint32_t> level, rank;
+    std::vector<int32_t> P;
+    std::vector<Shortcut> shortcuts;
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> up;    // E_up: u -> (x, w)
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> down;  // E_down into u: (x, w) for (x,u)
+    std::vector<std::array<uint64_t, NSTAT>> stats;
+};
+
+}  // namespace
+
+struct orc_ch {
+    CH ch;
+};
+
+namespace {
+
+uint64_t select_key(int32_t p, uint32_t u, uint32_t tie_mode, uint32_t seed) {
+    uint32_t hi = uint32_t(p) ^ 0x80000000u;  // order-preserving map of int32 onto uint32
+    uint32_t lo = tie_mode == 0 ? fmix32(u ^ seed) : u;
+    return (uint64_t(hi) << 32) | lo;
+}
+
+// Alg. 4 for one vertex, given the round's witness distances.
+int32_t score_one(const Overlay& g, uint32_t u,
+                  const std::unordered_map<uint64_t, uint32_t>& dist) {
+    int64_t p = -int64_t(g.in[u].size() + g.out[u].size());
+    for (const auto& [v1, w1] : g.in[u])
+        for (const auto& [v2, w2] : g.out[u]) {
+            if (v1 == v2) continue;
+            auto it = dist.find(pair_key(v1, v2));
+            uint32_t dh = it == dist.end() ? INF : it->second;
+            if (keep(sat_add(w1, w2), dh)) ++p;
+        }
+    return int32_t(p);
+}
+
+void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
+           const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t seed) {
+    Overlay g;
+    load(g, n, off, tgt, w);
+    ch.n = n;
+    ch.H = H;
+    ch.level.assign(n, INF);
+    ch.P.assign(n, 0);
+    ch.up.assign(n, {});
+    ch.down.assign(n, {});
+    HopSearch hs(n);
+    std::unordered_map<uint64_t, uint32_t> dist;
+
+    uint64_t live = n;
+    uint64_t live_edges = 0;
+    for (uint32_t u = 0; u < n; ++u) live_edges += g.out[u].size();
+
+    std::vector<uint32_t> A(n);
+    for (uint32_t u = 0; u < n; ++u) A[u] = u;
+    std::vector<char> inA(n, 0), inF(n, 0);
+
+    for (uint32_t r = 0; live > 0; ++r) {
+        std::array<uint64_t, NSTAT> st{};
+        st[ST_AFFECTED] = A.size();
+
+        // Step 1: LocalSearch for the affected set.
+        for (uint32_t u : A) inA[u] = 1;
+        st[ST_SCORE_SOURCES] = local_search(g, inA, A, H, hs, dist);
+
+        // Step 2: Score.
+        for (uint32_t u : A) ch.P[u] = score_one(g, u, dist);
+        for (uint32_t u : A) inA[u] = 0;
+
+        // Step 3: Select (strict local minimum of the key over N(u)).
+        std::vector<uint32_t> F;
+        for (uint32_t u = 0; u < n; ++u) {
+            if (!g.alive[u]) continue;
+            uint64_t ku = select_key(ch.P[u], u, tie_mode, seed);
+            bool minimal = true;
+            for (const auto& [v, wv] : g.out[u])
+                if (select_key(ch.P[v], v, tie_mode, seed) <= ku) minimal = false;
+            for (const auto& [v, wv] : g.in[u])
+                if (select_key(ch.P[v], v, tie_mode, seed) <= ku) minimal = false;
+            if (minimal) F.push_back(u);
+        }
+        st[ST_SELECTED] = F.size();
+
+        // Step 4: Contract. Witness distances for the candidates of V_F on
+        // the same overlay.
+        for (uint32_t u : F) inF[u] = 1;
+        st[ST_CONTRACT_SOURCES] = local_search(g, inF, F, H, hs, dist);
+
+        std::map<std::pair<uint32_t, uint32_t>, std::pair<uint32_t, uint32_t>> best;
+        for (uint32_t u : F) {
+            ch.level[u] = r;
+            for (const auto& [x, wx] : g.out[u]) ch.up[u].push_back({x, wx});
+            for (const auto& [x, wx] : g.in[u]) ch.down[u].push_back({x, wx});
+            for (const auto& [v1, w1] : g.in[u])
+                for (const auto& [v2, w2] : g.out[u]) {
+                    if (v1 == v2) continue;
+                    ++st[ST_CANDIDATES];
+                    uint32_t via = sat_add(w1, w2);
+                    auto it = dist.find(pair_key(v1, v2));
+                    uint32_t dh = it == dist.end() ? INF : it->second;
+                    if (!keep(via, dh)) continue;
+                    ++st[ST_KEPT];
+                    auto key = std::make_pair(v1, v2);
+                    auto cand = std::make_pair(via, u);
+                    auto b = best.find(key);
+                    if (b == best.end() || cand < b->second) best[key] = cand;
+                }
+        }
+        st[ST_MERGED] = best.size();
+
+        // Next affected set: neighbours of V_F in this round's overlay.
+        std::vector<uint32_t> nextA;
+        for (uint32_t u : F) {
+            for (const auto& [x, wx] : g.out[u]) nextA.push_back(x);
+            for (const auto& [x, wx] : g.in[u]) nextA.push_back(x);
+        }
+        std::sort(nextA.begin(), nextA.end());
+        nextA.erase(std::unique(nextA.begin(), nextA.end()), nextA.end());
+
+        // Insert merged shortcuts that are new or strictly better.
+        for (const auto& [key, val] : best) {
+            auto [v1, v2] = key;
+            auto [ws, via] = val;
+            auto it = g.out[v1].find(v2);
+            if (it == g.out[v1].end()) {
+                ++live_edges;
+            } else if (!(ws < it->second)) {
+                continue;
+            }
+            g.out[v1][v2] = ws;
+            g.in[v2][v1] = ws;
+            ch.shortcuts.push_back({r, v1, v2, ws, via});
+            ++st[ST_INSERTED];
+        }
+
+        // Remove V_F and its incident edges.
+        for (uint32_t u : F) {
+            for (const auto& [x, wx] : g.out[u]) g.in[x].erase(u);
+            for (const auto& [x, wx] : g.in[u]) g.out[x].erase(u);
+            live_edges -= g.out[u].size() + g.in[u].size();
+            g.out[u].clear();
+            g.in[u].clear();
+            g.alive[u] = 0;
+            inF[u] = 0;
+        }
+        live -= F.size();
+        st[ST_VO_AFTER] = live;
+        st[ST_EO_AFTER] = live_edges;
+        ch.stats.push_back(st);
+        A.swap(nextA);
+    }
+
+    // Postprocess: rank by (level, score, id).
+    std::vector<uint32_t> order(n);
+    for (uint32_t u = 0; u < n; ++u) order[u] = u;
+    std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+        return std::make_tuple(ch.level[a], ch.P[a], a) <
+               std::make_tuple(ch.level[b], ch.P[b], b);
+    });
+    ch.rank.assign(n, 0);
+    for (uint32_t i = 0; i < n; ++i) ch.rank[order[i]] = i;
+}
+
+// Textbook Dijkstra with a binary heap over an adjacency given as a function.
+template <class Nbrs>
+void dijkstra(uint32_t n, uint32_t s, Nbrs nbrs, std::vector<uint32_t>& d,
+              uint64_t* settled) {
+    d.assign(n, INF);
+    std::vector<char> done(n, 0);
+    using QE = std::pair<uint32_t, uint32_t>;
+    std::priority_queue<QE, std::vector<QE>, std::greater<QE>> pq;
+    d[s] = 0;
+    pq.push({0, s});
+    uint64_t cnt = 0;
+    while (!pq.empty()) {
+        auto [du, u] = pq.top();
+        pq.pop();
+        if (done[u]) continue;
+        done[u] = 1;
+        ++cnt;
+        nbrs(u, [&](uint32_t v, uint32_t wv) {
+            uint32_t nd = sat_add(du, wv);
+            if (nd < d[v]) {
+                d[v] = nd;
+                pq.push({nd, v});
+            }
+        });
+    }
+    if (settled) *settled = cnt;
+}
+
+// Dijkstra whose labels live in a hash map, so that its cost follows the
+// search space rather than n (used by the CH query).
+template <class Nbrs>
+void dijkstra_sparse(uint32_t s, Nbrs nbrs, std::unordered_map<uint32_t, uint32_t>& d) {
+    d.clear();
+    std::unordered_map<uint32_t, char> done;
+    using QE = std::pair<uint32_t, uint32_t>;
+    std::priority_queue<QE, std::vector<QE>, std::greater<QE>> pq;
+    d[s] = 0;
+    pq.push({0, s});
+    while (!pq.empty()) {
+        auto [du, u] = pq.top();
+        pq.pop();
+        if (done.count(u)) continue;
+        done[u] = 1;
+        nbrs(u, [&](uint32_t v, uint32_t wv) {
+            uint32_t nd = sat_add(du, wv);
+            auto it = d.find(v);
+            if (it == d.end() || nd < it->second) {
+                d[v] = nd;
+                pq.push({nd, v});
+            }
+        });
+    }
+}
+
+// Sec. 5: forward upward search from s, backward upward search from t, both
+// run to exhaustion; the answer is the least d_s(v) + d_t(v) over the
+// vertices both reach. `settled` receives the two search-space sizes summed.
+uint32_t query(const CH& ch, uint32_t s, uint32_t t, uint64_t* settled) {
+    std::unordered_map<uint32_t, uint32_t> ds, dt;
+    dijkstra_sparse(s, [&](uint32_t u, auto f) {
+        for (const auto& [x, wx] : ch.up[u]) f(x, wx);
+    }, ds);
+    dijkstra_sparse(t, [&](uint32_t u, auto f) {
+        for (const auto& [x, wx] : ch.down[u]) f(x, wx);
+    }, dt);
+    uint32_t mu = INF;
+    for (const auto& [v, dv] : ds) {
+        auto it = dt.find(v);
+        if (it != dt.end()) mu = std::min(mu, sat_add(dv, it->second));
+    }
+    if (settled) *settled = ds.size() + dt.size();
+    return mu;
+}
+
+}  // namespace
+
+extern "C" {
+
+int orc_build(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
+              const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t tie_seed,
+              orc_ch** out) {
+    if (!out || !validate(n, m, off, tgt, w) || tie_mode > 1) return ORC_EINVAL;
+    orc_ch* h = new orc_ch();
+    build(h->ch, n, off, tgt, w, H, tie_mode, tie_seed);
+    *out = h;
+    return ORC_OK;
+}
+
+void orc_free(orc_ch* h) { delete h; }
+
+uint32_t orc_rounds(const orc_ch* h) { return uint32_t(h->ch.stats.size()); }
+uint32_t orc_nstat(void) { return NSTAT; }
+
+void orc_get_stats(const orc_ch* h, uint64_t* out) {
+    for (size_t r = 0; r < h->ch.stats.size(); ++r)
+        for (int f = 0; f < NSTAT; ++f) out[r * NSTAT + f] = h->ch.stats[r][f];
+}
+
+void orc_get_level(const orc_ch* h, uint32_t* out) {
+    std::memcpy(out, h->ch.level.data(), sizeof(uint32_t) * h->ch.n);
+}
+void orc_get_priority(const orc_ch* h, int32_t* out) {
+    std::memcpy(out, h->ch.P.data(), sizeof(int32_t) * h->ch.n);
+}
+void orc_get_rank(const orc_ch* h, uint32_t* out) {
+    std::memcpy(out, h->ch.rank.data(), sizeof(uint32_t) * h->ch.n);
+}
+
+uint64_t orc_num_shortcuts(const orc_ch* h) { return h->ch.shortcuts.size(); }
+void orc_get_shortcuts(const orc_ch* h, uint32_t* out5) {
+    size_t i = 0;
+    for (const auto& s : h->ch.shortcuts) {
+        out5[i++] = s.round;
+        out5[i++] = s.v1;
+        out5[i++] = s.v2;
+        out5[i++] = s.w;
+        out5[i++] = s.via;
+    }
+}
+
+// Upward edges (u, x, w) and downward edges (x, u, w), each as triples.
+uint64_t orc_num_up(const orc_ch* h) {
+    uint64_t c = 0;
+    for (const auto& l : h->ch.up) c += l.size();
+    return c;
+}
+uint64_t orc_num_down(const orc_ch* h) {
+    uint64_t c = 0;
+    for (const auto& l : h->ch.down) c += l.size();
+    return c;
+}
+void orc_get_up(const orc_ch* h, uint32_t* out3) {
+    size_t i = 0;
+    for (uint32_t u = 0; u < h->ch.n; ++u)
+        for (const auto& [x, wx] : h->ch.up[u]) {
+            out3[i++] = u;
+            out3[i++] = x;
+            out3[i++] = wx;
+        }
+}
+void orc_get_down(const orc_ch* h, uint32_t* out3) {
+    size_t i = 0;
+    for (uint32_t u = 0; u < h->ch.n; ++u)
+        for (const auto& [x, wx] : h->ch.down[u]) {
+            out3[i++] = x;
+            out3[i++] = u;
+            out3[i++] = wx;
+        }
+}
+
+void orc_query_batch(const orc_ch* h, uint64_t k, const uint32_t* s, const uint32_t* t,
+                     uint32_t* out, uint64_t* settled) {
+    for (uint64_t i = 0; i < k; ++i)
+        out[i] = query(h->ch, s[i], t[i], settled ? settled + i : nullptr);
+}
+
+// Scores of every vertex of the input graph as round 0 computes them.
+int orc_round0_scores(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
+                      const uint32_t* w, uint32_t H, int32_t* P) {
+    if (!validate(n, m, off, tgt, w)) return ORC_EINVAL;
+    Overlay g;
+    load(g, n, off, tgt, w);
+    std::vector<uint32_t> A(n);
+    std::vector<char> inA(n, 1);
+    for (uint32_t u = 0; u < n; ++u) A[u] = u;
+    HopSearch hs(n);
+    std::unordered_map<uint64_t, uint32_t> dist;
+    local_search(g, inA, A, H, hs, dist);
+    for (uint32_t u = 0; u < n; ++u) P[u] = score_one(g, u, dist);
+    return ORC_OK;
+}
+
+// Normalised input (self-loops dropped, parallel edges merged by min) as an
+// out-CSR sorted by head. Call with off_out == NULL to get the edge count.
+int orc_normalize(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
+                  const uint32_t* w, uint64_t* m_out, uint64_t* off_out,
+                  uint32_t* tgt_out, uint32_t* w_out) {
+    if (!validate(n, m, off, tgt, w)) return ORC_EINVAL;
+    Overlay g;
+    load(g, n, off, tgt, w);
+    uint64_t c = 0;
+    for (uint32_t u = 0; u < n; ++u) c += g.out[u].size();
+    *m_out = c;
+    if (!off_out) return ORC_OK;
+    uint64_t e = 0;
+    for (uint32_t u = 0; u < n; ++u) {
+        off_out[u] = e;
+        for (const auto& [v, wv] : g.out[u]) {
+            tgt_out[e] = v;
+            w_out[e] = wv;
+            ++e;
+        }
+    }
+    off_out[n] = e;
+    return ORC_OK;
+}
+
+// d_H from `src` on the normalised input graph, for every vertex.
+int orc_hop_limited(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
+                    const uint32_t* w, uint32_t H, uint32_t src, uint32_t* dist) {
+    if (!validate(n, m, off, tgt, w) || src >= n) return ORC_EINVAL;
+    Overlay g;
+    load(g, n, off, tgt, w);
+    HopSearch hs(n);
+    hs.run(g.out, src, H);
+    for (uint32_t v = 0; v < n; ++v) dist[v] = hs.dist(v);
+    return ORC_OK;
+}
+
+// Exact single-source distances on the normalised input graph (Dijkstra).
+int orc_dijkstra(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
+                 const uint32_t* w, uint32_t src, uint32_t* dist) {
+    if (!validate(n, m, off, tgt, w) || src >= n) return ORC_EINVAL;
+    Overlay g;
+    load(g, n, off, tgt, w);
+    std::vector<uint32_t> d;
+    dijkstra(n, src, [&](uint32_t u, auto f) {
+        for (const auto& [x, wx] : g.out[u]) f(x, wx);
+    }, d, nullptr);
+    std::memcpy(dist, d.data(), sizeof(uint32_t) * n);
+    return ORC_OK;
+}
+
+// Exact s-t distances for a batch of pairs on the input graph (one Dijkstra
+// per distinct source, pairs grouped by source).
+int orc_dijkstra_pairs(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
+                       const uint32_t* w, uint64_t k, const uint32_t* s,
+                       const uint32_t* t, uint32_t* out) {
+    if (!validate(n, m, off, tgt, w)) return ORC_EINVAL;
+    Overlay g;
+    load(g, n, off, tgt, w);
+    std::vector<uint64_t> idx(k);
+    for (uint64_t i = 0; i < k; ++i) {
+        if (s[i] >= n || t[i] >= n) return ORC_EINVAL;
+        idx[i] = i;
+    }
+    std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t b) { return s[a] < s[b]; });
+    std::vector<uint32_t> d;
+    uint32_t cur = INF;
+    for (uint64_t i : idx) {
+        if (s[i] != cur) {
+            cur = s[i];
+            dijkstra(n, cur, [&](uint32_t u, auto f) {
+                for (const auto& [x, wx] : g.out[u]) f(x, wx);
+            }, d, nullptr);
+        }
+        out[i] = d[t[i]];
+    }
+    return ORC_OK;
+}
+
+}  // extern "C"
