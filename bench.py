@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark: CH construction + a batch of s-t queries on one GB300 per rank.
+
+One step = the whole hot path on the road-like workload: ``ch_build`` of the
+1M-vertex geometric 3-NN graph (inputs already in device memory) followed by
+one batch of 1M uniform random s-t queries through ``ch_query_batch``.
+
+Headline ``value``: CH build seconds per step (the paper's headline metric,
+lower is better). The same line carries the shortcut count, the queries/sec
+of the batch, the per-kernel roofline of the dominant kernel, the CPU oracle
+timed on a bounded sample, the SM clocks seen during the timed region and an
+end-to-end measurement through host buffers.
+
+Multi-GPU: the path does not shard (a round needs the global selection and
+merge), so ``--gpus N`` runs N independent replicas, one per rank; the
+reported times are the maximum over ranks.
+
+``--impl reference`` times the CPU oracle (the only reference this method
+has: the paper ships no code) on host cores, on a bounded sample of the same
+workload, scaled to the workload's size.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2412_18008_gb300 import inputs as I  # noqa: E402
+
+WORKLOADS = {
+    # name: (n, graph seed, query seed, queries)
+    "geo1M": (1_000_000, 3, 4, 1_000_000),
+    "geo256K": (256_000, 100, 101, 1_000_000),
+}
+METRIC = "CH build seconds & shortcut count; batched s-t queries/sec; p99 query latency"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="geo1M", choices=sorted(WORKLOADS))
+    ap.add_argument("--hop-limit", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.devnull if False else f"/tmp/ch_clocks_{os.getpid()}.csv", "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.out.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample_build(n_full: int, hop_limit: int, sample_n: int = 100_000):
+    """Oracle build on a sample graph of the same family, scaled linearly
+    (by vertex count) to the full workload. Returns (scaled_s, raw_s, threads)."""
+    import oracle as O
+    g = I.geometric_knn_graph(sample_n, seed=7)
+    t0 = time.perf_counter()
+    O.build_ch(g, hop_limit)
+    raw = time.perf_counter() - t0
+    return raw * (n_full / sample_n), raw, 1
+
+
+def run_reference(args):
+    n, gseed, qseed, nq = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    sample_n = 100_000
+    O.build_ch(I.geometric_knn_graph(2000, seed=7), args.hop_limit)  # load + warm
+    g = I.geometric_knn_graph(sample_n, seed=7)
+    for _ in range(args.warmup):
+        O.build_ch(g, args.hop_limit)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.build_ch(g, args.hop_limit)
+        times.append(time.perf_counter() - t0)
+    scale = n / sample_n
+    value = statistics.mean(times) * scale
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": value * 1000, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "vertices": n, "hop_limit": args.hop_limit},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": f"oracle build of a {sample_n}-vertex graph of the same "
+                                   f"geometric 3-NN family, mean of {args.steps} runs, scaled "
+                                   f"linearly by vertex count to {n} vertices"},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2412_18008_gb300 import ch
+
+    n, gseed, qseed, nq = WORKLOADS[args.workload]
+    g = I.geometric_knn_graph(n, seed=gseed)
+    s_h, t_h = I.random_pairs(n, nq, seed=qseed)
+    off_d = torch.from_numpy(g.offsets.view(np.int64)).to(dev)
+    tgt_d = torch.from_numpy(g.targets.view(np.int32)).to(dev)
+    w_d = torch.from_numpy(g.weights.view(np.int32)).to(dev)
+    s_d = torch.from_numpy(s_h.view(np.int32)).to(dev)
+    t_d = torch.from_numpy(t_h.view(np.int32)).to(dev)
+    out_d = torch.empty(nq, dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+
+    def step():
+        h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
+                        hop_limit=args.hop_limit, stream=stream)
+        h.query_batch_raw(s_d.data_ptr(), t_d.data_ptr(), nq, out_d.data_ptr(), None, sp)
+        return h
+
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            h = step()
+        stream.synchronize()
+        h.close()
+
+    # timed region
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = ch.kernel_launches()
+    step_ms, build_ms, query_ms = [], [], []
+    stats = None
+    handles = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)  # evict the inputs from L2 (outside the events)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
+                            hop_limit=args.hop_limit, stream=stream)
+            e1.record(stream)
+            h.query_batch_raw(s_d.data_ptr(), t_d.data_ptr(), nq, out_d.data_ptr(), None, sp)
+            e2.record(stream)
+        stream.synchronize()
+        step_ms.append(e0.elapsed_time(e2))
+        build_ms.append(e0.elapsed_time(e1))
+        query_ms.append(e1.elapsed_time(e2))
+        stats = h.stats()
+        handles.append(h)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    launches = ch.kernel_launches() - launches0
+    clocks = sampler.stop()
+    h_last = handles[-1]
+    h_last.query_status(stream)
+    for h in handles[:-1]:
+        h.close()
+
+    mean_step = statistics.mean(step_ms)
+    mean_build = statistics.mean(build_ms)
+    mean_query = statistics.mean(query_ms)
+    if world > 1:
+        tt = torch.tensor([mean_step, mean_build, mean_query], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        mean_step, mean_build, mean_query = tt.tolist()
+
+    # search-space size on a sample of the batch (the paper's query iterations)
+    samp = 100_000
+    dd, st = h_last.query(s_d[:samp], t_d[:samp], want_settled=True, stream=stream)
+    stream.synchronize()
+    mean_ss = float(st.cpu().numpy().view(np.uint32).mean())
+
+    # roofline of the dominant kernel: the witness search
+    peak, peak_src = load_peaks()
+    wit_gbs = stats["witness_bytes"] / (stats["witness_ms"] * 1e-3) / 1e9 if stats["witness_ms"] else 0.0
+    phases = {k: stats[k] for k in ("normalise_ms", "score_ms", "select_ms", "prep_ms",
+                                    "contract_ms", "update_ms", "postprocess_ms")}
+    roofline = {
+        "kernel": "k_witness (score + contract witness searches)",
+        "bound": "hbm", "achieved": round(wit_gbs, 1), "peak": peak, "unit": "GB/s",
+        "frac": round(wit_gbs / peak, 4), "traffic": None,
+        "peak_source": peak_src,
+        "bytes_per_launch": stats["witness_bytes"] / max(1, stats["witness_launches"]),
+        "ms_per_launch": stats["witness_ms"] / max(1, stats["witness_launches"]),
+        "share_of_build": round(stats["witness_ms"] / mean_build, 3) if mean_build else None,
+    }
+
+    # end to end through host buffers (H2D of the CSR and the queries, D2H of
+    # the answers, inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        e2e_build, e2e_q = [], []
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hh = ch.CH.build(g, hop_limit=args.hop_limit)
+            t1 = time.perf_counter()
+            hh.query(s_h, t_h)
+            t2 = time.perf_counter()
+            e2e_build.append(t1 - t0)
+            e2e_q.append(t2 - t1)
+            hh.close()
+        h2d = g.offsets.nbytes + g.targets.nbytes + g.weights.nbytes + s_h.nbytes + t_h.nbytes
+        e2e = {"value": statistics.mean(e2e_build), "unit": "s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(nq * 4),
+               "queries_per_s": nq / statistics.mean(e2e_q)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        scaled, raw, cores = cpu_sample_build(n, args.hop_limit)
+        cpu = {"value": scaled, "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle build of a 100000-vertex graph of the same family "
+                         f"({raw:.2f} s, one thread), scaled linearly by vertex count to {n}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": mean_build / 1000.0, "unit": "s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": mean_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "vertices": n, "edges": int(g.m),
+                       "queries": nq, "hop_limit": args.hop_limit,
+                       "parallelism": f"replicas{world}",
+                       "l2": "flushed before each step (2x L2 buffer write)"},
+            "shortcuts": stats["shortcuts"], "rounds": stats["rounds"],
+            "queries_per_s": nq / (mean_query / 1000.0), "query_batch_ms": mean_query,
+            "mean_search_space": mean_ss,
+            "build_phases_ms": phases,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    h_last.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * ch.h - C ABI of the GB300 contraction-hierarchy library (libch.so).
+ *
+ * Round-synchronous contraction-hierarchy (CH) construction and batched CH
+ * s-t distance queries, after "Parallel Contraction Hierarchies Can Be
+ * Efficient and Scalable" (arXiv 2412.18008). Every step runs in CUDA
+ * kernels for sm_103a on one GPU; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *   - Return value: CH_OK (0) or a negative CH_E* code. On error nothing is
+ *     written to output handles, and ch_last_error() describes the failure
+ *     (a thread-local string owned by the library, valid until the calling
+ *     thread's next call into it).
+ *   - Vertex ids are uint32 in [0, n). Weights are uint32 in
+ *     [1, 0xFFFFFFFE]. CH_INF (0xFFFFFFFF) means "unreachable". Distances
+ *     are exact sums; a distance >= 2^32 - 1 is reported as CH_INF.
+ *   - The caller owns every input and output buffer it passes; the library
+ *     owns ch_t and all device memory behind it until ch_free().
+ *   - Everything is deterministic: the same graph and parameters give a
+ *     bitwise-identical hierarchy and identical query answers.
+ *   - A handle keeps one set of query work buffers: query batches on one
+ *     ch_t must not overlap in time (issue them on one stream, or wait
+ *     between streams). Separate handles are independent. No call may race
+ *     with ch_free() of the same handle.
+ */
+#ifndef GB300_CH_H
+#define GB300_CH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CH_OK 0
+#define CH_EINVAL (-1)    /* bad argument, id out of range, weight 0 or 0xFFFFFFFF */
+#define CH_ENOMEM (-2)    /* device or host allocation failed */
+#define CH_ECUDA (-3)     /* a CUDA call failed (message in ch_last_error) */
+#define CH_ETIMEOUT (-4)  /* a bounded device-side wait expired */
+#define CH_ERANGE (-5)    /* a size limit of this library was exceeded */
+
+#define CH_INF 0xFFFFFFFFu
+
+/* Tie-break label of the selection key (Alg. 5 breaks ties "by the label of
+ * each vertex"): CH_TIE_HASHED uses the MurmurHash3 32-bit finaliser of
+ * (id XOR tie_seed), a bijection; CH_TIE_ID uses the id itself. */
+#define CH_TIE_HASHED 0u
+#define CH_TIE_ID 1u
+
+/* Vertex score: CH_PRIO_EDGE_DIFF is the edge difference of Alg. 4. */
+#define CH_PRIO_EDGE_DIFF 0u
+
+/* Input graph, a directed out-CSR (Sec. 4.1: "our input graph is given in
+ * the CSR format"). offsets[n+1] (offsets[0] = 0, non-decreasing,
+ * offsets[n] = m), targets[m], weights[m]. Self-loops are dropped and
+ * parallel edges merged by minimum weight. Pointers are host memory when
+ * on_device = 0 and device memory of the current device when on_device = 1.
+ * The library only reads them, and only during ch_build. */
+typedef struct {
+    uint32_t n;
+    uint64_t m;
+    const uint64_t *offsets;
+    const uint32_t *targets;
+    const uint32_t *weights;
+    int32_t on_device;
+} ch_graph_t;
+
+/* Construction parameters. Fill with ch_default_params() first.
+ *   hop_limit  H of the witness test: a candidate shortcut (v1, u, v2) is kept
+ *              iff w(v1,u) + w(u,v2) <= d_H(v1, v2), the least weight of a
+ *              walk with at most H edges in the current overlay graph
+ *              (Alg. 3, 4, 6 with a hop bound in place of the unstated
+ *              settled-vertex bound). Any H >= 0 yields exact distances;
+ *              default 5.
+ *   priority   CH_PRIO_EDGE_DIFF.
+ *   tie_break  CH_TIE_HASHED (default) or CH_TIE_ID; tie_seed feeds the hash.
+ *   max_candidates_per_vertex  must be UINT64_MAX (contract every vertex).
+ *   stream     cudaStream_t the build runs on (NULL: the legacy stream).
+ *              ch_build returns after the work on it has finished. */
+typedef struct {
+    uint32_t hop_limit;
+    uint32_t priority;
+    uint32_t tie_break;
+    uint32_t tie_seed;
+    uint64_t max_candidates_per_vertex;
+    void *stream;
+} ch_params_t;
+
+typedef struct ch_s ch_t;
+
+/* Summary of a built hierarchy. */
+typedef struct {
+    uint32_t n;             /* vertices */
+    uint64_t m_input;       /* edges after normalisation */
+    uint32_t rounds;        /* contraction rounds (= levels) */
+    uint64_t shortcuts;     /* shortcuts inserted over all rounds */
+    uint64_t up_edges;      /* |E_up|: out-edges of each vertex at its contraction */
+    uint64_t down_edges;    /* |E_down|: in-edges of each vertex at its contraction */
+    double build_ms;        /* device time of ch_build, ms (CUDA events) */
+    uint64_t witness_sources;   /* witness searches run, score + contract */
+    uint64_t witness_fallback;  /* of which ran on the global-memory path */
+    /* Device time per phase, ms, summed over rounds (CUDA events on the
+     * build stream): input normalisation, rescoring (steps 1-2), selection,
+     * contraction bookkeeping, contraction witness searches, overlay update,
+     * ranking and CSR construction. */
+    double normalise_ms, score_ms, select_ms, prep_ms, contract_ms, update_ms, postprocess_ms;
+    /* The witness-search kernels alone (both phases): device time, launch
+     * count, and algorithmic bytes read: 4 per search (source id), 12 per
+     * vertex whose out-list is read (offset + degree), 8 per adjacency entry
+     * read (id + weight). */
+    double witness_ms;
+    uint64_t witness_launches;
+    uint64_t witness_bytes;
+} ch_stats_t;
+
+/* Number of per-round statistics fields written by ch_get_round_stats, in
+ * this order: affected |A_r|, score sources |N_in(A_r)|, selected |V_F|,
+ * contract sources |N_in(V_F)|, candidates (in x out pairs of V_F, v1 != v2),
+ * kept (pass the witness test), merged (distinct (v1, v2) among kept),
+ * inserted (shortcuts written), live vertices after, live edges after. */
+#define CH_NSTAT 10u
+
+void ch_default_params(ch_params_t *p);
+
+/* Build a contraction hierarchy of `g` (Alg. 2: rounds of LocalSearch,
+ * Score, Select, Contract until the overlay is empty; then Postprocess,
+ * which ranks vertices by (level, score, id)). On success *out receives a
+ * new handle. Errors: CH_EINVAL for a malformed graph or parameter,
+ * CH_ENOMEM, CH_ECUDA, CH_ERANGE (more than 2^32 - 1 hierarchy edges). */
+int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out);
+
+/* Batched s-t distances (Sec. 5): for i < k, dist_out[i] = length of a
+ * shortest path src[i] -> dst[i] in the input graph, via the upward search
+ * from src[i] over E_up and from dst[i] over reversed E_down, minimised over
+ * the vertices both reach. src, dst, dist_out (uint32[k]) and settled_out
+ * (uint32[k] or NULL: number of vertices the two searches reached, the
+ * paper's "query iterations") are DEVICE pointers; the work is enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy stream) and the call returns
+ * without waiting. Ids >= n give CH_EINVAL for the whole batch (checked on
+ * the device; the status is returned by the next synchronising call on the
+ * handle, or by ch_query_status). k = 0 is a no-op. */
+int ch_query_batch(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                   uint32_t *dist_out, uint32_t *settled_out, void *stream);
+
+/* Same as ch_query_batch with HOST pointers: copies the batch to the device,
+ * runs it, copies the answers back, and returns when they are in dist_out. */
+int ch_query_batch_host(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                        uint32_t *dist_out, uint32_t *settled_out);
+
+/* Waits for `stream` and reports (then clears) a device-side error recorded
+ * by earlier ch_query_batch calls on this handle. */
+int ch_query_status(ch_t *ch, void *stream);
+
+int ch_get_stats(const ch_t *ch, ch_stats_t *out);
+
+/* Copies min(rounds, max_rounds) rows of CH_NSTAT uint64 values to `out`. */
+int ch_get_round_stats(const ch_t *ch, uint64_t *out, uint32_t max_rounds);
+
+/* Copies the hierarchy to HOST buffers; any pointer may be NULL to skip it.
+ *   level[n]    round in which each vertex was contracted
+ *   priority[n] its score (int32) when it was contracted
+ *   rank[n]     its position in the (level, score, id) order
+ *   shortcuts   5 x uint32 per shortcut: (round, v1, v2, w, via), sorted by
+ *               (round, v1, v2); ch_stats_t.shortcuts rows
+ *   up          3 x uint32 per upward edge (u, x, w), sorted by (u, x);
+ *               ch_stats_t.up_edges rows
+ *   down        3 x uint32 per downward edge (x, u, w), sorted by (u, x);
+ *               ch_stats_t.down_edges rows */
+int ch_export(const ch_t *ch, uint32_t *level, int32_t *priority, uint32_t *rank,
+              uint32_t *shortcuts, uint32_t *up, uint32_t *down);
+
+void ch_free(ch_t *ch);
+
+const char *ch_last_error(void);
+
+/* Library version string, e.g. "gb300-ch 0.1 sm_103a". */
+const char *ch_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all handles, all threads). Instrumentation for benchmarks. */
+uint64_t ch_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_CH_H */

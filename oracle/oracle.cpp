@@ -439,6 +439,7 @@ void dijkstra_sparse(uint32_t s, Nbrs nbrs, std::unordered_map<uint32_t, uint32_
         done[u] = 1;
         nbrs(u, [&](uint32_t v, uint32_t wv) {
             uint32_t nd = sat_add(du, wv);
+            if (nd == INF) return;  // not reachable within the uint32 range
             auto it = d.find(v);
             if (it == d.end() || nd < it->second) {
                 d[v] = nd;
@@ -450,7 +451,8 @@ void dijkstra_sparse(uint32_t s, Nbrs nbrs, std::unordered_map<uint32_t, uint32_
 
 // Sec. 5: forward upward search from s, backward upward search from t, both
 // run to exhaustion; the answer is the least d_s(v) + d_t(v) over the
-// vertices both reach. `settled` receives the two search-space sizes summed.
+// vertices both reach. `settled` receives the two search-space sizes summed
+// (vertices reached at a distance below INF, counted once per direction).
 uint32_t query(const CH& ch, uint32_t s, uint32_t t, uint64_t* settled) {
     std::unordered_map<uint32_t, uint32_t> ds, dt;
     dijkstra_sparse(s, [&](uint32_t u, auto f) {

@@ -1,0 +1,269 @@
+"""Python binding of ``libch.so`` (the C ABI declared in ``include/ch.h``).
+
+Argument marshalling only: every step of construction and querying runs in
+the library's CUDA kernels. Device buffers come from PyTorch CUDA tensors
+(``data_ptr()``); host buffers from NumPy arrays. There is no CPU fallback:
+if the library cannot be loaded, :func:`load` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CH_OK = 0
+CH_EINVAL = -1
+CH_ENOMEM = -2
+CH_ECUDA = -3
+CH_ETIMEOUT = -4
+CH_ERANGE = -5
+CH_INF = 0xFFFFFFFF
+CH_TIE_HASHED = 0
+CH_TIE_ID = 1
+CH_PRIO_EDGE_DIFF = 0
+CH_NSTAT = 10
+
+ROUND_STAT_FIELDS = ("affected", "score_sources", "selected", "contract_sources",
+                     "candidates", "kept", "merged", "inserted", "vo_after", "eo_after")
+
+
+class CHError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class GraphT(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("m", C.c_uint64), ("offsets", C.c_void_p),
+                ("targets", C.c_void_p), ("weights", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class ParamsT(C.Structure):
+    _fields_ = [("hop_limit", C.c_uint32), ("priority", C.c_uint32), ("tie_break", C.c_uint32),
+                ("tie_seed", C.c_uint32), ("max_candidates_per_vertex", C.c_uint64),
+                ("stream", C.c_void_p)]
+
+
+class StatsT(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("m_input", C.c_uint64), ("rounds", C.c_uint32),
+                ("shortcuts", C.c_uint64), ("up_edges", C.c_uint64), ("down_edges", C.c_uint64),
+                ("build_ms", C.c_double), ("witness_sources", C.c_uint64),
+                ("witness_fallback", C.c_uint64),
+                ("normalise_ms", C.c_double), ("score_ms", C.c_double), ("select_ms", C.c_double),
+                ("prep_ms", C.c_double), ("contract_ms", C.c_double), ("update_ms", C.c_double),
+                ("postprocess_ms", C.c_double), ("witness_ms", C.c_double),
+                ("witness_launches", C.c_uint64), ("witness_bytes", C.c_uint64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libch.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libch.so not found at {path}; run the build first")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.ch_default_params.argtypes = [C.POINTER(ParamsT)]
+    lib.ch_default_params.restype = None
+    lib.ch_build.argtypes = [C.POINTER(GraphT), C.POINTER(ParamsT), C.POINTER(P)]
+    lib.ch_query_batch.argtypes = [P, P, P, C.c_uint64, P, P, P]
+    lib.ch_query_batch_host.argtypes = [P, P, P, C.c_uint64, P, P]
+    lib.ch_query_status.argtypes = [P, P]
+    lib.ch_get_stats.argtypes = [P, C.POINTER(StatsT)]
+    lib.ch_get_round_stats.argtypes = [P, P, C.c_uint32]
+    lib.ch_export.argtypes = [P, P, P, P, P, P, P]
+    for f in ("ch_build", "ch_query_batch", "ch_query_batch_host", "ch_query_status",
+              "ch_get_stats", "ch_get_round_stats", "ch_export"):
+        getattr(lib, f).restype = C.c_int
+    lib.ch_free.argtypes = [P]
+    lib.ch_free.restype = None
+    lib.ch_last_error.restype = C.c_char_p
+    lib.ch_version.restype = C.c_char_p
+    lib.ch_kernel_launches.restype = C.c_uint64
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != CH_OK:
+        raise CHError(rc, _lib.ch_last_error().decode(errors="replace"))
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hp(a):
+    return a.ctypes.data_as(C.c_void_p) if a.size else None
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def default_params() -> ParamsT:
+    p = ParamsT()
+    load().ch_default_params(C.byref(p))
+    return p
+
+
+class CH:
+    """A contraction hierarchy owned by libch.so."""
+
+    def __init__(self, handle: C.c_void_p):
+        self._h = handle
+
+    # -- construction -----------------------------------------------------
+    @classmethod
+    def build(cls, graph=None, *, n=None, offsets=None, targets=None, weights=None,
+              hop_limit: int = 5, tie_break: int = CH_TIE_HASHED, tie_seed: int = 0,
+              stream=None) -> "CH":
+        """ch_build on a graph given as an ``inputs.Graph`` / NumPy CSR (host
+        memory) or as CUDA tensors ``offsets`` (int64), ``targets`` and
+        ``weights`` (int32 views of uint32 values) in device memory."""
+        lib = load()
+        if graph is not None:
+            n, offsets, targets, weights = graph.n, graph.offsets, graph.targets, graph.weights
+        g = GraphT()
+        g.n = int(n)
+        keep = []
+        if _is_torch(offsets):
+            import torch
+            for t in (offsets, targets, weights):
+                if not t.is_cuda or not t.is_contiguous():
+                    raise ValueError("device CSR tensors must be contiguous CUDA tensors")
+            if offsets.dtype != torch.int64 or targets.element_size() != 4 or weights.element_size() != 4:
+                raise ValueError("offsets must be int64, targets/weights 32-bit")
+            g.m = int(targets.numel())
+            g.offsets, g.targets, g.weights = offsets.data_ptr(), targets.data_ptr(), weights.data_ptr()
+            g.on_device = 1
+            st = _stream_ptr(stream)
+        else:
+            off = _host(offsets, np.uint64)
+            tgt = _host(targets, np.uint32)
+            w = _host(weights, np.uint32)
+            keep = [off, tgt, w]
+            g.m = int(tgt.size)
+            g.offsets, g.targets, g.weights = _hp(off), _hp(tgt), _hp(w)
+            g.on_device = 0
+            st = C.c_void_p(None) if stream is None else _stream_ptr(stream)
+        p = default_params()
+        p.hop_limit = hop_limit
+        p.tie_break = tie_break
+        p.tie_seed = tie_seed & 0xFFFFFFFF
+        p.stream = st
+        h = C.c_void_p()
+        _check(lib.ch_build(C.byref(g), C.byref(p), C.byref(h)))
+        del keep
+        return cls(h)
+
+    # -- queries ----------------------------------------------------------
+    def query(self, src, dst, want_settled: bool = False, stream=None):
+        """Batched s-t distances. CUDA tensors -> async on ``stream`` (device
+        outputs returned as int32 tensors holding uint32 bit patterns); NumPy
+        arrays -> synchronous host call returning uint32 arrays."""
+        lib = load()
+        if _is_torch(src):
+            import torch
+            if src.shape != dst.shape:
+                raise ValueError("sources and targets differ in length")
+            k = src.numel()
+            out = torch.empty(k, dtype=torch.int32, device=src.device)
+            settled = torch.empty(k, dtype=torch.int32, device=src.device) if want_settled else None
+            _check(lib.ch_query_batch(self._h, src.data_ptr(), dst.data_ptr(), k, out.data_ptr(),
+                                      settled.data_ptr() if settled is not None else None,
+                                      _stream_ptr(stream)))
+            return (out, settled) if want_settled else out
+        s = _host(src, np.uint32)
+        t = _host(dst, np.uint32)
+        if s.shape != t.shape:
+            raise ValueError("sources and targets differ in length")
+        out = np.empty(s.size, np.uint32)
+        settled = np.empty(s.size, np.uint32) if want_settled else None
+        _check(lib.ch_query_batch_host(self._h, _hp(s), _hp(t), s.size, _hp(out),
+                                       _hp(settled) if settled is not None else None))
+        return (out, settled) if want_settled else out
+
+    def query_status(self, stream=None):
+        _check(load().ch_query_status(self._h, _stream_ptr(stream)))
+
+    def query_batch_raw(self, src_ptr: int, dst_ptr: int, k: int, out_ptr: int,
+                        settled_ptr: int | None, stream_ptr: int):
+        """ch_query_batch on raw device pointers (used inside timed loops)."""
+        _check(load().ch_query_batch(self._h, src_ptr, dst_ptr, k, out_ptr, settled_ptr,
+                                     stream_ptr))
+
+    # -- introspection ----------------------------------------------------
+    def stats(self) -> dict:
+        s = StatsT()
+        _check(load().ch_get_stats(self._h, C.byref(s)))
+        return {name: getattr(s, name) for name, _ in StatsT._fields_}
+
+    def round_stats(self) -> np.ndarray:
+        r = self.stats()["rounds"]
+        out = np.zeros((r, CH_NSTAT), np.uint64)
+        if r:
+            _check(load().ch_get_round_stats(self._h, _hp(out), r))
+        return out
+
+    def export(self) -> dict:
+        st = self.stats()
+        n = st["n"]
+        level = np.empty(n, np.uint32)
+        prio = np.empty(n, np.int32)
+        rank = np.empty(n, np.uint32)
+        sc = np.empty((st["shortcuts"], 5), np.uint32)
+        up = np.empty((st["up_edges"], 3), np.uint32)
+        down = np.empty((st["down_edges"], 3), np.uint32)
+        _check(load().ch_export(self._h, _hp(level), _hp(prio), _hp(rank), _hp(sc), _hp(up),
+                                _hp(down)))
+        return dict(level=level, priority=prio, rank=rank, shortcuts=sc, up=up, down=down)
+
+    def close(self):
+        if self._h:
+            load().ch_free(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version() -> str:
+    return load().ch_version().decode()
+
+
+def kernel_launches() -> int:
+    """CUDA kernels libch.so has launched in this process."""
+    return int(load().ch_kernel_launches())

@@ -1,0 +1,297 @@
+// C ABI of libch.so: argument checks, error translation, host-side export.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <tuple>
+
+#include "handle.cuh"
+
+namespace gbch {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+}
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_last_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+int device_sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        sms = 152;
+    if (dev >= 0 && dev < 64) cached[dev] = sms;
+    return sms;
+}
+
+template <class F>
+int guarded(F &&f) {
+    try {
+        f();
+        return CH_OK;
+    } catch (const Error &e) {
+        g_last_error = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return CH_ENOMEM;
+    } catch (const std::exception &e) {
+        g_last_error = e.what();
+        return CH_ECUDA;
+    }
+}
+
+}  // namespace gbch
+
+using namespace gbch;
+
+extern "C" {
+
+const char *ch_last_error(void) { return g_last_error.c_str(); }
+
+const char *ch_version(void) { return "gb300-ch 0.1 sm_103a"; }
+
+uint64_t ch_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void ch_default_params(ch_params_t *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->hop_limit = 5;
+    p->priority = CH_PRIO_EDGE_DIFF;
+    p->tie_break = CH_TIE_HASHED;
+    p->tie_seed = 0;
+    p->max_candidates_per_vertex = UINT64_MAX;
+    p->stream = nullptr;
+}
+
+int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out) {
+    if (!g || !out) {
+        g_last_error = "null graph or output handle";
+        return CH_EINVAL;
+    }
+    ch_params_t p;
+    if (params) p = *params;
+    else ch_default_params(&p);
+    if (p.priority != CH_PRIO_EDGE_DIFF) {
+        g_last_error = "unsupported priority mode";
+        return CH_EINVAL;
+    }
+    if (p.tie_break > CH_TIE_ID) {
+        g_last_error = "unknown tie_break";
+        return CH_EINVAL;
+    }
+    if (p.max_candidates_per_vertex != UINT64_MAX) {
+        g_last_error = "max_candidates_per_vertex must be UINT64_MAX";
+        return CH_EINVAL;
+    }
+    if (g->n == 0xFFFFFFFFu) {
+        g_last_error = "n must be below 2^32 - 1";
+        return CH_ERANGE;
+    }
+    if (g->n > 0 && (!g->offsets || (g->m > 0 && (!g->targets || !g->weights)))) {
+        g_last_error = "null CSR array";
+        return CH_EINVAL;
+    }
+    ch_s *h = new (std::nothrow) ch_s();
+    if (!h) {
+        g_last_error = "host allocation failed";
+        return CH_ENOMEM;
+    }
+    int rc = guarded([&] {
+        CH_CUDA_TRY(cudaGetDevice(&h->device));
+        build_hierarchy(h, g, &p);
+        query_init(h);
+        h->stats.n = h->n;
+        h->stats.m_input = h->m_input;
+        h->stats.rounds = (uint32_t)h->round_stats.size();
+        h->stats.shortcuts = h->n_shortcuts;
+        h->stats.up_edges = h->n_up;
+        h->stats.down_edges = h->n_down;
+        h->stats.normalise_ms = h->t_norm_ms;
+        h->stats.score_ms = h->t_score_ms;
+        h->stats.select_ms = h->t_select_ms;
+        h->stats.prep_ms = h->t_prep_ms;
+        h->stats.contract_ms = h->t_contract_ms;
+        h->stats.update_ms = h->t_update_ms;
+        h->stats.postprocess_ms = h->t_post_ms;
+        h->stats.witness_ms = h->t_witness_ms;
+        h->stats.witness_launches = h->witness_launches;
+        h->stats.witness_bytes = h->witness_bytes;
+    });
+    if (rc != CH_OK) {
+        delete h;
+        cudaGetLastError();
+        return rc;
+    }
+    *out = h;
+    return CH_OK;
+}
+
+int ch_query_batch(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                   uint32_t *dist_out, uint32_t *settled_out, void *stream) {
+    if (!ch) {
+        g_last_error = "null handle";
+        return CH_EINVAL;
+    }
+    if (k == 0) return CH_OK;
+    if (!src || !dst || !dist_out) {
+        g_last_error = "null query array";
+        return CH_EINVAL;
+    }
+    return guarded([&] {
+        query_batch(ch, src, dst, k, dist_out, settled_out, (cudaStream_t)stream);
+    });
+}
+
+int ch_query_status(ch_t *ch, void *stream) {
+    if (!ch) {
+        g_last_error = "null handle";
+        return CH_EINVAL;
+    }
+    uint32_t err = 0;
+    int rc = guarded([&] {
+        cudaStream_t st = (cudaStream_t)stream;
+        CH_CUDA_TRY(cudaMemcpyAsync(&err, ch->qerr.ptr, 4, cudaMemcpyDeviceToHost, st));
+        CH_CUDA_TRY(cudaStreamSynchronize(st));
+        if (err) CH_CUDA_TRY(cudaMemsetAsync(ch->qerr.ptr, 0, 4, st));
+        CH_CUDA_TRY(cudaStreamSynchronize(st));
+    });
+    if (rc != CH_OK) return rc;
+    if (err) {
+        g_last_error = "query vertex id out of range";
+        return CH_EINVAL;
+    }
+    return CH_OK;
+}
+
+int ch_query_batch_host(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                        uint32_t *dist_out, uint32_t *settled_out) {
+    if (!ch) {
+        g_last_error = "null handle";
+        return CH_EINVAL;
+    }
+    if (k == 0) return CH_OK;
+    if (!src || !dst || !dist_out) {
+        g_last_error = "null query array";
+        return CH_EINVAL;
+    }
+    int rc = guarded([&] {
+        DevBuf<uint32_t> buf;
+        buf.alloc(k * (settled_out ? 4 : 3));
+        uint32_t *ds = buf.ptr, *dt = buf.ptr + k, *dd = buf.ptr + 2 * k;
+        uint32_t *dset = settled_out ? buf.ptr + 3 * k : nullptr;
+        cudaStream_t st = nullptr;
+        CH_CUDA_TRY(cudaMemcpyAsync(ds, src, k * 4, cudaMemcpyHostToDevice, st));
+        CH_CUDA_TRY(cudaMemcpyAsync(dt, dst, k * 4, cudaMemcpyHostToDevice, st));
+        query_batch(ch, ds, dt, k, dd, dset, st);
+        CH_CUDA_TRY(cudaMemcpyAsync(dist_out, dd, k * 4, cudaMemcpyDeviceToHost, st));
+        if (dset)
+            CH_CUDA_TRY(cudaMemcpyAsync(settled_out, dset, k * 4, cudaMemcpyDeviceToHost, st));
+        CH_CUDA_TRY(cudaStreamSynchronize(st));
+    });
+    if (rc != CH_OK) return rc;
+    return ch_query_status(ch, nullptr);
+}
+
+int ch_get_stats(const ch_t *ch, ch_stats_t *out) {
+    if (!ch || !out) {
+        g_last_error = "null argument";
+        return CH_EINVAL;
+    }
+    *out = ch->stats;
+    return CH_OK;
+}
+
+int ch_get_round_stats(const ch_t *ch, uint64_t *out, uint32_t max_rounds) {
+    if (!ch || (!out && max_rounds)) {
+        g_last_error = "null argument";
+        return CH_EINVAL;
+    }
+    const uint32_t r = std::min<uint32_t>(max_rounds, (uint32_t)ch->round_stats.size());
+    for (uint32_t i = 0; i < r; ++i)
+        for (uint32_t f = 0; f < CH_NSTAT; ++f) out[(size_t)i * CH_NSTAT + f] = ch->round_stats[i][f];
+    return CH_OK;
+}
+
+int ch_export(const ch_t *ch, uint32_t *level, int32_t *priority, uint32_t *rank,
+              uint32_t *shortcuts, uint32_t *up, uint32_t *down) {
+    if (!ch) {
+        g_last_error = "null handle";
+        return CH_EINVAL;
+    }
+    return guarded([&] {
+        const uint32_t n = ch->n;
+        if (level && n) CH_CUDA_TRY(cudaMemcpy(level, ch->level.ptr, n * 4ull, cudaMemcpyDeviceToHost));
+        if (priority && n) CH_CUDA_TRY(cudaMemcpy(priority, ch->prio.ptr, n * 4ull, cudaMemcpyDeviceToHost));
+        if (rank && n) CH_CUDA_TRY(cudaMemcpy(rank, ch->rank.ptr, n * 4ull, cudaMemcpyDeviceToHost));
+        if (shortcuts && ch->n_shortcuts) {
+            const uint64_t k = ch->n_shortcuts;
+            std::vector<uint4> sc(k);
+            std::vector<uint32_t> rr(k);
+            CH_CUDA_TRY(cudaMemcpy(sc.data(), ch->sc.ptr, k * sizeof(uint4), cudaMemcpyDeviceToHost));
+            CH_CUDA_TRY(cudaMemcpy(rr.data(), ch->sc_round.ptr, k * 4, cudaMemcpyDeviceToHost));
+            std::vector<uint64_t> idx(k);
+            std::iota(idx.begin(), idx.end(), 0);
+            std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t b) {
+                return std::make_tuple(rr[a], sc[a].x, sc[a].y) < std::make_tuple(rr[b], sc[b].x, sc[b].y);
+            });
+            for (uint64_t i = 0; i < k; ++i) {
+                const uint4 &c = sc[idx[i]];
+                uint32_t *o = shortcuts + 5 * i;
+                o[0] = rr[idx[i]];
+                o[1] = c.x;
+                o[2] = c.y;
+                o[3] = c.z;
+                o[4] = c.w;
+            }
+        }
+        for (int dir = 0; dir < 2; ++dir) {
+            uint32_t *dst = dir == 0 ? up : down;
+            const uint64_t cnt = dir == 0 ? ch->n_up : ch->n_down;
+            if (!dst || !cnt) continue;
+            std::vector<uint32_t> off(n + 1), perm(n);
+            std::vector<uint2> adj(cnt);
+            CH_CUDA_TRY(cudaMemcpy(off.data(), (dir == 0 ? ch->up_off : ch->dn_off).ptr, (n + 1ull) * 4,
+                                   cudaMemcpyDeviceToHost));
+            CH_CUDA_TRY(cudaMemcpy(adj.data(), (dir == 0 ? ch->up_adj : ch->dn_adj).ptr,
+                                   cnt * sizeof(uint2), cudaMemcpyDeviceToHost));
+            CH_CUDA_TRY(cudaMemcpy(perm.data(), ch->perm.ptr, n * 4ull, cudaMemcpyDeviceToHost));
+            // rows (lower endpoint u, other endpoint x, w), sorted by (u, x)
+            std::vector<std::array<uint32_t, 3>> rows;
+            rows.reserve(cnt);
+            for (uint32_t i = 0; i < n; ++i)
+                for (uint32_t j = off[i]; j < off[i + 1]; ++j)
+                    rows.push_back({perm[i], perm[adj[j].x], adj[j].y});
+            std::sort(rows.begin(), rows.end());
+            for (uint64_t i = 0; i < cnt; ++i) {
+                uint32_t *o = dst + 3 * i;
+                if (dir == 0) {
+                    o[0] = rows[i][0];
+                    o[1] = rows[i][1];
+                } else {
+                    o[0] = rows[i][1];
+                    o[1] = rows[i][0];
+                }
+                o[2] = rows[i][2];
+            }
+        }
+    });
+}
+
+void ch_free(ch_t *ch) { delete ch; }
+
+}  // extern "C"

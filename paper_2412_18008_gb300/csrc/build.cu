@@ -1,0 +1,1514 @@
+// Round-synchronous contraction-hierarchy construction on one GPU.
+//
+// Paper: "Parallel Contraction Hierarchies Can Be Efficient and Scalable"
+// (arXiv 2412.18008), Alg. 2 (round loop), Alg. 3 (LocalSearch, batched per
+// source), Alg. 4 (Score = edge difference), Alg. 5 (Select = strict local
+// minimum of the score, ties by label), Alg. 6 (Contract), Sec. 4 (overlay in
+// CSR form, duplicate shortcuts keep the minimum weight) and the
+// Postprocess paragraph of Sec. 4 (vertices ranked by level, then score).
+//
+// GPU design (one round = the steps below, one host synchronisation):
+//   1 score_prep     A_r: P[u] = -(|N_in|+|N_out|); sources N_in(A_r) listed
+//   2 witness SCORE  one warp per source s: hop-limited Bellman-Ford from s
+//                    in shared memory, then every pair (s, u, v2) with u in
+//                    A_r adds 1 to P[u] when w(s,u)+w(u,v2) <= d_H(s, v2)
+//   3 select         V_F = strict local minima of key(u) = (P[u], tie(u))
+//   4 contract_prep  sources N_in(V_F), next affected set N(V_F), bounds
+//   -- host reads the round's counters once and grows buffers if needed --
+//   5 witness PRUNE  same search; kept candidates merged per (s, v2) in
+//                    shared memory (min weight, then min via) and checked
+//                    against the existing overlay edge
+//   6 emit_ch        out/in lists of V_F become E_up / E_down
+//   7 compact_lists  neighbour lists of N(V_F) drop the contracted vertices
+//   8 reserve        lists short of slack are moved by a prefix sum over
+//                    their new capacities
+//   9 insert         shortcuts appended into the slack (or weights lowered)
+//  10 compact VO     stable compaction of the live-vertex list
+//
+// The witness distance is d_H(a, b), the least weight of a walk a -> b with
+// at most H edges in the round's overlay (INF if none); a candidate
+// (v1, u, v2), v1 != v2, is kept iff w(v1,u) + w(u,v2) <= d_H(v1, v2). Each
+// search keeps only partial walks lighter than the heaviest candidate
+// weight of its source, which leaves every decision unchanged: a walk at
+// least that heavy can only show d_H >= the candidate's weight.
+//
+// Everything the kernels compute is a function of the overlay's edge *sets*
+// (searches take minima, selection compares keys, merges take minima), so
+// results do not depend on the order in which atomics append to lists.
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "handle.cuh"
+#include "prims.cuh"
+
+namespace gbch {
+namespace {
+
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+constexpr uint32_t ERR_INPUT = 1u;
+constexpr uint32_t ERR_REC_OVERFLOW = 2u;
+constexpr uint32_t ERR_CH_OVERFLOW = 4u;
+
+constexpr int MODE_SCORE = 0;
+constexpr int MODE_PRUNE = 1;
+
+// Shared-memory search state of one warp.
+constexpr int WIT_WARPS = 4;       // warps per block
+constexpr int WIT_TBITS = 8;       // hash table of 2^8 vertices
+constexpr int WIT_T = 1 << WIT_TBITS;
+constexpr int WIT_FC = 128;        // frontier capacity per level
+constexpr int WIT_MC = 128;        // distinct targets merged per source
+
+struct Ctl {
+    uint32_t nVO, nVO2, nS, nS2, nF, nAnext, nOvf, nRec;
+    uint32_t err, work, work2, pad;
+    unsigned long long candBound, degFout, degFin, degAnext;
+    unsigned long long cand, kept, merged, inserted, newEdges;
+    unsigned long long out_tail, in_tail, ch_up_tail, ch_dn_tail;
+    unsigned long long relocOut, relocIn;
+    unsigned long long wit_sources, wit_fallback, wit_vertices, wit_edges, wit_middles,
+        wit_midedges;
+};
+
+struct Dev {
+    uint32_t n;
+    uint32_t H;
+    uint32_t tie_mode, tie_seed;
+    uint64_t *out_beg, *in_beg;
+    uint32_t *out_deg, *in_deg, *out_cap, *in_cap;
+    uint2 *out_adj, *in_adj;
+    uint32_t *level;
+    int32_t *P;
+    uint32_t *amark, *smark;
+    uint32_t *new_out, *new_in;
+    Ctl *ctl;
+};
+
+struct WArgs {
+    Dev d;
+    const uint32_t *S;       // source list
+    const uint32_t *nS;      // its length (device)
+    uint32_t *work;          // dynamic work counter
+    uint32_t round;
+    uint32_t *ovf;           // overflowed sources
+    uint4 *rec;              // PRUNE: shortcut records (v1, v2, w, via)
+    uint8_t *rec_flag;       // PRUNE: 1 = lowers an existing edge
+    uint64_t rec_cap;
+};
+
+struct Dense {
+    uint32_t *dist, *fst, *fa, *fb, *fda, *fdb, *touched, *mt;
+    unsigned long long *merge;
+    uint32_t nslots;
+};
+
+__device__ __forceinline__ uint64_t select_key(const Dev &d, uint32_t v) {
+    uint32_t hi = (uint32_t)d.P[v] ^ 0x80000000u;
+    uint32_t lo = d.tie_mode == CH_TIE_ID ? v : murmur_fmix32(v ^ d.tie_seed);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+template <int MODE>
+__device__ __forceinline__ bool is_middle(const Dev &d, uint32_t u, uint32_t r) {
+    if (MODE == MODE_SCORE) return d.amark[u] == r;
+    return d.level[u] == r;
+}
+
+__device__ __forceinline__ uint32_t lane_bits(uint32_t lo, uint32_t hi) {
+    uint32_t h = hi >= 32 ? FULL : ((1u << hi) - 1u);
+    return h & ~((1u << lo) - 1u);
+}
+
+// --------------------------------------------------------------------------
+// Normalisation (drop self-loops, merge parallel edges by minimum weight)
+// --------------------------------------------------------------------------
+
+__global__ void k_validate_offsets(const uint64_t *off, uint32_t n, uint64_t m, Ctl *ctl) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += gridDim.x * blockDim.x) {
+        bool bad = off[i] > off[i + 1];
+        if (i == 0 && off[0] != 0) bad = true;
+        if (i == n - 1 && off[n] != m) bad = true;
+        if (bad) atomicOr(&ctl->err, ERR_INPUT);
+    }
+}
+
+__global__ void k_edge_keys(const uint64_t *off, const uint32_t *tgt, const uint32_t *w,
+                            uint32_t n, uint64_t m, uint64_t *keys, uint32_t *vals, Ctl *ctl) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = n;  // largest u with off[u] <= e
+        while (hi - lo > 1) {
+            uint32_t mid = lo + (hi - lo) / 2;
+            if (off[mid] <= e) lo = mid; else hi = mid;
+        }
+        uint32_t v = tgt[e], ww = w[e];
+        if (v >= n || ww == 0 || ww == INF) atomicOr(&ctl->err, ERR_INPUT);
+        keys[e] = ((uint64_t)lo << 32) | (v < n ? v : 0);
+        vals[e] = ww;
+    }
+}
+
+__global__ void k_norm_flags(const uint64_t *keys, uint64_t m, uint32_t *flag) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[e];
+        bool head = e == 0 || keys[e - 1] != k;
+        flag[e] = head && (uint32_t)(k >> 32) != (uint32_t)k ? 1u : 0u;
+    }
+}
+
+__global__ void k_norm_scatter(const uint64_t *keys, const uint32_t *vals, uint64_t m,
+                               const uint32_t *pos, uint64_t *okeys, uint32_t *ovals) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[e];
+        bool head = e == 0 || keys[e - 1] != k;
+        if (!head || (uint32_t)(k >> 32) == (uint32_t)k) continue;
+        uint32_t ww = vals[e];
+        for (uint64_t f = e + 1; f < m && keys[f] == k; ++f) ww = min(ww, vals[f]);
+        okeys[pos[e]] = k;
+        ovals[pos[e]] = ww;
+    }
+}
+
+__global__ void k_swap_key_halves(uint64_t *keys, uint64_t m) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[e];
+        keys[e] = (k << 32) | (k >> 32);
+    }
+}
+
+// Degrees and segment starts of a (u, v)-sorted edge list keyed by u.
+__global__ void k_seg_heads(const uint64_t *keys, uint64_t m, uint64_t *first) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = (uint32_t)(keys[e] >> 32);
+        if (e == 0 || (uint32_t)(keys[e - 1] >> 32) != u) first[u] = e;
+    }
+}
+
+__global__ void k_seg_deg(const uint64_t *keys, uint64_t m, const uint64_t *first,
+                          uint32_t *deg) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = (uint32_t)(keys[e] >> 32);
+        if (e + 1 == m || (uint32_t)(keys[e + 1] >> 32) != u) deg[u] = (uint32_t)(e + 1 - first[u]);
+    }
+}
+
+__host__ __device__ __forceinline__ uint32_t initial_cap(uint32_t deg) {
+    return deg < 2 ? deg + 2 : 2 * deg;
+}
+
+__global__ void k_caps(const uint32_t *deg, uint32_t n, uint32_t *cap, uint64_t *cap64) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        uint32_t c = initial_cap(deg[v]);
+        cap[v] = c;
+        cap64[v] = c;
+    }
+}
+
+__global__ void k_fill_adj(const uint64_t *keys, const uint32_t *vals, uint64_t m,
+                           const uint64_t *first, const uint64_t *beg, uint2 *adj) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = (uint32_t)(keys[e] >> 32);
+        adj[beg[u] + (e - first[u])] = make_uint2((uint32_t)keys[e], vals[e]);
+    }
+}
+
+__global__ void k_iota(uint32_t *a, uint32_t n) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        a[v] = v;
+}
+
+// --------------------------------------------------------------------------
+// Step 1: rescoring set and witness sources
+// --------------------------------------------------------------------------
+
+__global__ void k_score_prep(Dev d, const uint32_t *A, uint32_t nA, uint32_t stamp,
+                             uint32_t *S) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nA;
+         i += gridDim.x * blockDim.x) {
+        uint32_t u = A[i];
+        uint32_t od = d.out_deg[u], id = d.in_deg[u];
+        d.P[u] = -(int32_t)(od + id);
+        uint64_t ib = d.in_beg[u];
+        for (uint32_t j = 0; j < id; ++j) {
+            uint32_t v1 = d.in_adj[ib + j].x;
+            if (atomicExch(&d.smark[v1], stamp) != stamp) S[atomicAdd(&d.ctl->nS, 1u)] = v1;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Steps 2 and 5: witness searches, one warp per source
+// --------------------------------------------------------------------------
+
+struct WarpSmem {
+    uint32_t key[WIT_T];
+    uint32_t val[WIT_T];
+    uint32_t fst[WIT_T];
+    uint2 front[2][WIT_FC];
+    uint32_t mkey[WIT_MC];
+    unsigned long long mval[WIT_MC];
+    uint32_t cnt[32];
+    uint32_t nf[2];
+    uint32_t flag;
+};
+
+__device__ __forceinline__ uint32_t ht_hash(uint32_t v, int bits) {
+    return (v * 2654435761u) >> (32 - bits);
+}
+
+// Slot of v in an open-addressing table (inserting it if absent), or EMPTY
+// when the table is full.
+__device__ __forceinline__ uint32_t ht_insert(uint32_t *keys, int bits, uint32_t v) {
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t h = ht_hash(v, bits);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        uint32_t k = keys[h];
+        if (k == v) return h;
+        if (k == EMPTY) {
+            uint32_t old = atomicCAS(&keys[h], EMPTY, v);
+            if (old == EMPTY || old == v) return h;
+        }
+        h = (h + 1) & mask;
+    }
+    return EMPTY;
+}
+
+__device__ __forceinline__ uint32_t ht_find(const uint32_t *keys, int bits, uint32_t v) {
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t h = ht_hash(v, bits);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        uint32_t k = keys[h];
+        if (k == v) return h;
+        if (k == EMPTY) return EMPTY;
+        h = (h + 1) & mask;
+    }
+    return EMPTY;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
+    __shared__ WarpSmem smem[WIT_WARPS];
+    WarpSmem &w = smem[threadIdx.x >> 5];
+    const uint32_t lane = lane_id();
+    const Dev d = a.d;
+    Ctl *ctl = d.ctl;
+    const uint32_t nS = *a.nS;
+    const uint32_t r = a.round;
+    unsigned long long c_src = 0, c_vert = 0, c_edge = 0, c_mid = 0, c_midedge = 0;
+    unsigned long long c_cand = 0, c_kept = 0, c_merged = 0, c_ins = 0, c_new = 0;
+
+    while (true) {
+        uint32_t i = 0;
+        if (lane == 0) i = atomicAdd(a.work, 1u);
+        i = __shfl_sync(FULL, i, 0);
+        if (i >= nS) break;
+        const uint32_t s = a.S[i];
+        const uint64_t sb = d.out_beg[s];
+        const uint32_t sd = d.out_deg[s];
+        c_src += (lane == 0);
+
+        // Phase 0: heaviest candidate weight of this source.
+        uint32_t bound = 0;
+        for (uint32_t c0 = 0; c0 < sd; c0 += 32) {
+            const uint32_t j = c0 + lane;
+            const bool valid = j < sd;
+            const uint2 e = valid ? d.out_adj[sb + j] : make_uint2(0, 0);
+            const bool mid = valid && is_middle<MODE>(d, e.x, r);
+            const uint32_t cnt = mid ? d.out_deg[e.x] : 0;
+            const uint64_t ub = mid ? d.out_beg[e.x] : 0;
+            c_mid += mid;
+            c_midedge += cnt;
+            const uint32_t incl = warp_incl_scan(cnt);
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            const uint32_t excl = incl - cnt;
+            for (uint32_t b = 0; b < total; b += 32) {
+                const uint32_t idx = b + lane;
+                const uint32_t o = warp_owner(excl, idx);
+                const uint64_t ub_o = __shfl_sync(FULL, ub, o);
+                const uint32_t w1 = __shfl_sync(FULL, e.y, o);
+                const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                if (idx < total) {
+                    const uint2 e2 = d.out_adj[ub_o + (idx - ex_o)];
+                    if (e2.x != s) bound = max(bound, sat_add(w1, e2.y));
+                }
+            }
+        }
+        bound = warp_max(bound);
+        if (bound == 0) continue;  // no candidate pair from this source
+
+        // Phase 1: hop-limited Bellman-Ford from s, levels 1..H, each level
+        // relaxing from the previous level's values (frontier snapshots).
+        for (uint32_t t = lane; t < WIT_T; t += 32) {
+            w.key[t] = EMPTY;
+            w.val[t] = INF;
+            w.fst[t] = 0;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const uint32_t h = ht_hash(s, WIT_TBITS);
+            w.key[h] = s;
+            w.val[h] = 0;
+            w.front[0][0] = make_uint2(h, 0);
+            w.nf[0] = 1;
+            w.nf[1] = 0;
+            w.flag = 0;
+        }
+        __syncwarp();
+        uint32_t cur = 0;
+        for (uint32_t lvl = 1; lvl <= d.H; ++lvl) {
+            const uint32_t nfront = w.nf[cur];
+            const uint32_t nxt = cur ^ 1u;
+            __syncwarp();
+            if (lane == 0) w.nf[nxt] = 0;
+            __syncwarp();
+            for (uint32_t f0 = 0; f0 < nfront; f0 += 32) {
+                const uint32_t fi = f0 + lane;
+                const bool fv = fi < nfront;
+                const uint2 fe = fv ? w.front[cur][fi] : make_uint2(0, 0);
+                const uint32_t x = fv ? w.key[fe.x] : 0;
+                const uint32_t cnt = fv ? d.out_deg[x] : 0;
+                const uint64_t xb = fv ? d.out_beg[x] : 0;
+                c_vert += fv;
+                c_edge += cnt;
+                const uint32_t incl = warp_incl_scan(cnt);
+                const uint32_t total = __shfl_sync(FULL, incl, 31);
+                const uint32_t excl = incl - cnt;
+                for (uint32_t b = 0; b < total; b += 32) {
+                    const uint32_t idx = b + lane;
+                    const uint32_t o = warp_owner(excl, idx);
+                    const uint64_t xb_o = __shfl_sync(FULL, xb, o);
+                    const uint32_t dx_o = __shfl_sync(FULL, fe.y, o);
+                    const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                    if (idx < total) {
+                        const uint2 e = d.out_adj[xb_o + (idx - ex_o)];
+                        const uint32_t nd = sat_add(dx_o, e.y);
+                        if (nd < bound) {
+                            const uint32_t slot = ht_insert(w.key, WIT_TBITS, e.x);
+                            if (slot == EMPTY) {
+                                w.flag = 1;
+                            } else {
+                                const uint32_t old = atomicMin(&w.val[slot], nd);
+                                if (nd < old && atomicExch(&w.fst[slot], lvl) != lvl) {
+                                    const uint32_t p = atomicAdd(&w.nf[nxt], 1u);
+                                    if (p < WIT_FC) w.front[nxt][p] = make_uint2(slot, 0);
+                                    else w.flag = 1;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (w.flag) break;
+            const uint32_t nn = w.nf[nxt];
+            for (uint32_t p = lane; p < nn; p += 32) w.front[nxt][p].y = w.val[w.front[nxt][p].x];
+            __syncwarp();
+            cur = nxt;
+            if (nn == 0) break;
+        }
+        __syncwarp();
+        if (w.flag) {
+            if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
+            continue;
+        }
+
+        // Phase 2: decisions for every candidate (s, u, v2).
+        if (MODE == MODE_PRUNE) {
+            for (uint32_t t = lane; t < WIT_MC; t += 32) {
+                w.mkey[t] = EMPTY;
+                w.mval[t] = ~0ull;
+            }
+        }
+        __syncwarp();
+        uint32_t l_cand = 0, l_kept = 0;
+        for (uint32_t c0 = 0; c0 < sd; c0 += 32) {
+            const uint32_t j = c0 + lane;
+            const bool valid = j < sd;
+            const uint2 e = valid ? d.out_adj[sb + j] : make_uint2(0, 0);
+            const bool mid = valid && is_middle<MODE>(d, e.x, r);
+            const uint32_t cnt = mid ? d.out_deg[e.x] : 0;
+            const uint64_t ub = mid ? d.out_beg[e.x] : 0;
+            const uint32_t incl = warp_incl_scan(cnt);
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            const uint32_t excl = incl - cnt;
+            if (MODE == MODE_SCORE) w.cnt[lane] = 0;
+            __syncwarp();
+            for (uint32_t b = 0; b < total; b += 32) {
+                const uint32_t idx = b + lane;
+                const uint32_t o = warp_owner(excl, idx);
+                const uint64_t ub_o = __shfl_sync(FULL, ub, o);
+                const uint32_t w1 = __shfl_sync(FULL, e.y, o);
+                const uint32_t u_o = __shfl_sync(FULL, e.x, o);
+                const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                if (idx < total) {
+                    const uint2 e2 = d.out_adj[ub_o + (idx - ex_o)];
+                    if (e2.x != s) {
+                        const uint32_t via = sat_add(w1, e2.y);
+                        const uint32_t slot = ht_find(w.key, WIT_TBITS, e2.x);
+                        const uint32_t dh = slot == EMPTY ? INF : w.val[slot];
+                        ++l_cand;
+                        if (via != INF && via <= dh) {
+                            ++l_kept;
+                            if (MODE == MODE_SCORE) {
+                                atomicAdd(&w.cnt[o], 1u);
+                            } else {
+                                const uint32_t ms = ht_insert(w.mkey, 7, e2.x);
+                                if (ms == EMPTY) w.flag = 1;
+                                else atomicMin(&w.mval[ms], ((unsigned long long)via << 32) | u_o);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (MODE == MODE_SCORE && mid && w.cnt[lane]) atomicAdd(&d.P[e.x], (int32_t)w.cnt[lane]);
+            __syncwarp();
+        }
+        if (MODE == MODE_PRUNE) {
+            __syncwarp();
+            if (w.flag) {
+                if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
+                continue;
+            }
+            c_cand += l_cand;
+            c_kept += l_kept;
+            uint32_t l_new = 0;
+            for (uint32_t t0 = 0; t0 < WIT_MC; t0 += 32) {
+                const uint32_t t = t0 + lane;
+                const uint32_t v2 = w.mkey[t];
+                const bool have = v2 != EMPTY;
+                const unsigned long long mv = w.mval[t];
+                const uint32_t ws = (uint32_t)(mv >> 32), via = (uint32_t)mv;
+                bool found = false;
+                uint32_t ew = INF;
+                if (have) {
+                    for (uint32_t j = 0; j < sd; ++j) {
+                        const uint2 e = d.out_adj[sb + j];
+                        if (e.x == v2) {
+                            found = true;
+                            ew = e.y;
+                            break;
+                        }
+                    }
+                }
+                const bool emit = have && (!found || ws < ew);
+                c_merged += have;
+                const uint32_t pos = warp_append(emit, &ctl->nRec);
+                if (emit) {
+                    if (pos < a.rec_cap) {
+                        a.rec[pos] = make_uint4(s, v2, ws, via);
+                        a.rec_flag[pos] = found ? 1 : 0;
+                    } else {
+                        atomicOr(&ctl->err, ERR_REC_OVERFLOW);
+                    }
+                    if (!found) atomicAdd(&d.new_in[v2], 1u);
+                    ++c_ins;
+                    if (!found) ++l_new;
+                }
+            }
+            const uint32_t tot_new = warp_sum(l_new);
+            c_new += l_new;
+            if (lane == 0) d.new_out[s] = tot_new;
+            __syncwarp();
+        }
+    }
+    // Counters (lane-local sums folded per warp).
+    c_src = warp_sum((uint32_t)c_src);
+#define FOLD64(x)                                                               \
+    {                                                                           \
+        unsigned long long v_ = x;                                              \
+        for (int o_ = 16; o_ > 0; o_ >>= 1) v_ += __shfl_xor_sync(FULL, v_, o_); \
+        x = v_;                                                                 \
+    }
+    FOLD64(c_vert) FOLD64(c_edge) FOLD64(c_mid) FOLD64(c_midedge) FOLD64(c_cand)
+    FOLD64(c_kept) FOLD64(c_merged) FOLD64(c_ins) FOLD64(c_new)
+#undef FOLD64
+    if (lane == 0) {
+        atomicAdd(&ctl->wit_sources, c_src);
+        atomicAdd(&ctl->wit_vertices, c_vert);
+        atomicAdd(&ctl->wit_edges, c_edge);
+        atomicAdd(&ctl->wit_middles, c_mid);
+        atomicAdd(&ctl->wit_midedges, c_midedge);
+        if (MODE == MODE_PRUNE) {
+            atomicAdd(&ctl->cand, c_cand);
+            atomicAdd(&ctl->kept, c_kept);
+            atomicAdd(&ctl->merged, c_merged);
+            atomicAdd(&ctl->inserted, c_ins);
+            atomicAdd(&ctl->newEdges, c_new);
+        }
+    }
+}
+
+// Same search for the sources whose ball overflowed shared memory: one block
+// per slot of dense per-vertex arrays in global memory (no capacity limit).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
+    const Dev d = a.d;
+    Ctl *ctl = d.ctl;
+    const uint32_t n = d.n;
+    const uint32_t r = a.round;
+    const size_t base = (size_t)blockIdx.x * n;
+    uint32_t *dist = dn.dist + base, *fst = dn.fst + base, *touched = dn.touched + base;
+    uint32_t *fa = dn.fa + base, *fb = dn.fb + base, *fda = dn.fda + base, *fdb = dn.fdb + base;
+    uint32_t *mt = dn.mt + base;
+    unsigned long long *merge = dn.merge + base;
+    __shared__ uint32_t s_item, s_bound, s_nt, s_nm, s_nf[2];
+    __shared__ unsigned long long s_cnt[5];
+    const uint32_t tid = threadIdx.x;
+    const uint32_t nOvf = ctl->nOvf;
+    while (true) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(&ctl->work2, 1u);
+        if (tid < 5) s_cnt[tid] = 0;
+        __syncthreads();
+        const uint32_t i = s_item;
+        if (i >= nOvf) break;
+        const uint32_t s = a.ovf[i];
+        const uint64_t sb = d.out_beg[s];
+        const uint32_t sd = d.out_deg[s];
+        if (tid == 0) {
+            s_bound = 0;
+            s_nt = 1;
+            s_nm = 0;
+            s_nf[0] = 1;
+            s_nf[1] = 0;
+            dist[s] = 0;
+            touched[0] = s;
+            fa[0] = s;
+            fda[0] = 0;
+            atomicAdd(&ctl->wit_fallback, 1ull);
+        }
+        __syncthreads();
+        for (uint32_t j = tid; j < sd; j += blockDim.x) {
+            const uint2 e = d.out_adj[sb + j];
+            if (!is_middle<MODE>(d, e.x, r)) continue;
+            const uint64_t ub = d.out_beg[e.x];
+            const uint32_t ud = d.out_deg[e.x];
+            uint32_t bmax = 0;
+            for (uint32_t jj = 0; jj < ud; ++jj) {
+                const uint2 e2 = d.out_adj[ub + jj];
+                if (e2.x != s) bmax = max(bmax, sat_add(e.y, e2.y));
+            }
+            atomicMax(&s_bound, bmax);
+        }
+        __syncthreads();
+        const uint32_t bound = s_bound;
+        uint32_t *cur = fa, *curd = fda, *nx = fb, *nxd = fdb;
+        for (uint32_t lvl = 1; lvl <= d.H && bound > 0; ++lvl) {
+            const uint32_t nf = s_nf[(lvl - 1) & 1];
+            __syncthreads();
+            if (tid == 0) s_nf[lvl & 1] = 0;
+            __syncthreads();
+            for (uint32_t f = tid; f < nf; f += blockDim.x) {
+                const uint32_t x = cur[f], dx = curd[f];
+                const uint64_t xb = d.out_beg[x];
+                const uint32_t xd = d.out_deg[x];
+                for (uint32_t j = 0; j < xd; ++j) {
+                    const uint2 e = d.out_adj[xb + j];
+                    const uint32_t nd = sat_add(dx, e.y);
+                    if (nd >= bound) continue;
+                    const uint32_t old = atomicMin(&dist[e.x], nd);
+                    if (nd < old) {
+                        if (old == INF) touched[atomicAdd(&s_nt, 1u)] = e.x;
+                        if (atomicExch(&fst[e.x], lvl) != lvl) nx[atomicAdd(&s_nf[lvl & 1], 1u)] = e.x;
+                    }
+                }
+            }
+            __syncthreads();
+            const uint32_t nn = s_nf[lvl & 1];
+            for (uint32_t p = tid; p < nn; p += blockDim.x) nxd[p] = dist[nx[p]];
+            __syncthreads();
+            uint32_t *t1 = cur, *t2 = curd;
+            cur = nx;
+            curd = nxd;
+            nx = t1;
+            nxd = t2;
+            if (nn == 0) break;
+        }
+        // decisions
+        unsigned long long l_cand = 0, l_kept = 0;
+        for (uint32_t j = tid; j < sd; j += blockDim.x) {
+            const uint2 e = d.out_adj[sb + j];
+            if (!is_middle<MODE>(d, e.x, r)) continue;
+            const uint64_t ub = d.out_beg[e.x];
+            const uint32_t ud = d.out_deg[e.x];
+            int32_t kept_u = 0;
+            for (uint32_t jj = 0; jj < ud; ++jj) {
+                const uint2 e2 = d.out_adj[ub + jj];
+                if (e2.x == s) continue;
+                const uint32_t via = sat_add(e.y, e2.y);
+                const uint32_t dh = dist[e2.x];
+                ++l_cand;
+                if (via != INF && via <= dh) {
+                    ++l_kept;
+                    ++kept_u;
+                    if (MODE == MODE_PRUNE) {
+                        const unsigned long long old =
+                            atomicMin(&merge[e2.x], ((unsigned long long)via << 32) | e.x);
+                        if (old == ~0ull) mt[atomicAdd(&s_nm, 1u)] = e2.x;
+                    }
+                }
+            }
+            if (MODE == MODE_SCORE && kept_u) atomicAdd(&d.P[e.x], kept_u);
+        }
+        __syncthreads();
+        if (MODE == MODE_PRUNE) {
+            atomicAdd(&s_cnt[0], l_cand);
+            atomicAdd(&s_cnt[1], l_kept);
+            const uint32_t nm = s_nm;
+            unsigned long long l_ins = 0, l_new = 0;
+            for (uint32_t p = tid; p < nm; p += blockDim.x) {
+                const uint32_t v2 = mt[p];
+                const unsigned long long mv = merge[v2];
+                merge[v2] = ~0ull;
+                const uint32_t ws = (uint32_t)(mv >> 32), via = (uint32_t)mv;
+                bool found = false;
+                uint32_t ew = INF;
+                for (uint32_t j = 0; j < sd; ++j) {
+                    const uint2 e = d.out_adj[sb + j];
+                    if (e.x == v2) {
+                        found = true;
+                        ew = e.y;
+                        break;
+                    }
+                }
+                if (found && !(ws < ew)) continue;
+                const uint32_t pos = atomicAdd(&ctl->nRec, 1u);
+                if (pos < a.rec_cap) {
+                    a.rec[pos] = make_uint4(s, v2, ws, via);
+                    a.rec_flag[pos] = found ? 1 : 0;
+                } else {
+                    atomicOr(&ctl->err, ERR_REC_OVERFLOW);
+                }
+                ++l_ins;
+                if (!found) {
+                    ++l_new;
+                    atomicAdd(&d.new_in[v2], 1u);
+                }
+            }
+            atomicAdd(&s_cnt[2], l_ins);
+            atomicAdd(&s_cnt[3], l_new);
+            __syncthreads();
+            if (tid == 0) {
+                atomicAdd(&ctl->cand, s_cnt[0]);
+                atomicAdd(&ctl->kept, s_cnt[1]);
+                atomicAdd(&ctl->merged, (unsigned long long)nm);
+                atomicAdd(&ctl->inserted, s_cnt[2]);
+                atomicAdd(&ctl->newEdges, s_cnt[3]);
+                d.new_out[s] = (uint32_t)s_cnt[3];
+            }
+        }
+        __syncthreads();
+        const uint32_t nt = s_nt;
+        for (uint32_t p = tid; p < nt; p += blockDim.x) {
+            const uint32_t v = touched[p];
+            dist[v] = INF;
+            fst[v] = 0;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Step 3: select strict local minima of the key
+// --------------------------------------------------------------------------
+
+__global__ void k_select(Dev d, const uint32_t *VO, uint32_t nVO, uint32_t r, uint32_t *F) {
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = warp * 32; base < nVO; base += nwarps * 32) {
+        const uint32_t i = base + lane;
+        const bool valid = i < nVO;
+        const uint32_t u = valid ? VO[i] : 0;
+        const uint64_t ku = valid ? select_key(d, u) : 0;
+        const uint32_t od = valid ? d.out_deg[u] : 0;
+        const uint32_t id = valid ? d.in_deg[u] : 0;
+        const uint64_t ob = valid ? d.out_beg[u] : 0;
+        const uint64_t ib = valid ? d.in_beg[u] : 0;
+        const uint32_t c = od + id;
+        const uint32_t incl = warp_incl_scan(c);
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        const uint32_t excl = incl - c;
+        bool beaten = false;
+        for (uint32_t b = 0; b < total; b += 32) {
+            const uint32_t idx = b + lane;
+            const uint32_t o = warp_owner(excl, idx);
+            const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+            const uint32_t od_o = __shfl_sync(FULL, od, o);
+            const uint64_t ob_o = __shfl_sync(FULL, ob, o);
+            const uint64_t ib_o = __shfl_sync(FULL, ib, o);
+            const uint64_t ku_o = __shfl_sync(FULL, ku, o);
+            bool bt = false;
+            if (idx < total) {
+                const uint32_t jj = idx - ex_o;
+                const uint32_t nb = jj < od_o ? d.out_adj[ob_o + jj].x : d.in_adj[ib_o + (jj - od_o)].x;
+                bt = select_key(d, nb) < ku_o;
+            }
+            const uint32_t B = __ballot_sync(FULL, bt);
+            const uint32_t lo = max(excl, b), hi = min(excl + c, b + 32);
+            if (hi > lo && (B & lane_bits(lo - b, hi - b))) beaten = true;
+        }
+        const bool sel = valid && !beaten;
+        if (sel) d.level[u] = r;
+        const uint32_t pos = warp_append(sel, &d.ctl->nF);
+        if (sel) F[pos] = u;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Step 4: contraction bookkeeping for V_F
+// --------------------------------------------------------------------------
+
+__global__ void k_contract_prep(Dev d, const uint32_t *F, uint32_t src_stamp, uint32_t next_r,
+                                uint32_t *S2, uint32_t *Anext) {
+    const uint32_t nF = d.ctl->nF;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF;
+         i += gridDim.x * blockDim.x) {
+        const uint32_t u = F[i];
+        const uint32_t od = d.out_deg[u], id = d.in_deg[u];
+        const uint64_t ob = d.out_beg[u], ib = d.in_beg[u];
+        atomicAdd(&d.ctl->candBound, (unsigned long long)od * id);
+        atomicAdd(&d.ctl->degFout, (unsigned long long)od);
+        atomicAdd(&d.ctl->degFin, (unsigned long long)id);
+        for (uint32_t j = 0; j < id + od; ++j) {
+            const uint32_t x = j < id ? d.in_adj[ib + j].x : d.out_adj[ob + (j - id)].x;
+            if (j < id && atomicExch(&d.smark[x], src_stamp) != src_stamp)
+                S2[atomicAdd(&d.ctl->nS2, 1u)] = x;
+            if (atomicExch(&d.amark[x], next_r) != next_r) {
+                Anext[atomicAdd(&d.ctl->nAnext, 1u)] = x;
+                atomicAdd(&d.ctl->degAnext, (unsigned long long)(d.out_deg[x] + d.in_deg[x]));
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Steps 6-9: CH edges, list maintenance, insertion
+// --------------------------------------------------------------------------
+
+__global__ void k_emit_ch(Dev d, const uint32_t *F, uint32_t nF, uint2 *ch_up, uint2 *ch_dn,
+                          uint64_t *up_beg, uint32_t *up_deg, uint64_t *dn_beg,
+                          uint32_t *dn_deg, uint64_t up_cap, uint64_t dn_cap) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF;
+         i += gridDim.x * blockDim.x) {
+        const uint32_t u = F[i];
+        const uint32_t od = d.out_deg[u], id = d.in_deg[u];
+        const uint64_t ob = d.out_beg[u], ib = d.in_beg[u];
+        const uint64_t pu = atomicAdd(&d.ctl->ch_up_tail, (unsigned long long)od);
+        const uint64_t pd = atomicAdd(&d.ctl->ch_dn_tail, (unsigned long long)id);
+        if (pu + od > up_cap || pd + id > dn_cap) {
+            atomicOr(&d.ctl->err, ERR_CH_OVERFLOW);
+            continue;
+        }
+        for (uint32_t j = 0; j < od; ++j) ch_up[pu + j] = d.out_adj[ob + j];
+        for (uint32_t j = 0; j < id; ++j) ch_dn[pd + j] = d.in_adj[ib + j];
+        up_beg[u] = pu;
+        up_deg[u] = od;
+        dn_beg[u] = pd;
+        dn_deg[u] = id;
+    }
+}
+
+__global__ void k_compact_lists(Dev d, const uint32_t *X, uint32_t nX, uint32_t r) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nX;
+         i += gridDim.x * blockDim.x) {
+        const uint32_t x = X[i];
+        {
+            const uint64_t b = d.out_beg[x];
+            const uint32_t dg = d.out_deg[x];
+            uint32_t k = 0;
+            for (uint32_t j = 0; j < dg; ++j) {
+                const uint2 e = d.out_adj[b + j];
+                if (d.level[e.x] != r) d.out_adj[b + k++] = e;
+            }
+            d.out_deg[x] = k;
+        }
+        {
+            const uint64_t b = d.in_beg[x];
+            const uint32_t dg = d.in_deg[x];
+            uint32_t k = 0;
+            for (uint32_t j = 0; j < dg; ++j) {
+                const uint2 e = d.in_adj[b + j];
+                if (d.level[e.x] != r) d.in_adj[b + k++] = e;
+            }
+            d.in_deg[x] = k;
+        }
+    }
+}
+
+__global__ void k_reserve(Dev d, const uint32_t *X, uint32_t nX, uint64_t *reqO,
+                          uint64_t *reqI) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nX;
+         i += gridDim.x * blockDim.x) {
+        const uint32_t x = X[i];
+        const uint32_t no = d.new_out[x], ni = d.new_in[x];
+        d.new_out[x] = 0;
+        d.new_in[x] = 0;
+        const uint32_t needO = d.out_deg[x] + no, needI = d.in_deg[x] + ni;
+        reqO[i] = needO > d.out_cap[x] ? (uint64_t)max(2u * needO, 4u) : 0;
+        reqI[i] = needI > d.in_cap[x] ? (uint64_t)max(2u * needI, 4u) : 0;
+    }
+}
+
+__global__ void k_relocate(Dev d, const uint32_t *X, uint32_t nX, const uint64_t *reqO,
+                           const uint64_t *posO, const uint64_t *reqI, const uint64_t *posI) {
+    const uint64_t to = d.ctl->out_tail, ti = d.ctl->in_tail;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nX;
+         i += gridDim.x * blockDim.x) {
+        const uint32_t x = X[i];
+        if (reqO[i]) {
+            const uint64_t nb = to + posO[i], ob = d.out_beg[x];
+            const uint32_t dg = d.out_deg[x];
+            for (uint32_t j = 0; j < dg; ++j) d.out_adj[nb + j] = d.out_adj[ob + j];
+            d.out_beg[x] = nb;
+            d.out_cap[x] = (uint32_t)reqO[i];
+        }
+        if (reqI[i]) {
+            const uint64_t nb = ti + posI[i], ob = d.in_beg[x];
+            const uint32_t dg = d.in_deg[x];
+            for (uint32_t j = 0; j < dg; ++j) d.in_adj[nb + j] = d.in_adj[ob + j];
+            d.in_beg[x] = nb;
+            d.in_cap[x] = (uint32_t)reqI[i];
+        }
+    }
+}
+
+__global__ void k_advance_tails(Ctl *ctl) {
+    ctl->out_tail += ctl->relocOut;
+    ctl->in_tail += ctl->relocIn;
+}
+
+__global__ void k_insert(Dev d, const uint4 *rec, const uint8_t *flag, uint32_t r,
+                         uint4 *log, uint32_t *log_round, uint64_t log_base) {
+    const uint32_t nRec = d.ctl->nRec;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nRec;
+         i += gridDim.x * blockDim.x) {
+        const uint4 c = rec[i];  // (v1, v2, w, via)
+        if (flag[i]) {
+            // Lower an existing edge. It sits among the list's entries from
+            // before this kernel, ahead of anything appended concurrently.
+            const uint64_t ob = d.out_beg[c.x];
+            const uint32_t oc = d.out_cap[c.x];
+            for (uint32_t j = 0; j < oc; ++j)
+                if (d.out_adj[ob + j].x == c.y) {
+                    d.out_adj[ob + j].y = c.z;
+                    break;
+                }
+            const uint64_t ib = d.in_beg[c.y];
+            const uint32_t ic = d.in_cap[c.y];
+            for (uint32_t j = 0; j < ic; ++j)
+                if (d.in_adj[ib + j].x == c.x) {
+                    d.in_adj[ib + j].y = c.z;
+                    break;
+                }
+        } else {
+            const uint32_t p = atomicAdd(&d.out_deg[c.x], 1u);
+            d.out_adj[d.out_beg[c.x] + p] = make_uint2(c.y, c.z);
+            const uint32_t q = atomicAdd(&d.in_deg[c.y], 1u);
+            d.in_adj[d.in_beg[c.y] + q] = make_uint2(c.x, c.z);
+        }
+        log[log_base + i] = c;
+        log_round[log_base + i] = r;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Postprocess: rank by (level, score, id) and the rank-ordered CSRs
+// --------------------------------------------------------------------------
+
+__global__ void k_rank_keys(const uint32_t *level, const int32_t *P, uint32_t n, uint64_t *keys,
+                            uint32_t *vals) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        keys[v] = ((uint64_t)level[v] << 32) | ((uint32_t)P[v] ^ 0x80000000u);
+        vals[v] = v;
+    }
+}
+
+__global__ void k_rank_from_perm(const uint32_t *perm, uint32_t n, uint32_t *rank) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        rank[perm[i]] = i;
+}
+
+__global__ void k_ranked_deg(const uint32_t *perm, uint32_t n, const uint32_t *deg,
+                             uint32_t *rdeg) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        rdeg[i] = deg[perm[i]];
+    if (blockIdx.x == 0 && threadIdx.x == 0) rdeg[n] = 0;
+}
+
+__global__ void k_ranked_fill(const uint32_t *perm, const uint32_t *rank, uint32_t n,
+                              const uint64_t *beg, const uint32_t *deg, const uint2 *src,
+                              const uint32_t *off, uint2 *dst) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t v = perm[i];
+        const uint32_t dg = deg[v];
+        const uint64_t b = beg[v];
+        uint2 *out = dst + off[i];
+        for (uint32_t j = 0; j < dg; ++j) {
+            const uint2 e = src[b + j];
+            out[j] = make_uint2(rank[e.x], e.y);
+        }
+        // insertion sort by target rank: the list order becomes canonical
+        for (uint32_t j = 1; j < dg; ++j) {
+            const uint2 t = out[j];
+            uint32_t k = j;
+            while (k > 0 && out[k - 1].x > t.x) {
+                out[k] = out[k - 1];
+                --k;
+            }
+            out[k] = t;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Host side
+// --------------------------------------------------------------------------
+
+int bits_for(uint64_t x) {
+    int b = 0;
+    while (b < 64 && (x >> b) != 0) ++b;
+    return b;
+}
+
+struct EventPool {
+    std::vector<cudaEvent_t> evs;
+    size_t used = 0;
+    cudaEvent_t get() {
+        if (used == evs.size()) {
+            cudaEvent_t e;
+            CH_CUDA_TRY(cudaEventCreate(&e));
+            evs.push_back(e);
+        }
+        return evs[used++];
+    }
+    ~EventPool() {
+        for (auto e : evs) cudaEventDestroy(e);
+    }
+};
+
+struct Span {
+    cudaEvent_t a, b;
+    double *acc;
+};
+
+struct Builder {
+    ch_s *h;
+    cudaStream_t st;
+    uint32_t n;
+    uint64_t m_in;
+    Dev d{};
+    // overlay storage
+    DevBuf<uint64_t> out_beg, in_beg;
+    DevBuf<uint32_t> out_deg, in_deg, out_cap, in_cap;
+    DevBuf<uint2> out_adj, in_adj;
+    DevBuf<uint32_t> level, amark, smark, new_out, new_in;
+    DevBuf<int32_t> P;
+    DevBuf<Ctl> ctl;
+    Ctl *hctl = nullptr;  // pinned
+    // lists
+    DevBuf<uint32_t> VO, VO2, A, Anext, S, S2, F, ovf, tmp;
+    DevBuf<uint64_t> reqO, reqI, posO, posI;
+    DevBuf<uint32_t> scan32;
+    DevBuf<uint64_t> scan64;
+    // records and log
+    DevBuf<uint4> rec;
+    DevBuf<uint8_t> rec_flag;
+    DevBuf<uint4> log;
+    DevBuf<uint32_t> log_round;
+    uint64_t log_count = 0;
+    // CH edges per vertex (id order)
+    DevBuf<uint2> ch_up, ch_dn;
+    DevBuf<uint64_t> ch_up_beg, ch_dn_beg;
+    DevBuf<uint32_t> ch_up_deg, ch_dn_deg;
+    // dense fallback
+    DevBuf<uint32_t> dn32;
+    DevBuf<unsigned long long> dn64;
+    Dense dense{};
+    int sms = 152;
+    EventPool pool;
+    std::vector<Span> spans;
+
+    void mark(double *acc, cudaEvent_t a) {
+        cudaEvent_t b = pool.get();
+        CH_CUDA_TRY(cudaEventRecord(b, st));
+        spans.push_back({a, b, acc});
+    }
+    cudaEvent_t start() {
+        cudaEvent_t a = pool.get();
+        CH_CUDA_TRY(cudaEventRecord(a, st));
+        return a;
+    }
+
+    void sync_ctl() {
+        CH_CUDA_TRY(cudaMemcpyAsync(hctl, ctl.ptr, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        CH_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hctl->err & ERR_INPUT) throw Error{CH_EINVAL, "graph has a malformed offset, id or weight"};
+        if (hctl->err) throw Error{CH_ECUDA, "internal capacity error " + std::to_string(hctl->err)};
+    }
+
+    void normalise(const ch_graph_t *g);
+    void run_rounds();
+    void postprocess();
+    template <int MODE>
+    void witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_max, uint32_t r);
+};
+
+#define CTL_OFF(field) offsetof(Ctl, field)
+
+void Builder::normalise(const ch_graph_t *g) {
+    const uint64_t m = g->m;
+    if (m >= 0xFFFFFFFFull) throw Error{CH_ERANGE, "more than 2^32 - 2 input edges"};
+    DevBuf<uint64_t> off_d;
+    DevBuf<uint32_t> tgt_d, w_d;
+    const uint64_t *off = g->offsets;
+    const uint32_t *tgt = g->targets, *wt = g->weights;
+    if (!g->on_device) {
+        off_d.alloc(n + 1);
+        tgt_d.alloc(m);
+        w_d.alloc(m);
+        CH_CUDA_TRY(cudaMemcpyAsync(off_d.ptr, off, (n + 1) * sizeof(uint64_t),
+                                    cudaMemcpyHostToDevice, st));
+        if (m) {
+            CH_CUDA_TRY(cudaMemcpyAsync(tgt_d.ptr, tgt, m * 4, cudaMemcpyHostToDevice, st));
+            CH_CUDA_TRY(cudaMemcpyAsync(w_d.ptr, wt, m * 4, cudaMemcpyHostToDevice, st));
+        }
+        off = off_d.ptr;
+        tgt = tgt_d.ptr;
+        wt = w_d.ptr;
+    }
+    k_validate_offsets<<<grid_for(n, 256, sms * 8), 256, 0, st>>>(off, n, m, ctl.ptr);
+    CH_CHECK_LAUNCH();
+    sync_ctl();
+
+    DevBuf<uint64_t> keys, tkeys;
+    DevBuf<uint32_t> vals, tvals, flags;
+    keys.alloc(m);
+    vals.alloc(m);
+    tkeys.alloc(m);
+    tvals.alloc(m);
+    flags.alloc(m);
+    const int gm = grid_for(m, 256, sms * 16);
+    if (m) {
+        k_edge_keys<<<gm, 256, 0, st>>>(off, tgt, wt, n, m, keys.ptr, vals.ptr, ctl.ptr);
+        CH_CHECK_LAUNCH();
+    }
+    sync_ctl();
+    off_d.release();
+    tgt_d.release();
+    w_d.release();
+    const int vb = bits_for(n ? n - 1 : 0);
+    std::vector<int> digits;
+    append_digits(digits, 0, vb);
+    append_digits(digits, 32, vb);
+    radix_sort_pairs(keys.ptr, vals.ptr, tkeys.ptr, tvals.ptr, m, digits, st);
+    uint64_t m1 = 0;
+    if (m) {
+        k_norm_flags<<<gm, 256, 0, st>>>(keys.ptr, m, flags.ptr);
+        CH_CHECK_LAUNCH();
+        exclusive_scan<uint32_t>(flags.ptr, flags.ptr, nullptr, m, &ctl.ptr->nVO2, scan32.ptr, st);
+        sync_ctl();
+        m1 = hctl->nVO2;
+        k_norm_scatter<<<gm, 256, 0, st>>>(keys.ptr, vals.ptr, m, flags.ptr, tkeys.ptr, tvals.ptr);
+        CH_CHECK_LAUNCH();
+    }
+    h->m_input = m1;
+    flags.release();
+    // tkeys/tvals now hold the normalised (u, v)-sorted edges
+    out_deg.alloc(n);
+    in_deg.alloc(n);
+    out_cap.alloc(n);
+    in_cap.alloc(n);
+    out_beg.alloc(n + 1);
+    in_beg.alloc(n + 1);
+    DevBuf<uint64_t> first;
+    first.alloc(n);
+    const int gn = grid_for(n, 256, sms * 8);
+    const int gm1 = grid_for(m1, 256, sms * 16);
+    for (int dir = 0; dir < 2; ++dir) {
+        DevBuf<uint32_t> &deg = dir == 0 ? out_deg : in_deg;
+        DevBuf<uint32_t> &cap = dir == 0 ? out_cap : in_cap;
+        DevBuf<uint64_t> &beg = dir == 0 ? out_beg : in_beg;
+        DevBuf<uint2> &adj = dir == 0 ? out_adj : in_adj;
+        if (dir == 1 && m1) {
+            k_swap_key_halves<<<gm1, 256, 0, st>>>(tkeys.ptr, m1);
+            CH_CHECK_LAUNCH();
+            radix_sort_pairs(tkeys.ptr, tvals.ptr, keys.ptr, vals.ptr, m1, digits, st);
+        }
+        deg.zero(st);
+        if (m1) {
+            k_seg_heads<<<gm1, 256, 0, st>>>(tkeys.ptr, m1, first.ptr);
+            CH_CHECK_LAUNCH();
+            k_seg_deg<<<gm1, 256, 0, st>>>(tkeys.ptr, m1, first.ptr, deg.ptr);
+            CH_CHECK_LAUNCH();
+        }
+        k_caps<<<gn, 256, 0, st>>>(deg.ptr, n, cap.ptr, beg.ptr);
+        CH_CHECK_LAUNCH();
+        exclusive_scan<uint64_t>(beg.ptr, beg.ptr, nullptr, n, beg.ptr + n, scan64.ptr, st);
+        uint64_t total = 0;
+        CH_CUDA_TRY(cudaMemcpyAsync(&total, beg.ptr + n, 8, cudaMemcpyDeviceToHost, st));
+        CH_CUDA_TRY(cudaStreamSynchronize(st));
+        adj.alloc(total + total / 2 + 1024);
+        if (m1) {
+            k_fill_adj<<<gm1, 256, 0, st>>>(tkeys.ptr, tvals.ptr, m1, first.ptr, beg.ptr, adj.ptr);
+            CH_CHECK_LAUNCH();
+        }
+        if (dir == 0) hctl->out_tail = total; else hctl->in_tail = total;
+    }
+    CH_CUDA_TRY(cudaMemcpyAsync(&ctl.ptr->out_tail, &hctl->out_tail, 16, cudaMemcpyHostToDevice, st));
+    CH_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+template <int MODE>
+void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_max, uint32_t r) {
+    CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->nOvf, 0, 4, st));
+    CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->work, 0, 8, st));  // work, work2
+    WArgs a;
+    a.d = d;
+    a.S = Sl;
+    a.nS = nS_dev;
+    a.work = &ctl.ptr->work;
+    a.round = r;
+    a.ovf = ovf.ptr;
+    a.rec = rec.ptr;
+    a.rec_flag = rec_flag.ptr;
+    a.rec_cap = rec.count;
+    cudaEvent_t e0 = start();
+    const int blocks = grid_for((uint64_t)nS_max, WIT_WARPS, sms * 8);
+    k_witness<MODE><<<blocks, WIT_WARPS * 32, 0, st>>>(a);
+    CH_CHECK_LAUNCH();
+    k_witness_dense<MODE><<<dense.nslots, 256, 0, st>>>(a, dense);
+    CH_CHECK_LAUNCH();
+    mark(&h->t_witness_ms, e0);
+    h->witness_launches += 2;
+}
+
+void Builder::run_rounds() {
+    const int gn = grid_for(n, 256, sms * 8);
+    // live vertex list and A_0 = V
+    k_iota<<<gn, 256, 0, st>>>(VO.ptr, n);
+    CH_CHECK_LAUNCH();
+    k_iota<<<gn, 256, 0, st>>>(A.ptr, n);
+    CH_CHECK_LAUNCH();
+    hctl->nVO = n;
+    CH_CUDA_TRY(cudaMemcpyAsync(&ctl.ptr->nVO, &hctl->nVO, 4, cudaMemcpyHostToDevice, st));
+    uint32_t nA = n, nVO = n;
+    uint64_t live_edges = h->m_input;
+    for (uint32_t r = 0; nVO > 0; ++r) {
+        if (r > 0x7FFFFFF0u) throw Error{CH_ERANGE, "too many rounds"};
+        // reset per-round counters
+        CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->nS, 0, 4 * 6, st));  // nS nS2 nF nAnext nOvf nRec
+        CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->candBound, 0, 8 * 4, st));
+        // 1-2: score the affected set
+        cudaEvent_t e0 = start();
+        const uint32_t sstamp = 2 * r + 1, cstamp = 2 * r + 2;
+        if (nA) {
+            k_score_prep<<<grid_for(nA, 256, sms * 8), 256, 0, st>>>(d, A.ptr, nA, sstamp, S.ptr);
+            CH_CHECK_LAUNCH();
+            witness<MODE_SCORE>(S.ptr, &ctl.ptr->nS, nA * 4 + 32 > n ? n : nA * 4 + 32, r);
+        }
+        mark(&h->t_score_ms, e0);
+        // 3: select
+        e0 = start();
+        k_select<<<grid_for((uint64_t)nVO, 256, sms * 8), 256, 0, st>>>(d, VO.ptr, nVO, r, F.ptr);
+        CH_CHECK_LAUNCH();
+        mark(&h->t_select_ms, e0);
+        // 4: contraction bookkeeping
+        e0 = start();
+        k_contract_prep<<<grid_for((uint64_t)nVO, 256, sms * 8), 256, 0, st>>>(
+            d, F.ptr, cstamp, r + 1, S2.ptr, Anext.ptr);
+        CH_CHECK_LAUNCH();
+        mark(&h->t_prep_ms, e0);
+        sync_ctl();
+        const Ctl c = *hctl;
+        const uint32_t nF = c.nF, nS2 = c.nS2, nAnext = c.nAnext;
+        if (nF == 0) throw Error{CH_ECUDA, "internal: empty selection"};
+        // capacities for this round's contraction
+        const uint64_t cb = c.candBound;
+        if (rec.count < cb) {
+            rec.grow(std::max<uint64_t>(cb, rec.count * 2), 0, st);
+            rec_flag.grow(rec.count, 0, st);
+        }
+        if (log.count < log_count + cb) {
+            const uint64_t want = std::max<uint64_t>(log_count + cb, log.count * 2);
+            log.grow(want, log_count, st);
+            log_round.grow(want, log_count, st);
+        }
+        if (ch_up.count < c.ch_up_tail + c.degFout)
+            ch_up.grow(std::max<uint64_t>(c.ch_up_tail + c.degFout, ch_up.count * 2), c.ch_up_tail, st);
+        if (ch_dn.count < c.ch_dn_tail + c.degFin)
+            ch_dn.grow(std::max<uint64_t>(c.ch_dn_tail + c.degFin, ch_dn.count * 2), c.ch_dn_tail, st);
+        const uint64_t grow_bound = 2 * c.degAnext + 2 * cb + 4ull * nAnext;
+        bool regrow = false;
+        if (out_adj.count < c.out_tail + grow_bound) {
+            out_adj.grow(std::max<uint64_t>(c.out_tail + grow_bound, out_adj.count * 2), c.out_tail, st);
+            regrow = true;
+        }
+        if (in_adj.count < c.in_tail + grow_bound) {
+            in_adj.grow(std::max<uint64_t>(c.in_tail + grow_bound, in_adj.count * 2), c.in_tail, st);
+            regrow = true;
+        }
+        if (regrow) {
+            d.out_adj = out_adj.ptr;
+            d.in_adj = in_adj.ptr;
+        }
+        CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->cand, 0, 8 * 5, st));
+        // 5: witness searches for V_F's candidates
+        e0 = start();
+        if (nS2) witness<MODE_PRUNE>(S2.ptr, &ctl.ptr->nS2, nS2, r);
+        mark(&h->t_contract_ms, e0);
+        // 6-10
+        e0 = start();
+        k_emit_ch<<<grid_for(nF, 256, sms * 8), 256, 0, st>>>(
+            d, F.ptr, nF, ch_up.ptr, ch_dn.ptr, ch_up_beg.ptr, ch_up_deg.ptr, ch_dn_beg.ptr,
+            ch_dn_deg.ptr, ch_up.count, ch_dn.count);
+        CH_CHECK_LAUNCH();
+        if (nAnext) {
+            const int ga = grid_for(nAnext, 256, sms * 8);
+            k_compact_lists<<<ga, 256, 0, st>>>(d, Anext.ptr, nAnext, r);
+            CH_CHECK_LAUNCH();
+            k_reserve<<<ga, 256, 0, st>>>(d, Anext.ptr, nAnext, reqO.ptr, reqI.ptr);
+            CH_CHECK_LAUNCH();
+            exclusive_scan<uint64_t>(reqO.ptr, posO.ptr, nullptr, nAnext, reinterpret_cast<uint64_t *>(&ctl.ptr->relocOut),
+                                     scan64.ptr, st);
+            exclusive_scan<uint64_t>(reqI.ptr, posI.ptr, nullptr, nAnext, reinterpret_cast<uint64_t *>(&ctl.ptr->relocIn),
+                                     scan64.ptr, st);
+            k_relocate<<<ga, 256, 0, st>>>(d, Anext.ptr, nAnext, reqO.ptr, posO.ptr, reqI.ptr,
+                                           posI.ptr);
+            CH_CHECK_LAUNCH();
+            k_advance_tails<<<1, 1, 0, st>>>(ctl.ptr);
+            CH_CHECK_LAUNCH();
+        }
+        const uint64_t rec_bound = std::max<uint64_t>(cb, 1);
+        k_insert<<<grid_for(rec_bound, 256, sms * 8), 256, 0, st>>>(
+            d, rec.ptr, rec_flag.ptr, r, log.ptr, log_round.ptr, log_count);
+        CH_CHECK_LAUNCH();
+        compact_alive(VO.ptr, &ctl.ptr->nVO, nVO, level.ptr, VO2.ptr, &ctl.ptr->nVO2, tmp.ptr,
+                      scan32.ptr, st);
+        std::swap(VO, VO2);
+        CH_CUDA_TRY(cudaMemcpyAsync(&ctl.ptr->nVO, &ctl.ptr->nVO2, 4, cudaMemcpyDeviceToDevice, st));
+        std::swap(A, Anext);
+        mark(&h->t_update_ms, e0);
+        // read this round's contraction counters (one more sync per round
+        // keeps the bookkeeping simple; the next round needs nothing from it)
+        sync_ctl();
+        const Ctl c2 = *hctl;
+        std::array<uint64_t, CH_NSTAT> st_row{};
+        st_row[0] = nA;
+        st_row[1] = c.nS;
+        st_row[2] = nF;
+        st_row[3] = nS2;
+        st_row[4] = c2.cand;
+        st_row[5] = c2.kept;
+        st_row[6] = c2.merged;
+        st_row[7] = c2.inserted;
+        nVO -= nF;
+        st_row[8] = nVO;
+        live_edges = live_edges - c.degFout - c.degFin + c2.newEdges;
+        st_row[9] = live_edges;
+        h->round_stats.push_back(st_row);
+        if (c2.nRec > rec.count) throw Error{CH_ECUDA, "internal: record overflow"};
+        log_count += c2.nRec;
+        nA = nAnext;
+    }
+    h->n_shortcuts = log_count;
+    h->witness_bytes = 0;
+}
+
+void Builder::postprocess() {
+    const int gn = grid_for(n, 256, sms * 8);
+    DevBuf<uint64_t> keys, tkeys;
+    DevBuf<uint32_t> vals, tvals;
+    keys.alloc(n);
+    tkeys.alloc(n);
+    vals.alloc(n);
+    tvals.alloc(n);
+    k_rank_keys<<<gn, 256, 0, st>>>(level.ptr, P.ptr, n, keys.ptr, vals.ptr);
+    CH_CHECK_LAUNCH();
+    std::vector<int> digits;
+    append_digits(digits, 0, 32);
+    append_digits(digits, 32, bits_for(h->round_stats.size()));
+    radix_sort_pairs(keys.ptr, vals.ptr, tkeys.ptr, tvals.ptr, n, digits, st);
+    h->perm = std::move(vals);
+    h->rank.alloc(n);
+    k_rank_from_perm<<<gn, 256, 0, st>>>(h->perm.ptr, n, h->rank.ptr);
+    CH_CHECK_LAUNCH();
+    const uint64_t n_up = hctl->ch_up_tail, n_dn = hctl->ch_dn_tail;
+    if (n_up >= 0xFFFFFFFFull || n_dn >= 0xFFFFFFFFull)
+        throw Error{CH_ERANGE, "hierarchy has 2^32 - 1 or more edges in one direction"};
+    h->n_up = n_up;
+    h->n_down = n_dn;
+    for (int dir = 0; dir < 2; ++dir) {
+        DevBuf<uint32_t> &off = dir == 0 ? h->up_off : h->dn_off;
+        DevBuf<uint2> &adj = dir == 0 ? h->up_adj : h->dn_adj;
+        off.alloc(n + 1);
+        adj.alloc(dir == 0 ? n_up : n_dn);
+        k_ranked_deg<<<gn, 256, 0, st>>>(h->perm.ptr, n, dir == 0 ? ch_up_deg.ptr : ch_dn_deg.ptr,
+                                         off.ptr);
+        CH_CHECK_LAUNCH();
+        exclusive_scan<uint32_t>(off.ptr, off.ptr, nullptr, (uint64_t)n + 1, nullptr, scan32.ptr, st);
+        k_ranked_fill<<<gn, 256, 0, st>>>(h->perm.ptr, h->rank.ptr, n,
+                                          dir == 0 ? ch_up_beg.ptr : ch_dn_beg.ptr,
+                                          dir == 0 ? ch_up_deg.ptr : ch_dn_deg.ptr,
+                                          dir == 0 ? ch_up.ptr : ch_dn.ptr, off.ptr, adj.ptr);
+        CH_CHECK_LAUNCH();
+    }
+    CH_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
+    Builder b;
+    b.h = h;
+    b.st = (cudaStream_t)p->stream;
+    b.n = g->n;
+    b.m_in = g->m;
+    b.sms = device_sm_count();
+    const uint32_t n = g->n;
+    h->n = n;
+    h->hop_limit = p->hop_limit;
+    CH_CUDA_TRY(cudaMallocHost(&b.hctl, sizeof(Ctl)));
+    struct PinnedFree {
+        Ctl *p;
+        ~PinnedFree() {
+            if (p) cudaFreeHost(p);
+        }
+    } pf{b.hctl};
+    std::memset(b.hctl, 0, sizeof(Ctl));
+    b.ctl.alloc(1);
+    b.ctl.zero(b.st);
+    b.scan32.alloc(kScanScratch);
+    b.scan64.alloc(kScanScratch);
+
+    cudaEvent_t t0 = b.start();
+    if (n == 0) {
+        if (g->m != 0) throw Error{CH_EINVAL, "n = 0 with m > 0"};
+        h->level.alloc(0);
+        h->prio.alloc(0);
+        h->rank.alloc(0);
+        h->perm.alloc(0);
+        h->up_off.alloc(1);
+        h->dn_off.alloc(1);
+        h->up_off.zero(b.st);
+        h->dn_off.zero(b.st);
+        h->up_adj.alloc(0);
+        h->dn_adj.alloc(0);
+        h->sc.alloc(0);
+        h->sc_round.alloc(0);
+        CH_CUDA_TRY(cudaStreamSynchronize(b.st));
+        return;
+    }
+    b.normalise(g);
+    b.mark(&h->t_norm_ms, t0);
+
+    b.level.alloc(n);
+    b.level.fill_ff(b.st);
+    b.P.alloc(n);
+    b.P.zero(b.st);
+    b.amark.alloc(n);
+    b.amark.zero(b.st);
+    b.smark.alloc(n);
+    b.smark.zero(b.st);
+    b.new_out.alloc(n);
+    b.new_out.zero(b.st);
+    b.new_in.alloc(n);
+    b.new_in.zero(b.st);
+    for (auto *l : {&b.VO, &b.VO2, &b.A, &b.Anext, &b.S, &b.S2, &b.F, &b.ovf}) l->alloc(n);
+    b.tmp.alloc((size_t)n + 1);
+    b.reqO.alloc(n);
+    b.reqI.alloc(n);
+    b.posO.alloc(n);
+    b.posI.alloc(n);
+    const uint64_t m1 = h->m_input;
+    b.rec.alloc(std::max<uint64_t>(1024, m1));
+    b.rec_flag.alloc(b.rec.count);
+    b.log.alloc(std::max<uint64_t>(1024, m1));
+    b.log_round.alloc(b.log.count);
+    b.ch_up.alloc(m1 + 1024);
+    b.ch_dn.alloc(m1 + 1024);
+    b.ch_up_beg.alloc(n);
+    b.ch_dn_beg.alloc(n);
+    b.ch_up_deg.alloc(n);
+    b.ch_dn_deg.alloc(n);
+    // dense fallback slots: 10 uint32 + 1 uint64 arrays of n per slot, <= 2 GiB
+    const uint64_t per_slot = (uint64_t)n * (8 * 4 + 8);
+    uint32_t slots = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(64, (2ull << 30) / per_slot));
+    b.dense.nslots = slots;
+    b.dn32.alloc((size_t)slots * n * 8);
+    b.dn64.alloc((size_t)slots * n);
+    {
+        const size_t sn = (size_t)slots * n;
+        uint32_t *p32 = b.dn32.ptr;
+        b.dense.dist = p32;
+        b.dense.fst = p32 + sn;
+        b.dense.fa = p32 + 2 * sn;
+        b.dense.fb = p32 + 3 * sn;
+        b.dense.fda = p32 + 4 * sn;
+        b.dense.fdb = p32 + 5 * sn;
+        b.dense.touched = p32 + 6 * sn;
+        b.dense.mt = p32 + 7 * sn;
+        b.dense.merge = b.dn64.ptr;
+        CH_CUDA_TRY(cudaMemsetAsync(b.dense.dist, 0xFF, sn * 4, b.st));
+        CH_CUDA_TRY(cudaMemsetAsync(b.dense.fst, 0, sn * 4, b.st));
+        CH_CUDA_TRY(cudaMemsetAsync(b.dense.merge, 0xFF, sn * 8, b.st));
+    }
+
+    Dev &d = b.d;
+    d.n = n;
+    d.H = p->hop_limit;
+    d.tie_mode = p->tie_break;
+    d.tie_seed = p->tie_seed;
+    d.out_beg = b.out_beg.ptr;
+    d.in_beg = b.in_beg.ptr;
+    d.out_deg = b.out_deg.ptr;
+    d.in_deg = b.in_deg.ptr;
+    d.out_cap = b.out_cap.ptr;
+    d.in_cap = b.in_cap.ptr;
+    d.out_adj = b.out_adj.ptr;
+    d.in_adj = b.in_adj.ptr;
+    d.level = b.level.ptr;
+    d.P = b.P.ptr;
+    d.amark = b.amark.ptr;
+    d.smark = b.smark.ptr;
+    d.new_out = b.new_out.ptr;
+    d.new_in = b.new_in.ptr;
+    d.ctl = b.ctl.ptr;
+
+    b.run_rounds();
+    cudaEvent_t t1 = b.start();
+    b.postprocess();
+    b.mark(&h->t_post_ms, t1);
+    b.mark(&h->stats.build_ms, t0);
+    CH_CUDA_TRY(cudaStreamSynchronize(b.st));
+
+    for (const Span &s : b.spans) {
+        float ms = 0;
+        CH_CUDA_TRY(cudaEventElapsedTime(&ms, s.a, s.b));
+        *s.acc += ms;
+    }
+    const Ctl &c = *b.hctl;
+    h->stats.witness_sources = c.wit_sources + c.wit_fallback;
+    h->stats.witness_fallback = c.wit_fallback;
+    // Algorithmic bytes of the witness kernels: per search the source id
+    // (4 B); per vertex whose out-list is read its offset and degree (12 B);
+    // per adjacency entry read (id + weight, 8 B).
+    h->witness_bytes = 4 * (c.wit_sources + c.wit_fallback) + 12 * c.wit_vertices +
+                       8 * c.wit_edges + 12 * c.wit_middles + 8 * c.wit_midedges;
+
+    h->level = std::move(b.level);
+    h->prio = std::move(b.P);
+    h->sc = std::move(b.log);
+    h->sc_round = std::move(b.log_round);
+}
+
+}  // namespace gbch

@@ -1,0 +1,68 @@
+// The library-owned hierarchy handle (ch_t) and the entry points shared by
+// the build, query and API translation units.
+#pragma once
+
+#include <array>
+#include <vector>
+
+#include "common.cuh"
+
+struct ch_s {
+    uint32_t n = 0;
+    uint64_t m_input = 0;
+    uint32_t hop_limit = 0;
+    int device = 0;
+
+    // Hierarchy in rank order (Sec. 5 layout): vertex i of these arrays is the
+    // vertex of rank i; targets are ranks too. up_* hold E_up (out-edges of a
+    // vertex at its contraction, all to higher ranks), dn_* hold E_down stored
+    // at the lower endpoint (in-edges at contraction, reversed for the
+    // backward search).
+    gbch::DevBuf<uint32_t> rank;     // [n] id -> rank
+    gbch::DevBuf<uint32_t> perm;     // [n] rank -> id
+    gbch::DevBuf<uint32_t> up_off;   // [n+1]
+    gbch::DevBuf<uint32_t> dn_off;   // [n+1]
+    gbch::DevBuf<uint2> up_adj;      // (target rank, weight)
+    gbch::DevBuf<uint2> dn_adj;
+
+    // Build products kept for export.
+    gbch::DevBuf<uint32_t> level;    // [n]
+    gbch::DevBuf<int32_t> prio;      // [n]
+    gbch::DevBuf<uint4> sc;          // shortcut log (v1, v2, w, via)
+    gbch::DevBuf<uint32_t> sc_round; // round of each log entry
+    uint64_t n_shortcuts = 0;
+    uint64_t n_up = 0, n_down = 0;
+
+    std::vector<std::array<uint64_t, CH_NSTAT>> round_stats;
+    ch_stats_t stats{};
+
+    // Per-phase device time of the build (ms) and the witness kernels'
+    // algorithmic traffic, for the roofline report.
+    double t_score_ms = 0, t_select_ms = 0, t_prep_ms = 0, t_contract_ms = 0,
+           t_update_ms = 0, t_norm_ms = 0, t_post_ms = 0;
+    double t_witness_ms = 0;
+    uint64_t witness_bytes = 0;
+    uint64_t witness_launches = 0;
+
+    // Query state.
+    gbch::DevBuf<uint32_t> qerr;            // device error word of query batches
+    gbch::DevBuf<uint32_t> qwork;           // work counters
+    gbch::DevBuf<uint32_t> q_ovf_list;      // overflowed queries
+    gbch::DevBuf<uint32_t> q_dense;         // fallback slots
+    uint32_t q_slots = 0;
+    uint64_t q_ovf_cap = 0;
+};
+
+namespace gbch {
+
+// Build a hierarchy into `h` (h->n etc. are set by the callee).
+void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p);
+
+// Enqueue a query batch on `st` (device pointers).
+void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                 uint32_t *dist_out, uint32_t *settled_out, cudaStream_t st);
+
+// Prepare query scratch after a build.
+void query_init(ch_s *h);
+
+}  // namespace gbch

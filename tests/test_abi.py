@@ -1,0 +1,77 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a and exports
+every entry point include/ch.h declares (no device calls)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2412_18008_gb300 import build as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "include", "ch.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(ch_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("ch_build", "ch_query_batch", "ch_query_batch_host", "ch_free",
+                 "ch_export", "ch_get_stats", "ch_last_error"):
+        assert must in names
+
+
+def test_library_builds_and_exports_every_symbol():
+    lib_path = B.build()
+    assert os.path.exists(lib_path)
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (ch_\w+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_reports_version():
+    lib = C.CDLL(B.build())
+    lib.ch_version.restype = C.c_char_p
+    assert b"sm_103a" in lib.ch_version()
+
+
+def test_struct_layouts_match_header():
+    from paper_2412_18008_gb300 import ch
+    # offsets of the C structs, computed by the host compiler from ch.h
+    src = r'''
+    #include <stddef.h>
+    #include <stdio.h>
+    #include "ch.h"
+    int main(void) {
+      printf("%zu %zu %zu\n", sizeof(ch_graph_t), sizeof(ch_params_t), sizeof(ch_stats_t));
+      printf("%zu %zu\n", offsetof(ch_params_t, stream), offsetof(ch_stats_t, witness_bytes));
+      return 0;
+    }'''
+    tmp = "/tmp/ch_layout_check"
+    with open(tmp + ".c", "w") as f:
+        f.write(src)
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), tmp + ".c", "-o", tmp], check=True)
+    vals = subprocess.run([tmp], capture_output=True, text=True, check=True).stdout.split()
+    sizes = list(map(int, vals))
+    assert sizes[0] == C.sizeof(ch.GraphT)
+    assert sizes[1] == C.sizeof(ch.ParamsT)
+    assert sizes[2] == C.sizeof(ch.StatsT)
+    assert sizes[3] == ch.ParamsT.stream.offset
+    assert sizes[4] == ch.StatsT.witness_bytes.offset
+
+
+def test_no_cpu_fallback_in_product_package():
+    pkg = os.path.join(os.path.dirname(HEADER), "..", "paper_2412_18008_gb300")
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh")):
+                text = open(os.path.join(root, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
