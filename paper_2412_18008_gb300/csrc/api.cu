@@ -171,6 +171,10 @@ int ch_query_status(ch_t *ch, void *stream) {
         CH_CUDA_TRY(cudaStreamSynchronize(st));
     });
     if (rc != CH_OK) return rc;
+    if (err & 2u) {
+        g_last_error = "internal index check failed in a query kernel";
+        return CH_ECUDA;
+    }
     if (err) {
         g_last_error = "query vertex id out of range";
         return CH_EINVAL;

@@ -50,6 +50,7 @@ constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t ERR_INPUT = 1u;
 constexpr uint32_t ERR_REC_OVERFLOW = 2u;
 constexpr uint32_t ERR_CH_OVERFLOW = 4u;
+constexpr uint32_t ERR_BOUND = 8u;  // an index check failed; the access was skipped
 
 constexpr int MODE_SCORE = 0;
 constexpr int MODE_PRUNE = 1;
@@ -84,6 +85,7 @@ struct Dev {
     uint32_t *amark, *smark;
     uint32_t *new_out, *new_in;
     Ctl *ctl;
+    uint64_t out_arena, in_arena;  // arena capacities (entries), for index checks
 };
 
 struct WArgs {
@@ -114,6 +116,25 @@ template <int MODE>
 __device__ __forceinline__ bool is_middle(const Dev &d, uint32_t u, uint32_t r) {
     if (MODE == MODE_SCORE) return d.amark[u] == r;
     return d.level[u] == r;
+}
+
+// Index checks: a list must lie inside its arena and hold ids below n. A
+// failed check sets ERR_BOUND (reported as an error by the host) and the
+// caller skips the access instead of faulting.
+__device__ __forceinline__ bool out_list_ok(const Dev &d, uint64_t beg, uint32_t deg) {
+    if (beg + deg <= d.out_arena) return true;
+    atomicOr(&d.ctl->err, ERR_BOUND);
+    return false;
+}
+__device__ __forceinline__ bool in_list_ok(const Dev &d, uint64_t beg, uint32_t deg) {
+    if (beg + deg <= d.in_arena) return true;
+    atomicOr(&d.ctl->err, ERR_BOUND);
+    return false;
+}
+__device__ __forceinline__ bool id_ok(const Dev &d, uint32_t v) {
+    if (v < d.n) return true;
+    atomicOr(&d.ctl->err, ERR_BOUND);
+    return false;
 }
 
 __device__ __forceinline__ uint32_t lane_bits(uint32_t lo, uint32_t hi) {
@@ -235,11 +256,14 @@ __global__ void k_score_prep(Dev d, const uint32_t *A, uint32_t nA, uint32_t sta
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nA;
          i += gridDim.x * blockDim.x) {
         uint32_t u = A[i];
+        if (!id_ok(d, u)) continue;
         uint32_t od = d.out_deg[u], id = d.in_deg[u];
         d.P[u] = -(int32_t)(od + id);
         uint64_t ib = d.in_beg[u];
+        if (!in_list_ok(d, ib, id)) continue;
         for (uint32_t j = 0; j < id; ++j) {
             uint32_t v1 = d.in_adj[ib + j].x;
+            if (!id_ok(d, v1)) continue;
             if (atomicExch(&d.smark[v1], stamp) != stamp) S[atomicAdd(&d.ctl->nS, 1u)] = v1;
         }
     }
@@ -258,7 +282,6 @@ struct WarpSmem {
     unsigned long long mval[WIT_MC];
     uint32_t cnt[32];
     uint32_t nf[2];
-    uint32_t flag;
 };
 
 __device__ __forceinline__ uint32_t ht_hash(uint32_t v, int bits) {
@@ -312,8 +335,16 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         i = __shfl_sync(FULL, i, 0);
         if (i >= nS) break;
         const uint32_t s = a.S[i];
+        if (s >= d.n) {
+            if (lane == 0) atomicOr(&ctl->err, ERR_BOUND);
+            continue;
+        }
         const uint64_t sb = d.out_beg[s];
         const uint32_t sd = d.out_deg[s];
+        if (sb + sd > d.out_arena) {
+            if (lane == 0) atomicOr(&ctl->err, ERR_BOUND);
+            continue;
+        }
         c_src += (lane == 0);
 
         // Phase 0: heaviest candidate weight of this source.
@@ -322,9 +353,10 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             const uint32_t j = c0 + lane;
             const bool valid = j < sd;
             const uint2 e = valid ? d.out_adj[sb + j] : make_uint2(0, 0);
-            const bool mid = valid && is_middle<MODE>(d, e.x, r);
-            const uint32_t cnt = mid ? d.out_deg[e.x] : 0;
+            const bool mid = valid && id_ok(d, e.x) && is_middle<MODE>(d, e.x, r);
+            uint32_t cnt = mid ? d.out_deg[e.x] : 0;
             const uint64_t ub = mid ? d.out_beg[e.x] : 0;
+            if (mid && !out_list_ok(d, ub, cnt)) cnt = 0;
             c_mid += mid;
             c_midedge += cnt;
             const uint32_t incl = warp_incl_scan(cnt);
@@ -358,25 +390,26 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             w.key[h] = s;
             w.val[h] = 0;
             w.front[0][0] = make_uint2(h, 0);
-            w.nf[0] = 1;
-            w.nf[1] = 0;
-            w.flag = 0;
         }
-        __syncwarp();
+        // Control values (frontier size, overflow) stay in registers and are
+        // made warp-uniform by __shfl_sync / __any_sync, never by polling
+        // shared memory.
+        uint32_t nfront = 1;
+        bool overflowed = false;
         uint32_t cur = 0;
-        for (uint32_t lvl = 1; lvl <= d.H; ++lvl) {
-            const uint32_t nfront = w.nf[cur];
+        for (uint32_t lvl = 1; lvl <= d.H && nfront > 0; ++lvl) {
             const uint32_t nxt = cur ^ 1u;
-            __syncwarp();
             if (lane == 0) w.nf[nxt] = 0;
             __syncwarp();
+            bool ovf = false;
             for (uint32_t f0 = 0; f0 < nfront; f0 += 32) {
                 const uint32_t fi = f0 + lane;
                 const bool fv = fi < nfront;
                 const uint2 fe = fv ? w.front[cur][fi] : make_uint2(0, 0);
                 const uint32_t x = fv ? w.key[fe.x] : 0;
-                const uint32_t cnt = fv ? d.out_deg[x] : 0;
+                uint32_t cnt = fv ? d.out_deg[x] : 0;
                 const uint64_t xb = fv ? d.out_beg[x] : 0;
+                if (fv && !out_list_ok(d, xb, cnt)) cnt = 0;
                 c_vert += fv;
                 c_edge += cnt;
                 const uint32_t incl = warp_incl_scan(cnt);
@@ -391,16 +424,16 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                     if (idx < total) {
                         const uint2 e = d.out_adj[xb_o + (idx - ex_o)];
                         const uint32_t nd = sat_add(dx_o, e.y);
-                        if (nd < bound) {
+                        if (nd < bound && id_ok(d, e.x)) {
                             const uint32_t slot = ht_insert(w.key, WIT_TBITS, e.x);
                             if (slot == EMPTY) {
-                                w.flag = 1;
+                                ovf = true;
                             } else {
                                 const uint32_t old = atomicMin(&w.val[slot], nd);
                                 if (nd < old && atomicExch(&w.fst[slot], lvl) != lvl) {
                                     const uint32_t p = atomicAdd(&w.nf[nxt], 1u);
                                     if (p < WIT_FC) w.front[nxt][p] = make_uint2(slot, 0);
-                                    else w.flag = 1;
+                                    else ovf = true;
                                 }
                             }
                         }
@@ -408,15 +441,20 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                 }
             }
             __syncwarp();
-            if (w.flag) break;
-            const uint32_t nn = w.nf[nxt];
+            if (__any_sync(FULL, ovf)) {
+                overflowed = true;
+                break;
+            }
+            uint32_t nn = 0;
+            if (lane == 0) nn = w.nf[nxt];
+            nn = __shfl_sync(FULL, nn, 0);
             for (uint32_t p = lane; p < nn; p += 32) w.front[nxt][p].y = w.val[w.front[nxt][p].x];
             __syncwarp();
             cur = nxt;
-            if (nn == 0) break;
+            nfront = nn;
         }
         __syncwarp();
-        if (w.flag) {
+        if (overflowed) {
             if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
             continue;
         }
@@ -430,13 +468,15 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         }
         __syncwarp();
         uint32_t l_cand = 0, l_kept = 0;
+        bool mover = false;
         for (uint32_t c0 = 0; c0 < sd; c0 += 32) {
             const uint32_t j = c0 + lane;
             const bool valid = j < sd;
             const uint2 e = valid ? d.out_adj[sb + j] : make_uint2(0, 0);
-            const bool mid = valid && is_middle<MODE>(d, e.x, r);
-            const uint32_t cnt = mid ? d.out_deg[e.x] : 0;
+            const bool mid = valid && id_ok(d, e.x) && is_middle<MODE>(d, e.x, r);
+            uint32_t cnt = mid ? d.out_deg[e.x] : 0;
             const uint64_t ub = mid ? d.out_beg[e.x] : 0;
+            if (mid && !out_list_ok(d, ub, cnt)) cnt = 0;
             const uint32_t incl = warp_incl_scan(cnt);
             const uint32_t total = __shfl_sync(FULL, incl, 31);
             const uint32_t excl = incl - cnt;
@@ -462,7 +502,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                                 atomicAdd(&w.cnt[o], 1u);
                             } else {
                                 const uint32_t ms = ht_insert(w.mkey, 7, e2.x);
-                                if (ms == EMPTY) w.flag = 1;
+                                if (ms == EMPTY) mover = true;
                                 else atomicMin(&w.mval[ms], ((unsigned long long)via << 32) | u_o);
                             }
                         }
@@ -475,7 +515,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         }
         if (MODE == MODE_PRUNE) {
             __syncwarp();
-            if (w.flag) {
+            if (__any_sync(FULL, mover)) {
                 if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
                 continue;
             }
@@ -573,8 +613,12 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
         const uint32_t i = s_item;
         if (i >= nOvf) break;
         const uint32_t s = a.ovf[i];
-        const uint64_t sb = d.out_beg[s];
-        const uint32_t sd = d.out_deg[s];
+        const uint64_t sb = s < n ? d.out_beg[s] : 0;
+        const uint32_t sd = (s < n && out_list_ok(d, sb, d.out_deg[s])) ? d.out_deg[s] : 0;
+        if (s >= n) {
+            if (tid == 0) atomicOr(&ctl->err, ERR_BOUND);
+            continue;
+        }
         if (tid == 0) {
             s_bound = 0;
             s_nt = 1;
@@ -590,9 +634,9 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
         __syncthreads();
         for (uint32_t j = tid; j < sd; j += blockDim.x) {
             const uint2 e = d.out_adj[sb + j];
-            if (!is_middle<MODE>(d, e.x, r)) continue;
+            if (!id_ok(d, e.x) || !is_middle<MODE>(d, e.x, r)) continue;
             const uint64_t ub = d.out_beg[e.x];
-            const uint32_t ud = d.out_deg[e.x];
+            const uint32_t ud = out_list_ok(d, ub, d.out_deg[e.x]) ? d.out_deg[e.x] : 0;
             uint32_t bmax = 0;
             for (uint32_t jj = 0; jj < ud; ++jj) {
                 const uint2 e2 = d.out_adj[ub + jj];
@@ -611,11 +655,11 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             for (uint32_t f = tid; f < nf; f += blockDim.x) {
                 const uint32_t x = cur[f], dx = curd[f];
                 const uint64_t xb = d.out_beg[x];
-                const uint32_t xd = d.out_deg[x];
+                const uint32_t xd = out_list_ok(d, xb, d.out_deg[x]) ? d.out_deg[x] : 0;
                 for (uint32_t j = 0; j < xd; ++j) {
                     const uint2 e = d.out_adj[xb + j];
                     const uint32_t nd = sat_add(dx, e.y);
-                    if (nd >= bound) continue;
+                    if (nd >= bound || !id_ok(d, e.x)) continue;
                     const uint32_t old = atomicMin(&dist[e.x], nd);
                     if (nd < old) {
                         if (old == INF) touched[atomicAdd(&s_nt, 1u)] = e.x;
@@ -638,13 +682,13 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
         unsigned long long l_cand = 0, l_kept = 0;
         for (uint32_t j = tid; j < sd; j += blockDim.x) {
             const uint2 e = d.out_adj[sb + j];
-            if (!is_middle<MODE>(d, e.x, r)) continue;
+            if (!id_ok(d, e.x) || !is_middle<MODE>(d, e.x, r)) continue;
             const uint64_t ub = d.out_beg[e.x];
-            const uint32_t ud = d.out_deg[e.x];
+            const uint32_t ud = out_list_ok(d, ub, d.out_deg[e.x]) ? d.out_deg[e.x] : 0;
             int32_t kept_u = 0;
             for (uint32_t jj = 0; jj < ud; ++jj) {
                 const uint2 e2 = d.out_adj[ub + jj];
-                if (e2.x == s) continue;
+                if (e2.x == s || !id_ok(d, e2.x)) continue;
                 const uint32_t via = sat_add(e.y, e2.y);
                 const uint32_t dh = dist[e2.x];
                 ++l_cand;
@@ -729,11 +773,12 @@ __global__ void k_select(Dev d, const uint32_t *VO, uint32_t nVO, uint32_t r, ui
         const uint32_t i = base + lane;
         const bool valid = i < nVO;
         const uint32_t u = valid ? VO[i] : 0;
-        const uint64_t ku = valid ? select_key(d, u) : 0;
-        const uint32_t od = valid ? d.out_deg[u] : 0;
-        const uint32_t id = valid ? d.in_deg[u] : 0;
-        const uint64_t ob = valid ? d.out_beg[u] : 0;
-        const uint64_t ib = valid ? d.in_beg[u] : 0;
+        const bool uok = valid && id_ok(d, u);
+        const uint64_t ku = uok ? select_key(d, u) : 0;
+        const uint64_t ob = uok ? d.out_beg[u] : 0;
+        const uint64_t ib = uok ? d.in_beg[u] : 0;
+        const uint32_t od = (uok && out_list_ok(d, ob, d.out_deg[u])) ? d.out_deg[u] : 0;
+        const uint32_t id = (uok && in_list_ok(d, ib, d.in_deg[u])) ? d.in_deg[u] : 0;
         const uint32_t c = od + id;
         const uint32_t incl = warp_incl_scan(c);
         const uint32_t total = __shfl_sync(FULL, incl, 31);
@@ -751,13 +796,13 @@ __global__ void k_select(Dev d, const uint32_t *VO, uint32_t nVO, uint32_t r, ui
             if (idx < total) {
                 const uint32_t jj = idx - ex_o;
                 const uint32_t nb = jj < od_o ? d.out_adj[ob_o + jj].x : d.in_adj[ib_o + (jj - od_o)].x;
-                bt = select_key(d, nb) < ku_o;
+                bt = id_ok(d, nb) && select_key(d, nb) < ku_o;
             }
             const uint32_t B = __ballot_sync(FULL, bt);
             const uint32_t lo = max(excl, b), hi = min(excl + c, b + 32);
             if (hi > lo && (B & lane_bits(lo - b, hi - b))) beaten = true;
         }
-        const bool sel = valid && !beaten;
+        const bool sel = uok && !beaten;
         if (sel) d.level[u] = r;
         const uint32_t pos = warp_append(sel, &d.ctl->nF);
         if (sel) F[pos] = u;
@@ -774,13 +819,16 @@ __global__ void k_contract_prep(Dev d, const uint32_t *F, uint32_t src_stamp, ui
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF;
          i += gridDim.x * blockDim.x) {
         const uint32_t u = F[i];
-        const uint32_t od = d.out_deg[u], id = d.in_deg[u];
+        if (!id_ok(d, u)) continue;
         const uint64_t ob = d.out_beg[u], ib = d.in_beg[u];
+        const uint32_t od = out_list_ok(d, ob, d.out_deg[u]) ? d.out_deg[u] : 0;
+        const uint32_t id = in_list_ok(d, ib, d.in_deg[u]) ? d.in_deg[u] : 0;
         atomicAdd(&d.ctl->candBound, (unsigned long long)od * id);
         atomicAdd(&d.ctl->degFout, (unsigned long long)od);
         atomicAdd(&d.ctl->degFin, (unsigned long long)id);
         for (uint32_t j = 0; j < id + od; ++j) {
             const uint32_t x = j < id ? d.in_adj[ib + j].x : d.out_adj[ob + (j - id)].x;
+            if (!id_ok(d, x)) continue;
             if (j < id && atomicExch(&d.smark[x], src_stamp) != src_stamp)
                 S2[atomicAdd(&d.ctl->nS2, 1u)] = x;
             if (atomicExch(&d.amark[x], next_r) != next_r) {
@@ -801,8 +849,10 @@ __global__ void k_emit_ch(Dev d, const uint32_t *F, uint32_t nF, uint2 *ch_up, u
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF;
          i += gridDim.x * blockDim.x) {
         const uint32_t u = F[i];
-        const uint32_t od = d.out_deg[u], id = d.in_deg[u];
+        if (!id_ok(d, u)) continue;
         const uint64_t ob = d.out_beg[u], ib = d.in_beg[u];
+        const uint32_t od = out_list_ok(d, ob, d.out_deg[u]) ? d.out_deg[u] : 0;
+        const uint32_t id = in_list_ok(d, ib, d.in_deg[u]) ? d.in_deg[u] : 0;
         const uint64_t pu = atomicAdd(&d.ctl->ch_up_tail, (unsigned long long)od);
         const uint64_t pd = atomicAdd(&d.ctl->ch_dn_tail, (unsigned long long)id);
         if (pu + od > up_cap || pd + id > dn_cap) {
@@ -822,25 +872,32 @@ __global__ void k_compact_lists(Dev d, const uint32_t *X, uint32_t nX, uint32_t 
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nX;
          i += gridDim.x * blockDim.x) {
         const uint32_t x = X[i];
+        if (!id_ok(d, x)) continue;
         {
             const uint64_t b = d.out_beg[x];
             const uint32_t dg = d.out_deg[x];
-            uint32_t k = 0;
-            for (uint32_t j = 0; j < dg; ++j) {
-                const uint2 e = d.out_adj[b + j];
-                if (d.level[e.x] != r) d.out_adj[b + k++] = e;
+            if (out_list_ok(d, b, dg)) {
+                uint32_t k = 0;
+                for (uint32_t j = 0; j < dg; ++j) {
+                    const uint2 e = d.out_adj[b + j];
+                    if (!id_ok(d, e.x)) continue;
+                    if (d.level[e.x] != r) d.out_adj[b + k++] = e;
+                }
+                d.out_deg[x] = k;
             }
-            d.out_deg[x] = k;
         }
         {
             const uint64_t b = d.in_beg[x];
             const uint32_t dg = d.in_deg[x];
-            uint32_t k = 0;
-            for (uint32_t j = 0; j < dg; ++j) {
-                const uint2 e = d.in_adj[b + j];
-                if (d.level[e.x] != r) d.in_adj[b + k++] = e;
+            if (in_list_ok(d, b, dg)) {
+                uint32_t k = 0;
+                for (uint32_t j = 0; j < dg; ++j) {
+                    const uint2 e = d.in_adj[b + j];
+                    if (!id_ok(d, e.x)) continue;
+                    if (d.level[e.x] != r) d.in_adj[b + k++] = e;
+                }
+                d.in_deg[x] = k;
             }
-            d.in_deg[x] = k;
         }
     }
 }
@@ -868,6 +925,7 @@ __global__ void k_relocate(Dev d, const uint32_t *X, uint32_t nX, const uint64_t
         if (reqO[i]) {
             const uint64_t nb = to + posO[i], ob = d.out_beg[x];
             const uint32_t dg = d.out_deg[x];
+            if (!out_list_ok(d, nb, (uint32_t)reqO[i]) || !out_list_ok(d, ob, dg)) continue;
             for (uint32_t j = 0; j < dg; ++j) d.out_adj[nb + j] = d.out_adj[ob + j];
             d.out_beg[x] = nb;
             d.out_cap[x] = (uint32_t)reqO[i];
@@ -875,6 +933,7 @@ __global__ void k_relocate(Dev d, const uint32_t *X, uint32_t nX, const uint64_t
         if (reqI[i]) {
             const uint64_t nb = ti + posI[i], ob = d.in_beg[x];
             const uint32_t dg = d.in_deg[x];
+            if (!in_list_ok(d, nb, (uint32_t)reqI[i]) || !in_list_ok(d, ob, dg)) continue;
             for (uint32_t j = 0; j < dg; ++j) d.in_adj[nb + j] = d.in_adj[ob + j];
             d.in_beg[x] = nb;
             d.in_cap[x] = (uint32_t)reqI[i];
@@ -893,18 +952,19 @@ __global__ void k_insert(Dev d, const uint4 *rec, const uint8_t *flag, uint32_t 
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nRec;
          i += gridDim.x * blockDim.x) {
         const uint4 c = rec[i];  // (v1, v2, w, via)
+        if (!id_ok(d, c.x) || !id_ok(d, c.y)) continue;
         if (flag[i]) {
             // Lower an existing edge. It sits among the list's entries from
             // before this kernel, ahead of anything appended concurrently.
             const uint64_t ob = d.out_beg[c.x];
-            const uint32_t oc = d.out_cap[c.x];
+            const uint32_t oc = out_list_ok(d, ob, d.out_cap[c.x]) ? d.out_cap[c.x] : 0;
             for (uint32_t j = 0; j < oc; ++j)
                 if (d.out_adj[ob + j].x == c.y) {
                     d.out_adj[ob + j].y = c.z;
                     break;
                 }
             const uint64_t ib = d.in_beg[c.y];
-            const uint32_t ic = d.in_cap[c.y];
+            const uint32_t ic = in_list_ok(d, ib, d.in_cap[c.y]) ? d.in_cap[c.y] : 0;
             for (uint32_t j = 0; j < ic; ++j)
                 if (d.in_adj[ib + j].x == c.x) {
                     d.in_adj[ib + j].y = c.z;
@@ -912,9 +972,15 @@ __global__ void k_insert(Dev d, const uint4 *rec, const uint8_t *flag, uint32_t 
                 }
         } else {
             const uint32_t p = atomicAdd(&d.out_deg[c.x], 1u);
-            d.out_adj[d.out_beg[c.x] + p] = make_uint2(c.y, c.z);
+            if (p < d.out_cap[c.x] && out_list_ok(d, d.out_beg[c.x], p + 1))
+                d.out_adj[d.out_beg[c.x] + p] = make_uint2(c.y, c.z);
+            else
+                atomicOr(&d.ctl->err, ERR_BOUND);
             const uint32_t q = atomicAdd(&d.in_deg[c.y], 1u);
-            d.in_adj[d.in_beg[c.y] + q] = make_uint2(c.x, c.z);
+            if (q < d.in_cap[c.y] && in_list_ok(d, d.in_beg[c.y], q + 1))
+                d.in_adj[d.in_beg[c.y] + q] = make_uint2(c.x, c.z);
+            else
+                atomicOr(&d.ctl->err, ERR_BOUND);
         }
         log[log_base + i] = c;
         log_round[log_base + i] = r;
@@ -947,14 +1013,28 @@ __global__ void k_ranked_deg(const uint32_t *perm, uint32_t n, const uint32_t *d
 
 __global__ void k_ranked_fill(const uint32_t *perm, const uint32_t *rank, uint32_t n,
                               const uint64_t *beg, const uint32_t *deg, const uint2 *src,
-                              const uint32_t *off, uint2 *dst) {
+                              uint64_t src_count, const uint32_t *off, uint64_t dst_count,
+                              uint2 *dst, Ctl *ctl) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t v = perm[i];
+        if (v >= n) {
+            atomicOr(&ctl->err, ERR_BOUND);
+            continue;
+        }
         const uint32_t dg = deg[v];
         const uint64_t b = beg[v];
+        if (b + dg > src_count || (uint64_t)off[i] + dg > dst_count || off[i + 1] - off[i] != dg) {
+            atomicOr(&ctl->err, ERR_BOUND);
+            continue;
+        }
         uint2 *out = dst + off[i];
         for (uint32_t j = 0; j < dg; ++j) {
             const uint2 e = src[b + j];
+            if (e.x >= n) {
+                atomicOr(&ctl->err, ERR_BOUND);
+                out[j] = make_uint2(0, INF);
+                continue;
+            }
             out[j] = make_uint2(rank[e.x], e.y);
         }
         // insertion sort by target rank: the list order becomes canonical
@@ -1053,6 +1133,7 @@ struct Builder {
         CH_CUDA_TRY(cudaMemcpyAsync(hctl, ctl.ptr, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         CH_CUDA_TRY(cudaStreamSynchronize(st));
         if (hctl->err & ERR_INPUT) throw Error{CH_EINVAL, "graph has a malformed offset, id or weight"};
+        if (hctl->err & ERR_BOUND) throw Error{CH_ECUDA, "internal index check failed"};
         if (hctl->err) throw Error{CH_ECUDA, "internal capacity error " + std::to_string(hctl->err)};
     }
 
@@ -1260,6 +1341,8 @@ void Builder::run_rounds() {
         if (regrow) {
             d.out_adj = out_adj.ptr;
             d.in_adj = in_adj.ptr;
+            d.out_arena = out_adj.count;
+            d.in_arena = in_adj.count;
         }
         CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->cand, 0, 8 * 5, st));
         // 5: witness searches for V_F's candidates
@@ -1359,10 +1442,12 @@ void Builder::postprocess() {
         k_ranked_fill<<<gn, 256, 0, st>>>(h->perm.ptr, h->rank.ptr, n,
                                           dir == 0 ? ch_up_beg.ptr : ch_dn_beg.ptr,
                                           dir == 0 ? ch_up_deg.ptr : ch_dn_deg.ptr,
-                                          dir == 0 ? ch_up.ptr : ch_dn.ptr, off.ptr, adj.ptr);
+                                          dir == 0 ? ch_up.ptr : ch_dn.ptr,
+                                          dir == 0 ? hctl->ch_up_tail : hctl->ch_dn_tail, off.ptr,
+                                          dir == 0 ? n_up : n_dn, adj.ptr, ctl.ptr);
         CH_CHECK_LAUNCH();
     }
-    CH_CUDA_TRY(cudaStreamSynchronize(st));
+    sync_ctl();
 }
 
 }  // namespace
@@ -1476,6 +1561,8 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     d.in_cap = b.in_cap.ptr;
     d.out_adj = b.out_adj.ptr;
     d.in_adj = b.in_adj.ptr;
+    d.out_arena = b.out_adj.count;
+    d.in_arena = b.in_adj.count;
     d.level = b.level.ptr;
     d.P = b.P.ptr;
     d.amark = b.amark.ptr;

@@ -8,12 +8,12 @@
 // gives exact shortest distances on any graph with positive weights, and
 // the result cannot depend on the order of the relaxations.
 //
-// One warp serves one query at a time and pulls the next index from a
-// counter (persistent grid). Its labels live in a shared-memory hash table
-// whose entries carry both directions' distances, so the meeting minimum is
-// one pass over the table. A query whose search spaces do not fit is
-// redone by a second kernel that keeps labels in dense per-vertex arrays in
-// global memory (one block per array slot).
+// One block serves one query at a time and pulls the next index from a
+// counter (persistent grid, three blocks per SM). Its labels live in a
+// shared-memory hash table whose entries carry both directions' distances,
+// so the meeting minimum is one pass over the table. A query whose search
+// spaces do not fit is redone by a second kernel that keeps labels in dense
+// per-vertex arrays in global memory (one block per array slot).
 
 #include <algorithm>
 
@@ -24,80 +24,95 @@ namespace {
 
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t QERR_RANGE = 1u;
+constexpr uint32_t QERR_BOUND = 2u;  // an index check failed; the access was skipped
 
-constexpr int Q_WARPS = 4;            // warps per block
-constexpr int Q_TBITS = 10;           // 1024 vertices per query table
-constexpr int Q_T = 1 << Q_TBITS;
-constexpr int Q_FC = 512;             // frontier capacity
+constexpr int QB_THREADS = 256;        // threads per query block
+constexpr int QB_TBITS = 12;           // 4096 vertices per query table
+constexpr int QB_T = 1 << QB_TBITS;
+constexpr int QB_FC = 1280;            // frontier capacity
 constexpr uint64_t Q_CHUNK = 1u << 22;  // queries per launch pair
 
-struct QSmem {
-    uint32_t key[Q_T];
-    uint32_t df[Q_T];
-    uint32_t db[Q_T];
-    uint32_t fst[Q_T];
-    uint32_t front[2][Q_FC];
+// Shared state of one query block: a hash table of reached vertices whose
+// entries carry both directions' labels, and a double-buffered frontier.
+struct QBSmem {
+    uint32_t key[QB_T];
+    uint32_t df[QB_T];
+    uint32_t db[QB_T];
+    uint32_t fst[QB_T];
+    uint32_t front[2][QB_FC];
     uint32_t nf[2];
-    uint32_t flag;
+    uint32_t item, ovf, mu, cnt, ss, st;
 };
 
 struct QArgs {
     uint32_t n;
+    uint32_t n_up, n_dn;  // edge counts of the two CSRs, for index checks
     const uint32_t *rank;
     const uint32_t *up_off, *dn_off;
     const uint2 *up_adj, *dn_adj;
     const uint32_t *src, *dst;
     uint32_t *out, *settled;
     uint64_t k;
-    uint32_t *work;      // [0]: warp path counter, [1]: fallback counter, [2]: overflow count
+    uint32_t *work;      // [0]: block path counter, [1]: fallback counter, [2]: overflow count
     uint32_t *ovf;
     uint32_t *err;
 };
 
-__device__ __forceinline__ uint32_t q_hash(uint32_t v) {
-    return (v * 2654435761u) >> (32 - Q_TBITS);
+__device__ __forceinline__ uint32_t qb_hash(uint32_t v) {
+    return (v * 2654435761u) >> (32 - QB_TBITS);
 }
 
-__device__ __forceinline__ uint32_t q_insert(uint32_t *keys, uint32_t v) {
-    uint32_t h = q_hash(v);
-    for (uint32_t probe = 0; probe < (uint32_t)Q_T; ++probe) {
+__device__ __forceinline__ uint32_t qb_insert(uint32_t *keys, uint32_t v) {
+    uint32_t h = qb_hash(v);
+    for (uint32_t probe = 0; probe < (uint32_t)QB_T; ++probe) {
         uint32_t k = keys[h];
         if (k == v) return h;
         if (k == EMPTY) {
             uint32_t old = atomicCAS(&keys[h], EMPTY, v);
             if (old == EMPTY || old == v) return h;
         }
-        h = (h + 1) & (Q_T - 1);
+        h = (h + 1) & (QB_T - 1);
     }
     return EMPTY;
 }
 
-// Label-correcting upward search of one direction inside the warp's table.
-// Returns false on table or frontier overflow.
-__device__ bool warp_search(QSmem &q, uint32_t root_slot, uint32_t *dist,
-                            const uint32_t *off, const uint2 *adj, uint32_t &stamp) {
-    const uint32_t lane = lane_id();
-    if (lane == 0) {
-        q.front[0][0] = root_slot;
-        q.nf[0] = 1;
-    }
-    __syncwarp();
-    uint32_t cur = 0;
+// Label-correcting upward search of one direction inside the block's table,
+// from the root whose slot the caller put in front[0][0] (with nf[0] = 1).
+// Returns false on table or frontier overflow. Every control value
+// (frontier size, overflow flag) is read by all threads between two
+// barriers and written only after the second, so no thread can see a value
+// meant for a later step.
+__device__ bool block_search(QBSmem &q, uint32_t *dist, const uint32_t *off, const uint2 *adj,
+                             uint32_t n, uint32_t n_edges, uint32_t *err, uint32_t &stamp) {
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+    uint32_t c = 0;
     while (true) {
-        const uint32_t nfront = q.nf[cur];
-        if (nfront == 0) break;
-        const uint32_t nxt = cur ^ 1u;
+        __syncthreads();
+        const uint32_t nfront = q.nf[c];
+        const uint32_t ovf = q.ovf;
+        __syncthreads();
+        if (ovf) return false;
+        if (nfront == 0) return true;
         ++stamp;
-        __syncwarp();
-        if (lane == 0) q.nf[nxt] = 0;
-        __syncwarp();
-        for (uint32_t f0 = 0; f0 < nfront; f0 += 32) {
+        if (tid == 0) q.nf[c ^ 1u] = 0;
+        __syncthreads();
+        // each warp flattens the out-edges of 32 frontier vertices at a time
+        for (uint32_t f0 = warp * 32; f0 < nfront; f0 += nwarps * 32) {
             const uint32_t fi = f0 + lane;
-            const bool fv = fi < nfront;
-            const uint32_t slot = fv ? q.front[cur][fi] : 0;
-            const uint32_t x = fv ? q.key[slot] : 0;
-            const uint32_t b = fv ? off[x] : 0;
-            const uint32_t cnt = fv ? off[x + 1] - b : 0;
+            const bool fv = fi < nfront && fi < (uint32_t)QB_FC;
+            uint32_t slot = fv ? q.front[c][fi] : 0;
+            bool sok = fv && slot < (uint32_t)QB_T;
+            if (fv && !sok) atomicOr(err, QERR_BOUND);
+            const uint32_t x = sok ? q.key[slot] : 0;
+            const bool xok = sok && x < n;
+            if (sok && !xok) atomicOr(err, QERR_BOUND);
+            const uint32_t b = xok ? off[x] : 0;
+            const uint32_t e_end = xok ? off[x + 1] : 0;
+            uint32_t cnt = 0;
+            if (xok && b <= e_end && e_end <= n_edges) cnt = e_end - b;
+            else if (xok) atomicOr(err, QERR_BOUND);
+            if (!xok) slot = 0;
             const uint32_t incl = warp_incl_scan(cnt);
             const uint32_t total = __shfl_sync(FULL, incl, 31);
             const uint32_t excl = incl - cnt;
@@ -110,41 +125,42 @@ __device__ bool warp_search(QSmem &q, uint32_t root_slot, uint32_t *dist,
                 if (idx < total) {
                     const uint2 e = adj[b_o + (idx - ex_o)];
                     const uint32_t nd = sat_add(dist[slot_o], e.y);
-                    if (nd != INF) {
-                        const uint32_t ys = q_insert(q.key, e.x);
+                    if (e.x >= n) {
+                        atomicOr(err, QERR_BOUND);
+                    } else if (nd != INF) {
+                        const uint32_t ys = qb_insert(q.key, e.x);
                         if (ys == EMPTY) {
-                            q.flag = 1;
+                            q.ovf = 1;
                         } else {
                             const uint32_t old = atomicMin(&dist[ys], nd);
                             if (nd < old && atomicExch(&q.fst[ys], stamp) != stamp) {
-                                const uint32_t p = atomicAdd(&q.nf[nxt], 1u);
-                                if (p < (uint32_t)Q_FC) q.front[nxt][p] = ys;
-                                else q.flag = 1;
+                                const uint32_t p = atomicAdd(&q.nf[c ^ 1u], 1u);
+                                if (p < (uint32_t)QB_FC) q.front[c ^ 1u][p] = ys;
+                                else q.ovf = 1;
                             }
                         }
                     }
                 }
             }
         }
-        __syncwarp();
-        if (q.flag) return false;
-        cur = nxt;
+        c ^= 1u;
     }
-    return true;
 }
 
-__global__ void __launch_bounds__(Q_WARPS * 32) k_query_warp(QArgs a) {
-    extern __shared__ __align__(16) unsigned char q_raw[];
-    QSmem &q = reinterpret_cast<QSmem *>(q_raw)[threadIdx.x >> 5];
-    const uint32_t lane = lane_id();
+__global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
+    extern __shared__ __align__(16) unsigned char qb_raw[];
+    QBSmem &q = *reinterpret_cast<QBSmem *>(qb_raw);
+    const uint32_t tid = threadIdx.x;
+    uint32_t stamp = 0;
     while (true) {
-        uint32_t i = 0;
-        if (lane == 0) i = atomicAdd(&a.work[0], 1u);
-        i = __shfl_sync(FULL, i, 0);
+        __syncthreads();
+        if (tid == 0) q.item = atomicAdd(&a.work[0], 1u);
+        __syncthreads();
+        const uint32_t i = q.item;
         if (i >= a.k) break;
         const uint32_t s = a.src[i], t = a.dst[i];
         if (s >= a.n || t >= a.n) {
-            if (lane == 0) {
+            if (tid == 0) {
                 atomicOr(a.err, QERR_RANGE);
                 a.out[i] = INF;
                 if (a.settled) a.settled[i] = 0;
@@ -152,34 +168,49 @@ __global__ void __launch_bounds__(Q_WARPS * 32) k_query_warp(QArgs a) {
             continue;
         }
         const uint32_t rs = a.rank[s], rt = a.rank[t];
-        for (uint32_t j = lane; j < (uint32_t)Q_T; j += 32) {
+        if (rs >= a.n || rt >= a.n) {
+            if (tid == 0) {
+                atomicOr(a.err, QERR_BOUND);
+                a.out[i] = INF;
+            }
+            continue;
+        }
+        for (uint32_t j = tid; j < (uint32_t)QB_T; j += blockDim.x) {
             q.key[j] = EMPTY;
             q.df[j] = INF;
             q.db[j] = INF;
             q.fst[j] = 0;
         }
-        __syncwarp();
-        if (lane == 0) q.flag = 0;
-        uint32_t ss = 0, st = 0;
-        if (lane == 0) {
-            ss = q_insert(q.key, rs);
+        stamp = 0;
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t ss = qb_insert(q.key, rs);
             q.df[ss] = 0;
-            st = q_insert(q.key, rt);
+            const uint32_t st = qb_insert(q.key, rt);
             q.db[st] = 0;
+            q.ss = ss;
+            q.st = st;
+            q.ovf = 0;
+            q.mu = INF;
+            q.cnt = 0;
+            q.front[0][0] = ss;
+            q.nf[0] = 1;
         }
-        ss = __shfl_sync(FULL, ss, 0);
-        st = __shfl_sync(FULL, st, 0);
-        __syncwarp();
-        uint32_t stamp = 0;
-        bool ok = warp_search(q, ss, q.df, a.up_off, a.up_adj, stamp);
-        if (ok) ok = warp_search(q, st, q.db, a.dn_off, a.dn_adj, stamp);
+        bool ok = block_search(q, q.df, a.up_off, a.up_adj, a.n, a.n_up, a.err, stamp);
+        if (ok) {
+            __syncthreads();
+            if (tid == 0) {
+                q.front[0][0] = q.st;
+                q.nf[0] = 1;
+            }
+            ok = block_search(q, q.db, a.dn_off, a.dn_adj, a.n, a.n_dn, a.err, stamp);
+        }
         if (!ok) {
-            if (lane == 0) a.ovf[atomicAdd(&a.work[2], 1u)] = i;
-            __syncwarp();
+            if (tid == 0) a.ovf[atomicAdd(&a.work[2], 1u)] = i;
             continue;
         }
         uint32_t mu = INF, cnt = 0;
-        for (uint32_t j = lane; j < (uint32_t)Q_T; j += 32) {
+        for (uint32_t j = tid; j < (uint32_t)QB_T; j += blockDim.x) {
             const uint32_t f = q.df[j], g = q.db[j];
             mu = min(mu, sat_add(f, g));
             cnt += (f != INF) + (g != INF);
@@ -189,11 +220,15 @@ __global__ void __launch_bounds__(Q_WARPS * 32) k_query_warp(QArgs a) {
             mu = min(mu, __shfl_xor_sync(FULL, mu, o));
             cnt += __shfl_xor_sync(FULL, cnt, o);
         }
-        if (lane == 0) {
-            a.out[i] = mu;
-            if (a.settled) a.settled[i] = cnt;
+        if (lane_id() == 0) {
+            atomicMin(&q.mu, mu);
+            atomicAdd(&q.cnt, cnt);
         }
-        __syncwarp();
+        __syncthreads();
+        if (tid == 0) {
+            a.out[i] = q.mu;
+            if (a.settled) a.settled[i] = q.cnt;
+        }
     }
 }
 
@@ -205,7 +240,8 @@ struct QDense {
 
 __device__ void dense_search(uint32_t root, uint32_t *dist, uint32_t *fst, uint32_t *fa,
                              uint32_t *fb, uint32_t *touched, uint32_t *s_nt, uint32_t *s_nf,
-                             const uint32_t *off, const uint2 *adj, uint32_t &stamp) {
+                             const uint32_t *off, const uint2 *adj, uint32_t n,
+                             uint32_t n_edges, uint32_t *err, uint32_t &stamp) {
     const uint32_t tid = threadIdx.x;
     if (tid == 0) {
         dist[root] = 0;
@@ -225,11 +261,24 @@ __device__ void dense_search(uint32_t root, uint32_t *dist, uint32_t *fst, uint3
         __syncthreads();
         for (uint32_t f = tid; f < nf; f += blockDim.x) {
             const uint32_t x = cur[f];
+            if (x >= n) {
+                atomicOr(err, QERR_BOUND);
+                continue;
+            }
             const uint32_t dx = dist[x];
-            for (uint32_t j = off[x]; j < off[x + 1]; ++j) {
+            const uint32_t jb = off[x], je = off[x + 1];
+            if (jb > je || je > n_edges) {
+                atomicOr(err, QERR_BOUND);
+                continue;
+            }
+            for (uint32_t j = jb; j < je; ++j) {
                 const uint2 e = adj[j];
                 const uint32_t nd = sat_add(dx, e.y);
                 if (nd == INF) continue;
+                if (e.x >= n) {
+                    atomicOr(err, QERR_BOUND);
+                    continue;
+                }
                 const uint32_t old = atomicMin(&dist[e.x], nd);
                 if (nd < old) {
                     if (old == INF) touched[atomicAdd(s_nt, 1u)] = e.x;
@@ -264,11 +313,17 @@ __global__ void __launch_bounds__(256) k_query_dense(QArgs a, QDense dn) {
         if (s_item >= novf) break;
         const uint32_t i = a.ovf[s_item];
         const uint32_t rs = a.rank[a.src[i]], rt = a.rank[a.dst[i]];
+        if (rs >= a.n || rt >= a.n) {
+            if (tid == 0) atomicOr(a.err, QERR_BOUND);
+            continue;
+        }
         // forward labels live in df, backward in db; touched lists both
-        dense_search(rs, df, fst, fa, fb, touched, &s_nt, s_nf, a.up_off, a.up_adj, stamp);
+        dense_search(rs, df, fst, fa, fb, touched, &s_nt, s_nf, a.up_off, a.up_adj, a.n, a.n_up,
+                     a.err, stamp);
         __syncthreads();
         const uint32_t nt_f = s_nt;
-        dense_search(rt, db, fst, fa, fb, touched, &s_nt, s_nf, a.dn_off, a.dn_adj, stamp);
+        dense_search(rt, db, fst, fa, fb, touched, &s_nt, s_nf, a.dn_off, a.dn_adj, a.n, a.n_dn,
+                     a.err, stamp);
         __syncthreads();
         const uint32_t nt = s_nt;
         // The touched list holds each vertex reached forward once (first nt_f
@@ -295,7 +350,7 @@ __global__ void __launch_bounds__(256) k_query_dense(QArgs a, QDense dn) {
     }
 }
 
-int g_q_blocks_per_sm = -1;
+int g_qb_blocks_per_sm = -1;
 
 }  // namespace
 
@@ -315,14 +370,14 @@ void query_init(ch_s *h) {
     // df, db: INF; fst: 0; the rest need no initial value
     CH_CUDA_TRY(cudaMemset(h->q_dense.ptr, 0xFF, sn * 2 * 4));
     CH_CUDA_TRY(cudaMemset(h->q_dense.ptr + 2 * sn, 0, sn * 4));
-    if (g_q_blocks_per_sm < 0) {
-        const size_t smem = sizeof(QSmem) * Q_WARPS;
-        CH_CUDA_TRY(cudaFuncSetAttribute(k_query_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (g_qb_blocks_per_sm < 0) {
+        const size_t smem = sizeof(QBSmem);
+        CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
         int b = 0;
-        CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_warp,
-                                                                  Q_WARPS * 32, smem));
-        g_q_blocks_per_sm = std::max(1, b);
+        CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block, QB_THREADS,
+                                                                  smem));
+        g_qb_blocks_per_sm = std::max(1, b);
     }
     CH_CUDA_TRY(cudaDeviceSynchronize());
 }
@@ -330,7 +385,7 @@ void query_init(ch_s *h) {
 void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
                  uint32_t *dist_out, uint32_t *settled_out, cudaStream_t st) {
     if (k == 0) return;
-    const size_t smem = sizeof(QSmem) * Q_WARPS;
+    const size_t smem = sizeof(QBSmem);
     const int sms = device_sm_count();
     const size_t sn = (size_t)h->q_slots * std::max<uint32_t>(h->n, 1);
     QDense dn;
@@ -345,6 +400,8 @@ void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
         const uint64_t kc = std::min<uint64_t>(Q_CHUNK, k - c0);
         QArgs a;
         a.n = h->n;
+        a.n_up = (uint32_t)h->n_up;
+        a.n_dn = (uint32_t)h->n_down;
         a.rank = h->rank.ptr;
         a.up_off = h->up_off.ptr;
         a.dn_off = h->dn_off.ptr;
@@ -359,9 +416,8 @@ void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
         a.ovf = h->q_ovf_list.ptr;
         a.err = h->qerr.ptr;
         CH_CUDA_TRY(cudaMemsetAsync(h->qwork.ptr, 0, 4 * sizeof(uint32_t), st));
-        const uint64_t want = (kc + Q_WARPS - 1) / Q_WARPS;
-        const int blocks = (int)std::min<uint64_t>(want, (uint64_t)sms * g_q_blocks_per_sm);
-        k_query_warp<<<blocks, Q_WARPS * 32, smem, st>>>(a);
+        const int blocks = (int)std::min<uint64_t>(kc, (uint64_t)sms * g_qb_blocks_per_sm);
+        k_query_block<<<blocks, QB_THREADS, smem, st>>>(a);
         CH_CHECK_LAUNCH();
         k_query_dense<<<h->q_slots, 256, 0, st>>>(a, dn);
         CH_CHECK_LAUNCH();
