@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--hop-limit", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--build-only", action="store_true",
+                    help="time the CH build alone (profiling the build kernels)")
+    ap.add_argument("--queries", type=int, default=None,
+                    help="query batch size (default: the workload's)")
     return ap.parse_args()
 
 
@@ -181,6 +185,8 @@ def main():
     from paper_2412_18008_gb300 import ch
 
     n, gseed, qseed, nq = WORKLOADS[args.workload]
+    if args.queries is not None:
+        nq = args.queries
     g = I.geometric_knn_graph(n, seed=gseed)
     s_h, t_h = I.random_pairs(n, nq, seed=qseed)
     off_d = torch.from_numpy(g.offsets.view(np.int64)).to(dev)
@@ -196,7 +202,8 @@ def main():
     def step():
         h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
                         hop_limit=args.hop_limit, stream=stream)
-        h.query_batch_raw(s_d.data_ptr(), t_d.data_ptr(), nq, out_d.data_ptr(), None, sp)
+        if not args.build_only:
+            h.query_batch_raw(s_d.data_ptr(), t_d.data_ptr(), nq, out_d.data_ptr(), None, sp)
         return h
 
     torch.cuda.synchronize()
@@ -225,7 +232,8 @@ def main():
             h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
                             hop_limit=args.hop_limit, stream=stream)
             e1.record(stream)
-            h.query_batch_raw(s_d.data_ptr(), t_d.data_ptr(), nq, out_d.data_ptr(), None, sp)
+            if not args.build_only:
+                h.query_batch_raw(s_d.data_ptr(), t_d.data_ptr(), nq, out_d.data_ptr(), None, sp)
             e2.record(stream)
         stream.synchronize()
         step_ms.append(e0.elapsed_time(e2))
@@ -252,8 +260,21 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         mean_step, mean_build, mean_query = tt.tolist()
 
+    # per-round profile: the paper observes that most of the work sits in the
+    # first rounds; report the split
+    rt = h_last.round_times()
+    rs = h_last.round_stats()
+    k10 = min(10, len(rt))
+    round_profile = {
+        "rounds": int(len(rt)),
+        "ms_first_10_rounds": float(rt[:k10, :5].sum()),
+        "ms_other_rounds": float(rt[k10:, :5].sum()),
+        "witness_ms_first_10_rounds": float(rt[:k10, 5].sum()),
+        "vertices_left_after_10_rounds": int(rs[k10 - 1, 8]) if k10 else 0,
+    }
+
     # search-space size on a sample of the batch (the paper's query iterations)
-    samp = 100_000
+    samp = min(100_000, nq)
     dd, st = h_last.query(s_d[:samp], t_d[:samp], want_settled=True, stream=stream)
     stream.synchronize()
     mean_ss = float(st.cpu().numpy().view(np.uint32).mean())
@@ -314,6 +335,7 @@ def main():
             "queries_per_s": nq / (mean_query / 1000.0), "query_batch_ms": mean_query,
             "mean_search_space": mean_ss,
             "build_phases_ms": phases,
+            "round_profile": round_profile,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

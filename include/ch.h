@@ -98,7 +98,7 @@ typedef struct {
     uint64_t down_edges;    /* |E_down|: in-edges of each vertex at its contraction */
     double build_ms;        /* device time of ch_build, ms (CUDA events) */
     uint64_t witness_sources;   /* witness searches run, score + contract */
-    uint64_t witness_fallback;  /* of which ran on the global-memory path */
+    uint64_t witness_fallback;  /* of which outgrew a warp's shared-memory tables */
     /* Device time per phase, ms, summed over rounds (CUDA events on the
      * build stream): input normalisation, rescoring (steps 1-2), selection,
      * contraction bookkeeping, contraction witness searches, overlay update,
@@ -111,6 +111,7 @@ typedef struct {
     double witness_ms;
     uint64_t witness_launches;
     uint64_t witness_bytes;
+    uint64_t witness_dense;     /* of which outgrew a block's tables too (global-memory path) */
 } ch_stats_t;
 
 /* Number of per-round statistics fields written by ch_get_round_stats, in
@@ -155,6 +156,14 @@ int ch_get_stats(const ch_t *ch, ch_stats_t *out);
 
 /* Copies min(rounds, max_rounds) rows of CH_NSTAT uint64 values to `out`. */
 int ch_get_round_stats(const ch_t *ch, uint64_t *out, uint32_t max_rounds);
+
+/* Per-round device time (ms, CUDA events on the build stream), CH_NTIME
+ * doubles per round in this order: rescoring (steps 1-2), selection,
+ * contraction bookkeeping, contraction witness searches, overlay update,
+ * witness-search kernels alone (both phases). The per-round breakdown of
+ * the paper's Sec. 6 experiments. */
+#define CH_NTIME 6u
+int ch_get_round_times(const ch_t *ch, double *out, uint32_t max_rounds);
 
 /* Copies the hierarchy to HOST buffers; any pointer may be NULL to skip it.
  *   level[n]    round in which each vertex was contracted

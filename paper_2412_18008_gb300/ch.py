@@ -25,6 +25,8 @@ CH_TIE_HASHED = 0
 CH_TIE_ID = 1
 CH_PRIO_EDGE_DIFF = 0
 CH_NSTAT = 10
+CH_NTIME = 6
+ROUND_TIME_FIELDS = ("score_ms", "select_ms", "prep_ms", "contract_ms", "update_ms", "witness_ms")
 
 ROUND_STAT_FIELDS = ("affected", "score_sources", "selected", "contract_sources",
                      "candidates", "kept", "merged", "inserted", "vo_after", "eo_after")
@@ -55,7 +57,8 @@ class StatsT(C.Structure):
                 ("normalise_ms", C.c_double), ("score_ms", C.c_double), ("select_ms", C.c_double),
                 ("prep_ms", C.c_double), ("contract_ms", C.c_double), ("update_ms", C.c_double),
                 ("postprocess_ms", C.c_double), ("witness_ms", C.c_double),
-                ("witness_launches", C.c_uint64), ("witness_bytes", C.c_uint64)]
+                ("witness_launches", C.c_uint64), ("witness_bytes", C.c_uint64),
+                ("witness_dense", C.c_uint64)]
 
 
 _lib = None
@@ -85,9 +88,10 @@ def load(build_if_missing: bool = True):
     lib.ch_query_status.argtypes = [P, P]
     lib.ch_get_stats.argtypes = [P, C.POINTER(StatsT)]
     lib.ch_get_round_stats.argtypes = [P, P, C.c_uint32]
+    lib.ch_get_round_times.argtypes = [P, P, C.c_uint32]
     lib.ch_export.argtypes = [P, P, P, P, P, P, P]
     for f in ("ch_build", "ch_query_batch", "ch_query_batch_host", "ch_query_status",
-              "ch_get_stats", "ch_get_round_stats", "ch_export"):
+              "ch_get_stats", "ch_get_round_stats", "ch_get_round_times", "ch_export"):
         getattr(lib, f).restype = C.c_int
     lib.ch_free.argtypes = [P]
     lib.ch_free.restype = None
@@ -227,6 +231,14 @@ class CH:
         out = np.zeros((r, CH_NSTAT), np.uint64)
         if r:
             _check(load().ch_get_round_stats(self._h, _hp(out), r))
+        return out
+
+    def round_times(self) -> np.ndarray:
+        """Per-round device time (ms) of each phase, ROUND_TIME_FIELDS columns."""
+        r = self.stats()["rounds"]
+        out = np.zeros((r, CH_NTIME), np.float64)
+        if r:
+            _check(load().ch_get_round_times(self._h, _hp(out), r))
         return out
 
     def export(self) -> dict:

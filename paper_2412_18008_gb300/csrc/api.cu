@@ -231,6 +231,17 @@ int ch_get_round_stats(const ch_t *ch, uint64_t *out, uint32_t max_rounds) {
     return CH_OK;
 }
 
+int ch_get_round_times(const ch_t *ch, double *out, uint32_t max_rounds) {
+    if (!ch || (!out && max_rounds)) {
+        g_last_error = "null argument";
+        return CH_EINVAL;
+    }
+    const uint32_t r = std::min<uint32_t>(max_rounds, (uint32_t)ch->round_times.size());
+    for (uint32_t i = 0; i < r; ++i)
+        for (uint32_t f = 0; f < CH_NTIME; ++f) out[(size_t)i * CH_NTIME + f] = ch->round_times[i][f];
+    return CH_OK;
+}
+
 int ch_export(const ch_t *ch, uint32_t *level, int32_t *priority, uint32_t *rank,
               uint32_t *shortcuts, uint32_t *up, uint32_t *down) {
     if (!ch) {

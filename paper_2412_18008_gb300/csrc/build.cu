@@ -64,13 +64,13 @@ constexpr int WIT_MC = 128;        // distinct targets merged per source
 
 struct Ctl {
     uint32_t nVO, nVO2, nS, nS2, nF, nAnext, nOvf, nRec;
-    uint32_t err, work, work2, pad;
+    uint32_t err, work, work2, work3, nOvf2, pad;
     unsigned long long candBound, degFout, degFin, degAnext;
     unsigned long long cand, kept, merged, inserted, newEdges;
     unsigned long long out_tail, in_tail, ch_up_tail, ch_dn_tail;
     unsigned long long relocOut, relocIn;
     unsigned long long wit_sources, wit_fallback, wit_vertices, wit_edges, wit_middles,
-        wit_midedges;
+        wit_midedges, wit_block;
 };
 
 struct Dev {
@@ -94,7 +94,8 @@ struct WArgs {
     const uint32_t *nS;      // its length (device)
     uint32_t *work;          // dynamic work counter
     uint32_t round;
-    uint32_t *ovf;           // overflowed sources
+    uint32_t *ovf;           // sources the warp tier could not hold (for the block tier)
+    uint32_t *ovf2;          // sources the block tier could not hold (for the dense tier)
     uint4 *rec;              // PRUNE: shortcut records (v1, v2, w, via)
     uint8_t *rec_flag;       // PRUNE: 1 = lowers an existing edge
     uint64_t rec_cap;
@@ -345,7 +346,10 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             if (lane == 0) atomicOr(&ctl->err, ERR_BOUND);
             continue;
         }
-        c_src += (lane == 0);
+        // Algorithmic-traffic counters of this source, added to the totals
+        // only if this tier completes it (an overflowed source is redone,
+        // and counted, by the next tier).
+        unsigned long long l_vert = 0, l_edge = 0, l_mid = 0, l_midedge = 0;
 
         // Phase 0: heaviest candidate weight of this source.
         uint32_t bound = 0;
@@ -357,8 +361,8 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             uint32_t cnt = mid ? d.out_deg[e.x] : 0;
             const uint64_t ub = mid ? d.out_beg[e.x] : 0;
             if (mid && !out_list_ok(d, ub, cnt)) cnt = 0;
-            c_mid += mid;
-            c_midedge += cnt;
+            l_mid += mid;
+            l_midedge += cnt;
             const uint32_t incl = warp_incl_scan(cnt);
             const uint32_t total = __shfl_sync(FULL, incl, 31);
             const uint32_t excl = incl - cnt;
@@ -375,7 +379,12 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             }
         }
         bound = warp_max(bound);
-        if (bound == 0) continue;  // no candidate pair from this source
+        if (bound == 0) {  // no candidate pair from this source
+            c_src += (lane == 0);
+            c_mid += l_mid;
+            c_midedge += l_midedge;
+            continue;
+        }
 
         // Phase 1: hop-limited Bellman-Ford from s, levels 1..H, each level
         // relaxing from the previous level's values (frontier snapshots).
@@ -410,8 +419,8 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                 uint32_t cnt = fv ? d.out_deg[x] : 0;
                 const uint64_t xb = fv ? d.out_beg[x] : 0;
                 if (fv && !out_list_ok(d, xb, cnt)) cnt = 0;
-                c_vert += fv;
-                c_edge += cnt;
+                l_vert += fv;
+                l_edge += cnt;
                 const uint32_t incl = warp_incl_scan(cnt);
                 const uint32_t total = __shfl_sync(FULL, incl, 31);
                 const uint32_t excl = incl - cnt;
@@ -560,6 +569,11 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             if (lane == 0) d.new_out[s] = tot_new;
             __syncwarp();
         }
+        c_src += (lane == 0);
+        c_vert += l_vert;
+        c_edge += l_edge;
+        c_mid += l_mid;
+        c_midedge += l_midedge;
     }
     // Counters (lane-local sums folded per warp).
     c_src = warp_sum((uint32_t)c_src);
@@ -574,6 +588,290 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
 #undef FOLD64
     if (lane == 0) {
         atomicAdd(&ctl->wit_sources, c_src);
+        atomicAdd(&ctl->wit_vertices, c_vert);
+        atomicAdd(&ctl->wit_edges, c_edge);
+        atomicAdd(&ctl->wit_middles, c_mid);
+        atomicAdd(&ctl->wit_midedges, c_midedge);
+        if (MODE == MODE_PRUNE) {
+            atomicAdd(&ctl->cand, c_cand);
+            atomicAdd(&ctl->kept, c_kept);
+            atomicAdd(&ctl->merged, c_merged);
+            atomicAdd(&ctl->inserted, c_ins);
+            atomicAdd(&ctl->newEdges, c_new);
+        }
+    }
+}
+
+// Block tier: the same search for sources whose ball outgrew a warp's
+// tables, run by a whole block with tables 16 times larger in shared memory
+// (about 105 KB, two blocks per SM). Sources that outgrow these too go on to
+// the dense tier. Control values (frontier size, overflow flag, bound) are
+// read by all threads between two barriers and written only after the
+// second.
+constexpr int WB_THREADS = 256;
+constexpr int WB_TBITS = 12;
+constexpr int WB_T = 1 << WB_TBITS;
+constexpr int WB_FC = 2048;
+constexpr int WB_MBITS = 11;
+constexpr int WB_M = 1 << WB_MBITS;
+
+struct BlkSmem {
+    uint32_t key[WB_T];
+    uint32_t val[WB_T];
+    uint32_t fst[WB_T];
+    uint2 front[2][WB_FC];
+    uint32_t mkey[WB_M];
+    unsigned long long mval[WB_M];
+    uint32_t cntw[WB_THREADS / 32][32];
+    uint32_t nf[2];
+    uint32_t item, ovf, bound, nnew;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
+    extern __shared__ __align__(16) unsigned char wb_raw[];
+    BlkSmem &b = *reinterpret_cast<BlkSmem *>(wb_raw);
+    const Dev d = a.d;
+    Ctl *ctl = d.ctl;
+    const uint32_t r = a.round;
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const uint32_t nIn = ctl->nOvf;
+    unsigned long long c_src = 0, c_vert = 0, c_edge = 0, c_mid = 0, c_midedge = 0;
+    unsigned long long c_cand = 0, c_kept = 0, c_merged = 0, c_ins = 0, c_new = 0;
+    while (true) {
+        __syncthreads();
+        if (tid == 0) b.item = atomicAdd(&ctl->work3, 1u);
+        __syncthreads();
+        const uint32_t i = b.item;
+        if (i >= nIn) break;
+        const uint32_t s = a.ovf[i];
+        if (s >= d.n) {
+            if (tid == 0) atomicOr(&ctl->err, ERR_BOUND);
+            continue;
+        }
+        const uint64_t sb = d.out_beg[s];
+        const uint32_t sd = d.out_deg[s];
+        if (sb + sd > d.out_arena) {
+            if (tid == 0) atomicOr(&ctl->err, ERR_BOUND);
+            continue;
+        }
+        unsigned long long l_vert = 0, l_edge = 0, l_mid = 0, l_midedge = 0, l_cand = 0, l_kept = 0;
+        for (uint32_t t = tid; t < (uint32_t)WB_T; t += blockDim.x) {
+            b.key[t] = EMPTY;
+            b.val[t] = INF;
+            b.fst[t] = 0;
+        }
+        if (MODE == MODE_PRUNE)
+            for (uint32_t t = tid; t < (uint32_t)WB_M; t += blockDim.x) {
+                b.mkey[t] = EMPTY;
+                b.mval[t] = ~0ull;
+            }
+        if (tid == 0) {
+            b.bound = 0;
+            b.ovf = 0;
+            b.nnew = 0;
+        }
+        __syncthreads();
+        // Phase 0: heaviest candidate weight of the source.
+        uint32_t lb = 0;
+        for (uint32_t j = tid; j < sd; j += blockDim.x) {
+            const uint2 e = d.out_adj[sb + j];
+            if (!id_ok(d, e.x) || !is_middle<MODE>(d, e.x, r)) continue;
+            const uint64_t ub = d.out_beg[e.x];
+            const uint32_t ud = out_list_ok(d, ub, d.out_deg[e.x]) ? d.out_deg[e.x] : 0;
+            ++l_mid;
+            l_midedge += ud;
+            for (uint32_t jj = 0; jj < ud; ++jj) {
+                const uint2 e2 = d.out_adj[ub + jj];
+                if (e2.x != s) lb = max(lb, sat_add(e.y, e2.y));
+            }
+        }
+        if (lb) atomicMax(&b.bound, lb);
+        __syncthreads();
+        const uint32_t bound = b.bound;
+        if (bound == 0) {
+            c_src += (tid == 0);
+            c_mid += l_mid;
+            c_midedge += l_midedge;
+            continue;
+        }
+        if (tid == 0) {
+            const uint32_t h = ht_insert(b.key, WB_TBITS, s);
+            b.val[h] = 0;
+            b.front[0][0] = make_uint2(h, 0);
+            b.nf[0] = 1;
+            b.nf[1] = 0;
+        }
+        // Phase 1: hop-limited Bellman-Ford, one level per iteration, each
+        // level relaxing from the previous level's values (snapshots).
+        uint32_t cur = 0;
+        for (uint32_t lvl = 1; lvl <= d.H; ++lvl) {
+            __syncthreads();
+            const uint32_t nfront = b.nf[cur];
+            const uint32_t ovf = b.ovf;
+            __syncthreads();
+            if (ovf || nfront == 0) break;
+            const uint32_t nxt = cur ^ 1u;
+            if (tid == 0) b.nf[nxt] = 0;
+            __syncthreads();
+            for (uint32_t f0 = warp * 32; f0 < nfront; f0 += nwarps * 32) {
+                const uint32_t fi = f0 + lane;
+                const bool fv = fi < nfront && fi < (uint32_t)WB_FC;
+                const uint2 fe = fv ? b.front[cur][fi] : make_uint2(0, 0);
+                const bool fok = fv && fe.x < (uint32_t)WB_T;
+                if (fv && !fok) atomicOr(&ctl->err, ERR_BOUND);
+                const uint32_t x = fok ? b.key[fe.x] : 0;
+                const bool xok = fok && id_ok(d, x);
+                uint32_t cnt = xok ? d.out_deg[x] : 0;
+                const uint64_t xb = xok ? d.out_beg[x] : 0;
+                if (xok && !out_list_ok(d, xb, cnt)) cnt = 0;
+                l_vert += xok;
+                l_edge += cnt;
+                const uint32_t incl = warp_incl_scan(cnt);
+                const uint32_t total = __shfl_sync(FULL, incl, 31);
+                const uint32_t excl = incl - cnt;
+                for (uint32_t base = 0; base < total; base += 32) {
+                    const uint32_t idx = base + lane;
+                    const uint32_t o = warp_owner(excl, idx);
+                    const uint64_t xb_o = __shfl_sync(FULL, xb, o);
+                    const uint32_t dx_o = __shfl_sync(FULL, fe.y, o);
+                    const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                    if (idx >= total) continue;
+                    const uint2 e = d.out_adj[xb_o + (idx - ex_o)];
+                    const uint32_t nd = sat_add(dx_o, e.y);
+                    if (nd >= bound || !id_ok(d, e.x)) continue;
+                    const uint32_t slot = ht_insert(b.key, WB_TBITS, e.x);
+                    if (slot == EMPTY) {
+                        b.ovf = 1;
+                        continue;
+                    }
+                    const uint32_t old = atomicMin(&b.val[slot], nd);
+                    if (nd < old && atomicExch(&b.fst[slot], lvl) != lvl) {
+                        const uint32_t p = atomicAdd(&b.nf[nxt], 1u);
+                        if (p < (uint32_t)WB_FC) b.front[nxt][p] = make_uint2(slot, 0);
+                        else b.ovf = 1;
+                    }
+                }
+            }
+            __syncthreads();
+            const uint32_t nn = min(b.nf[nxt], (uint32_t)WB_FC);
+            for (uint32_t p = tid; p < nn; p += blockDim.x) b.front[nxt][p].y = b.val[b.front[nxt][p].x];
+            cur = nxt;
+        }
+        __syncthreads();
+        const uint32_t ovf1 = b.ovf;
+        __syncthreads();
+        if (ovf1) {
+            if (tid == 0) a.ovf2[atomicAdd(&ctl->nOvf2, 1u)] = s;
+            continue;
+        }
+        // Phase 2: decisions, each warp taking 32 of the source's out-edges.
+        for (uint32_t c0 = warp * 32; c0 < sd; c0 += nwarps * 32) {
+            const uint32_t j = c0 + lane;
+            const bool valid = j < sd;
+            const uint2 e = valid ? d.out_adj[sb + j] : make_uint2(0, 0);
+            const bool mid = valid && id_ok(d, e.x) && is_middle<MODE>(d, e.x, r);
+            uint32_t cnt = mid ? d.out_deg[e.x] : 0;
+            const uint64_t ub = mid ? d.out_beg[e.x] : 0;
+            if (mid && !out_list_ok(d, ub, cnt)) cnt = 0;
+            const uint32_t incl = warp_incl_scan(cnt);
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            const uint32_t excl = incl - cnt;
+            if (MODE == MODE_SCORE) b.cntw[warp][lane] = 0;
+            __syncwarp();
+            for (uint32_t base = 0; base < total; base += 32) {
+                const uint32_t idx = base + lane;
+                const uint32_t o = warp_owner(excl, idx);
+                const uint64_t ub_o = __shfl_sync(FULL, ub, o);
+                const uint32_t w1 = __shfl_sync(FULL, e.y, o);
+                const uint32_t u_o = __shfl_sync(FULL, e.x, o);
+                const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                if (idx >= total) continue;
+                const uint2 e2 = d.out_adj[ub_o + (idx - ex_o)];
+                if (e2.x == s) continue;
+                const uint32_t via = sat_add(w1, e2.y);
+                const uint32_t slot = ht_find(b.key, WB_TBITS, e2.x);
+                const uint32_t dh = slot == EMPTY ? INF : b.val[slot];
+                ++l_cand;
+                if (via == INF || via > dh) continue;
+                ++l_kept;
+                if (MODE == MODE_SCORE) {
+                    atomicAdd(&b.cntw[warp][o], 1u);
+                } else {
+                    const uint32_t ms = ht_insert(b.mkey, WB_MBITS, e2.x);
+                    if (ms == EMPTY) b.ovf = 1;
+                    else atomicMin(&b.mval[ms], ((unsigned long long)via << 32) | u_o);
+                }
+            }
+            __syncwarp();
+            if (MODE == MODE_SCORE && mid && b.cntw[warp][lane])
+                atomicAdd(&d.P[e.x], (int32_t)b.cntw[warp][lane]);
+            __syncwarp();
+        }
+        __syncthreads();
+        if (MODE == MODE_PRUNE) {
+            const uint32_t ovf2 = b.ovf;
+            __syncthreads();
+            if (ovf2) {
+                if (tid == 0) a.ovf2[atomicAdd(&ctl->nOvf2, 1u)] = s;
+                continue;
+            }
+            uint32_t l_new = 0;
+            for (uint32_t t = tid; t < (uint32_t)WB_M; t += blockDim.x) {
+                const uint32_t v2 = b.mkey[t];
+                if (v2 == EMPTY) continue;
+                const unsigned long long mv = b.mval[t];
+                const uint32_t ws = (uint32_t)(mv >> 32), via = (uint32_t)mv;
+                bool found = false;
+                uint32_t ew = INF;
+                for (uint32_t j = 0; j < sd; ++j) {
+                    const uint2 e = d.out_adj[sb + j];
+                    if (e.x == v2) {
+                        found = true;
+                        ew = e.y;
+                        break;
+                    }
+                }
+                ++c_merged;
+                if (found && !(ws < ew)) continue;
+                const uint32_t pos = atomicAdd(&ctl->nRec, 1u);
+                if (pos < a.rec_cap) {
+                    a.rec[pos] = make_uint4(s, v2, ws, via);
+                    a.rec_flag[pos] = found ? 1 : 0;
+                } else {
+                    atomicOr(&ctl->err, ERR_REC_OVERFLOW);
+                }
+                ++c_ins;
+                if (!found) {
+                    ++l_new;
+                    atomicAdd(&d.new_in[v2], 1u);
+                }
+            }
+            if (l_new) atomicAdd(&b.nnew, l_new);
+            __syncthreads();
+            if (tid == 0) d.new_out[s] = b.nnew;
+            c_cand += l_cand;
+            c_kept += l_kept;
+            c_new += l_new;
+        }
+        c_src += (tid == 0);
+        c_vert += l_vert;
+        c_edge += l_edge;
+        c_mid += l_mid;
+        c_midedge += l_midedge;
+    }
+#define FOLD64(x)                                                               \
+    {                                                                           \
+        unsigned long long v_ = x;                                              \
+        for (int o_ = 16; o_ > 0; o_ >>= 1) v_ += __shfl_xor_sync(FULL, v_, o_); \
+        x = v_;                                                                 \
+    }
+    FOLD64(c_src) FOLD64(c_vert) FOLD64(c_edge) FOLD64(c_mid) FOLD64(c_midedge) FOLD64(c_cand)
+    FOLD64(c_kept) FOLD64(c_merged) FOLD64(c_ins) FOLD64(c_new)
+#undef FOLD64
+    if (lane == 0) {
+        atomicAdd(&ctl->wit_block, c_src);
         atomicAdd(&ctl->wit_vertices, c_vert);
         atomicAdd(&ctl->wit_edges, c_edge);
         atomicAdd(&ctl->wit_middles, c_mid);
@@ -604,7 +902,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
     __shared__ uint32_t s_item, s_bound, s_nt, s_nm, s_nf[2];
     __shared__ unsigned long long s_cnt[5];
     const uint32_t tid = threadIdx.x;
-    const uint32_t nOvf = ctl->nOvf;
+    const uint32_t nOvf = ctl->nOvf2;
     while (true) {
         __syncthreads();
         if (tid == 0) s_item = atomicAdd(&ctl->work2, 1u);
@@ -612,7 +910,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
         __syncthreads();
         const uint32_t i = s_item;
         if (i >= nOvf) break;
-        const uint32_t s = a.ovf[i];
+        const uint32_t s = a.ovf2[i];
         const uint64_t sb = s < n ? d.out_beg[s] : 0;
         const uint32_t sd = (s < n && out_list_ok(d, sb, d.out_deg[s])) ? d.out_deg[s] : 0;
         if (s >= n) {
@@ -1079,6 +1377,7 @@ struct EventPool {
 struct Span {
     cudaEvent_t a, b;
     double *acc;
+    int round, phase;  // phase: index into the per-round timing row, or -1
 };
 
 struct Builder {
@@ -1096,7 +1395,8 @@ struct Builder {
     DevBuf<Ctl> ctl;
     Ctl *hctl = nullptr;  // pinned
     // lists
-    DevBuf<uint32_t> VO, VO2, A, Anext, S, S2, F, ovf, tmp;
+    DevBuf<uint32_t> VO, VO2, A, Anext, S, S2, F, ovf, ovf2, tmp;
+    int blk_blocks = 152;
     DevBuf<uint64_t> reqO, reqI, posO, posI;
     DevBuf<uint32_t> scan32;
     DevBuf<uint64_t> scan64;
@@ -1118,10 +1418,11 @@ struct Builder {
     EventPool pool;
     std::vector<Span> spans;
 
-    void mark(double *acc, cudaEvent_t a) {
+    int cur_round = -1;
+    void mark(double *acc, cudaEvent_t a, int phase = -1) {
         cudaEvent_t b = pool.get();
         CH_CUDA_TRY(cudaEventRecord(b, st));
-        spans.push_back({a, b, acc});
+        spans.push_back({a, b, acc, cur_round, phase});
     }
     cudaEvent_t start() {
         cudaEvent_t a = pool.get();
@@ -1252,7 +1553,7 @@ void Builder::normalise(const ch_graph_t *g) {
 template <int MODE>
 void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_max, uint32_t r) {
     CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->nOvf, 0, 4, st));
-    CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->work, 0, 8, st));  // work, work2
+    CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->work, 0, 16, st));  // work, work2, work3, nOvf2
     WArgs a;
     a.d = d;
     a.S = Sl;
@@ -1260,6 +1561,7 @@ void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_ma
     a.work = &ctl.ptr->work;
     a.round = r;
     a.ovf = ovf.ptr;
+    a.ovf2 = ovf2.ptr;
     a.rec = rec.ptr;
     a.rec_flag = rec_flag.ptr;
     a.rec_cap = rec.count;
@@ -1267,10 +1569,12 @@ void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_ma
     const int blocks = grid_for((uint64_t)nS_max, WIT_WARPS, sms * 8);
     k_witness<MODE><<<blocks, WIT_WARPS * 32, 0, st>>>(a);
     CH_CHECK_LAUNCH();
+    k_witness_block<MODE><<<blk_blocks, WB_THREADS, sizeof(BlkSmem), st>>>(a);
+    CH_CHECK_LAUNCH();
     k_witness_dense<MODE><<<dense.nslots, 256, 0, st>>>(a, dense);
     CH_CHECK_LAUNCH();
-    mark(&h->t_witness_ms, e0);
-    h->witness_launches += 2;
+    mark(&h->t_witness_ms, e0, 5);
+    h->witness_launches += 3;
 }
 
 void Builder::run_rounds() {
@@ -1286,6 +1590,7 @@ void Builder::run_rounds() {
     uint64_t live_edges = h->m_input;
     for (uint32_t r = 0; nVO > 0; ++r) {
         if (r > 0x7FFFFFF0u) throw Error{CH_ERANGE, "too many rounds"};
+        cur_round = (int)r;
         // reset per-round counters
         CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->nS, 0, 4 * 6, st));  // nS nS2 nF nAnext nOvf nRec
         CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->candBound, 0, 8 * 4, st));
@@ -1297,18 +1602,18 @@ void Builder::run_rounds() {
             CH_CHECK_LAUNCH();
             witness<MODE_SCORE>(S.ptr, &ctl.ptr->nS, nA * 4 + 32 > n ? n : nA * 4 + 32, r);
         }
-        mark(&h->t_score_ms, e0);
+        mark(&h->t_score_ms, e0, 0);
         // 3: select
         e0 = start();
         k_select<<<grid_for((uint64_t)nVO, 256, sms * 8), 256, 0, st>>>(d, VO.ptr, nVO, r, F.ptr);
         CH_CHECK_LAUNCH();
-        mark(&h->t_select_ms, e0);
+        mark(&h->t_select_ms, e0, 1);
         // 4: contraction bookkeeping
         e0 = start();
         k_contract_prep<<<grid_for((uint64_t)nVO, 256, sms * 8), 256, 0, st>>>(
             d, F.ptr, cstamp, r + 1, S2.ptr, Anext.ptr);
         CH_CHECK_LAUNCH();
-        mark(&h->t_prep_ms, e0);
+        mark(&h->t_prep_ms, e0, 2);
         sync_ctl();
         const Ctl c = *hctl;
         const uint32_t nF = c.nF, nS2 = c.nS2, nAnext = c.nAnext;
@@ -1348,7 +1653,7 @@ void Builder::run_rounds() {
         // 5: witness searches for V_F's candidates
         e0 = start();
         if (nS2) witness<MODE_PRUNE>(S2.ptr, &ctl.ptr->nS2, nS2, r);
-        mark(&h->t_contract_ms, e0);
+        mark(&h->t_contract_ms, e0, 3);
         // 6-10
         e0 = start();
         k_emit_ch<<<grid_for(nF, 256, sms * 8), 256, 0, st>>>(
@@ -1380,7 +1685,7 @@ void Builder::run_rounds() {
         std::swap(VO, VO2);
         CH_CUDA_TRY(cudaMemcpyAsync(&ctl.ptr->nVO, &ctl.ptr->nVO2, 4, cudaMemcpyDeviceToDevice, st));
         std::swap(A, Anext);
-        mark(&h->t_update_ms, e0);
+        mark(&h->t_update_ms, e0, 4);
         // read this round's contraction counters (one more sync per round
         // keeps the bookkeeping simple; the next round needs nothing from it)
         sync_ctl();
@@ -1508,7 +1813,18 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     b.new_out.zero(b.st);
     b.new_in.alloc(n);
     b.new_in.zero(b.st);
-    for (auto *l : {&b.VO, &b.VO2, &b.A, &b.Anext, &b.S, &b.S2, &b.F, &b.ovf}) l->alloc(n);
+    for (auto *l : {&b.VO, &b.VO2, &b.A, &b.Anext, &b.S, &b.S2, &b.F, &b.ovf, &b.ovf2}) l->alloc(n);
+    {
+        const int smem = (int)sizeof(BlkSmem);
+        CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_SCORE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_PRUNE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int per_sm = 0;
+        CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_witness_block<MODE_PRUNE>,
+                                                                  WB_THREADS, smem));
+        b.blk_blocks = b.sms * std::max(1, per_sm);
+    }
     b.tmp.alloc((size_t)n + 1);
     b.reqO.alloc(n);
     b.reqI.alloc(n);
@@ -1525,9 +1841,10 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     b.ch_dn_beg.alloc(n);
     b.ch_up_deg.alloc(n);
     b.ch_dn_deg.alloc(n);
-    // dense fallback slots: 10 uint32 + 1 uint64 arrays of n per slot, <= 2 GiB
+    // dense fallback slots: 8 uint32 + 1 uint64 arrays of n per slot, about
+    // 1 GiB in all (at least 2 slots, at most 64)
     const uint64_t per_slot = (uint64_t)n * (8 * 4 + 8);
-    uint32_t slots = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(64, (2ull << 30) / per_slot));
+    uint32_t slots = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(64, (1024ull << 20) / per_slot));
     b.dense.nslots = slots;
     b.dn32.alloc((size_t)slots * n * 8);
     b.dn64.alloc((size_t)slots * n);
@@ -1572,24 +1889,29 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     d.ctl = b.ctl.ptr;
 
     b.run_rounds();
+    b.cur_round = -1;
     cudaEvent_t t1 = b.start();
     b.postprocess();
     b.mark(&h->t_post_ms, t1);
     b.mark(&h->stats.build_ms, t0);
     CH_CUDA_TRY(cudaStreamSynchronize(b.st));
 
+    h->round_times.assign(h->round_stats.size(), {});
     for (const Span &s : b.spans) {
         float ms = 0;
         CH_CUDA_TRY(cudaEventElapsedTime(&ms, s.a, s.b));
         *s.acc += ms;
+        if (s.round >= 0 && s.phase >= 0 && (size_t)s.round < h->round_times.size())
+            h->round_times[s.round][s.phase] += ms;
     }
     const Ctl &c = *b.hctl;
-    h->stats.witness_sources = c.wit_sources + c.wit_fallback;
-    h->stats.witness_fallback = c.wit_fallback;
+    h->stats.witness_sources = c.wit_sources + c.wit_block + c.wit_fallback;
+    h->stats.witness_fallback = c.wit_block + c.wit_fallback;
+    h->stats.witness_dense = c.wit_fallback;
     // Algorithmic bytes of the witness kernels: per search the source id
     // (4 B); per vertex whose out-list is read its offset and degree (12 B);
     // per adjacency entry read (id + weight, 8 B).
-    h->witness_bytes = 4 * (c.wit_sources + c.wit_fallback) + 12 * c.wit_vertices +
+    h->witness_bytes = 4 * (c.wit_sources + c.wit_block + c.wit_fallback) + 12 * c.wit_vertices +
                        8 * c.wit_edges + 12 * c.wit_middles + 8 * c.wit_midedges;
 
     h->level = std::move(b.level);

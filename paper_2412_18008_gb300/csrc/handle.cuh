@@ -34,6 +34,7 @@ struct ch_s {
     uint64_t n_up = 0, n_down = 0;
 
     std::vector<std::array<uint64_t, CH_NSTAT>> round_stats;
+    std::vector<std::array<double, CH_NTIME>> round_times;
     ch_stats_t stats{};
 
     // Per-phase device time of the build (ms) and the witness kernels'

@@ -33,14 +33,17 @@ constexpr int QB_FC = 1280;            // frontier capacity
 constexpr uint64_t Q_CHUNK = 1u << 22;  // queries per launch pair
 
 // Shared state of one query block: a hash table of reached vertices whose
-// entries carry both directions' labels, and a double-buffered frontier.
+// entries carry both directions' labels, per-direction frontier stamps, a
+// double-buffered frontier holding both directions' entries (slot | dir<<31)
+// and a triple-buffered frontier counter, so that one barrier per level
+// suffices (see block_search).
 struct QBSmem {
     uint32_t key[QB_T];
     uint32_t df[QB_T];
     uint32_t db[QB_T];
-    uint32_t fst[QB_T];
+    uint32_t fst[QB_T];  // last level that queued the slot: bits 0-15 forward, 16-31 backward
     uint32_t front[2][QB_FC];
-    uint32_t nf[2];
+    uint32_t cnt3[3];
     uint32_t item, ovf, mu, cnt, ss, st;
 };
 
@@ -76,43 +79,68 @@ __device__ __forceinline__ uint32_t qb_insert(uint32_t *keys, uint32_t v) {
     return EMPTY;
 }
 
-// Label-correcting upward search of one direction inside the block's table,
-// from the root whose slot the caller put in front[0][0] (with nf[0] = 1).
-// Returns false on table or frontier overflow. Every control value
-// (frontier size, overflow flag) is read by all threads between two
-// barriers and written only after the second, so no thread can see a value
-// meant for a later step.
-__device__ bool block_search(QBSmem &q, uint32_t *dist, const uint32_t *off, const uint2 *adj,
-                             uint32_t n, uint32_t n_edges, uint32_t *err, uint32_t &stamp) {
+// Marks `slot` as queued for level `lvl` in direction `dir`; true if it was
+// not queued for that level and direction yet.
+__device__ __forceinline__ bool qb_claim(uint32_t *fst, uint32_t slot, uint32_t dir, uint32_t lvl) {
+    const uint32_t shift = dir ? 16u : 0u;
+    uint32_t old = fst[slot];
+    while (true) {
+        if (((old >> shift) & 0xFFFFu) == lvl) return false;
+        const uint32_t want = (old & ~(0xFFFFu << shift)) | (lvl << shift);
+        const uint32_t prev = atomicCAS(&fst[slot], old, want);
+        if (prev == old) return true;
+        old = prev;
+    }
+}
+
+// Both upward searches at once, label-correcting over the rank DAG: the
+// frontier holds forward (E_up) and backward (reversed E_down) entries,
+// each level relaxes the out-edges of every queued vertex with its current
+// label, and the search ends when no label changed. With PRUNE, a relaxation
+// whose new label is not below the best meeting sum found so far is skipped
+// (it cannot improve the answer); the answer is always recomputed at the
+// end as the least df + db over the table, so it is exact either way.
+//
+// Barrier discipline: the only barrier of a level is at its top. The
+// frontier counter of level k lives in cnt3[k % 3]; thread 0 clears the
+// counter of level k + 2 during level k, when no thread reads it any more.
+template <bool PRUNE>
+__device__ bool block_search(QBSmem &q, const QArgs &a) {
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
-    uint32_t c = 0;
-    while (true) {
+    for (uint32_t lvl = 1;; ++lvl) {
         __syncthreads();
-        const uint32_t nfront = q.nf[c];
+        const uint32_t cur = (lvl - 1) & 1u;
+        const uint32_t nfront = q.cnt3[(lvl - 1) % 3];
         const uint32_t ovf = q.ovf;
-        __syncthreads();
         if (ovf) return false;
         if (nfront == 0) return true;
-        ++stamp;
-        if (tid == 0) q.nf[c ^ 1u] = 0;
-        __syncthreads();
-        // each warp flattens the out-edges of 32 frontier vertices at a time
+        if (lvl >= 0xFFFFu) {  // a label-correcting search on a DAG never gets here
+            if (tid == 0) atomicOr(a.err, QERR_BOUND);
+            return false;
+        }
+        if (tid == 0) q.cnt3[(lvl + 1) % 3] = 0;
+        const uint32_t nxt_cnt = lvl % 3;
         for (uint32_t f0 = warp * 32; f0 < nfront; f0 += nwarps * 32) {
             const uint32_t fi = f0 + lane;
             const bool fv = fi < nfront && fi < (uint32_t)QB_FC;
-            uint32_t slot = fv ? q.front[c][fi] : 0;
-            bool sok = fv && slot < (uint32_t)QB_T;
-            if (fv && !sok) atomicOr(err, QERR_BOUND);
+            const uint32_t ent = fv ? q.front[cur][fi] : 0;
+            const uint32_t dir = ent >> 31;
+            uint32_t slot = ent & 0x7FFFFFFFu;
+            const bool sok = fv && slot < (uint32_t)QB_T;
+            if (fv && !sok) atomicOr(a.err, QERR_BOUND);
             const uint32_t x = sok ? q.key[slot] : 0;
-            const bool xok = sok && x < n;
-            if (sok && !xok) atomicOr(err, QERR_BOUND);
+            const bool xok = sok && x < a.n;
+            if (sok && !xok) atomicOr(a.err, QERR_BOUND);
+            const uint32_t *off = dir ? a.dn_off : a.up_off;
+            const uint32_t n_edges = dir ? a.n_dn : a.n_up;
             const uint32_t b = xok ? off[x] : 0;
             const uint32_t e_end = xok ? off[x + 1] : 0;
             uint32_t cnt = 0;
             if (xok && b <= e_end && e_end <= n_edges) cnt = e_end - b;
-            else if (xok) atomicOr(err, QERR_BOUND);
+            else if (xok) atomicOr(a.err, QERR_BOUND);
             if (!xok) slot = 0;
+            const uint32_t dx = xok ? (dir ? q.db[slot] : q.df[slot]) : INF;
             const uint32_t incl = warp_incl_scan(cnt);
             const uint32_t total = __shfl_sync(FULL, incl, 31);
             const uint32_t excl = incl - cnt;
@@ -121,37 +149,44 @@ __device__ bool block_search(QBSmem &q, uint32_t *dist, const uint32_t *off, con
                 const uint32_t o = warp_owner(excl, idx);
                 const uint32_t b_o = __shfl_sync(FULL, b, o);
                 const uint32_t ex_o = __shfl_sync(FULL, excl, o);
-                const uint32_t slot_o = __shfl_sync(FULL, slot, o);
-                if (idx < total) {
-                    const uint2 e = adj[b_o + (idx - ex_o)];
-                    const uint32_t nd = sat_add(dist[slot_o], e.y);
-                    if (e.x >= n) {
-                        atomicOr(err, QERR_BOUND);
-                    } else if (nd != INF) {
-                        const uint32_t ys = qb_insert(q.key, e.x);
-                        if (ys == EMPTY) {
-                            q.ovf = 1;
-                        } else {
-                            const uint32_t old = atomicMin(&dist[ys], nd);
-                            if (nd < old && atomicExch(&q.fst[ys], stamp) != stamp) {
-                                const uint32_t p = atomicAdd(&q.nf[c ^ 1u], 1u);
-                                if (p < (uint32_t)QB_FC) q.front[c ^ 1u][p] = ys;
-                                else q.ovf = 1;
-                            }
-                        }
-                    }
+                const uint32_t dx_o = __shfl_sync(FULL, dx, o);
+                const uint32_t dir_o = __shfl_sync(FULL, dir, o);
+                if (idx >= total) continue;
+                const uint2 e = (dir_o ? a.dn_adj : a.up_adj)[b_o + (idx - ex_o)];
+                const uint32_t nd = sat_add(dx_o, e.y);
+                if (e.x >= a.n) {
+                    atomicOr(a.err, QERR_BOUND);
+                    continue;
+                }
+                if (nd == INF) continue;
+                if (PRUNE && nd >= q.mu) continue;
+                const uint32_t ys = qb_insert(q.key, e.x);
+                if (ys == EMPTY) {
+                    q.ovf = 1;
+                    continue;
+                }
+                uint32_t *dist = dir_o ? q.db : q.df;
+                const uint32_t old = atomicMin(&dist[ys], nd);
+                if (nd >= old) continue;
+                if (PRUNE) {
+                    const uint32_t other = dir_o ? q.df[ys] : q.db[ys];
+                    if (other != INF) atomicMin(&q.mu, sat_add(nd, other));
+                }
+                if (qb_claim(q.fst, ys, dir_o, lvl)) {
+                    const uint32_t p = atomicAdd(&q.cnt3[nxt_cnt], 1u);
+                    if (p < (uint32_t)QB_FC) q.front[cur ^ 1u][p] = ys | (dir_o << 31);
+                    else q.ovf = 1;
                 }
             }
         }
-        c ^= 1u;
     }
 }
 
+template <bool PRUNE>
 __global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
     extern __shared__ __align__(16) unsigned char qb_raw[];
     QBSmem &q = *reinterpret_cast<QBSmem *>(qb_raw);
     const uint32_t tid = threadIdx.x;
-    uint32_t stamp = 0;
     while (true) {
         __syncthreads();
         if (tid == 0) q.item = atomicAdd(&a.work[0], 1u);
@@ -181,34 +216,30 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
             q.db[j] = INF;
             q.fst[j] = 0;
         }
-        stamp = 0;
         __syncthreads();
         if (tid == 0) {
             const uint32_t ss = qb_insert(q.key, rs);
             q.df[ss] = 0;
             const uint32_t st = qb_insert(q.key, rt);
             q.db[st] = 0;
-            q.ss = ss;
-            q.st = st;
             q.ovf = 0;
-            q.mu = INF;
+            q.mu = ss == st ? 0u : INF;
             q.cnt = 0;
             q.front[0][0] = ss;
-            q.nf[0] = 1;
+            q.front[0][1] = st | 0x80000000u;
+            q.cnt3[0] = 2;
+            q.cnt3[1] = 0;
+            q.cnt3[2] = 0;
         }
-        bool ok = block_search(q, q.df, a.up_off, a.up_adj, a.n, a.n_up, a.err, stamp);
-        if (ok) {
-            __syncthreads();
-            if (tid == 0) {
-                q.front[0][0] = q.st;
-                q.nf[0] = 1;
-            }
-            ok = block_search(q, q.db, a.dn_off, a.dn_adj, a.n, a.n_dn, a.err, stamp);
-        }
+        const bool ok = block_search<PRUNE>(q, a);
         if (!ok) {
             if (tid == 0) a.ovf[atomicAdd(&a.work[2], 1u)] = i;
             continue;
         }
+        // q.mu only steered pruning; the answer is the least meeting sum.
+        __syncthreads();
+        if (tid == 0) q.mu = INF;
+        __syncthreads();
         uint32_t mu = INF, cnt = 0;
         for (uint32_t j = tid; j < (uint32_t)QB_T; j += blockDim.x) {
             const uint32_t f = q.df[j], g = q.db[j];
@@ -364,7 +395,7 @@ void query_init(ch_s *h) {
     // per slot: df, db, fst, two frontiers (n each) and the touched list
     // of both directions (2n)
     const uint64_t per_slot = (uint64_t)std::max<uint32_t>(n, 1) * 7 * 4;
-    h->q_slots = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(64, (1ull << 30) / per_slot));
+    h->q_slots = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(64, (256ull << 20) / per_slot));
     h->q_dense.alloc((size_t)h->q_slots * std::max<uint32_t>(n, 1) * 7);
     const size_t sn = (size_t)h->q_slots * std::max<uint32_t>(n, 1);
     // df, db: INF; fst: 0; the rest need no initial value
@@ -372,11 +403,13 @@ void query_init(ch_s *h) {
     CH_CUDA_TRY(cudaMemset(h->q_dense.ptr + 2 * sn, 0, sn * 4));
     if (g_qb_blocks_per_sm < 0) {
         const size_t smem = sizeof(QBSmem);
-        CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
+        CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int b = 0;
-        CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block, QB_THREADS,
-                                                                  smem));
+        CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true>,
+                                                                  QB_THREADS, smem));
         g_qb_blocks_per_sm = std::max(1, b);
     }
     CH_CUDA_TRY(cudaDeviceSynchronize());
@@ -417,7 +450,10 @@ void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
         a.err = h->qerr.ptr;
         CH_CUDA_TRY(cudaMemsetAsync(h->qwork.ptr, 0, 4 * sizeof(uint32_t), st));
         const int blocks = (int)std::min<uint64_t>(kc, (uint64_t)sms * g_qb_blocks_per_sm);
-        k_query_block<<<blocks, QB_THREADS, smem, st>>>(a);
+        // Pruned searches unless the caller asked for search-space sizes,
+        // which are defined by the exhaustive upward searches.
+        if (settled_out) k_query_block<false><<<blocks, QB_THREADS, smem, st>>>(a);
+        else k_query_block<true><<<blocks, QB_THREADS, smem, st>>>(a);
         CH_CHECK_LAUNCH();
         k_query_dense<<<h->q_slots, 256, 0, st>>>(a, dn);
         CH_CHECK_LAUNCH();

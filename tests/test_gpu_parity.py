@@ -235,3 +235,23 @@ def test_id_tie_break_on_long_chain():
     och = O.build_ch(g, 5, O.TIE_ID)
     gch = gpu_build(g, 5, 1)
     assert_same_hierarchy(gch, och)
+
+
+@pytest.mark.parametrize("which", ["geo", "grid", "digraph"])
+def test_pruned_queries_match_exhaustive_and_oracle(which):
+    # without search-space counts the query prunes relaxations that cannot
+    # beat the best meeting sum so far; the answers must not change
+    if which == "geo":
+        g = I.geometric_knn_graph(60_000, seed=31)
+    elif which == "grid":
+        g, _ = I.workload("grid64")
+    else:
+        g = I.random_digraph(1200, 7000, 1, 1000, seed=32, allow_loops=False)
+    gch = gpu_build(g, 5)
+    s, t = I.random_pairs(g.n, 20_000, seed=33)
+    pruned = gch.query(s, t)
+    full, settled = gch.query(s, t, want_settled=True)
+    assert np.array_equal(pruned, full)
+    och = O.build_ch(g, 5)
+    idx = np.arange(0, s.size, 7)
+    assert np.array_equal(pruned[idx], och.query(s[idx], t[idx]))
