@@ -99,6 +99,11 @@ struct WArgs {
     uint4 *rec;              // PRUNE: shortcut records (v1, v2, w, via)
     uint8_t *rec_flag;       // PRUNE: 1 = lowers an existing edge
     uint64_t rec_cap;
+    // Routing to the block tier without a warp attempt: every source when
+    // the phase has at most route_all sources (too few to fill the GPU one
+    // warp each, so per-source latency decides), and any source whose
+    // middles' out-degrees sum above route_deg (its ball would overflow).
+    uint32_t route_all, route_deg;
 };
 
 struct Dense {
@@ -327,6 +332,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
     Ctl *ctl = d.ctl;
     const uint32_t nS = *a.nS;
     const uint32_t r = a.round;
+    const bool route_all = nS <= a.route_all;
     unsigned long long c_src = 0, c_vert = 0, c_edge = 0, c_mid = 0, c_midedge = 0;
     unsigned long long c_cand = 0, c_kept = 0, c_merged = 0, c_ins = 0, c_new = 0;
 
@@ -338,6 +344,10 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         const uint32_t s = a.S[i];
         if (s >= d.n) {
             if (lane == 0) atomicOr(&ctl->err, ERR_BOUND);
+            continue;
+        }
+        if (route_all) {
+            if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
             continue;
         }
         const uint64_t sb = d.out_beg[s];
@@ -379,6 +389,10 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             }
         }
         bound = warp_max(bound);
+        if (warp_sum((uint32_t)l_midedge) > a.route_deg) {
+            if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
+            continue;
+        }
         if (bound == 0) {  // no candidate pair from this source
             c_src += (lane == 0);
             c_mid += l_mid;
@@ -1565,6 +1579,8 @@ void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_ma
     a.rec = rec.ptr;
     a.rec_flag = rec_flag.ptr;
     a.rec_cap = rec.count;
+    a.route_all = (uint32_t)blk_blocks * 2;
+    a.route_deg = 64;
     cudaEvent_t e0 = start();
     const int blocks = grid_for((uint64_t)nS_max, WIT_WARPS, sms * 8);
     k_witness<MODE><<<blocks, WIT_WARPS * 32, 0, st>>>(a);

@@ -66,4 +66,5 @@ void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
 // Prepare query scratch after a build.
 void query_init(ch_s *h);
 
+
 }  // namespace gbch

@@ -29,20 +29,30 @@ constexpr uint32_t QERR_BOUND = 2u;  // an index check failed; the access was sk
 constexpr int QB_THREADS = 256;        // threads per query block
 constexpr int QB_TBITS = 12;           // 4096 vertices per query table
 constexpr int QB_T = 1 << QB_TBITS;
-constexpr int QB_FC = 1280;            // frontier capacity
+constexpr int QB_FC = 2048;            // frontier capacity
 constexpr uint64_t Q_CHUNK = 1u << 22;  // queries per launch pair
 
-// Shared state of one query block: a hash table of reached vertices whose
-// entries carry both directions' labels, per-direction frontier stamps, a
-// double-buffered frontier holding both directions' entries (slot | dir<<31)
-// and a triple-buffered frontier counter, so that one barrier per level
-// suffices (see block_search).
+// Shared state of one query block (about 70 KB, three blocks per SM): a
+// hash table of reached vertices whose entries carry both directions'
+// labels, claim bitmaps that keep a slot from being queued twice in one
+// level and direction (one bitmap per level parity, the idle one cleared
+// during the level), a double-buffered frontier holding both directions'
+// entries (slot | dir<<31) and a triple-buffered frontier counter, so that
+// one barrier per level suffices (see block_search).
+constexpr int QB_CW = QB_T / 32;  // claim-bitmap words per direction
 struct QBSmem {
     uint32_t key[QB_T];
     uint32_t df[QB_T];
     uint32_t db[QB_T];
-    uint32_t fst[QB_T];  // last level that queued the slot: bits 0-15 forward, 16-31 backward
+    uint32_t claim[2][2][QB_CW];  // [level parity][direction][word]
     uint32_t front[2][QB_FC];
+    // one tile of frontier entries, flattened block-wide: exclusive prefix of
+    // their out-degrees, first edge index, label, slot | dir << 31
+    uint32_t t_excl[QB_THREADS];
+    uint32_t t_beg[QB_THREADS];
+    uint32_t t_dx[QB_THREADS];
+    uint32_t t_ent[QB_THREADS];
+    uint32_t wtot[QB_THREADS / 32 + 1];
     uint32_t cnt3[3];
     uint32_t item, ovf, mu, cnt, ss, st;
 };
@@ -79,18 +89,11 @@ __device__ __forceinline__ uint32_t qb_insert(uint32_t *keys, uint32_t v) {
     return EMPTY;
 }
 
-// Marks `slot` as queued for level `lvl` in direction `dir`; true if it was
-// not queued for that level and direction yet.
-__device__ __forceinline__ bool qb_claim(uint32_t *fst, uint32_t slot, uint32_t dir, uint32_t lvl) {
-    const uint32_t shift = dir ? 16u : 0u;
-    uint32_t old = fst[slot];
-    while (true) {
-        if (((old >> shift) & 0xFFFFu) == lvl) return false;
-        const uint32_t want = (old & ~(0xFFFFu << shift)) | (lvl << shift);
-        const uint32_t prev = atomicCAS(&fst[slot], old, want);
-        if (prev == old) return true;
-        old = prev;
-    }
+// Marks `slot` as queued in direction `dir` for the next level (bitmap of
+// the level's parity); true if it was not queued yet.
+__device__ __forceinline__ bool qb_claim(QBSmem &q, uint32_t slot, uint32_t dir, uint32_t lvl) {
+    const uint32_t bit = 1u << (slot & 31u);
+    return !(atomicOr(&q.claim[lvl & 1u][dir][slot >> 5], bit) & bit);
 }
 
 // Both upward searches at once, label-correcting over the rank DAG: the
@@ -120,13 +123,18 @@ __device__ bool block_search(QBSmem &q, const QArgs &a) {
             return false;
         }
         if (tid == 0) q.cnt3[(lvl + 1) % 3] = 0;
+        // the bitmap of the other parity was last used two levels ago and is
+        // next used one level from now
+        for (uint32_t j = tid; j < 2u * QB_CW; j += blockDim.x) (&q.claim[(lvl + 1) & 1u][0][0])[j] = 0;
         const uint32_t nxt_cnt = lvl % 3;
-        for (uint32_t f0 = warp * 32; f0 < nfront; f0 += nwarps * 32) {
-            const uint32_t fi = f0 + lane;
+        // Tiles of blockDim frontier entries; the out-edges of a tile are
+        // spread evenly over all threads of the block.
+        for (uint32_t t0 = 0; t0 < nfront; t0 += blockDim.x) {
+            const uint32_t fi = t0 + tid;
             const bool fv = fi < nfront && fi < (uint32_t)QB_FC;
             const uint32_t ent = fv ? q.front[cur][fi] : 0;
             const uint32_t dir = ent >> 31;
-            uint32_t slot = ent & 0x7FFFFFFFu;
+            const uint32_t slot = ent & 0x7FFFFFFFu;
             const bool sok = fv && slot < (uint32_t)QB_T;
             if (fv && !sok) atomicOr(a.err, QERR_BOUND);
             const uint32_t x = sok ? q.key[slot] : 0;
@@ -139,21 +147,34 @@ __device__ bool block_search(QBSmem &q, const QArgs &a) {
             uint32_t cnt = 0;
             if (xok && b <= e_end && e_end <= n_edges) cnt = e_end - b;
             else if (xok) atomicOr(a.err, QERR_BOUND);
-            if (!xok) slot = 0;
-            const uint32_t dx = xok ? (dir ? q.db[slot] : q.df[slot]) : INF;
+            const uint32_t dx = cnt ? (dir ? q.db[slot] : q.df[slot]) : INF;
+            // block-wide exclusive scan of cnt
             const uint32_t incl = warp_incl_scan(cnt);
-            const uint32_t total = __shfl_sync(FULL, incl, 31);
-            const uint32_t excl = incl - cnt;
-            for (uint32_t base = 0; base < total; base += 32) {
-                const uint32_t idx = base + lane;
-                const uint32_t o = warp_owner(excl, idx);
-                const uint32_t b_o = __shfl_sync(FULL, b, o);
-                const uint32_t ex_o = __shfl_sync(FULL, excl, o);
-                const uint32_t dx_o = __shfl_sync(FULL, dx, o);
-                const uint32_t dir_o = __shfl_sync(FULL, dir, o);
-                if (idx >= total) continue;
-                const uint2 e = (dir_o ? a.dn_adj : a.up_adj)[b_o + (idx - ex_o)];
-                const uint32_t nd = sat_add(dx_o, e.y);
+            if (lane == 31) q.wtot[warp] = incl;
+            q.t_beg[tid] = b;
+            q.t_dx[tid] = dx;
+            q.t_ent[tid] = ent;
+            __syncthreads();
+            uint32_t wbase = 0, total = 0;
+            for (uint32_t w2 = 0; w2 < nwarps; ++w2) {
+                const uint32_t wt = q.wtot[w2];
+                if (w2 < warp) wbase += wt;
+                total += wt;
+            }
+            q.t_excl[tid] = wbase + incl - cnt;
+            __syncthreads();
+            for (uint32_t e0 = tid; e0 < total; e0 += blockDim.x) {
+                // owner entry: the largest k with t_excl[k] <= e0
+                uint32_t lo = 0, hi = blockDim.x;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (q.t_excl[mid] <= e0) lo = mid;
+                    else hi = mid;
+                }
+                const uint32_t oent = q.t_ent[lo];
+                const uint32_t odir = oent >> 31;
+                const uint2 e = (odir ? a.dn_adj : a.up_adj)[q.t_beg[lo] + (e0 - q.t_excl[lo])];
+                const uint32_t nd = sat_add(q.t_dx[lo], e.y);
                 if (e.x >= a.n) {
                     atomicOr(a.err, QERR_BOUND);
                     continue;
@@ -165,19 +186,20 @@ __device__ bool block_search(QBSmem &q, const QArgs &a) {
                     q.ovf = 1;
                     continue;
                 }
-                uint32_t *dist = dir_o ? q.db : q.df;
+                uint32_t *dist = odir ? q.db : q.df;
                 const uint32_t old = atomicMin(&dist[ys], nd);
                 if (nd >= old) continue;
                 if (PRUNE) {
-                    const uint32_t other = dir_o ? q.df[ys] : q.db[ys];
+                    const uint32_t other = odir ? q.df[ys] : q.db[ys];
                     if (other != INF) atomicMin(&q.mu, sat_add(nd, other));
                 }
-                if (qb_claim(q.fst, ys, dir_o, lvl)) {
+                if (qb_claim(q, ys, odir, lvl)) {
                     const uint32_t p = atomicAdd(&q.cnt3[nxt_cnt], 1u);
-                    if (p < (uint32_t)QB_FC) q.front[cur ^ 1u][p] = ys | (dir_o << 31);
+                    if (p < (uint32_t)QB_FC) q.front[cur ^ 1u][p] = ys | (odir << 31);
                     else q.ovf = 1;
                 }
             }
+            __syncthreads();
         }
     }
 }
@@ -214,8 +236,8 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
             q.key[j] = EMPTY;
             q.df[j] = INF;
             q.db[j] = INF;
-            q.fst[j] = 0;
         }
+        for (uint32_t j = tid; j < 4u * QB_CW; j += blockDim.x) (&q.claim[0][0][0])[j] = 0;
         __syncthreads();
         if (tid == 0) {
             const uint32_t ss = qb_insert(q.key, rs);
@@ -395,7 +417,7 @@ void query_init(ch_s *h) {
     // per slot: df, db, fst, two frontiers (n each) and the touched list
     // of both directions (2n)
     const uint64_t per_slot = (uint64_t)std::max<uint32_t>(n, 1) * 7 * 4;
-    h->q_slots = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(64, (256ull << 20) / per_slot));
+    h->q_slots = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(64, (1024ull << 20) / per_slot));
     h->q_dense.alloc((size_t)h->q_slots * std::max<uint32_t>(n, 1) * 7);
     const size_t sn = (size_t)h->q_slots * std::max<uint32_t>(n, 1);
     // df, db: INF; fst: 0; the rest need no initial value
