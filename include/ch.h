@@ -148,6 +148,30 @@ int ch_query_batch(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t 
 int ch_query_batch_host(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t k,
                         uint32_t *dist_out, uint32_t *settled_out);
 
+/* Largest batch ch_query_batch_static accepts. */
+#define CH_STATIC_QUERY_MAX (1u << 18)
+
+/* The same batched s-t distances as ch_query_batch (device pointers, async on
+ * `stream`, no search-space sizes), for callers that must not allocate
+ * device memory: a serving thread that may not block on the device-wide
+ * synchronisation an allocation can imply, or a process whose device memory
+ * is entirely reserved by another allocator. The paper has no counterpart;
+ * this is plumbing of this library.
+ *
+ * The call allocates nothing: its per-call scratch (work counters and the
+ * list of queries that outgrow the shared-memory search) is a file-scope
+ * device array of about 1 MiB, which every GPU that loads the library holds
+ * until the process exits. The first call on a device resolves that array's
+ * device address (cudaGetSymbolAddress) with the device current, so make
+ * the first call on each device before any stream capture. All calls on a
+ * device share the array, which keeps the last call's contents (the call
+ * clears the counters it needs): calls whose work overlaps on the GPU race
+ * on it, so serialise them (one stream, or events), across handles too.
+ * Errors: CH_ERANGE when k > CH_STATIC_QUERY_MAX; ids >= n are reported by
+ * ch_query_status as for ch_query_batch. */
+int ch_query_batch_static(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                          uint32_t *dist_out, void *stream);
+
 /* Waits for `stream` and reports (then clears) a device-side error recorded
  * by earlier ch_query_batch calls on this handle. */
 int ch_query_status(ch_t *ch, void *stream);

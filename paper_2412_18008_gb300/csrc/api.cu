@@ -157,6 +157,26 @@ int ch_query_batch(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t 
     });
 }
 
+int ch_query_batch_static(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                          uint32_t *dist_out, void *stream) {
+    if (!ch) {
+        g_last_error = "null handle";
+        return CH_EINVAL;
+    }
+    if (k > CH_STATIC_QUERY_MAX) {
+        g_last_error = "batch larger than CH_STATIC_QUERY_MAX queries";
+        return CH_ERANGE;
+    }
+    if (k == 0) return CH_OK;
+    if (!src || !dst || !dist_out) {
+        g_last_error = "null query array";
+        return CH_EINVAL;
+    }
+    return guarded([&] {
+        query_batch_static(ch, src, dst, k, dist_out, (cudaStream_t)stream);
+    });
+}
+
 int ch_query_status(ch_t *ch, void *stream) {
     if (!ch) {
         g_last_error = "null handle";

@@ -66,5 +66,8 @@ void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
 // Prepare query scratch after a build.
 void query_init(ch_s *h);
 
+// Enqueue a query batch whose per-call scratch is a static device array.
+void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                        uint32_t *dist_out, cudaStream_t st);
 
 }  // namespace gbch

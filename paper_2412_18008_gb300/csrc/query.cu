@@ -16,6 +16,7 @@
 // per-vertex arrays in global memory (one block per array slot).
 
 #include <algorithm>
+#include <mutex>
 
 #include "handle.cuh"
 
@@ -480,6 +481,87 @@ void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
         k_query_dense<<<h->q_slots, 256, 0, st>>>(a, dn);
         CH_CHECK_LAUNCH();
     }
+}
+
+// ---------------------------------------------------------------------------
+// Query batches that allocate nothing (ch_query_batch_static)
+// ---------------------------------------------------------------------------
+//
+// Same kernels as query_batch; the only difference is where the per-call
+// scratch lives (the work counters and the list of queries handed to the
+// dense kernel). Here it is one file-scope device array, so a call needs no
+// allocation at all; every GPU that loads the library holds the array
+// (about 1 MiB) until the process exits. The array is shared by all calls
+// and all handles on a device: calls whose work overlaps on the GPU race on
+// it and must be serialised by the caller (one stream, or events).
+
+namespace {
+
+constexpr uint32_t kStaticScratchHead = 4;  // [0] block counter, [1] dense counter, [2] overflow count
+__device__ __align__(256) uint32_t g_static_query_scratch[kStaticScratchHead + CH_STATIC_QUERY_MAX];
+
+std::mutex g_static_mu;
+uint32_t *g_static_ptr[64] = {nullptr};
+
+// Device address of the scratch array for the current device. The first call
+// on a device resolves it (cudaGetSymbolAddress) with that device current;
+// later calls reuse it.
+uint32_t *static_scratch() {
+    int dev = 0;
+    CH_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) throw Error{CH_ERANGE, "device ordinal above 63"};
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        CH_CUDA_TRY(cudaGetSymbolAddress(&p, g_static_query_scratch));
+        g_static_ptr[dev] = static_cast<uint32_t *>(p);
+    }
+    return g_static_ptr[dev];
+}
+
+}  // namespace
+
+void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                        uint32_t *dist_out, cudaStream_t st) {
+    if (k > CH_STATIC_QUERY_MAX)
+        throw Error{CH_ERANGE, "batch larger than CH_STATIC_QUERY_MAX queries"};
+    if (k == 0) return;
+    uint32_t *scratch = static_scratch();
+    const size_t smem = sizeof(QBSmem);
+    const int sms = device_sm_count();
+    const size_t sn = (size_t)h->q_slots * std::max<uint32_t>(h->n, 1);
+    QDense dn;
+    dn.df = h->q_dense.ptr;
+    dn.db = dn.df + sn;
+    dn.fst = dn.df + 2 * sn;
+    dn.fa = dn.df + 3 * sn;
+    dn.fb = dn.df + 4 * sn;
+    dn.touched = dn.df + 5 * sn;
+    dn.nslots = h->q_slots;
+    QArgs a;
+    a.n = h->n;
+    a.n_up = (uint32_t)h->n_up;
+    a.n_dn = (uint32_t)h->n_down;
+    a.rank = h->rank.ptr;
+    a.up_off = h->up_off.ptr;
+    a.dn_off = h->dn_off.ptr;
+    a.up_adj = h->up_adj.ptr;
+    a.dn_adj = h->dn_adj.ptr;
+    a.src = src;
+    a.dst = dst;
+    a.out = dist_out;
+    a.settled = nullptr;
+    a.k = k;
+    a.work = scratch;
+    a.ovf = scratch + kStaticScratchHead;
+    a.err = h->qerr.ptr;
+    // the counters keep the previous call's values: clear them
+    CH_CUDA_TRY(cudaMemsetAsync(scratch, 0, kStaticScratchHead * sizeof(uint32_t), st));
+    const int blocks = (int)std::min<uint64_t>(k, (uint64_t)sms * g_qb_blocks_per_sm);
+    k_query_block<true><<<blocks, QB_THREADS, smem, st>>>(a);
+    CH_CHECK_LAUNCH();
+    k_query_dense<<<h->q_slots, 256, 0, st>>>(a, dn);
+    CH_CHECK_LAUNCH();
 }
 
 }  // namespace gbch
