@@ -59,6 +59,12 @@ def parse():
                     help="time the CH build alone (profiling the build kernels)")
     ap.add_argument("--queries", type=int, default=None,
                     help="query batch size (default: the workload's)")
+    ap.add_argument("--compare-learned", action="store_true",
+                    help="train the learned priority on traces of 20 seeded 256K-vertex graphs "
+                         "of the family and compare it with the edge difference on the held-out "
+                         "1M-vertex graph (seed 5)")
+    ap.add_argument("--train-graphs", type=int, default=20)
+    ap.add_argument("--train-epochs", type=int, default=4)
     return ap.parse_args()
 
 
@@ -168,10 +174,85 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def compare_learned(args):
+    """Learned priority vs edge difference (one JSON line)."""
+    import torch
+    from paper_2412_18008_gb300 import ch
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    rows, labels = [], []
+    for seed in range(100, 100 + args.train_graphs):
+        g = I.geometric_knn_graph(256_000, seed=seed)
+        tr = ch.CH.build(g, hop_limit=args.hop_limit, trace=True).export_trace()
+        rows.append(tr["rows"])
+        labels.append(ch.training_labels(tr["rows"]))
+    rows = np.concatenate(rows)
+    labels = np.concatenate(labels)
+    t_traces = time.perf_counter() - t0
+    drows = torch.from_numpy(rows).to(dev)
+    dlab = torch.from_numpy(labels).to(dev)
+    w = torch.from_numpy(ch.mlp_init(11)).to(dev)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss = ch.mlp_train(drows, dlab, w, epochs=args.train_epochs, batch=8192)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    weights = w.cpu().numpy()
+    g = I.geometric_knn_graph(1_000_000, seed=5)
+    s_h, t_h = I.random_pairs(g.n, 1_000_000, seed=6)
+    off = torch.from_numpy(g.offsets.view(np.int64)).to(dev)
+    tgt = torch.from_numpy(g.targets.view(np.int32)).to(dev)
+    wt = torch.from_numpy(g.weights.view(np.int32)).to(dev)
+    ds = torch.from_numpy(s_h.view(np.int32)).to(dev)
+    dt = torch.from_numpy(t_h.view(np.int32)).to(dev)
+    res = {}
+    answers = {}
+    for name, mw in (("edge_difference", None), ("learned", weights)):
+        times = []
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            h = ch.CH.build(n=g.n, offsets=off, targets=tgt, weights=wt, hop_limit=args.hop_limit,
+                            mlp_weights=mw)
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+            if k + 1 < args.warmup + args.steps:
+                h.close()
+        st = h.stats()
+        d, sett = h.query(ds[:100_000], dt[:100_000], want_settled=True)
+        full = h.query(ds, dt)
+        torch.cuda.synchronize()
+        answers[name] = full.cpu().numpy()
+        res[name] = {"build_s": statistics.mean(times) / 1000.0, "shortcuts": st["shortcuts"],
+                     "rounds": st["rounds"],
+                     "mean_search_space": float(sett.cpu().numpy().view(np.uint32).mean())}
+        h.close()
+    line = {
+        "metric": "learned vs edge-difference priority: CH build seconds, shortcut count, "
+                  "mean upward search-space size",
+        "config": {"workload": "geo1M-learned", "vertices": g.n, "test_seed": 5,
+                   "train_graphs": args.train_graphs, "train_vertices_each": 256_000,
+                   "train_rows": int(rows.shape[0]), "train_epochs": args.train_epochs},
+        "results": res,
+        "distances_identical_1M_queries": bool(np.array_equal(answers["edge_difference"],
+                                                              answers["learned"])),
+        "train_loss_per_epoch": [float(x) for x in loss],
+        "trace_seconds": t_traces, "train_seconds": t_train,
+        "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 MLP / u32 graph",
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.compare_learned:
+        compare_learned(args)
         return
     import torch
     import torch.distributed as dist

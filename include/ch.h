@@ -47,8 +47,19 @@ extern "C" {
 #define CH_TIE_HASHED 0u
 #define CH_TIE_ID 1u
 
-/* Vertex score: CH_PRIO_EDGE_DIFF is the edge difference of Alg. 4. */
+/* Vertex score: CH_PRIO_EDGE_DIFF is the edge difference of Alg. 4.
+ * CH_PRIO_LEARNED (no counterpart in the paper) replaces it by
+ * round(1024 * MLP(features)), an MLP 12 -> 64 -> 64 -> 1 over the integer
+ * features of the rescored vertex (see ch_export_trace), BF16 weights on the
+ * tensor cores with FP32 accumulation. The edge difference is still computed
+ * (it is a feature). Any priority yields a hierarchy with exact distances. */
 #define CH_PRIO_EDGE_DIFF 0u
+#define CH_PRIO_LEARNED 1u
+
+/* MLP parameters, FP32, in this order: W1[12][64] (input-major), b1[64],
+ * W2[64][64] (input-major), b2[64], W3[64], b3. */
+#define CH_MLP_NPARAM 5057u
+#define CH_NFEAT 12u
 
 /* Input graph, a directed out-CSR (Sec. 4.1: "our input graph is given in
  * the CSR format"). offsets[n+1] (offsets[0] = 0, non-decreasing,
@@ -76,7 +87,11 @@ typedef struct {
  *   tie_break  CH_TIE_HASHED (default) or CH_TIE_ID; tie_seed feeds the hash.
  *   max_candidates_per_vertex  must be UINT64_MAX (contract every vertex).
  *   stream     cudaStream_t the build runs on (NULL: the legacy stream).
- *              ch_build returns after the work on it has finished. */
+ *              ch_build returns after the work on it has finished.
+ *   mlp_weights  host pointer to CH_MLP_NPARAM floats (CH_PRIO_LEARNED only;
+ *              read during ch_build).
+ *   trace      nonzero: record one row per rescoring (its features) and the
+ *              priority each rescoring produced, for ch_export_trace. */
 typedef struct {
     uint32_t hop_limit;
     uint32_t priority;
@@ -84,7 +99,17 @@ typedef struct {
     uint32_t tie_seed;
     uint64_t max_candidates_per_vertex;
     void *stream;
+    const float *mlp_weights;
+    int32_t trace;
+    int32_t reserved;
 } ch_params_t;
+
+/* Training parameters of ch_mlp_train (Adam, mean squared error). */
+typedef struct {
+    uint32_t epochs;   /* passes over the samples; 0 = compute the gradient of the first batch only */
+    uint32_t batch;    /* samples per step */
+    float lr, beta1, beta2, eps;
+} ch_train_params_t;
 
 typedef struct ch_s ch_t;
 
@@ -112,6 +137,7 @@ typedef struct {
     uint64_t witness_launches;
     uint64_t witness_bytes;
     uint64_t witness_dense;     /* of which outgrew a block's tables too (global-memory path) */
+    uint64_t trace_rows;        /* rescorings recorded (params.trace or CH_PRIO_LEARNED) */
 } ch_stats_t;
 
 /* Number of per-round statistics fields written by ch_get_round_stats, in
@@ -201,6 +227,42 @@ int ch_get_round_times(const ch_t *ch, double *out, uint32_t max_rounds);
  *               ch_stats_t.down_edges rows */
 int ch_export(const ch_t *ch, uint32_t *level, int32_t *priority, uint32_t *rank,
               uint32_t *shortcuts, uint32_t *up, uint32_t *down);
+
+/* Learned-priority data of a build made with params.trace (or the learned
+ * priority), to HOST buffers; any pointer may be NULL.
+ *   rows     14 int64 per rescoring, in rescoring order within each round:
+ *            round, vertex, then its 12 features on the overlay of that
+ *            round: kept pairs S, |N_in|, |N_out|, distinct neighbours, edge
+ *            difference S - |N_in| - |N_out|, incident edges removed by
+ *            earlier contractions, hierarchy depth (1 + the largest depth
+ *            among contracted neighbours, 0 if none), round,
+ *            |N_in| * |N_out|, degree in the normalised input, times
+ *            rescored before, mean incident weight (integer division).
+ *            Rows of one round are sorted by vertex.
+ *   prio     per row, the int32 priority the rescoring produced.
+ *   labels   per vertex (n), the training label: its edge difference at its
+ *            last rescoring plus its depth, both at its contraction.
+ * ch_stats_t.trace_rows rows. */
+int ch_export_trace(const ch_t *ch, int64_t *rows, int32_t *prio, int32_t *labels);
+
+/* Trains the priority MLP on DEVICE data: rows (n x 14 int64 as exported by
+ * ch_export_trace), labels (n floats), weights_io (CH_MLP_NPARAM floats, the
+ * start point on entry, the trained weights on return). loss_out (host,
+ * `epochs` floats, or NULL) receives each epoch's mean squared error; with
+ * epochs = 0 nothing is trained and grad_out (device, CH_MLP_NPARAM floats,
+ * or NULL) receives the gradient of the mean squared error over the first
+ * `batch` rows. Forward passes round as the tensor-core inference does; the
+ * sums run in a fixed order, so training is deterministic. Synchronous on
+ * `stream`. */
+int ch_mlp_train(const int64_t *rows, const float *labels, uint64_t n,
+                 const ch_train_params_t *tp, float *weights_io, float *loss_out,
+                 float *grad_out, void *stream);
+
+/* MLP outputs for trace rows on the device (the inference the learned
+ * priority runs, before scaling by 1024): rows (n x 14 int64, device),
+ * weights (host, CH_MLP_NPARAM floats), y_out (device, n floats). */
+int ch_mlp_forward(const float *weights, const int64_t *rows, uint64_t n, float *y_out,
+                   void *stream);
 
 void ch_free(ch_t *ch);
 

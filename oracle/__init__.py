@@ -57,6 +57,15 @@ def _load():
         lib.orc_build.argtypes = [u32, u64, P, P, P, u32, u32, u32, C.POINTER(P)]
         lib.orc_build.restype = C.c_int
         lib.orc_free.argtypes = [P]
+        lib.orc_build2.argtypes = [u32, u64, P, P, P, u32, u32, u32, C.c_int, u64, P, P, P,
+                                   C.POINTER(P)]
+        lib.orc_build2.restype = C.c_int
+        lib.orc_num_trace.argtypes = [P]
+        lib.orc_num_trace.restype = u64
+        lib.orc_get_trace.argtypes = [P, P]
+        lib.orc_get_trace.restype = None
+        lib.orc_get_labels.argtypes = [P, P]
+        lib.orc_get_labels.restype = None
         for name in ("orc_rounds",):
             getattr(lib, name).argtypes = [P]
             getattr(lib, name).restype = u32
@@ -139,12 +148,27 @@ class OracleCH:
             pass
 
 
-def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int = 0) -> OracleCH:
-    """Run the oracle's round algorithm on graph ``g`` (see ``oracle.cpp``)."""
+def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int = 0,
+             trace: bool = False, replay=None) -> OracleCH:
+    """Run the oracle's round algorithm on graph ``g`` (see ``oracle.cpp``).
+
+    ``trace`` records the learned-priority features of every rescoring
+    (``OracleCH.trace``: rows of round, vertex, 12 features; ``labels``).
+    ``replay`` = (rounds, vertices, priorities) arrays replaces the edge
+    difference by the given int32 priorities of each (round, vertex).
+    """
     lib = _load()
     args, keep = _graph_args(g)
     h = C.c_void_p()
-    rc = lib.orc_build(*args, hop_limit, tie_break, tie_seed & 0xFFFFFFFF, C.byref(h))
+    if replay is None:
+        rr = ru = rpv = np.zeros(0, np.uint32)
+        rpv = np.zeros(0, np.int32)
+    else:
+        rr = np.ascontiguousarray(replay[0], np.uint32)
+        ru = np.ascontiguousarray(replay[1], np.uint32)
+        rpv = np.ascontiguousarray(replay[2], np.int32)
+    rc = lib.orc_build2(*args, hop_limit, tie_break, tie_seed & 0xFFFFFFFF, int(trace),
+                        rr.size, _p(rr), _p(ru), _p(rpv), C.byref(h))
     if rc != 0:
         raise ValueError(f"oracle rejected the graph or parameters (status {rc})")
     n = g.n
@@ -170,8 +194,18 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
     stats = np.empty((rounds, lib.orc_nstat()), np.uint64)
     if rounds:
         lib.orc_get_stats(h, _p(stats))
+    nt = lib.orc_num_trace(h)
+    tr = np.empty((nt, 14), np.int64)
+    if nt:
+        lib.orc_get_trace(h, _p(tr))
+    labels = np.empty(n, np.int32)
+    if n:
+        lib.orc_get_labels(h, _p(labels))
     del keep
-    return OracleCH(n, hop_limit, level, prio, rank, sc, up, down, stats, h)
+    och = OracleCH(n, hop_limit, level, prio, rank, sc, up, down, stats, h)
+    och.trace = tr
+    och.labels = labels
+    return och
 
 
 def round0_scores(g, hop_limit: int = 5) -> np.ndarray:

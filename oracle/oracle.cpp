@@ -73,6 +73,7 @@
 #include <functional>
 #include <map>
 #include <queue>
+#include <stdexcept>
 #include <tuple>
 #include <unordered_map>
 #include <utility>
@@ -237,6 +238,16 @@ struct CH {
     std::vector<std::vector<std::pair<uint32_t, uint32_t>>> up;    // E_up: u -> (x, w)
     std::vector<std::vector<std::pair<uint32_t, uint32_t>>> down;  // E_down into u: (x, w) for (x,u)
     std::vector<std::array<uint64_t, NSTAT>> stats;
+    // Per-vertex bookkeeping behind the features of the learned priority:
+    // edge difference at the last rescoring, incident edges removed by
+    // contractions so far, hierarchy depth (1 + the largest depth among
+    // contracted neighbours, 0 if none), times rescored, degree in the
+    // normalised input, and the training label (edge difference at
+    // contraction plus depth at contraction).
+    std::vector<int32_t> ed_last, depth, label;
+    std::vector<uint32_t> cn, rescore, orig_deg;
+    // One row per rescoring: round, vertex, then the 12 integer features.
+    std::vector<std::array<int64_t, 14>> trace;
 };
 
 }  // namespace
@@ -267,10 +278,51 @@ int32_t score_one(const Overlay& g, uint32_t u,
     return int32_t(p);
 }
 
+// The 12 integer features of u on the current overlay (learned priority; the
+// paper has no counterpart): kept pairs S, |N_in|, |N_out|, distinct
+// neighbours, edge difference, removed incident edges, depth, round,
+// |N_in|*|N_out|, input degree, times rescored before, mean incident weight
+// (integer division; 0 without edges).
+std::array<int64_t, 12> features(const Overlay& g, const CH& ch, uint32_t u, int32_t ed, uint32_t r) {
+    const int64_t in = g.in[u].size(), out = g.out[u].size();
+    int64_t common = 0;
+    uint64_t wsum = 0;
+    for (const auto& [x, wx] : g.in[u]) {
+        if (g.out[u].count(x)) ++common;
+        wsum += wx;
+    }
+    for (const auto& [x, wx] : g.out[u]) wsum += wx;
+    std::array<int64_t, 12> f{};
+    f[0] = int64_t(ed) + in + out;
+    f[1] = in;
+    f[2] = out;
+    f[3] = in + out - common;
+    f[4] = ed;
+    f[5] = ch.cn[u];
+    f[6] = ch.depth[u];
+    f[7] = r;
+    f[8] = in * out;
+    f[9] = ch.orig_deg[u];
+    f[10] = ch.rescore[u];
+    f[11] = (in + out) ? int64_t(wsum / uint64_t(in + out)) : 0;
+    return f;
+}
+
+// Priorities to use instead of the edge difference, keyed by (round, vertex).
+using Replay = std::map<std::pair<uint32_t, uint32_t>, int32_t>;
+
 void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
-           const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t seed) {
+           const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t seed,
+           bool want_trace = false, const Replay* replay = nullptr) {
     Overlay g;
     load(g, n, off, tgt, w);
+    ch.ed_last.assign(n, 0);
+    ch.depth.assign(n, 0);
+    ch.label.assign(n, 0);
+    ch.cn.assign(n, 0);
+    ch.rescore.assign(n, 0);
+    ch.orig_deg.assign(n, 0);
+    for (uint32_t u = 0; u < n; ++u) ch.orig_deg[u] = uint32_t(g.in[u].size() + g.out[u].size());
     ch.n = n;
     ch.H = H;
     ch.level.assign(n, INF);
@@ -296,8 +348,28 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
         for (uint32_t u : A) inA[u] = 1;
         st[ST_SCORE_SOURCES] = local_search(g, inA, A, H, hs, dist);
 
-        // Step 2: Score.
-        for (uint32_t u : A) ch.P[u] = score_one(g, u, dist);
+        // Step 2: Score (edge difference), or the replayed priority; the
+        // features are taken from the same overlay.
+        for (uint32_t u : A) {
+            const int32_t ed = score_one(g, u, dist);
+            if (want_trace) {
+                const auto f = features(g, ch, u, ed, r);
+                std::array<int64_t, 14> row{};
+                row[0] = r;
+                row[1] = u;
+                for (int k = 0; k < 12; ++k) row[2 + k] = f[k];
+                ch.trace.push_back(row);
+            }
+            ch.ed_last[u] = ed;
+            ++ch.rescore[u];
+            if (replay) {
+                auto it = replay->find({r, u});
+                if (it == replay->end()) throw std::runtime_error("replay has no priority");
+                ch.P[u] = it->second;
+            } else {
+                ch.P[u] = ed;
+            }
+        }
         for (uint32_t u : A) inA[u] = 0;
 
         // Step 3: Select (strict local minimum of the key over N(u)).
@@ -366,7 +438,19 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
             ++st[ST_INSERTED];
         }
 
-        // Remove V_F and its incident edges.
+        // Remove V_F and its incident edges; neighbours inherit depth and
+        // count the removed edges.
+        for (uint32_t u : F) {
+            ch.label[u] = ch.ed_last[u] + ch.depth[u];
+            for (const auto& [x, wx] : g.out[u]) {
+                ++ch.cn[x];
+                ch.depth[x] = std::max(ch.depth[x], ch.depth[u] + 1);
+            }
+            for (const auto& [x, wx] : g.in[u]) {
+                ++ch.cn[x];
+                ch.depth[x] = std::max(ch.depth[x], ch.depth[u] + 1);
+            }
+        }
         for (uint32_t u : F) {
             for (const auto& [x, wx] : g.out[u]) g.in[x].erase(u);
             for (const auto& [x, wx] : g.in[u]) g.out[x].erase(u);
@@ -482,6 +566,39 @@ int orc_build(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
     build(h->ch, n, off, tgt, w, H, tie_mode, tie_seed);
     *out = h;
     return ORC_OK;
+}
+
+// Build with the learned-priority bookkeeping: `want_trace` records the
+// features of every rescoring; a non-empty replay (round, vertex, priority)
+// list replaces the edge difference by the given priorities (it must cover
+// every rescoring the run makes, else ORC_EINVAL).
+int orc_build2(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
+               const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t tie_seed,
+               int want_trace, uint64_t nreplay, const uint32_t* rp_round, const uint32_t* rp_u,
+               const int32_t* rp_p, orc_ch** out) {
+    if (!out || !validate(n, m, off, tgt, w) || tie_mode > 1) return ORC_EINVAL;
+    Replay rp;
+    for (uint64_t i = 0; i < nreplay; ++i) rp[{rp_round[i], rp_u[i]}] = rp_p[i];
+    orc_ch* h = new orc_ch();
+    try {
+        build(h->ch, n, off, tgt, w, H, tie_mode, tie_seed, want_trace != 0,
+              nreplay ? &rp : nullptr);
+    } catch (const std::exception&) {
+        delete h;
+        return ORC_EINVAL;
+    }
+    *out = h;
+    return ORC_OK;
+}
+
+uint64_t orc_num_trace(const orc_ch* h) { return h->ch.trace.size(); }
+void orc_get_trace(const orc_ch* h, int64_t* out14) {
+    size_t i = 0;
+    for (const auto& row : h->ch.trace)
+        for (int k = 0; k < 14; ++k) out14[i++] = row[k];
+}
+void orc_get_labels(const orc_ch* h, int32_t* out) {
+    std::memcpy(out, h->ch.label.data(), sizeof(int32_t) * h->ch.n);
 }
 
 void orc_free(orc_ch* h) { delete h; }

@@ -24,6 +24,9 @@ CH_INF = 0xFFFFFFFF
 CH_TIE_HASHED = 0
 CH_TIE_ID = 1
 CH_PRIO_EDGE_DIFF = 0
+CH_PRIO_LEARNED = 1
+CH_MLP_NPARAM = 5057
+CH_NFEAT = 12
 CH_NSTAT = 10
 CH_NTIME = 6
 ROUND_TIME_FIELDS = ("score_ms", "select_ms", "prep_ms", "contract_ms", "update_ms", "witness_ms")
@@ -46,7 +49,13 @@ class GraphT(C.Structure):
 class ParamsT(C.Structure):
     _fields_ = [("hop_limit", C.c_uint32), ("priority", C.c_uint32), ("tie_break", C.c_uint32),
                 ("tie_seed", C.c_uint32), ("max_candidates_per_vertex", C.c_uint64),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("mlp_weights", C.c_void_p), ("trace", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class TrainT(C.Structure):
+    _fields_ = [("epochs", C.c_uint32), ("batch", C.c_uint32), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
 
 class StatsT(C.Structure):
@@ -58,7 +67,7 @@ class StatsT(C.Structure):
                 ("prep_ms", C.c_double), ("contract_ms", C.c_double), ("update_ms", C.c_double),
                 ("postprocess_ms", C.c_double), ("witness_ms", C.c_double),
                 ("witness_launches", C.c_uint64), ("witness_bytes", C.c_uint64),
-                ("witness_dense", C.c_uint64)]
+                ("witness_dense", C.c_uint64), ("trace_rows", C.c_uint64)]
 
 
 _lib = None
@@ -92,6 +101,11 @@ def load(build_if_missing: bool = True):
     lib.ch_export.argtypes = [P, P, P, P, P, P, P]
     for f in ("ch_build", "ch_query_batch", "ch_query_batch_host", "ch_query_status",
               "ch_get_stats", "ch_get_round_stats", "ch_get_round_times", "ch_export"):
+        getattr(lib, f).restype = C.c_int
+    lib.ch_export_trace.argtypes = [P, P, P, P]
+    lib.ch_mlp_train.argtypes = [P, P, C.c_uint64, C.POINTER(TrainT), P, P, P, P]
+    lib.ch_mlp_forward.argtypes = [P, P, C.c_uint64, P, P]
+    for f in ("ch_export_trace", "ch_mlp_train", "ch_mlp_forward"):
         getattr(lib, f).restype = C.c_int
     lib.ch_free.argtypes = [P]
     lib.ch_free.restype = None
@@ -144,7 +158,7 @@ class CH:
     @classmethod
     def build(cls, graph=None, *, n=None, offsets=None, targets=None, weights=None,
               hop_limit: int = 5, tie_break: int = CH_TIE_HASHED, tie_seed: int = 0,
-              stream=None) -> "CH":
+              stream=None, mlp_weights=None, trace: bool = False) -> "CH":
         """ch_build on a graph given as an ``inputs.Graph`` / NumPy CSR (host
         memory) or as CUDA tensors ``offsets`` (int64), ``targets`` and
         ``weights`` (int32 views of uint32 values) in device memory."""
@@ -179,6 +193,14 @@ class CH:
         p.tie_break = tie_break
         p.tie_seed = tie_seed & 0xFFFFFFFF
         p.stream = st
+        p.trace = int(bool(trace))
+        if mlp_weights is not None:
+            wts = np.ascontiguousarray(mlp_weights, dtype=np.float32)
+            if wts.size != CH_MLP_NPARAM:
+                raise ValueError(f"mlp_weights needs {CH_MLP_NPARAM} floats")
+            keep.append(wts)
+            p.priority = CH_PRIO_LEARNED
+            p.mlp_weights = wts.ctypes.data_as(C.c_void_p)
         h = C.c_void_p()
         _check(lib.ch_build(C.byref(g), C.byref(p), C.byref(h)))
         del keep
@@ -254,6 +276,17 @@ class CH:
                                 _hp(down)))
         return dict(level=level, priority=prio, rank=rank, shortcuts=sc, up=up, down=down)
 
+    def export_trace(self) -> dict:
+        """Rows (round, vertex, 12 features), the priority of each row, and
+        the per-vertex training labels (builds made with trace=True)."""
+        st = self.stats()
+        k = st["trace_rows"]
+        rows = np.empty((k, 14), np.int64)
+        prio = np.empty(k, np.int32)
+        labels = np.empty(st["n"], np.int32)
+        _check(load().ch_export_trace(self._h, _hp(rows), _hp(prio), _hp(labels)))
+        return dict(rows=rows, prio=prio, labels=labels)
+
     def close(self):
         if self._h:
             load().ch_free(self._h)
@@ -270,6 +303,56 @@ class CH:
             self.close()
         except Exception:
             pass
+
+
+def training_labels(rows) -> np.ndarray:
+    """Target of each trace row (float32): sign(x) * log2(1 + |x|) of the
+    score x = edge difference + 2 * hierarchy depth at that rescoring. The
+    network learns this score from the 12 (equally transformed) features;
+    the transform is monotone, so the learned priority orders vertices as
+    the score does. On road-like graphs the score yields shallower
+    hierarchies with smaller search spaces than the edge difference alone."""
+    rows = np.asarray(rows)
+    x = (rows[:, 2 + 4] + 2 * rows[:, 2 + 6]).astype(np.float64)
+    return (np.sign(x) * np.log2(1.0 + np.abs(x))).astype(np.float32)
+
+
+def mlp_init(seed: int = 0, scale: float = 0.3) -> np.ndarray:
+    """Initial MLP weights (float32, CH_MLP_NPARAM): normal weights scaled by
+    scale / sqrt(fan_in), zero biases."""
+    rng = np.random.default_rng(seed)
+    nin, nh = CH_NFEAT, 64
+    w1 = rng.normal(0, scale / np.sqrt(nin), (nin, nh))
+    w2 = rng.normal(0, scale / np.sqrt(nh), (nh, nh))
+    w3 = rng.normal(0, scale / np.sqrt(nh), nh)
+    return np.concatenate([w1.ravel(), np.zeros(nh), w2.ravel(), np.zeros(nh), w3,
+                           [0.0]]).astype(np.float32)
+
+
+def mlp_train(rows, labels, weights, epochs=3, batch=8192, lr=2e-3, beta1=0.9,
+              beta2=0.999, eps=1e-8, stream=None):
+    """ch_mlp_train on CUDA tensors: rows int64 [n, 14], labels float32 [n],
+    weights float32 [CH_MLP_NPARAM] (updated in place). With epochs=0
+    returns the gradient of the first batch instead of training."""
+    import torch
+    tp = TrainT(epochs, batch, lr, beta1, beta2, eps)
+    n = rows.shape[0]
+    loss = np.zeros(max(epochs, 1), np.float32)
+    grad = torch.zeros(CH_MLP_NPARAM, dtype=torch.float32, device=weights.device)
+    _check(load().ch_mlp_train(rows.data_ptr(), labels.data_ptr(), n, C.byref(tp),
+                               weights.data_ptr(), _hp(loss), grad.data_ptr(),
+                               _stream_ptr(stream)))
+    return (grad, loss) if epochs == 0 else loss
+
+
+def mlp_forward(weights, rows, stream=None):
+    """ch_mlp_forward: MLP outputs for trace rows (CUDA int64 tensor [n, 14])."""
+    import torch
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    y = torch.empty(rows.shape[0], dtype=torch.float32, device=rows.device)
+    _check(load().ch_mlp_forward(_hp(w), rows.data_ptr(), rows.shape[0], y.data_ptr(),
+                                 _stream_ptr(stream)))
+    return y
 
 
 def version() -> str:

@@ -7,6 +7,7 @@
 #include <tuple>
 
 #include "handle.cuh"
+#include "mlp.cuh"
 
 namespace gbch {
 
@@ -76,6 +77,9 @@ void ch_default_params(ch_params_t *p) {
     p->tie_seed = 0;
     p->max_candidates_per_vertex = UINT64_MAX;
     p->stream = nullptr;
+    p->mlp_weights = nullptr;
+    p->trace = 0;
+    p->reserved = 0;
 }
 
 int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out) {
@@ -86,8 +90,12 @@ int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out) {
     ch_params_t p;
     if (params) p = *params;
     else ch_default_params(&p);
-    if (p.priority != CH_PRIO_EDGE_DIFF) {
+    if (p.priority != CH_PRIO_EDGE_DIFF && p.priority != CH_PRIO_LEARNED) {
         g_last_error = "unsupported priority mode";
+        return CH_EINVAL;
+    }
+    if (p.priority == CH_PRIO_LEARNED && !p.mlp_weights) {
+        g_last_error = "CH_PRIO_LEARNED needs mlp_weights";
         return CH_EINVAL;
     }
     if (p.tie_break > CH_TIE_ID) {
@@ -131,6 +139,7 @@ int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out) {
         h->stats.witness_ms = h->t_witness_ms;
         h->stats.witness_launches = h->witness_launches;
         h->stats.witness_bytes = h->witness_bytes;
+        h->stats.trace_rows = h->trace_rows;
     });
     if (rc != CH_OK) {
         delete h;
@@ -324,6 +333,65 @@ int ch_export(const ch_t *ch, uint32_t *level, int32_t *priority, uint32_t *rank
                 o[2] = rows[i][2];
             }
         }
+    });
+}
+
+int ch_export_trace(const ch_t *ch, int64_t *rows, int32_t *prio, int32_t *labels) {
+    if (!ch) {
+        g_last_error = "null handle";
+        return CH_EINVAL;
+    }
+    return guarded([&] {
+        const uint64_t k = ch->trace_rows;
+        if (labels && ch->n) {
+            if (ch->labels.count < ch->n) throw Error{CH_EINVAL, "no labels recorded"};
+            CH_CUDA_TRY(cudaMemcpy(labels, ch->labels.ptr, ch->n * 4ull, cudaMemcpyDeviceToHost));
+        }
+        if (!k || (!rows && !prio)) return;
+        std::vector<long long> r(k * 14);
+        std::vector<int32_t> pr(k);
+        CH_CUDA_TRY(cudaMemcpy(r.data(), ch->trace.ptr, k * 14 * sizeof(long long), cudaMemcpyDeviceToHost));
+        CH_CUDA_TRY(cudaMemcpy(pr.data(), ch->trace_prio.ptr, k * 4, cudaMemcpyDeviceToHost));
+        std::vector<uint64_t> idx(k);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t b) {
+            return std::make_pair(r[a * 14], r[a * 14 + 1]) < std::make_pair(r[b * 14], r[b * 14 + 1]);
+        });
+        for (uint64_t i = 0; i < k; ++i) {
+            if (rows)
+                for (int c = 0; c < 14; ++c) rows[i * 14 + c] = r[idx[i] * 14 + c];
+            if (prio) prio[i] = pr[idx[i]];
+        }
+    });
+}
+
+int ch_mlp_train(const int64_t *rows, const float *labels, uint64_t n, const ch_train_params_t *tp,
+                 float *weights_io, float *loss_out, float *grad_out, void *stream) {
+    if (!rows || !labels || !tp || !weights_io || n == 0 || tp->batch == 0) {
+        g_last_error = "bad training arguments";
+        return CH_EINVAL;
+    }
+    return guarded([&] {
+        mlp_train(reinterpret_cast<const long long *>(rows), labels, n, tp, weights_io, loss_out,
+                  grad_out, (cudaStream_t)stream);
+    });
+}
+
+int ch_mlp_forward(const float *weights, const int64_t *rows, uint64_t n, float *y_out,
+                   void *stream) {
+    if (!weights || (n && (!rows || !y_out))) {
+        g_last_error = "bad inference arguments";
+        return CH_EINVAL;
+    }
+    return guarded([&] {
+        cudaStream_t st = (cudaStream_t)stream;
+        MlpDevice m;
+        m.load(weights, st);
+        DevBuf<float> x;
+        x.alloc(n * 16);
+        rows_to_features(reinterpret_cast<const long long *>(rows), n, x.ptr, st);
+        m.infer(x.ptr, n, y_out, st);
+        CH_CUDA_TRY(cudaStreamSynchronize(st));
     });
 }
 

@@ -41,6 +41,7 @@
 #include <cstring>
 
 #include "handle.cuh"
+#include "mlp.cuh"
 #include "prims.cuh"
 
 namespace gbch {
@@ -86,6 +87,9 @@ struct Dev {
     uint32_t *new_out, *new_in;
     Ctl *ctl;
     uint64_t out_arena, in_arena;  // arena capacities (entries), for index checks
+    // learned-priority bookkeeping (see k_features)
+    uint32_t *cn, *depth, *rescore, *orig_deg;
+    int32_t *ed_last, *label;
 };
 
 struct WArgs {
@@ -1074,6 +1078,92 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
 }
 
 // --------------------------------------------------------------------------
+// Learned priority: features of the rescored vertices
+// --------------------------------------------------------------------------
+
+// For u in A_r, right after its edge difference was computed (P[u]): its 12
+// integer features (see ch_export_trace) as a trace row (round, u, f[12])
+// and as transformed floats for the MLP; then ed_last[u] = P[u] and one more
+// rescoring is counted.
+__global__ void k_features(Dev d, const uint32_t *A, uint32_t nA, uint32_t r, long long *rows,
+                           float *x) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nA;
+         i += gridDim.x * blockDim.x) {
+        const uint32_t u = A[i];
+        if (!id_ok(d, u)) continue;
+        const uint64_t ob = d.out_beg[u], ib = d.in_beg[u];
+        const uint32_t od = out_list_ok(d, ob, d.out_deg[u]) ? d.out_deg[u] : 0;
+        const uint32_t id = in_list_ok(d, ib, d.in_deg[u]) ? d.in_deg[u] : 0;
+        long long common = 0;
+        unsigned long long wsum = 0;
+        for (uint32_t j = 0; j < id; ++j) {
+            const uint2 e = d.in_adj[ib + j];
+            wsum += e.y;
+            for (uint32_t k = 0; k < od; ++k)
+                if (d.out_adj[ob + k].x == e.x) {
+                    ++common;
+                    break;
+                }
+        }
+        for (uint32_t k = 0; k < od; ++k) wsum += d.out_adj[ob + k].y;
+        const int32_t ed = d.P[u];
+        long long f[MLP_NIN];
+        f[0] = (long long)ed + id + od;
+        f[1] = id;
+        f[2] = od;
+        f[3] = (long long)id + od - common;
+        f[4] = ed;
+        f[5] = d.cn[u];
+        f[6] = d.depth[u];
+        f[7] = r;
+        f[8] = (long long)id * od;
+        f[9] = d.orig_deg[u];
+        f[10] = d.rescore[u];
+        f[11] = (id + od) ? (long long)(wsum / (unsigned long long)(id + od)) : 0;
+        if (rows) {
+            long long *row = rows + (uint64_t)i * 14;
+            row[0] = r;
+            row[1] = u;
+            for (int k = 0; k < MLP_NIN; ++k) row[2 + k] = f[k];
+        }
+        if (x) {
+            float *xr = x + (uint64_t)i * 16;
+            for (int k = 0; k < 16; ++k) xr[k] = k < MLP_NIN ? feature_transform(f[k]) : 0.f;
+        }
+        d.ed_last[u] = ed;
+        d.rescore[u] += 1;
+    }
+}
+
+// P[u] = round(1024 * y) (ties to even), clamped to +-2^30; log the priority.
+__global__ void k_apply_learned(Dev d, const uint32_t *A, uint32_t nA, const float *y, int32_t *log) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nA;
+         i += gridDim.x * blockDim.x) {
+        const uint32_t u = A[i];
+        if (!id_ok(d, u)) continue;
+        float v = y[i] * 1024.f;
+        if (!(v == v)) v = 0.f;  // NaN
+        v = fminf(fmaxf(v, -1073741824.f), 1073741824.f);
+        const int32_t p = __float2int_rn(v);
+        d.P[u] = p;
+        if (log) log[i] = p;
+    }
+}
+
+__global__ void k_log_priority(const Dev d, const uint32_t *A, uint32_t nA, int32_t *log) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nA;
+         i += gridDim.x * blockDim.x) {
+        const uint32_t u = A[i];
+        log[i] = u < d.n ? d.P[u] : 0;
+    }
+}
+
+__global__ void k_orig_deg(Dev d) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < d.n; v += gridDim.x * blockDim.x)
+        d.orig_deg[v] = d.out_deg[v] + d.in_deg[v];
+}
+
+// --------------------------------------------------------------------------
 // Step 3: select strict local minima of the key
 // --------------------------------------------------------------------------
 
@@ -1173,6 +1263,17 @@ __global__ void k_emit_ch(Dev d, const uint32_t *F, uint32_t nF, uint2 *ch_up, u
         }
         for (uint32_t j = 0; j < od; ++j) ch_up[pu + j] = d.out_adj[ob + j];
         for (uint32_t j = 0; j < id; ++j) ch_dn[pd + j] = d.in_adj[ib + j];
+        // learned-priority bookkeeping: the label of u, and its neighbours
+        // inherit depth and count the removed edges (V_F is independent, so
+        // no neighbour is being contracted and depth[u] is stable here)
+        const uint32_t du = d.depth[u];
+        d.label[u] = d.ed_last[u] + (int32_t)du;
+        for (uint32_t j = 0; j < od + id; ++j) {
+            const uint32_t x = j < od ? d.out_adj[ob + j].x : d.in_adj[ib + (j - od)].x;
+            if (!id_ok(d, x)) continue;
+            atomicAdd(&d.cn[x], 1u);
+            atomicMax(&d.depth[x], du + 1);
+        }
         up_beg[u] = pu;
         up_deg[u] = od;
         dn_beg[u] = pd;
@@ -1424,6 +1525,15 @@ struct Builder {
     DevBuf<uint2> ch_up, ch_dn;
     DevBuf<uint64_t> ch_up_beg, ch_dn_beg;
     DevBuf<uint32_t> ch_up_deg, ch_dn_deg;
+    // learned priority
+    DevBuf<uint32_t> cn, depth, rescore, orig_deg;
+    DevBuf<int32_t> ed_last, label;
+    DevBuf<long long> trace;     // 14 int64 per rescoring
+    DevBuf<int32_t> trace_prio;  // priority per rescoring
+    uint64_t trace_count = 0;
+    bool tracing = false, learned = false;
+    MlpDevice mlp;
+    DevBuf<float> fx, fy;
     // dense fallback
     DevBuf<uint32_t> dn32;
     DevBuf<unsigned long long> dn64;
@@ -1617,6 +1727,27 @@ void Builder::run_rounds() {
             k_score_prep<<<grid_for(nA, 256, sms * 8), 256, 0, st>>>(d, A.ptr, nA, sstamp, S.ptr);
             CH_CHECK_LAUNCH();
             witness<MODE_SCORE>(S.ptr, &ctl.ptr->nS, nA * 4 + 32 > n ? n : nA * 4 + 32, r);
+            if (tracing || learned) {
+                if (tracing && trace.count < (trace_count + nA) * 14) {
+                    const uint64_t want = std::max<uint64_t>(trace_count + nA, trace.count / 14 * 2);
+                    trace.grow(want * 14, trace_count * 14, st);
+                    trace_prio.grow(want, trace_count, st);
+                }
+                long long *rows = tracing ? trace.ptr + trace_count * 14 : nullptr;
+                int32_t *plog = tracing ? trace_prio.ptr + trace_count : nullptr;
+                const int ga = grid_for(nA, 256, sms * 8);
+                k_features<<<ga, 256, 0, st>>>(d, A.ptr, nA, r, rows, learned ? fx.ptr : nullptr);
+                CH_CHECK_LAUNCH();
+                if (learned) {
+                    mlp.infer(fx.ptr, nA, fy.ptr, st);
+                    k_apply_learned<<<ga, 256, 0, st>>>(d, A.ptr, nA, fy.ptr, plog);
+                    CH_CHECK_LAUNCH();
+                } else if (plog) {
+                    k_log_priority<<<ga, 256, 0, st>>>(d, A.ptr, nA, plog);
+                    CH_CHECK_LAUNCH();
+                }
+                if (tracing) trace_count += nA;
+            }
         }
         mark(&h->t_score_ms, e0, 0);
         // 3: select
@@ -1881,6 +2012,29 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
         CH_CUDA_TRY(cudaMemsetAsync(b.dense.merge, 0xFF, sn * 8, b.st));
     }
 
+    b.cn.alloc(n);
+    b.cn.zero(b.st);
+    b.depth.alloc(n);
+    b.depth.zero(b.st);
+    b.rescore.alloc(n);
+    b.rescore.zero(b.st);
+    b.orig_deg.alloc(n);
+    b.ed_last.alloc(n);
+    b.ed_last.zero(b.st);
+    b.label.alloc(n);
+    b.label.zero(b.st);
+    b.tracing = p->trace != 0;
+    b.learned = p->priority == CH_PRIO_LEARNED;
+    if (b.learned) {
+        b.mlp.load(p->mlp_weights, b.st);
+        b.fx.alloc((size_t)n * 16);
+        b.fy.alloc(n);
+    }
+    if (b.tracing) {
+        b.trace.alloc((size_t)n * 14 * 2);
+        b.trace_prio.alloc((size_t)n * 2);
+    }
+
     Dev &d = b.d;
     d.n = n;
     d.H = p->hop_limit;
@@ -1903,6 +2057,14 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     d.new_out = b.new_out.ptr;
     d.new_in = b.new_in.ptr;
     d.ctl = b.ctl.ptr;
+    d.cn = b.cn.ptr;
+    d.depth = b.depth.ptr;
+    d.rescore = b.rescore.ptr;
+    d.orig_deg = b.orig_deg.ptr;
+    d.ed_last = b.ed_last.ptr;
+    d.label = b.label.ptr;
+    k_orig_deg<<<grid_for(n, 256, b.sms * 8), 256, 0, b.st>>>(d);
+    CH_CHECK_LAUNCH();
 
     b.run_rounds();
     b.cur_round = -1;
@@ -1932,6 +2094,10 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
 
     h->level = std::move(b.level);
     h->prio = std::move(b.P);
+    h->labels = std::move(b.label);
+    h->trace = std::move(b.trace);
+    h->trace_prio = std::move(b.trace_prio);
+    h->trace_rows = b.trace_count;
     h->sc = std::move(b.log);
     h->sc_round = std::move(b.log_round);
 }

@@ -33,6 +33,12 @@ struct ch_s {
     uint64_t n_shortcuts = 0;
     uint64_t n_up = 0, n_down = 0;
 
+    // learned-priority trace (params.trace): rows, priorities, labels
+    gbch::DevBuf<long long> trace;
+    gbch::DevBuf<int32_t> trace_prio;
+    gbch::DevBuf<int32_t> labels;
+    uint64_t trace_rows = 0;
+
     std::vector<std::array<uint64_t, CH_NSTAT>> round_stats;
     std::vector<std::array<double, CH_NTIME>> round_times;
     ch_stats_t stats{};
