@@ -63,6 +63,12 @@ def parse():
                     help="train the learned priority on traces of 20 seeded 256K-vertex graphs "
                          "of the family and compare it with the edge difference on the held-out "
                          "1M-vertex graph (seed 5)")
+    ap.add_argument("--serve", action="store_true",
+                    help="continuous-batching server: max throughput, then Poisson arrivals at "
+                         "50/80/95%% of it (p50/p99 latency), against one batch call per request")
+    ap.add_argument("--serve-workload", default="geo1M",
+                    help="geo1M or geo16M (16M-vertex graph of the same family, seed 6)")
+    ap.add_argument("--serve-requests", type=int, default=40_000)
     ap.add_argument("--train-graphs", type=int, default=20)
     ap.add_argument("--train-epochs", type=int, default=4)
     return ap.parse_args()
@@ -246,10 +252,84 @@ def compare_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_bench(args):
+    """Serving: one JSON line with throughput and latency percentiles."""
+    import torch
+    from paper_2412_18008_gb300 import ch
+    dev = torch.device("cuda", 0)
+    if args.serve_workload == "geo16M":
+        n, gseed = 16_000_000, 6
+    else:
+        n, gseed = 1_000_000, 3
+    g = I.geometric_knn_graph(n, seed=gseed)
+    h = ch.CH.build(g, hop_limit=args.hop_limit)
+    st = h.stats()
+    nreq = args.serve_requests
+    src, ks, tg = ch.request_mix(n, nreq, seed=7)
+    expected = h.query(np.repeat(src, ks), tg)
+
+    def pct(lat_ns):
+        return {"p50_us": float(np.percentile(lat_ns, 50)) / 1e3,
+                "p99_us": float(np.percentile(lat_ns, 99)) / 1e3}
+
+    out = {}
+    with ch.Server(h, blocks=0, ring=1 << 14, pool=1 << 24, idle_ms=20_000) as sv:
+        # saturated: everything due at once
+        t0 = time.perf_counter()
+        ans, lat, svc = sv.replay(src, ks, tg, np.zeros(nreq, np.uint64))
+        makespan = float(lat.max()) * 1e-9
+        assert np.array_equal(ans, expected), "served answers differ from batch answers"
+        max_rps = nreq / makespan
+        out["saturated"] = {"requests_per_s": max_rps, "queries_per_s": float(ks.sum()) / makespan,
+                            **pct(lat), "service": pct(svc)}
+        for frac in (0.5, 0.8, 0.95):
+            arr = ch.poisson_arrivals(nreq, max_rps * frac, seed=int(100 * frac))
+            ans, lat, svc = sv.replay(src, ks, tg, arr)
+            assert np.array_equal(ans, expected)
+            span = (float(arr[-1]) + float(lat[-1])) * 1e-9
+            out[f"poisson_{int(frac * 100)}pct"] = {
+                "offered_requests_per_s": max_rps * frac, "achieved_requests_per_s": nreq / span,
+                **pct(lat), "service": pct(svc)}
+    # unbatched baseline: one synchronous batch call per request
+    m = min(nreq, 2000)
+    ds = torch.from_numpy(np.repeat(src[:m], ks[:m]).view(np.int32)).to(dev)
+    dt = torch.from_numpy(tg[:int(ks[:m].sum())].view(np.int32)).to(dev)
+    dout = torch.empty_like(dt)
+    offs = np.concatenate([[0], np.cumsum(ks[:m].astype(np.int64))]).astype(np.int64)
+    stream = torch.cuda.Stream()
+    lat_u = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(m):
+        a, b = int(offs[i]), int(offs[i + 1])
+        t1 = time.perf_counter()
+        h.query_batch_raw(ds[a:].data_ptr(), dt[a:].data_ptr(), b - a, dout[a:].data_ptr(), None,
+                          stream.cuda_stream)
+        stream.synchronize()
+        lat_u.append((time.perf_counter() - t1) * 1e9)
+    span_u = time.perf_counter() - t0
+    assert np.array_equal(dout.cpu().numpy().view(np.uint32), expected[:int(ks[:m].sum())])
+    out["unbatched_one_call_per_request"] = {"requests_per_s": m / span_u,
+                                             **pct(np.array(lat_u))}
+    line = {
+        "metric": "served queries: requests/s and p50/p99 latency, continuous batching vs one "
+                  "batch call per request",
+        "config": {"workload": f"{args.serve_workload}-serve", "vertices": n, "edges": int(g.m),
+                   "requests": nreq, "mean_targets_per_request": float(ks.mean()),
+                   "one_to_many_fraction": 0.2, "targets_max": 1024,
+                   "server_blocks": 2 * 152, "build_s": st["build_ms"] / 1e3},
+        "results": out, "dtype": "u32", "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.serve:
+        serve_bench(args)
         return
     if args.compare_learned:
         compare_learned(args)

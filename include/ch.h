@@ -38,6 +38,7 @@ extern "C" {
 #define CH_ECUDA (-3)     /* a CUDA call failed (message in ch_last_error) */
 #define CH_ETIMEOUT (-4)  /* a bounded device-side wait expired */
 #define CH_ERANGE (-5)    /* a size limit of this library was exceeded */
+#define CH_EAGAIN (-6)    /* no room right now (query server): retry after polling */
 
 #define CH_INF 0xFFFFFFFFu
 
@@ -263,6 +264,58 @@ int ch_mlp_train(const int64_t *rows, const float *labels, uint64_t n,
  * weights (host, CH_MLP_NPARAM floats), y_out (device, n floats). */
 int ch_mlp_forward(const float *weights, const int64_t *rows, uint64_t n, float *y_out,
                    void *stream);
+
+/* ---- Query server: continuous batching (no counterpart in the paper) ----
+ *
+ * A persistent kernel on its own stream keeps `blocks` slots busy with
+ * requests published by the host: a source and 1..k targets (k = 1 is an
+ * s-t query, k > 1 one-to-many). A free slot takes the next published
+ * request at once, so requests that arrive while others are on the device
+ * are admitted as slots free up and overlap with them. Admission is by
+ * memory: targets and answers live in a pool of `pool` entries and the ring
+ * holds `ring` requests; ch_server_submit returns CH_EAGAIN when either is
+ * full (poll completed requests, then retry). Each answer equals what
+ * ch_query_batch returns for the same pair. The kernel's idle wait is
+ * bounded by idle_ms: after that long without a request it ends, and later
+ * submits return CH_ETIMEOUT. The handle `ch` must outlive the server. */
+typedef struct {
+    uint32_t blocks;   /* slots; 0 = two per SM */
+    uint32_t ring;     /* requests in flight at most */
+    uint64_t pool;     /* target/answer entries at most */
+    uint32_t idle_ms;  /* idle limit of the device loop */
+    uint32_t reserved;
+} ch_server_params_t;
+
+typedef struct ch_server_s ch_server_t;
+
+int ch_server_start(ch_t *ch, const ch_server_params_t *params, ch_server_t **out);
+
+/* Copies the k targets (host memory) and publishes the request; *ticket
+ * identifies it for ch_server_poll. */
+int ch_server_submit(ch_server_t *sv, uint32_t s, const uint32_t *targets, uint32_t k,
+                     uint64_t *ticket);
+
+/* *done = 1 and the k answers in dist_out (host) once the request has been
+ * served, else *done = 0. device_ns (or NULL) receives its service time on
+ * the device. A served ticket is retired by this call. */
+int ch_server_poll(ch_server_t *sv, uint64_t ticket, uint32_t *dist_out, int32_t *done,
+                   uint64_t *device_ns);
+
+/* Replays a request schedule (host arrays): request i = (src[i], its k[i]
+ * targets at targets[toff[i]..]), due at arrival_ns[i] after the call
+ * starts. Answers go to answers[toff[i]..]; latency_ns[i] = time from the
+ * scheduled arrival to the moment its answers were seen on the host;
+ * service_ns[i] (or NULL) = time on the device. Fails with CH_ETIMEOUT
+ * after limit_s seconds. */
+int ch_server_replay(ch_server_t *sv, uint64_t nreq, const uint32_t *src, const uint32_t *k,
+                     const uint64_t *toff, const uint32_t *targets, const uint64_t *arrival_ns,
+                     uint32_t *answers, uint64_t *latency_ns, uint64_t *service_ns,
+                     double limit_s);
+
+/* Stops the device loop once every published request is served (a bounded
+ * wait) and frees the server. Returns CH_ECUDA if an index or capacity
+ * check failed in the device loop during the server's life. */
+int ch_server_stop(ch_server_t *sv);
 
 void ch_free(ch_t *ch);
 

@@ -20,6 +20,7 @@ CH_ENOMEM = -2
 CH_ECUDA = -3
 CH_ETIMEOUT = -4
 CH_ERANGE = -5
+CH_EAGAIN = -6
 CH_INF = 0xFFFFFFFF
 CH_TIE_HASHED = 0
 CH_TIE_ID = 1
@@ -51,6 +52,11 @@ class ParamsT(C.Structure):
                 ("tie_seed", C.c_uint32), ("max_candidates_per_vertex", C.c_uint64),
                 ("stream", C.c_void_p), ("mlp_weights", C.c_void_p), ("trace", C.c_int32),
                 ("reserved", C.c_int32)]
+
+
+class ServerParamsT(C.Structure):
+    _fields_ = [("blocks", C.c_uint32), ("ring", C.c_uint32), ("pool", C.c_uint64),
+                ("idle_ms", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class TrainT(C.Structure):
@@ -106,6 +112,14 @@ def load(build_if_missing: bool = True):
     lib.ch_mlp_train.argtypes = [P, P, C.c_uint64, C.POINTER(TrainT), P, P, P, P]
     lib.ch_mlp_forward.argtypes = [P, P, C.c_uint64, P, P]
     for f in ("ch_export_trace", "ch_mlp_train", "ch_mlp_forward"):
+        getattr(lib, f).restype = C.c_int
+    lib.ch_server_start.argtypes = [P, C.POINTER(ServerParamsT), C.POINTER(P)]
+    lib.ch_server_submit.argtypes = [P, C.c_uint32, P, C.c_uint32, C.POINTER(C.c_uint64)]
+    lib.ch_server_poll.argtypes = [P, C.c_uint64, P, C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
+    lib.ch_server_replay.argtypes = [P, C.c_uint64, P, P, P, P, P, P, P, P, C.c_double]
+    lib.ch_server_stop.argtypes = [P]
+    for f in ("ch_server_start", "ch_server_submit", "ch_server_poll", "ch_server_replay",
+              "ch_server_stop"):
         getattr(lib, f).restype = C.c_int
     lib.ch_free.argtypes = [P]
     lib.ch_free.restype = None
@@ -303,6 +317,89 @@ class CH:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Query server (continuous batching) over a built hierarchy."""
+
+    def __init__(self, ch: CH, blocks: int = 0, ring: int = 1 << 14, pool: int = 1 << 22,
+                 idle_ms: int = 5000):
+        self._ch = ch
+        p = ServerParamsT(blocks, ring, pool, idle_ms, 0)
+        self._h = C.c_void_p()
+        _check(load().ch_server_start(ch._h, C.byref(p), C.byref(self._h)))
+
+    def submit(self, s: int, targets) -> int | None:
+        """Ticket of the published request, or None when the server is full."""
+        t = _host(targets, np.uint32)
+        tk = C.c_uint64()
+        rc = load().ch_server_submit(self._h, int(s), _hp(t), t.size, C.byref(tk))
+        if rc == CH_EAGAIN:
+            return None
+        _check(rc)
+        return tk.value
+
+    def poll(self, ticket: int, k: int):
+        """Answers (uint32[k]) once served, else None."""
+        out = np.empty(k, np.uint32)
+        done = C.c_int32()
+        _check(load().ch_server_poll(self._h, ticket, _hp(out), C.byref(done), None))
+        return out if done.value else None
+
+    def replay(self, src, ks, targets, arrival_ns, limit_s: float = 300.0):
+        """Serve a schedule: request i = (src[i], targets[toff[i]:toff[i]+ks[i]])
+        due at arrival_ns[i]. Returns (answers per target, latency_ns,
+        service_ns) arrays."""
+        src = _host(src, np.uint32)
+        ks = _host(ks, np.uint32)
+        toff = np.zeros(ks.size, np.uint64)
+        if ks.size:
+            toff[1:] = np.cumsum(ks[:-1], dtype=np.uint64)
+        tg = _host(targets, np.uint32)
+        arr = _host(arrival_ns, np.uint64)
+        ans = np.empty(tg.size, np.uint32)
+        lat = np.empty(ks.size, np.uint64)
+        svc = np.empty(ks.size, np.uint64)
+        _check(load().ch_server_replay(self._h, ks.size, _hp(src), _hp(ks), _hp(toff), _hp(tg),
+                                       _hp(arr), _hp(ans), _hp(lat), _hp(svc), limit_s))
+        return ans, lat, svc
+
+    def stop(self):
+        if self._h:
+            h, self._h = self._h, None
+            _check(load().ch_server_stop(h))
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.stop()
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
+
+
+def request_mix(n: int, count: int, seed: int, one_to_many: float = 0.2, kmax: int = 1024):
+    """Seeded request mix: sources uniform in [0, n); with probability
+    1 - one_to_many a single target, else k = floor(2**U[0, log2 kmax])
+    targets (log-uniform 1..kmax), all uniform. Returns (src, ks, targets)."""
+    rng = np.random.default_rng(seed)
+    src = rng.integers(0, n, size=count, dtype=np.int64).astype(np.uint32)
+    many = rng.random(count) < one_to_many
+    ks = np.where(many, np.floor(2.0 ** (rng.random(count) * np.log2(kmax))), 1).astype(np.uint32)
+    ks = np.maximum(ks, 1)
+    targets = rng.integers(0, n, size=int(ks.sum()), dtype=np.int64).astype(np.uint32)
+    return src, ks, targets
+
+
+def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
+    """Arrival times (ns) of a Poisson process of the given rate."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1e9 / rate_per_s, size=count)
+    return np.cumsum(gaps).astype(np.uint64)
 
 
 def training_labels(rows) -> np.ndarray:

@@ -395,6 +395,80 @@ int ch_mlp_forward(const float *weights, const int64_t *rows, uint64_t n, float 
     });
 }
 
+int ch_server_start(ch_t *ch, const ch_server_params_t *params, ch_server_t **out) {
+    if (!ch || !params || !out || params->ring == 0 || params->pool == 0) {
+        g_last_error = "bad server arguments";
+        return CH_EINVAL;
+    }
+    ch_server_s *sv = server_new();
+    if (!sv) {
+        g_last_error = "host allocation failed";
+        return CH_ENOMEM;
+    }
+    const int rc = guarded([&] { server_start(sv, ch, params); });
+    if (rc != CH_OK) {
+        guarded([&] { server_free(sv); });
+        server_delete(sv);
+        return rc;
+    }
+    *out = sv;
+    return CH_OK;
+}
+
+int ch_server_submit(ch_server_t *sv, uint32_t s, const uint32_t *targets, uint32_t k,
+                     uint64_t *ticket) {
+    if (!sv || !targets || !ticket || k == 0) {
+        g_last_error = "bad submit arguments";
+        return CH_EINVAL;
+    }
+    int rc = CH_OK;
+    const int g = guarded([&] { rc = server_submit(sv, s, targets, k, ticket); });
+    if (g != CH_OK) return g;
+    if (rc == CH_EAGAIN) g_last_error = "server full";
+    if (rc == CH_ETIMEOUT) g_last_error = "server kernel has ended (idle limit)";
+    return rc;
+}
+
+int ch_server_poll(ch_server_t *sv, uint64_t ticket, uint32_t *dist_out, int32_t *done,
+                   uint64_t *device_ns) {
+    if (!sv || !done) {
+        g_last_error = "bad poll arguments";
+        return CH_EINVAL;
+    }
+    return guarded([&] { *done = server_poll(sv, ticket, dist_out, device_ns) ? 1 : 0; });
+}
+
+int ch_server_replay(ch_server_t *sv, uint64_t nreq, const uint32_t *src, const uint32_t *k,
+                     const uint64_t *toff, const uint32_t *targets, const uint64_t *arrival_ns,
+                     uint32_t *answers, uint64_t *latency_ns, uint64_t *service_ns,
+                     double limit_s) {
+    if (!sv || (nreq && (!src || !k || !toff || !targets || !arrival_ns || !answers || !latency_ns))) {
+        g_last_error = "bad replay arguments";
+        return CH_EINVAL;
+    }
+    return guarded([&] {
+        server_replay(sv, nreq, src, k, toff, targets, arrival_ns, answers, latency_ns, service_ns,
+                      limit_s);
+    });
+}
+
+int ch_server_stop(ch_server_t *sv) {
+    if (!sv) return CH_OK;
+    uint32_t status = 0;
+    int rc = guarded([&] {
+        const int r = server_stop(sv, &status);
+        if (r != CH_OK) throw Error{r, "server kernel did not finish within its bounded wait"};
+    });
+    guarded([&] { server_free(sv); });
+    server_delete(sv);
+    if (rc != CH_OK) return rc;
+    if (status & 2u) {
+        g_last_error = "index or capacity check failed in the server loop";
+        return CH_ECUDA;
+    }
+    return CH_OK;
+}
+
 void ch_free(ch_t *ch) { delete ch; }
 
 }  // extern "C"

@@ -7,6 +7,8 @@
 
 #include "common.cuh"
 
+struct ch_server_s;
+
 struct ch_s {
     uint32_t n = 0;
     uint64_t m_input = 0;
@@ -75,5 +77,17 @@ void query_init(ch_s *h);
 // Enqueue a query batch whose per-call scratch is a static device array.
 void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
                         uint32_t *dist_out, cudaStream_t st);
+
+// Query server (serve.cu).
+ch_server_s *server_new();
+void server_delete(ch_server_s *sv);
+void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p);
+int server_submit(ch_server_s *sv, uint32_t s, const uint32_t *targets, uint32_t k, uint64_t *ticket);
+bool server_poll(ch_server_s *sv, uint64_t ticket, uint32_t *out, uint64_t *dev_ns);
+int server_stop(ch_server_s *sv, uint32_t *status);
+void server_free(ch_server_s *sv);
+void server_replay(ch_server_s *sv, uint64_t nreq, const uint32_t *src, const uint32_t *k,
+                   const uint64_t *toff, const uint32_t *targets, const uint64_t *arrival_ns,
+                   uint32_t *answers, uint64_t *latency_ns, uint64_t *service_ns, double limit_s);
 
 }  // namespace gbch

@@ -1,0 +1,540 @@
+// Device-resident query server with continuous batching (no counterpart in
+// the paper, which runs queries one after another).
+//
+// A persistent kernel keeps one block per slot busy. The host publishes
+// requests into a ring in mapped pinned memory (a source and 1..k targets;
+// k = 1 is an s-t query, k > 1 one-to-many); any block that is free claims
+// the next published request, so requests that arrive while others are
+// being served are picked up as soon as a slot frees, and their work
+// overlaps with the work already on the device. Admission is by memory:
+// targets and answers live in a fixed pool, and a request is only published
+// when the ring and the pool have room for it (ch_server_submit returns
+// CH_EAGAIN otherwise).
+//
+// Each query is the same bidirectional upward search as ch_query_batch
+// (label-correcting over the rank DAG, pruned by the best meeting sum), with
+// its labels in a per-block hash table in global memory large enough for any
+// search space of the hierarchy, so a request never needs a second kernel.
+//
+// Waits are bounded: a block that finds no work sleeps in short steps and
+// gives up after the idle limit (device globaltimer), recording a timeout;
+// the host's stop call waits a bounded time for the kernel.
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <thread>
+
+#include "handle.cuh"
+
+namespace gbch {
+namespace {
+
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+constexpr int SV_THREADS = 256;
+
+struct SvDesc {  // one request, written by the host before publication
+    uint32_t s, k;
+    uint64_t off;  // first target / answer in the pool
+};
+
+struct SvCtl {  // mapped host memory, written by the host only
+    volatile uint64_t published;  // requests [0, published) are readable
+    volatile uint32_t stop;
+    uint32_t pad;
+};
+
+struct SvArgs {
+    uint32_t n, n_up, n_dn;
+    const uint32_t *rank, *up_off, *dn_off;
+    const uint2 *up_adj, *dn_adj;
+    SvCtl *ctl;                  // mapped
+    const SvDesc *desc;          // mapped ring
+    const uint32_t *targets;     // mapped pool
+    uint32_t *answers;           // mapped pool
+    uint32_t *done;              // mapped ring: sequence + 1 when served
+    unsigned long long *t_begin, *t_end;  // mapped ring: device time (ns)
+    uint32_t ring;
+    unsigned long long *claimed;  // device counter
+    unsigned *status;             // device: 1 = idle limit reached, 2 = index or capacity check failed
+    unsigned long long idle_ns;
+    // per-block scratch (global memory)
+    uint32_t tbits;               // table of 2^tbits slots
+    uint32_t fcap;                // frontier capacity
+    uint32_t *key, *df, *db, *fst, *front, *touched;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+struct Tab {
+    uint32_t *key, *df, *db, *fst, *front, *touched;
+    uint32_t mask, fcap;
+};
+
+__device__ __forceinline__ uint32_t sv_insert(const Tab &t, uint32_t v, uint32_t bits, uint32_t *ntouch) {
+    uint32_t h = (v * 2654435761u) >> (32 - bits);
+    for (uint32_t probe = 0; probe <= t.mask; ++probe) {
+        const uint32_t k = t.key[h];
+        if (k == v) return h;
+        if (k == EMPTY) {
+            const uint32_t old = atomicCAS(&t.key[h], EMPTY, v);
+            if (old == EMPTY) {
+                t.touched[atomicAdd(ntouch, 1u)] = h;
+                return h;
+            }
+            if (old == v) return h;
+        }
+        h = (h + 1) & t.mask;
+    }
+    return EMPTY;
+}
+
+__device__ __forceinline__ bool sv_claim(uint32_t *fst, uint32_t slot, uint32_t dir, uint32_t lvl) {
+    const uint32_t shift = dir ? 16u : 0u;
+    uint32_t old = fst[slot];
+    while (true) {
+        if (((old >> shift) & 0xFFFFu) == lvl) return false;
+        const uint32_t want = (old & ~(0xFFFFu << shift)) | (lvl << shift);
+        const uint32_t prev = atomicCAS(&fst[slot], old, want);
+        if (prev == old) return true;
+        old = prev;
+    }
+}
+
+// One s-t query by the whole block; every control value is read between
+// two barriers (see the batch kernel). Returns INF when unreachable.
+__device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_t rt,
+                             uint32_t *s_cnt3, uint32_t *s_ovf, uint32_t *s_mu, uint32_t *s_nt) {
+    const uint32_t tid = threadIdx.x;
+    __syncthreads();
+    if (tid == 0) {
+        *s_nt = 0;
+        const uint32_t ss = sv_insert(t, rs, a.tbits, s_nt);
+        const uint32_t st = sv_insert(t, rt, a.tbits, s_nt);
+        t.df[ss] = 0;
+        t.db[st] = 0;
+        t.front[0] = ss;
+        t.front[1] = st | 0x80000000u;
+        s_cnt3[0] = 2;
+        s_cnt3[1] = 0;
+        s_cnt3[2] = 0;
+        *s_ovf = 0;
+        *s_mu = ss == st ? 0u : INF;
+    }
+    for (uint32_t lvl = 1;; ++lvl) {
+        __syncthreads();
+        const uint32_t cur = (lvl - 1) & 1u;
+        const uint32_t nfront = s_cnt3[(lvl - 1) % 3];
+        const uint32_t ovf = *s_ovf;
+        if (ovf || nfront == 0 || lvl >= 0xFFFFu) break;
+        if (tid == 0) s_cnt3[(lvl + 1) % 3] = 0;
+        const uint32_t *fr = t.front + (size_t)cur * t.fcap;
+        uint32_t *fn = t.front + (size_t)(cur ^ 1u) * t.fcap;
+        for (uint32_t f = tid; f < nfront && f < t.fcap; f += blockDim.x) {
+            const uint32_t ent = fr[f];
+            const uint32_t dir = ent >> 31, slot = ent & 0x7FFFFFFFu;
+            if (slot > t.mask) {
+                atomicOr(a.status, 2u);
+                continue;
+            }
+            const uint32_t x = t.key[slot];
+            if (x >= a.n) {
+                atomicOr(a.status, 2u);
+                continue;
+            }
+            const uint32_t *off = dir ? a.dn_off : a.up_off;
+            const uint2 *adj = dir ? a.dn_adj : a.up_adj;
+            const uint32_t ne = dir ? a.n_dn : a.n_up;
+            const uint32_t b = off[x], e_end = off[x + 1];
+            if (b > e_end || e_end > ne) {
+                atomicOr(a.status, 2u);
+                continue;
+            }
+            uint32_t *dist = dir ? t.db : t.df;
+            const uint32_t dx = dist[slot];
+            for (uint32_t j = b; j < e_end; ++j) {
+                const uint2 e = adj[j];
+                const uint32_t nd = sat_add(dx, e.y);
+                if (e.x >= a.n) {
+                    atomicOr(a.status, 2u);
+                    continue;
+                }
+                if (nd == INF || nd >= *(volatile uint32_t *)s_mu) continue;
+                const uint32_t ys = sv_insert(t, e.x, a.tbits, s_nt);
+                if (ys == EMPTY) {
+                    *s_ovf = 1;
+                    continue;
+                }
+                const uint32_t old = atomicMin(&dist[ys], nd);
+                if (nd >= old) continue;
+                const uint32_t other = dir ? t.df[ys] : t.db[ys];
+                if (other != INF) atomicMin(s_mu, sat_add(nd, other));
+                if (sv_claim(t.fst, ys, dir, lvl)) {
+                    const uint32_t p = atomicAdd(&s_cnt3[lvl % 3], 1u);
+                    if (p < t.fcap) fn[p] = ys | (dir << 31);
+                    else *s_ovf = 1;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (*s_ovf && tid == 0) atomicOr(a.status, 2u);
+    // the answer: least meeting sum over the reached vertices
+    const uint32_t nt = *s_nt;
+    uint32_t mu = INF;
+    for (uint32_t p = tid; p < nt; p += blockDim.x) {
+        const uint32_t sl = t.touched[p];
+        mu = min(mu, sat_add(t.df[sl], t.db[sl]));
+    }
+    __syncthreads();
+    if (tid == 0) *s_mu = INF;
+    __syncthreads();
+    atomicMin(s_mu, mu);
+    __syncthreads();
+    const uint32_t res = *s_mu;
+    // reset the slots this query touched
+    for (uint32_t p = tid; p < nt; p += blockDim.x) {
+        const uint32_t sl = t.touched[p];
+        t.key[sl] = EMPTY;
+        t.df[sl] = INF;
+        t.db[sl] = INF;
+        t.fst[sl] = 0;
+    }
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(SV_THREADS) k_serve(SvArgs a) {
+    __shared__ unsigned long long s_req;
+    __shared__ uint32_t s_go, s_cnt3[3], s_ovf, s_mu, s_nt;
+    const uint32_t tid = threadIdx.x;
+    Tab t;
+    const size_t tsz = (size_t)1 << a.tbits;
+    t.key = a.key + blockIdx.x * tsz;
+    t.df = a.df + blockIdx.x * tsz;
+    t.db = a.db + blockIdx.x * tsz;
+    t.fst = a.fst + blockIdx.x * tsz;
+    t.touched = a.touched + blockIdx.x * tsz;
+    t.front = a.front + blockIdx.x * (size_t)a.fcap * 2;
+    t.mask = (uint32_t)tsz - 1;
+    t.fcap = a.fcap;
+    while (true) {
+        // claim the next published request (thread 0), waiting boundedly
+        if (tid == 0) {
+            s_go = 0;
+            const unsigned long long t0 = globaltimer();
+            while (true) {
+                const unsigned long long pub = a.ctl->published;
+                unsigned long long cur = *(volatile unsigned long long *)a.claimed;
+                if (cur < pub) {
+                    if (atomicCAS(a.claimed, cur, cur + 1) == cur) {
+                        s_req = cur;
+                        s_go = 1;
+                        break;
+                    }
+                    continue;
+                }
+                if (a.ctl->stop) break;
+                if (globaltimer() - t0 > a.idle_ns) {
+                    atomicOr(a.status, 1u);
+                    break;
+                }
+                __nanosleep(2000);
+            }
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const unsigned long long i = s_req;
+        __threadfence_system();
+        const uint32_t slot = (uint32_t)(i % a.ring);
+        const volatile SvDesc *d = a.desc + slot;
+        const uint32_t s = d->s, k = d->k;
+        const uint64_t off = d->off;
+        if (tid == 0) a.t_begin[slot] = globaltimer();
+        const bool ok_s = s < a.n;
+        const uint32_t rs = ok_s ? a.rank[s] : 0;
+        for (uint32_t j = 0; j < k; ++j) {
+            const uint32_t tv = ((const volatile uint32_t *)a.targets)[off + j];
+            uint32_t ans = INF;
+            if (ok_s && tv < a.n) ans = sv_query(a, t, rs, a.rank[tv], s_cnt3, &s_ovf, &s_mu, &s_nt);
+            if (tid == 0) a.answers[off + j] = ans;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            a.t_end[slot] = globaltimer();
+            __threadfence_system();
+            ((volatile uint32_t *)a.done)[slot] = (uint32_t)(i + 1);
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+template <class T>
+struct Mapped {
+    T *h = nullptr;
+    T *d = nullptr;
+    void alloc(size_t n) {
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, std::max<size_t>(n, 1) * sizeof(T), cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{CH_ENOMEM, "mapped host allocation failed"};
+        }
+        h = static_cast<T *>(p);
+        std::memset(p, 0, std::max<size_t>(n, 1) * sizeof(T));
+        void *dp = nullptr;
+        CH_CUDA_TRY(cudaHostGetDevicePointer(&dp, p, 0));
+        d = static_cast<T *>(dp);
+    }
+    ~Mapped() {
+        if (h) cudaFreeHost(h);
+    }
+};
+
+}  // namespace gbch
+
+struct ch_server_s {
+    ch_s *h = nullptr;
+    cudaStream_t st = nullptr;
+    uint32_t nblocks = 0, ring = 0;
+    uint64_t pool = 0;
+    unsigned long long idle_ns = 0;
+    gbch::Mapped<gbch::SvCtl> ctl;
+    gbch::Mapped<gbch::SvDesc> desc;
+    gbch::Mapped<uint32_t> targets, answers, done;
+    gbch::Mapped<unsigned long long> t_begin, t_end;
+    gbch::DevBuf<uint32_t> scratch;
+    gbch::DevBuf<unsigned long long> claimed;
+    gbch::DevBuf<unsigned> status;
+    // host-side ring and pool state
+    uint64_t next_seq = 0, retired = 0, pool_head = 0, pool_tail = 0;
+    std::vector<uint64_t> slot_off, slot_end;
+    std::vector<uint32_t> slot_k;
+    std::vector<char> consumed;
+    bool running = false;
+};
+
+namespace gbch {
+
+void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
+    sv->h = h;
+    sv->ring = p->ring;
+    sv->pool = p->pool;
+    sv->idle_ns = (unsigned long long)p->idle_ms * 1000000ull;
+    const int sms = device_sm_count();
+    sv->nblocks = p->blocks ? p->blocks : (uint32_t)sms * 2;
+    uint32_t tbits = 10;
+    while (tbits < 24 && ((1u << tbits) < std::min<uint32_t>(h->n, 1u << 17))) ++tbits;
+    const size_t T = (size_t)1 << tbits;
+    const size_t fcap = 2 * T;
+    sv->ctl.alloc(1);
+    sv->desc.alloc(sv->ring);
+    sv->targets.alloc(sv->pool);
+    sv->answers.alloc(sv->pool);
+    sv->done.alloc(sv->ring);
+    sv->t_begin.alloc(sv->ring);
+    sv->t_end.alloc(sv->ring);
+    sv->slot_off.assign(sv->ring, 0);
+    sv->slot_end.assign(sv->ring, 0);
+    sv->slot_k.assign(sv->ring, 0);
+    sv->consumed.assign(sv->ring, 0);
+    // per block: key, df, db, fst, touched (T each) and two frontiers (fcap each)
+    const size_t per_block = 5 * T + 2 * fcap;
+    sv->scratch.alloc(per_block * sv->nblocks);
+    uint32_t *base = sv->scratch.ptr;
+    const size_t NB = sv->nblocks;
+    CH_CUDA_TRY(cudaStreamCreateWithFlags(&sv->st, cudaStreamNonBlocking));
+    CH_CUDA_TRY(cudaMemsetAsync(base, 0xFF, 3 * T * NB * 4, sv->st));           // key, df, db
+    CH_CUDA_TRY(cudaMemsetAsync(base + 3 * T * NB, 0, T * NB * 4, sv->st));      // fst
+    sv->claimed.alloc(1);
+    sv->claimed.zero(sv->st);
+    sv->status.alloc(1);
+    sv->status.zero(sv->st);
+    SvArgs a;
+    a.n = h->n;
+    a.n_up = (uint32_t)h->n_up;
+    a.n_dn = (uint32_t)h->n_down;
+    a.rank = h->rank.ptr;
+    a.up_off = h->up_off.ptr;
+    a.dn_off = h->dn_off.ptr;
+    a.up_adj = h->up_adj.ptr;
+    a.dn_adj = h->dn_adj.ptr;
+    a.ctl = sv->ctl.d;
+    a.desc = sv->desc.d;
+    a.targets = sv->targets.d;
+    a.answers = sv->answers.d;
+    a.done = sv->done.d;
+    a.t_begin = sv->t_begin.d;
+    a.t_end = sv->t_end.d;
+    a.ring = sv->ring;
+    a.claimed = sv->claimed.ptr;
+    a.status = sv->status.ptr;
+    a.idle_ns = sv->idle_ns;
+    a.tbits = tbits;
+    a.fcap = (uint32_t)fcap;
+    a.key = base;
+    a.df = base + T * NB;
+    a.db = base + 2 * T * NB;
+    a.fst = base + 3 * T * NB;
+    a.touched = base + 4 * T * NB;
+    a.front = base + 5 * T * NB;
+    k_serve<<<sv->nblocks, SV_THREADS, 0, sv->st>>>(a);
+    CH_CHECK_LAUNCH();
+    sv->running = true;
+}
+
+// Reserve k contiguous pool entries (ring allocator); false if no room.
+bool pool_reserve(ch_server_s *sv, uint32_t k, uint64_t &off, uint64_t &end) {
+    const uint64_t P = sv->pool;
+    if (k > P) return false;
+    uint64_t head = sv->pool_head;
+    const uint64_t in_wrap = head % P;
+    if (in_wrap + k > P) head += P - in_wrap;  // skip the tail end of the pool
+    if (head + k - sv->pool_tail > P) return false;
+    off = head % P;
+    end = head + k;
+    sv->pool_head = head + k;
+    return true;
+}
+
+int server_submit(ch_server_s *sv, uint32_t s, const uint32_t *targets, uint32_t k, uint64_t *ticket) {
+    if (!sv->running) return CH_EINVAL;
+    if (k == 0) return CH_EINVAL;
+    if (sv->next_seq - sv->retired >= sv->ring) {
+        // full: make sure the kernel is still serving before asking to retry
+        const cudaError_t e = cudaStreamQuery(sv->st);
+        if (e == cudaSuccess) return CH_ETIMEOUT;
+        if (e != cudaErrorNotReady) throw Error{CH_ECUDA, cudaGetErrorString(e)};
+        return CH_EAGAIN;
+    }
+    uint64_t off = 0, end = 0;
+    if (!pool_reserve(sv, k, off, end)) return CH_EAGAIN;
+    const uint64_t seq = sv->next_seq;
+    const uint32_t slot = (uint32_t)(seq % sv->ring);
+    std::memcpy(sv->targets.h + off, targets, k * sizeof(uint32_t));
+    sv->desc.h[slot] = SvDesc{s, k, off};
+    sv->done.h[slot] = 0;
+    sv->slot_off[slot] = off;
+    sv->slot_end[slot] = end;
+    sv->slot_k[slot] = k;
+    sv->consumed[slot] = 0;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    sv->ctl.h->published = seq + 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    sv->next_seq = seq + 1;
+    *ticket = seq;
+    return CH_OK;
+}
+
+bool server_poll(ch_server_s *sv, uint64_t ticket, uint32_t *out, uint64_t *dev_ns) {
+    const uint32_t slot = (uint32_t)(ticket % sv->ring);
+    if (ticket < sv->retired || ticket >= sv->next_seq) throw Error{CH_EINVAL, "unknown ticket"};
+    if (*(volatile uint32_t *)&sv->done.h[slot] != (uint32_t)(ticket + 1)) return false;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    if (out) std::memcpy(out, sv->answers.h + sv->slot_off[slot], sv->slot_k[slot] * sizeof(uint32_t));
+    if (dev_ns) *dev_ns = sv->t_end.h[slot] - sv->t_begin.h[slot];
+    sv->consumed[slot] = 1;
+    while (sv->retired < sv->next_seq && sv->consumed[sv->retired % sv->ring]) {
+        const uint32_t rs = (uint32_t)(sv->retired % sv->ring);
+        sv->pool_tail = sv->slot_end[rs];
+        sv->consumed[rs] = 0;
+        ++sv->retired;
+    }
+    if (sv->retired == sv->next_seq) sv->pool_tail = sv->pool_head;
+    return true;
+}
+
+int server_stop(ch_server_s *sv, uint32_t *status) {
+    if (!sv->running) return CH_OK;
+    sv->ctl.h->stop = 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    // bounded wait: the kernel ends once no request is left, or at the idle limit
+    const auto t0 = std::chrono::steady_clock::now();
+    const double limit_s = (double)sv->idle_ns * 1e-9 + 30.0;
+    while (true) {
+        const cudaError_t e = cudaStreamQuery(sv->st);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) throw Error{CH_ECUDA, std::string("server kernel: ") + cudaGetErrorString(e)};
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit_s)
+            return CH_ETIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    sv->running = false;
+    CH_CUDA_TRY(cudaMemcpy(status, sv->status.ptr, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    return CH_OK;
+}
+
+bool server_alive(ch_server_s *sv) {
+    const cudaError_t e = cudaStreamQuery(sv->st);
+    if (e == cudaErrorNotReady) return true;
+    if (e != cudaSuccess) throw Error{CH_ECUDA, cudaGetErrorString(e)};
+    return false;
+}
+
+ch_server_s *server_new() { return new (std::nothrow) ch_server_s(); }
+void server_delete(ch_server_s *sv) { delete sv; }
+
+void server_free(ch_server_s *sv) {
+    if (sv->running) {
+        uint32_t st = 0;
+        server_stop(sv, &st);
+    }
+    if (sv->st) cudaStreamDestroy(sv->st);
+}
+
+// Replays a request schedule against the server: request i is submitted at
+// start + arrival_ns[i] (or as soon as there is room), completions are
+// polled in between, and each request's latency is the time from its
+// scheduled arrival to the moment its answers were seen on the host.
+void server_replay(ch_server_s *sv, uint64_t nreq, const uint32_t *src, const uint32_t *k,
+                   const uint64_t *toff, const uint32_t *targets, const uint64_t *arrival_ns,
+                   uint32_t *answers, uint64_t *latency_ns, uint64_t *service_ns, double limit_s) {
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    auto now_ns = [&] {
+        return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clk::now() - t0).count();
+    };
+    std::vector<uint64_t> ticket(nreq);
+    std::vector<uint64_t> inflight;  // request indices submitted, not yet seen done
+    inflight.reserve(sv->ring);
+    uint64_t next = 0, finished = 0;
+    while (finished < nreq) {
+        // submit what is due
+        while (next < nreq && arrival_ns[next] <= now_ns()) {
+            const int rc = server_submit(sv, src[next], targets + toff[next], k[next], &ticket[next]);
+            if (rc == CH_EAGAIN) break;
+            if (rc != CH_OK) throw Error{rc, "server stopped serving during the replay"};
+            inflight.push_back(next);
+            ++next;
+        }
+        // poll completions
+        size_t w = 0;
+        for (size_t q = 0; q < inflight.size(); ++q) {
+            const uint64_t i = inflight[q];
+            uint64_t dev = 0;
+            if (server_poll(sv, ticket[i], answers + toff[i], &dev)) {
+                latency_ns[i] = now_ns() - arrival_ns[i];
+                if (service_ns) service_ns[i] = dev;
+                ++finished;
+            } else {
+                inflight[w++] = i;
+            }
+        }
+        inflight.resize(w);
+        if (std::chrono::duration<double>(clk::now() - t0).count() > limit_s)
+            throw Error{CH_ETIMEOUT, "replay exceeded its time limit"};
+        if (!server_alive(sv)) throw Error{CH_ETIMEOUT, "server kernel ended during the replay"};
+    }
+}
+
+}  // namespace gbch
