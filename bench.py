@@ -274,6 +274,7 @@ def serve_bench(args):
 
     out = {}
     with ch.Server(h, blocks=0, ring=1 << 14, pool=1 << 24, idle_ms=20_000) as sv:
+        nblocks = sv.blocks
         # saturated: everything due at once
         t0 = time.perf_counter()
         ans, lat, svc = sv.replay(src, ks, tg, np.zeros(nreq, np.uint64))
@@ -317,7 +318,7 @@ def serve_bench(args):
         "config": {"workload": f"{args.serve_workload}-serve", "vertices": n, "edges": int(g.m),
                    "requests": nreq, "mean_targets_per_request": float(ks.mean()),
                    "one_to_many_fraction": 0.2, "targets_max": 1024,
-                   "server_blocks": 2 * 152, "build_s": st["build_ms"] / 1e3},
+                   "server_blocks": nblocks, "build_s": st["build_ms"] / 1e3},
         "results": out, "dtype": "u32", "data": "synthetic",
     }
     print(json.dumps(line), flush=True)

@@ -267,19 +267,20 @@ int ch_mlp_forward(const float *weights, const int64_t *rows, uint64_t n, float 
 
 /* ---- Query server: continuous batching (no counterpart in the paper) ----
  *
- * A persistent kernel on its own stream keeps `blocks` slots busy with
- * requests published by the host: a source and 1..k targets (k = 1 is an
- * s-t query, k > 1 one-to-many). A free slot takes the next published
- * request at once, so requests that arrive while others are on the device
- * are admitted as slots free up and overlap with them. Admission is by
- * memory: targets and answers live in a pool of `pool` entries and the ring
- * holds `ring` requests; ch_server_submit returns CH_EAGAIN when either is
- * full (poll completed requests, then retry). Each answer equals what
- * ch_query_batch returns for the same pair. The kernel's idle wait is
+ * A persistent kernel on its own stream serves requests published by the
+ * host: a source and 1..k targets (k = 1 is an s-t query, k > 1
+ * one-to-many). The unit of work is one (source, target) pair; its blocks
+ * take pairs in publication order, so the targets of a large request are
+ * spread over all free blocks and requests that arrive while others are on
+ * the device start as blocks free up, overlapping with them. Admission is
+ * by memory: targets and answers live in a pool of `pool` entries and the
+ * ring holds `ring` requests; ch_server_submit returns CH_EAGAIN when
+ * either is full (poll completed requests, then retry). Each answer equals
+ * what ch_query_batch returns for the same pair. The kernel's idle wait is
  * bounded by idle_ms: after that long without a request it ends, and later
  * submits return CH_ETIMEOUT. The handle `ch` must outlive the server. */
 typedef struct {
-    uint32_t blocks;   /* slots; 0 = two per SM */
+    uint32_t blocks;   /* blocks of the device loop; 0 = as many as are resident at once */
     uint32_t ring;     /* requests in flight at most */
     uint64_t pool;     /* target/answer entries at most */
     uint32_t idle_ms;  /* idle limit of the device loop */
@@ -289,6 +290,9 @@ typedef struct {
 typedef struct ch_server_s ch_server_t;
 
 int ch_server_start(ch_t *ch, const ch_server_params_t *params, ch_server_t **out);
+
+/* Number of blocks the device loop runs (after the default is resolved). */
+uint32_t ch_server_blocks(const ch_server_t *sv);
 
 /* Copies the k targets (host memory) and publishes the request; *ticket
  * identifies it for ch_server_poll. */

@@ -118,6 +118,8 @@ def load(build_if_missing: bool = True):
     lib.ch_server_poll.argtypes = [P, C.c_uint64, P, C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
     lib.ch_server_replay.argtypes = [P, C.c_uint64, P, P, P, P, P, P, P, P, C.c_double]
     lib.ch_server_stop.argtypes = [P]
+    lib.ch_server_blocks.argtypes = [P]
+    lib.ch_server_blocks.restype = C.c_uint32
     for f in ("ch_server_start", "ch_server_submit", "ch_server_poll", "ch_server_replay",
               "ch_server_stop"):
         getattr(lib, f).restype = C.c_int
@@ -328,6 +330,11 @@ class Server:
         p = ServerParamsT(blocks, ring, pool, idle_ms, 0)
         self._h = C.c_void_p()
         _check(load().ch_server_start(ch._h, C.byref(p), C.byref(self._h)))
+
+    @property
+    def blocks(self) -> int:
+        """Blocks of the device loop."""
+        return int(load().ch_server_blocks(self._h))
 
     def submit(self, s: int, targets) -> int | None:
         """Ticket of the published request, or None when the server is full."""

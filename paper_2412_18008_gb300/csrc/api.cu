@@ -415,6 +415,8 @@ int ch_server_start(ch_t *ch, const ch_server_params_t *params, ch_server_t **ou
     return CH_OK;
 }
 
+uint32_t ch_server_blocks(const ch_server_t *sv) { return sv ? server_blocks(sv) : 0; }
+
 int ch_server_submit(ch_server_t *sv, uint32_t s, const uint32_t *targets, uint32_t k,
                      uint64_t *ticket) {
     if (!sv || !targets || !ticket || k == 0) {

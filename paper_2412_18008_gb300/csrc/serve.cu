@@ -1,24 +1,27 @@
 // Device-resident query server with continuous batching (no counterpart in
 // the paper, which runs queries one after another).
 //
-// A persistent kernel keeps one block per slot busy. The host publishes
-// requests into a ring in mapped pinned memory (a source and 1..k targets;
-// k = 1 is an s-t query, k > 1 one-to-many); any block that is free claims
-// the next published request, so requests that arrive while others are
-// being served are picked up as soon as a slot frees, and their work
-// overlaps with the work already on the device. Admission is by memory:
-// targets and answers live in a fixed pool, and a request is only published
+// A persistent kernel keeps its blocks busy with requests published by the
+// host into mapped pinned memory: a source and 1..k targets (k = 1 is an
+// s-t query, k > 1 one-to-many). The unit of work is one (source, target)
+// pair: a request's targets occupy consecutive positions of a pool, and
+// blocks take pool positions in order from a device counter, so the
+// targets of one large request are spread over every free block, and
+// requests that arrive while others are on the device start as soon as a
+// block frees. The block that finishes a request's last target publishes its
+// completion. Admission is by memory: the host publishes a request only
 // when the ring and the pool have room for it (ch_server_submit returns
 // CH_EAGAIN otherwise).
 //
-// Each query is the same bidirectional upward search as ch_query_batch
-// (label-correcting over the rank DAG, pruned by the best meeting sum), with
-// its labels in a per-block hash table in global memory large enough for any
-// search space of the hierarchy, so a request never needs a second kernel.
+// Each pair runs the batch kernel's shared-memory search (the same
+// bidirectional upward search with the same pruning); a pair whose search
+// spaces overflow the shared table is redone in the same block on a per-block
+// hash table in global memory, so a request never needs a second kernel.
 //
 // Waits are bounded: a block that finds no work sleeps in short steps and
-// gives up after the idle limit (device globaltimer), recording a timeout;
-// the host's stop call waits a bounded time for the kernel.
+// gives up after the idle limit (device globaltimer), which closes the loop
+// for every block and records a timeout; the host's stop call waits a
+// bounded time for the kernel.
 
 #include <algorithm>
 #include <atomic>
@@ -28,39 +31,40 @@
 #include <thread>
 
 #include "handle.cuh"
+#include "qsearch.cuh"
 
 namespace gbch {
 namespace {
 
-constexpr uint32_t EMPTY = 0xFFFFFFFFu;
-constexpr int SV_THREADS = 256;
-
 struct SvDesc {  // one request, written by the host before publication
     uint32_t s, k;
-    uint64_t off;  // first target / answer in the pool
+    uint64_t pos;  // pool position (monotone) of its first target
+    uint64_t seq;  // its ticket
 };
 
 struct SvCtl {  // mapped host memory, written by the host only
-    volatile uint64_t published;  // requests [0, published) are readable
-    volatile uint32_t stop;
+    uint64_t published;  // pool positions [0, published) are readable
+    uint32_t stop;
     uint32_t pad;
 };
 
 struct SvArgs {
-    uint32_t n, n_up, n_dn;
-    const uint32_t *rank, *up_off, *dn_off;
-    const uint2 *up_adj, *dn_adj;
+    QArgs q;                     // hierarchy and the error word (status)
     SvCtl *ctl;                  // mapped
     const SvDesc *desc;          // mapped ring
+    const uint32_t *item_req;    // mapped pool: ring slot of the request owning each entry
     const uint32_t *targets;     // mapped pool
     uint32_t *answers;           // mapped pool
-    uint32_t *done;              // mapped ring: sequence + 1 when served
+    uint32_t *done;              // mapped ring: ticket + 1 when served
     unsigned long long *t_begin, *t_end;  // mapped ring: device time (ns)
     uint32_t ring;
-    unsigned long long *claimed;  // device counter
+    uint64_t pool;
+    unsigned long long *claimed;  // device: next pool position to take
+    uint32_t *finished;           // device: targets served per ring slot
+    uint32_t *closing;            // device: set once a block reached the idle limit
     unsigned *status;             // device: 1 = idle limit reached, 2 = index or capacity check failed
     unsigned long long idle_ns;
-    // per-block scratch (global memory)
+    // per-block fallback tables (global memory)
     uint32_t tbits;               // table of 2^tbits slots
     uint32_t fcap;                // frontier capacity
     uint32_t *key, *df, *db, *fst, *front, *touched;
@@ -70,6 +74,18 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_sys(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
 struct Tab {
@@ -107,10 +123,13 @@ __device__ __forceinline__ bool sv_claim(uint32_t *fst, uint32_t slot, uint32_t 
     }
 }
 
-// One s-t query by the whole block; every control value is read between
-// two barriers (see the batch kernel). Returns INF when unreachable.
+// Fallback for a pair whose search spaces overflow the shared table: the
+// same search, one frontier entry per thread, labels in the block's global
+// hash table. Control values (s_cnt3, s_ovf) are read between two barriers
+// as in block_search. Returns INF when unreachable.
 __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_t rt,
                              uint32_t *s_cnt3, uint32_t *s_ovf, uint32_t *s_mu, uint32_t *s_nt) {
+    const QArgs &g = a.q;
     const uint32_t tid = threadIdx.x;
     __syncthreads();
     if (tid == 0) {
@@ -140,20 +159,20 @@ __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_
             const uint32_t ent = fr[f];
             const uint32_t dir = ent >> 31, slot = ent & 0x7FFFFFFFu;
             if (slot > t.mask) {
-                atomicOr(a.status, 2u);
+                atomicOr(a.status, QERR_BOUND);
                 continue;
             }
             const uint32_t x = t.key[slot];
-            if (x >= a.n) {
-                atomicOr(a.status, 2u);
+            if (x >= g.n) {
+                atomicOr(a.status, QERR_BOUND);
                 continue;
             }
-            const uint32_t *off = dir ? a.dn_off : a.up_off;
-            const uint2 *adj = dir ? a.dn_adj : a.up_adj;
-            const uint32_t ne = dir ? a.n_dn : a.n_up;
+            const uint32_t *off = dir ? g.dn_off : g.up_off;
+            const uint2 *adj = dir ? g.dn_adj : g.up_adj;
+            const uint32_t ne = dir ? g.n_dn : g.n_up;
             const uint32_t b = off[x], e_end = off[x + 1];
             if (b > e_end || e_end > ne) {
-                atomicOr(a.status, 2u);
+                atomicOr(a.status, QERR_BOUND);
                 continue;
             }
             uint32_t *dist = dir ? t.db : t.df;
@@ -161,8 +180,8 @@ __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_
             for (uint32_t j = b; j < e_end; ++j) {
                 const uint2 e = adj[j];
                 const uint32_t nd = sat_add(dx, e.y);
-                if (e.x >= a.n) {
-                    atomicOr(a.status, 2u);
+                if (e.x >= g.n) {
+                    atomicOr(a.status, QERR_BOUND);
                     continue;
                 }
                 if (nd == INF || nd >= *(volatile uint32_t *)s_mu) continue;
@@ -184,7 +203,7 @@ __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_
         }
     }
     __syncthreads();
-    if (*s_ovf && tid == 0) atomicOr(a.status, 2u);
+    if (*s_ovf && tid == 0) atomicOr(a.status, QERR_BOUND);
     // the answer: least meeting sum over the reached vertices
     const uint32_t nt = *s_nt;
     uint32_t mu = INF;
@@ -210,10 +229,14 @@ __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_
     return res;
 }
 
-__global__ void __launch_bounds__(SV_THREADS) k_serve(SvArgs a) {
-    __shared__ unsigned long long s_req;
-    __shared__ uint32_t s_go, s_cnt3[3], s_ovf, s_mu, s_nt;
+__global__ void __launch_bounds__(QB_THREADS) k_serve(SvArgs a) {
+    extern __shared__ __align__(16) unsigned char qb_raw[];
+    QBSmem &q = *reinterpret_cast<QBSmem *>(qb_raw);
+    __shared__ uint32_t s_go, s_src, s_tgt, s_k, s_slot, s_first;
+    __shared__ unsigned long long s_seq;
+    __shared__ uint64_t s_e;
     const uint32_t tid = threadIdx.x;
+    const QArgs &g = a.q;
     Tab t;
     const size_t tsz = (size_t)1 << a.tbits;
     t.key = a.key + blockIdx.x * tsz;
@@ -225,51 +248,81 @@ __global__ void __launch_bounds__(SV_THREADS) k_serve(SvArgs a) {
     t.mask = (uint32_t)tsz - 1;
     t.fcap = a.fcap;
     while (true) {
-        // claim the next published request (thread 0), waiting boundedly
+        __syncthreads();
+        // thread 0 takes the next pool position and waits (boundedly) until
+        // the host has published it
         if (tid == 0) {
             s_go = 0;
-            const unsigned long long t0 = globaltimer();
-            while (true) {
-                const unsigned long long pub = a.ctl->published;
-                unsigned long long cur = *(volatile unsigned long long *)a.claimed;
-                if (cur < pub) {
-                    if (atomicCAS(a.claimed, cur, cur + 1) == cur) {
-                        s_req = cur;
+            if (!*(volatile uint32_t *)a.closing) {
+                const unsigned long long pos = atomicAdd(a.claimed, 1ull);
+                const unsigned long long t0 = globaltimer();
+                unsigned sleep_ns = 256;
+                while (true) {
+                    if (ld_acquire_sys(&a.ctl->published) > pos) {
                         s_go = 1;
                         break;
                     }
-                    continue;
+                    // stop is set after the last publication: look again first
+                    if (ld_acquire_sys(&a.ctl->stop)) {
+                        s_go = ld_acquire_sys(&a.ctl->published) > pos;
+                        break;
+                    }
+                    if (*(volatile uint32_t *)a.closing) break;
+                    if (globaltimer() - t0 > a.idle_ns) {
+                        atomicOr(a.status, 1u);
+                        atomicExch(a.closing, 1u);
+                        break;
+                    }
+                    __nanosleep(sleep_ns);
+                    sleep_ns = min(2u * sleep_ns, 8192u);
                 }
-                if (a.ctl->stop) break;
-                if (globaltimer() - t0 > a.idle_ns) {
-                    atomicOr(a.status, 1u);
-                    break;
+                if (s_go) {
+                    const uint64_t e = pos % a.pool;
+                    const uint32_t slot = ((const volatile uint32_t *)a.item_req)[e];
+                    if (slot < a.ring) {
+                        const volatile SvDesc *d = a.desc + slot;
+                        s_src = d->s;
+                        s_k = d->k;
+                        s_seq = d->seq;
+                        s_first = d->pos == pos;
+                        s_tgt = ((const volatile uint32_t *)a.targets)[e];
+                        s_slot = slot;
+                        s_e = e;
+                        if (s_first) a.t_begin[slot] = globaltimer();
+                    } else {
+                        atomicOr(a.status, QERR_BOUND);
+                        s_go = 2;  // skip the entry
+                    }
                 }
-                __nanosleep(2000);
             }
         }
         __syncthreads();
-        if (!s_go) break;
-        const unsigned long long i = s_req;
-        __threadfence_system();
-        const uint32_t slot = (uint32_t)(i % a.ring);
-        const volatile SvDesc *d = a.desc + slot;
-        const uint32_t s = d->s, k = d->k;
-        const uint64_t off = d->off;
-        if (tid == 0) a.t_begin[slot] = globaltimer();
-        const bool ok_s = s < a.n;
-        const uint32_t rs = ok_s ? a.rank[s] : 0;
-        for (uint32_t j = 0; j < k; ++j) {
-            const uint32_t tv = ((const volatile uint32_t *)a.targets)[off + j];
-            uint32_t ans = INF;
-            if (ok_s && tv < a.n) ans = sv_query(a, t, rs, a.rank[tv], s_cnt3, &s_ovf, &s_mu, &s_nt);
-            if (tid == 0) a.answers[off + j] = ans;
+        const uint32_t go = s_go;
+        if (!go) break;
+        if (go != 1) continue;
+        const uint32_t s = s_src, tv = s_tgt;
+        uint32_t ans = INF;
+        if (s < g.n && tv < g.n) {
+            const uint32_t rs = g.rank[s], rt = g.rank[tv];
+            if (rs < g.n && rt < g.n) {
+                uint32_t cnt;
+                if (!block_query<true>(q, g, rs, rt, ans, cnt))
+                    ans = sv_query(a, t, rs, rt, q.cnt3, &q.ovf, &q.mu, &q.cnt);
+            } else if (tid == 0) {
+                atomicOr(a.status, QERR_BOUND);
+            }
         }
-        __syncthreads();
         if (tid == 0) {
-            a.t_end[slot] = globaltimer();
+            const uint32_t slot = s_slot;
+            ((volatile uint32_t *)a.answers)[s_e] = ans;
             __threadfence_system();
-            ((volatile uint32_t *)a.done)[slot] = (uint32_t)(i + 1);
+            if (atomicAdd(&a.finished[slot], 1u) + 1u == s_k) {
+                // last target of the request: publish its completion
+                atomicExch(&a.finished[slot], 0u);
+                a.t_end[slot] = globaltimer();
+                __threadfence_system();
+                ((volatile uint32_t *)a.done)[slot] = (uint32_t)(s_seq + 1);
+            }
         }
     }
 }
@@ -311,14 +364,15 @@ struct ch_server_s {
     unsigned long long idle_ns = 0;
     gbch::Mapped<gbch::SvCtl> ctl;
     gbch::Mapped<gbch::SvDesc> desc;
-    gbch::Mapped<uint32_t> targets, answers, done;
+    gbch::Mapped<uint32_t> item_req, targets, answers, done;
     gbch::Mapped<unsigned long long> t_begin, t_end;
     gbch::DevBuf<uint32_t> scratch;
     gbch::DevBuf<unsigned long long> claimed;
+    gbch::DevBuf<uint32_t> finished, closing;
     gbch::DevBuf<unsigned> status;
     // host-side ring and pool state
     uint64_t next_seq = 0, retired = 0, pool_head = 0, pool_tail = 0;
-    std::vector<uint64_t> slot_off, slot_end;
+    std::vector<uint64_t> slot_pos;
     std::vector<uint32_t> slot_k;
     std::vector<char> consumed;
     bool running = false;
@@ -332,20 +386,25 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     sv->pool = p->pool;
     sv->idle_ns = (unsigned long long)p->idle_ms * 1000000ull;
     const int sms = device_sm_count();
-    sv->nblocks = p->blocks ? p->blocks : (uint32_t)sms * 2;
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(QBSmem)));
+    int per_sm = 0;
+    CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, QB_THREADS,
+                                                              sizeof(QBSmem)));
+    sv->nblocks = p->blocks ? p->blocks : (uint32_t)sms * (uint32_t)std::max(per_sm, 1);
     uint32_t tbits = 10;
     while (tbits < 24 && ((1u << tbits) < std::min<uint32_t>(h->n, 1u << 17))) ++tbits;
     const size_t T = (size_t)1 << tbits;
     const size_t fcap = 2 * T;
     sv->ctl.alloc(1);
     sv->desc.alloc(sv->ring);
+    sv->item_req.alloc(sv->pool);
     sv->targets.alloc(sv->pool);
     sv->answers.alloc(sv->pool);
     sv->done.alloc(sv->ring);
     sv->t_begin.alloc(sv->ring);
     sv->t_end.alloc(sv->ring);
-    sv->slot_off.assign(sv->ring, 0);
-    sv->slot_end.assign(sv->ring, 0);
+    sv->slot_pos.assign(sv->ring, 0);
     sv->slot_k.assign(sv->ring, 0);
     sv->consumed.assign(sv->ring, 0);
     // per block: key, df, db, fst, touched (T each) and two frontiers (fcap each)
@@ -358,26 +417,35 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     CH_CUDA_TRY(cudaMemsetAsync(base + 3 * T * NB, 0, T * NB * 4, sv->st));      // fst
     sv->claimed.alloc(1);
     sv->claimed.zero(sv->st);
+    sv->finished.alloc(sv->ring);
+    sv->finished.zero(sv->st);
+    sv->closing.alloc(1);
+    sv->closing.zero(sv->st);
     sv->status.alloc(1);
     sv->status.zero(sv->st);
-    SvArgs a;
-    a.n = h->n;
-    a.n_up = (uint32_t)h->n_up;
-    a.n_dn = (uint32_t)h->n_down;
-    a.rank = h->rank.ptr;
-    a.up_off = h->up_off.ptr;
-    a.dn_off = h->dn_off.ptr;
-    a.up_adj = h->up_adj.ptr;
-    a.dn_adj = h->dn_adj.ptr;
+    SvArgs a{};
+    a.q.n = h->n;
+    a.q.n_up = (uint32_t)h->n_up;
+    a.q.n_dn = (uint32_t)h->n_down;
+    a.q.rank = h->rank.ptr;
+    a.q.up_off = h->up_off.ptr;
+    a.q.dn_off = h->dn_off.ptr;
+    a.q.up_adj = h->up_adj.ptr;
+    a.q.dn_adj = h->dn_adj.ptr;
+    a.q.err = sv->status.ptr;
     a.ctl = sv->ctl.d;
     a.desc = sv->desc.d;
+    a.item_req = sv->item_req.d;
     a.targets = sv->targets.d;
     a.answers = sv->answers.d;
     a.done = sv->done.d;
     a.t_begin = sv->t_begin.d;
     a.t_end = sv->t_end.d;
     a.ring = sv->ring;
+    a.pool = sv->pool;
     a.claimed = sv->claimed.ptr;
+    a.finished = sv->finished.ptr;
+    a.closing = sv->closing.ptr;
     a.status = sv->status.ptr;
     a.idle_ns = sv->idle_ns;
     a.tbits = tbits;
@@ -388,23 +456,27 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     a.fst = base + 3 * T * NB;
     a.touched = base + 4 * T * NB;
     a.front = base + 5 * T * NB;
-    k_serve<<<sv->nblocks, SV_THREADS, 0, sv->st>>>(a);
+    k_serve<<<sv->nblocks, QB_THREADS, sizeof(QBSmem), sv->st>>>(a);
     CH_CHECK_LAUNCH();
     sv->running = true;
 }
 
-// Reserve k contiguous pool entries (ring allocator); false if no room.
-bool pool_reserve(ch_server_s *sv, uint32_t k, uint64_t &off, uint64_t &end) {
-    const uint64_t P = sv->pool;
-    if (k > P) return false;
-    uint64_t head = sv->pool_head;
-    const uint64_t in_wrap = head % P;
-    if (in_wrap + k > P) head += P - in_wrap;  // skip the tail end of the pool
-    if (head + k - sv->pool_tail > P) return false;
-    off = head % P;
-    end = head + k;
-    sv->pool_head = head + k;
+// Reserve k consecutive pool positions (a ring; a request may wrap around
+// the end of the pool); false if no room.
+bool pool_reserve(ch_server_s *sv, uint32_t k, uint64_t &pos) {
+    if (sv->pool_head + k - sv->pool_tail > sv->pool) return false;
+    pos = sv->pool_head;
+    sv->pool_head += k;
     return true;
+}
+
+// Copies n entries between a host array and the pool ring at position pos.
+template <class F>
+void pool_span(uint64_t P, uint64_t pos, uint64_t n, F &&f) {
+    const uint64_t e = pos % P;
+    const uint64_t n1 = std::min<uint64_t>(n, P - e);
+    f(e, 0, n1);
+    if (n1 < n) f(0, n1, n - n1);
 }
 
 int server_submit(ch_server_s *sv, uint32_t s, const uint32_t *targets, uint32_t k, uint64_t *ticket) {
@@ -417,19 +489,22 @@ int server_submit(ch_server_s *sv, uint32_t s, const uint32_t *targets, uint32_t
         if (e != cudaErrorNotReady) throw Error{CH_ECUDA, cudaGetErrorString(e)};
         return CH_EAGAIN;
     }
-    uint64_t off = 0, end = 0;
-    if (!pool_reserve(sv, k, off, end)) return CH_EAGAIN;
+    if (k > sv->pool) return CH_EINVAL;
+    uint64_t pos = 0;
+    if (!pool_reserve(sv, k, pos)) return CH_EAGAIN;
     const uint64_t seq = sv->next_seq;
     const uint32_t slot = (uint32_t)(seq % sv->ring);
-    std::memcpy(sv->targets.h + off, targets, k * sizeof(uint32_t));
-    sv->desc.h[slot] = SvDesc{s, k, off};
+    pool_span(sv->pool, pos, k, [&](uint64_t e, uint64_t j, uint64_t n) {
+        std::memcpy(sv->targets.h + e, targets + j, n * sizeof(uint32_t));
+        std::fill(sv->item_req.h + e, sv->item_req.h + e + n, slot);
+    });
+    sv->desc.h[slot] = SvDesc{s, k, pos, seq};
     sv->done.h[slot] = 0;
-    sv->slot_off[slot] = off;
-    sv->slot_end[slot] = end;
+    sv->slot_pos[slot] = pos;
     sv->slot_k[slot] = k;
     sv->consumed[slot] = 0;
     std::atomic_thread_fence(std::memory_order_seq_cst);
-    sv->ctl.h->published = seq + 1;
+    *(volatile uint64_t *)&sv->ctl.h->published = pos + k;
     std::atomic_thread_fence(std::memory_order_seq_cst);
     sv->next_seq = seq + 1;
     *ticket = seq;
@@ -441,22 +516,24 @@ bool server_poll(ch_server_s *sv, uint64_t ticket, uint32_t *out, uint64_t *dev_
     if (ticket < sv->retired || ticket >= sv->next_seq) throw Error{CH_EINVAL, "unknown ticket"};
     if (*(volatile uint32_t *)&sv->done.h[slot] != (uint32_t)(ticket + 1)) return false;
     std::atomic_thread_fence(std::memory_order_acquire);
-    if (out) std::memcpy(out, sv->answers.h + sv->slot_off[slot], sv->slot_k[slot] * sizeof(uint32_t));
+    if (out)
+        pool_span(sv->pool, sv->slot_pos[slot], sv->slot_k[slot], [&](uint64_t e, uint64_t j, uint64_t n) {
+            std::memcpy(out + j, sv->answers.h + e, n * sizeof(uint32_t));
+        });
     if (dev_ns) *dev_ns = sv->t_end.h[slot] - sv->t_begin.h[slot];
     sv->consumed[slot] = 1;
     while (sv->retired < sv->next_seq && sv->consumed[sv->retired % sv->ring]) {
         const uint32_t rs = (uint32_t)(sv->retired % sv->ring);
-        sv->pool_tail = sv->slot_end[rs];
+        sv->pool_tail = sv->slot_pos[rs] + sv->slot_k[rs];
         sv->consumed[rs] = 0;
         ++sv->retired;
     }
-    if (sv->retired == sv->next_seq) sv->pool_tail = sv->pool_head;
     return true;
 }
 
 int server_stop(ch_server_s *sv, uint32_t *status) {
     if (!sv->running) return CH_OK;
-    sv->ctl.h->stop = 1;
+    *(volatile uint32_t *)&sv->ctl.h->stop = 1;
     std::atomic_thread_fence(std::memory_order_seq_cst);
     // bounded wait: the kernel ends once no request is left, or at the idle limit
     const auto t0 = std::chrono::steady_clock::now();
@@ -480,6 +557,8 @@ bool server_alive(ch_server_s *sv) {
     if (e != cudaSuccess) throw Error{CH_ECUDA, cudaGetErrorString(e)};
     return false;
 }
+
+uint32_t server_blocks(const ch_server_s *sv) { return sv->nblocks; }
 
 ch_server_s *server_new() { return new (std::nothrow) ch_server_s(); }
 void server_delete(ch_server_s *sv) { delete sv; }
