@@ -43,6 +43,10 @@ WORKLOADS = {
 }
 METRIC = "CH build seconds & shortcut count; batched s-t queries/sec; p99 query latency"
 L2_BYTES = 129 * 1024 * 1024
+# DRAM bytes (read + write) of one k_query_block launch on the full query
+# batch, from an ncu capture of this kernel (None until captured for the
+# current kernel).
+QUERY_TRAFFIC_PER_LAUNCH = None
 
 
 def parse():
@@ -55,6 +59,8 @@ def parse():
     ap.add_argument("--hop-limit", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default query kernel configuration")
     ap.add_argument("--build-only", action="store_true",
                     help="time the CH build alone (profiling the build kernels)")
     ap.add_argument("--queries", type=int, default=None,
@@ -361,18 +367,25 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
 
+    qcfg = None  # query kernel configuration, chosen by the autotuner during warm-up
+
     def step():
         h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
                         hop_limit=args.hop_limit, stream=stream)
+        if qcfg is not None:
+            h.set_query_config(*qcfg)
         if not args.build_only:
             h.query_batch_raw(s_d.data_ptr(), t_d.data_ptr(), nq, out_d.data_ptr(), None, sp)
         return h
 
     torch.cuda.synchronize()
-    for _ in range(args.warmup):
+    tune_ms = None
+    for wi in range(args.warmup):
         with torch.cuda.stream(stream):
             h = step()
         stream.synchronize()
+        if wi == 0 and not args.no_autotune:
+            qcfg, tune_ms = h.autotune_queries(sample=1 << 16, seed=11, stream=stream)
         h.close()
 
     # timed region
@@ -393,6 +406,8 @@ def main():
             e0.record(stream)
             h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
                             hop_limit=args.hop_limit, stream=stream)
+            if qcfg is not None:
+                h.set_query_config(*qcfg)
             e1.record(stream)
             if not args.build_only:
                 h.query_batch_raw(s_d.data_ptr(), t_d.data_ptr(), nq, out_d.data_ptr(), None, sp)
@@ -411,6 +426,7 @@ def main():
     clocks = sampler.stop()
     h_last = handles[-1]
     h_last.query_status(stream)
+    q_exp, q_edges = h_last.query_work(stream)  # the last step's batch
     for h in handles[:-1]:
         h.close()
 
@@ -441,20 +457,38 @@ def main():
     stream.synchronize()
     mean_ss = float(st.cpu().numpy().view(np.uint32).mean())
 
-    # roofline of the dominant kernel: the witness search
+    # roofline of the dominant kernel: the query block kernel (k_query_block,
+    # one persistent launch per batch of up to 4M queries). Algorithmic bytes
+    # per launch: 12 B per expanded frontier entry (its two CSR offsets and
+    # its label), 8 B per adjacency entry scanned (id + weight), 20 B per
+    # query (source, target, answer, two rank lookups); counted by the kernel.
     peak, peak_src = load_peaks()
     wit_gbs = stats["witness_bytes"] / (stats["witness_ms"] * 1e-3) / 1e9 if stats["witness_ms"] else 0.0
     phases = {k: stats[k] for k in ("normalise_ms", "score_ms", "select_ms", "prep_ms",
                                     "contract_ms", "update_ms", "postprocess_ms")}
-    roofline = {
-        "kernel": "k_witness (score + contract witness searches)",
-        "bound": "hbm", "achieved": round(wit_gbs, 1), "peak": peak, "unit": "GB/s",
-        "frac": round(wit_gbs / peak, 4), "traffic": None,
-        "peak_source": peak_src,
-        "bytes_per_launch": stats["witness_bytes"] / max(1, stats["witness_launches"]),
-        "ms_per_launch": stats["witness_ms"] / max(1, stats["witness_launches"]),
-        "share_of_build": round(stats["witness_ms"] / mean_build, 3) if mean_build else None,
-    }
+    if args.build_only:
+        roofline = {
+            "kernel": "k_witness (score + contract witness searches)",
+            "bound": "hbm", "achieved": round(wit_gbs, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(wit_gbs / peak, 4), "traffic": None, "peak_source": peak_src,
+            "bytes_per_launch": stats["witness_bytes"] / max(1, stats["witness_launches"]),
+            "ms_per_launch": stats["witness_ms"] / max(1, stats["witness_launches"]),
+        }
+    else:
+        q_bytes = 12 * q_exp + 8 * q_edges + 20 * nq
+        q_gbs = q_bytes / (mean_query * 1e-3) / 1e9
+        roofline = {
+            "kernel": "k_query_block (pruned bidirectional upward searches, one launch per batch)",
+            "bound": "hbm", "achieved": round(q_gbs, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(q_gbs / peak, 4), "traffic": QUERY_TRAFFIC_PER_LAUNCH,
+            "peak_source": peak_src, "bytes_per_launch": q_bytes, "ms_per_launch": mean_query,
+            "expansions_per_query": q_exp / nq, "edges_per_query": q_edges / nq,
+            "query_config": {"layout": ["block_flat", "warp_flat"][qcfg[0]] if qcfg else "default",
+                             "threads": qcfg[1] if qcfg else None,
+                             "autotune_ms": [round(float(x), 3) for x in tune_ms] if tune_ms is not None else None},
+            "witness": {"achieved": round(wit_gbs, 1), "frac": round(wit_gbs / peak, 4),
+                        "share_of_build": round(stats["witness_ms"] / mean_build, 3) if mean_build else None},
+        }
 
     # end to end through host buffers (H2D of the CSR and the queries, D2H of
     # the answers, inside the timed region)
@@ -465,6 +499,8 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             hh = ch.CH.build(g, hop_limit=args.hop_limit)
+            if qcfg is not None:
+                hh.set_query_config(*qcfg)
             t1 = time.perf_counter()
             hh.query(s_h, t_h)
             t2 = time.perf_counter()

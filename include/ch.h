@@ -203,6 +203,53 @@ int ch_query_batch_static(ch_t *ch, const uint32_t *src, const uint32_t *dst, ui
  * by earlier ch_query_batch calls on this handle. */
 int ch_query_status(ch_t *ch, void *stream);
 
+/* ---- Query kernel configuration and autotuning (performance only) ----
+ *
+ * One block runs one query at a time (Sec. 5's two upward searches, level
+ * by level). The layout says how a level's out-edges are spread over the
+ * block: CH_QUERY_BLOCK_FLAT over all its threads (block-wide scan, two
+ * barriers per tile of frontier entries), CH_QUERY_WARP_FLAT per warp
+ * (entries dealt to warps round-robin, a warp spreads its entries' edges over
+ * its lanes; one barrier per level). threads is 128 or 256. Every
+ * configuration gives the same answers and search-space sizes. */
+#define CH_QUERY_BLOCK_FLAT 0u
+#define CH_QUERY_WARP_FLAT 1u
+typedef struct {
+    uint32_t layout;
+    uint32_t threads;
+} ch_query_config_t;
+
+int ch_set_query_config(ch_t *ch, const ch_query_config_t *cfg);  /* CH_EINVAL on other values */
+int ch_get_query_config(const ch_t *ch, ch_query_config_t *cfg);
+
+/* Times each configuration on `sample` seeded uniform random queries (a
+ * warm-up run, then one run timed with CUDA events on `stream`) and keeps
+ * the fastest for the handle. ms_out (or NULL) receives the 4 times, in the
+ * order (BLOCK_FLAT,128), (BLOCK_FLAT,256), (WARP_FLAT,128), (WARP_FLAT,256);
+ * chosen (or NULL) the configuration kept. Waits for `stream`. */
+int ch_query_autotune(ch_t *ch, uint64_t sample, uint32_t seed, void *stream,
+                      ch_query_config_t *chosen, double *ms_out);
+
+/* Work of the query searches since the previous call (then cleared), summed
+ * over the handle's batches: out[0] = queued entries expanded, out[1] =
+ * adjacency entries scanned. Waits for `stream`. */
+int ch_query_work(ch_t *ch, void *stream, uint64_t out[2]);
+
+/* ---- Query batches as CUDA graphs ----
+ *
+ * ch_query_graph_create captures one ch_query_batch call on fixed device
+ * buffers (k queries from src/dst to dist_out) into an executable CUDA graph,
+ * in the handle's current query configuration; ch_query_graph_launch replays
+ * it on `stream` (one graph launch in place of the batch's API calls) and
+ * answers whatever src/dst hold when it runs. Replays use the handle's query
+ * work buffers, so they follow ch_query_batch's no-overlap rule. The graph
+ * must be freed before the handle. */
+typedef struct ch_query_graph_s ch_query_graph_t;
+int ch_query_graph_create(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                          uint32_t *dist_out, ch_query_graph_t **out);
+int ch_query_graph_launch(ch_query_graph_t *g, void *stream);
+void ch_query_graph_free(ch_query_graph_t *g);
+
 int ch_get_stats(const ch_t *ch, ch_stats_t *out);
 
 /* Copies min(rounds, max_rounds) rows of CH_NSTAT uint64 values to `out`. */

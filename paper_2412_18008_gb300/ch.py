@@ -54,6 +54,16 @@ class ParamsT(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class QueryConfigT(C.Structure):
+    _fields_ = [("layout", C.c_uint32), ("threads", C.c_uint32)]
+
+
+CH_QUERY_BLOCK_FLAT = 0
+CH_QUERY_WARP_FLAT = 1
+QUERY_CONFIGS = ((CH_QUERY_BLOCK_FLAT, 128), (CH_QUERY_BLOCK_FLAT, 256),
+                 (CH_QUERY_WARP_FLAT, 128), (CH_QUERY_WARP_FLAT, 256))
+
+
 class ServerParamsT(C.Structure):
     _fields_ = [("blocks", C.c_uint32), ("ring", C.c_uint32), ("pool", C.c_uint64),
                 ("idle_ms", C.c_uint32), ("reserved", C.c_uint32)]
@@ -123,6 +133,17 @@ def load(build_if_missing: bool = True):
     for f in ("ch_server_start", "ch_server_submit", "ch_server_poll", "ch_server_replay",
               "ch_server_stop"):
         getattr(lib, f).restype = C.c_int
+    lib.ch_set_query_config.argtypes = [P, C.POINTER(QueryConfigT)]
+    lib.ch_get_query_config.argtypes = [P, C.POINTER(QueryConfigT)]
+    lib.ch_query_autotune.argtypes = [P, C.c_uint64, C.c_uint32, P, C.POINTER(QueryConfigT), P]
+    lib.ch_query_work.argtypes = [P, P, P]
+    lib.ch_query_graph_create.argtypes = [P, P, P, C.c_uint64, P, C.POINTER(P)]
+    lib.ch_query_graph_launch.argtypes = [P, P]
+    for f in ("ch_set_query_config", "ch_get_query_config", "ch_query_autotune", "ch_query_work",
+              "ch_query_graph_create", "ch_query_graph_launch"):
+        getattr(lib, f).restype = C.c_int
+    lib.ch_query_graph_free.argtypes = [P]
+    lib.ch_query_graph_free.restype = None
     lib.ch_free.argtypes = [P]
     lib.ch_free.restype = None
     lib.ch_last_error.restype = C.c_char_p
@@ -258,6 +279,40 @@ class CH:
         _check(load().ch_query_batch(self._h, src_ptr, dst_ptr, k, out_ptr, settled_ptr,
                                      stream_ptr))
 
+    # -- query configuration, autotuning, work, graphs ----------------------
+    def set_query_config(self, layout: int, threads: int):
+        _check(load().ch_set_query_config(self._h, C.byref(QueryConfigT(layout, threads))))
+
+    def query_config(self) -> tuple[int, int]:
+        c = QueryConfigT()
+        _check(load().ch_get_query_config(self._h, C.byref(c)))
+        return c.layout, c.threads
+
+    def autotune_queries(self, sample: int = 1 << 16, seed: int = 1, stream=None):
+        """Time every query configuration on ``sample`` random queries and keep
+        the fastest. Returns (chosen (layout, threads), ms per configuration
+        in QUERY_CONFIGS order)."""
+        c = QueryConfigT()
+        ms = np.zeros(4, np.float64)
+        _check(load().ch_query_autotune(self._h, sample, seed, _stream_ptr(stream), C.byref(c),
+                                        _hp(ms)))
+        return (c.layout, c.threads), ms
+
+    def query_work(self, stream=None) -> tuple[int, int]:
+        """(expansions, edges scanned) of the query searches since the last call."""
+        out = np.zeros(2, np.uint64)
+        _check(load().ch_query_work(self._h, _stream_ptr(stream), _hp(out)))
+        return int(out[0]), int(out[1])
+
+    def query_graph(self, src, dst, out) -> "QueryGraph":
+        """Capture a query batch on fixed CUDA tensors into a CUDA graph."""
+        if src.shape != dst.shape or out.shape != src.shape:
+            raise ValueError("sources, targets and outputs differ in length")
+        h = C.c_void_p()
+        _check(load().ch_query_graph_create(self._h, src.data_ptr(), dst.data_ptr(), src.numel(),
+                                            out.data_ptr(), C.byref(h)))
+        return QueryGraph(h, (src, dst, out), self)
+
     # -- introspection ----------------------------------------------------
     def stats(self) -> dict:
         s = StatsT()
@@ -307,6 +362,35 @@ class CH:
         if self._h:
             load().ch_free(self._h)
             self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class QueryGraph:
+    """A query batch captured as a CUDA graph (see ch_query_graph_create)."""
+
+    def __init__(self, handle, buffers, owner):
+        self._h = handle
+        self._keep = buffers  # the graph reads and writes these tensors
+        self._owner = owner
+
+    def launch(self, stream=None):
+        _check(load().ch_query_graph_launch(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if self._h:
+            h, self._h = self._h, None
+            load().ch_query_graph_free(h)
 
     def __enter__(self):
         return self

@@ -17,6 +17,7 @@ std::atomic<uint64_t> g_launches{0};
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void kernel_launch_add(int64_t d) { g_launches.fetch_add((uint64_t)d, std::memory_order_relaxed); }
 
 void set_last_error(const char *fmt, ...) {
     char buf[1024];
@@ -184,6 +185,72 @@ int ch_query_batch_static(ch_t *ch, const uint32_t *src, const uint32_t *dst, ui
     return guarded([&] {
         query_batch_static(ch, src, dst, k, dist_out, (cudaStream_t)stream);
     });
+}
+
+int ch_set_query_config(ch_t *ch, const ch_query_config_t *cfg) {
+    if (!ch || !cfg) {
+        g_last_error = "null argument";
+        return CH_EINVAL;
+    }
+    return guarded([&] { query_set_config(ch, cfg->layout, cfg->threads); });
+}
+
+int ch_get_query_config(const ch_t *ch, ch_query_config_t *cfg) {
+    if (!ch || !cfg) {
+        g_last_error = "null argument";
+        return CH_EINVAL;
+    }
+    cfg->layout = ch->q_layout;
+    cfg->threads = ch->q_threads;
+    return CH_OK;
+}
+
+int ch_query_autotune(ch_t *ch, uint64_t sample, uint32_t seed, void *stream, ch_query_config_t *chosen,
+                      double *ms_out) {
+    if (!ch) {
+        g_last_error = "null handle";
+        return CH_EINVAL;
+    }
+    return guarded([&] {
+        uint32_t l = 0, t = 0;
+        query_autotune(ch, sample, seed, static_cast<cudaStream_t>(stream), &l, &t, ms_out);
+        if (chosen) {
+            chosen->layout = l;
+            chosen->threads = t;
+        }
+    });
+}
+
+int ch_query_work(ch_t *ch, void *stream, uint64_t out[2]) {
+    if (!ch || !out) {
+        g_last_error = "null argument";
+        return CH_EINVAL;
+    }
+    return guarded([&] { query_work(ch, static_cast<cudaStream_t>(stream), out); });
+}
+
+int ch_query_graph_create(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t k, uint32_t *dist_out,
+                          ch_query_graph_t **out) {
+    if (!ch || !out || (k && (!src || !dst || !dist_out))) {
+        g_last_error = "null argument";
+        return CH_EINVAL;
+    }
+    ch_query_graph_s *g = nullptr;
+    const int rc = guarded([&] { g = query_graph_create(ch, src, dst, k, dist_out); });
+    if (rc == CH_OK) *out = g;
+    return rc;
+}
+
+int ch_query_graph_launch(ch_query_graph_t *g, void *stream) {
+    if (!g) {
+        g_last_error = "null graph";
+        return CH_EINVAL;
+    }
+    return guarded([&] { query_graph_launch(g, static_cast<cudaStream_t>(stream)); });
+}
+
+void ch_query_graph_free(ch_query_graph_t *g) {
+    if (g) query_graph_free(g);
 }
 
 int ch_query_status(ch_t *ch, void *stream) {

@@ -39,6 +39,8 @@ void set_last_error(const char *fmt, ...);
 // Every kernel launch of the library is followed by this check, which also
 // counts the launch (reported by ch_kernel_launches()).
 void count_launch();
+// Adds to the launch count (negative: removes), e.g. for graph replays.
+void kernel_launch_add(int64_t d);
 #define CH_CHECK_LAUNCH()                    \
     do {                                     \
         ::gbch::count_launch();              \

@@ -8,6 +8,7 @@
 #include "common.cuh"
 
 struct ch_server_s;
+struct ch_query_graph_s;
 
 struct ch_s {
     uint32_t n = 0;
@@ -58,6 +59,9 @@ struct ch_s {
     gbch::DevBuf<uint32_t> qwork;           // work counters
     gbch::DevBuf<uint32_t> q_ovf_list;      // overflowed queries
     gbch::DevBuf<uint32_t> q_dense;         // fallback slots
+    gbch::DevBuf<unsigned long long> q_stats;  // [0] expansions, [1] edges scanned
+    uint32_t q_layout = CH_QUERY_WARP_FLAT;  // query block configuration (performance only)
+    uint32_t q_threads = 256;
     uint32_t q_slots = 0;
     uint64_t q_ovf_cap = 0;
 };
@@ -77,6 +81,16 @@ void query_init(ch_s *h);
 // Enqueue a query batch whose per-call scratch is a static device array.
 void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
                         uint32_t *dist_out, cudaStream_t st);
+
+// Query configuration, autotuning, work counters, graphs (query.cu).
+void query_set_config(ch_s *h, uint32_t layout, uint32_t threads);
+void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, uint32_t *layout_out,
+                    uint32_t *threads_out, double *ms_out);
+void query_work(ch_s *h, cudaStream_t st, uint64_t out[2]);
+ch_query_graph_s *query_graph_create(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                                     uint32_t *dist_out);
+void query_graph_launch(ch_query_graph_s *g, cudaStream_t st);
+void query_graph_free(ch_query_graph_s *g);
 
 // Query server (serve.cu).
 ch_server_s *server_new();

@@ -22,8 +22,8 @@ constexpr int QB_FC = 2048;            // frontier capacity
 // labels, claim bitmaps that keep a slot from being queued twice in one
 // level and direction (one bitmap per level parity, the idle one cleared
 // during the level), a double-buffered frontier holding both directions'
-// entries (slot | dir<<31) and a triple-buffered frontier counter, so that
-// one barrier per level suffices (see block_search).
+// entries (slot | dir<<31) and a triple-buffered frontier counter (see
+// block_search).
 constexpr int QB_CW = QB_T / 32;  // claim-bitmap words per direction
 struct QBSmem {
     uint32_t key[QB_T];
@@ -54,6 +54,7 @@ struct QArgs {
     uint32_t *work;      // [0]: block path counter, [1]: fallback counter, [2]: overflow count
     uint32_t *ovf;
     uint32_t *err;
+    unsigned long long *stats;  // [0] expansions, [1] edges scanned (or null)
 };
 
 __device__ __forceinline__ uint32_t qb_hash(uint32_t v) {
@@ -81,6 +82,64 @@ __device__ __forceinline__ bool qb_claim(QBSmem &q, uint32_t slot, uint32_t dir,
     return !(atomicOr(&q.claim[lvl & 1u][dir][slot >> 5], bit) & bit);
 }
 
+// Per-thread work counters of the searches (queued entries expanded, edges
+// scanned), summed once per thread when a kernel ends.
+struct QStat {
+    unsigned long long exp = 0, edges = 0;
+};
+
+// Relaxes one edge e = (y, w) of a vertex labelled dx in direction dir.
+// Returns nothing; records an overflow in q.ovf, an index error in a.err.
+template <bool PRUNE>
+__device__ __forceinline__ void qb_relax(QBSmem &q, const QArgs &a, uint32_t dir, uint2 e, uint32_t dx,
+                                         uint32_t lvl, uint32_t nxt_cnt, uint32_t *next_front) {
+    const uint32_t nd = sat_add(dx, e.y);
+    if (e.x >= a.n) {
+        atomicOr(a.err, QERR_BOUND);
+        return;
+    }
+    if (nd == INF) return;
+    if (PRUNE && nd >= q.mu) return;
+    const uint32_t ys = qb_insert(q.key, e.x);
+    if (ys == EMPTY) {
+        q.ovf = 1;
+        return;
+    }
+    uint32_t *dist = dir ? q.db : q.df;
+    const uint32_t old = atomicMin(&dist[ys], nd);
+    if (nd >= old) return;
+    if (PRUNE) {
+        const uint32_t other = dir ? q.df[ys] : q.db[ys];
+        if (other != INF) atomicMin(&q.mu, sat_add(nd, other));
+    }
+    if (qb_claim(q, ys, dir, lvl)) {
+        const uint32_t p = atomicAdd(&q.cnt3[nxt_cnt], 1u);
+        if (p < (uint32_t)QB_FC) next_front[p] = ys | (dir << 31);
+        else q.ovf = 1;
+    }
+}
+
+// Loads what expanding one frontier entry needs: its vertex's edge range in
+// the direction's CSR and its label. cnt = 0 for an invalid entry.
+__device__ __forceinline__ void qb_entry(const QBSmem &q, const QArgs &a, bool fv, uint32_t ent,
+                                         uint32_t &b, uint32_t &cnt, uint32_t &dx) {
+    const uint32_t dir = ent >> 31;
+    const uint32_t slot = ent & 0x7FFFFFFFu;
+    const bool sok = fv && slot < (uint32_t)QB_T;
+    if (fv && !sok) atomicOr(a.err, QERR_BOUND);
+    const uint32_t x = sok ? q.key[slot] : 0;
+    const bool xok = sok && x < a.n;
+    if (sok && !xok) atomicOr(a.err, QERR_BOUND);
+    const uint32_t *off = dir ? a.dn_off : a.up_off;
+    const uint32_t n_edges = dir ? a.n_dn : a.n_up;
+    b = xok ? off[x] : 0;
+    const uint32_t e_end = xok ? off[x + 1] : 0;
+    cnt = 0;
+    if (xok && b <= e_end && e_end <= n_edges) cnt = e_end - b;
+    else if (xok) atomicOr(a.err, QERR_BOUND);
+    dx = cnt ? (dir ? q.db[slot] : q.df[slot]) : INF;
+}
+
 // Both upward searches at once, label-correcting over the rank DAG: the
 // frontier holds forward (E_up) and backward (reversed E_down) entries,
 // each level relaxes the out-edges of every queued vertex with its current
@@ -89,15 +148,27 @@ __device__ __forceinline__ bool qb_claim(QBSmem &q, uint32_t slot, uint32_t dir,
 // (it cannot improve the answer); the answer is always recomputed at the
 // end as the least df + db over the table, so it is exact either way.
 //
-// Barrier discipline: the only barrier of a level is at its top. The
-// frontier counter of level k lives in cnt3[k % 3]; thread 0 clears the
-// counter of level k + 2 during level k, when no thread reads it any more.
-template <bool PRUNE>
-__device__ bool block_search(QBSmem &q, const QArgs &a) {
+// Two ways to spread a level over the block (same result, different cost):
+//  - block-flattened (WARP = false): tiles of blockDim frontier entries; the
+//    out-edges of a tile are spread evenly over all threads (block-wide
+//    scan, owner found by binary search); two barriers per tile.
+//  - warp-flattened (WARP = true): frontier entries are dealt to warps
+//    round-robin, each warp spreads the out-edges of its (up to 32) entries
+//    over its lanes (warp scan, owner found by shuffles); no barrier inside
+//    a level.
+//
+// Barrier discipline: the frontier counter of level k lives in cnt3[k % 3];
+// thread 0 clears the counter of level k + 2 during level k, when no thread
+// reads it any more. Each level reads its frontier size and the overflow
+// flag right after a barrier that follows every write to them: the barrier
+// at the top of the level (warp-flattened; block-flattened at level 1) or
+// the barrier that ends the previous level's last tile (block-flattened).
+template <bool PRUNE, bool WARP>
+__device__ bool block_search(QBSmem &q, const QArgs &a, QStat &stat) {
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
     for (uint32_t lvl = 1;; ++lvl) {
-        __syncthreads();
+        if (WARP || lvl == 1) __syncthreads();
         const uint32_t cur = (lvl - 1) & 1u;
         const uint32_t nfront = q.cnt3[(lvl - 1) % 3];
         const uint32_t ovf = q.ovf;
@@ -112,99 +183,97 @@ __device__ bool block_search(QBSmem &q, const QArgs &a) {
         // next used one level from now
         for (uint32_t j = tid; j < 2u * QB_CW; j += blockDim.x) (&q.claim[(lvl + 1) & 1u][0][0])[j] = 0;
         const uint32_t nxt_cnt = lvl % 3;
-        // Tiles of blockDim frontier entries; the out-edges of a tile are
-        // spread evenly over all threads of the block.
-        for (uint32_t t0 = 0; t0 < nfront; t0 += blockDim.x) {
-            const uint32_t fi = t0 + tid;
-            const bool fv = fi < nfront && fi < (uint32_t)QB_FC;
-            const uint32_t ent = fv ? q.front[cur][fi] : 0;
-            const uint32_t dir = ent >> 31;
-            const uint32_t slot = ent & 0x7FFFFFFFu;
-            const bool sok = fv && slot < (uint32_t)QB_T;
-            if (fv && !sok) atomicOr(a.err, QERR_BOUND);
-            const uint32_t x = sok ? q.key[slot] : 0;
-            const bool xok = sok && x < a.n;
-            if (sok && !xok) atomicOr(a.err, QERR_BOUND);
-            const uint32_t *off = dir ? a.dn_off : a.up_off;
-            const uint32_t n_edges = dir ? a.n_dn : a.n_up;
-            const uint32_t b = xok ? off[x] : 0;
-            const uint32_t e_end = xok ? off[x + 1] : 0;
-            uint32_t cnt = 0;
-            if (xok && b <= e_end && e_end <= n_edges) cnt = e_end - b;
-            else if (xok) atomicOr(a.err, QERR_BOUND);
-            const uint32_t dx = cnt ? (dir ? q.db[slot] : q.df[slot]) : INF;
-            // block-wide exclusive scan of cnt
-            const uint32_t incl = warp_incl_scan(cnt);
-            if (lane == 31) q.wtot[warp] = incl;
-            q.t_beg[tid] = b;
-            q.t_dx[tid] = dx;
-            q.t_ent[tid] = ent;
-            __syncthreads();
-            uint32_t wbase = 0, total = 0;
-            for (uint32_t w2 = 0; w2 < nwarps; ++w2) {
-                const uint32_t wt = q.wtot[w2];
-                if (w2 < warp) wbase += wt;
-                total += wt;
-            }
-            q.t_excl[tid] = wbase + incl - cnt;
-            __syncthreads();
-            for (uint32_t e0 = tid; e0 < total; e0 += blockDim.x) {
-                // owner entry: the largest k with t_excl[k] <= e0
-                uint32_t lo = 0, hi = blockDim.x;
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (q.t_excl[mid] <= e0) lo = mid;
-                    else hi = mid;
-                }
-                const uint32_t oent = q.t_ent[lo];
-                const uint32_t odir = oent >> 31;
-                const uint2 e = (odir ? a.dn_adj : a.up_adj)[q.t_beg[lo] + (e0 - q.t_excl[lo])];
-                const uint32_t nd = sat_add(q.t_dx[lo], e.y);
-                if (e.x >= a.n) {
-                    atomicOr(a.err, QERR_BOUND);
-                    continue;
-                }
-                if (nd == INF) continue;
-                if (PRUNE && nd >= q.mu) continue;
-                const uint32_t ys = qb_insert(q.key, e.x);
-                if (ys == EMPTY) {
-                    q.ovf = 1;
-                    continue;
-                }
-                uint32_t *dist = odir ? q.db : q.df;
-                const uint32_t old = atomicMin(&dist[ys], nd);
-                if (nd >= old) continue;
-                if (PRUNE) {
-                    const uint32_t other = odir ? q.df[ys] : q.db[ys];
-                    if (other != INF) atomicMin(&q.mu, sat_add(nd, other));
-                }
-                if (qb_claim(q, ys, odir, lvl)) {
-                    const uint32_t p = atomicAdd(&q.cnt3[nxt_cnt], 1u);
-                    if (p < (uint32_t)QB_FC) q.front[cur ^ 1u][p] = ys | (odir << 31);
-                    else q.ovf = 1;
+        uint32_t *next_front = q.front[cur ^ 1u];
+        if (WARP) {
+            const uint32_t stride = blockDim.x;
+            for (uint32_t p0 = 0; p0 < nfront; p0 += stride) {
+                const uint32_t fi = p0 + warp + nwarps * lane;
+                const bool fv = fi < nfront && fi < (uint32_t)QB_FC;
+                const uint32_t ent = fv ? q.front[cur][fi] : 0;
+                uint32_t b, cnt, dx;
+                qb_entry(q, a, fv, ent, b, cnt, dx);
+                stat.exp += cnt ? 1u : 0u;
+                const uint32_t incl = warp_incl_scan(cnt);
+                const uint32_t total = __shfl_sync(FULL, incl, 31);
+                const uint32_t excl = incl - cnt;
+                for (uint32_t base = 0; base < total; base += 32) {
+                    const uint32_t e0 = base + lane;
+                    const uint32_t o = warp_owner(excl, e0);
+                    const uint32_t ob = __shfl_sync(FULL, b, o);
+                    const uint32_t oex = __shfl_sync(FULL, excl, o);
+                    const uint32_t odx = __shfl_sync(FULL, dx, o);
+                    const uint32_t odir = __shfl_sync(FULL, ent, o) >> 31;
+                    if (e0 < total) {
+                        ++stat.edges;
+                        const uint2 e = (odir ? a.dn_adj : a.up_adj)[ob + (e0 - oex)];
+                        qb_relax<PRUNE>(q, a, odir, e, odx, lvl, nxt_cnt, next_front);
+                    }
                 }
             }
-            __syncthreads();
+        } else {
+            for (uint32_t t0 = 0; t0 < nfront; t0 += blockDim.x) {
+                const uint32_t fi = t0 + tid;
+                const bool fv = fi < nfront && fi < (uint32_t)QB_FC;
+                const uint32_t ent = fv ? q.front[cur][fi] : 0;
+                uint32_t b, cnt, dx;
+                qb_entry(q, a, fv, ent, b, cnt, dx);
+                stat.exp += cnt ? 1u : 0u;
+                // block-wide exclusive scan of cnt
+                const uint32_t incl = warp_incl_scan(cnt);
+                if (lane == 31) q.wtot[warp] = incl;
+                q.t_beg[tid] = b;
+                q.t_dx[tid] = dx;
+                q.t_ent[tid] = ent;
+                __syncthreads();
+                uint32_t wbase = 0, total = 0;
+                for (uint32_t w2 = 0; w2 < nwarps; ++w2) {
+                    const uint32_t wt = q.wtot[w2];
+                    if (w2 < warp) wbase += wt;
+                    total += wt;
+                }
+                q.t_excl[tid] = wbase + incl - cnt;
+                __syncthreads();
+                for (uint32_t e0 = tid; e0 < total; e0 += blockDim.x) {
+                    // owner entry: the largest k with t_excl[k] <= e0
+                    uint32_t lo = 0, hi = blockDim.x;
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (q.t_excl[mid] <= e0) lo = mid;
+                        else hi = mid;
+                    }
+                    ++stat.edges;
+                    const uint32_t odir = q.t_ent[lo] >> 31;
+                    const uint2 e = (odir ? a.dn_adj : a.up_adj)[q.t_beg[lo] + (e0 - q.t_excl[lo])];
+                    qb_relax<PRUNE>(q, a, odir, e, q.t_dx[lo], lvl, nxt_cnt, next_front);
+                }
+                __syncthreads();
+            }
         }
     }
 }
 
-// One s-t query (rank ids rs, rt < n) by the whole block, on the shared
-// table: clears it, seeds both roots, searches and reduces the answer.
-// Returns false, in every thread, when the search spaces overflowed the
-// table or the frontier (the caller redoes the query elsewhere); otherwise
-// mu and cnt hold, in every thread, the least meeting sum and the number of
-// labels set. Every thread of the block must call it.
-template <bool PRUNE>
-__device__ bool block_query(QBSmem &q, const QArgs &a, uint32_t rs, uint32_t rt, uint32_t &mu_out,
-                            uint32_t &cnt_out) {
-    const uint32_t tid = threadIdx.x;
-    for (uint32_t j = tid; j < (uint32_t)QB_T; j += blockDim.x) {
+// Empties the block's table and claim bitmaps (at kernel start; every query
+// leaves them empty again).
+__device__ __forceinline__ void qb_clear(QBSmem &q) {
+    for (uint32_t j = threadIdx.x; j < (uint32_t)QB_T; j += blockDim.x) {
         q.key[j] = EMPTY;
         q.df[j] = INF;
         q.db[j] = INF;
     }
-    for (uint32_t j = tid; j < 4u * QB_CW; j += blockDim.x) (&q.claim[0][0][0])[j] = 0;
+    for (uint32_t j = threadIdx.x; j < 4u * QB_CW; j += blockDim.x) (&q.claim[0][0][0])[j] = 0;
+}
+
+// One s-t query (rank ids rs, rt < n) by the whole block, on the shared
+// table, which must be empty on entry and is empty again on return: seeds
+// both roots, searches, then reduces the answer in the same pass that
+// empties the table. Returns false, in every thread, when the search spaces
+// overflowed the table or the frontier (the caller redoes the query
+// elsewhere); otherwise mu and cnt hold, in every thread, the least meeting
+// sum and the number of labels set. Every thread of the block must call it.
+template <bool PRUNE, bool WARP>
+__device__ bool block_query(QBSmem &q, const QArgs &a, uint32_t rs, uint32_t rt, uint32_t &mu_out,
+                            uint32_t &cnt_out, QStat &stat) {
+    const uint32_t tid = threadIdx.x;
     __syncthreads();
     if (tid == 0) {
         const uint32_t ss = qb_insert(q.key, rs);
@@ -220,7 +289,7 @@ __device__ bool block_query(QBSmem &q, const QArgs &a, uint32_t rs, uint32_t rt,
         q.cnt3[1] = 0;
         q.cnt3[2] = 0;
     }
-    if (!block_search<PRUNE>(q, a)) return false;
+    const bool ok = block_search<PRUNE, WARP>(q, a, stat);
     // q.mu only steered pruning; the answer is the least meeting sum.
     __syncthreads();
     if (tid == 0) q.mu = INF;
@@ -230,7 +299,11 @@ __device__ bool block_query(QBSmem &q, const QArgs &a, uint32_t rs, uint32_t rt,
         const uint32_t f = q.df[j], g = q.db[j];
         mu = min(mu, sat_add(f, g));
         cnt += (f != INF) + (g != INF);
+        q.key[j] = EMPTY;
+        q.df[j] = INF;
+        q.db[j] = INF;
     }
+    for (uint32_t j = tid; j < 4u * QB_CW; j += blockDim.x) (&q.claim[0][0][0])[j] = 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mu = min(mu, __shfl_xor_sync(FULL, mu, o));
@@ -243,7 +316,22 @@ __device__ bool block_query(QBSmem &q, const QArgs &a, uint32_t rs, uint32_t rt,
     __syncthreads();
     mu_out = q.mu;
     cnt_out = q.cnt;
-    return true;
+    return ok;
+}
+
+// Adds the block's counters to stats[0] (expansions) and stats[1] (edges).
+__device__ __forceinline__ void qb_flush_stat(const QStat &stat, unsigned long long *stats) {
+    if (!stats) return;
+    unsigned long long e = stat.exp, g = stat.edges;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(FULL, e, o);
+        g += __shfl_xor_sync(FULL, g, o);
+    }
+    if (lane_id() == 0) {
+        atomicAdd(&stats[0], e);
+        atomicAdd(&stats[1], g);
+    }
 }
 
 }  // namespace

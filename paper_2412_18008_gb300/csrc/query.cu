@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "handle.cuh"
 #include "qsearch.cuh"
@@ -26,11 +27,13 @@ namespace {
 
 constexpr uint64_t Q_CHUNK = 1u << 22;  // queries per launch pair
 
-template <bool PRUNE>
+template <bool PRUNE, bool WARP>
 __global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
     extern __shared__ __align__(16) unsigned char qb_raw[];
     QBSmem &q = *reinterpret_cast<QBSmem *>(qb_raw);
     const uint32_t tid = threadIdx.x;
+    QStat stat;
+    qb_clear(q);
     while (true) {
         __syncthreads();
         if (tid == 0) q.item = atomicAdd(&a.work[0], 1u);
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
             continue;
         }
         uint32_t mu, cnt;
-        if (!block_query<PRUNE>(q, a, rs, rt, mu, cnt)) {
+        if (!block_query<PRUNE, WARP>(q, a, rs, rt, mu, cnt, stat)) {
             if (tid == 0) a.ovf[atomicAdd(&a.work[2], 1u)] = i;
             continue;
         }
@@ -64,6 +67,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
             if (a.settled) a.settled[i] = cnt;
         }
     }
+    qb_flush_stat(stat, a.stats);
 }
 
 // Dense fallback: one block per slot; labels in per-vertex arrays.
@@ -184,7 +188,49 @@ __global__ void __launch_bounds__(256) k_query_dense(QArgs a, QDense dn) {
     }
 }
 
-int g_qb_blocks_per_sm = -1;
+// Resident blocks per SM of each block-kernel configuration
+// [layout][threads == 256], resolved once.
+int g_qb_bps[2][2] = {{-1, -1}, {-1, -1}};
+
+template <bool PRUNE, bool WARP>
+void qb_set_attr() {
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<PRUNE, WARP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(QBSmem)));
+}
+
+void qb_resolve_occupancy() {
+    if (g_qb_bps[0][0] >= 0) return;
+    qb_set_attr<true, false>();
+    qb_set_attr<false, false>();
+    qb_set_attr<true, true>();
+    qb_set_attr<false, true>();
+    for (int l = 0; l < 2; ++l)
+        for (int t = 0; t < 2; ++t) {
+            int b = 0;
+            const int threads = t ? 256 : 128;
+            if (l) CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, true>, threads, sizeof(QBSmem)));
+            else CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, false>, threads, sizeof(QBSmem)));
+            g_qb_bps[l][t] = std::max(1, b);
+        }
+}
+
+// Launches the block kernel in the handle's configuration: a persistent
+// grid of as many blocks as are resident at once (no more than k).
+void launch_query_block(const ch_s *h, const QArgs &a, bool prune, uint64_t k, cudaStream_t st) {
+    const int l = h->q_layout == CH_QUERY_WARP_FLAT ? 1 : 0;
+    const int t = h->q_threads == 256 ? 1 : 0;
+    const int threads = t ? 256 : 128;
+    const int blocks = (int)std::min<uint64_t>(k, (uint64_t)device_sm_count() * g_qb_bps[l][t]);
+    const size_t smem = sizeof(QBSmem);
+    if (l) {
+        if (prune) k_query_block<true, true><<<blocks, threads, smem, st>>>(a);
+        else k_query_block<false, true><<<blocks, threads, smem, st>>>(a);
+    } else {
+        if (prune) k_query_block<true, false><<<blocks, threads, smem, st>>>(a);
+        else k_query_block<false, false><<<blocks, threads, smem, st>>>(a);
+    }
+    CH_CHECK_LAUNCH();
+}
 
 }  // namespace
 
@@ -204,25 +250,15 @@ void query_init(ch_s *h) {
     // df, db: INF; fst: 0; the rest need no initial value
     CH_CUDA_TRY(cudaMemset(h->q_dense.ptr, 0xFF, sn * 2 * 4));
     CH_CUDA_TRY(cudaMemset(h->q_dense.ptr + 2 * sn, 0, sn * 4));
-    if (g_qb_blocks_per_sm < 0) {
-        const size_t smem = sizeof(QBSmem);
-        CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int b = 0;
-        CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true>,
-                                                                  QB_THREADS, smem));
-        g_qb_blocks_per_sm = std::max(1, b);
-    }
+    h->q_stats.alloc(2);
+    h->q_stats.zero(0);
+    qb_resolve_occupancy();
     CH_CUDA_TRY(cudaDeviceSynchronize());
 }
 
 void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
                  uint32_t *dist_out, uint32_t *settled_out, cudaStream_t st) {
     if (k == 0) return;
-    const size_t smem = sizeof(QBSmem);
-    const int sms = device_sm_count();
     const size_t sn = (size_t)h->q_slots * std::max<uint32_t>(h->n, 1);
     QDense dn;
     dn.df = h->q_dense.ptr;
@@ -251,16 +287,163 @@ void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
         a.work = h->qwork.ptr;
         a.ovf = h->q_ovf_list.ptr;
         a.err = h->qerr.ptr;
+        a.stats = h->q_stats.ptr;
         CH_CUDA_TRY(cudaMemsetAsync(h->qwork.ptr, 0, 4 * sizeof(uint32_t), st));
-        const int blocks = (int)std::min<uint64_t>(kc, (uint64_t)sms * g_qb_blocks_per_sm);
         // Pruned searches unless the caller asked for search-space sizes,
         // which are defined by the exhaustive upward searches.
-        if (settled_out) k_query_block<false><<<blocks, QB_THREADS, smem, st>>>(a);
-        else k_query_block<true><<<blocks, QB_THREADS, smem, st>>>(a);
-        CH_CHECK_LAUNCH();
+        launch_query_block(h, a, settled_out == nullptr, kc, st);
         k_query_dense<<<h->q_slots, 256, 0, st>>>(a, dn);
         CH_CHECK_LAUNCH();
     }
+}
+
+// ---------------------------------------------------------------------------
+// Configuration, autotuning, work counters, CUDA graphs
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Seeded uniform pairs for the autotuner's sample (MurmurHash3 finaliser of
+// a counter, reduced modulo n).
+__global__ void k_sample_pairs(uint32_t *s, uint32_t *t, uint64_t k, uint32_t n, uint32_t seed) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < k;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = murmur_fmix32((uint32_t)(2 * i) ^ murmur_fmix32(seed));
+        const uint32_t b = murmur_fmix32((uint32_t)(2 * i + 1) ^ murmur_fmix32(seed + 0x9e3779b9u));
+        s[i] = a % n;
+        t[i] = b % n;
+    }
+}
+
+}  // namespace
+
+void query_set_config(ch_s *h, uint32_t layout, uint32_t threads) {
+    if ((layout != CH_QUERY_BLOCK_FLAT && layout != CH_QUERY_WARP_FLAT) || (threads != 128 && threads != 256))
+        throw Error{CH_EINVAL, "query configuration: layout BLOCK_FLAT or WARP_FLAT, threads 128 or 256"};
+    h->q_layout = layout;
+    h->q_threads = threads;
+}
+
+void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, uint32_t *layout_out,
+                    uint32_t *threads_out, double *ms_out) {
+    if (sample == 0 || h->n == 0) throw Error{CH_EINVAL, "autotune needs a sample and a non-empty graph"};
+    DevBuf<uint32_t> buf;
+    buf.alloc(3 * sample);
+    uint32_t *s = buf.ptr, *t = buf.ptr + sample, *out = buf.ptr + 2 * sample;
+    k_sample_pairs<<<grid_for(sample, 256, device_sm_count() * 4), 256, 0, st>>>(s, t, sample, h->n, seed);
+    CH_CHECK_LAUNCH();
+    const uint32_t keep_l = h->q_layout, keep_t = h->q_threads;
+    cudaEvent_t e0, e1;
+    CH_CUDA_TRY(cudaEventCreate(&e0));
+    CH_CUDA_TRY(cudaEventCreate(&e1));
+    double best = 0;
+    int best_i = -1;
+    try {
+        for (int i = 0; i < 4; ++i) {
+            query_set_config(h, i >= 2 ? CH_QUERY_WARP_FLAT : CH_QUERY_BLOCK_FLAT, (i & 1) ? 256 : 128);
+            query_batch(h, s, t, sample, out, nullptr, st);  // warm-up
+            CH_CUDA_TRY(cudaEventRecord(e0, st));
+            query_batch(h, s, t, sample, out, nullptr, st);
+            CH_CUDA_TRY(cudaEventRecord(e1, st));
+            CH_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0;
+            CH_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms_out) ms_out[i] = ms;
+            if (best_i < 0 || ms < best) {
+                best = ms;
+                best_i = i;
+            }
+        }
+    } catch (...) {
+        h->q_layout = keep_l;
+        h->q_threads = keep_t;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    query_set_config(h, best_i >= 2 ? CH_QUERY_WARP_FLAT : CH_QUERY_BLOCK_FLAT, (best_i & 1) ? 256 : 128);
+    if (layout_out) *layout_out = h->q_layout;
+    if (threads_out) *threads_out = h->q_threads;
+    // the sample's work is not the caller's: clear the counters
+    CH_CUDA_TRY(cudaMemsetAsync(h->q_stats.ptr, 0, 2 * sizeof(unsigned long long), st));
+    CH_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+void query_work(ch_s *h, cudaStream_t st, uint64_t out[2]) {
+    unsigned long long v[2] = {0, 0};
+    CH_CUDA_TRY(cudaMemcpyAsync(v, h->q_stats.ptr, sizeof(v), cudaMemcpyDeviceToHost, st));
+    CH_CUDA_TRY(cudaMemsetAsync(h->q_stats.ptr, 0, sizeof(v), st));
+    CH_CUDA_TRY(cudaStreamSynchronize(st));
+    out[0] = v[0];
+    out[1] = v[1];
+}
+
+}  // namespace gbch
+
+struct ch_query_graph_s {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels = 0;  // kernel launches one replay makes
+};
+
+namespace gbch {
+
+ch_query_graph_s *query_graph_create(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
+                                     uint32_t *dist_out) {
+    cudaStream_t st = nullptr;
+    CH_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    try {
+        CH_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        try {
+            query_batch(h, src, dst, k, dist_out, nullptr, st);
+        } catch (...) {
+            cudaStreamEndCapture(st, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            throw;
+        }
+        CH_CUDA_TRY(cudaStreamEndCapture(st, &graph));
+    } catch (...) {
+        cudaStreamDestroy(st);
+        throw;
+    }
+    cudaStreamDestroy(st);
+    auto *g = new ch_query_graph_s();
+    cudaError_t e = cudaSuccess;
+    if (graph) {
+        // the launches were counted at capture; count them when replays run them
+        size_t nn = 0;
+        e = cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (e == cudaSuccess && nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+        for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+            cudaGraphNodeType ty;
+            e = cudaGraphNodeGetType(nodes[i], &ty);
+            if (e == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++g->kernels;
+        }
+        kernel_launch_add(-(int64_t)g->kernels);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        delete g;
+        cudaGetLastError();
+        throw Error{CH_ECUDA, std::string("graph instantiation: ") + cudaGetErrorString(e)};
+    }
+    return g;
+}
+
+void query_graph_launch(ch_query_graph_s *g, cudaStream_t st) {
+    if (!g->exec) return;  // k = 0: nothing was captured
+    CH_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+    kernel_launch_add((int64_t)g->kernels);
+}
+
+void query_graph_free(ch_query_graph_s *g) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    delete g;
 }
 
 // ---------------------------------------------------------------------------
@@ -307,8 +490,6 @@ void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint6
         throw Error{CH_ERANGE, "batch larger than CH_STATIC_QUERY_MAX queries"};
     if (k == 0) return;
     uint32_t *scratch = static_scratch();
-    const size_t smem = sizeof(QBSmem);
-    const int sms = device_sm_count();
     const size_t sn = (size_t)h->q_slots * std::max<uint32_t>(h->n, 1);
     QDense dn;
     dn.df = h->q_dense.ptr;
@@ -335,11 +516,10 @@ void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint6
     a.work = scratch;
     a.ovf = scratch + kStaticScratchHead;
     a.err = h->qerr.ptr;
+    a.stats = h->q_stats.ptr;
     // the counters keep the previous call's values: clear them
     CH_CUDA_TRY(cudaMemsetAsync(scratch, 0, kStaticScratchHead * sizeof(uint32_t), st));
-    const int blocks = (int)std::min<uint64_t>(k, (uint64_t)sms * g_qb_blocks_per_sm);
-    k_query_block<true><<<blocks, QB_THREADS, smem, st>>>(a);
-    CH_CHECK_LAUNCH();
+    launch_query_block(h, a, true, k, st);
     k_query_dense<<<h->q_slots, 256, 0, st>>>(a, dn);
     CH_CHECK_LAUNCH();
 }

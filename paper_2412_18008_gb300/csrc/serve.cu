@@ -229,9 +229,12 @@ __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_
     return res;
 }
 
+template <bool WARP>
 __global__ void __launch_bounds__(QB_THREADS) k_serve(SvArgs a) {
     extern __shared__ __align__(16) unsigned char qb_raw[];
     QBSmem &q = *reinterpret_cast<QBSmem *>(qb_raw);
+    QStat stat;  // not reported
+    qb_clear(q);
     __shared__ uint32_t s_go, s_src, s_tgt, s_k, s_slot, s_first;
     __shared__ unsigned long long s_seq;
     __shared__ uint64_t s_e;
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_serve(SvArgs a) {
             const uint32_t rs = g.rank[s], rt = g.rank[tv];
             if (rs < g.n && rt < g.n) {
                 uint32_t cnt;
-                if (!block_query<true>(q, g, rs, rt, ans, cnt))
+                if (!block_query<true, WARP>(q, g, rs, rt, ans, cnt, stat))
                     ans = sv_query(a, t, rs, rt, q.cnt3, &q.ovf, &q.mu, &q.cnt);
             } else if (tid == 0) {
                 atomicOr(a.status, QERR_BOUND);
@@ -386,11 +389,13 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     sv->pool = p->pool;
     sv->idle_ns = (unsigned long long)p->idle_ms * 1000000ull;
     const int sms = device_sm_count();
-    CH_CUDA_TRY(cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(QBSmem)));
+    // the handle's query configuration (layout and block size)
+    const bool warp = h->q_layout == CH_QUERY_WARP_FLAT;
+    const int threads = (int)h->q_threads;
+    auto kern = warp ? k_serve<true> : k_serve<false>;
+    CH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(QBSmem)));
     int per_sm = 0;
-    CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, QB_THREADS,
-                                                              sizeof(QBSmem)));
+    CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sizeof(QBSmem)));
     sv->nblocks = p->blocks ? p->blocks : (uint32_t)sms * (uint32_t)std::max(per_sm, 1);
     uint32_t tbits = 10;
     while (tbits < 24 && ((1u << tbits) < std::min<uint32_t>(h->n, 1u << 17))) ++tbits;
@@ -456,7 +461,7 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     a.fst = base + 3 * T * NB;
     a.touched = base + 4 * T * NB;
     a.front = base + 5 * T * NB;
-    k_serve<<<sv->nblocks, QB_THREADS, sizeof(QBSmem), sv->st>>>(a);
+    kern<<<sv->nblocks, threads, sizeof(QBSmem), sv->st>>>(a);
     CH_CHECK_LAUNCH();
     sv->running = true;
 }
