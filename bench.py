@@ -485,6 +485,7 @@ def main():
             "expansions_per_query": q_exp / nq, "edges_per_query": q_edges / nq,
             "query_config": {"layout": ["block_flat", "warp_flat"][qcfg[0]] if qcfg else "default",
                              "threads": qcfg[1] if qcfg else None,
+                             "small_tables_first": bool(qcfg[2]) if qcfg else None,
                              "autotune_ms": [round(float(x), 3) for x in tune_ms] if tune_ms is not None else None},
             "witness": {"achieved": round(wit_gbs, 1), "frac": round(wit_gbs / peak, 4),
                         "share_of_build": round(stats["witness_ms"] / mean_build, 3) if mean_build else None},

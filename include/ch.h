@@ -206,17 +206,23 @@ int ch_query_status(ch_t *ch, void *stream);
 /* ---- Query kernel configuration and autotuning (performance only) ----
  *
  * One block runs one query at a time (Sec. 5's two upward searches, level
- * by level). The layout says how a level's out-edges are spread over the
- * block: CH_QUERY_BLOCK_FLAT over all its threads (block-wide scan, two
- * barriers per tile of frontier entries), CH_QUERY_WARP_FLAT per warp
- * (entries dealt to warps round-robin, a warp spreads its entries' edges over
- * its lanes; one barrier per level). threads is 128 or 256. Every
- * configuration gives the same answers and search-space sizes. */
+ * by level), its labels in a shared-memory hash table. The layout says how a
+ * level's out-edges are spread over the block: CH_QUERY_BLOCK_FLAT over all
+ * its threads (block-wide scan, two barriers per tile of frontier entries),
+ * CH_QUERY_WARP_FLAT per warp (entries dealt to warps round-robin, a warp
+ * spreads its entries' edges over its lanes; one barrier per level).
+ * threads is 128 or 256. small_first = 1 runs a first pass on 2048-slot
+ * tables, which fit twice as many blocks per SM, and redoes only the
+ * queries that overflow them on 4096-slot tables; 0 uses 4096-slot tables
+ * only. Queries that overflow those go to a kernel with per-vertex label
+ * arrays. Every configuration gives the same answers and search-space
+ * sizes. */
 #define CH_QUERY_BLOCK_FLAT 0u
 #define CH_QUERY_WARP_FLAT 1u
 typedef struct {
     uint32_t layout;
     uint32_t threads;
+    uint32_t small_first;
 } ch_query_config_t;
 
 int ch_set_query_config(ch_t *ch, const ch_query_config_t *cfg);  /* CH_EINVAL on other values */
@@ -224,9 +230,10 @@ int ch_get_query_config(const ch_t *ch, ch_query_config_t *cfg);
 
 /* Times each configuration on `sample` seeded uniform random queries (a
  * warm-up run, then one run timed with CUDA events on `stream`) and keeps
- * the fastest for the handle. ms_out (or NULL) receives the 4 times, in the
- * order (BLOCK_FLAT,128), (BLOCK_FLAT,256), (WARP_FLAT,128), (WARP_FLAT,256);
- * chosen (or NULL) the configuration kept. Waits for `stream`. */
+ * the fastest for the handle. ms_out (or NULL) receives the 8 times, in the
+ * order index = 4 * small_first + 2 * (layout == WARP_FLAT) +
+ * (threads == 256); chosen (or NULL) the configuration kept. Waits for
+ * `stream`. */
 int ch_query_autotune(ch_t *ch, uint64_t sample, uint32_t seed, void *stream,
                       ch_query_config_t *chosen, double *ms_out);
 

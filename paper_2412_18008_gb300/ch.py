@@ -55,13 +55,14 @@ class ParamsT(C.Structure):
 
 
 class QueryConfigT(C.Structure):
-    _fields_ = [("layout", C.c_uint32), ("threads", C.c_uint32)]
+    _fields_ = [("layout", C.c_uint32), ("threads", C.c_uint32), ("small_first", C.c_uint32)]
 
 
 CH_QUERY_BLOCK_FLAT = 0
 CH_QUERY_WARP_FLAT = 1
-QUERY_CONFIGS = ((CH_QUERY_BLOCK_FLAT, 128), (CH_QUERY_BLOCK_FLAT, 256),
-                 (CH_QUERY_WARP_FLAT, 128), (CH_QUERY_WARP_FLAT, 256))
+# (layout, threads, small_first) in the autotuner's order
+QUERY_CONFIGS = tuple((lay, thr, sf) for sf in (0, 1) for lay in (CH_QUERY_BLOCK_FLAT, CH_QUERY_WARP_FLAT)
+                      for thr in (128, 256))
 
 
 class ServerParamsT(C.Structure):
@@ -280,23 +281,23 @@ class CH:
                                      stream_ptr))
 
     # -- query configuration, autotuning, work, graphs ----------------------
-    def set_query_config(self, layout: int, threads: int):
-        _check(load().ch_set_query_config(self._h, C.byref(QueryConfigT(layout, threads))))
+    def set_query_config(self, layout: int, threads: int, small_first: int = 0):
+        _check(load().ch_set_query_config(self._h, C.byref(QueryConfigT(layout, threads, small_first))))
 
-    def query_config(self) -> tuple[int, int]:
+    def query_config(self) -> tuple[int, int, int]:
         c = QueryConfigT()
         _check(load().ch_get_query_config(self._h, C.byref(c)))
-        return c.layout, c.threads
+        return c.layout, c.threads, c.small_first
 
     def autotune_queries(self, sample: int = 1 << 16, seed: int = 1, stream=None):
         """Time every query configuration on ``sample`` random queries and keep
-        the fastest. Returns (chosen (layout, threads), ms per configuration
-        in QUERY_CONFIGS order)."""
+        the fastest. Returns (chosen (layout, threads, small_first), ms per
+        configuration in QUERY_CONFIGS order)."""
         c = QueryConfigT()
-        ms = np.zeros(4, np.float64)
+        ms = np.zeros(8, np.float64)
         _check(load().ch_query_autotune(self._h, sample, seed, _stream_ptr(stream), C.byref(c),
                                         _hp(ms)))
-        return (c.layout, c.threads), ms
+        return (c.layout, c.threads, c.small_first), ms
 
     def query_work(self, stream=None) -> tuple[int, int]:
         """(expansions, edges scanned) of the query searches since the last call."""

@@ -192,7 +192,7 @@ int ch_set_query_config(ch_t *ch, const ch_query_config_t *cfg) {
         g_last_error = "null argument";
         return CH_EINVAL;
     }
-    return guarded([&] { query_set_config(ch, cfg->layout, cfg->threads); });
+    return guarded([&] { query_set_config(ch, cfg->layout, cfg->threads, cfg->small_first); });
 }
 
 int ch_get_query_config(const ch_t *ch, ch_query_config_t *cfg) {
@@ -202,6 +202,7 @@ int ch_get_query_config(const ch_t *ch, ch_query_config_t *cfg) {
     }
     cfg->layout = ch->q_layout;
     cfg->threads = ch->q_threads;
+    cfg->small_first = ch->q_small_first;
     return CH_OK;
 }
 
@@ -211,14 +212,7 @@ int ch_query_autotune(ch_t *ch, uint64_t sample, uint32_t seed, void *stream, ch
         g_last_error = "null handle";
         return CH_EINVAL;
     }
-    return guarded([&] {
-        uint32_t l = 0, t = 0;
-        query_autotune(ch, sample, seed, static_cast<cudaStream_t>(stream), &l, &t, ms_out);
-        if (chosen) {
-            chosen->layout = l;
-            chosen->threads = t;
-        }
-    });
+    return guarded([&] { query_autotune(ch, sample, seed, static_cast<cudaStream_t>(stream), chosen, ms_out); });
 }
 
 int ch_query_work(ch_t *ch, void *stream, uint64_t out[2]) {

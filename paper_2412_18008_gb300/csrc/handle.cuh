@@ -62,6 +62,7 @@ struct ch_s {
     gbch::DevBuf<unsigned long long> q_stats;  // [0] expansions, [1] edges scanned
     uint32_t q_layout = CH_QUERY_WARP_FLAT;  // query block configuration (performance only)
     uint32_t q_threads = 256;
+    uint32_t q_small_first = 1;  // first pass on 2^11-slot tables
     uint32_t q_slots = 0;
     uint64_t q_ovf_cap = 0;
 };
@@ -83,9 +84,9 @@ void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint6
                         uint32_t *dist_out, cudaStream_t st);
 
 // Query configuration, autotuning, work counters, graphs (query.cu).
-void query_set_config(ch_s *h, uint32_t layout, uint32_t threads);
-void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, uint32_t *layout_out,
-                    uint32_t *threads_out, double *ms_out);
+void query_set_config(ch_s *h, uint32_t layout, uint32_t threads, uint32_t small_first);
+void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch_query_config_t *chosen,
+                    double *ms_out);
 void query_work(ch_s *h, cudaStream_t st, uint64_t out[2]);
 ch_query_graph_s *query_graph_create(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
                                      uint32_t *dist_out);

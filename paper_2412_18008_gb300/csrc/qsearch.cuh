@@ -12,25 +12,27 @@ constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t QERR_RANGE = 1u;
 constexpr uint32_t QERR_BOUND = 2u;  // an index check failed; the access was skipped
 
-constexpr int QB_THREADS = 256;        // threads per query block
-constexpr int QB_TBITS = 12;           // 4096 vertices per query table
-constexpr int QB_T = 1 << QB_TBITS;
-constexpr int QB_FC = 2048;            // frontier capacity
+constexpr int QB_THREADS = 256;  // threads per query block, at most
 
-// Shared state of one query block (about 70 KB, three blocks per SM): a
-// hash table of reached vertices whose entries carry both directions'
-// labels, claim bitmaps that keep a slot from being queued twice in one
-// level and direction (one bitmap per level parity, the idle one cleared
-// during the level), a double-buffered frontier holding both directions'
-// entries (slot | dir<<31) and a triple-buffered frontier counter (see
-// block_search).
-constexpr int QB_CW = QB_T / 32;  // claim-bitmap words per direction
+// Shared state of one query block, for a table of 2^TB vertices (TB = 12:
+// about 69 KB, three blocks per SM; TB = 11: about 35 KB, six): a hash table
+// of reached vertices whose entries carry both directions' labels, claim
+// bitmaps that keep a slot from being queued twice in one level and
+// direction (one bitmap per level parity, the idle one cleared during the
+// level), a double-buffered frontier holding both directions' entries
+// (slot | dir<<31) and a triple-buffered frontier counter (see block_search).
+template <int TB>
 struct QBSmem {
-    uint32_t key[QB_T];
-    uint32_t df[QB_T];
-    uint32_t db[QB_T];
-    uint32_t claim[2][2][QB_CW];  // [level parity][direction][word]
-    uint32_t front[2][QB_FC];
+    static constexpr uint32_t T = 1u << TB;   // table slots
+    // frontier capacity (the small table's is trimmed so that six blocks fit
+    // an SM's 228 KB of shared memory)
+    static constexpr uint32_t FC = TB >= 12 ? T / 2 : 3 * T / 8;
+    static constexpr uint32_t CW = T / 32;    // claim-bitmap words per direction
+    uint32_t key[T];
+    uint32_t df[T];
+    uint32_t db[T];
+    uint32_t claim[2][2][CW];  // [level parity][direction][word]
+    uint32_t front[2][FC];
     // one tile of frontier entries, flattened block-wide: exclusive prefix of
     // their out-degrees, first edge index, label, slot | dir << 31
     uint32_t t_excl[QB_THREADS];
@@ -51,33 +53,39 @@ struct QArgs {
     const uint32_t *src, *dst;
     uint32_t *out, *settled;
     uint64_t k;
-    uint32_t *work;      // [0]: block path counter, [1]: fallback counter, [2]: overflow count
+    // Work items and counters. A block kernel takes items from work[ctr]:
+    // query j for j < k, or, with in_list, query in_list[j] for
+    // j < work[in_cnt]. A query whose search overflows is appended to ovf,
+    // counted in work[ovf_cnt]. The dense kernel takes ovf entries from
+    // work[1].
+    uint32_t *work;
+    const uint32_t *in_list;
+    uint32_t in_cnt, ctr, ovf_cnt;
     uint32_t *ovf;
     uint32_t *err;
     unsigned long long *stats;  // [0] expansions, [1] edges scanned (or null)
 };
 
-__device__ __forceinline__ uint32_t qb_hash(uint32_t v) {
-    return (v * 2654435761u) >> (32 - QB_TBITS);
-}
-
+template <int TB>
 __device__ __forceinline__ uint32_t qb_insert(uint32_t *keys, uint32_t v) {
-    uint32_t h = qb_hash(v);
-    for (uint32_t probe = 0; probe < (uint32_t)QB_T; ++probe) {
+    constexpr uint32_t T = 1u << TB;
+    uint32_t h = (v * 2654435761u) >> (32 - TB);
+    for (uint32_t probe = 0; probe < T; ++probe) {
         uint32_t k = keys[h];
         if (k == v) return h;
         if (k == EMPTY) {
             uint32_t old = atomicCAS(&keys[h], EMPTY, v);
             if (old == EMPTY || old == v) return h;
         }
-        h = (h + 1) & (QB_T - 1);
+        h = (h + 1) & (T - 1);
     }
     return EMPTY;
 }
 
 // Marks `slot` as queued in direction `dir` for the next level (bitmap of
 // the level's parity); true if it was not queued yet.
-__device__ __forceinline__ bool qb_claim(QBSmem &q, uint32_t slot, uint32_t dir, uint32_t lvl) {
+template <int TB>
+__device__ __forceinline__ bool qb_claim(QBSmem<TB> &q, uint32_t slot, uint32_t dir, uint32_t lvl) {
     const uint32_t bit = 1u << (slot & 31u);
     return !(atomicOr(&q.claim[lvl & 1u][dir][slot >> 5], bit) & bit);
 }
@@ -90,8 +98,8 @@ struct QStat {
 
 // Relaxes one edge e = (y, w) of a vertex labelled dx in direction dir.
 // Returns nothing; records an overflow in q.ovf, an index error in a.err.
-template <bool PRUNE>
-__device__ __forceinline__ void qb_relax(QBSmem &q, const QArgs &a, uint32_t dir, uint2 e, uint32_t dx,
+template <bool PRUNE, int TB>
+__device__ __forceinline__ void qb_relax(QBSmem<TB> &q, const QArgs &a, uint32_t dir, uint2 e, uint32_t dx,
                                          uint32_t lvl, uint32_t nxt_cnt, uint32_t *next_front) {
     const uint32_t nd = sat_add(dx, e.y);
     if (e.x >= a.n) {
@@ -100,7 +108,7 @@ __device__ __forceinline__ void qb_relax(QBSmem &q, const QArgs &a, uint32_t dir
     }
     if (nd == INF) return;
     if (PRUNE && nd >= q.mu) return;
-    const uint32_t ys = qb_insert(q.key, e.x);
+    const uint32_t ys = qb_insert<TB>(q.key, e.x);
     if (ys == EMPTY) {
         q.ovf = 1;
         return;
@@ -114,18 +122,19 @@ __device__ __forceinline__ void qb_relax(QBSmem &q, const QArgs &a, uint32_t dir
     }
     if (qb_claim(q, ys, dir, lvl)) {
         const uint32_t p = atomicAdd(&q.cnt3[nxt_cnt], 1u);
-        if (p < (uint32_t)QB_FC) next_front[p] = ys | (dir << 31);
+        if (p < QBSmem<TB>::FC) next_front[p] = ys | (dir << 31);
         else q.ovf = 1;
     }
 }
 
 // Loads what expanding one frontier entry needs: its vertex's edge range in
 // the direction's CSR and its label. cnt = 0 for an invalid entry.
-__device__ __forceinline__ void qb_entry(const QBSmem &q, const QArgs &a, bool fv, uint32_t ent,
+template <int TB>
+__device__ __forceinline__ void qb_entry(const QBSmem<TB> &q, const QArgs &a, bool fv, uint32_t ent,
                                          uint32_t &b, uint32_t &cnt, uint32_t &dx) {
     const uint32_t dir = ent >> 31;
     const uint32_t slot = ent & 0x7FFFFFFFu;
-    const bool sok = fv && slot < (uint32_t)QB_T;
+    const bool sok = fv && slot < QBSmem<TB>::T;
     if (fv && !sok) atomicOr(a.err, QERR_BOUND);
     const uint32_t x = sok ? q.key[slot] : 0;
     const bool xok = sok && x < a.n;
@@ -163,8 +172,9 @@ __device__ __forceinline__ void qb_entry(const QBSmem &q, const QArgs &a, bool f
 // flag right after a barrier that follows every write to them: the barrier
 // at the top of the level (warp-flattened; block-flattened at level 1) or
 // the barrier that ends the previous level's last tile (block-flattened).
-template <bool PRUNE, bool WARP>
-__device__ bool block_search(QBSmem &q, const QArgs &a, QStat &stat) {
+template <bool PRUNE, bool WARP, int TB>
+__device__ bool block_search(QBSmem<TB> &q, const QArgs &a, QStat &stat) {
+    constexpr uint32_t FC = QBSmem<TB>::FC, CW = QBSmem<TB>::CW;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
     for (uint32_t lvl = 1;; ++lvl) {
@@ -181,14 +191,14 @@ __device__ bool block_search(QBSmem &q, const QArgs &a, QStat &stat) {
         if (tid == 0) q.cnt3[(lvl + 1) % 3] = 0;
         // the bitmap of the other parity was last used two levels ago and is
         // next used one level from now
-        for (uint32_t j = tid; j < 2u * QB_CW; j += blockDim.x) (&q.claim[(lvl + 1) & 1u][0][0])[j] = 0;
+        for (uint32_t j = tid; j < 2u * CW; j += blockDim.x) (&q.claim[(lvl + 1) & 1u][0][0])[j] = 0;
         const uint32_t nxt_cnt = lvl % 3;
         uint32_t *next_front = q.front[cur ^ 1u];
         if (WARP) {
             const uint32_t stride = blockDim.x;
             for (uint32_t p0 = 0; p0 < nfront; p0 += stride) {
                 const uint32_t fi = p0 + warp + nwarps * lane;
-                const bool fv = fi < nfront && fi < (uint32_t)QB_FC;
+                const bool fv = fi < nfront && fi < FC;
                 const uint32_t ent = fv ? q.front[cur][fi] : 0;
                 uint32_t b, cnt, dx;
                 qb_entry(q, a, fv, ent, b, cnt, dx);
@@ -206,14 +216,14 @@ __device__ bool block_search(QBSmem &q, const QArgs &a, QStat &stat) {
                     if (e0 < total) {
                         ++stat.edges;
                         const uint2 e = (odir ? a.dn_adj : a.up_adj)[ob + (e0 - oex)];
-                        qb_relax<PRUNE>(q, a, odir, e, odx, lvl, nxt_cnt, next_front);
+                        qb_relax<PRUNE, TB>(q, a, odir, e, odx, lvl, nxt_cnt, next_front);
                     }
                 }
             }
         } else {
             for (uint32_t t0 = 0; t0 < nfront; t0 += blockDim.x) {
                 const uint32_t fi = t0 + tid;
-                const bool fv = fi < nfront && fi < (uint32_t)QB_FC;
+                const bool fv = fi < nfront && fi < FC;
                 const uint32_t ent = fv ? q.front[cur][fi] : 0;
                 uint32_t b, cnt, dx;
                 qb_entry(q, a, fv, ent, b, cnt, dx);
@@ -244,7 +254,7 @@ __device__ bool block_search(QBSmem &q, const QArgs &a, QStat &stat) {
                     ++stat.edges;
                     const uint32_t odir = q.t_ent[lo] >> 31;
                     const uint2 e = (odir ? a.dn_adj : a.up_adj)[q.t_beg[lo] + (e0 - q.t_excl[lo])];
-                    qb_relax<PRUNE>(q, a, odir, e, q.t_dx[lo], lvl, nxt_cnt, next_front);
+                    qb_relax<PRUNE, TB>(q, a, odir, e, q.t_dx[lo], lvl, nxt_cnt, next_front);
                 }
                 __syncthreads();
             }
@@ -254,13 +264,14 @@ __device__ bool block_search(QBSmem &q, const QArgs &a, QStat &stat) {
 
 // Empties the block's table and claim bitmaps (at kernel start; every query
 // leaves them empty again).
-__device__ __forceinline__ void qb_clear(QBSmem &q) {
-    for (uint32_t j = threadIdx.x; j < (uint32_t)QB_T; j += blockDim.x) {
+template <int TB>
+__device__ __forceinline__ void qb_clear(QBSmem<TB> &q) {
+    for (uint32_t j = threadIdx.x; j < QBSmem<TB>::T; j += blockDim.x) {
         q.key[j] = EMPTY;
         q.df[j] = INF;
         q.db[j] = INF;
     }
-    for (uint32_t j = threadIdx.x; j < 4u * QB_CW; j += blockDim.x) (&q.claim[0][0][0])[j] = 0;
+    for (uint32_t j = threadIdx.x; j < 4u * QBSmem<TB>::CW; j += blockDim.x) (&q.claim[0][0][0])[j] = 0;
 }
 
 // One s-t query (rank ids rs, rt < n) by the whole block, on the shared
@@ -270,15 +281,15 @@ __device__ __forceinline__ void qb_clear(QBSmem &q) {
 // overflowed the table or the frontier (the caller redoes the query
 // elsewhere); otherwise mu and cnt hold, in every thread, the least meeting
 // sum and the number of labels set. Every thread of the block must call it.
-template <bool PRUNE, bool WARP>
-__device__ bool block_query(QBSmem &q, const QArgs &a, uint32_t rs, uint32_t rt, uint32_t &mu_out,
+template <bool PRUNE, bool WARP, int TB>
+__device__ bool block_query(QBSmem<TB> &q, const QArgs &a, uint32_t rs, uint32_t rt, uint32_t &mu_out,
                             uint32_t &cnt_out, QStat &stat) {
     const uint32_t tid = threadIdx.x;
     __syncthreads();
     if (tid == 0) {
-        const uint32_t ss = qb_insert(q.key, rs);
+        const uint32_t ss = qb_insert<TB>(q.key, rs);
         q.df[ss] = 0;
-        const uint32_t st = qb_insert(q.key, rt);
+        const uint32_t st = qb_insert<TB>(q.key, rt);
         q.db[st] = 0;
         q.ovf = 0;
         q.mu = ss == st ? 0u : INF;
@@ -289,13 +300,13 @@ __device__ bool block_query(QBSmem &q, const QArgs &a, uint32_t rs, uint32_t rt,
         q.cnt3[1] = 0;
         q.cnt3[2] = 0;
     }
-    const bool ok = block_search<PRUNE, WARP>(q, a, stat);
+    const bool ok = block_search<PRUNE, WARP, TB>(q, a, stat);
     // q.mu only steered pruning; the answer is the least meeting sum.
     __syncthreads();
     if (tid == 0) q.mu = INF;
     __syncthreads();
     uint32_t mu = INF, cnt = 0;
-    for (uint32_t j = tid; j < (uint32_t)QB_T; j += blockDim.x) {
+    for (uint32_t j = tid; j < QBSmem<TB>::T; j += blockDim.x) {
         const uint32_t f = q.df[j], g = q.db[j];
         mu = min(mu, sat_add(f, g));
         cnt += (f != INF) + (g != INF);
@@ -303,7 +314,7 @@ __device__ bool block_query(QBSmem &q, const QArgs &a, uint32_t rs, uint32_t rt,
         q.df[j] = INF;
         q.db[j] = INF;
     }
-    for (uint32_t j = tid; j < 4u * QB_CW; j += blockDim.x) (&q.claim[0][0][0])[j] = 0;
+    for (uint32_t j = tid; j < 4u * QBSmem<TB>::CW; j += blockDim.x) (&q.claim[0][0][0])[j] = 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mu = min(mu, __shfl_xor_sync(FULL, mu, o));

@@ -27,19 +27,25 @@ namespace {
 
 constexpr uint64_t Q_CHUNK = 1u << 22;  // queries per launch pair
 
-template <bool PRUNE, bool WARP>
+template <bool PRUNE, bool WARP, int TB>
 __global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
     extern __shared__ __align__(16) unsigned char qb_raw[];
-    QBSmem &q = *reinterpret_cast<QBSmem *>(qb_raw);
+    QBSmem<TB> &q = *reinterpret_cast<QBSmem<TB> *>(qb_raw);
     const uint32_t tid = threadIdx.x;
     QStat stat;
     qb_clear(q);
+    const uint64_t nitems = a.in_list ? a.work[a.in_cnt] : a.k;
     while (true) {
         __syncthreads();
-        if (tid == 0) q.item = atomicAdd(&a.work[0], 1u);
+        if (tid == 0) q.item = atomicAdd(&a.work[a.ctr], 1u);
         __syncthreads();
-        const uint32_t i = q.item;
-        if (i >= a.k) break;
+        const uint32_t j = q.item;
+        if (j >= nitems) break;
+        const uint32_t i = a.in_list ? a.in_list[j] : j;
+        if (i >= a.k) {
+            if (tid == 0) atomicOr(a.err, QERR_BOUND);
+            continue;
+        }
         const uint32_t s = a.src[i], t = a.dst[i];
         if (s >= a.n || t >= a.n) {
             if (tid == 0) {
@@ -58,8 +64,8 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
             continue;
         }
         uint32_t mu, cnt;
-        if (!block_query<PRUNE, WARP>(q, a, rs, rt, mu, cnt, stat)) {
-            if (tid == 0) a.ovf[atomicAdd(&a.work[2], 1u)] = i;
+        if (!block_query<PRUNE, WARP, TB>(q, a, rs, rt, mu, cnt, stat)) {
+            if (tid == 0) a.ovf[atomicAdd(&a.work[a.ovf_cnt], 1u)] = i;
             continue;
         }
         if (tid == 0) {
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(256) k_query_dense(QArgs a, QDense dn) {
     uint32_t *fa = dn.fa + base, *fb = dn.fb + base, *touched = dn.touched + 2 * base;
     __shared__ uint32_t s_item, s_nt, s_nf[2], s_mu;
     const uint32_t tid = threadIdx.x;
-    const uint32_t novf = a.work[2];
+    const uint32_t novf = a.work[a.ovf_cnt];
     uint32_t stamp = 0;
     while (true) {
         __syncthreads();
@@ -189,47 +195,57 @@ __global__ void __launch_bounds__(256) k_query_dense(QArgs a, QDense dn) {
 }
 
 // Resident blocks per SM of each block-kernel configuration
-// [layout][threads == 256], resolved once.
-int g_qb_bps[2][2] = {{-1, -1}, {-1, -1}};
+// [table bits == 11][layout][threads == 256], resolved once.
+int g_qb_bps[2][2][2] = {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}};
 
-template <bool PRUNE, bool WARP>
-void qb_set_attr() {
-    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<PRUNE, WARP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(QBSmem)));
-}
-
-void qb_resolve_occupancy() {
-    if (g_qb_bps[0][0] >= 0) return;
-    qb_set_attr<true, false>();
-    qb_set_attr<false, false>();
-    qb_set_attr<true, true>();
-    qb_set_attr<false, true>();
+template <int TB>
+void qb_resolve(int s) {
+    const int smem = (int)sizeof(QBSmem<TB>);
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true, false, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<false, false, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true, true, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<false, true, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     for (int l = 0; l < 2; ++l)
         for (int t = 0; t < 2; ++t) {
             int b = 0;
             const int threads = t ? 256 : 128;
-            if (l) CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, true>, threads, sizeof(QBSmem)));
-            else CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, false>, threads, sizeof(QBSmem)));
-            g_qb_bps[l][t] = std::max(1, b);
+            if (l) CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, true, TB>, threads, smem));
+            else CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, false, TB>, threads, smem));
+            g_qb_bps[s][l][t] = std::max(1, b);
         }
 }
 
-// Launches the block kernel in the handle's configuration: a persistent
-// grid of as many blocks as are resident at once (no more than k).
-void launch_query_block(const ch_s *h, const QArgs &a, bool prune, uint64_t k, cudaStream_t st) {
+void qb_resolve_occupancy() {
+    if (g_qb_bps[0][0][0] >= 0) return;
+    qb_resolve<12>(0);
+    qb_resolve<11>(1);
+}
+
+template <int TB>
+void launch_tb(const QArgs &a, bool prune, bool warp, int blocks, int threads, cudaStream_t st) {
+    const size_t smem = sizeof(QBSmem<TB>);
+    if (warp) {
+        if (prune) k_query_block<true, true, TB><<<blocks, threads, smem, st>>>(a);
+        else k_query_block<false, true, TB><<<blocks, threads, smem, st>>>(a);
+    } else {
+        if (prune) k_query_block<true, false, TB><<<blocks, threads, smem, st>>>(a);
+        else k_query_block<false, false, TB><<<blocks, threads, smem, st>>>(a);
+    }
+    CH_CHECK_LAUNCH();
+}
+
+// Launches one block-kernel pass in the handle's layout and block size: a
+// persistent grid of as many blocks as are resident at once (no more than
+// the items), with 2^11-slot tables when small is set, else 2^12.
+void launch_query_block(const ch_s *h, const QArgs &a, bool prune, bool small, uint64_t items,
+                        cudaStream_t st) {
     const int l = h->q_layout == CH_QUERY_WARP_FLAT ? 1 : 0;
     const int t = h->q_threads == 256 ? 1 : 0;
     const int threads = t ? 256 : 128;
-    const int blocks = (int)std::min<uint64_t>(k, (uint64_t)device_sm_count() * g_qb_bps[l][t]);
-    const size_t smem = sizeof(QBSmem);
-    if (l) {
-        if (prune) k_query_block<true, true><<<blocks, threads, smem, st>>>(a);
-        else k_query_block<false, true><<<blocks, threads, smem, st>>>(a);
-    } else {
-        if (prune) k_query_block<true, false><<<blocks, threads, smem, st>>>(a);
-        else k_query_block<false, false><<<blocks, threads, smem, st>>>(a);
-    }
-    CH_CHECK_LAUNCH();
+    const int blocks = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>(items, (uint64_t)device_sm_count() * g_qb_bps[small ? 1 : 0][l][t]));
+    if (small) launch_tb<11>(a, prune, l == 1, blocks, threads, st);
+    else launch_tb<12>(a, prune, l == 1, blocks, threads, st);
 }
 
 }  // namespace
@@ -238,9 +254,9 @@ void query_init(ch_s *h) {
     const uint32_t n = h->n;
     h->qerr.alloc(1);
     h->qerr.zero(0);
-    h->qwork.alloc(4);
+    h->qwork.alloc(8);
     h->q_ovf_cap = Q_CHUNK;
-    h->q_ovf_list.alloc(Q_CHUNK);
+    h->q_ovf_list.alloc(2 * Q_CHUNK);  // overflow lists of the two block-kernel passes
     // per slot: df, db, fst, two frontiers (n each) and the touched list
     // of both directions (2n)
     const uint64_t per_slot = (uint64_t)std::max<uint32_t>(n, 1) * 7 * 4;
@@ -285,13 +301,29 @@ void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
         a.settled = settled_out ? settled_out + c0 : nullptr;
         a.k = kc;
         a.work = h->qwork.ptr;
-        a.ovf = h->q_ovf_list.ptr;
         a.err = h->qerr.ptr;
         a.stats = h->q_stats.ptr;
-        CH_CUDA_TRY(cudaMemsetAsync(h->qwork.ptr, 0, 4 * sizeof(uint32_t), st));
+        a.in_list = nullptr;
+        a.in_cnt = 0;
+        CH_CUDA_TRY(cudaMemsetAsync(h->qwork.ptr, 0, 8 * sizeof(uint32_t), st));
         // Pruned searches unless the caller asked for search-space sizes,
         // which are defined by the exhaustive upward searches.
-        launch_query_block(h, a, settled_out == nullptr, kc, st);
+        const bool prune = settled_out == nullptr;
+        if (h->q_small_first) {
+            // pass 1 on small tables (twice the resident queries); the
+            // queries that overflow them are redone on the large tables
+            a.ctr = 0;
+            a.ovf = h->q_ovf_list.ptr + Q_CHUNK;
+            a.ovf_cnt = 4;
+            launch_query_block(h, a, prune, true, kc, st);
+            a.ctr = 3;
+            a.in_list = h->q_ovf_list.ptr + Q_CHUNK;
+            a.in_cnt = 4;
+        }
+        a.ctr = a.in_list ? 3 : 0;
+        a.ovf = h->q_ovf_list.ptr;
+        a.ovf_cnt = 2;
+        launch_query_block(h, a, prune, false, kc, st);
         k_query_dense<<<h->q_slots, 256, 0, st>>>(a, dn);
         CH_CHECK_LAUNCH();
     }
@@ -317,30 +349,37 @@ __global__ void k_sample_pairs(uint32_t *s, uint32_t *t, uint64_t k, uint32_t n,
 
 }  // namespace
 
-void query_set_config(ch_s *h, uint32_t layout, uint32_t threads) {
-    if ((layout != CH_QUERY_BLOCK_FLAT && layout != CH_QUERY_WARP_FLAT) || (threads != 128 && threads != 256))
-        throw Error{CH_EINVAL, "query configuration: layout BLOCK_FLAT or WARP_FLAT, threads 128 or 256"};
+void query_set_config(ch_s *h, uint32_t layout, uint32_t threads, uint32_t small_first) {
+    if ((layout != CH_QUERY_BLOCK_FLAT && layout != CH_QUERY_WARP_FLAT) || (threads != 128 && threads != 256) ||
+        small_first > 1)
+        throw Error{CH_EINVAL, "query configuration: layout BLOCK_FLAT or WARP_FLAT, threads 128 or 256, "
+                               "small_first 0 or 1"};
     h->q_layout = layout;
     h->q_threads = threads;
+    h->q_small_first = small_first;
 }
 
-void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, uint32_t *layout_out,
-                    uint32_t *threads_out, double *ms_out) {
+void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch_query_config_t *chosen,
+                    double *ms_out) {
     if (sample == 0 || h->n == 0) throw Error{CH_EINVAL, "autotune needs a sample and a non-empty graph"};
     DevBuf<uint32_t> buf;
     buf.alloc(3 * sample);
     uint32_t *s = buf.ptr, *t = buf.ptr + sample, *out = buf.ptr + 2 * sample;
     k_sample_pairs<<<grid_for(sample, 256, device_sm_count() * 4), 256, 0, st>>>(s, t, sample, h->n, seed);
     CH_CHECK_LAUNCH();
-    const uint32_t keep_l = h->q_layout, keep_t = h->q_threads;
+    const uint32_t keep_l = h->q_layout, keep_t = h->q_threads, keep_s = h->q_small_first;
     cudaEvent_t e0, e1;
     CH_CUDA_TRY(cudaEventCreate(&e0));
     CH_CUDA_TRY(cudaEventCreate(&e1));
+    auto apply = [&](int i) {
+        query_set_config(h, (i & 2) ? CH_QUERY_WARP_FLAT : CH_QUERY_BLOCK_FLAT, (i & 1) ? 256 : 128,
+                         (i & 4) ? 1 : 0);
+    };
     double best = 0;
     int best_i = -1;
     try {
-        for (int i = 0; i < 4; ++i) {
-            query_set_config(h, i >= 2 ? CH_QUERY_WARP_FLAT : CH_QUERY_BLOCK_FLAT, (i & 1) ? 256 : 128);
+        for (int i = 0; i < 8; ++i) {
+            apply(i);
             query_batch(h, s, t, sample, out, nullptr, st);  // warm-up
             CH_CUDA_TRY(cudaEventRecord(e0, st));
             query_batch(h, s, t, sample, out, nullptr, st);
@@ -357,15 +396,19 @@ void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ui
     } catch (...) {
         h->q_layout = keep_l;
         h->q_threads = keep_t;
+        h->q_small_first = keep_s;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         throw;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    query_set_config(h, best_i >= 2 ? CH_QUERY_WARP_FLAT : CH_QUERY_BLOCK_FLAT, (best_i & 1) ? 256 : 128);
-    if (layout_out) *layout_out = h->q_layout;
-    if (threads_out) *threads_out = h->q_threads;
+    apply(best_i);
+    if (chosen) {
+        chosen->layout = h->q_layout;
+        chosen->threads = h->q_threads;
+        chosen->small_first = h->q_small_first;
+    }
     // the sample's work is not the caller's: clear the counters
     CH_CUDA_TRY(cudaMemsetAsync(h->q_stats.ptr, 0, 2 * sizeof(unsigned long long), st));
     CH_CUDA_TRY(cudaStreamSynchronize(st));
@@ -514,12 +557,17 @@ void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint6
     a.settled = nullptr;
     a.k = k;
     a.work = scratch;
+    a.in_list = nullptr;
+    a.in_cnt = 0;
+    a.ctr = 0;
     a.ovf = scratch + kStaticScratchHead;
+    a.ovf_cnt = 2;
     a.err = h->qerr.ptr;
     a.stats = h->q_stats.ptr;
     // the counters keep the previous call's values: clear them
     CH_CUDA_TRY(cudaMemsetAsync(scratch, 0, kStaticScratchHead * sizeof(uint32_t), st));
-    launch_query_block(h, a, true, k, st);
+    // one block-kernel pass (large tables): the scratch holds one list
+    launch_query_block(h, a, true, false, k, st);
     k_query_dense<<<h->q_slots, 256, 0, st>>>(a, dn);
     CH_CHECK_LAUNCH();
 }

@@ -232,7 +232,7 @@ __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_
 template <bool WARP>
 __global__ void __launch_bounds__(QB_THREADS) k_serve(SvArgs a) {
     extern __shared__ __align__(16) unsigned char qb_raw[];
-    QBSmem &q = *reinterpret_cast<QBSmem *>(qb_raw);
+    QBSmem<12> &q = *reinterpret_cast<QBSmem<12> *>(qb_raw);
     QStat stat;  // not reported
     qb_clear(q);
     __shared__ uint32_t s_go, s_src, s_tgt, s_k, s_slot, s_first;
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_serve(SvArgs a) {
             const uint32_t rs = g.rank[s], rt = g.rank[tv];
             if (rs < g.n && rt < g.n) {
                 uint32_t cnt;
-                if (!block_query<true, WARP>(q, g, rs, rt, ans, cnt, stat))
+                if (!block_query<true, WARP, 12>(q, g, rs, rt, ans, cnt, stat))
                     ans = sv_query(a, t, rs, rt, q.cnt3, &q.ovf, &q.mu, &q.cnt);
             } else if (tid == 0) {
                 atomicOr(a.status, QERR_BOUND);
@@ -393,9 +393,9 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     const bool warp = h->q_layout == CH_QUERY_WARP_FLAT;
     const int threads = (int)h->q_threads;
     auto kern = warp ? k_serve<true> : k_serve<false>;
-    CH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(QBSmem)));
+    CH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(QBSmem<12>)));
     int per_sm = 0;
-    CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sizeof(QBSmem)));
+    CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sizeof(QBSmem<12>)));
     sv->nblocks = p->blocks ? p->blocks : (uint32_t)sms * (uint32_t)std::max(per_sm, 1);
     uint32_t tbits = 10;
     while (tbits < 24 && ((1u << tbits) < std::min<uint32_t>(h->n, 1u << 17))) ++tbits;
@@ -461,7 +461,7 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     a.fst = base + 3 * T * NB;
     a.touched = base + 4 * T * NB;
     a.front = base + 5 * T * NB;
-    kern<<<sv->nblocks, threads, sizeof(QBSmem), sv->st>>>(a);
+    kern<<<sv->nblocks, threads, sizeof(QBSmem<12>), sv->st>>>(a);
     CH_CHECK_LAUNCH();
     sv->running = true;
 }

@@ -53,6 +53,8 @@ def test_struct_layouts_match_header():
     int main(void) {
       printf("%zu %zu %zu\n", sizeof(ch_graph_t), sizeof(ch_params_t), sizeof(ch_stats_t));
       printf("%zu %zu\n", offsetof(ch_params_t, stream), offsetof(ch_stats_t, witness_bytes));
+      printf("%zu %zu %zu\n", sizeof(ch_query_config_t), sizeof(ch_server_params_t),
+             offsetof(ch_server_params_t, idle_ms));
       return 0;
     }'''
     tmp = "/tmp/ch_layout_check"
@@ -66,6 +68,9 @@ def test_struct_layouts_match_header():
     assert sizes[2] == C.sizeof(ch.StatsT)
     assert sizes[3] == ch.ParamsT.stream.offset
     assert sizes[4] == ch.StatsT.witness_bytes.offset
+    assert sizes[5] == C.sizeof(ch.QueryConfigT)
+    assert sizes[6] == C.sizeof(ch.ServerParamsT)
+    assert sizes[7] == ch.ServerParamsT.idle_ms.offset
 
 
 def test_no_cpu_fallback_in_product_package():

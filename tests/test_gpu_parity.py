@@ -126,6 +126,14 @@ def test_full_size_road_like_graph():
     same = s == t
     assert (d[same] == 0).all()
     assert (st >= 2 - same).all()
+    # the pruned searches the benchmark times, in both table tiers and both
+    # layouts, answer every pair of the batch as the exhaustive ones do
+    for cfg in ((1, 256, 0), (1, 256, 1), (0, 256, 1)):
+        gch.set_query_config(*cfg)
+        dp = gch.query(ds, dt)
+        torch.cuda.synchronize()
+        gch.query_status()
+        assert np.array_equal(dp.cpu().numpy().view(np.uint32), d), cfg
 
 
 def test_dense_graph_exercises_global_memory_paths():

@@ -26,11 +26,12 @@ def geo():
     return g, _ch().CH.build(g, hop_limit=5), O.build_ch(g, 5)
 
 
-@pytest.mark.parametrize("layout,threads", [(0, 128), (0, 256), (1, 128), (1, 256)])
-def test_every_configuration_gives_the_oracle_answers(geo, layout, threads):
+@pytest.mark.parametrize("layout,threads,small", [(lay, thr, sf) for sf in (0, 1) for lay in (0, 1)
+                                                  for thr in (128, 256)])
+def test_every_configuration_gives_the_oracle_answers(geo, layout, threads, small):
     g, gch, och = geo
-    gch.set_query_config(layout, threads)
-    assert gch.query_config() == (layout, threads)
+    gch.set_query_config(layout, threads, small)
+    assert gch.query_config() == (layout, threads, small)
     s, t = I.random_pairs(g.n, 20_000, seed=82)
     d, st = gch.query(s, t, want_settled=True)
     od, ost = och.query(s, t, want_settled=True)
@@ -47,18 +48,18 @@ def test_configurations_on_a_dense_random_digraph():
     och = O.build_ch(g, 4)
     s, t = I.random_pairs(g.n, 5000, seed=84)
     want = och.query(s, t)
-    for layout, threads in _ch().QUERY_CONFIGS:
-        gch.set_query_config(layout, threads)
-        assert np.array_equal(gch.query(s, t), want), (layout, threads)
+    for cfg in _ch().QUERY_CONFIGS:
+        gch.set_query_config(*cfg)
+        assert np.array_equal(gch.query(s, t), want), cfg
 
 
 def test_invalid_configuration_is_rejected(geo):
     ch = _ch()
     _, gch, _ = geo
     before = gch.query_config()
-    for layout, threads in ((2, 256), (0, 64), (1, 512)):
+    for cfg in ((2, 256, 0), (0, 64, 0), (1, 512, 0), (1, 256, 2)):
         with pytest.raises(ch.CHError) as ei:
-            gch.set_query_config(layout, threads)
+            gch.set_query_config(*cfg)
         assert ei.value.code == ch.CH_EINVAL
     assert gch.query_config() == before
 
@@ -90,9 +91,11 @@ def test_work_counters(geo):
     assert gch.query_work() == (0, 0)  # cleared by the read
 
 
-def test_graph_replay_matches_batch_calls(geo):
+@pytest.mark.parametrize("small", [0, 1])
+def test_graph_replay_matches_batch_calls(geo, small):
     torch = _torch()
     g, gch, och = geo
+    gch.set_query_config(1, 256, small)
     k = 3000
     s1, t1 = I.random_pairs(g.n, k, seed=87)
     s2, t2 = I.random_pairs(g.n, k, seed=88)
