@@ -40,12 +40,28 @@ WORKLOADS = {
     # name: (n, graph seed, query seed, queries)
     "geo1M": (1_000_000, 3, 4, 1_000_000),
     "geo256K": (256_000, 100, 101, 1_000_000),
+    # RMAT stress graph: 2^21 vertices, 2^25 edge samples (a=.57, b=c=.19),
+    # weights U[1,1000]; built with a finite candidate bound (--cmax)
+    "rmat2M": (1 << 21, 8, 9, 100_000),
 }
+
+
+def make_graph(name: str, sample: bool = False):
+    """The workload's graph, or (sample=True) the small graph of the same
+    family whose oracle build stands in for the CPU baseline."""
+    n, gseed, _, _ = WORKLOADS[name]
+    if name.startswith("rmat"):
+        if sample:  # same samples per vertex (16) at 2^12 vertices
+            return I.rmat_graph(scale=12, nsamples=1 << 16, wmax=1000, seed=7)
+        return I.rmat_graph(scale=21, nsamples=1 << 25, wmax=1000, seed=gseed)
+    if sample:
+        return I.geometric_knn_graph(100_000, seed=7)
+    return I.geometric_knn_graph(n, seed=gseed)
 METRIC = "CH build seconds & shortcut count; batched s-t queries/sec; p99 query latency"
 L2_BYTES = 129 * 1024 * 1024
-# DRAM bytes (read + write) of one k_query_block launch on the full query
-# batch, from an ncu capture of this kernel (None until captured for the
-# current kernel).
+# DRAM bytes (read + write) of the k_query_block launches of the full 1M
+# query batch (first pass + overflow redo), from an ncu capture of the
+# current kernel on this workload (set to None when the kernel changes).
 QUERY_TRAFFIC_PER_LAUNCH = None
 
 
@@ -57,6 +73,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="geo1M", choices=sorted(WORKLOADS))
     ap.add_argument("--hop-limit", type=int, default=5)
+    ap.add_argument("--cmax", type=int, default=None,
+                    help="candidate bound |N_in|*|N_out| of a contractible vertex (default: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
@@ -76,6 +94,9 @@ def parse():
                     help="geo1M or geo16M (16M-vertex graph of the same family, seed 6)")
     ap.add_argument("--serve-requests", type=int, default=40_000)
     ap.add_argument("--train-graphs", type=int, default=20)
+    ap.add_argument("--tune-build", action="store_true",
+                    help="with --compare-learned: pick the hop limit and witness routing with the "
+                         "build autotuner first")
     ap.add_argument("--train-epochs", type=int, default=4)
     return ap.parse_args()
 
@@ -142,15 +163,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_sample_build(n_full: int, hop_limit: int, sample_n: int = 100_000):
+def cpu_sample_build(workload: str, hop_limit: int, cmax):
     """Oracle build on a sample graph of the same family, scaled linearly
-    (by vertex count) to the full workload. Returns (scaled_s, raw_s, threads)."""
+    (by vertex count) to the full workload. Returns (scaled_s, raw_s,
+    threads, sample vertices)."""
     import oracle as O
-    g = I.geometric_knn_graph(sample_n, seed=7)
+    g = make_graph(workload, sample=True)
     t0 = time.perf_counter()
-    O.build_ch(g, hop_limit)
+    O.build_ch(g, hop_limit, cmax=O.CMAX_ALL if cmax is None else cmax)
     raw = time.perf_counter() - t0
-    return raw * (n_full / sample_n), raw, 1
+    return raw * (WORKLOADS[workload][0] / g.n), raw, 1, g.n
 
 
 def run_reference(args):
@@ -159,15 +181,16 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle as O
-    sample_n = 100_000
+    cmax = O.CMAX_ALL if args.cmax is None else args.cmax
     O.build_ch(I.geometric_knn_graph(2000, seed=7), args.hop_limit)  # load + warm
-    g = I.geometric_knn_graph(sample_n, seed=7)
+    g = make_graph(args.workload, sample=True)
+    sample_n = g.n
     for _ in range(args.warmup):
-        O.build_ch(g, args.hop_limit)
+        O.build_ch(g, args.hop_limit, cmax=cmax)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        O.build_ch(g, args.hop_limit)
+        O.build_ch(g, args.hop_limit, cmax=cmax)
         times.append(time.perf_counter() - t0)
     scale = n / sample_n
     value = statistics.mean(times) * scale
@@ -176,10 +199,11 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value * 1000, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": args.workload, "vertices": n, "hop_limit": args.hop_limit},
+        "config": {"workload": args.workload, "vertices": n, "hop_limit": args.hop_limit,
+                   "cmax": args.cmax},
         "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"oracle build of a {sample_n}-vertex graph of the same "
-                                   f"geometric 3-NN family, mean of {args.steps} runs, scaled "
+                                   f"family ({args.workload}), mean of {args.steps} runs, scaled "
                                    f"linearly by vertex count to {n} vertices"},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -187,15 +211,39 @@ def run_reference(args):
 
 
 def compare_learned(args):
-    """Learned priority vs edge difference (one JSON line)."""
+    """Learned priority vs edge difference (one JSON line). geo1M: trained on
+    traces of 20 seeded 256K-vertex graphs of the family, compared on a
+    held-out 1M graph (seed 5). rmat2M: trained on traces of seeded 2^17-vertex
+    RMAT graphs (2^21 samples each) under the same candidate bound, compared
+    on the 2M stress graph, with the hop limit and witness routing chosen by
+    the build autotuner (--tune-build)."""
     import torch
     from paper_2412_18008_gb300 import ch
     dev = torch.device("cuda", 0)
+    rmat = args.workload.startswith("rmat")
+    cmax = args.cmax
+    hop_limit, route_deg, tune_rows = args.hop_limit, 0, None
+    if rmat:
+        train_graph = lambda seed: I.rmat_graph(scale=17, nsamples=1 << 21, wmax=1000, seed=seed)
+        seeds = range(200, 200 + args.train_graphs)
+        g = make_graph(args.workload)
+        test_seed, nq_cmp, n_ss = WORKLOADS[args.workload][1], 100_000, 10_000
+    else:
+        train_graph = lambda seed: I.geometric_knn_graph(256_000, seed=seed)
+        seeds = range(100, 100 + args.train_graphs)
+        g = I.geometric_knn_graph(1_000_000, seed=5)
+        test_seed, nq_cmp, n_ss = 5, 1_000_000, 100_000
+    if args.tune_build:
+        h, tune_rows, k = ch.CH.build_autotune(g, hop_limits=(1, 2, 3, 4, 5), route_degs=(32, 64, 128),
+                                               sample=1 << 14, queries_per_build=nq_cmp,
+                                               max_candidates_per_vertex=cmax)
+        hop_limit, route_deg = tune_rows[k]["hop_limit"], tune_rows[k]["witness_route_deg"]
+        h.close()
     t0 = time.perf_counter()
     rows, labels = [], []
-    for seed in range(100, 100 + args.train_graphs):
-        g = I.geometric_knn_graph(256_000, seed=seed)
-        tr = ch.CH.build(g, hop_limit=args.hop_limit, trace=True).export_trace()
+    for seed in seeds:
+        tr = ch.CH.build(train_graph(seed), hop_limit=hop_limit, trace=True,
+                         max_candidates_per_vertex=cmax, witness_route_deg=route_deg).export_trace()
         rows.append(tr["rows"])
         labels.append(ch.training_labels(tr["rows"]))
     rows = np.concatenate(rows)
@@ -210,8 +258,7 @@ def compare_learned(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     weights = w.cpu().numpy()
-    g = I.geometric_knn_graph(1_000_000, seed=5)
-    s_h, t_h = I.random_pairs(g.n, 1_000_000, seed=6)
+    s_h, t_h = I.random_pairs(g.n, nq_cmp, seed=6)
     off = torch.from_numpy(g.offsets.view(np.int64)).to(dev)
     tgt = torch.from_numpy(g.targets.view(np.int32)).to(dev)
     wt = torch.from_numpy(g.weights.view(np.int32)).to(dev)
@@ -225,8 +272,9 @@ def compare_learned(args):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            h = ch.CH.build(n=g.n, offsets=off, targets=tgt, weights=wt, hop_limit=args.hop_limit,
-                            mlp_weights=mw)
+            h = ch.CH.build(n=g.n, offsets=off, targets=tgt, weights=wt, hop_limit=hop_limit,
+                            mlp_weights=mw, max_candidates_per_vertex=cmax,
+                            witness_route_deg=route_deg)
             e1.record()
             torch.cuda.synchronize()
             if k >= args.warmup:
@@ -234,23 +282,31 @@ def compare_learned(args):
             if k + 1 < args.warmup + args.steps:
                 h.close()
         st = h.stats()
-        d, sett = h.query(ds[:100_000], dt[:100_000], want_settled=True)
+        d, sett = h.query(ds[:n_ss], dt[:n_ss], want_settled=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
         full = h.query(ds, dt)
+        e1.record()
         torch.cuda.synchronize()
         answers[name] = full.cpu().numpy()
         res[name] = {"build_s": statistics.mean(times) / 1000.0, "shortcuts": st["shortcuts"],
-                     "rounds": st["rounds"],
+                     "rounds": st["rounds"], "core_vertices": st["core_vertices"],
+                     "queries_per_s": nq_cmp / (e0.elapsed_time(e1) * 1e-3),
                      "mean_search_space": float(sett.cpu().numpy().view(np.uint32).mean())}
         h.close()
     line = {
         "metric": "learned vs edge-difference priority: CH build seconds, shortcut count, "
                   "mean upward search-space size",
-        "config": {"workload": "geo1M-learned", "vertices": g.n, "test_seed": 5,
-                   "train_graphs": args.train_graphs, "train_vertices_each": 256_000,
-                   "train_rows": int(rows.shape[0]), "train_epochs": args.train_epochs},
+        "config": {"workload": f"{args.workload}-learned", "vertices": g.n, "edges": int(g.m),
+                   "test_seed": test_seed, "train_graphs": args.train_graphs,
+                   "train_vertices_each": int(train_graph(seeds[0]).n) if rmat else 256_000,
+                   "train_rows": int(rows.shape[0]), "train_epochs": args.train_epochs,
+                   "cmax": cmax, "hop_limit": hop_limit, "witness_route_deg": route_deg},
+        "build_autotune": tune_rows,
         "results": res,
-        "distances_identical_1M_queries": bool(np.array_equal(answers["edge_difference"],
-                                                              answers["learned"])),
+        "distances_identical": bool(np.array_equal(answers["edge_difference"], answers["learned"])),
+        "queries_compared": nq_cmp,
         "train_loss_per_epoch": [float(x) for x in loss],
         "trace_seconds": t_traces, "train_seconds": t_train,
         "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 MLP / u32 graph",
@@ -355,7 +411,7 @@ def main():
     n, gseed, qseed, nq = WORKLOADS[args.workload]
     if args.queries is not None:
         nq = args.queries
-    g = I.geometric_knn_graph(n, seed=gseed)
+    g = make_graph(args.workload)
     s_h, t_h = I.random_pairs(n, nq, seed=qseed)
     off_d = torch.from_numpy(g.offsets.view(np.int64)).to(dev)
     tgt_d = torch.from_numpy(g.targets.view(np.int32)).to(dev)
@@ -371,7 +427,7 @@ def main():
 
     def step():
         h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
-                        hop_limit=args.hop_limit, stream=stream)
+                        hop_limit=args.hop_limit, stream=stream, max_candidates_per_vertex=args.cmax)
         if qcfg is not None:
             h.set_query_config(*qcfg)
         if not args.build_only:
@@ -405,7 +461,8 @@ def main():
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
             h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
-                            hop_limit=args.hop_limit, stream=stream)
+                            hop_limit=args.hop_limit, stream=stream,
+                            max_candidates_per_vertex=args.cmax)
             if qcfg is not None:
                 h.set_query_config(*qcfg)
             e1.record(stream)
@@ -475,17 +532,22 @@ def main():
             "ms_per_launch": stats["witness_ms"] / max(1, stats["witness_launches"]),
         }
     else:
-        q_bytes = 12 * q_exp + 8 * q_edges + 20 * nq
+        # with stalling each expansion also reads the other CSR's two offsets
+        stall = bool(qcfg[3]) if qcfg else False
+        q_bytes = (20 if stall else 12) * q_exp + 8 * q_edges + 20 * nq
         q_gbs = q_bytes / (mean_query * 1e-3) / 1e9
         roofline = {
             "kernel": "k_query_block (pruned bidirectional upward searches, one launch per batch)",
             "bound": "hbm", "achieved": round(q_gbs, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(q_gbs / peak, 4), "traffic": QUERY_TRAFFIC_PER_LAUNCH,
+            "frac": round(q_gbs / peak, 4),
+            "traffic": QUERY_TRAFFIC_PER_LAUNCH if args.workload == "geo1M" and nq == 1_000_000 else None,
             "peak_source": peak_src, "bytes_per_launch": q_bytes, "ms_per_launch": mean_query,
+            "launch": "one batch = the small-table pass + its overflow redo (two launches)",
             "expansions_per_query": q_exp / nq, "edges_per_query": q_edges / nq,
             "query_config": {"layout": ["block_flat", "warp_flat"][qcfg[0]] if qcfg else "default",
                              "threads": qcfg[1] if qcfg else None,
                              "small_tables_first": bool(qcfg[2]) if qcfg else None,
+                             "stall_on_demand": bool(qcfg[3]) if qcfg else None,
                              "autotune_ms": [round(float(x), 3) for x in tune_ms] if tune_ms is not None else None},
             "witness": {"achieved": round(wit_gbs, 1), "frac": round(wit_gbs / peak, 4),
                         "share_of_build": round(stats["witness_ms"] / mean_build, 3) if mean_build else None},
@@ -499,7 +561,7 @@ def main():
         for _ in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            hh = ch.CH.build(g, hop_limit=args.hop_limit)
+            hh = ch.CH.build(g, hop_limit=args.hop_limit, max_candidates_per_vertex=args.cmax)
             if qcfg is not None:
                 hh.set_query_config(*qcfg)
             t1 = time.perf_counter()
@@ -515,9 +577,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        scaled, raw, cores = cpu_sample_build(n, args.hop_limit)
+        scaled, raw, cores, sn = cpu_sample_build(args.workload, args.hop_limit, args.cmax)
         cpu = {"value": scaled, "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": f"oracle build of a 100000-vertex graph of the same family "
+               "sample": f"oracle build of a {sn}-vertex graph of the same family "
                          f"({raw:.2f} s, one thread), scaled linearly by vertex count to {n}"}
 
     if rank == 0:
@@ -527,6 +589,7 @@ def main():
             "ms_per_step": mean_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": args.workload, "vertices": n, "edges": int(g.m),
+                       "cmax": args.cmax, "core_vertices": stats["core_vertices"],
                        "queries": nq, "hop_limit": args.hop_limit,
                        "parallelism": f"replicas{world}",
                        "l2": "flushed before each step (2x L2 buffer write)"},

@@ -86,13 +86,31 @@ typedef struct {
  *              default 5.
  *   priority   CH_PRIO_EDGE_DIFF.
  *   tie_break  CH_TIE_HASHED (default) or CH_TIE_ID; tie_seed feeds the hash.
- *   max_candidates_per_vertex  must be UINT64_MAX (contract every vertex).
+ *   max_candidates_per_vertex  Cmax: a rescored vertex u with
+ *              |N_in(u)| * |N_out(u)| > Cmax is not eligible (not scored,
+ *              never selected) until a later rescoring finds it within the
+ *              bound. When a round finds no eligible vertex, the live
+ *              vertices form the core: they get that round's index as their
+ *              level (and score INT32_MAX - 1), their overlay edges become
+ *              E_up and E_down, and construction stops. Queries then also
+ *              search the core, so distances stay exact. UINT64_MAX (the
+ *              default) contracts every vertex.
  *   stream     cudaStream_t the build runs on (NULL: the legacy stream).
  *              ch_build returns after the work on it has finished.
  *   mlp_weights  host pointer to CH_MLP_NPARAM floats (CH_PRIO_LEARNED only;
  *              read during ch_build).
  *   trace      nonzero: record one row per rescoring (its features) and the
- *              priority each rescoring produced, for ch_export_trace. */
+ *              priority each rescoring produced, for ch_export_trace.
+ *   witness_route_deg  a witness source whose middles' out-degrees sum above
+ *              this runs on a block (8 warps) instead of one warp; 0 = 64.
+ *              Performance only: the hierarchy does not depend on it.
+ *   witness_ball_limit  θ, the settled-vertex cap of Alg. 3 read per hop
+ *              level: a witness search keeps only labels below its source's
+ *              heaviest candidate weight and stops after the first hop level
+ *              at which more than θ vertices (the source included) hold one;
+ *              the distances of that level replace d_H. Still upper bounds
+ *              on real walks, so distances stay exact (only more shortcuts
+ *              may be kept). 0 = no bound (the default). */
 typedef struct {
     uint32_t hop_limit;
     uint32_t priority;
@@ -102,7 +120,9 @@ typedef struct {
     void *stream;
     const float *mlp_weights;
     int32_t trace;
-    int32_t reserved;
+    uint32_t witness_route_deg;
+    uint32_t witness_ball_limit;
+    uint32_t reserved;
 } ch_params_t;
 
 /* Training parameters of ch_mlp_train (Adam, mean squared error). */
@@ -139,6 +159,7 @@ typedef struct {
     uint64_t witness_bytes;
     uint64_t witness_dense;     /* of which outgrew a block's tables too (global-memory path) */
     uint64_t trace_rows;        /* rescorings recorded (params.trace or CH_PRIO_LEARNED) */
+    uint64_t core_vertices;     /* vertices left uncontracted (finite max_candidates_per_vertex) */
 } ch_stats_t;
 
 /* Number of per-round statistics fields written by ch_get_round_stats, in
@@ -215,7 +236,10 @@ int ch_query_status(ch_t *ch, void *stream);
  * tables, which fit twice as many blocks per SM, and redoes only the
  * queries that overflow them on 4096-slot tables; 0 uses 4096-slot tables
  * only. Queries that overflow those go to a kernel with per-vertex label
- * arrays. Every configuration gives the same answers and search-space
+ * arrays. stall = 1 (warp layout only) skips expanding a vertex whose label
+ * a reached higher neighbour already beats through one edge ("stall on
+ * demand"; it applies to pruned searches, not to those that report search-
+ * space sizes). Every configuration gives the same answers and search-space
  * sizes. */
 #define CH_QUERY_BLOCK_FLAT 0u
 #define CH_QUERY_WARP_FLAT 1u
@@ -223,6 +247,7 @@ typedef struct {
     uint32_t layout;
     uint32_t threads;
     uint32_t small_first;
+    uint32_t stall;
 } ch_query_config_t;
 
 int ch_set_query_config(ch_t *ch, const ch_query_config_t *cfg);  /* CH_EINVAL on other values */
@@ -230,12 +255,42 @@ int ch_get_query_config(const ch_t *ch, ch_query_config_t *cfg);
 
 /* Times each configuration on `sample` seeded uniform random queries (a
  * warm-up run, then one run timed with CUDA events on `stream`) and keeps
- * the fastest for the handle. ms_out (or NULL) receives the 8 times, in the
- * order index = 4 * small_first + 2 * (layout == WARP_FLAT) +
- * (threads == 256); chosen (or NULL) the configuration kept. Waits for
+ * the fastest for the handle. ms_out (or NULL) receives the 12 times: index
+ * 4 * small_first + 2 * (layout == WARP_FLAT) + (threads == 256) without
+ * stalling, then 8 + 2 * small_first + (threads == 256) for the warp layout
+ * with stalling; chosen (or NULL) the configuration kept. Waits for
  * `stream`. */
 int ch_query_autotune(ch_t *ch, uint64_t sample, uint32_t seed, void *stream,
                       ch_query_config_t *chosen, double *ms_out);
+
+/* ---- Build autotuning ----
+ *
+ * Builds `graph` once per (hop limit, witness_route_deg) pair of the two
+ * lists, other parameters as in `params` (NULL: defaults), and times each
+ * build (ch_stats_t.build_ms) and a batch of `sample` seeded uniform random
+ * queries on it (a warm-up run, then one run timed with CUDA events on
+ * params->stream). A candidate's cost is
+ *     build_ms + query_ms * queries_per_build / sample;
+ * the cheapest hierarchy is returned in *out and the others are freed.
+ * results (or NULL) receives one row per candidate, hop limits outer, and
+ * *chosen (or NULL) the index of the kept one. The hop limit changes the
+ * hierarchy (every hop limit gives exact distances); the routing threshold
+ * does not. */
+typedef struct {
+    uint32_t hop_limit;
+    uint32_t witness_route_deg;
+    double build_ms;
+    double query_ms;
+    double cost;
+    uint64_t shortcuts;
+    uint64_t core_vertices;
+} ch_tune_row_t;
+
+int ch_build_autotune(const ch_graph_t *graph, const ch_params_t *params,
+                      const uint32_t *hop_limits, uint32_t n_hop,
+                      const uint32_t *route_degs, uint32_t n_route, uint64_t sample,
+                      double queries_per_build, ch_t **out, ch_tune_row_t *results,
+                      uint32_t *chosen);
 
 /* Work of the query searches since the previous call (then cleared), summed
  * over the handle's batches: out[0] = queued entries expanded, out[1] =

@@ -58,7 +58,7 @@ def _load():
         lib.orc_build.restype = C.c_int
         lib.orc_free.argtypes = [P]
         lib.orc_build2.argtypes = [u32, u64, P, P, P, u32, u32, u32, C.c_int, u64, P, P, P,
-                                   C.POINTER(P)]
+                                   u64, u64, C.POINTER(P)]
         lib.orc_build2.restype = C.c_int
         lib.orc_num_trace.argtypes = [P]
         lib.orc_num_trace.restype = u64
@@ -79,7 +79,7 @@ def _load():
             getattr(lib, name).restype = None
         lib.orc_query_batch.argtypes = [P, u64, P, P, P, P]
         lib.orc_query_batch.restype = None
-        lib.orc_round0_scores.argtypes = [u32, u64, P, P, P, u32, P]
+        lib.orc_round0_scores.argtypes = [u32, u64, P, P, P, u32, u64, P]
         lib.orc_normalize.argtypes = [u32, u64, P, P, P, P, P, P, P]
         lib.orc_hop_limited.argtypes = [u32, u64, P, P, P, u32, u32, P]
         lib.orc_dijkstra.argtypes = [u32, u64, P, P, P, u32, P]
@@ -148,14 +148,22 @@ class OracleCH:
             pass
 
 
+CMAX_ALL = (1 << 64) - 1
+
+
 def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int = 0,
-             trace: bool = False, replay=None) -> OracleCH:
+             trace: bool = False, replay=None, cmax: int = CMAX_ALL,
+             ball: int = CMAX_ALL) -> OracleCH:
     """Run the oracle's round algorithm on graph ``g`` (see ``oracle.cpp``).
 
     ``trace`` records the learned-priority features of every rescoring
     (``OracleCH.trace``: rows of round, vertex, 12 features; ``labels``).
     ``replay`` = (rounds, vertices, priorities) arrays replaces the edge
     difference by the given int32 priorities of each (round, vertex).
+    ``cmax`` bounds |N_in| * |N_out| of a contractible vertex; the vertices
+    left when none is eligible form the core. ``ball`` bounds each witness
+    search: it stops after the first hop level at which more than ``ball``
+    vertices hold a label (see ``oracle.cpp``).
     """
     lib = _load()
     args, keep = _graph_args(g)
@@ -168,7 +176,7 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
         ru = np.ascontiguousarray(replay[1], np.uint32)
         rpv = np.ascontiguousarray(replay[2], np.int32)
     rc = lib.orc_build2(*args, hop_limit, tie_break, tie_seed & 0xFFFFFFFF, int(trace),
-                        rr.size, _p(rr), _p(ru), _p(rpv), C.byref(h))
+                        rr.size, _p(rr), _p(ru), _p(rpv), int(cmax), int(ball), C.byref(h))
     if rc != 0:
         raise ValueError(f"oracle rejected the graph or parameters (status {rc})")
     n = g.n
@@ -208,11 +216,12 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
     return och
 
 
-def round0_scores(g, hop_limit: int = 5) -> np.ndarray:
-    """Scores P[u] of every vertex as round 0 computes them (Alg. 3 + 4)."""
+def round0_scores(g, hop_limit: int = 5, ball: int = None) -> np.ndarray:
+    """Scores P[u] of every vertex as round 0 computes them (Alg. 3 + 4),
+    with an optional witness ball bound."""
     args, keep = _graph_args(g)
     P = np.empty(g.n, np.int32)
-    rc = _load().orc_round0_scores(*args, hop_limit, _p(P))
+    rc = _load().orc_round0_scores(*args, hop_limit, CMAX_ALL if ball is None else int(ball), _p(P))
     if rc != 0:
         raise ValueError("invalid graph")
     return P

@@ -35,7 +35,12 @@
 //     distance d_H(a, b) = least weight of a walk a -> b with at most H edges
 //     in the current overlay graph (INF if none), which is exact and does not
 //     depend on any visiting order. The contracted vertex itself is not
-//     excluded from the search.
+//     excluded from the search. An optional ball bound stands in for the
+//     cap: the search from a stops after the first hop level h at which more
+//     than `ball` vertices hold a label below a's heaviest candidate weight,
+//     and d_h replaces d_H (still an upper bound on a real walk, so the
+//     distances stay exact; only more shortcuts may be kept). Unbounded by
+//     default.
 //   * Shortcut predicate: a candidate (v1, u, v2) with v1 != v2 is kept iff
 //     w(v1,u) + w(u,v2) <= d_H(v1, v2). For H >= 2 this is the paper's
 //     "equals the witness distance" test; for H < 2 it is its natural
@@ -57,6 +62,17 @@
 //     candidate whose via-weight is INF is never kept: it cannot lie on a
 //     path shorter than INF, so no representable distance needs it.
 //   * Rank: by (level, score at contraction, id), all ascending.
+//   * Candidate bound Cmax (partial hierarchy): a rescored vertex u with
+//     |N_in(u)| * |N_out(u)| > Cmax is not eligible: it is not scored (no
+//     witness search; its score becomes INT32_MAX - 1) and never selected,
+//     until a later rescoring finds it within the bound. When a round finds
+//     no eligible vertex, the live vertices form the core: they all get that
+//     round's index as their level, their overlay out- and in-edges become
+//     E_up and E_down as if contracted (no shortcuts), and construction
+//     stops; that last round has no statistics row. The upward searches of
+//     a query then also run every core-core edge in their direction, which
+//     is a full search inside the core. Cmax = 2^64 - 1 contracts every
+//     vertex.
 //
 // Why the result preserves every distance, for any H, tie-break or score:
 // take a shortest path in the round-r overlay between two vertices that
@@ -165,7 +181,13 @@ struct HopSearch {
 
     explicit HopSearch(uint32_t n) : prev(n, INF), cur(n, INF), seen(n, 0) {}
 
-    void run(const std::vector<Adj>& out, uint32_t s, uint32_t H) {
+    // Levels 1..H of a hop-synchronous search from s that keeps only labels
+    // below `bound` (a walk at or above the bound cannot decide a candidate:
+    // keep(via, d) holds for every via <= bound whenever d >= bound). After
+    // each level, if more than `ball` vertices (s included) hold a label, the
+    // search stops there and the labels of that level are its result.
+    void run(const std::vector<Adj>& out, uint32_t s, uint32_t H, uint32_t bound = INF,
+             uint64_t ball = ~uint64_t(0)) {
         for (uint32_t x : reached) {
             prev[x] = cur[x] = INF;
             seen[x] = 0;
@@ -181,7 +203,7 @@ struct HopSearch {
                 uint32_t dx = prev[x];
                 for (const auto& [y, wy] : out[x]) {
                     uint32_t nd = sat_add(dx, wy);
-                    if (nd < cur[y]) {
+                    if (nd < bound && nd < cur[y]) {
                         cur[y] = nd;
                         if (!seen[y]) {
                             seen[y] = 1;
@@ -191,6 +213,7 @@ struct HopSearch {
                 }
             }
             for (uint32_t x : reached) prev[x] = cur[x];
+            if (reached.size() > ball) break;
         }
     }
     uint32_t dist(uint32_t v) const { return seen[v] ? cur[v] : INF; }
@@ -202,10 +225,14 @@ uint64_t pair_key(uint32_t a, uint32_t b) { return (uint64_t(a) << 32) | b; }
 
 // Alg. 3 with the d_H reading: for every source s with an out-neighbour u in
 // `middle`, compute d_H from s and record it for every target v in N_out(u),
-// v != s. Returns the number of sources searched.
+// v != s. The search keeps labels below the heaviest candidate weight of s
+// and, with a finite ball bound, stops after the first level at which it
+// holds more than `ball` vertices (the settled-vertex cap of Alg. 3, read
+// per hop level). Returns the number of sources searched.
 uint64_t local_search(const Overlay& g, const std::vector<char>& middle,
                       const std::vector<uint32_t>& middle_list, uint32_t H,
-                      HopSearch& hs, std::unordered_map<uint64_t, uint32_t>& dist) {
+                      HopSearch& hs, std::unordered_map<uint64_t, uint32_t>& dist,
+                      uint64_t ball = ~uint64_t(0)) {
     std::vector<uint32_t> sources;
     for (uint32_t u : middle_list)
         for (const auto& [v1, w1] : g.in[u]) sources.push_back(v1);
@@ -213,7 +240,14 @@ uint64_t local_search(const Overlay& g, const std::vector<char>& middle,
     sources.erase(std::unique(sources.begin(), sources.end()), sources.end());
     dist.clear();
     for (uint32_t s : sources) {
-        hs.run(g.out, s, H);
+        uint32_t bound = 0;  // heaviest candidate weight of s
+        for (const auto& [u, w1] : g.out[s]) {
+            if (!middle[u]) continue;
+            for (const auto& [v, w2] : g.out[u])
+                if (v != s) bound = std::max(bound, sat_add(w1, w2));
+        }
+        if (bound == 0) continue;  // no candidate from s
+        hs.run(g.out, s, H, bound, ball);
         for (const auto& [u, w1] : g.out[s]) {
             if (!middle[u]) continue;
             for (const auto& [v, w2] : g.out[u]) {
@@ -311,9 +345,12 @@ std::array<int64_t, 12> features(const Overlay& g, const CH& ch, uint32_t u, int
 // Priorities to use instead of the edge difference, keyed by (round, vertex).
 using Replay = std::map<std::pair<uint32_t, uint32_t>, int32_t>;
 
+constexpr int32_t P_INELIGIBLE = 2147483646;  // INT32_MAX - 1
+
 void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
            const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t seed,
-           bool want_trace = false, const Replay* replay = nullptr) {
+           bool want_trace = false, const Replay* replay = nullptr,
+           uint64_t cmax = ~uint64_t(0), uint64_t ball = ~uint64_t(0)) {
     Overlay g;
     load(g, n, off, tgt, w);
     ch.ed_last.assign(n, 0);
@@ -338,19 +375,29 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
 
     std::vector<uint32_t> A(n);
     for (uint32_t u = 0; u < n; ++u) A[u] = u;
-    std::vector<char> inA(n, 0), inF(n, 0);
+    std::vector<char> inA(n, 0), inF(n, 0), eligible(n, 1);
 
     for (uint32_t r = 0; live > 0; ++r) {
         std::array<uint64_t, NSTAT> st{};
         st[ST_AFFECTED] = A.size();
 
+        // Eligibility under the candidate bound; only eligible members of A
+        // are scored.
+        std::vector<uint32_t> Ae;
+        for (uint32_t u : A) {
+            const uint64_t prod = uint64_t(g.in[u].size()) * uint64_t(g.out[u].size());
+            eligible[u] = prod <= cmax;
+            if (eligible[u]) Ae.push_back(u);
+            else ch.P[u] = P_INELIGIBLE;
+        }
+
         // Step 1: LocalSearch for the affected set.
-        for (uint32_t u : A) inA[u] = 1;
-        st[ST_SCORE_SOURCES] = local_search(g, inA, A, H, hs, dist);
+        for (uint32_t u : Ae) inA[u] = 1;
+        st[ST_SCORE_SOURCES] = local_search(g, inA, Ae, H, hs, dist, ball);
 
         // Step 2: Score (edge difference), or the replayed priority; the
         // features are taken from the same overlay.
-        for (uint32_t u : A) {
+        for (uint32_t u : Ae) {
             const int32_t ed = score_one(g, u, dist);
             if (want_trace) {
                 const auto f = features(g, ch, u, ed, r);
@@ -370,12 +417,12 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
                 ch.P[u] = ed;
             }
         }
-        for (uint32_t u : A) inA[u] = 0;
+        for (uint32_t u : Ae) inA[u] = 0;
 
         // Step 3: Select (strict local minimum of the key over N(u)).
         std::vector<uint32_t> F;
         for (uint32_t u = 0; u < n; ++u) {
-            if (!g.alive[u]) continue;
+            if (!g.alive[u] || !eligible[u]) continue;
             uint64_t ku = select_key(ch.P[u], u, tie_mode, seed);
             bool minimal = true;
             for (const auto& [v, wv] : g.out[u])
@@ -386,10 +433,22 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
         }
         st[ST_SELECTED] = F.size();
 
+        // No eligible vertex left: the live vertices are the core.
+        if (F.empty()) {
+            for (uint32_t u = 0; u < n; ++u) {
+                if (!g.alive[u]) continue;
+                ch.level[u] = r;
+                for (const auto& [x, wx] : g.out[u]) ch.up[u].push_back({x, wx});
+                for (const auto& [x, wx] : g.in[u]) ch.down[u].push_back({x, wx});
+                ch.label[u] = ch.ed_last[u] + ch.depth[u];
+            }
+            break;
+        }
+
         // Step 4: Contract. Witness distances for the candidates of V_F on
         // the same overlay.
         for (uint32_t u : F) inF[u] = 1;
-        st[ST_CONTRACT_SOURCES] = local_search(g, inF, F, H, hs, dist);
+        st[ST_CONTRACT_SOURCES] = local_search(g, inF, F, H, hs, dist, ball);
 
         std::map<std::pair<uint32_t, uint32_t>, std::pair<uint32_t, uint32_t>> best;
         for (uint32_t u : F) {
@@ -575,14 +634,14 @@ int orc_build(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
 int orc_build2(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
                const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t tie_seed,
                int want_trace, uint64_t nreplay, const uint32_t* rp_round, const uint32_t* rp_u,
-               const int32_t* rp_p, orc_ch** out) {
+               const int32_t* rp_p, uint64_t cmax, uint64_t ball, orc_ch** out) {
     if (!out || !validate(n, m, off, tgt, w) || tie_mode > 1) return ORC_EINVAL;
     Replay rp;
     for (uint64_t i = 0; i < nreplay; ++i) rp[{rp_round[i], rp_u[i]}] = rp_p[i];
     orc_ch* h = new orc_ch();
     try {
         build(h->ch, n, off, tgt, w, H, tie_mode, tie_seed, want_trace != 0,
-              nreplay ? &rp : nullptr);
+              nreplay ? &rp : nullptr, cmax, ball);
     } catch (const std::exception&) {
         delete h;
         return ORC_EINVAL;
@@ -671,7 +730,7 @@ void orc_query_batch(const orc_ch* h, uint64_t k, const uint32_t* s, const uint3
 
 // Scores of every vertex of the input graph as round 0 computes them.
 int orc_round0_scores(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
-                      const uint32_t* w, uint32_t H, int32_t* P) {
+                      const uint32_t* w, uint32_t H, uint64_t ball, int32_t* P) {
     if (!validate(n, m, off, tgt, w)) return ORC_EINVAL;
     Overlay g;
     load(g, n, off, tgt, w);
@@ -680,7 +739,7 @@ int orc_round0_scores(uint32_t n, uint64_t m, const uint64_t* off, const uint32_
     for (uint32_t u = 0; u < n; ++u) A[u] = u;
     HopSearch hs(n);
     std::unordered_map<uint64_t, uint32_t> dist;
-    local_search(g, inA, A, H, hs, dist);
+    local_search(g, inA, A, H, hs, dist, ball);
     for (uint32_t u = 0; u < n; ++u) P[u] = score_one(g, u, dist);
     return ORC_OK;
 }

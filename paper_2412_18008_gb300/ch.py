@@ -51,18 +51,27 @@ class ParamsT(C.Structure):
     _fields_ = [("hop_limit", C.c_uint32), ("priority", C.c_uint32), ("tie_break", C.c_uint32),
                 ("tie_seed", C.c_uint32), ("max_candidates_per_vertex", C.c_uint64),
                 ("stream", C.c_void_p), ("mlp_weights", C.c_void_p), ("trace", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("witness_route_deg", C.c_uint32), ("witness_ball_limit", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+class TuneRowT(C.Structure):
+    _fields_ = [("hop_limit", C.c_uint32), ("witness_route_deg", C.c_uint32),
+                ("build_ms", C.c_double), ("query_ms", C.c_double), ("cost", C.c_double),
+                ("shortcuts", C.c_uint64), ("core_vertices", C.c_uint64)]
 
 
 class QueryConfigT(C.Structure):
-    _fields_ = [("layout", C.c_uint32), ("threads", C.c_uint32), ("small_first", C.c_uint32)]
+    _fields_ = [("layout", C.c_uint32), ("threads", C.c_uint32), ("small_first", C.c_uint32),
+                ("stall", C.c_uint32)]
 
 
 CH_QUERY_BLOCK_FLAT = 0
 CH_QUERY_WARP_FLAT = 1
-# (layout, threads, small_first) in the autotuner's order
-QUERY_CONFIGS = tuple((lay, thr, sf) for sf in (0, 1) for lay in (CH_QUERY_BLOCK_FLAT, CH_QUERY_WARP_FLAT)
-                      for thr in (128, 256))
+# (layout, threads, small_first, stall) in the autotuner's order
+QUERY_CONFIGS = (tuple((lay, thr, sf, 0) for sf in (0, 1) for lay in (CH_QUERY_BLOCK_FLAT, CH_QUERY_WARP_FLAT)
+                       for thr in (128, 256)) +
+                 tuple((CH_QUERY_WARP_FLAT, thr, sf, 1) for sf in (0, 1) for thr in (128, 256)))
 
 
 class ServerParamsT(C.Structure):
@@ -84,7 +93,8 @@ class StatsT(C.Structure):
                 ("prep_ms", C.c_double), ("contract_ms", C.c_double), ("update_ms", C.c_double),
                 ("postprocess_ms", C.c_double), ("witness_ms", C.c_double),
                 ("witness_launches", C.c_uint64), ("witness_bytes", C.c_uint64),
-                ("witness_dense", C.c_uint64), ("trace_rows", C.c_uint64)]
+                ("witness_dense", C.c_uint64), ("trace_rows", C.c_uint64),
+                ("core_vertices", C.c_uint64)]
 
 
 _lib = None
@@ -134,6 +144,10 @@ def load(build_if_missing: bool = True):
     for f in ("ch_server_start", "ch_server_submit", "ch_server_poll", "ch_server_replay",
               "ch_server_stop"):
         getattr(lib, f).restype = C.c_int
+    lib.ch_build_autotune.argtypes = [C.POINTER(GraphT), C.POINTER(ParamsT), P, C.c_uint32, P,
+                                      C.c_uint32, C.c_uint64, C.c_double, C.POINTER(P),
+                                      C.POINTER(TuneRowT), C.POINTER(C.c_uint32)]
+    lib.ch_build_autotune.restype = C.c_int
     lib.ch_set_query_config.argtypes = [P, C.POINTER(QueryConfigT)]
     lib.ch_get_query_config.argtypes = [P, C.POINTER(QueryConfigT)]
     lib.ch_query_autotune.argtypes = [P, C.c_uint64, C.c_uint32, P, C.POINTER(QueryConfigT), P]
@@ -193,14 +207,10 @@ class CH:
         self._h = handle
 
     # -- construction -----------------------------------------------------
-    @classmethod
-    def build(cls, graph=None, *, n=None, offsets=None, targets=None, weights=None,
-              hop_limit: int = 5, tie_break: int = CH_TIE_HASHED, tie_seed: int = 0,
-              stream=None, mlp_weights=None, trace: bool = False) -> "CH":
-        """ch_build on a graph given as an ``inputs.Graph`` / NumPy CSR (host
-        memory) or as CUDA tensors ``offsets`` (int64), ``targets`` and
-        ``weights`` (int32 views of uint32 values) in device memory."""
-        lib = load()
+    @staticmethod
+    def _marshal(graph, n, offsets, targets, weights, hop_limit, tie_break, tie_seed, stream,
+                 mlp_weights, trace, max_candidates_per_vertex, witness_route_deg,
+                 witness_ball_limit=None):
         if graph is not None:
             n, offsets, targets, weights = graph.n, graph.offsets, graph.targets, graph.weights
         g = GraphT()
@@ -232,6 +242,10 @@ class CH:
         p.tie_seed = tie_seed & 0xFFFFFFFF
         p.stream = st
         p.trace = int(bool(trace))
+        p.witness_route_deg = int(witness_route_deg)
+        p.witness_ball_limit = 0 if witness_ball_limit is None else int(witness_ball_limit)
+        if max_candidates_per_vertex is not None:
+            p.max_candidates_per_vertex = int(max_candidates_per_vertex)
         if mlp_weights is not None:
             wts = np.ascontiguousarray(mlp_weights, dtype=np.float32)
             if wts.size != CH_MLP_NPARAM:
@@ -239,10 +253,52 @@ class CH:
             keep.append(wts)
             p.priority = CH_PRIO_LEARNED
             p.mlp_weights = wts.ctypes.data_as(C.c_void_p)
+        return g, p, keep
+
+    @classmethod
+    def build(cls, graph=None, *, n=None, offsets=None, targets=None, weights=None,
+              hop_limit: int = 5, tie_break: int = CH_TIE_HASHED, tie_seed: int = 0,
+              stream=None, mlp_weights=None, trace: bool = False,
+              max_candidates_per_vertex: int | None = None, witness_route_deg: int = 0,
+              witness_ball_limit: int | None = None) -> "CH":
+        """ch_build on a graph given as an ``inputs.Graph`` / NumPy CSR (host
+        memory) or as CUDA tensors ``offsets`` (int64), ``targets`` and
+        ``weights`` (int32 views of uint32 values) in device memory.
+        ``max_candidates_per_vertex`` (Cmax) bounds |N_in| * |N_out| of a
+        contractible vertex; None contracts every vertex.
+        ``witness_ball_limit`` (θ) stops a witness search after the first hop
+        level at which more than θ vertices hold a label; None = unbounded."""
+        g, p, keep = cls._marshal(graph, n, offsets, targets, weights, hop_limit, tie_break,
+                                  tie_seed, stream, mlp_weights, trace, max_candidates_per_vertex,
+                                  witness_route_deg, witness_ball_limit)
         h = C.c_void_p()
-        _check(lib.ch_build(C.byref(g), C.byref(p), C.byref(h)))
+        _check(load().ch_build(C.byref(g), C.byref(p), C.byref(h)))
         del keep
         return cls(h)
+
+    @classmethod
+    def build_autotune(cls, graph=None, *, hop_limits=(2, 3, 4, 5), route_degs=(32, 64, 128),
+                       sample: int = 1 << 15, queries_per_build: float = 1e6, n=None,
+                       offsets=None, targets=None, weights=None, tie_break: int = CH_TIE_HASHED,
+                       tie_seed: int = 0, stream=None, mlp_weights=None,
+                       max_candidates_per_vertex: int | None = None,
+                       witness_ball_limit: int | None = None):
+        """ch_build_autotune: builds once per (hop limit, routing threshold),
+        keeps the cheapest. Returns (CH, rows as dicts, chosen index)."""
+        g, p, keep = cls._marshal(graph, n, offsets, targets, weights, 5, tie_break, tie_seed,
+                                  stream, mlp_weights, False, max_candidates_per_vertex, 0,
+                                  witness_ball_limit)
+        hl = np.ascontiguousarray(hop_limits, dtype=np.uint32)
+        rd = np.ascontiguousarray(route_degs, dtype=np.uint32)
+        rows = (TuneRowT * (hl.size * rd.size))()
+        chosen = C.c_uint32()
+        h = C.c_void_p()
+        _check(load().ch_build_autotune(C.byref(g), C.byref(p), _hp(hl), hl.size, _hp(rd), rd.size,
+                                        sample, float(queries_per_build), C.byref(h), rows,
+                                        C.byref(chosen)))
+        del keep
+        out = [{f: getattr(r, f) for f, _ in TuneRowT._fields_} for r in rows]
+        return cls(h), out, int(chosen.value)
 
     # -- queries ----------------------------------------------------------
     def query(self, src, dst, want_settled: bool = False, stream=None):
@@ -281,23 +337,24 @@ class CH:
                                      stream_ptr))
 
     # -- query configuration, autotuning, work, graphs ----------------------
-    def set_query_config(self, layout: int, threads: int, small_first: int = 0):
-        _check(load().ch_set_query_config(self._h, C.byref(QueryConfigT(layout, threads, small_first))))
+    def set_query_config(self, layout: int, threads: int, small_first: int = 0, stall: int = 0):
+        _check(load().ch_set_query_config(self._h, C.byref(QueryConfigT(layout, threads, small_first,
+                                                                        stall))))
 
-    def query_config(self) -> tuple[int, int, int]:
+    def query_config(self) -> tuple[int, int, int, int]:
         c = QueryConfigT()
         _check(load().ch_get_query_config(self._h, C.byref(c)))
-        return c.layout, c.threads, c.small_first
+        return c.layout, c.threads, c.small_first, c.stall
 
     def autotune_queries(self, sample: int = 1 << 16, seed: int = 1, stream=None):
         """Time every query configuration on ``sample`` random queries and keep
-        the fastest. Returns (chosen (layout, threads, small_first), ms per
-        configuration in QUERY_CONFIGS order)."""
+        the fastest. Returns (chosen (layout, threads, small_first, stall), ms
+        per configuration in QUERY_CONFIGS order)."""
         c = QueryConfigT()
-        ms = np.zeros(8, np.float64)
+        ms = np.zeros(12, np.float64)
         _check(load().ch_query_autotune(self._h, sample, seed, _stream_ptr(stream), C.byref(c),
                                         _hp(ms)))
-        return (c.layout, c.threads, c.small_first), ms
+        return (c.layout, c.threads, c.small_first, c.stall), ms
 
     def query_work(self, stream=None) -> tuple[int, int]:
         """(expansions, edges scanned) of the query searches since the last call."""

@@ -80,6 +80,8 @@ void ch_default_params(ch_params_t *p) {
     p->stream = nullptr;
     p->mlp_weights = nullptr;
     p->trace = 0;
+    p->witness_route_deg = 0;
+    p->witness_ball_limit = 0;
     p->reserved = 0;
 }
 
@@ -101,10 +103,6 @@ int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out) {
     }
     if (p.tie_break > CH_TIE_ID) {
         g_last_error = "unknown tie_break";
-        return CH_EINVAL;
-    }
-    if (p.max_candidates_per_vertex != UINT64_MAX) {
-        g_last_error = "max_candidates_per_vertex must be UINT64_MAX";
         return CH_EINVAL;
     }
     if (g->n == 0xFFFFFFFFu) {
@@ -140,7 +138,8 @@ int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out) {
         h->stats.witness_ms = h->t_witness_ms;
         h->stats.witness_launches = h->witness_launches;
         h->stats.witness_bytes = h->witness_bytes;
-        h->stats.trace_rows = h->trace_rows;
+        h->stats.trace_rows = h->trace_valid;
+        h->stats.core_vertices = h->core_size;
     });
     if (rc != CH_OK) {
         delete h;
@@ -187,12 +186,69 @@ int ch_query_batch_static(ch_t *ch, const uint32_t *src, const uint32_t *dst, ui
     });
 }
 
+int ch_build_autotune(const ch_graph_t *graph, const ch_params_t *params, const uint32_t *hop_limits,
+                      uint32_t n_hop, const uint32_t *route_degs, uint32_t n_route, uint64_t sample,
+                      double queries_per_build, ch_t **out, ch_tune_row_t *results, uint32_t *chosen) {
+    if (!graph || !out || !hop_limits || !route_degs || n_hop == 0 || n_route == 0 || sample == 0 ||
+        !(queries_per_build >= 0)) {
+        g_last_error = "bad autotune arguments";
+        return CH_EINVAL;
+    }
+    ch_params_t base;
+    if (params) base = *params;
+    else ch_default_params(&base);
+    ch_t *best = nullptr;
+    double best_cost = 0;
+    uint32_t best_i = 0;
+    for (uint32_t i = 0; i < n_hop; ++i)
+        for (uint32_t j = 0; j < n_route; ++j) {
+            ch_params_t p = base;
+            p.hop_limit = hop_limits[i];
+            p.witness_route_deg = route_degs[j];
+            ch_t *h = nullptr;
+            int rc = ch_build(graph, &p, &h);
+            if (rc != CH_OK) {
+                if (best) ch_free(best);
+                return rc;
+            }
+            double qms = 0;
+            rc = guarded([&] { qms = query_time_sample(h, sample, 1234u + i, (cudaStream_t)p.stream); });
+            if (rc != CH_OK) {
+                ch_free(h);
+                if (best) ch_free(best);
+                return rc;
+            }
+            const double cost = h->stats.build_ms + qms * queries_per_build / (double)sample;
+            const uint32_t k = i * n_route + j;
+            if (results) {
+                results[k].hop_limit = p.hop_limit;
+                results[k].witness_route_deg = p.witness_route_deg;
+                results[k].build_ms = h->stats.build_ms;
+                results[k].query_ms = qms;
+                results[k].cost = cost;
+                results[k].shortcuts = h->stats.shortcuts;
+                results[k].core_vertices = h->stats.core_vertices;
+            }
+            if (!best || cost < best_cost) {
+                if (best) ch_free(best);
+                best = h;
+                best_cost = cost;
+                best_i = k;
+            } else {
+                ch_free(h);
+            }
+        }
+    *out = best;
+    if (chosen) *chosen = best_i;
+    return CH_OK;
+}
+
 int ch_set_query_config(ch_t *ch, const ch_query_config_t *cfg) {
     if (!ch || !cfg) {
         g_last_error = "null argument";
         return CH_EINVAL;
     }
-    return guarded([&] { query_set_config(ch, cfg->layout, cfg->threads, cfg->small_first); });
+    return guarded([&] { query_set_config(ch, cfg->layout, cfg->threads, cfg->small_first, cfg->stall); });
 }
 
 int ch_get_query_config(const ch_t *ch, ch_query_config_t *cfg) {
@@ -203,6 +259,7 @@ int ch_get_query_config(const ch_t *ch, ch_query_config_t *cfg) {
     cfg->layout = ch->q_layout;
     cfg->threads = ch->q_threads;
     cfg->small_first = ch->q_small_first;
+    cfg->stall = ch->q_stall;
     return CH_OK;
 }
 
@@ -413,12 +470,16 @@ int ch_export_trace(const ch_t *ch, int64_t *rows, int32_t *prio, int32_t *label
         std::vector<int32_t> pr(k);
         CH_CUDA_TRY(cudaMemcpy(r.data(), ch->trace.ptr, k * 14 * sizeof(long long), cudaMemcpyDeviceToHost));
         CH_CUDA_TRY(cudaMemcpy(pr.data(), ch->trace_prio.ptr, k * 4, cudaMemcpyDeviceToHost));
-        std::vector<uint64_t> idx(k);
-        std::iota(idx.begin(), idx.end(), 0);
+        // rows of rescorings that were not eligible are marked with round -1
+        std::vector<uint64_t> idx;
+        idx.reserve(ch->trace_valid);
+        for (uint64_t i = 0; i < k; ++i)
+            if (r[i * 14] >= 0) idx.push_back(i);
+        if (idx.size() != ch->trace_valid) throw Error{CH_ECUDA, "internal: trace row count"};
         std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t b) {
             return std::make_pair(r[a * 14], r[a * 14 + 1]) < std::make_pair(r[b * 14], r[b * 14 + 1]);
         });
-        for (uint64_t i = 0; i < k; ++i) {
+        for (uint64_t i = 0; i < idx.size(); ++i) {
             if (rows)
                 for (int c = 0; c < 14; ++c) rows[i * 14 + c] = r[idx[i] * 14 + c];
             if (prio) prio[i] = pr[idx[i]];

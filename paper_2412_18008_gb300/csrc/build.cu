@@ -72,6 +72,7 @@ struct Ctl {
     unsigned long long relocOut, relocIn;
     unsigned long long wit_sources, wit_fallback, wit_vertices, wit_edges, wit_middles,
         wit_midedges, wit_block;
+    unsigned long long trace_valid;  // trace rows of eligible rescorings
 };
 
 struct Dev {
@@ -90,7 +91,17 @@ struct Dev {
     // learned-priority bookkeeping (see k_features)
     uint32_t *cn, *depth, *rescore, *orig_deg;
     int32_t *ed_last, *label;
+    // candidate bound: a rescored vertex with |N_in| * |N_out| > cmax is not
+    // eligible (not scored, never selected) until rescored within the bound
+    uint64_t cmax;
+    uint8_t *inel;
+    // witness ball bound: a search stops after the first hop level at which
+    // more than `ball` vertices (the source included) hold a label
+    uint32_t ball;
 };
+
+constexpr int32_t P_INELIGIBLE = 2147483646;  // INT32_MAX - 1
+constexpr uint32_t AMARK_NONE = 0xFFFFFFFFu;   // never a round index
 
 struct WArgs {
     Dev d;
@@ -112,9 +123,14 @@ struct WArgs {
 
 struct Dense {
     uint32_t *dist, *fst, *fa, *fb, *fda, *fdb, *touched, *mt;
+    uint32_t *direct;  // weight of the edge (s, v) of the current source s, INF if none
     unsigned long long *merge;
     uint32_t nslots;
 };
+
+// Sources with more out-edges than this skip the shared-memory tiers (their
+// balls and existing-edge checks belong to the global-memory tier).
+constexpr uint32_t DENSE_SD = 1024;
 
 __device__ __forceinline__ uint64_t select_key(const Dev &d, uint32_t v) {
     uint32_t hi = (uint32_t)d.P[v] ^ 0x80000000u;
@@ -261,20 +277,42 @@ __global__ void k_iota(uint32_t *a, uint32_t n) {
 // Step 1: rescoring set and witness sources
 // --------------------------------------------------------------------------
 
+// One warp per rescored vertex u: its score starts at the edge term, and its
+// in-neighbours become witness sources (each once per round).
 __global__ void k_score_prep(Dev d, const uint32_t *A, uint32_t nA, uint32_t stamp,
                              uint32_t *S) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nA;
-         i += gridDim.x * blockDim.x) {
-        uint32_t u = A[i];
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nA; i += nwarps) {
+        const uint32_t u = A[i];
         if (!id_ok(d, u)) continue;
-        uint32_t od = d.out_deg[u], id = d.in_deg[u];
-        d.P[u] = -(int32_t)(od + id);
-        uint64_t ib = d.in_beg[u];
+        const uint32_t od = d.out_deg[u], id = d.in_deg[u];
+        if ((uint64_t)od * id > d.cmax) {
+            // not eligible: no score, and not a middle of this round's
+            // score searches
+            if (lane == 0) {
+                d.inel[u] = 1;
+                d.P[u] = P_INELIGIBLE;
+                d.amark[u] = AMARK_NONE;
+            }
+            continue;
+        }
+        if (lane == 0) {
+            d.inel[u] = 0;
+            d.P[u] = -(int32_t)(od + id);
+        }
+        const uint64_t ib = d.in_beg[u];
         if (!in_list_ok(d, ib, id)) continue;
-        for (uint32_t j = 0; j < id; ++j) {
-            uint32_t v1 = d.in_adj[ib + j].x;
-            if (!id_ok(d, v1)) continue;
-            if (atomicExch(&d.smark[v1], stamp) != stamp) S[atomicAdd(&d.ctl->nS, 1u)] = v1;
+        for (uint32_t j0 = 0; j0 < id; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            bool add = false;
+            uint32_t v1 = 0;
+            if (j < id) {
+                v1 = d.in_adj[ib + j].x;
+                add = id_ok(d, v1) && atomicExch(&d.smark[v1], stamp) != stamp;
+            }
+            const uint32_t pos = warp_append(add, &d.ctl->nS);
+            if (add) S[pos] = v1;
         }
     }
 }
@@ -300,7 +338,7 @@ __device__ __forceinline__ uint32_t ht_hash(uint32_t v, int bits) {
 
 // Slot of v in an open-addressing table (inserting it if absent), or EMPTY
 // when the table is full.
-__device__ __forceinline__ uint32_t ht_insert(uint32_t *keys, int bits, uint32_t v) {
+__device__ __forceinline__ uint32_t ht_insert(uint32_t *keys, int bits, uint32_t v, bool *created = nullptr) {
     const uint32_t mask = (1u << bits) - 1u;
     uint32_t h = ht_hash(v, bits);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
@@ -308,7 +346,11 @@ __device__ __forceinline__ uint32_t ht_insert(uint32_t *keys, int bits, uint32_t
         if (k == v) return h;
         if (k == EMPTY) {
             uint32_t old = atomicCAS(&keys[h], EMPTY, v);
-            if (old == EMPTY || old == v) return h;
+            if (old == EMPTY) {
+                if (created) *created = true;
+                return h;
+            }
+            if (old == v) return h;
         }
         h = (h + 1) & mask;
     }
@@ -358,6 +400,10 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         const uint32_t sd = d.out_deg[s];
         if (sb + sd > d.out_arena) {
             if (lane == 0) atomicOr(&ctl->err, ERR_BOUND);
+            continue;
+        }
+        if (sd > DENSE_SD) {  // a hub: straight to the global-memory tier
+            if (lane == 0) a.ovf2[atomicAdd(&ctl->nOvf2, 1u)] = s;
             continue;
         }
         // Algorithmic-traffic counters of this source, added to the totals
@@ -422,13 +468,15 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         // made warp-uniform by __shfl_sync / __any_sync, never by polling
         // shared memory.
         uint32_t nfront = 1;
+        uint32_t nkeys = 1;  // vertices holding a label (the ball), warp-uniform
         bool overflowed = false;
         uint32_t cur = 0;
-        for (uint32_t lvl = 1; lvl <= d.H && nfront > 0; ++lvl) {
+        for (uint32_t lvl = 1; lvl <= d.H && nfront > 0 && nkeys <= d.ball; ++lvl) {
             const uint32_t nxt = cur ^ 1u;
             if (lane == 0) w.nf[nxt] = 0;
             __syncwarp();
             bool ovf = false;
+            uint32_t l_created = 0;
             for (uint32_t f0 = 0; f0 < nfront; f0 += 32) {
                 const uint32_t fi = f0 + lane;
                 const bool fv = fi < nfront;
@@ -452,7 +500,9 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                         const uint2 e = d.out_adj[xb_o + (idx - ex_o)];
                         const uint32_t nd = sat_add(dx_o, e.y);
                         if (nd < bound && id_ok(d, e.x)) {
-                            const uint32_t slot = ht_insert(w.key, WIT_TBITS, e.x);
+                            bool created = false;
+                            const uint32_t slot = ht_insert(w.key, WIT_TBITS, e.x, &created);
+                            l_created += created;
                             if (slot == EMPTY) {
                                 ovf = true;
                             } else {
@@ -472,6 +522,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                 overflowed = true;
                 break;
             }
+            nkeys += warp_sum(l_created);
             uint32_t nn = 0;
             if (lane == 0) nn = w.nf[nxt];
             nn = __shfl_sync(FULL, nn, 0);
@@ -642,7 +693,7 @@ struct BlkSmem {
     unsigned long long mval[WB_M];
     uint32_t cntw[WB_THREADS / 32][32];
     uint32_t nf[2];
-    uint32_t item, ovf, bound, nnew;
+    uint32_t item, ovf, bound, nnew, nkeys;
 };
 
 template <int MODE>
@@ -672,6 +723,10 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
         const uint32_t sd = d.out_deg[s];
         if (sb + sd > d.out_arena) {
             if (tid == 0) atomicOr(&ctl->err, ERR_BOUND);
+            continue;
+        }
+        if (sd > DENSE_SD) {  // a hub: straight to the global-memory tier
+            if (tid == 0) a.ovf2[atomicAdd(&ctl->nOvf2, 1u)] = s;
             continue;
         }
         unsigned long long l_vert = 0, l_edge = 0, l_mid = 0, l_midedge = 0, l_cand = 0, l_kept = 0;
@@ -720,6 +775,7 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             b.front[0][0] = make_uint2(h, 0);
             b.nf[0] = 1;
             b.nf[1] = 0;
+            b.nkeys = 1;
         }
         // Phase 1: hop-limited Bellman-Ford, one level per iteration, each
         // level relaxing from the previous level's values (snapshots).
@@ -728,8 +784,9 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             __syncthreads();
             const uint32_t nfront = b.nf[cur];
             const uint32_t ovf = b.ovf;
+            const uint32_t nkeys = b.nkeys;
             __syncthreads();
-            if (ovf || nfront == 0) break;
+            if (ovf || nfront == 0 || nkeys > d.ball) break;
             const uint32_t nxt = cur ^ 1u;
             if (tid == 0) b.nf[nxt] = 0;
             __syncthreads();
@@ -759,7 +816,9 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
                     const uint2 e = d.out_adj[xb_o + (idx - ex_o)];
                     const uint32_t nd = sat_add(dx_o, e.y);
                     if (nd >= bound || !id_ok(d, e.x)) continue;
-                    const uint32_t slot = ht_insert(b.key, WB_TBITS, e.x);
+                    bool created = false;
+                    const uint32_t slot = ht_insert(b.key, WB_TBITS, e.x, &created);
+                    if (created) atomicAdd(&b.nkeys, 1u);
                     if (slot == EMPTY) {
                         b.ovf = 1;
                         continue;
@@ -915,7 +974,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
     const size_t base = (size_t)blockIdx.x * n;
     uint32_t *dist = dn.dist + base, *fst = dn.fst + base, *touched = dn.touched + base;
     uint32_t *fa = dn.fa + base, *fb = dn.fb + base, *fda = dn.fda + base, *fdb = dn.fdb + base;
-    uint32_t *mt = dn.mt + base;
+    uint32_t *mt = dn.mt + base, *direct = dn.direct + base;
     unsigned long long *merge = dn.merge + base;
     __shared__ uint32_t s_item, s_bound, s_nt, s_nm, s_nf[2];
     __shared__ unsigned long long s_cnt[5];
@@ -963,18 +1022,32 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
         __syncthreads();
         const uint32_t bound = s_bound;
         uint32_t *cur = fa, *curd = fda, *nx = fb, *nxd = fdb;
+        const uint32_t lane = lane_id(), warp = tid >> 5, nwarps = blockDim.x >> 5;
         for (uint32_t lvl = 1; lvl <= d.H && bound > 0; ++lvl) {
             const uint32_t nf = s_nf[(lvl - 1) & 1];
             __syncthreads();
             if (tid == 0) s_nf[lvl & 1] = 0;
             __syncthreads();
-            for (uint32_t f = tid; f < nf; f += blockDim.x) {
-                const uint32_t x = cur[f], dx = curd[f];
-                const uint64_t xb = d.out_beg[x];
-                const uint32_t xd = out_list_ok(d, xb, d.out_deg[x]) ? d.out_deg[x] : 0;
-                for (uint32_t j = 0; j < xd; ++j) {
-                    const uint2 e = d.out_adj[xb + j];
-                    const uint32_t nd = sat_add(dx, e.y);
+            // each warp takes 32 frontier entries and spreads their out-edges
+            // over its lanes
+            for (uint32_t f0 = warp * 32; f0 < nf; f0 += nwarps * 32) {
+                const uint32_t f = f0 + lane;
+                const bool fv = f < nf;
+                const uint32_t x = fv ? cur[f] : 0, dx = fv ? curd[f] : 0;
+                const uint64_t xb = fv ? d.out_beg[x] : 0;
+                const uint32_t xd = (fv && out_list_ok(d, xb, d.out_deg[x])) ? d.out_deg[x] : 0;
+                const uint32_t incl = warp_incl_scan(xd);
+                const uint32_t total = __shfl_sync(FULL, incl, 31);
+                const uint32_t excl = incl - xd;
+                for (uint32_t b0 = 0; b0 < total; b0 += 32) {
+                    const uint32_t idx = b0 + lane;
+                    const uint32_t o = warp_owner(excl, idx);
+                    const uint64_t xb_o = __shfl_sync(FULL, xb, o);
+                    const uint32_t dx_o = __shfl_sync(FULL, dx, o);
+                    const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                    if (idx >= total) continue;
+                    const uint2 e = d.out_adj[xb_o + (idx - ex_o)];
+                    const uint32_t nd = sat_add(dx_o, e.y);
                     if (nd >= bound || !id_ok(d, e.x)) continue;
                     const uint32_t old = atomicMin(&dist[e.x], nd);
                     if (nd < old) {
@@ -992,7 +1065,15 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             curd = nxd;
             nx = t1;
             nxd = t2;
-            if (nn == 0) break;
+            if (nn == 0 || s_nt > d.ball) break;  // s_nt: vertices holding a label
+        }
+        // the source's direct edges, for the existing-edge test
+        if (MODE == MODE_PRUNE) {
+            for (uint32_t j = tid; j < sd; j += blockDim.x) {
+                const uint2 e = d.out_adj[sb + j];
+                if (e.x < n) direct[e.x] = e.y;
+            }
+            __syncthreads();
         }
         // decisions
         unsigned long long l_cand = 0, l_kept = 0;
@@ -1031,16 +1112,8 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
                 const unsigned long long mv = merge[v2];
                 merge[v2] = ~0ull;
                 const uint32_t ws = (uint32_t)(mv >> 32), via = (uint32_t)mv;
-                bool found = false;
-                uint32_t ew = INF;
-                for (uint32_t j = 0; j < sd; ++j) {
-                    const uint2 e = d.out_adj[sb + j];
-                    if (e.x == v2) {
-                        found = true;
-                        ew = e.y;
-                        break;
-                    }
-                }
+                const uint32_t ew = direct[v2];
+                const bool found = ew != INF;
                 if (found && !(ws < ew)) continue;
                 const uint32_t pos = atomicAdd(&ctl->nRec, 1u);
                 if (pos < a.rec_cap) {
@@ -1074,6 +1147,11 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             dist[v] = INF;
             fst[v] = 0;
         }
+        if (MODE == MODE_PRUNE)
+            for (uint32_t j = tid; j < sd; j += blockDim.x) {
+                const uint2 e = d.out_adj[sb + j];
+                if (e.x < n) direct[e.x] = INF;
+            }
     }
 }
 
@@ -1091,6 +1169,11 @@ __global__ void k_features(Dev d, const uint32_t *A, uint32_t nA, uint32_t r, lo
          i += gridDim.x * blockDim.x) {
         const uint32_t u = A[i];
         if (!id_ok(d, u)) continue;
+        if (d.inel[u]) {  // not scored: a row marked with round -1 (dropped on export)
+            if (rows) rows[(uint64_t)i * 14] = -1;
+            continue;
+        }
+        if (rows) atomicAdd(&d.ctl->trace_valid, 1ull);
         const uint64_t ob = d.out_beg[u], ib = d.in_beg[u];
         const uint32_t od = out_list_ok(d, ob, d.out_deg[u]) ? d.out_deg[u] : 0;
         const uint32_t id = in_list_ok(d, ib, d.in_deg[u]) ? d.in_deg[u] : 0;
@@ -1141,6 +1224,10 @@ __global__ void k_apply_learned(Dev d, const uint32_t *A, uint32_t nA, const flo
          i += gridDim.x * blockDim.x) {
         const uint32_t u = A[i];
         if (!id_ok(d, u)) continue;
+        if (d.inel[u]) {
+            if (log) log[i] = P_INELIGIBLE;
+            continue;
+        }
         float v = y[i] * 1024.f;
         if (!(v == v)) v = 0.f;  // NaN
         v = fminf(fmaxf(v, -1073741824.f), 1073741824.f);
@@ -1204,7 +1291,7 @@ __global__ void k_select(Dev d, const uint32_t *VO, uint32_t nVO, uint32_t r, ui
             const uint32_t lo = max(excl, b), hi = min(excl + c, b + 32);
             if (hi > lo && (B & lane_bits(lo - b, hi - b))) beaten = true;
         }
-        const bool sel = uok && !beaten;
+        const bool sel = uok && !beaten && !d.inel[u];
         if (sel) d.level[u] = r;
         const uint32_t pos = warp_append(sel, &d.ctl->nF);
         if (sel) F[pos] = u;
@@ -1215,29 +1302,46 @@ __global__ void k_select(Dev d, const uint32_t *VO, uint32_t nVO, uint32_t r, ui
 // Step 4: contraction bookkeeping for V_F
 // --------------------------------------------------------------------------
 
+// One warp per selected vertex u: counts its candidates and edges, and
+// marks its neighbours as next round's affected set and its in-neighbours as
+// the contraction phase's witness sources (each once).
 __global__ void k_contract_prep(Dev d, const uint32_t *F, uint32_t src_stamp, uint32_t next_r,
                                 uint32_t *S2, uint32_t *Anext) {
     const uint32_t nF = d.ctl->nF;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF;
-         i += gridDim.x * blockDim.x) {
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nF; i += nwarps) {
         const uint32_t u = F[i];
         if (!id_ok(d, u)) continue;
         const uint64_t ob = d.out_beg[u], ib = d.in_beg[u];
         const uint32_t od = out_list_ok(d, ob, d.out_deg[u]) ? d.out_deg[u] : 0;
         const uint32_t id = in_list_ok(d, ib, d.in_deg[u]) ? d.in_deg[u] : 0;
-        atomicAdd(&d.ctl->candBound, (unsigned long long)od * id);
-        atomicAdd(&d.ctl->degFout, (unsigned long long)od);
-        atomicAdd(&d.ctl->degFin, (unsigned long long)id);
-        for (uint32_t j = 0; j < id + od; ++j) {
-            const uint32_t x = j < id ? d.in_adj[ib + j].x : d.out_adj[ob + (j - id)].x;
-            if (!id_ok(d, x)) continue;
-            if (j < id && atomicExch(&d.smark[x], src_stamp) != src_stamp)
-                S2[atomicAdd(&d.ctl->nS2, 1u)] = x;
-            if (atomicExch(&d.amark[x], next_r) != next_r) {
-                Anext[atomicAdd(&d.ctl->nAnext, 1u)] = x;
-                atomicAdd(&d.ctl->degAnext, (unsigned long long)(d.out_deg[x] + d.in_deg[x]));
-            }
+        if (lane == 0) {
+            atomicAdd(&d.ctl->candBound, (unsigned long long)od * id);
+            atomicAdd(&d.ctl->degFout, (unsigned long long)od);
+            atomicAdd(&d.ctl->degFin, (unsigned long long)id);
         }
+        unsigned long long deg_sum = 0;
+        for (uint32_t j0 = 0; j0 < id + od; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            bool src = false, aff = false;
+            uint32_t x = 0;
+            if (j < id + od) {
+                x = j < id ? d.in_adj[ib + j].x : d.out_adj[ob + (j - id)].x;
+                if (id_ok(d, x)) {
+                    src = j < id && atomicExch(&d.smark[x], src_stamp) != src_stamp;
+                    aff = atomicExch(&d.amark[x], next_r) != next_r;
+                    if (aff) deg_sum += d.out_deg[x] + d.in_deg[x];
+                }
+            }
+            const uint32_t ps = warp_append(src, &d.ctl->nS2);
+            if (src) S2[ps] = x;
+            const uint32_t pa = warp_append(aff, &d.ctl->nAnext);
+            if (aff) Anext[pa] = x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) deg_sum += __shfl_xor_sync(FULL, deg_sum, o);
+        if (lane == 0 && deg_sum) atomicAdd(&d.ctl->degAnext, deg_sum);
     }
 }
 
@@ -1245,72 +1349,95 @@ __global__ void k_contract_prep(Dev d, const uint32_t *F, uint32_t src_stamp, ui
 // Steps 6-9: CH edges, list maintenance, insertion
 // --------------------------------------------------------------------------
 
+// One warp per selected vertex u: its out-edges become E_up, its in-edges
+// E_down. With core set, F is the live list of a round that found no
+// eligible vertex: every live vertex gets level r and its overlay edges, and
+// no neighbour bookkeeping is done (the build ends).
 __global__ void k_emit_ch(Dev d, const uint32_t *F, uint32_t nF, uint2 *ch_up, uint2 *ch_dn,
                           uint64_t *up_beg, uint32_t *up_deg, uint64_t *dn_beg,
-                          uint32_t *dn_deg, uint64_t up_cap, uint64_t dn_cap) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF;
-         i += gridDim.x * blockDim.x) {
+                          uint32_t *dn_deg, uint64_t up_cap, uint64_t dn_cap, bool core, uint32_t r) {
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nF; i += nwarps) {
         const uint32_t u = F[i];
         if (!id_ok(d, u)) continue;
         const uint64_t ob = d.out_beg[u], ib = d.in_beg[u];
         const uint32_t od = out_list_ok(d, ob, d.out_deg[u]) ? d.out_deg[u] : 0;
         const uint32_t id = in_list_ok(d, ib, d.in_deg[u]) ? d.in_deg[u] : 0;
-        const uint64_t pu = atomicAdd(&d.ctl->ch_up_tail, (unsigned long long)od);
-        const uint64_t pd = atomicAdd(&d.ctl->ch_dn_tail, (unsigned long long)id);
+        unsigned long long pu = 0, pd = 0;
+        if (lane == 0) {
+            pu = atomicAdd(&d.ctl->ch_up_tail, (unsigned long long)od);
+            pd = atomicAdd(&d.ctl->ch_dn_tail, (unsigned long long)id);
+        }
+        pu = __shfl_sync(FULL, pu, 0);
+        pd = __shfl_sync(FULL, pd, 0);
         if (pu + od > up_cap || pd + id > dn_cap) {
-            atomicOr(&d.ctl->err, ERR_CH_OVERFLOW);
+            if (lane == 0) atomicOr(&d.ctl->err, ERR_CH_OVERFLOW);
             continue;
         }
-        for (uint32_t j = 0; j < od; ++j) ch_up[pu + j] = d.out_adj[ob + j];
-        for (uint32_t j = 0; j < id; ++j) ch_dn[pd + j] = d.in_adj[ib + j];
-        // learned-priority bookkeeping: the label of u, and its neighbours
-        // inherit depth and count the removed edges (V_F is independent, so
-        // no neighbour is being contracted and depth[u] is stable here)
+        for (uint32_t j = lane; j < od; j += 32) ch_up[pu + j] = d.out_adj[ob + j];
+        for (uint32_t j = lane; j < id; j += 32) ch_dn[pd + j] = d.in_adj[ib + j];
         const uint32_t du = d.depth[u];
-        d.label[u] = d.ed_last[u] + (int32_t)du;
-        for (uint32_t j = 0; j < od + id; ++j) {
+        if (lane == 0) {
+            up_beg[u] = pu;
+            up_deg[u] = od;
+            dn_beg[u] = pd;
+            dn_deg[u] = id;
+            if (core) d.level[u] = r;
+            d.label[u] = d.ed_last[u] + (int32_t)du;
+        }
+        if (core) continue;
+        // learned-priority bookkeeping: neighbours inherit depth and count
+        // the removed edges (V_F is independent, so no neighbour is being
+        // contracted and depth[u] is stable here)
+        for (uint32_t j = lane; j < od + id; j += 32) {
             const uint32_t x = j < od ? d.out_adj[ob + j].x : d.in_adj[ib + (j - od)].x;
             if (!id_ok(d, x)) continue;
             atomicAdd(&d.cn[x], 1u);
             atomicMax(&d.depth[x], du + 1);
         }
-        up_beg[u] = pu;
-        up_deg[u] = od;
-        dn_beg[u] = pd;
-        dn_deg[u] = id;
     }
 }
 
+// Stable in-place removal of this round's contracted vertices from a list,
+// by one warp (32 entries per step; writes never pass the reads).
+__device__ __forceinline__ uint32_t warp_compact_list(const Dev &d, uint2 *adj, uint64_t b, uint32_t dg,
+                                                      uint32_t r) {
+    const uint32_t lane = lane_id();
+    uint32_t k = 0;
+    for (uint32_t j0 = 0; j0 < dg; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        uint2 e = make_uint2(0, 0);
+        bool keep = false;
+        if (j < dg) {
+            e = adj[b + j];
+            keep = id_ok(d, e.x) && d.level[e.x] != r;
+        }
+        const uint32_t m = __ballot_sync(FULL, keep);
+        if (keep) adj[b + k + __popc(m & ((1u << lane) - 1u))] = e;
+        k += __popc(m);
+        __syncwarp();
+    }
+    return k;
+}
+
+// One warp per affected vertex x: drop this round's contracted vertices from
+// its out- and in-lists.
 __global__ void k_compact_lists(Dev d, const uint32_t *X, uint32_t nX, uint32_t r) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nX;
-         i += gridDim.x * blockDim.x) {
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nX; i += nwarps) {
         const uint32_t x = X[i];
         if (!id_ok(d, x)) continue;
-        {
-            const uint64_t b = d.out_beg[x];
-            const uint32_t dg = d.out_deg[x];
-            if (out_list_ok(d, b, dg)) {
-                uint32_t k = 0;
-                for (uint32_t j = 0; j < dg; ++j) {
-                    const uint2 e = d.out_adj[b + j];
-                    if (!id_ok(d, e.x)) continue;
-                    if (d.level[e.x] != r) d.out_adj[b + k++] = e;
-                }
-                d.out_deg[x] = k;
-            }
+        const uint64_t ob = d.out_beg[x], ib = d.in_beg[x];
+        const uint32_t od = d.out_deg[x], id = d.in_deg[x];
+        if (out_list_ok(d, ob, od)) {
+            const uint32_t k = warp_compact_list(d, d.out_adj, ob, od, r);
+            if (lane == 0) d.out_deg[x] = k;
         }
-        {
-            const uint64_t b = d.in_beg[x];
-            const uint32_t dg = d.in_deg[x];
-            if (in_list_ok(d, b, dg)) {
-                uint32_t k = 0;
-                for (uint32_t j = 0; j < dg; ++j) {
-                    const uint2 e = d.in_adj[b + j];
-                    if (!id_ok(d, e.x)) continue;
-                    if (d.level[e.x] != r) d.in_adj[b + k++] = e;
-                }
-                d.in_deg[x] = k;
-            }
+        if (in_list_ok(d, ib, id)) {
+            const uint32_t k = warp_compact_list(d, d.in_adj, ib, id, r);
+            if (lane == 0) d.in_deg[x] = k;
         }
     }
 }
@@ -1329,27 +1456,36 @@ __global__ void k_reserve(Dev d, const uint32_t *X, uint32_t nX, uint64_t *reqO,
     }
 }
 
+// One warp per affected vertex whose list outgrew its capacity: copy it to
+// its new place at the arena tail.
 __global__ void k_relocate(Dev d, const uint32_t *X, uint32_t nX, const uint64_t *reqO,
                            const uint64_t *posO, const uint64_t *reqI, const uint64_t *posI) {
     const uint64_t to = d.ctl->out_tail, ti = d.ctl->in_tail;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nX;
-         i += gridDim.x * blockDim.x) {
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nX; i += nwarps) {
         const uint32_t x = X[i];
         if (reqO[i]) {
             const uint64_t nb = to + posO[i], ob = d.out_beg[x];
             const uint32_t dg = d.out_deg[x];
-            if (!out_list_ok(d, nb, (uint32_t)reqO[i]) || !out_list_ok(d, ob, dg)) continue;
-            for (uint32_t j = 0; j < dg; ++j) d.out_adj[nb + j] = d.out_adj[ob + j];
-            d.out_beg[x] = nb;
-            d.out_cap[x] = (uint32_t)reqO[i];
+            if (out_list_ok(d, nb, (uint32_t)reqO[i]) && out_list_ok(d, ob, dg)) {
+                for (uint32_t j = lane; j < dg; j += 32) d.out_adj[nb + j] = d.out_adj[ob + j];
+                if (lane == 0) {
+                    d.out_beg[x] = nb;
+                    d.out_cap[x] = (uint32_t)reqO[i];
+                }
+            }
         }
         if (reqI[i]) {
             const uint64_t nb = ti + posI[i], ob = d.in_beg[x];
             const uint32_t dg = d.in_deg[x];
-            if (!in_list_ok(d, nb, (uint32_t)reqI[i]) || !in_list_ok(d, ob, dg)) continue;
-            for (uint32_t j = 0; j < dg; ++j) d.in_adj[nb + j] = d.in_adj[ob + j];
-            d.in_beg[x] = nb;
-            d.in_cap[x] = (uint32_t)reqI[i];
+            if (in_list_ok(d, nb, (uint32_t)reqI[i]) && in_list_ok(d, ob, dg)) {
+                for (uint32_t j = lane; j < dg; j += 32) d.in_adj[nb + j] = d.in_adj[ob + j];
+                if (lane == 0) {
+                    d.in_beg[x] = nb;
+                    d.in_cap[x] = (uint32_t)reqI[i];
+                }
+            }
         }
     }
 }
@@ -1506,12 +1642,14 @@ struct Builder {
     DevBuf<uint32_t> out_deg, in_deg, out_cap, in_cap;
     DevBuf<uint2> out_adj, in_adj;
     DevBuf<uint32_t> level, amark, smark, new_out, new_in;
+    DevBuf<uint8_t> inel;
     DevBuf<int32_t> P;
     DevBuf<Ctl> ctl;
     Ctl *hctl = nullptr;  // pinned
     // lists
     DevBuf<uint32_t> VO, VO2, A, Anext, S, S2, F, ovf, ovf2, tmp;
     int blk_blocks = 152;
+    uint32_t route_deg = 64;  // witness sources above this middle-degree sum go to the block tier
     DevBuf<uint64_t> reqO, reqI, posO, posI;
     DevBuf<uint32_t> scan32;
     DevBuf<uint64_t> scan64;
@@ -1563,6 +1701,7 @@ struct Builder {
     }
 
     void normalise(const ch_graph_t *g);
+    void emit_core(uint32_t r, uint32_t nVO, uint64_t live_edges);
     void run_rounds();
     void postprocess();
     template <int MODE>
@@ -1690,7 +1829,7 @@ void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_ma
     a.rec_flag = rec_flag.ptr;
     a.rec_cap = rec.count;
     a.route_all = (uint32_t)blk_blocks * 2;
-    a.route_deg = 64;
+    a.route_deg = route_deg;
     cudaEvent_t e0 = start();
     const int blocks = grid_for((uint64_t)nS_max, WIT_WARPS, sms * 8);
     k_witness<MODE><<<blocks, WIT_WARPS * 32, 0, st>>>(a);
@@ -1701,6 +1840,22 @@ void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_ma
     CH_CHECK_LAUNCH();
     mark(&h->t_witness_ms, e0, 5);
     h->witness_launches += 3;
+}
+
+void Builder::emit_core(uint32_t r, uint32_t nVO, uint64_t live_edges) {
+    cudaEvent_t e0 = start();
+    const Ctl c = *hctl;
+    if (ch_up.count < c.ch_up_tail + live_edges)
+        ch_up.grow(c.ch_up_tail + live_edges, c.ch_up_tail, st);
+    if (ch_dn.count < c.ch_dn_tail + live_edges)
+        ch_dn.grow(c.ch_dn_tail + live_edges, c.ch_dn_tail, st);
+    k_emit_ch<<<grid_for((uint64_t)nVO * 32, 256, sms * 8), 256, 0, st>>>(
+        d, VO.ptr, nVO, ch_up.ptr, ch_dn.ptr, ch_up_beg.ptr, ch_up_deg.ptr, ch_dn_beg.ptr,
+        ch_dn_deg.ptr, ch_up.count, ch_dn.count, true, r);
+    CH_CHECK_LAUNCH();
+    mark(&h->t_update_ms, e0);
+    sync_ctl();
+    h->core_size = nVO;
 }
 
 void Builder::run_rounds() {
@@ -1724,7 +1879,8 @@ void Builder::run_rounds() {
         cudaEvent_t e0 = start();
         const uint32_t sstamp = 2 * r + 1, cstamp = 2 * r + 2;
         if (nA) {
-            k_score_prep<<<grid_for(nA, 256, sms * 8), 256, 0, st>>>(d, A.ptr, nA, sstamp, S.ptr);
+            k_score_prep<<<grid_for((uint64_t)nA * 32, 256, sms * 8), 256, 0, st>>>(d, A.ptr, nA, sstamp,
+                                                                                    S.ptr);
             CH_CHECK_LAUNCH();
             witness<MODE_SCORE>(S.ptr, &ctl.ptr->nS, nA * 4 + 32 > n ? n : nA * 4 + 32, r);
             if (tracing || learned) {
@@ -1757,14 +1913,20 @@ void Builder::run_rounds() {
         mark(&h->t_select_ms, e0, 1);
         // 4: contraction bookkeeping
         e0 = start();
-        k_contract_prep<<<grid_for((uint64_t)nVO, 256, sms * 8), 256, 0, st>>>(
+        k_contract_prep<<<grid_for((uint64_t)nVO * 32, 256, sms * 8), 256, 0, st>>>(
             d, F.ptr, cstamp, r + 1, S2.ptr, Anext.ptr);
         CH_CHECK_LAUNCH();
         mark(&h->t_prep_ms, e0, 2);
         sync_ctl();
         const Ctl c = *hctl;
         const uint32_t nF = c.nF, nS2 = c.nS2, nAnext = c.nAnext;
-        if (nF == 0) throw Error{CH_ECUDA, "internal: empty selection"};
+        if (nF == 0) {
+            // no eligible vertex left (only possible with a finite bound):
+            // the live vertices are the core
+            if (d.cmax == UINT64_MAX) throw Error{CH_ECUDA, "internal: empty selection"};
+            emit_core(r, nVO, live_edges);
+            break;
+        }
         // capacities for this round's contraction
         const uint64_t cb = c.candBound;
         if (rec.count < cb) {
@@ -1803,13 +1965,14 @@ void Builder::run_rounds() {
         mark(&h->t_contract_ms, e0, 3);
         // 6-10
         e0 = start();
-        k_emit_ch<<<grid_for(nF, 256, sms * 8), 256, 0, st>>>(
+        k_emit_ch<<<grid_for((uint64_t)nF * 32, 256, sms * 8), 256, 0, st>>>(
             d, F.ptr, nF, ch_up.ptr, ch_dn.ptr, ch_up_beg.ptr, ch_up_deg.ptr, ch_dn_beg.ptr,
-            ch_dn_deg.ptr, ch_up.count, ch_dn.count);
+            ch_dn_deg.ptr, ch_up.count, ch_dn.count, false, r);
         CH_CHECK_LAUNCH();
         if (nAnext) {
             const int ga = grid_for(nAnext, 256, sms * 8);
-            k_compact_lists<<<ga, 256, 0, st>>>(d, Anext.ptr, nAnext, r);
+            const int gw = grid_for((uint64_t)nAnext * 32, 256, sms * 8);
+            k_compact_lists<<<gw, 256, 0, st>>>(d, Anext.ptr, nAnext, r);
             CH_CHECK_LAUNCH();
             k_reserve<<<ga, 256, 0, st>>>(d, Anext.ptr, nAnext, reqO.ptr, reqI.ptr);
             CH_CHECK_LAUNCH();
@@ -1817,7 +1980,7 @@ void Builder::run_rounds() {
                                      scan64.ptr, st);
             exclusive_scan<uint64_t>(reqI.ptr, posI.ptr, nullptr, nAnext, reinterpret_cast<uint64_t *>(&ctl.ptr->relocIn),
                                      scan64.ptr, st);
-            k_relocate<<<ga, 256, 0, st>>>(d, Anext.ptr, nAnext, reqO.ptr, posO.ptr, reqI.ptr,
+            k_relocate<<<gw, 256, 0, st>>>(d, Anext.ptr, nAnext, reqO.ptr, posO.ptr, reqI.ptr,
                                            posI.ptr);
             CH_CHECK_LAUNCH();
             k_advance_tails<<<1, 1, 0, st>>>(ctl.ptr);
@@ -1911,6 +2074,7 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     b.n = g->n;
     b.m_in = g->m;
     b.sms = device_sm_count();
+    if (p->witness_route_deg) b.route_deg = p->witness_route_deg;
     const uint32_t n = g->n;
     h->n = n;
     h->hop_limit = p->hop_limit;
@@ -1954,6 +2118,8 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     b.P.zero(b.st);
     b.amark.alloc(n);
     b.amark.zero(b.st);
+    b.inel.alloc(n);
+    b.inel.zero(b.st);
     b.smark.alloc(n);
     b.smark.zero(b.st);
     b.new_out.alloc(n);
@@ -1988,12 +2154,14 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     b.ch_dn_beg.alloc(n);
     b.ch_up_deg.alloc(n);
     b.ch_dn_deg.alloc(n);
-    // dense fallback slots: 8 uint32 + 1 uint64 arrays of n per slot, about
-    // 1 GiB in all (at least 2 slots, at most 64)
-    const uint64_t per_slot = (uint64_t)n * (8 * 4 + 8);
-    uint32_t slots = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(64, (1024ull << 20) / per_slot));
+    // dense fallback slots: 9 uint32 + 1 uint64 arrays of n per slot; the
+    // pool is 1 GiB, or 128 B per input edge up to 8 GiB (graphs with hubs
+    // send many sources here), with 2 to 256 slots
+    const uint64_t per_slot = (uint64_t)n * (9 * 4 + 8);
+    const uint64_t pool_bytes = std::min<uint64_t>(8ull << 30, std::max<uint64_t>(1ull << 30, 128 * m1));
+    uint32_t slots = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(256, pool_bytes / per_slot));
     b.dense.nslots = slots;
-    b.dn32.alloc((size_t)slots * n * 8);
+    b.dn32.alloc((size_t)slots * n * 9);
     b.dn64.alloc((size_t)slots * n);
     {
         const size_t sn = (size_t)slots * n;
@@ -2006,7 +2174,9 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
         b.dense.fdb = p32 + 5 * sn;
         b.dense.touched = p32 + 6 * sn;
         b.dense.mt = p32 + 7 * sn;
+        b.dense.direct = p32 + 8 * sn;
         b.dense.merge = b.dn64.ptr;
+        CH_CUDA_TRY(cudaMemsetAsync(b.dense.direct, 0xFF, sn * 4, b.st));
         CH_CUDA_TRY(cudaMemsetAsync(b.dense.dist, 0xFF, sn * 4, b.st));
         CH_CUDA_TRY(cudaMemsetAsync(b.dense.fst, 0, sn * 4, b.st));
         CH_CUDA_TRY(cudaMemsetAsync(b.dense.merge, 0xFF, sn * 8, b.st));
@@ -2063,6 +2233,9 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     d.orig_deg = b.orig_deg.ptr;
     d.ed_last = b.ed_last.ptr;
     d.label = b.label.ptr;
+    d.cmax = p->max_candidates_per_vertex;
+    d.inel = b.inel.ptr;
+    d.ball = p->witness_ball_limit ? p->witness_ball_limit : 0xFFFFFFFFu;
     k_orig_deg<<<grid_for(n, 256, b.sms * 8), 256, 0, b.st>>>(d);
     CH_CHECK_LAUNCH();
 
@@ -2097,7 +2270,8 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     h->labels = std::move(b.label);
     h->trace = std::move(b.trace);
     h->trace_prio = std::move(b.trace_prio);
-    h->trace_rows = b.trace_count;
+    h->trace_rows = b.trace_count;          // row slots, marked ones included
+    h->trace_valid = c.trace_valid;
     h->sc = std::move(b.log);
     h->sc_round = std::move(b.log_round);
 }

@@ -40,7 +40,9 @@ struct ch_s {
     gbch::DevBuf<long long> trace;
     gbch::DevBuf<int32_t> trace_prio;
     gbch::DevBuf<int32_t> labels;
-    uint64_t trace_rows = 0;
+    uint64_t trace_rows = 0;   // row slots of the trace (rows of ineligible rescorings marked)
+    uint64_t trace_valid = 0;  // rows of eligible rescorings
+    uint64_t core_size = 0;
 
     std::vector<std::array<uint64_t, CH_NSTAT>> round_stats;
     std::vector<std::array<double, CH_NTIME>> round_times;
@@ -63,6 +65,7 @@ struct ch_s {
     uint32_t q_layout = CH_QUERY_WARP_FLAT;  // query block configuration (performance only)
     uint32_t q_threads = 256;
     uint32_t q_small_first = 1;  // first pass on 2^11-slot tables
+    uint32_t q_stall = 1;        // stall on demand (warp layout, pruned searches)
     uint32_t q_slots = 0;
     uint64_t q_ovf_cap = 0;
 };
@@ -84,10 +87,12 @@ void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint6
                         uint32_t *dist_out, cudaStream_t st);
 
 // Query configuration, autotuning, work counters, graphs (query.cu).
-void query_set_config(ch_s *h, uint32_t layout, uint32_t threads, uint32_t small_first);
+void query_set_config(ch_s *h, uint32_t layout, uint32_t threads, uint32_t small_first, uint32_t stall);
 void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch_query_config_t *chosen,
                     double *ms_out);
 void query_work(ch_s *h, cudaStream_t st, uint64_t out[2]);
+// Device time (ms) of a batch of `sample` seeded random queries (after one warm-up batch).
+double query_time_sample(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st);
 ch_query_graph_s *query_graph_create(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
                                      uint32_t *dist_out);
 void query_graph_launch(ch_query_graph_s *g, cudaStream_t st);

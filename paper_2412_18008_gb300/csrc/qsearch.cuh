@@ -82,6 +82,27 @@ __device__ __forceinline__ uint32_t qb_insert(uint32_t *keys, uint32_t v) {
     return EMPTY;
 }
 
+// Slot of v, or EMPTY if v is not in the table (read-only probe; an insert
+// racing with it may be missed, which only makes a stall test weaker).
+template <int TB>
+__device__ __forceinline__ uint32_t qb_find(const uint32_t *keys, uint32_t v) {
+    constexpr uint32_t T = 1u << TB;
+    uint32_t h = (v * 2654435761u) >> (32 - TB);
+    for (uint32_t probe = 0; probe < T; ++probe) {
+        const uint32_t k = keys[h];
+        if (k == v) return h;
+        if (k == EMPTY) return EMPTY;
+        h = (h + 1) & (T - 1);
+    }
+    return EMPTY;
+}
+
+// Bits lo..hi-1 of a lane mask (0 <= lo <= hi <= 32).
+__device__ __forceinline__ uint32_t qb_lane_range(uint32_t lo, uint32_t hi) {
+    const uint32_t h = hi >= 32 ? FULL : ((1u << hi) - 1u);
+    return h & ~((1u << lo) - 1u);
+}
+
 // Marks `slot` as queued in direction `dir` for the next level (bitmap of
 // the level's parity); true if it was not queued yet.
 template <int TB>
@@ -172,7 +193,7 @@ __device__ __forceinline__ void qb_entry(const QBSmem<TB> &q, const QArgs &a, bo
 // flag right after a barrier that follows every write to them: the barrier
 // at the top of the level (warp-flattened; block-flattened at level 1) or
 // the barrier that ends the previous level's last tile (block-flattened).
-template <bool PRUNE, bool WARP, int TB>
+template <bool PRUNE, bool WARP, int TB, bool STALL>
 __device__ bool block_search(QBSmem<TB> &q, const QArgs &a, QStat &stat) {
     constexpr uint32_t FC = QBSmem<TB>::FC, CW = QBSmem<TB>::CW;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
@@ -203,6 +224,49 @@ __device__ bool block_search(QBSmem<TB> &q, const QArgs &a, QStat &stat) {
                 uint32_t b, cnt, dx;
                 qb_entry(q, a, fv, ent, b, cnt, dx);
                 stat.exp += cnt ? 1u : 0u;
+                if (STALL) {
+                    // Stall on demand: the entry's vertex x is not expanded
+                    // when a reached higher neighbour y gives a shorter path
+                    // to it (forward: an E_down edge y -> x with
+                    // df[y] + w < df[x]; backward: an E_up edge x -> y with
+                    // w + db[y] < db[x]). Its label then exceeds the true
+                    // distance, so x with that label lies on no shortest
+                    // up-path; a vertex whose label is exact is never stalled,
+                    // and a later improvement queues x again.
+                    const uint32_t dir = ent >> 31;
+                    const uint32_t slot = ent & 0x7FFFFFFFu;
+                    const uint32_t x = cnt ? q.key[slot] : 0;
+                    const uint32_t *soff = dir ? a.up_off : a.dn_off;
+                    const uint32_t s_edges = dir ? a.n_up : a.n_dn;
+                    const uint32_t sb = cnt ? soff[x] : 0;
+                    const uint32_t se = cnt ? soff[x + 1] : 0;
+                    uint32_t scnt = 0;
+                    if (cnt && sb <= se && se <= s_edges) scnt = se - sb;
+                    else if (cnt) atomicOr(a.err, QERR_BOUND);
+                    const uint32_t sincl = warp_incl_scan(scnt);
+                    const uint32_t stotal = __shfl_sync(FULL, sincl, 31);
+                    const uint32_t sexcl = sincl - scnt;
+                    bool stalled = false;
+                    for (uint32_t base = 0; base < stotal; base += 32) {
+                        const uint32_t e0 = base + lane;
+                        const uint32_t o = warp_owner(sexcl, e0);
+                        const uint32_t osb = __shfl_sync(FULL, sb, o);
+                        const uint32_t oex = __shfl_sync(FULL, sexcl, o);
+                        const uint32_t odx = __shfl_sync(FULL, dx, o);
+                        const uint32_t odir = __shfl_sync(FULL, ent, o) >> 31;
+                        bool st = false;
+                        if (e0 < stotal) {
+                            ++stat.edges;
+                            const uint2 e = (odir ? a.up_adj : a.dn_adj)[osb + (e0 - oex)];
+                            const uint32_t ys = e.x < a.n ? qb_find<TB>(q.key, e.x) : EMPTY;
+                            if (ys != EMPTY) st = sat_add(odir ? q.db[ys] : q.df[ys], e.y) < odx;
+                        }
+                        const uint32_t B = __ballot_sync(FULL, st);
+                        const uint32_t lo = max(sexcl, base), hi = min(sexcl + scnt, base + 32);
+                        if (hi > lo && (B & qb_lane_range(lo - base, hi - base))) stalled = true;
+                    }
+                    if (stalled) cnt = 0;
+                }
                 const uint32_t incl = warp_incl_scan(cnt);
                 const uint32_t total = __shfl_sync(FULL, incl, 31);
                 const uint32_t excl = incl - cnt;
@@ -281,7 +345,7 @@ __device__ __forceinline__ void qb_clear(QBSmem<TB> &q) {
 // overflowed the table or the frontier (the caller redoes the query
 // elsewhere); otherwise mu and cnt hold, in every thread, the least meeting
 // sum and the number of labels set. Every thread of the block must call it.
-template <bool PRUNE, bool WARP, int TB>
+template <bool PRUNE, bool WARP, int TB, bool STALL = false>
 __device__ bool block_query(QBSmem<TB> &q, const QArgs &a, uint32_t rs, uint32_t rt, uint32_t &mu_out,
                             uint32_t &cnt_out, QStat &stat) {
     const uint32_t tid = threadIdx.x;
@@ -300,7 +364,7 @@ __device__ bool block_query(QBSmem<TB> &q, const QArgs &a, uint32_t rs, uint32_t
         q.cnt3[1] = 0;
         q.cnt3[2] = 0;
     }
-    const bool ok = block_search<PRUNE, WARP, TB>(q, a, stat);
+    const bool ok = block_search<PRUNE, WARP, TB, STALL>(q, a, stat);
     // q.mu only steered pruning; the answer is the least meeting sum.
     __syncthreads();
     if (tid == 0) q.mu = INF;

@@ -27,7 +27,7 @@ namespace {
 
 constexpr uint64_t Q_CHUNK = 1u << 22;  // queries per launch pair
 
-template <bool PRUNE, bool WARP, int TB>
+template <bool PRUNE, bool WARP, int TB, bool STALL>
 __global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
     extern __shared__ __align__(16) unsigned char qb_raw[];
     QBSmem<TB> &q = *reinterpret_cast<QBSmem<TB> *>(qb_raw);
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
             continue;
         }
         uint32_t mu, cnt;
-        if (!block_query<PRUNE, WARP, TB>(q, a, rs, rt, mu, cnt, stat)) {
+        if (!block_query<PRUNE, WARP, TB, STALL>(q, a, rs, rt, mu, cnt, stat)) {
             if (tid == 0) a.ovf[atomicAdd(&a.work[a.ovf_cnt], 1u)] = i;
             continue;
         }
@@ -195,22 +195,25 @@ __global__ void __launch_bounds__(256) k_query_dense(QArgs a, QDense dn) {
 }
 
 // Resident blocks per SM of each block-kernel configuration
-// [table bits == 11][layout][threads == 256], resolved once.
-int g_qb_bps[2][2][2] = {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}};
+// [table bits == 11][block-flat, warp-flat, warp-flat with stalling]
+// [threads == 256], resolved once.
+int g_qb_bps[2][3][2] = {{{-1, -1}, {-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}, {-1, -1}}};
 
 template <int TB>
 void qb_resolve(int s) {
     const int smem = (int)sizeof(QBSmem<TB>);
-    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true, false, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<false, false, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true, true, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<false, true, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    for (int l = 0; l < 2; ++l)
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true, false, TB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<false, false, TB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true, true, TB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<false, true, TB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true, true, TB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    for (int l = 0; l < 3; ++l)
         for (int t = 0; t < 2; ++t) {
             int b = 0;
             const int threads = t ? 256 : 128;
-            if (l) CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, true, TB>, threads, smem));
-            else CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, false, TB>, threads, smem));
+            if (l == 2) CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, true, TB, true>, threads, smem));
+            else if (l == 1) CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, true, TB, false>, threads, smem));
+            else CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, false, TB, false>, threads, smem));
             g_qb_bps[s][l][t] = std::max(1, b);
         }
 }
@@ -222,30 +225,34 @@ void qb_resolve_occupancy() {
 }
 
 template <int TB>
-void launch_tb(const QArgs &a, bool prune, bool warp, int blocks, int threads, cudaStream_t st) {
+void launch_tb(const QArgs &a, bool prune, bool warp, bool stall, int blocks, int threads, cudaStream_t st) {
     const size_t smem = sizeof(QBSmem<TB>);
     if (warp) {
-        if (prune) k_query_block<true, true, TB><<<blocks, threads, smem, st>>>(a);
-        else k_query_block<false, true, TB><<<blocks, threads, smem, st>>>(a);
+        if (prune && stall) k_query_block<true, true, TB, true><<<blocks, threads, smem, st>>>(a);
+        else if (prune) k_query_block<true, true, TB, false><<<blocks, threads, smem, st>>>(a);
+        else k_query_block<false, true, TB, false><<<blocks, threads, smem, st>>>(a);
     } else {
-        if (prune) k_query_block<true, false, TB><<<blocks, threads, smem, st>>>(a);
-        else k_query_block<false, false, TB><<<blocks, threads, smem, st>>>(a);
+        if (prune) k_query_block<true, false, TB, false><<<blocks, threads, smem, st>>>(a);
+        else k_query_block<false, false, TB, false><<<blocks, threads, smem, st>>>(a);
     }
     CH_CHECK_LAUNCH();
 }
 
 // Launches one block-kernel pass in the handle's layout and block size: a
 // persistent grid of as many blocks as are resident at once (no more than
-// the items), with 2^11-slot tables when small is set, else 2^12.
+// the items), with 2^11-slot tables when small is set, else 2^12. Stall on
+// demand applies to pruned searches in the warp layout only.
 void launch_query_block(const ch_s *h, const QArgs &a, bool prune, bool small, uint64_t items,
                         cudaStream_t st) {
-    const int l = h->q_layout == CH_QUERY_WARP_FLAT ? 1 : 0;
+    const bool warp = h->q_layout == CH_QUERY_WARP_FLAT;
+    const bool stall = warp && prune && h->q_stall;
+    const int l = stall ? 2 : (warp ? 1 : 0);
     const int t = h->q_threads == 256 ? 1 : 0;
     const int threads = t ? 256 : 128;
     const int blocks = (int)std::max<uint64_t>(
         1, std::min<uint64_t>(items, (uint64_t)device_sm_count() * g_qb_bps[small ? 1 : 0][l][t]));
-    if (small) launch_tb<11>(a, prune, l == 1, blocks, threads, st);
-    else launch_tb<12>(a, prune, l == 1, blocks, threads, st);
+    if (small) launch_tb<11>(a, prune, warp, stall, blocks, threads, st);
+    else launch_tb<12>(a, prune, warp, stall, blocks, threads, st);
 }
 
 }  // namespace
@@ -349,14 +356,15 @@ __global__ void k_sample_pairs(uint32_t *s, uint32_t *t, uint64_t k, uint32_t n,
 
 }  // namespace
 
-void query_set_config(ch_s *h, uint32_t layout, uint32_t threads, uint32_t small_first) {
+void query_set_config(ch_s *h, uint32_t layout, uint32_t threads, uint32_t small_first, uint32_t stall) {
     if ((layout != CH_QUERY_BLOCK_FLAT && layout != CH_QUERY_WARP_FLAT) || (threads != 128 && threads != 256) ||
-        small_first > 1)
+        small_first > 1 || stall > 1 || (stall && layout != CH_QUERY_WARP_FLAT))
         throw Error{CH_EINVAL, "query configuration: layout BLOCK_FLAT or WARP_FLAT, threads 128 or 256, "
-                               "small_first 0 or 1"};
+                               "small_first 0 or 1, stall 0 or 1 (WARP_FLAT only)"};
     h->q_layout = layout;
     h->q_threads = threads;
     h->q_small_first = small_first;
+    h->q_stall = stall;
 }
 
 void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch_query_config_t *chosen,
@@ -367,18 +375,24 @@ void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch
     uint32_t *s = buf.ptr, *t = buf.ptr + sample, *out = buf.ptr + 2 * sample;
     k_sample_pairs<<<grid_for(sample, 256, device_sm_count() * 4), 256, 0, st>>>(s, t, sample, h->n, seed);
     CH_CHECK_LAUNCH();
-    const uint32_t keep_l = h->q_layout, keep_t = h->q_threads, keep_s = h->q_small_first;
+    const uint32_t keep_l = h->q_layout, keep_t = h->q_threads, keep_s = h->q_small_first,
+                   keep_st = h->q_stall;
     cudaEvent_t e0, e1;
     CH_CUDA_TRY(cudaEventCreate(&e0));
     CH_CUDA_TRY(cudaEventCreate(&e1));
+    // candidates 0-7: 4 * small_first + 2 * warp layout + (threads == 256);
+    // 8-11: warp layout with stalling, 8 + 2 * small_first + (threads == 256)
     auto apply = [&](int i) {
-        query_set_config(h, (i & 2) ? CH_QUERY_WARP_FLAT : CH_QUERY_BLOCK_FLAT, (i & 1) ? 256 : 128,
-                         (i & 4) ? 1 : 0);
+        if (i < 8)
+            query_set_config(h, (i & 2) ? CH_QUERY_WARP_FLAT : CH_QUERY_BLOCK_FLAT, (i & 1) ? 256 : 128,
+                             (i & 4) ? 1 : 0, 0);
+        else
+            query_set_config(h, CH_QUERY_WARP_FLAT, (i & 1) ? 256 : 128, (i & 2) ? 1 : 0, 1);
     };
     double best = 0;
     int best_i = -1;
     try {
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < 12; ++i) {
             apply(i);
             query_batch(h, s, t, sample, out, nullptr, st);  // warm-up
             CH_CUDA_TRY(cudaEventRecord(e0, st));
@@ -397,6 +411,7 @@ void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch
         h->q_layout = keep_l;
         h->q_threads = keep_t;
         h->q_small_first = keep_s;
+        h->q_stall = keep_st;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         throw;
@@ -408,10 +423,43 @@ void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch
         chosen->layout = h->q_layout;
         chosen->threads = h->q_threads;
         chosen->small_first = h->q_small_first;
+        chosen->stall = h->q_stall;
     }
     // the sample's work is not the caller's: clear the counters
     CH_CUDA_TRY(cudaMemsetAsync(h->q_stats.ptr, 0, 2 * sizeof(unsigned long long), st));
     CH_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+double query_time_sample(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st) {
+    if (sample == 0 || h->n == 0) return 0.0;
+    DevBuf<uint32_t> buf;
+    buf.alloc(3 * sample);
+    uint32_t *s = buf.ptr, *t = buf.ptr + sample, *out = buf.ptr + 2 * sample;
+    k_sample_pairs<<<grid_for(sample, 256, device_sm_count() * 4), 256, 0, st>>>(s, t, sample, h->n, seed);
+    CH_CHECK_LAUNCH();
+    cudaEvent_t e0, e1;
+    CH_CUDA_TRY(cudaEventCreate(&e0));
+    CH_CUDA_TRY(cudaEventCreate(&e1));
+    float ms = 0;
+    cudaError_t e = cudaSuccess;
+    try {
+        query_batch(h, s, t, sample, out, nullptr, st);  // warm-up
+        CH_CUDA_TRY(cudaEventRecord(e0, st));
+        query_batch(h, s, t, sample, out, nullptr, st);
+        CH_CUDA_TRY(cudaEventRecord(e1, st));
+        CH_CUDA_TRY(cudaEventSynchronize(e1));
+        e = cudaEventElapsedTime(&ms, e0, e1);
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) throw Error{CH_ECUDA, cudaGetErrorString(e)};
+    CH_CUDA_TRY(cudaMemsetAsync(h->q_stats.ptr, 0, 2 * sizeof(unsigned long long), st));
+    CH_CUDA_TRY(cudaStreamSynchronize(st));
+    return ms;
 }
 
 void query_work(ch_s *h, cudaStream_t st, uint64_t out[2]) {

@@ -52,7 +52,7 @@ struct SvArgs {
     QArgs q;                     // hierarchy and the error word (status)
     SvCtl *ctl;                  // mapped
     const SvDesc *desc;          // mapped ring
-    const uint32_t *item_req;    // mapped pool: ring slot of the request owning each entry
+    const uint32_t *item_req;    // mapped pool: ticket + 1 of the request owning each entry
     const uint32_t *targets;     // mapped pool
     uint32_t *answers;           // mapped pool
     uint32_t *done;              // mapped ring: ticket + 1 when served
@@ -85,6 +85,19 @@ __device__ __forceinline__ uint64_t ld_acquire_sys(const uint64_t *p) {
 __device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Relaxed system-scope loads of host-written (mapped) data.
+__device__ __forceinline__ uint32_t ld_sys(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t ld_sys(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -280,21 +293,39 @@ __global__ void __launch_bounds__(QB_THREADS) k_serve(SvArgs a) {
                     sleep_ns = min(2u * sleep_ns, 8192u);
                 }
                 if (s_go) {
+                    // The entry names its request (ticket + 1); the request's
+                    // descriptor must carry that ticket and cover this
+                    // position. Both were written before the publication, so
+                    // they match at once; the bounded re-read only guards
+                    // against seeing them late.
                     const uint64_t e = pos % a.pool;
-                    const uint32_t slot = ((const volatile uint32_t *)a.item_req)[e];
-                    if (slot < a.ring) {
-                        const volatile SvDesc *d = a.desc + slot;
-                        s_src = d->s;
-                        s_k = d->k;
-                        s_seq = d->seq;
-                        s_first = d->pos == pos;
-                        s_tgt = ((const volatile uint32_t *)a.targets)[e];
-                        s_slot = slot;
-                        s_e = e;
-                        if (s_first) a.t_begin[slot] = globaltimer();
-                    } else {
-                        atomicOr(a.status, QERR_BOUND);
-                        s_go = 2;  // skip the entry
+                    const unsigned long long t1 = globaltimer();
+                    s_go = 2;  // skip the entry unless it validates
+                    while (true) {
+                        const uint32_t v = ld_sys(a.item_req + e);
+                        if (v != 0) {
+                            const uint32_t slot = (v - 1) % a.ring;
+                            const SvDesc *d = a.desc + slot;
+                            const uint64_t dseq = ld_sys(&d->seq), dpos = ld_sys(&d->pos);
+                            const uint32_t dk = ld_sys(&d->k);
+                            if ((uint32_t)(dseq + 1) == v && dpos <= pos && pos < dpos + dk) {
+                                s_src = ld_sys(&d->s);
+                                s_k = dk;
+                                s_seq = dseq;
+                                s_first = dpos == pos;
+                                s_tgt = ld_sys(a.targets + e);
+                                s_slot = slot;
+                                s_e = e;
+                                if (s_first) a.t_begin[slot] = globaltimer();
+                                s_go = 1;
+                                break;
+                            }
+                        }
+                        if (globaltimer() - t1 > 1000000000ull) {  // 1 s: report and skip
+                            atomicOr(a.status, QERR_BOUND);
+                            break;
+                        }
+                        __nanosleep(256);
                     }
                 }
             }
@@ -501,7 +532,7 @@ int server_submit(ch_server_s *sv, uint32_t s, const uint32_t *targets, uint32_t
     const uint32_t slot = (uint32_t)(seq % sv->ring);
     pool_span(sv->pool, pos, k, [&](uint64_t e, uint64_t j, uint64_t n) {
         std::memcpy(sv->targets.h + e, targets + j, n * sizeof(uint32_t));
-        std::fill(sv->item_req.h + e, sv->item_req.h + e + n, slot);
+        std::fill(sv->item_req.h + e, sv->item_req.h + e + n, (uint32_t)(seq + 1));
     });
     sv->desc.h[slot] = SvDesc{s, k, pos, seq};
     sv->done.h[slot] = 0;

@@ -128,7 +128,7 @@ def test_full_size_road_like_graph():
     assert (st >= 2 - same).all()
     # the pruned searches the benchmark times, in both table tiers and both
     # layouts, answer every pair of the batch as the exhaustive ones do
-    for cfg in ((1, 256, 0), (1, 256, 1), (0, 256, 1)):
+    for cfg in ((1, 256, 0, 0), (1, 256, 1, 0), (0, 256, 1, 0), (1, 256, 1, 1)):
         gch.set_query_config(*cfg)
         dp = gch.query(ds, dt)
         torch.cuda.synchronize()

@@ -146,6 +146,55 @@ def test_round0_scores_bruteforce(seed, H):
     assert O.round0_scores(g, H).tolist() == want
 
 
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("H,ball", [(3, 2), (4, 4), (5, 6), (2, 1), (5, 100)])
+def test_round0_scores_with_ball_bound_bruteforce(seed, H, ball):
+    # The bounded witness search, written out: labels below the source's
+    # heaviest candidate weight, levels 1..H, stopping after the first level
+    # at which more than `ball` vertices hold such a label.
+    g = I.random_digraph(9, 26, 1, 6, seed=320 + seed)
+    adj = _adj(g)
+    radj = {u: {} for u in range(g.n)}
+    for u in adj:
+        for v, w in adj[u].items():
+            radj[v][u] = w
+    dist = {}
+    for s in range(g.n):
+        bound = max([w1 + w2 for u, w1 in adj[s].items() for v, w2 in adj[u].items() if v != s],
+                    default=0)
+        if bound == 0:
+            continue
+        for h in range(1, H + 1):
+            lab = {v: d for v, d in _walk_bruteforce(adj, s, h).items() if d < bound}
+            if len(lab) > ball:
+                break
+        dist[s] = lab
+    want = []
+    for u in range(g.n):
+        cnt = 0
+        for v1, w1 in radj[u].items():
+            for v2, w2 in adj[u].items():
+                if v1 != v2 and w1 + w2 <= dist.get(v1, {}).get(v2, INF):
+                    cnt += 1
+        want.append(cnt - len(radj[u]) - len(adj[u]))
+    assert O.round0_scores(g, H, ball=ball).tolist() == want
+
+
+@pytest.mark.parametrize("ball", [0, 1, 3, 10])
+@pytest.mark.parametrize("name,g", [(n, g) for n, g in small_families()
+                                    if n in ("digraph1", "sparse2", "grid8", "geo150", "rmat8",
+                                             "chain30")],
+                         ids=lambda x: x if isinstance(x, str) else "")
+def test_ball_bound_keeps_distances(name, g, ball):
+    ch = O.build_ch(g, 5, ball=ball)
+    ss, tt = np.meshgrid(np.arange(g.n), np.arange(g.n), indexing="ij")
+    d = ch.query(ss.ravel().astype(np.uint32), tt.ravel().astype(np.uint32))
+    assert np.array_equal(d.astype(np.uint64).reshape(g.n, g.n), all_pairs_truth(g))
+    # a bound at least the graph's size never stops a search
+    full, big = O.build_ch(g, 5), O.build_ch(g, 5, ball=g.n)
+    assert np.array_equal(full.shortcuts, big.shortcuts) and np.array_equal(full.rank, big.rank)
+
+
 # ---------------------------------------------------------------------------
 # The CH invariant: every upward-upward query equals the true distance
 # ---------------------------------------------------------------------------
@@ -287,3 +336,74 @@ def test_sampled_queries_on_grid_workload():
     # >99% of the vertices go in the first rounds on road-like inputs (Sec. 4.3)
     frac = np.cumsum(ch.stats[:, 2]) / g.n
     assert frac[min(40, len(frac) - 1)] > 0.99
+
+
+# ---------------------------------------------------------------------------
+# Candidate bound Cmax and the core (partial hierarchy)
+# ---------------------------------------------------------------------------
+
+P_INELIGIBLE = 2**31 - 2
+
+
+@pytest.mark.parametrize("cmax", [0, 1, 4, 12, 40])
+@pytest.mark.parametrize("name,g", [(n, g) for n, g in small_families()
+                                    if n in ("digraph0", "digraph3", "sparse1", "grid8", "geo150",
+                                             "rmat8", "star9", "chain30d")],
+                         ids=lambda x: x if isinstance(x, str) else "")
+def test_core_queries_equal_truth(name, g, cmax):
+    ch = O.build_ch(g, 5, cmax=cmax)
+    ss, tt = np.meshgrid(np.arange(g.n), np.arange(g.n), indexing="ij")
+    d = ch.query(ss.ravel().astype(np.uint32), tt.ravel().astype(np.uint32))
+    assert np.array_equal(d.astype(np.uint64).reshape(g.n, g.n), all_pairs_truth(g))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_core_invariants(seed):
+    g = I.random_digraph(80, 320, 1, 20, seed=40 + seed)
+    ch = O.build_ch(g, 5, cmax=9)
+    core = ch.level == ch.rounds
+    assert core.any() and (ch.level <= ch.rounds).all()
+    assert (ch.priority[core] == P_INELIGIBLE).all()
+    # the core takes the top ranks, in id order (equal level and score)
+    top = np.sort(ch.rank[core])
+    assert np.array_equal(top, np.arange(g.n - core.sum(), g.n))
+    assert np.array_equal(np.argsort(ch.rank)[g.n - core.sum():], np.flatnonzero(core))
+    # no shortcut after the last contraction round; core edges stay in the core
+    assert (ch.shortcuts[:, 0] < ch.rounds).all() if len(ch.shortcuts) else True
+    for u, x, _ in ch.up:
+        if core[u]:
+            assert core[x]
+    for x, u, _ in ch.down:
+        if core[u]:
+            assert core[x]
+    # contracted vertices were eligible when selected: |N_in| * |N_out| <= Cmax,
+    # which bounds the candidates they emitted
+    per_round = ch.stats[:, 4]
+    assert (per_round <= 9 * ch.stats[:, 2]).all()
+
+
+def test_core_closed_forms():
+    # complete digraph: (n - 1)^2 candidates exceed the bound, nothing is
+    # eligible, everything is core at level 0
+    g = I.complete_graph(6, 1)
+    ch = O.build_ch(g, 5, cmax=24)
+    assert ch.rounds == 0 and (ch.level == 0).all() and len(ch.shortcuts) == 0
+    assert len(ch.up) == 30 and len(ch.down) == 30
+    assert (ch.priority == P_INELIGIBLE).all()
+    # one bound higher the whole graph is contracted
+    assert (O.build_ch(g, 5, cmax=25).level < 2**32 - 1).all()
+    # star: the hub (k^2 candidates) waits for its leaves, then goes alone
+    g = I.star_graph(9, seed=9)
+    ch = O.build_ch(g, 5, cmax=1)
+    assert ch.rounds == 2 and ch.level[0] == 1 and (ch.level[1:] == 0).all()
+    assert len(ch.shortcuts) == 0
+    # bidirectional chain under Cmax = 1: only ends are eligible, so it is
+    # peeled from both ends without a single shortcut
+    for n in (5, 6, 9):
+        g = I.chain_graph(n, True, seed=n)
+        ch = O.build_ch(g, 5, cmax=1)
+        assert len(ch.shortcuts) == 0
+        assert ch.rounds == (n + 1) // 2 + (1 - n % 2)
+        assert (ch.level < ch.rounds).all()
+        lv = ch.level.astype(np.int64)
+        assert (lv[: n // 2] == np.arange(n // 2)).all() or n % 2 == 0

@@ -26,12 +26,12 @@ def geo():
     return g, _ch().CH.build(g, hop_limit=5), O.build_ch(g, 5)
 
 
-@pytest.mark.parametrize("layout,threads,small", [(lay, thr, sf) for sf in (0, 1) for lay in (0, 1)
-                                                  for thr in (128, 256)])
-def test_every_configuration_gives_the_oracle_answers(geo, layout, threads, small):
+@pytest.mark.parametrize("cfg", [(lay, thr, sf, 0) for sf in (0, 1) for lay in (0, 1) for thr in (128, 256)]
+                         + [(1, thr, sf, 1) for sf in (0, 1) for thr in (128, 256)])
+def test_every_configuration_gives_the_oracle_answers(geo, cfg):
     g, gch, och = geo
-    gch.set_query_config(layout, threads, small)
-    assert gch.query_config() == (layout, threads, small)
+    gch.set_query_config(*cfg)
+    assert gch.query_config() == cfg
     s, t = I.random_pairs(g.n, 20_000, seed=82)
     d, st = gch.query(s, t, want_settled=True)
     od, ost = och.query(s, t, want_settled=True)
@@ -57,7 +57,8 @@ def test_invalid_configuration_is_rejected(geo):
     ch = _ch()
     _, gch, _ = geo
     before = gch.query_config()
-    for cfg in ((2, 256, 0), (0, 64, 0), (1, 512, 0), (1, 256, 2)):
+    for cfg in ((2, 256, 0, 0), (0, 64, 0, 0), (1, 512, 0, 0), (1, 256, 2, 0), (0, 256, 0, 1),
+                (1, 256, 0, 2)):
         with pytest.raises(ch.CHError) as ei:
             gch.set_query_config(*cfg)
         assert ei.value.code == ch.CH_EINVAL
@@ -91,11 +92,11 @@ def test_work_counters(geo):
     assert gch.query_work() == (0, 0)  # cleared by the read
 
 
-@pytest.mark.parametrize("small", [0, 1])
-def test_graph_replay_matches_batch_calls(geo, small):
+@pytest.mark.parametrize("cfg", [(1, 256, 0, 0), (1, 256, 1, 0), (1, 256, 1, 1)])
+def test_graph_replay_matches_batch_calls(geo, cfg):
     torch = _torch()
     g, gch, och = geo
-    gch.set_query_config(1, 256, small)
+    gch.set_query_config(*cfg)
     k = 3000
     s1, t1 = I.random_pairs(g.n, k, seed=87)
     s2, t2 = I.random_pairs(g.n, k, seed=88)

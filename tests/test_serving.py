@@ -56,7 +56,13 @@ def test_same_answer_alone_and_in_the_mix(built):
             t0 = time.time()
             while res is None and time.time() - t0 < 30:
                 res = sv.poll(tk, int(ks[i]))
-            assert res is not None
+            if res is None:  # report the device loop's state with the failure
+                try:
+                    sv.stop()
+                    why = "the loop then stopped cleanly"
+                except ch.CHError as e:
+                    why = f"stopping the loop failed: {e}"
+                raise AssertionError(f"request {i} (k = {ks[i]}) not served in 30 s; {why}")
             assert np.array_equal(res, mix[a:b])
 
 
