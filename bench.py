@@ -62,7 +62,7 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) of the k_query_block launches of the full 1M
 # query batch (first pass + overflow redo), from an ncu capture of the
 # current kernel on this workload (set to None when the kernel changes).
-QUERY_TRAFFIC_PER_LAUNCH = None
+QUERY_TRAFFIC_PER_LAUNCH = 85_268_000
 
 
 def parse():
@@ -339,7 +339,7 @@ def serve_bench(args):
         nblocks = sv.blocks
         # saturated: everything due at once
         t0 = time.perf_counter()
-        ans, lat, svc = sv.replay(src, ks, tg, np.zeros(nreq, np.uint64))
+        ans, lat, svc = sv.replay(src, ks, tg, np.zeros(nreq, np.uint64), limit_s=1200.0)
         makespan = float(lat.max()) * 1e-9
         assert np.array_equal(ans, expected), "served answers differ from batch answers"
         max_rps = nreq / makespan
@@ -347,7 +347,7 @@ def serve_bench(args):
                             **pct(lat), "service": pct(svc)}
         for frac in (0.5, 0.8, 0.95):
             arr = ch.poisson_arrivals(nreq, max_rps * frac, seed=int(100 * frac))
-            ans, lat, svc = sv.replay(src, ks, tg, arr)
+            ans, lat, svc = sv.replay(src, ks, tg, arr, limit_s=1200.0)
             assert np.array_equal(ans, expected)
             span = (float(arr[-1]) + float(lat[-1])) * 1e-9
             out[f"poisson_{int(frac * 100)}pct"] = {
@@ -540,7 +540,10 @@ def main():
             "kernel": "k_query_block (pruned bidirectional upward searches, one launch per batch)",
             "bound": "hbm", "achieved": round(q_gbs, 1), "peak": peak, "unit": "GB/s",
             "frac": round(q_gbs / peak, 4),
-            "traffic": QUERY_TRAFFIC_PER_LAUNCH if args.workload == "geo1M" and nq == 1_000_000 else None,
+            # the captured traffic belongs to this workload in the default
+            # configuration (warp layout, 256 threads, small tables, stalling)
+            "traffic": (QUERY_TRAFFIC_PER_LAUNCH if args.workload == "geo1M" and nq == 1_000_000
+                        and (qcfg is None or tuple(qcfg) == (1, 256, 1, 1)) else None),
             "peak_source": peak_src, "bytes_per_launch": q_bytes, "ms_per_launch": mean_query,
             "launch": "one batch = the small-table pass + its overflow redo (two launches)",
             "expansions_per_query": q_exp / nq, "edges_per_query": q_edges / nq,

@@ -98,7 +98,18 @@ struct Dev {
     // witness ball bound: a search stops after the first hop level at which
     // more than `ball` vertices (the source included) hold a label
     uint32_t ball;
+    // In-round memo of the score phase's decisions (only without a ball
+    // bound, where both phases decide every candidate the same way):
+    // emask[p] for the overlay edge (s, u) at arena position p holds bit j
+    // set iff the candidate (s, u, j-th out-neighbour of u) was kept; valid
+    // when kround[u] == round + 1 (u rescored this round, at most 64
+    // out-edges).
+    unsigned long long *emask;
+    uint32_t *kround;
+    bool memo;
 };
+
+constexpr uint32_t MEMO_MAX_OUT = 64;
 
 constexpr int32_t P_INELIGIBLE = 2147483646;  // INT32_MAX - 1
 constexpr uint32_t AMARK_NONE = 0xFFFFFFFFu;   // never a round index
@@ -280,7 +291,7 @@ __global__ void k_iota(uint32_t *a, uint32_t n) {
 // One warp per rescored vertex u: its score starts at the edge term, and its
 // in-neighbours become witness sources (each once per round).
 __global__ void k_score_prep(Dev d, const uint32_t *A, uint32_t nA, uint32_t stamp,
-                             uint32_t *S) {
+                             uint32_t *S, uint32_t r) {
     const uint32_t lane = lane_id();
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nA; i += nwarps) {
@@ -300,6 +311,7 @@ __global__ void k_score_prep(Dev d, const uint32_t *A, uint32_t nA, uint32_t sta
         if (lane == 0) {
             d.inel[u] = 0;
             d.P[u] = -(int32_t)(od + id);
+            d.kround[u] = (d.memo && od <= MEMO_MAX_OUT) ? r + 1 : 0;
         }
         const uint64_t ib = d.in_beg[u];
         if (!in_list_ok(d, ib, id)) continue;
@@ -411,8 +423,10 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         // and counted, by the next tier).
         unsigned long long l_vert = 0, l_edge = 0, l_mid = 0, l_midedge = 0;
 
-        // Phase 0: heaviest candidate weight of this source.
+        // Phase 0: heaviest candidate weight of this source, and whether every
+        // contracted middle has its score-phase decisions memoised.
         uint32_t bound = 0;
+        bool memo_all = MODE == MODE_PRUNE && d.memo;
         for (uint32_t c0 = 0; c0 < sd; c0 += 32) {
             const uint32_t j = c0 + lane;
             const bool valid = j < sd;
@@ -421,6 +435,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             uint32_t cnt = mid ? d.out_deg[e.x] : 0;
             const uint64_t ub = mid ? d.out_beg[e.x] : 0;
             if (mid && !out_list_ok(d, ub, cnt)) cnt = 0;
+            if (MODE == MODE_PRUNE) memo_all = __all_sync(FULL, memo_all && (!mid || d.kround[e.x] == r + 1));
             l_mid += mid;
             l_midedge += cnt;
             const uint32_t incl = warp_incl_scan(cnt);
@@ -451,7 +466,9 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         }
 
         // Phase 1: hop-limited Bellman-Ford from s, levels 1..H, each level
-        // relaxing from the previous level's values (frontier snapshots).
+        // relaxing from the previous level's values (frontier snapshots);
+        // skipped when the decisions are memoised.
+        if (!memo_all) {
         for (uint32_t t = lane; t < WIT_T; t += 32) {
             w.key[t] = EMPTY;
             w.val[t] = INF;
@@ -536,6 +553,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
             continue;
         }
+        }  // Phase 1
 
         // Phase 2: decisions for every candidate (s, u, v2).
         if (MODE == MODE_PRUNE) {
@@ -559,6 +577,11 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             const uint32_t total = __shfl_sync(FULL, incl, 31);
             const uint32_t excl = incl - cnt;
             if (MODE == MODE_SCORE) w.cnt[lane] = 0;
+            // memo of this edge (s, u): recorded in the score phase, read in
+            // the contraction phase
+            const bool mk = mid && d.memo && d.kround[e.x] == r + 1;
+            if (MODE == MODE_SCORE && mk) d.emask[sb + j] = 0;
+            const unsigned long long mword = (MODE == MODE_PRUNE && memo_all && mid) ? d.emask[sb + j] : 0;
             __syncwarp();
             for (uint32_t b = 0; b < total; b += 32) {
                 const uint32_t idx = b + lane;
@@ -567,14 +590,25 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                 const uint32_t w1 = __shfl_sync(FULL, e.y, o);
                 const uint32_t u_o = __shfl_sync(FULL, e.x, o);
                 const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                const bool mk_o = __shfl_sync(FULL, mk, o);
+                const unsigned long long mw_o = __shfl_sync(FULL, mword, o);
                 if (idx < total) {
-                    const uint2 e2 = d.out_adj[ub_o + (idx - ex_o)];
+                    const uint32_t kj = idx - ex_o;  // index of v2 in u's out-list
+                    const uint2 e2 = d.out_adj[ub_o + kj];
                     if (e2.x != s) {
                         const uint32_t via = sat_add(w1, e2.y);
-                        const uint32_t slot = ht_find(w.key, WIT_TBITS, e2.x);
-                        const uint32_t dh = slot == EMPTY ? INF : w.val[slot];
+                        bool keepit;
+                        if (MODE == MODE_PRUNE && memo_all) {
+                            keepit = (mw_o >> kj) & 1ull;
+                        } else {
+                            const uint32_t slot = ht_find(w.key, WIT_TBITS, e2.x);
+                            const uint32_t dh = slot == EMPTY ? INF : w.val[slot];
+                            keepit = via != INF && via <= dh;
+                        }
+                        if (MODE == MODE_SCORE && keepit && mk_o)
+                            atomicOr(&d.emask[sb + c0 + o], 1ull << kj);
                         ++l_cand;
-                        if (via != INF && via <= dh) {
+                        if (keepit) {
                             ++l_kept;
                             if (MODE == MODE_SCORE) {
                                 atomicAdd(&w.cnt[o], 1u);
@@ -693,7 +727,7 @@ struct BlkSmem {
     unsigned long long mval[WB_M];
     uint32_t cntw[WB_THREADS / 32][32];
     uint32_t nf[2];
-    uint32_t item, ovf, bound, nnew, nkeys;
+    uint32_t item, ovf, bound, nnew, nkeys, memo_ok;
 };
 
 template <int MODE>
@@ -744,13 +778,16 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             b.bound = 0;
             b.ovf = 0;
             b.nnew = 0;
+            b.memo_ok = MODE == MODE_PRUNE && d.memo;
         }
         __syncthreads();
-        // Phase 0: heaviest candidate weight of the source.
+        // Phase 0: heaviest candidate weight of the source, and whether every
+        // contracted middle has its score-phase decisions memoised.
         uint32_t lb = 0;
         for (uint32_t j = tid; j < sd; j += blockDim.x) {
             const uint2 e = d.out_adj[sb + j];
             if (!id_ok(d, e.x) || !is_middle<MODE>(d, e.x, r)) continue;
+            if (MODE == MODE_PRUNE && d.kround[e.x] != r + 1) b.memo_ok = 0;
             const uint64_t ub = d.out_beg[e.x];
             const uint32_t ud = out_list_ok(d, ub, d.out_deg[e.x]) ? d.out_deg[e.x] : 0;
             ++l_mid;
@@ -763,13 +800,14 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
         if (lb) atomicMax(&b.bound, lb);
         __syncthreads();
         const uint32_t bound = b.bound;
+        const bool memo_all = b.memo_ok != 0;
         if (bound == 0) {
             c_src += (tid == 0);
             c_mid += l_mid;
             c_midedge += l_midedge;
             continue;
         }
-        if (tid == 0) {
+        if (tid == 0 && !memo_all) {
             const uint32_t h = ht_insert(b.key, WB_TBITS, s);
             b.val[h] = 0;
             b.front[0][0] = make_uint2(h, 0);
@@ -778,9 +816,10 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             b.nkeys = 1;
         }
         // Phase 1: hop-limited Bellman-Ford, one level per iteration, each
-        // level relaxing from the previous level's values (snapshots).
+        // level relaxing from the previous level's values (snapshots);
+        // skipped when the decisions are memoised.
         uint32_t cur = 0;
-        for (uint32_t lvl = 1; lvl <= d.H; ++lvl) {
+        for (uint32_t lvl = 1; lvl <= d.H && !memo_all; ++lvl) {
             __syncthreads();
             const uint32_t nfront = b.nf[cur];
             const uint32_t ovf = b.ovf;
@@ -856,6 +895,9 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             const uint32_t total = __shfl_sync(FULL, incl, 31);
             const uint32_t excl = incl - cnt;
             if (MODE == MODE_SCORE) b.cntw[warp][lane] = 0;
+            const bool mk = mid && d.memo && d.kround[e.x] == r + 1;
+            if (MODE == MODE_SCORE && mk) d.emask[sb + j] = 0;
+            const unsigned long long mword = (MODE == MODE_PRUNE && memo_all && mid) ? d.emask[sb + j] : 0;
             __syncwarp();
             for (uint32_t base = 0; base < total; base += 32) {
                 const uint32_t idx = base + lane;
@@ -864,14 +906,24 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
                 const uint32_t w1 = __shfl_sync(FULL, e.y, o);
                 const uint32_t u_o = __shfl_sync(FULL, e.x, o);
                 const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                const bool mk_o = __shfl_sync(FULL, mk, o);
+                const unsigned long long mw_o = __shfl_sync(FULL, mword, o);
                 if (idx >= total) continue;
-                const uint2 e2 = d.out_adj[ub_o + (idx - ex_o)];
+                const uint32_t kj = idx - ex_o;  // index of v2 in u's out-list
+                const uint2 e2 = d.out_adj[ub_o + kj];
                 if (e2.x == s) continue;
                 const uint32_t via = sat_add(w1, e2.y);
-                const uint32_t slot = ht_find(b.key, WB_TBITS, e2.x);
-                const uint32_t dh = slot == EMPTY ? INF : b.val[slot];
+                bool keepit;
+                if (MODE == MODE_PRUNE && memo_all) {
+                    keepit = (mw_o >> kj) & 1ull;
+                } else {
+                    const uint32_t slot = ht_find(b.key, WB_TBITS, e2.x);
+                    const uint32_t dh = slot == EMPTY ? INF : b.val[slot];
+                    keepit = via != INF && via <= dh;
+                }
+                if (MODE == MODE_SCORE && keepit && mk_o) atomicOr(&d.emask[sb + c0 + o], 1ull << kj);
                 ++l_cand;
-                if (via == INF || via > dh) continue;
+                if (!keepit) continue;
                 ++l_kept;
                 if (MODE == MODE_SCORE) {
                     atomicAdd(&b.cntw[warp][o], 1u);
@@ -976,7 +1028,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
     uint32_t *fa = dn.fa + base, *fb = dn.fb + base, *fda = dn.fda + base, *fdb = dn.fdb + base;
     uint32_t *mt = dn.mt + base, *direct = dn.direct + base;
     unsigned long long *merge = dn.merge + base;
-    __shared__ uint32_t s_item, s_bound, s_nt, s_nm, s_nf[2];
+    __shared__ uint32_t s_item, s_bound, s_nt, s_nm, s_nf[2], s_memo;
     __shared__ unsigned long long s_cnt[5];
     const uint32_t tid = threadIdx.x;
     const uint32_t nOvf = ctl->nOvf2;
@@ -1000,6 +1052,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             s_nm = 0;
             s_nf[0] = 1;
             s_nf[1] = 0;
+            s_memo = MODE == MODE_PRUNE && d.memo;
             dist[s] = 0;
             touched[0] = s;
             fa[0] = s;
@@ -1010,6 +1063,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
         for (uint32_t j = tid; j < sd; j += blockDim.x) {
             const uint2 e = d.out_adj[sb + j];
             if (!id_ok(d, e.x) || !is_middle<MODE>(d, e.x, r)) continue;
+            if (MODE == MODE_PRUNE && d.kround[e.x] != r + 1) s_memo = 0;
             const uint64_t ub = d.out_beg[e.x];
             const uint32_t ud = out_list_ok(d, ub, d.out_deg[e.x]) ? d.out_deg[e.x] : 0;
             uint32_t bmax = 0;
@@ -1021,9 +1075,10 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
         }
         __syncthreads();
         const uint32_t bound = s_bound;
+        const bool memo_all = s_memo != 0;  // decisions memoised: no search
         uint32_t *cur = fa, *curd = fda, *nx = fb, *nxd = fdb;
         const uint32_t lane = lane_id(), warp = tid >> 5, nwarps = blockDim.x >> 5;
-        for (uint32_t lvl = 1; lvl <= d.H && bound > 0; ++lvl) {
+        for (uint32_t lvl = 1; lvl <= d.H && bound > 0 && !memo_all; ++lvl) {
             const uint32_t nf = s_nf[(lvl - 1) & 1];
             __syncthreads();
             if (tid == 0) s_nf[lvl & 1] = 0;
@@ -1082,14 +1137,24 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             if (!id_ok(d, e.x) || !is_middle<MODE>(d, e.x, r)) continue;
             const uint64_t ub = d.out_beg[e.x];
             const uint32_t ud = out_list_ok(d, ub, d.out_deg[e.x]) ? d.out_deg[e.x] : 0;
+            const bool mk = d.memo && d.kround[e.x] == r + 1;
+            const unsigned long long mword = (MODE == MODE_PRUNE && memo_all) ? d.emask[sb + j] : 0;
+            unsigned long long rec_mask = 0;
             int32_t kept_u = 0;
             for (uint32_t jj = 0; jj < ud; ++jj) {
                 const uint2 e2 = d.out_adj[ub + jj];
                 if (e2.x == s || !id_ok(d, e2.x)) continue;
                 const uint32_t via = sat_add(e.y, e2.y);
-                const uint32_t dh = dist[e2.x];
+                bool keepit;
+                if (MODE == MODE_PRUNE && memo_all) {
+                    keepit = (mword >> jj) & 1ull;
+                } else {
+                    const uint32_t dh = dist[e2.x];
+                    keepit = via != INF && via <= dh;
+                }
+                if (MODE == MODE_SCORE && keepit && mk) rec_mask |= 1ull << jj;
                 ++l_cand;
-                if (via != INF && via <= dh) {
+                if (keepit) {
                     ++l_kept;
                     ++kept_u;
                     if (MODE == MODE_PRUNE) {
@@ -1100,6 +1165,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
                 }
             }
             if (MODE == MODE_SCORE && kept_u) atomicAdd(&d.P[e.x], kept_u);
+            if (MODE == MODE_SCORE && mk) d.emask[sb + j] = rec_mask;
         }
         __syncthreads();
         if (MODE == MODE_PRUNE) {
@@ -1641,8 +1707,9 @@ struct Builder {
     DevBuf<uint64_t> out_beg, in_beg;
     DevBuf<uint32_t> out_deg, in_deg, out_cap, in_cap;
     DevBuf<uint2> out_adj, in_adj;
-    DevBuf<uint32_t> level, amark, smark, new_out, new_in;
+    DevBuf<uint32_t> level, amark, smark, new_out, new_in, kround;
     DevBuf<uint8_t> inel;
+    DevBuf<unsigned long long> emask;  // one word per out-arena entry
     DevBuf<int32_t> P;
     DevBuf<Ctl> ctl;
     Ctl *hctl = nullptr;  // pinned
@@ -1880,7 +1947,7 @@ void Builder::run_rounds() {
         const uint32_t sstamp = 2 * r + 1, cstamp = 2 * r + 2;
         if (nA) {
             k_score_prep<<<grid_for((uint64_t)nA * 32, 256, sms * 8), 256, 0, st>>>(d, A.ptr, nA, sstamp,
-                                                                                    S.ptr);
+                                                                                    S.ptr, r);
             CH_CHECK_LAUNCH();
             witness<MODE_SCORE>(S.ptr, &ctl.ptr->nS, nA * 4 + 32 > n ? n : nA * 4 + 32, r);
             if (tracing || learned) {
@@ -1946,6 +2013,8 @@ void Builder::run_rounds() {
         bool regrow = false;
         if (out_adj.count < c.out_tail + grow_bound) {
             out_adj.grow(std::max<uint64_t>(c.out_tail + grow_bound, out_adj.count * 2), c.out_tail, st);
+            // the score phase's memo words stay with their arena positions
+            emask.grow(out_adj.count, c.out_tail, st);
             regrow = true;
         }
         if (in_adj.count < c.in_tail + grow_bound) {
@@ -1955,6 +2024,7 @@ void Builder::run_rounds() {
         if (regrow) {
             d.out_adj = out_adj.ptr;
             d.in_adj = in_adj.ptr;
+            d.emask = emask.ptr;
             d.out_arena = out_adj.count;
             d.in_arena = in_adj.count;
         }
@@ -2120,6 +2190,8 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     b.amark.zero(b.st);
     b.inel.alloc(n);
     b.inel.zero(b.st);
+    b.kround.alloc(n);
+    b.kround.zero(b.st);
     b.smark.alloc(n);
     b.smark.zero(b.st);
     b.new_out.alloc(n);
@@ -2236,6 +2308,12 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     d.cmax = p->max_candidates_per_vertex;
     d.inel = b.inel.ptr;
     d.ball = p->witness_ball_limit ? p->witness_ball_limit : 0xFFFFFFFFu;
+    // memoised in-round decisions need both phases to decide alike, which a
+    // ball bound (cut levels depend on each phase's own weight bound) breaks
+    d.memo = p->witness_ball_limit == 0;
+    b.emask.alloc(b.out_adj.count);
+    d.emask = b.emask.ptr;
+    d.kround = b.kround.ptr;
     k_orig_deg<<<grid_for(n, 256, b.sms * 8), 256, 0, b.st>>>(d);
     CH_CHECK_LAUNCH();
 

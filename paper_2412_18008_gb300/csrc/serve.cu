@@ -242,7 +242,7 @@ __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_
     return res;
 }
 
-template <bool WARP>
+template <bool WARP, bool STALL>
 __global__ void __launch_bounds__(QB_THREADS) k_serve(SvArgs a) {
     extern __shared__ __align__(16) unsigned char qb_raw[];
     QBSmem<12> &q = *reinterpret_cast<QBSmem<12> *>(qb_raw);
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_serve(SvArgs a) {
             const uint32_t rs = g.rank[s], rt = g.rank[tv];
             if (rs < g.n && rt < g.n) {
                 uint32_t cnt;
-                if (!block_query<true, WARP, 12>(q, g, rs, rt, ans, cnt, stat))
+                if (!block_query<true, WARP, 12, STALL>(q, g, rs, rt, ans, cnt, stat))
                     ans = sv_query(a, t, rs, rt, q.cnt3, &q.ovf, &q.mu, &q.cnt);
             } else if (tid == 0) {
                 atomicOr(a.status, QERR_BOUND);
@@ -423,7 +423,7 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     // the handle's query configuration (layout and block size)
     const bool warp = h->q_layout == CH_QUERY_WARP_FLAT;
     const int threads = (int)h->q_threads;
-    auto kern = warp ? k_serve<true> : k_serve<false>;
+    auto kern = warp ? (h->q_stall ? k_serve<true, true> : k_serve<true, false>) : k_serve<false, false>;
     CH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(QBSmem<12>)));
     int per_sm = 0;
     CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sizeof(QBSmem<12>)));
