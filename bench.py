@@ -43,6 +43,9 @@ WORKLOADS = {
     # RMAT stress graph: 2^21 vertices, 2^25 edge samples (a=.57, b=c=.19),
     # weights U[1,1000]; built with a finite candidate bound (--cmax)
     "rmat2M": (1 << 21, 8, 9, 100_000),
+    # the same family scaled down (16 edge samples per vertex)
+    "rmat128K": (1 << 17, 8, 9, 100_000),
+    "rmat32K": (1 << 15, 8, 9, 100_000),
 }
 
 
@@ -53,7 +56,8 @@ def make_graph(name: str, sample: bool = False):
     if name.startswith("rmat"):
         if sample:  # same samples per vertex (16) at 2^12 vertices
             return I.rmat_graph(scale=12, nsamples=1 << 16, wmax=1000, seed=7)
-        return I.rmat_graph(scale=21, nsamples=1 << 25, wmax=1000, seed=gseed)
+        scale = n.bit_length() - 1
+        return I.rmat_graph(scale=scale, nsamples=16 << scale, wmax=1000, seed=gseed)
     if sample:
         return I.geometric_knn_graph(100_000, seed=7)
     return I.geometric_knn_graph(n, seed=gseed)
@@ -75,6 +79,9 @@ def parse():
     ap.add_argument("--hop-limit", type=int, default=5)
     ap.add_argument("--cmax", type=int, default=None,
                     help="candidate bound |N_in|*|N_out| of a contractible vertex (default: none)")
+    ap.add_argument("--witness-ball", type=int, default=None,
+                    help="witness ball bound: stop a search after the first hop level that "
+                         "reaches more than this many vertices (default: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
@@ -163,14 +170,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_sample_build(workload: str, hop_limit: int, cmax):
+def cpu_sample_build(workload: str, hop_limit: int, cmax, ball=None):
     """Oracle build on a sample graph of the same family, scaled linearly
     (by vertex count) to the full workload. Returns (scaled_s, raw_s,
     threads, sample vertices)."""
     import oracle as O
     g = make_graph(workload, sample=True)
     t0 = time.perf_counter()
-    O.build_ch(g, hop_limit, cmax=O.CMAX_ALL if cmax is None else cmax)
+    O.build_ch(g, hop_limit, cmax=O.CMAX_ALL if cmax is None else cmax,
+               ball=O.CMAX_ALL if ball is None else ball)
     raw = time.perf_counter() - t0
     return raw * (WORKLOADS[workload][0] / g.n), raw, 1, g.n
 
@@ -182,15 +190,16 @@ def run_reference(args):
         return
     import oracle as O
     cmax = O.CMAX_ALL if args.cmax is None else args.cmax
+    ball = O.CMAX_ALL if args.witness_ball is None else args.witness_ball
     O.build_ch(I.geometric_knn_graph(2000, seed=7), args.hop_limit)  # load + warm
     g = make_graph(args.workload, sample=True)
     sample_n = g.n
     for _ in range(args.warmup):
-        O.build_ch(g, args.hop_limit, cmax=cmax)
+        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        O.build_ch(g, args.hop_limit, cmax=cmax)
+        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball)
         times.append(time.perf_counter() - t0)
     scale = n / sample_n
     value = statistics.mean(times) * scale
@@ -224,26 +233,29 @@ def compare_learned(args):
     cmax = args.cmax
     hop_limit, route_deg, tune_rows = args.hop_limit, 0, None
     if rmat:
-        train_graph = lambda seed: I.rmat_graph(scale=17, nsamples=1 << 21, wmax=1000, seed=seed)
-        seeds = range(200, 200 + args.train_graphs)
         g = make_graph(args.workload)
+        tscale = g.n.bit_length() - 3  # training graphs a quarter of the size
+        train_graph = lambda seed: I.rmat_graph(scale=tscale, nsamples=16 << tscale, wmax=1000, seed=seed)
+        seeds = range(200, 200 + args.train_graphs)
         test_seed, nq_cmp, n_ss = WORKLOADS[args.workload][1], 100_000, 10_000
     else:
         train_graph = lambda seed: I.geometric_knn_graph(256_000, seed=seed)
         seeds = range(100, 100 + args.train_graphs)
         g = I.geometric_knn_graph(1_000_000, seed=5)
         test_seed, nq_cmp, n_ss = 5, 1_000_000, 100_000
+    ball = args.witness_ball
     if args.tune_build:
         h, tune_rows, k = ch.CH.build_autotune(g, hop_limits=(1, 2, 3, 4, 5), route_degs=(32, 64, 128),
                                                sample=1 << 14, queries_per_build=nq_cmp,
-                                               max_candidates_per_vertex=cmax)
+                                               max_candidates_per_vertex=cmax, witness_ball_limit=ball)
         hop_limit, route_deg = tune_rows[k]["hop_limit"], tune_rows[k]["witness_route_deg"]
         h.close()
     t0 = time.perf_counter()
     rows, labels = [], []
     for seed in seeds:
         tr = ch.CH.build(train_graph(seed), hop_limit=hop_limit, trace=True,
-                         max_candidates_per_vertex=cmax, witness_route_deg=route_deg).export_trace()
+                         max_candidates_per_vertex=cmax, witness_route_deg=route_deg,
+                         witness_ball_limit=ball).export_trace()
         rows.append(tr["rows"])
         labels.append(ch.training_labels(tr["rows"]))
     rows = np.concatenate(rows)
@@ -274,7 +286,7 @@ def compare_learned(args):
             e0.record()
             h = ch.CH.build(n=g.n, offsets=off, targets=tgt, weights=wt, hop_limit=hop_limit,
                             mlp_weights=mw, max_candidates_per_vertex=cmax,
-                            witness_route_deg=route_deg)
+                            witness_route_deg=route_deg, witness_ball_limit=ball)
             e1.record()
             torch.cuda.synchronize()
             if k >= args.warmup:
@@ -300,9 +312,10 @@ def compare_learned(args):
                   "mean upward search-space size",
         "config": {"workload": f"{args.workload}-learned", "vertices": g.n, "edges": int(g.m),
                    "test_seed": test_seed, "train_graphs": args.train_graphs,
-                   "train_vertices_each": int(train_graph(seeds[0]).n) if rmat else 256_000,
+                   "train_vertices_each": (1 << tscale) if rmat else 256_000,
                    "train_rows": int(rows.shape[0]), "train_epochs": args.train_epochs,
-                   "cmax": cmax, "hop_limit": hop_limit, "witness_route_deg": route_deg},
+                   "cmax": cmax, "witness_ball_limit": ball, "hop_limit": hop_limit,
+                   "witness_route_deg": route_deg},
         "build_autotune": tune_rows,
         "results": res,
         "distances_identical": bool(np.array_equal(answers["edge_difference"], answers["learned"])),
@@ -427,7 +440,8 @@ def main():
 
     def step():
         h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
-                        hop_limit=args.hop_limit, stream=stream, max_candidates_per_vertex=args.cmax)
+                        hop_limit=args.hop_limit, stream=stream, max_candidates_per_vertex=args.cmax,
+                        witness_ball_limit=args.witness_ball)
         if qcfg is not None:
             h.set_query_config(*qcfg)
         if not args.build_only:
@@ -462,7 +476,7 @@ def main():
             e0.record(stream)
             h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
                             hop_limit=args.hop_limit, stream=stream,
-                            max_candidates_per_vertex=args.cmax)
+                            max_candidates_per_vertex=args.cmax, witness_ball_limit=args.witness_ball)
             if qcfg is not None:
                 h.set_query_config(*qcfg)
             e1.record(stream)
@@ -564,7 +578,8 @@ def main():
         for _ in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            hh = ch.CH.build(g, hop_limit=args.hop_limit, max_candidates_per_vertex=args.cmax)
+            hh = ch.CH.build(g, hop_limit=args.hop_limit, max_candidates_per_vertex=args.cmax,
+                             witness_ball_limit=args.witness_ball)
             if qcfg is not None:
                 hh.set_query_config(*qcfg)
             t1 = time.perf_counter()
@@ -580,7 +595,8 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        scaled, raw, cores, sn = cpu_sample_build(args.workload, args.hop_limit, args.cmax)
+        scaled, raw, cores, sn = cpu_sample_build(args.workload, args.hop_limit, args.cmax,
+                                                  args.witness_ball)
         cpu = {"value": scaled, "unit": "s", "cores": cores, "kind": "oracle",
                "sample": f"oracle build of a {sn}-vertex graph of the same family "
                          f"({raw:.2f} s, one thread), scaled linearly by vertex count to {n}"}
@@ -592,7 +608,8 @@ def main():
             "ms_per_step": mean_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": args.workload, "vertices": n, "edges": int(g.m),
-                       "cmax": args.cmax, "core_vertices": stats["core_vertices"],
+                       "cmax": args.cmax, "witness_ball": args.witness_ball,
+                       "core_vertices": stats["core_vertices"],
                        "queries": nq, "hop_limit": args.hop_limit,
                        "parallelism": f"replicas{world}",
                        "l2": "flushed before each step (2x L2 buffer write)"},

@@ -137,9 +137,9 @@ __device__ __forceinline__ bool sv_claim(uint32_t *fst, uint32_t slot, uint32_t 
 }
 
 // Fallback for a pair whose search spaces overflow the shared table: the
-// same search, one frontier entry per thread, labels in the block's global
-// hash table. Control values (s_cnt3, s_ovf) are read between two barriers
-// as in block_search. Returns INF when unreachable.
+// same search (warp-flattened levels, no stalling), labels in the block's
+// global hash table. Control values (s_cnt3, s_ovf) are read between two
+// barriers as in block_search. Returns INF when unreachable.
 __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_t rt,
                              uint32_t *s_cnt3, uint32_t *s_ovf, uint32_t *s_mu, uint32_t *s_nt) {
     const QArgs &g = a.q;
@@ -168,31 +168,46 @@ __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_
         if (tid == 0) s_cnt3[(lvl + 1) % 3] = 0;
         const uint32_t *fr = t.front + (size_t)cur * t.fcap;
         uint32_t *fn = t.front + (size_t)(cur ^ 1u) * t.fcap;
-        for (uint32_t f = tid; f < nfront && f < t.fcap; f += blockDim.x) {
-            const uint32_t ent = fr[f];
+        // frontier entries dealt to warps round-robin; each warp spreads its
+        // entries' out-edges over its lanes
+        const uint32_t lane = lane_id(), warp = tid >> 5, nwarps = blockDim.x >> 5;
+        for (uint32_t p0 = 0; p0 < nfront; p0 += blockDim.x) {
+            const uint32_t fi = p0 + warp + nwarps * lane;
+            const bool fv = fi < nfront && fi < t.fcap;
+            const uint32_t ent = fv ? fr[fi] : 0;
             const uint32_t dir = ent >> 31, slot = ent & 0x7FFFFFFFu;
-            if (slot > t.mask) {
+            bool ok = fv;
+            if (ok && slot > t.mask) {
                 atomicOr(a.status, QERR_BOUND);
-                continue;
+                ok = false;
             }
-            const uint32_t x = t.key[slot];
-            if (x >= g.n) {
+            const uint32_t x = ok ? t.key[slot] : 0;
+            if (ok && x >= g.n) {
                 atomicOr(a.status, QERR_BOUND);
-                continue;
+                ok = false;
             }
             const uint32_t *off = dir ? g.dn_off : g.up_off;
-            const uint2 *adj = dir ? g.dn_adj : g.up_adj;
             const uint32_t ne = dir ? g.n_dn : g.n_up;
-            const uint32_t b = off[x], e_end = off[x + 1];
-            if (b > e_end || e_end > ne) {
+            const uint32_t b = ok ? off[x] : 0, e_end = ok ? off[x + 1] : 0;
+            if (ok && (b > e_end || e_end > ne)) {
                 atomicOr(a.status, QERR_BOUND);
-                continue;
+                ok = false;
             }
-            uint32_t *dist = dir ? t.db : t.df;
-            const uint32_t dx = dist[slot];
-            for (uint32_t j = b; j < e_end; ++j) {
-                const uint2 e = adj[j];
-                const uint32_t nd = sat_add(dx, e.y);
+            const uint32_t cnt = ok ? e_end - b : 0;
+            const uint32_t dx = cnt ? (dir ? t.db[slot] : t.df[slot]) : INF;
+            const uint32_t incl = warp_incl_scan(cnt);
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            const uint32_t excl = incl - cnt;
+            for (uint32_t base = 0; base < total; base += 32) {
+                const uint32_t e0 = base + lane;
+                const uint32_t o = warp_owner(excl, e0);
+                const uint32_t ob = __shfl_sync(FULL, b, o);
+                const uint32_t oex = __shfl_sync(FULL, excl, o);
+                const uint32_t odx = __shfl_sync(FULL, dx, o);
+                const uint32_t odir = __shfl_sync(FULL, ent, o) >> 31;
+                if (e0 >= total) continue;
+                const uint2 e = (odir ? g.dn_adj : g.up_adj)[ob + (e0 - oex)];
+                const uint32_t nd = sat_add(odx, e.y);
                 if (e.x >= g.n) {
                     atomicOr(a.status, QERR_BOUND);
                     continue;
@@ -203,13 +218,14 @@ __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_
                     *s_ovf = 1;
                     continue;
                 }
+                uint32_t *dist = odir ? t.db : t.df;
                 const uint32_t old = atomicMin(&dist[ys], nd);
                 if (nd >= old) continue;
-                const uint32_t other = dir ? t.df[ys] : t.db[ys];
+                const uint32_t other = odir ? t.df[ys] : t.db[ys];
                 if (other != INF) atomicMin(s_mu, sat_add(nd, other));
-                if (sv_claim(t.fst, ys, dir, lvl)) {
+                if (sv_claim(t.fst, ys, odir, lvl)) {
                     const uint32_t p = atomicAdd(&s_cnt3[lvl % 3], 1u);
-                    if (p < t.fcap) fn[p] = ys | (dir << 31);
+                    if (p < t.fcap) fn[p] = ys | (odir << 31);
                     else *s_ovf = 1;
                 }
             }
