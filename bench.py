@@ -69,6 +69,18 @@ L2_BYTES = 129 * 1024 * 1024
 QUERY_TRAFFIC_PER_LAUNCH = 85_268_000
 
 
+def max_over_ranks(values, world: int, device):
+    """Per-rank timings -> their maximum over the ranks (on every rank).
+    Replicas run the same workload each; the slowest rank sets the time."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -504,10 +516,7 @@ def main():
     mean_step = statistics.mean(step_ms)
     mean_build = statistics.mean(build_ms)
     mean_query = statistics.mean(query_ms)
-    if world > 1:
-        tt = torch.tensor([mean_step, mean_build, mean_query], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        mean_step, mean_build, mean_query = tt.tolist()
+    mean_step, mean_build, mean_query = max_over_ranks([mean_step, mean_build, mean_query], world, dev)
 
     # per-round profile: the paper observes that most of the work sits in the
     # first rounds; report the split
@@ -614,7 +623,9 @@ def main():
                        "parallelism": f"replicas{world}",
                        "l2": "flushed before each step (2x L2 buffer write)"},
             "shortcuts": stats["shortcuts"], "rounds": stats["rounds"],
-            "queries_per_s": nq / (mean_query / 1000.0), "query_batch_ms": mean_query,
+            # every replica answers its own batch: whole-job queries over the
+            # slowest rank's batch time
+            "queries_per_s": world * nq / (mean_query / 1000.0), "query_batch_ms": mean_query,
             "mean_search_space": mean_ss,
             "build_phases_ms": phases,
             "round_profile": round_profile,

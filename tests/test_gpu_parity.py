@@ -58,7 +58,8 @@ def assert_same_queries(gch, och, s, t):
 def test_golden_examples(name):
     spec = load_golden(name)
     tie = 1 if spec.get("tie_break") == "id" else 0
-    g = gpu_build(spec["graph"], spec["hop_limit"], tie)
+    g = ch_mod().CH.build(spec["graph"], hop_limit=spec["hop_limit"], tie_break=tie,
+                          max_candidates_per_vertex=spec.get("cmax"))
     ex = g.export()
     assert ex["level"].tolist() == spec["expect_level"]
     assert ex["priority"].tolist() == spec["expect_priority"]
