@@ -352,7 +352,7 @@ def serve_bench(args):
     h = ch.CH.build(g, hop_limit=args.hop_limit)
     st = h.stats()
     nreq = args.serve_requests
-    src, ks, tg = ch.request_mix(n, nreq, seed=7)
+    src, ks, tg = I.request_mix(n, nreq, seed=7)
     expected = h.query(np.repeat(src, ks), tg)
 
     def pct(lat_ns):
@@ -371,7 +371,7 @@ def serve_bench(args):
         out["saturated"] = {"requests_per_s": max_rps, "queries_per_s": float(ks.sum()) / makespan,
                             **pct(lat), "service": pct(svc)}
         for frac in (0.5, 0.8, 0.95):
-            arr = ch.poisson_arrivals(nreq, max_rps * frac, seed=int(100 * frac))
+            arr = I.poisson_arrivals(nreq, max_rps * frac, seed=int(100 * frac))
             ans, lat, svc = sv.replay(src, ks, tg, arr, limit_s=1200.0)
             assert np.array_equal(ans, expected)
             span = (float(arr[-1]) + float(lat[-1])) * 1e-9

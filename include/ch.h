@@ -293,8 +293,9 @@ int ch_build_autotune(const ch_graph_t *graph, const ch_params_t *params,
                       uint32_t *chosen);
 
 /* Work of the query searches since the previous call (then cleared), summed
- * over the handle's batches: out[0] = queued entries expanded, out[1] =
- * adjacency entries scanned. Waits for `stream`. */
+ * over the handle's batches: out[0] = queued entries expanded (a stalled
+ * entry counts: its stall test read it), out[1] = adjacency entries scanned,
+ * the stall tests' included. Waits for `stream`. */
 int ch_query_work(ch_t *ch, void *stream, uint64_t out[2]);
 
 /* ---- Query batches as CUDA graphs ----

@@ -531,26 +531,6 @@ class Server:
             pass
 
 
-def request_mix(n: int, count: int, seed: int, one_to_many: float = 0.2, kmax: int = 1024):
-    """Seeded request mix: sources uniform in [0, n); with probability
-    1 - one_to_many a single target, else k = floor(2**U[0, log2 kmax])
-    targets (log-uniform 1..kmax), all uniform. Returns (src, ks, targets)."""
-    rng = np.random.default_rng(seed)
-    src = rng.integers(0, n, size=count, dtype=np.int64).astype(np.uint32)
-    many = rng.random(count) < one_to_many
-    ks = np.where(many, np.floor(2.0 ** (rng.random(count) * np.log2(kmax))), 1).astype(np.uint32)
-    ks = np.maximum(ks, 1)
-    targets = rng.integers(0, n, size=int(ks.sum()), dtype=np.int64).astype(np.uint32)
-    return src, ks, targets
-
-
-def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
-    """Arrival times (ns) of a Poisson process of the given rate."""
-    rng = np.random.default_rng(seed)
-    gaps = rng.exponential(1e9 / rate_per_s, size=count)
-    return np.cumsum(gaps).astype(np.uint64)
-
-
 def training_labels(rows) -> np.ndarray:
     """Target of each trace row (float32): sign(x) * log2(1 + |x|) of the
     score x = edge difference + 2 * hierarchy depth at that rescoring. The

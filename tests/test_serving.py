@@ -30,8 +30,8 @@ def _expected(gch, src, ks, targets):
 def test_mixed_stream_answers_equal_batch_answers(built):
     g, gch = built
     ch = _ch()
-    src, ks, targets = ch.request_mix(g.n, 3000, seed=72)
-    arr = ch.poisson_arrivals(src.size, rate_per_s=200_000, seed=73)
+    src, ks, targets = I.request_mix(g.n, 3000, seed=72)
+    arr = I.poisson_arrivals(src.size, rate_per_s=200_000, seed=73)
     with ch.Server(gch, blocks=96, ring=2048, pool=1 << 20, idle_ms=5000) as sv:
         ans, lat, svc = sv.replay(src, ks, targets, arr)
     assert np.array_equal(ans, _expected(gch, src, ks, targets))
@@ -45,7 +45,7 @@ def test_mixed_stream_answers_equal_batch_answers(built):
 def test_same_answer_alone_and_in_the_mix(built):
     g, gch = built
     ch = _ch()
-    src, ks, targets = ch.request_mix(g.n, 400, seed=74)
+    src, ks, targets = I.request_mix(g.n, 400, seed=74)
     toff = np.concatenate([[0], np.cumsum(ks.astype(np.int64))[:-1]]).astype(np.int64)
     with ch.Server(gch, blocks=32, ring=1024, pool=1 << 18) as sv:
         mix, _, _ = sv.replay(src, ks, targets, np.zeros(src.size, np.uint64))  # all at once
@@ -69,7 +69,7 @@ def test_same_answer_alone_and_in_the_mix(built):
 def test_admission_by_memory_and_ring(built):
     g, gch = built
     ch = _ch()
-    src, ks, targets = ch.request_mix(g.n, 600, seed=75, one_to_many=0.5)
+    src, ks, targets = I.request_mix(g.n, 600, seed=75, one_to_many=0.5)
     # a pool smaller than the sum of all targets and a short ring: requests
     # are admitted as earlier ones complete
     with ch.Server(gch, blocks=16, ring=64, pool=4096) as sv:
