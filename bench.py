@@ -182,17 +182,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_sample_build(workload: str, hop_limit: int, cmax, ball=None):
+def cpu_sample_build(workload: str, hop_limit: int, cmax, ball=None, threads: bool = False):
     """Oracle build on a sample graph of the same family, scaled linearly
     (by vertex count) to the full workload. Returns (scaled_s, raw_s,
-    threads, sample vertices)."""
+    threads used, sample vertices). threads: the -DORACLE_THREADS build,
+    whose witness searches run on every host thread."""
     import oracle as O
     g = make_graph(workload, sample=True)
     t0 = time.perf_counter()
     O.build_ch(g, hop_limit, cmax=O.CMAX_ALL if cmax is None else cmax,
-               ball=O.CMAX_ALL if ball is None else ball)
+               ball=O.CMAX_ALL if ball is None else ball, threads=threads)
     raw = time.perf_counter() - t0
-    return raw * (WORKLOADS[workload][0] / g.n), raw, 1, g.n
+    return raw * (WORKLOADS[workload][0] / g.n), raw, (os.cpu_count() or 1) if threads else 1, g.n
 
 
 def run_reference(args):
@@ -609,6 +610,12 @@ def main():
         cpu = {"value": scaled, "unit": "s", "cores": cores, "kind": "oracle",
                "sample": f"oracle build of a {sn}-vertex graph of the same family "
                          f"({raw:.2f} s, one thread), scaled linearly by vertex count to {n}"}
+        # the same oracle with its witness searches on every host thread
+        # (identical result; the rest of each round stays sequential)
+        mt_scaled, mt_raw, mt_cores, _ = cpu_sample_build(args.workload, args.hop_limit, args.cmax,
+                                                          args.witness_ball, threads=True)
+        cpu["threaded"] = {"value": mt_scaled, "unit": "s", "cores": mt_cores,
+                           "sample": f"same sample, -DORACLE_THREADS build ({mt_raw:.2f} s)"}
 
     if rank == 0:
         line = {

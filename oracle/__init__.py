@@ -23,6 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_LIB_MT = os.path.join(_LIB_DIR, "liboracle_mt.so")  # -DORACLE_THREADS
 INF = 0xFFFFFFFF
 
 STAT_FIELDS = ("affected", "score_sources", "selected", "contract_sources",
@@ -32,26 +33,29 @@ TIE_HASHED = 0
 TIE_ID = 1
 
 
-def build(force: bool = False) -> str:
-    """Compile ``oracle.cpp`` into ``_build/liboracle.so`` (portable flags)."""
+def build(force: bool = False, threads: bool = False) -> str:
+    """Compile ``oracle.cpp`` into ``_build/liboracle.so`` (portable flags),
+    or, with ``threads``, the -DORACLE_THREADS build ``liboracle_mt.so``."""
     os.makedirs(_LIB_DIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["g++", "-std=c++17", "-O2", "-shared", "-fPIC",
+    lib = _LIB_MT if threads else _LIB
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= os.path.getmtime(_SRC)):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
+    extra = ["-DORACLE_THREADS", "-pthread"] if threads else []
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-shared", "-fPIC", *extra,
                            "-o", tmp, _SRC])
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, lib)
+    return lib
 
 
-_lib = None
+_libs = {}
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = C.CDLL(build())
+def _load(threads: bool = False):
+    """The sequential oracle library, or (threads) its -DORACLE_THREADS build."""
+    if threads not in _libs:
+        lib = C.CDLL(build(threads=threads))
         P = C.c_void_p
         u32, u64, i32 = C.c_uint32, C.c_uint64, C.c_int32
         lib.orc_build.argtypes = [u32, u64, P, P, P, u32, u32, u32, C.POINTER(P)]
@@ -88,8 +92,8 @@ def _load():
                      "orc_dijkstra", "orc_dijkstra_pairs"):
             getattr(lib, name).restype = C.c_int
         del i32
-        _lib = lib
-    return _lib
+        _libs[threads] = lib
+    return _libs[threads]
 
 
 def _p(a):
@@ -117,6 +121,7 @@ class OracleCH:
     down: np.ndarray           # uint32[b, 3]: (x, u, w) downward edges
     stats: np.ndarray          # uint64[rounds, len(STAT_FIELDS)]
     _handle: C.c_void_p = field(default=None, repr=False)
+    _threads: bool = field(default=False, repr=False)  # which library owns the handle
 
     @property
     def rounds(self) -> int:
@@ -133,12 +138,13 @@ class OracleCH:
         out = np.empty(s.size, dtype=np.uint32)
         settled = np.empty(s.size, dtype=np.uint64)
         if s.size:
-            _load().orc_query_batch(self._handle, s.size, _p(s), _p(t), _p(out), _p(settled))
+            _load(self._threads).orc_query_batch(self._handle, s.size, _p(s), _p(t), _p(out),
+                                                 _p(settled))
         return (out, settled) if want_settled else out
 
     def close(self):
         if self._handle:
-            _load().orc_free(self._handle)
+            _load(self._threads).orc_free(self._handle)
             self._handle = None
 
     def __del__(self):
@@ -153,7 +159,7 @@ CMAX_ALL = (1 << 64) - 1
 
 def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int = 0,
              trace: bool = False, replay=None, cmax: int = CMAX_ALL,
-             ball: int = CMAX_ALL) -> OracleCH:
+             ball: int = CMAX_ALL, threads: bool = False) -> OracleCH:
     """Run the oracle's round algorithm on graph ``g`` (see ``oracle.cpp``).
 
     ``trace`` records the learned-priority features of every rescoring
@@ -163,9 +169,11 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
     ``cmax`` bounds |N_in| * |N_out| of a contractible vertex; the vertices
     left when none is eligible form the core. ``ball`` bounds each witness
     search: it stops after the first hop level at which more than ``ball``
-    vertices hold a label (see ``oracle.cpp``).
+    vertices hold a label (see ``oracle.cpp``). ``threads`` runs the
+    -DORACLE_THREADS build (witness searches on all host threads; the same
+    result).
     """
-    lib = _load()
+    lib = _load(threads)
     args, keep = _graph_args(g)
     h = C.c_void_p()
     if replay is None:
@@ -210,7 +218,7 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
     if n:
         lib.orc_get_labels(h, _p(labels))
     del keep
-    och = OracleCH(n, hop_limit, level, prio, rank, sc, up, down, stats, h)
+    och = OracleCH(n, hop_limit, level, prio, rank, sc, up, down, stats, h, threads)
     och.trace = tr
     och.labels = labels
     return och

@@ -6,7 +6,9 @@
 // baseline leg load it; the library's product path never does. It shares no
 // code, header, table or helper with the CUDA path.
 //
-// It is deliberately plain: single-threaded, ordered std::map adjacency,
+// It is deliberately plain: single-threaded (a build with -DORACLE_THREADS
+// runs each phase's witness searches on all host threads, with identical
+// results), ordered std::map adjacency,
 // every step applied literally in the order the paper gives it, no blocking,
 // no fusion, no pruning of searches. Where the paper leaves a detail open the
 // reading taken is stated next to the code.
@@ -84,6 +86,9 @@
 
 #include <algorithm>
 #include <array>
+#ifdef ORACLE_THREADS
+#include <thread>
+#endif
 #include <cstdint>
 #include <cstring>
 #include <functional>
@@ -232,30 +237,61 @@ uint64_t pair_key(uint32_t a, uint32_t b) { return (uint64_t(a) << 32) | b; }
 uint64_t local_search(const Overlay& g, const std::vector<char>& middle,
                       const std::vector<uint32_t>& middle_list, uint32_t H,
                       HopSearch& hs, std::unordered_map<uint64_t, uint32_t>& dist,
-                      uint64_t ball = ~uint64_t(0)) {
+                      uint64_t ball = ~uint64_t(0), std::vector<HopSearch>* per_thread = nullptr) {
     std::vector<uint32_t> sources;
     for (uint32_t u : middle_list)
         for (const auto& [v1, w1] : g.in[u]) sources.push_back(v1);
     std::sort(sources.begin(), sources.end());
     sources.erase(std::unique(sources.begin(), sources.end()), sources.end());
     dist.clear();
-    for (uint32_t s : sources) {
+    // One source's searches and its (pair, distance) records.
+    auto search = [&](uint32_t s, HopSearch& h, std::vector<std::pair<uint64_t, uint32_t>>& outp) {
         uint32_t bound = 0;  // heaviest candidate weight of s
         for (const auto& [u, w1] : g.out[s]) {
             if (!middle[u]) continue;
             for (const auto& [v, w2] : g.out[u])
                 if (v != s) bound = std::max(bound, sat_add(w1, w2));
         }
-        if (bound == 0) continue;  // no candidate from s
-        hs.run(g.out, s, H, bound, ball);
+        if (bound == 0) return;  // no candidate from s
+        h.run(g.out, s, H, bound, ball);
         for (const auto& [u, w1] : g.out[s]) {
             if (!middle[u]) continue;
             for (const auto& [v, w2] : g.out[u]) {
                 if (v == s) continue;
-                dist[pair_key(s, v)] = hs.dist(v);
+                outp.push_back({pair_key(s, v), h.dist(v)});
             }
         }
+    };
+#ifdef ORACLE_THREADS
+    // Threaded build: the sources are split over host threads, each with its
+    // own search state; every record depends on its source alone, so the map
+    // is the same as the sequential one.
+    std::vector<HopSearch> local;
+    if (!per_thread) {
+        per_thread = &local;
+        const unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+        for (unsigned t = 0; t < nt; ++t) local.emplace_back(uint32_t(g.out.size()));
     }
+    const size_t nt = per_thread->size();
+    std::vector<std::vector<std::pair<uint64_t, uint32_t>>> parts(nt);
+    std::vector<std::thread> pool;
+    for (size_t t = 0; t < nt; ++t)
+        pool.emplace_back([&, t] {
+            for (size_t i = t; i < sources.size(); i += nt) search(sources[i], (*per_thread)[t], parts[t]);
+        });
+    for (auto& th : pool) th.join();
+    for (const auto& p : parts)
+        for (const auto& [k, v] : p) dist[k] = v;
+    (void)hs;
+#else
+    (void)per_thread;
+    std::vector<std::pair<uint64_t, uint32_t>> recs;
+    for (uint32_t s : sources) {
+        recs.clear();
+        search(s, hs, recs);
+        for (const auto& [k, v] : recs) dist[k] = v;
+    }
+#endif
     return sources.size();
 }
 
@@ -368,6 +404,13 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
     ch.down.assign(n, {});
     HopSearch hs(n);
     std::unordered_map<uint64_t, uint32_t> dist;
+    std::vector<HopSearch>* per_thread = nullptr;
+#ifdef ORACLE_THREADS
+    std::vector<HopSearch> hs_pool;
+    for (unsigned t = 0, nt = std::max(1u, std::thread::hardware_concurrency()); t < nt; ++t)
+        hs_pool.emplace_back(n);
+    per_thread = &hs_pool;
+#endif
 
     uint64_t live = n;
     uint64_t live_edges = 0;
@@ -393,7 +436,7 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
 
         // Step 1: LocalSearch for the affected set.
         for (uint32_t u : Ae) inA[u] = 1;
-        st[ST_SCORE_SOURCES] = local_search(g, inA, Ae, H, hs, dist, ball);
+        st[ST_SCORE_SOURCES] = local_search(g, inA, Ae, H, hs, dist, ball, per_thread);
 
         // Step 2: Score (edge difference), or the replayed priority; the
         // features are taken from the same overlay.
@@ -448,7 +491,7 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
         // Step 4: Contract. Witness distances for the candidates of V_F on
         // the same overlay.
         for (uint32_t u : F) inF[u] = 1;
-        st[ST_CONTRACT_SOURCES] = local_search(g, inF, F, H, hs, dist, ball);
+        st[ST_CONTRACT_SOURCES] = local_search(g, inF, F, H, hs, dist, ball, per_thread);
 
         std::map<std::pair<uint32_t, uint32_t>, std::pair<uint32_t, uint32_t>> best;
         for (uint32_t u : F) {

@@ -409,3 +409,21 @@ def test_core_closed_forms():
         assert (ch.level < ch.rounds).all()
         lv = ch.level.astype(np.int64)
         assert (lv[: n // 2] == np.arange(n // 2)).all() or n % 2 == 0
+
+
+# ---------------------------------------------------------------------------
+# The threaded oracle build (-DORACLE_THREADS) gives the same hierarchy
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,g", [(n, g) for n, g in small_families()
+                                    if n in ("digraph2", "grid8", "geo150", "rmat8", "star9")],
+                         ids=lambda x: x if isinstance(x, str) else "")
+@pytest.mark.parametrize("cmax,ball", [(O.CMAX_ALL, O.CMAX_ALL), (6, O.CMAX_ALL), (O.CMAX_ALL, 4)])
+def test_threaded_build_is_identical(name, g, cmax, ball):
+    a = O.build_ch(g, 5, cmax=cmax, ball=ball, trace=True)
+    b = O.build_ch(g, 5, cmax=cmax, ball=ball, trace=True, threads=True)
+    for f in ("level", "priority", "rank", "shortcuts", "up", "down", "stats", "trace", "labels"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    s, t = np.meshgrid(np.arange(g.n), np.arange(g.n), indexing="ij")
+    s, t = s.ravel(), t.ravel()
+    assert np.array_equal(a.query(s, t), b.query(s, t))
