@@ -59,7 +59,8 @@ def test_golden_examples(name):
     spec = load_golden(name)
     tie = 1 if spec.get("tie_break") == "id" else 0
     g = ch_mod().CH.build(spec["graph"], hop_limit=spec["hop_limit"], tie_break=tie,
-                          max_candidates_per_vertex=spec.get("cmax"))
+                          max_candidates_per_vertex=spec.get("cmax"),
+                          witness_ball_limit=spec.get("ball"))
     ex = g.export()
     assert ex["level"].tolist() == spec["expect_level"]
     assert ex["priority"].tolist() == spec["expect_priority"]

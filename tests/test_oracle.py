@@ -47,9 +47,10 @@ def _walk_bruteforce(adj, src, H):
 def test_golden_examples(name):
     spec = load_golden(name)
     tie = O.TIE_ID if spec.get("tie_break") == "id" else O.TIE_HASHED
-    ch = O.build_ch(spec["graph"], spec["hop_limit"], tie, cmax=spec.get("cmax", O.CMAX_ALL))
+    ch = O.build_ch(spec["graph"], spec["hop_limit"], tie, cmax=spec.get("cmax", O.CMAX_ALL),
+                    ball=spec.get("ball", O.CMAX_ALL))
     assert ch.rounds == spec["expect_rounds"]
-    if "expect_stats" in spec:  # a single round's counters
+    if "expect_stats" in spec:  # every round's counters, row after row
         assert ch.stats.ravel().tolist() == spec["expect_stats"]
     assert ch.level.tolist() == spec["expect_level"]
     assert ch.priority.tolist() == spec["expect_priority"]
