@@ -224,6 +224,22 @@ int ch_query_batch_static(ch_t *ch, const uint32_t *src, const uint32_t *dst, ui
  * by earlier ch_query_batch calls on this handle. */
 int ch_query_status(ch_t *ch, void *stream);
 
+/* One-to-many distances from s to each of k targets (Sec. 5's query for
+ * every pair (s, dst[i])): dst and dist_out are device pointers, the call
+ * is asynchronous on `stream` like ch_query_batch and follows its no-overlap
+ * rule. CH_EINVAL if s >= n; target ids >= n are reported by
+ * ch_query_status. */
+int ch_query_one_to_many(ch_t *ch, uint32_t s, const uint32_t *dst, uint64_t k,
+                         uint32_t *dist_out, void *stream);
+
+/* Saves a built hierarchy to `path` (binary, little-endian; everything
+ * ch_query_batch, ch_export and ch_get_stats use, not learned-priority
+ * traces) and loads one back onto the current device. CH_EINVAL on I/O
+ * errors, a file that is not a saved hierarchy, or a truncated or
+ * inconsistent one; on error nothing is written to *out. */
+int ch_save(const ch_t *ch, const char *path);
+int ch_load(const char *path, ch_t **out);
+
 /* ---- Query kernel configuration and autotuning (performance only) ----
  *
  * One block runs one query at a time (Sec. 5's two upward searches, level

@@ -148,6 +148,11 @@ def load(build_if_missing: bool = True):
                                       C.c_uint32, C.c_uint64, C.c_double, C.POINTER(P),
                                       C.POINTER(TuneRowT), C.POINTER(C.c_uint32)]
     lib.ch_build_autotune.restype = C.c_int
+    lib.ch_query_one_to_many.argtypes = [P, C.c_uint32, P, C.c_uint64, P, P]
+    lib.ch_save.argtypes = [P, C.c_char_p]
+    lib.ch_load.argtypes = [C.c_char_p, C.POINTER(P)]
+    for f in ("ch_query_one_to_many", "ch_save", "ch_load"):
+        getattr(lib, f).restype = C.c_int
     lib.ch_set_query_config.argtypes = [P, C.POINTER(QueryConfigT)]
     lib.ch_get_query_config.argtypes = [P, C.POINTER(QueryConfigT)]
     lib.ch_query_autotune.argtypes = [P, C.c_uint64, C.c_uint32, P, C.POINTER(QueryConfigT), P]
@@ -335,6 +340,25 @@ class CH:
         """ch_query_batch on raw device pointers (used inside timed loops)."""
         _check(load().ch_query_batch(self._h, src_ptr, dst_ptr, k, out_ptr, settled_ptr,
                                      stream_ptr))
+
+    def query_one_to_many(self, s: int, dst, stream=None):
+        """Distances from s to every target of the CUDA tensor ``dst``
+        (int32 view of uint32 ids), asynchronous on ``stream``."""
+        import torch
+        out = torch.empty_like(dst)
+        _check(load().ch_query_one_to_many(self._h, int(s), dst.data_ptr(), dst.numel(),
+                                           out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    # -- saving and loading -------------------------------------------------
+    def save(self, path: str):
+        _check(load().ch_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str) -> "CH":
+        h = C.c_void_p()
+        _check(load().ch_load(os.fsencode(path), C.byref(h)))
+        return cls(h)
 
     # -- query configuration, autotuning, work, graphs ----------------------
     def set_query_config(self, layout: int, threads: int, small_first: int = 0, stall: int = 0):

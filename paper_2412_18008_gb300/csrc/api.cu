@@ -243,6 +243,38 @@ int ch_build_autotune(const ch_graph_t *graph, const ch_params_t *params, const 
     return CH_OK;
 }
 
+int ch_query_one_to_many(ch_t *ch, uint32_t s, const uint32_t *dst, uint64_t k, uint32_t *dist_out,
+                         void *stream) {
+    if (!ch || (k && (!dst || !dist_out))) {
+        g_last_error = "null argument";
+        return CH_EINVAL;
+    }
+    if (k && s >= ch->n) {
+        g_last_error = "source id out of range";
+        return CH_EINVAL;
+    }
+    return guarded([&] { query_one_to_many(ch, s, dst, k, dist_out, static_cast<cudaStream_t>(stream)); });
+}
+
+int ch_save(const ch_t *ch, const char *path) {
+    if (!ch || !path) {
+        g_last_error = "null argument";
+        return CH_EINVAL;
+    }
+    return guarded([&] { save_hierarchy(ch, path); });
+}
+
+int ch_load(const char *path, ch_t **out) {
+    if (!path || !out) {
+        g_last_error = "null argument";
+        return CH_EINVAL;
+    }
+    ch_s *h = nullptr;
+    const int rc = guarded([&] { h = load_hierarchy(path); });
+    if (rc == CH_OK) *out = h;
+    return rc;
+}
+
 int ch_set_query_config(ch_t *ch, const ch_query_config_t *cfg) {
     if (!ch || !cfg) {
         g_last_error = "null argument";

@@ -68,6 +68,7 @@ struct ch_s {
     uint32_t q_stall = 1;        // stall on demand (warp layout, pruned searches)
     uint32_t q_slots = 0;
     uint64_t q_ovf_cap = 0;
+    gbch::DevBuf<uint32_t> q_src_fill;  // repeated source of one-to-many queries
 };
 
 namespace gbch {
@@ -97,6 +98,12 @@ ch_query_graph_s *query_graph_create(ch_s *h, const uint32_t *src, const uint32_
                                      uint32_t *dist_out);
 void query_graph_launch(ch_query_graph_s *g, cudaStream_t st);
 void query_graph_free(ch_query_graph_s *g);
+
+// Saving and loading, one-to-many queries (io.cu).
+void save_hierarchy(const ch_s *h, const char *path);
+ch_s *load_hierarchy(const char *path);
+void query_one_to_many(ch_s *h, uint32_t s, const uint32_t *dst, uint64_t k, uint32_t *dist_out,
+                       cudaStream_t st);
 
 // Query server (serve.cu).
 ch_server_s *server_new();
