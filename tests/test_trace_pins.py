@@ -1,0 +1,123 @@
+"""Every trace row of every round, recomputed from definitions (no GPU).
+
+Each round's overlay is rebuilt from the exported hierarchy alone: the
+normalised input, with the logged shortcuts of earlier rounds applied (a
+logged shortcut is an insertion or a strictly lighter replacement), minus the
+vertices contracted in earlier rounds. The 12 features of each rescoring
+then follow from their definitions on that overlay: the score uses the
+plain hop-limited distance (oracle.hop_limited, pinned in test_oracle.py),
+the contracted-neighbour count and depth use the CH edges recorded at
+earlier contractions. This pins the round loop's bookkeeping, its overlay
+updates and its scores in every round, independently of the loop itself."""
+from collections import defaultdict
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2412_18008_gb300 import inputs as I
+from tests.graphs import INF, small_families
+
+
+def _graph_from_pairs(n, pairs):
+    if pairs:
+        src, dst, w = (np.array(x, dtype=np.int64) for x in zip(*[(a, b, c) for (a, b), c in pairs.items()]))
+    else:
+        src = dst = w = np.zeros(0, np.int64)
+    return I.csr_from_edges(n, src, dst, w)
+
+
+def _check(g, H, cmax=O.CMAX_ALL):
+    och = O.build_ch(g, H, trace=True, cmax=cmax)
+    n = g.n
+    off, tgt, w = O.normalize(g)
+    base = {}
+    for a in range(n):
+        for e in range(int(off[a]), int(off[a + 1])):
+            base[(a, int(tgt[e]))] = int(w[e])
+    orig_deg = np.zeros(n, np.int64)
+    for (a, b) in base:
+        orig_deg[a] += 1
+        orig_deg[b] += 1
+    level = och.level.astype(np.int64)
+    by_round = defaultdict(list)
+    for r, v1, v2, ws, via in och.shortcuts.tolist():
+        by_round[r].append((v1, v2, ws))
+    # CH edges recorded at each contraction: (contracted u, neighbour x)
+    ch_nb = defaultdict(list)  # u -> neighbours x (one entry per edge)
+    for u, x, _ in och.up.tolist():
+        ch_nb[u].append(x)
+    for x, u, _ in och.down.tolist():
+        ch_nb[u].append(x)
+    # depth: 1 + the deepest CH neighbour contracted earlier (0 if none)
+    nb_before = defaultdict(list)  # x -> contracted neighbours u (one per CH edge)
+    for u, xs in ch_nb.items():
+        for x in xs:
+            nb_before[x].append(u)
+
+    def depth_of(x, r):
+        ds = [depth_at_c(u) + 1 for u in nb_before[x] if level[u] < r]
+        return max(ds, default=0)
+
+    memo = {}
+
+    def depth_at_c(u):
+        if u not in memo:
+            memo[u] = depth_of(u, level[u])
+        return memo[u]
+
+    edges = dict(base)
+    rows = och.trace.tolist()
+    seen = defaultdict(int)
+    ri = 0
+    for r in range(och.rounds):
+        # overlay of round r: shortcuts of rounds < r applied, dead vertices removed
+        for v1, v2, ws in by_round.get(r - 1, []):
+            edges[(v1, v2)] = ws
+        live = {k: v for k, v in edges.items() if level[k[0]] >= r and level[k[1]] >= r}
+        gr = _graph_from_pairs(n, live)
+        out, inn = defaultdict(dict), defaultdict(dict)
+        for (a, b), c in live.items():
+            out[a][b] = c
+            inn[b][a] = c
+        dh = {}
+        while ri < len(rows) and rows[ri][0] == r:
+            _, x, *f = rows[ri]
+            ri += 1
+            i, o = len(inn[x]), len(out[x])
+            S = 0
+            for v1, w1 in inn[x].items():
+                if v1 not in dh:
+                    dh[v1] = O.hop_limited(gr, H, v1)
+                for v2, w2 in out[x].items():
+                    if v1 != v2 and w1 + w2 < INF and w1 + w2 <= dh[v1][v2]:
+                        S += 1
+            ed = S - i - o
+            wsum = sum(inn[x].values()) + sum(out[x].values())
+            cn = sum(1 for u in nb_before[x] if level[u] < r)
+            want = [S, i, o, len(set(inn[x]) | set(out[x])), ed, cn, depth_of(x, r), r, i * o,
+                    int(orig_deg[x]), seen[x], wsum // (i + o) if i + o else 0]
+            assert f == want, (r, x, f, want)
+            seen[x] += 1
+    assert ri == len(rows)
+    # the score at contraction is the last rescoring's edge difference
+    last_ed = {}
+    for r, x, *f in rows:
+        last_ed[x] = f[4]
+    contracted = level < och.rounds
+    for x in np.flatnonzero(contracted).tolist():
+        assert och.priority[x] == last_ed[x]
+        assert och.labels[x] == last_ed[x] + depth_at_c(x)
+
+
+@pytest.mark.parametrize("name,g", [(n, g) for n, g in small_families()
+                                    if n in ("digraph0", "digraph4", "sparse3", "grid8", "geo150",
+                                             "rmat8", "chain30", "star9")],
+                         ids=lambda x: x if isinstance(x, str) else "")
+@pytest.mark.parametrize("H", [2, 5])
+def test_trace_rows_recomputed_for_every_round(name, g, H):
+    _check(g, H)
+
+
+def test_trace_rows_recomputed_with_a_core():
+    _check(I.random_digraph(70, 300, 1, 20, seed=41), 5, cmax=9)
