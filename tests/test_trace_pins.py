@@ -121,3 +121,124 @@ def test_trace_rows_recomputed_for_every_round(name, g, H):
 
 def test_trace_rows_recomputed_with_a_core():
     _check(I.random_digraph(70, 300, 1, 20, seed=41), 5, cmax=9)
+
+
+# ---------------------------------------------------------------------------
+# Every round re-derived: affected set, eligibility, selection, candidates,
+# witness decisions, merge, insertion and the round's counters
+# ---------------------------------------------------------------------------
+
+P_INELIGIBLE = 2**31 - 2
+
+
+def _fmix32(h):
+    # MurmurHash3 32-bit finaliser (Appleby), as published
+    h ^= h >> 16
+    h = (h * 0x85EBCA6B) & 0xFFFFFFFF
+    h ^= h >> 13
+    h = (h * 0xC2B2AE35) & 0xFFFFFFFF
+    h ^= h >> 16
+    return h
+
+
+def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL):
+    och = O.build_ch(g, H, tie, tie_seed=seed, cmax=cmax)
+    n = g.n
+    off, tgt, w = O.normalize(g)
+    edges = {}
+    for a in range(n):
+        for e in range(int(off[a]), int(off[a + 1])):
+            edges[(a, int(tgt[e]))] = int(w[e])
+    log = defaultdict(set)
+    for r, v1, v2, ws, via in och.shortcuts.tolist():
+        log[r].add((v1, v2, ws, via))
+    level = och.level.astype(np.int64)
+    alive = np.ones(n, bool)
+    P = np.zeros(n, np.int64)
+    eligible = np.ones(n, bool)
+    A = set(range(n))
+
+    def key(u):
+        lo = u if tie == O.TIE_ID else _fmix32(u ^ seed)
+        return ((int(P[u]) & 0xFFFFFFFF) ^ 0x80000000) << 32 | lo
+
+    r = 0
+    while alive.any():
+        live = {k: v for k, v in edges.items() if alive[k[0]] and alive[k[1]]}
+        out, inn = defaultdict(dict), defaultdict(dict)
+        for (a, b), c in live.items():
+            out[a][b] = c
+            inn[b][a] = c
+        gr = _graph_from_pairs(n, live)
+        dh = {}
+
+        def d(v1, v2):
+            if v1 not in dh:
+                dh[v1] = O.hop_limited(gr, H, v1)
+            return int(dh[v1][v2])
+
+        def kept(v1, u, v2):
+            via = inn[u][v1] + out[u][v2]
+            return via < INF and via <= d(v1, v2), via
+
+        # rescoring of the affected set (Alg. 3, 4) under the candidate bound
+        score_sources = set()
+        for u in A:
+            eligible[u] = len(inn[u]) * len(out[u]) <= cmax
+            if not eligible[u]:
+                P[u] = P_INELIGIBLE
+                continue
+            score_sources |= set(inn[u])
+            S = sum(1 for v1 in inn[u] for v2 in out[u] if v1 != v2 and kept(v1, u, v2)[0])
+            P[u] = S - len(inn[u]) - len(out[u])
+        # selection (Alg. 5): strict local minima of the key over N(u)
+        F = [u for u in np.flatnonzero(alive).tolist() if eligible[u]
+             and all(key(u) < key(v) for v in set(inn[u]) | set(out[u]))]
+        if not F:
+            core = np.flatnonzero(alive)
+            assert (level[core] == r).all() and och.rounds == r
+            return och
+        assert sorted(F) == np.flatnonzero(level == r).tolist(), r
+        # contraction (Alg. 6): candidates, witness test, merge, insertion
+        best, cand, keep_n = {}, 0, 0
+        for u in F:
+            for v1 in inn[u]:
+                for v2 in out[u]:
+                    if v1 == v2:
+                        continue
+                    cand += 1
+                    ok, via = kept(v1, u, v2)
+                    if ok:
+                        keep_n += 1
+                        best[(v1, v2)] = min(best.get((v1, v2), (INF + 1, n)), (via, u))
+        inserted = {(v1, v2, wv, via) for (v1, v2), (wv, via) in best.items()
+                    if (v1, v2) not in live or wv < live[(v1, v2)]}
+        assert inserted == log[r], r
+        contract_sources = set().union(*(set(inn[u]) for u in F))
+        nextA = set().union(*(set(inn[u]) | set(out[u]) for u in F))
+        for v1, v2, wv, _ in inserted:
+            edges[(v1, v2)] = wv
+        for u in F:
+            alive[u] = False
+        live_after = sum(1 for (a, b) in edges if alive[a] and alive[b])
+        row = [len(A), len(score_sources), len(F), len(contract_sources), cand, keep_n, len(best),
+               len(inserted), int(alive.sum()), live_after]
+        assert och.stats[r].tolist() == row, (r, och.stats[r].tolist(), row)
+        A = {x for x in nextA if alive[x]}
+        r += 1
+    assert och.rounds == r
+    return och
+
+
+@pytest.mark.parametrize("name,g", [(n, g) for n, g in small_families()
+                                    if n in ("digraph1", "digraph5", "sparse0", "sparse4", "grid8",
+                                             "geo150", "rmat8", "chain30d", "star9", "complete6")],
+                         ids=lambda x: x if isinstance(x, str) else "")
+@pytest.mark.parametrize("H,tie", [(5, O.TIE_HASHED), (2, O.TIE_ID), (0, O.TIE_HASHED)])
+def test_every_round_rederived(name, g, H, tie):
+    _rederive(g, H, tie, seed=23)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_every_round_rederived_with_a_core(seed):
+    _rederive(I.random_digraph(70, 300, 1, 20, seed=50 + seed), 5, O.TIE_HASHED, cmax=9)
