@@ -141,8 +141,8 @@ def _fmix32(h):
     return h
 
 
-def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL):
-    och = O.build_ch(g, H, tie, tie_seed=seed, cmax=cmax)
+def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None):
+    och = O.build_ch(g, H, tie, tie_seed=seed, cmax=cmax, ball=O.CMAX_ALL if ball is None else ball)
     n = g.n
     off, tgt, w = O.normalize(g)
     edges = {}
@@ -172,19 +172,40 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL):
         gr = _graph_from_pairs(n, live)
         dh = {}
 
-        def d(v1, v2):
-            if v1 not in dh:
-                dh[v1] = O.hop_limited(gr, H, v1)
-            return int(dh[v1][v2])
+        def d(v1, v2, middles):
+            # witness distance of the phase whose contracted middles are
+            # `middles`: d_H, or with a ball bound the distances of the first
+            # level at which more than `ball` vertices hold a label below the
+            # source's heaviest candidate weight
+            if ball is None:
+                if v1 not in dh:
+                    dh[v1] = O.hop_limited(gr, H, v1)
+                return int(dh[v1][v2])
+            bound = max([c1 + c2 for u, c1 in out[v1].items() if u in middles
+                         for x, c2 in out[u].items() if x != v1], default=0)
+            keyd = (v1, bound)
+            if keyd not in dh:
+                lab = None
+                for h in range(1, H + 1):
+                    dist_h = O.hop_limited(gr, h, v1)
+                    lab = np.where(dist_h.astype(np.int64) < bound, dist_h, INF)
+                    if int((lab != INF).sum()) > ball:
+                        break
+                dh[keyd] = lab if lab is not None else np.where(np.arange(n) == v1, 0, INF)
+            return int(dh[keyd][v2])
+
+        phase = {"middles": set()}
 
         def kept(v1, u, v2):
             via = inn[u][v1] + out[u][v2]
-            return via < INF and via <= d(v1, v2), via
+            return via < INF and via <= d(v1, v2, phase["middles"]), via
 
         # rescoring of the affected set (Alg. 3, 4) under the candidate bound
         score_sources = set()
         for u in A:
             eligible[u] = len(inn[u]) * len(out[u]) <= cmax
+        phase["middles"] = {u for u in A if eligible[u]}
+        for u in A:
             if not eligible[u]:
                 P[u] = P_INELIGIBLE
                 continue
@@ -200,6 +221,7 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL):
             return och
         assert sorted(F) == np.flatnonzero(level == r).tolist(), r
         # contraction (Alg. 6): candidates, witness test, merge, insertion
+        phase["middles"] = set(F)
         best, cand, keep_n = {}, 0, 0
         for u in F:
             for v1 in inn[u]:
@@ -242,3 +264,11 @@ def test_every_round_rederived(name, g, H, tie):
 @pytest.mark.parametrize("seed", range(3))
 def test_every_round_rederived_with_a_core(seed):
     _rederive(I.random_digraph(70, 300, 1, 20, seed=50 + seed), 5, O.TIE_HASHED, cmax=9)
+
+
+@pytest.mark.parametrize("name,g", [(n, g) for n, g in small_families()
+                                    if n in ("digraph2", "sparse1", "grid8", "geo150", "rmat8")],
+                         ids=lambda x: x if isinstance(x, str) else "")
+@pytest.mark.parametrize("ball", [1, 3, 8])
+def test_every_round_rederived_with_a_ball_bound(name, g, ball):
+    _rederive(g, 4, O.TIE_HASHED, seed=5, ball=ball)
