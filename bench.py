@@ -81,6 +81,31 @@ def max_over_ranks(values, world: int, device):
     return t.tolist()
 
 
+def query_latency(h, s_d, t_d, stream, samples: int = 2000):
+    """p50/p99 (us) of single s-t queries, one ch_query_batch call each, timed
+    on the device; None (with the error) if the probe cannot run."""
+    try:
+        import torch
+        k = min(samples, s_d.numel())
+        out = torch.empty(1, dtype=torch.int32, device=s_d.device)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        sp = stream.cuda_stream
+        for _ in range(16):  # warm-up
+            h.query_batch_raw(s_d[0:].data_ptr(), t_d[0:].data_ptr(), 1, out.data_ptr(), None, sp)
+        for i in range(k):
+            a, b = ev[i]
+            a.record(stream)
+            h.query_batch_raw(s_d[i:].data_ptr(), t_d[i:].data_ptr(), 1, out.data_ptr(), None, sp)
+            b.record(stream)
+        stream.synchronize()
+        us = np.array([a.elapsed_time(b) * 1e3 for a, b in ev])
+        return {"p50_us": float(np.percentile(us, 50)), "p99_us": float(np.percentile(us, 99)),
+                "samples": int(k), "how": "one-pair ch_query_batch calls, CUDA events on the stream"}
+    except Exception as e:  # the probe must never cost the benchmark line
+        return {"p50_us": None, "p99_us": None, "error": repr(e)[:200]}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -538,6 +563,10 @@ def main():
     stream.synchronize()
     mean_ss = float(st.cpu().numpy().view(np.uint32).mean())
 
+    # single-query latency: one-pair batches on an idle GPU, each timed with
+    # CUDA events on the stream (outside the timed region)
+    latency = query_latency(h_last, s_d, t_d, stream, samples=2000)
+
     # roofline of the dominant kernel: the query block kernel (k_query_block,
     # one persistent launch per batch of up to 4M queries). Algorithmic bytes
     # per launch: 12 B per expanded frontier entry (its two CSR offsets and
@@ -634,6 +663,7 @@ def main():
             # slowest rank's batch time
             "queries_per_s": world * nq / (mean_query / 1000.0), "query_batch_ms": mean_query,
             "mean_search_space": mean_ss,
+            "query_latency": latency,
             "build_phases_ms": phases,
             "round_profile": round_profile,
             "roofline": roofline,
