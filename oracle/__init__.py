@@ -62,7 +62,13 @@ def _load(threads: bool = False):
         lib.orc_build.restype = C.c_int
         lib.orc_free.argtypes = [P]
         lib.orc_build2.argtypes = [u32, u64, P, P, P, u32, u32, u32, C.c_int, u64, P, P, P,
-                                   u64, u64, C.POINTER(P)]
+                                   u64, u64, u64, C.c_int, C.POINTER(P)]
+        lib.orc_num_pruned.argtypes = [P]
+        lib.orc_num_pruned.restype = u64
+        lib.orc_get_pruned.argtypes = [P, P]
+        lib.orc_get_pruned.restype = None
+        lib.orc_one_to_all.argtypes = [P, u64, P, P]
+        lib.orc_one_to_all.restype = C.c_int
         lib.orc_build2.restype = C.c_int
         lib.orc_num_trace.argtypes = [P]
         lib.orc_num_trace.restype = u64
@@ -142,6 +148,18 @@ class OracleCH:
                                                  _p(settled))
         return (out, settled) if want_settled else out
 
+    def one_to_all(self, sources) -> np.ndarray:
+        """Distances from each source to every vertex (upward search, then a
+        downward sweep in descending rank), uint32[len(sources), n]."""
+        s = np.ascontiguousarray(np.atleast_1d(sources), dtype=np.uint32)
+        out = np.empty((s.size, self.n), dtype=np.uint32)
+        if s.size and self.n:
+            if _load(self._threads).orc_one_to_all(self._handle, s.size, _p(s), _p(out)) != 0:
+                raise ValueError("source vertex out of range")
+        elif s.size:
+            raise ValueError("source vertex out of range")
+        return out
+
     def close(self):
         if self._handle:
             _load(self._threads).orc_free(self._handle)
@@ -159,7 +177,8 @@ CMAX_ALL = (1 << 64) - 1
 
 def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int = 0,
              trace: bool = False, replay=None, cmax: int = CMAX_ALL,
-             ball: int = CMAX_ALL, threads: bool = False) -> OracleCH:
+             ball: int = CMAX_ALL, threads: bool = False, theta: int = 0,
+             prune: bool = False) -> OracleCH:
     """Run the oracle's round algorithm on graph ``g`` (see ``oracle.cpp``).
 
     ``trace`` records the learned-priority features of every rescoring
@@ -169,9 +188,13 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
     ``cmax`` bounds |N_in| * |N_out| of a contractible vertex; the vertices
     left when none is eligible form the core. ``ball`` bounds each witness
     search: it stops after the first hop level at which more than ``ball``
-    vertices hold a label (see ``oracle.cpp``). ``threads`` runs the
-    -DORACLE_THREADS build (witness searches on all host threads; the same
-    result).
+    vertices hold a label (see ``oracle.cpp``). ``theta`` > 0 replaces the
+    hop-limited search by Alg. 3's Dijkstra capped at ``theta`` settled
+    vertices (``ball`` must then stay unbounded). ``prune`` deletes, after
+    each LocalSearch, the overlay edges heavier than the witness distance of
+    their pair (``OracleCH.pruned``: rows of round, s, v, w). ``threads`` runs
+    the -DORACLE_THREADS build (witness searches on all host threads; the
+    same result).
     """
     lib = _load(threads)
     args, keep = _graph_args(g)
@@ -184,7 +207,8 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
         ru = np.ascontiguousarray(replay[1], np.uint32)
         rpv = np.ascontiguousarray(replay[2], np.int32)
     rc = lib.orc_build2(*args, hop_limit, tie_break, tie_seed & 0xFFFFFFFF, int(trace),
-                        rr.size, _p(rr), _p(ru), _p(rpv), int(cmax), int(ball), C.byref(h))
+                        rr.size, _p(rr), _p(ru), _p(rpv), int(cmax), int(ball), int(theta),
+                        int(bool(prune)), C.byref(h))
     if rc != 0:
         raise ValueError(f"oracle rejected the graph or parameters (status {rc})")
     n = g.n
@@ -219,8 +243,13 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
         lib.orc_get_labels(h, _p(labels))
     del keep
     och = OracleCH(n, hop_limit, level, prio, rank, sc, up, down, stats, h, threads)
+    npr = lib.orc_num_pruned(h)
+    pruned = np.empty((npr, 4), np.uint32)
+    if npr:
+        lib.orc_get_pruned(h, _p(pruned))
     och.trace = tr
     och.labels = labels
+    och.pruned = pruned
     return och
 
 

@@ -43,6 +43,16 @@
 //     and d_h replaces d_H (still an upper bound on a real walk, so the
 //     distances stay exact; only more shortcuts may be kept). Unbounded by
 //     default.
+//   * Settled-vertex cap (optional, theta > 0): the search of Alg. 3 as
+//     written, a Dijkstra from the source that stops when all its targets or
+//     theta vertices are settled; an unsettled target's distance is INF.
+//     Equal labels are settled in id order, which makes the cap exact: the
+//     settled set is the first theta vertices in (distance, id) order. The
+//     hop limit and the ball bound do not apply in this mode.
+//   * Pruning (optional): after the searches of a round's LocalSearch, every
+//     overlay edge (s, v) heavier than the distance recorded for (s, v) is
+//     deleted (Alg. 3), before Score; the searches all see the overlay as it
+//     was before any deletion.
 //   * Shortcut predicate: a candidate (v1, u, v2) with v1 != v2 is kept iff
 //     w(v1,u) + w(u,v2) <= d_H(v1, v2). For H >= 2 this is the paper's
 //     "equals the witness distance" test; for H < 2 it is its natural
@@ -224,20 +234,95 @@ struct HopSearch {
     uint32_t dist(uint32_t v) const { return seen[v] ? cur[v] : INF; }
 };
 
+// Alg. 3's witness search as the paper states it: Dijkstra from s that stops
+// once every target is settled or once theta vertices (s included) are
+// settled. The heap is ordered by (distance, id), so with weights >= 1 the
+// vertices are settled in ascending (dist(s, v), v) order: the settled set is
+// the first theta vertices of that order, whatever the targets. A target
+// that was not settled gets INF.
+struct SettleSearch {
+    std::vector<uint32_t> d;
+    std::vector<char> done, want;
+    std::vector<uint32_t> touched;
+
+    explicit SettleSearch(uint32_t n) : d(n, INF), done(n, 0), want(n, 0) {}
+
+    void run(const std::vector<Adj>& out, uint32_t s, const std::vector<uint32_t>& targets,
+             uint64_t theta) {
+        for (uint32_t x : touched) {
+            d[x] = INF;
+            done[x] = 0;
+            want[x] = 0;
+        }
+        touched.clear();
+        uint64_t remaining = 0;
+        for (uint32_t v : targets)
+            if (!want[v]) {
+                want[v] = 1;
+                touched.push_back(v);
+                ++remaining;
+            }
+        using QE = std::pair<uint32_t, uint32_t>;  // (label, vertex)
+        std::priority_queue<QE, std::vector<QE>, std::greater<QE>> pq;
+        d[s] = 0;
+        touched.push_back(s);
+        pq.push({0, s});
+        uint64_t settled = 0;
+        while (!pq.empty() && remaining > 0 && settled < theta) {
+            auto [du, u] = pq.top();
+            pq.pop();
+            if (done[u]) continue;
+            done[u] = 1;
+            ++settled;
+            if (want[u]) {
+                want[u] = 0;
+                --remaining;
+            }
+            for (const auto& [v, wv] : out[u]) {
+                uint32_t nd = sat_add(du, wv);
+                if (nd < d[v]) {
+                    if (d[v] == INF) touched.push_back(v);
+                    d[v] = nd;
+                    pq.push({nd, v});
+                }
+            }
+        }
+    }
+    uint32_t dist(uint32_t v) const { return done[v] ? d[v] : INF; }
+};
+
+// Per-thread state of one witness search of either kind.
+struct Searcher {
+    HopSearch hop;
+    SettleSearch settle;
+    explicit Searcher(uint32_t n) : hop(n), settle(n) {}
+};
+
+// How the witness distances of a phase are computed: the hop-limited search
+// (optionally with the ball bound), or, with theta > 0, the settled-vertex
+// cap of Alg. 3.
+struct Witness {
+    uint32_t H = 0;
+    uint64_t ball = ~uint64_t(0);
+    uint64_t theta = 0;
+    bool prune = false;  // the recorded distances also decide edge deletions
+};
+
 bool keep(uint32_t via, uint32_t dh) { return via != INF && via <= dh; }
 
 uint64_t pair_key(uint32_t a, uint32_t b) { return (uint64_t(a) << 32) | b; }
 
-// Alg. 3 with the d_H reading: for every source s with an out-neighbour u in
-// `middle`, compute d_H from s and record it for every target v in N_out(u),
-// v != s. The search keeps labels below the heaviest candidate weight of s
-// and, with a finite ball bound, stops after the first level at which it
-// holds more than `ball` vertices (the settled-vertex cap of Alg. 3, read
-// per hop level). Returns the number of sources searched.
+// Alg. 3: for every source s with an out-neighbour u in `middle`, search from
+// s and record the witness distance for every target v in N_out(u), v != s
+// (the set V_n of s). With the d_H reading the search keeps labels below the
+// heaviest candidate weight of s and, with a finite ball bound, stops after
+// the first level at which it holds more than `ball` vertices (the settled-
+// vertex cap read per hop level). With theta > 0 it is the capped Dijkstra
+// of Alg. 3 itself. Returns the number of sources searched.
 uint64_t local_search(const Overlay& g, const std::vector<char>& middle,
-                      const std::vector<uint32_t>& middle_list, uint32_t H,
-                      HopSearch& hs, std::unordered_map<uint64_t, uint32_t>& dist,
-                      uint64_t ball = ~uint64_t(0), std::vector<HopSearch>* per_thread = nullptr) {
+                      const std::vector<uint32_t>& middle_list, const Witness& wit,
+                      Searcher& hs, std::unordered_map<uint64_t, uint32_t>& dist,
+                      std::vector<Searcher>* per_thread = nullptr) {
     std::vector<uint32_t> sources;
     for (uint32_t u : middle_list)
         for (const auto& [v1, w1] : g.in[u]) sources.push_back(v1);
@@ -245,28 +330,41 @@ uint64_t local_search(const Overlay& g, const std::vector<char>& middle,
     sources.erase(std::unique(sources.begin(), sources.end()), sources.end());
     dist.clear();
     // One source's searches and its (pair, distance) records.
-    auto search = [&](uint32_t s, HopSearch& h, std::vector<std::pair<uint64_t, uint32_t>>& outp) {
+    auto search = [&](uint32_t s, Searcher& h, std::vector<std::pair<uint64_t, uint32_t>>& outp) {
         uint32_t bound = 0;  // heaviest candidate weight of s
+        uint32_t direct = 0;  // heaviest overlay edge (s, v) to a target v
+        std::vector<uint32_t> targets;
         for (const auto& [u, w1] : g.out[s]) {
             if (!middle[u]) continue;
             for (const auto& [v, w2] : g.out[u])
-                if (v != s) bound = std::max(bound, sat_add(w1, w2));
+                if (v != s) {
+                    bound = std::max(bound, sat_add(w1, w2));
+                    targets.push_back(v);
+                    auto e = g.out[s].find(v);
+                    if (e != g.out[s].end()) direct = std::max(direct, e->second);
+                }
         }
-        if (bound == 0) return;  // no candidate from s
-        h.run(g.out, s, H, bound, ball);
-        for (const auto& [u, w1] : g.out[s]) {
-            if (!middle[u]) continue;
-            for (const auto& [v, w2] : g.out[u]) {
-                if (v == s) continue;
-                outp.push_back({pair_key(s, v), h.dist(v)});
-            }
+        if (targets.empty()) return;  // no candidate from s
+        if (wit.theta) {
+            h.settle.run(g.out, s, targets, wit.theta);
+            for (uint32_t v : targets) outp.push_back({pair_key(s, v), h.settle.dist(v)});
+        } else {
+            // Without a ball bound a label at or above the bound cannot
+            // change a decision, so the recorded value is exact d_H wherever
+            // it is used; with pruning that includes every d_H(s, v) below
+            // w(s, v), hence the wider bound. With a ball bound the
+            // candidate bound is part of the definition and stays.
+            const bool unbounded = wit.ball == ~uint64_t(0);
+            h.hop.run(g.out, s, wit.H, unbounded && wit.prune ? std::max(bound, direct) : bound,
+                      wit.ball);
+            for (uint32_t v : targets) outp.push_back({pair_key(s, v), h.hop.dist(v)});
         }
     };
 #ifdef ORACLE_THREADS
     // Threaded build: the sources are split over host threads, each with its
     // own search state; every record depends on its source alone, so the map
     // is the same as the sequential one.
-    std::vector<HopSearch> local;
+    std::vector<Searcher> local;
     if (!per_thread) {
         per_thread = &local;
         const unsigned nt = std::max(1u, std::thread::hardware_concurrency());
@@ -318,6 +416,8 @@ struct CH {
     std::vector<uint32_t> cn, rescore, orig_deg;
     // One row per rescoring: round, vertex, then the 12 integer features.
     std::vector<std::array<int64_t, 14>> trace;
+    // Overlay edges deleted by the pruning of Alg. 3: (round, s, v, w).
+    std::vector<std::array<uint32_t, 4>> pruned;
 };
 
 }  // namespace
@@ -386,7 +486,8 @@ constexpr int32_t P_INELIGIBLE = 2147483646;  // INT32_MAX - 1
 void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
            const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t seed,
            bool want_trace = false, const Replay* replay = nullptr,
-           uint64_t cmax = ~uint64_t(0), uint64_t ball = ~uint64_t(0)) {
+           uint64_t cmax = ~uint64_t(0), uint64_t ball = ~uint64_t(0), uint64_t theta = 0,
+           bool prune = false) {
     Overlay g;
     load(g, n, off, tgt, w);
     ch.ed_last.assign(n, 0);
@@ -402,11 +503,16 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
     ch.P.assign(n, 0);
     ch.up.assign(n, {});
     ch.down.assign(n, {});
-    HopSearch hs(n);
+    Witness wit;
+    wit.H = H;
+    wit.ball = ball;
+    wit.theta = theta;
+    wit.prune = prune;
+    Searcher hs(n);
     std::unordered_map<uint64_t, uint32_t> dist;
-    std::vector<HopSearch>* per_thread = nullptr;
+    std::vector<Searcher>* per_thread = nullptr;
 #ifdef ORACLE_THREADS
-    std::vector<HopSearch> hs_pool;
+    std::vector<Searcher> hs_pool;
     for (unsigned t = 0, nt = std::max(1u, std::thread::hardware_concurrency()); t < nt; ++t)
         hs_pool.emplace_back(n);
     per_thread = &hs_pool;
@@ -436,7 +542,28 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
 
         // Step 1: LocalSearch for the affected set.
         for (uint32_t u : Ae) inA[u] = 1;
-        st[ST_SCORE_SOURCES] = local_search(g, inA, Ae, H, hs, dist, ball, per_thread);
+        st[ST_SCORE_SOURCES] = local_search(g, inA, Ae, wit, hs, dist, per_thread);
+
+        // Pruning (Alg. 3, last step): an overlay edge (s, v) heavier than the
+        // witness distance just recorded for (s, v) is deleted. That distance
+        // is the weight of a walk s -> v that cannot use (s, v) itself (it
+        // weighs less), so every distance survives; deleting all such edges
+        // at once is safe too, since each is replaced by a walk of strictly
+        // lighter edges. All searches of the step see the overlay as it was
+        // before any deletion; Score and the rest of the round see it after.
+        if (prune) {
+            std::vector<std::pair<uint64_t, uint32_t>> recs(dist.begin(), dist.end());
+            std::sort(recs.begin(), recs.end());
+            for (const auto& [key, d] : recs) {
+                const uint32_t s = uint32_t(key >> 32), v = uint32_t(key);
+                auto it = g.out[s].find(v);
+                if (it == g.out[s].end() || !(it->second > d)) continue;
+                ch.pruned.push_back({r, s, v, it->second});
+                g.out[s].erase(it);
+                g.in[v].erase(s);
+                --live_edges;
+            }
+        }
 
         // Step 2: Score (edge difference), or the replayed priority; the
         // features are taken from the same overlay.
@@ -491,7 +618,7 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
         // Step 4: Contract. Witness distances for the candidates of V_F on
         // the same overlay.
         for (uint32_t u : F) inF[u] = 1;
-        st[ST_CONTRACT_SOURCES] = local_search(g, inF, F, H, hs, dist, ball, per_thread);
+        st[ST_CONTRACT_SOURCES] = local_search(g, inF, F, wit, hs, dist, per_thread);
 
         std::map<std::pair<uint32_t, uint32_t>, std::pair<uint32_t, uint32_t>> best;
         for (uint32_t u : F) {
@@ -656,6 +783,30 @@ uint32_t query(const CH& ch, uint32_t s, uint32_t t, uint64_t* settled) {
     return mu;
 }
 
+// One-to-all distances from s (the PHAST scheme the paper cites for SSSP on
+// a CH, Sec. 5): an upward search from s over E_up, then one sweep over all
+// vertices in descending rank, d(u) = min(d(u), d(x) + w) for every downward
+// edge (x, u). Such an edge comes from a vertex contracted in a later round
+// (u's in-neighbours at its contraction are outside V_F and outlive it), so
+// x has the higher rank and its value is final when u is reached. Core
+// vertices need no sweep: their E_up holds the core's edges, so the upward
+// search is already a full search inside the core; the sweep over their
+// core-core downward edges only re-offers walks and changes nothing.
+void one_to_all(const CH& ch, uint32_t s, uint32_t* d) {
+    std::unordered_map<uint32_t, uint32_t> ds;
+    dijkstra_sparse(s, [&](uint32_t u, auto f) {
+        for (const auto& [x, wx] : ch.up[u]) f(x, wx);
+    }, ds);
+    for (uint32_t v = 0; v < ch.n; ++v) d[v] = INF;
+    for (const auto& [v, dv] : ds) d[v] = dv;
+    std::vector<uint32_t> by_rank(ch.n);
+    for (uint32_t u = 0; u < ch.n; ++u) by_rank[ch.rank[u]] = u;
+    for (uint32_t i = ch.n; i-- > 0;) {
+        const uint32_t u = by_rank[i];
+        for (const auto& [x, wx] : ch.down[u]) d[u] = std::min(d[u], sat_add(d[x], wx));
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -677,19 +828,37 @@ int orc_build(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
 int orc_build2(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
                const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t tie_seed,
                int want_trace, uint64_t nreplay, const uint32_t* rp_round, const uint32_t* rp_u,
-               const int32_t* rp_p, uint64_t cmax, uint64_t ball, orc_ch** out) {
-    if (!out || !validate(n, m, off, tgt, w) || tie_mode > 1) return ORC_EINVAL;
+               const int32_t* rp_p, uint64_t cmax, uint64_t ball, uint64_t theta, int prune,
+               orc_ch** out) {
+    // the settled-vertex cap replaces the hop-limited search, ball bound included
+    if (!out || !validate(n, m, off, tgt, w) || tie_mode > 1 || (theta && ball != ~uint64_t(0)))
+        return ORC_EINVAL;
     Replay rp;
     for (uint64_t i = 0; i < nreplay; ++i) rp[{rp_round[i], rp_u[i]}] = rp_p[i];
     orc_ch* h = new orc_ch();
     try {
         build(h->ch, n, off, tgt, w, H, tie_mode, tie_seed, want_trace != 0,
-              nreplay ? &rp : nullptr, cmax, ball);
+              nreplay ? &rp : nullptr, cmax, ball, theta, prune != 0);
     } catch (const std::exception&) {
         delete h;
         return ORC_EINVAL;
     }
     *out = h;
+    return ORC_OK;
+}
+
+uint64_t orc_num_pruned(const orc_ch* h) { return h->ch.pruned.size(); }
+void orc_get_pruned(const orc_ch* h, uint32_t* out4) {
+    size_t i = 0;
+    for (const auto& row : h->ch.pruned)
+        for (int k = 0; k < 4; ++k) out4[i++] = row[k];
+}
+
+// One-to-all distances for k sources, row i of out (n entries) for src[i].
+int orc_one_to_all(const orc_ch* h, uint64_t k, const uint32_t* src, uint32_t* out) {
+    for (uint64_t i = 0; i < k; ++i)
+        if (src[i] >= h->ch.n) return ORC_EINVAL;
+    for (uint64_t i = 0; i < k; ++i) one_to_all(h->ch, src[i], out + i * uint64_t(h->ch.n));
     return ORC_OK;
 }
 
@@ -780,9 +949,12 @@ int orc_round0_scores(uint32_t n, uint64_t m, const uint64_t* off, const uint32_
     std::vector<uint32_t> A(n);
     std::vector<char> inA(n, 1);
     for (uint32_t u = 0; u < n; ++u) A[u] = u;
-    HopSearch hs(n);
+    Searcher hs(n);
+    Witness wit;
+    wit.H = H;
+    wit.ball = ball;
     std::unordered_map<uint64_t, uint32_t> dist;
-    local_search(g, inA, A, H, hs, dist, ball);
+    local_search(g, inA, A, wit, hs, dist);
     for (uint32_t u = 0; u < n; ++u) P[u] = score_one(g, u, dist);
     return ORC_OK;
 }

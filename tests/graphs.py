@@ -27,6 +27,8 @@ def load_golden(name):
                 spec["edges"].append(tuple(int(v) for v in vals))
             elif key == "shortcut":
                 spec["shortcuts"].append(tuple(int(v) for v in vals))
+            elif key == "pruned":
+                spec.setdefault("pruned", []).append(tuple(int(v) for v in vals))
             elif key == "query":
                 s, t, d = vals
                 spec["queries"].append((int(s), int(t), INF if d == "inf" else int(d)))

@@ -48,7 +48,9 @@ def test_golden_examples(name):
     spec = load_golden(name)
     tie = O.TIE_ID if spec.get("tie_break") == "id" else O.TIE_HASHED
     ch = O.build_ch(spec["graph"], spec["hop_limit"], tie, cmax=spec.get("cmax", O.CMAX_ALL),
-                    ball=spec.get("ball", O.CMAX_ALL))
+                    ball=spec.get("ball", O.CMAX_ALL), theta=spec.get("theta", 0),
+                    prune=bool(spec.get("prune", 0)))
+    assert sorted(map(tuple, ch.pruned.tolist())) == sorted(spec.get("pruned", []))
     assert ch.rounds == spec["expect_rounds"]
     if "expect_stats" in spec:  # every round's counters, row after row
         assert ch.stats.ravel().tolist() == spec["expect_stats"]

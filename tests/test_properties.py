@@ -1,6 +1,7 @@
 """Property tests over random small digraphs (no GPU): for any hop limit,
-tie-break, candidate bound and witness ball bound, every CH query equals the
-true distance, and every round re-derives from the definitions."""
+tie-break, candidate bound, witness ball bound, settled-vertex cap and
+pruning setting, every CH query and every one-to-all row equals the true
+distance, and every round re-derives from the definitions."""
 import numpy as np
 import pytest
 
@@ -23,14 +24,19 @@ def _case(draw):
     tie = draw(st.sampled_from([O.TIE_HASHED, O.TIE_ID]))
     cmax = draw(st.sampled_from([O.CMAX_ALL, 0, 1, 4, 16]))
     ball = draw(st.sampled_from([None, 1, 2, 5]))
-    return I.random_digraph(n, m, 1, wmax, seed=seed), H, tie, seed & 0xFFFF, cmax, ball
+    theta = 0 if ball is not None else draw(st.sampled_from([0, 0, 1, 2, 4, 9]))
+    prune = draw(st.booleans())
+    return (I.random_digraph(n, m, 1, wmax, seed=seed), H, tie, seed & 0xFFFF, cmax, ball, theta,
+            prune)
 
 
-@hyp.settings(max_examples=150, deadline=None, derandomize=True)
+@hyp.settings(max_examples=200, deadline=None, derandomize=True)
 @hyp.given(_case())
 def test_random_digraphs(case):
-    g, H, tie, seed, cmax, ball = case
-    och = _rederive(g, H, tie, seed=seed, cmax=cmax, ball=ball)
+    g, H, tie, seed, cmax, ball, theta, prune = case
+    och = _rederive(g, H, tie, seed=seed, cmax=cmax, ball=ball, theta=theta, prune=prune)
     s, t = np.meshgrid(np.arange(g.n), np.arange(g.n), indexing="ij")
     d = och.query(s.ravel().astype(np.uint32), t.ravel().astype(np.uint32))
-    assert np.array_equal(d.astype(np.uint64).reshape(g.n, g.n), all_pairs_truth(g))
+    truth = all_pairs_truth(g)
+    assert np.array_equal(d.astype(np.uint64).reshape(g.n, g.n), truth)
+    assert np.array_equal(och.one_to_all(np.arange(g.n)).astype(np.uint64), truth)

@@ -141,8 +141,27 @@ def _fmix32(h):
     return h
 
 
-def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None):
-    och = O.build_ch(g, H, tie, tie_seed=seed, cmax=cmax, ball=O.CMAX_ALL if ball is None else ball)
+def _settled_distances(gr, s, theta):
+    """Distances from s that a Dijkstra capped at theta settled vertices
+    reports: the true distance for the first theta vertices in (distance,
+    id) order, INF for the rest (scipy's Dijkstra, then a sort)."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import dijkstra
+
+    src, dst, w = gr.edges()
+    mat = sp.csr_matrix((w.astype(np.float64), (src, dst)), shape=(gr.n, gr.n))
+    dist = dijkstra(mat, directed=True, indices=s)
+    reach = np.flatnonzero(np.isfinite(dist))
+    order = reach[np.lexsort((reach, dist[reach]))]
+    out = np.full(gr.n, INF, np.uint64)
+    first = order[:theta]
+    out[first] = dist[first].astype(np.uint64)
+    return out
+
+
+def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=False):
+    och = O.build_ch(g, H, tie, tie_seed=seed, cmax=cmax, ball=O.CMAX_ALL if ball is None else ball,
+                     theta=theta, prune=prune)
     n = g.n
     off, tgt, w = O.normalize(g)
     edges = {}
@@ -157,26 +176,34 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None):
     P = np.zeros(n, np.int64)
     eligible = np.ones(n, bool)
     A = set(range(n))
+    pruned = []
 
     def key(u):
         lo = u if tie == O.TIE_ID else _fmix32(u ^ seed)
         return ((int(P[u]) & 0xFFFFFFFF) ^ 0x80000000) << 32 | lo
 
-    r = 0
-    while alive.any():
+    def overlay():
         live = {k: v for k, v in edges.items() if alive[k[0]] and alive[k[1]]}
         out, inn = defaultdict(dict), defaultdict(dict)
         for (a, b), c in live.items():
             out[a][b] = c
             inn[b][a] = c
-        gr = _graph_from_pairs(n, live)
-        dh = {}
+        return live, out, inn, _graph_from_pairs(n, live), {}
+
+    r = 0
+    while alive.any():
+        live, out, inn, gr, dh = overlay()
 
         def d(v1, v2, middles):
             # witness distance of the phase whose contracted middles are
-            # `middles`: d_H, or with a ball bound the distances of the first
+            # `middles`: d_H; or with a ball bound the distances of the first
             # level at which more than `ball` vertices hold a label below the
-            # source's heaviest candidate weight
+            # source's heaviest candidate weight; or with a settled-vertex
+            # cap the capped Dijkstra's
+            if theta:
+                if v1 not in dh:
+                    dh[v1] = _settled_distances(gr, v1, theta)
+                return int(dh[v1][v2])
             if ball is None:
                 if v1 not in dh:
                     dh[v1] = O.hop_limited(gr, H, v1)
@@ -194,23 +221,29 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None):
                 dh[keyd] = lab if lab is not None else np.where(np.arange(n) == v1, 0, INF)
             return int(dh[keyd][v2])
 
-        phase = {"middles": set()}
-
-        def kept(v1, u, v2):
-            via = inn[u][v1] + out[u][v2]
-            return via < INF and via <= d(v1, v2, phase["middles"]), via
-
-        # rescoring of the affected set (Alg. 3, 4) under the candidate bound
-        score_sources = set()
+        # rescoring of the affected set (Alg. 3, 4) under the candidate bound:
+        # every witness distance of the step on the overlay of the round start
         for u in A:
             eligible[u] = len(inn[u]) * len(out[u]) <= cmax
-        phase["middles"] = {u for u in A if eligible[u]}
+        middles = {u for u in A if eligible[u]}
+        score_sources = set().union(*(set(inn[u]) for u in middles))
+        score_d = {(v1, v2): d(v1, v2, middles) for u in middles
+                   for v1 in inn[u] for v2 in out[u] if v1 != v2}
+        if prune:
+            # Alg. 3's pruning: overlay edges heavier than their pair's
+            # witness distance leave before Score
+            for (s, v), dv in sorted(score_d.items()):
+                if (s, v) in live and live[(s, v)] > dv:
+                    pruned.append((r, s, v, live[(s, v)]))
+                    del edges[(s, v)]
+            live, out, inn, gr, dh = overlay()
         for u in A:
             if not eligible[u]:
                 P[u] = P_INELIGIBLE
                 continue
-            score_sources |= set(inn[u])
-            S = sum(1 for v1 in inn[u] for v2 in out[u] if v1 != v2 and kept(v1, u, v2)[0])
+            S = sum(1 for v1 in inn[u] for v2 in out[u]
+                    if v1 != v2 and inn[u][v1] + out[u][v2] < INF
+                    and inn[u][v1] + out[u][v2] <= score_d[(v1, v2)])
             P[u] = S - len(inn[u]) - len(out[u])
         # selection (Alg. 5): strict local minima of the key over N(u)
         F = [u for u in np.flatnonzero(alive).tolist() if eligible[u]
@@ -218,10 +251,11 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None):
         if not F:
             core = np.flatnonzero(alive)
             assert (level[core] == r).all() and och.rounds == r
-            return och
+            break
         assert sorted(F) == np.flatnonzero(level == r).tolist(), r
-        # contraction (Alg. 6): candidates, witness test, merge, insertion
-        phase["middles"] = set(F)
+        # contraction (Alg. 6): candidates, witness test on the overlay as it
+        # stands now, merge, insertion
+        middles = set(F)
         best, cand, keep_n = {}, 0, 0
         for u in F:
             for v1 in inn[u]:
@@ -229,8 +263,8 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None):
                     if v1 == v2:
                         continue
                     cand += 1
-                    ok, via = kept(v1, u, v2)
-                    if ok:
+                    via = inn[u][v1] + out[u][v2]
+                    if via < INF and via <= d(v1, v2, middles):
                         keep_n += 1
                         best[(v1, v2)] = min(best.get((v1, v2), (INF + 1, n)), (via, u))
         inserted = {(v1, v2, wv, via) for (v1, v2), (wv, via) in best.items()
@@ -249,6 +283,7 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None):
         A = {x for x in nextA if alive[x]}
         r += 1
     assert och.rounds == r
+    assert och.pruned.tolist() == [list(p) for p in pruned]
     return och
 
 
@@ -272,3 +307,35 @@ def test_every_round_rederived_with_a_core(seed):
 @pytest.mark.parametrize("ball", [1, 3, 8])
 def test_every_round_rederived_with_a_ball_bound(name, g, ball):
     _rederive(g, 4, O.TIE_HASHED, seed=5, ball=ball)
+
+
+@pytest.mark.parametrize("name,g", [(n, g) for n, g in small_families()
+                                    if n in ("digraph0", "digraph4", "sparse2", "grid8", "grid10u",
+                                             "geo150", "rmat8", "chain30", "star9", "complete6")],
+                         ids=lambda x: x if isinstance(x, str) else "")
+@pytest.mark.parametrize("theta", [1, 2, 5, 20, 10**6])
+def test_every_round_rederived_with_a_settled_cap(name, g, theta):
+    # Alg. 3's capped Dijkstra, pinned through scipy's Dijkstra and a sort
+    _rederive(g, 5, O.TIE_HASHED, seed=7, theta=theta)
+
+
+@pytest.mark.parametrize("name,g", [(n, g) for n, g in small_families()
+                                    if n in ("digraph1", "digraph3", "sparse3", "grid8", "grid10u",
+                                             "geo150", "geo120s", "rmat8", "chain30d")],
+                         ids=lambda x: x if isinstance(x, str) else "")
+@pytest.mark.parametrize("H,theta,ball", [(1, 0, None), (2, 0, None), (5, 0, None), (4, 0, 3),
+                                          (5, 4, None), (5, 30, None)])
+def test_every_round_rederived_with_pruning(name, g, H, theta, ball):
+    och = _rederive(g, H, O.TIE_HASHED, seed=9, ball=ball, theta=theta, prune=True)
+    if name.startswith("geo") and H >= 2 and not theta:
+        # hop-limited witnesses leave heavier edges behind that later rounds
+        # find shorter walks for
+        assert och.pruned.shape[0] > 0
+
+
+def test_every_round_rederived_with_pruning_and_a_core():
+    for seed in range(3):
+        _rederive(I.random_digraph(70, 300, 1, 20, seed=60 + seed), 2, O.TIE_HASHED, cmax=9,
+                  prune=True)
+        _rederive(I.random_digraph(70, 300, 1, 20, seed=63 + seed), 5, O.TIE_ID, cmax=9, theta=6,
+                  prune=True)
