@@ -62,7 +62,9 @@ def _load(threads: bool = False):
         lib.orc_build.restype = C.c_int
         lib.orc_free.argtypes = [P]
         lib.orc_build2.argtypes = [u32, u64, P, P, P, u32, u32, u32, C.c_int, u64, P, P, P,
-                                   u64, u64, u64, C.c_int, C.POINTER(P)]
+                                   u64, u64, u64, C.c_int, u64, C.POINTER(P)]
+        lib.orc_searches.argtypes = [P]
+        lib.orc_searches.restype = u64
         lib.orc_num_pruned.argtypes = [P]
         lib.orc_num_pruned.restype = u64
         lib.orc_get_pruned.argtypes = [P, P]
@@ -178,7 +180,7 @@ CMAX_ALL = (1 << 64) - 1
 def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int = 0,
              trace: bool = False, replay=None, cmax: int = CMAX_ALL,
              ball: int = CMAX_ALL, threads: bool = False, theta: int = 0,
-             prune: bool = False) -> OracleCH:
+             prune: bool = False, memo: int = 0) -> OracleCH:
     """Run the oracle's round algorithm on graph ``g`` (see ``oracle.cpp``).
 
     ``trace`` records the learned-priority features of every rescoring
@@ -192,7 +194,11 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
     hop-limited search by Alg. 3's Dijkstra capped at ``theta`` settled
     vertices (``ball`` must then stay unbounded). ``prune`` deletes, after
     each LocalSearch, the overlay edges heavier than the witness distance of
-    their pair (``OracleCH.pruned``: rows of round, s, v, w). ``threads`` runs
+    their pair (``OracleCH.pruned``: rows of round, s, v, w). ``memo`` > 0
+    keeps the witness distances across phases and rounds (pairs already
+    recorded are not searched again) and clears them at the end of a round
+    that leaves more than ``memo`` of them; ``OracleCH.searches`` counts the
+    witness searches run. ``threads`` runs
     the -DORACLE_THREADS build (witness searches on all host threads; the
     same result).
     """
@@ -208,7 +214,7 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
         rpv = np.ascontiguousarray(replay[2], np.int32)
     rc = lib.orc_build2(*args, hop_limit, tie_break, tie_seed & 0xFFFFFFFF, int(trace),
                         rr.size, _p(rr), _p(ru), _p(rpv), int(cmax), int(ball), int(theta),
-                        int(bool(prune)), C.byref(h))
+                        int(bool(prune)), int(memo), C.byref(h))
     if rc != 0:
         raise ValueError(f"oracle rejected the graph or parameters (status {rc})")
     n = g.n
@@ -250,6 +256,7 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
     och.trace = tr
     och.labels = labels
     och.pruned = pruned
+    och.searches = int(lib.orc_searches(h))
     return och
 
 

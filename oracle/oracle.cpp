@@ -10,8 +10,9 @@
 // runs each phase's witness searches on all host threads, with identical
 // results), ordered std::map adjacency,
 // every step applied literally in the order the paper gives it, no blocking,
-// no fusion, no pruning of searches. Where the paper leaves a detail open the
-// reading taken is stated next to the code.
+// no fusion; the one cut inside a search (labels that cannot decide
+// anything) is stated where it is made. Where the paper leaves a detail open
+// the reading taken is stated next to the code.
 //
 // Paper passages followed (arXiv 2412.18008):
 //   Sec. 2 notation: N_in, N_out, N over the overlay graph G_O.
@@ -53,6 +54,17 @@
 //     overlay edge (s, v) heavier than the distance recorded for (s, v) is
 //     deleted (Alg. 3), before Score; the searches all see the overlay as it
 //     was before any deletion.
+//   * Memoisation (optional): the distance map outlives the phase (Alg. 3's
+//     dist); a pair already in it is not searched again, and a source none
+//     of whose targets is new is not searched at all. Each search drops
+//     labels at or above the heaviest weight it has to decide (its new
+//     targets' candidate weights and, with pruning, the direct edges to
+//     them), so the value kept is the label the search held, else INF. The
+//     map is cleared at the end of a round that leaves more entries than a
+//     given limit (the paper clears its table lazily, once it is filled to
+//     a constant fraction). An old value is the weight of a walk in an
+//     earlier overlay, so it bounds the distance from above and the
+//     argument below still holds.
 //   * Shortcut predicate: a candidate (v1, u, v2) with v1 != v2 is kept iff
 //     w(v1,u) + w(u,v2) <= d_H(v1, v2). For H >= 2 this is the paper's
 //     "equals the witness distance" test; for H < 2 it is its natural
@@ -92,7 +104,9 @@
 // successor b outside V_F (V_F is independent) and a != b (weights are >= 1),
 // and w(a,u) + w(u,b) = dist(a, b) <= d_H(a, b), so (a, b) is kept, and the
 // edge (a, b) of the next overlay weighs at most that. Every shortcut weighs
-// as much as a real walk, so no distance can drop below the true one.
+// as much as a real walk, so no distance can drop below the true one. A
+// pruned edge (s, v) weighs more than dist(s, v), so it lies on no shortest
+// path, and deleting any number of such edges at once changes no distance.
 
 #include <algorithm>
 #include <array>
@@ -306,6 +320,7 @@ struct Witness {
     uint64_t ball = ~uint64_t(0);
     uint64_t theta = 0;
     bool prune = false;  // the recorded distances also decide edge deletions
+    bool memo = false;   // the distance map persists across phases and rounds
 };
 
 bool keep(uint32_t via, uint32_t dh) { return via != INF && via <= dh; }
@@ -322,29 +337,37 @@ uint64_t pair_key(uint32_t a, uint32_t b) { return (uint64_t(a) << 32) | b; }
 uint64_t local_search(const Overlay& g, const std::vector<char>& middle,
                       const std::vector<uint32_t>& middle_list, const Witness& wit,
                       Searcher& hs, std::unordered_map<uint64_t, uint32_t>& dist,
-                      std::vector<Searcher>* per_thread = nullptr) {
+                      std::vector<Searcher>* per_thread = nullptr,
+                      uint64_t* searched = nullptr) {
     std::vector<uint32_t> sources;
     for (uint32_t u : middle_list)
         for (const auto& [v1, w1] : g.in[u]) sources.push_back(v1);
     std::sort(sources.begin(), sources.end());
     sources.erase(std::unique(sources.begin(), sources.end()), sources.end());
-    dist.clear();
+    // Without memoisation each phase starts from an empty map. With it, the
+    // map holds every distance recorded since it was last cleared, and a
+    // target whose pair is already there is not searched for again (Alg. 3:
+    // (s, v) in dist is skipped); a source with no target left is not
+    // searched at all. Every recorded value is the weight of a real walk
+    // (or INF), so an old value is still an upper bound on the distance.
+    if (!wit.memo) dist.clear();
     // One source's searches and its (pair, distance) records.
     auto search = [&](uint32_t s, Searcher& h, std::vector<std::pair<uint64_t, uint32_t>>& outp) {
-        uint32_t bound = 0;  // heaviest candidate weight of s
+        uint32_t bound = 0;  // heaviest candidate weight of s (targets to search)
         uint32_t direct = 0;  // heaviest overlay edge (s, v) to a target v
         std::vector<uint32_t> targets;
         for (const auto& [u, w1] : g.out[s]) {
             if (!middle[u]) continue;
             for (const auto& [v, w2] : g.out[u])
-                if (v != s) {
+                if (v != s && !(wit.memo && dist.count(pair_key(s, v)))) {
                     bound = std::max(bound, sat_add(w1, w2));
                     targets.push_back(v);
                     auto e = g.out[s].find(v);
                     if (e != g.out[s].end()) direct = std::max(direct, e->second);
                 }
         }
-        if (targets.empty()) return;  // no candidate from s
+        if (targets.empty()) return;  // no candidate from s, or all memoised
+        outp.push_back({~uint64_t(0), 0});  // marks one search run
         if (wit.theta) {
             h.settle.run(g.out, s, targets, wit.theta);
             for (uint32_t v : targets) outp.push_back({pair_key(s, v), h.settle.dist(v)});
@@ -378,19 +401,46 @@ uint64_t local_search(const Overlay& g, const std::vector<char>& middle,
             for (size_t i = t; i < sources.size(); i += nt) search(sources[i], (*per_thread)[t], parts[t]);
         });
     for (auto& th : pool) th.join();
+    uint64_t runs = 0;
     for (const auto& p : parts)
-        for (const auto& [k, v] : p) dist[k] = v;
+        for (const auto& [k, v] : p) {
+            if (k == ~uint64_t(0)) ++runs;
+            else dist[k] = v;
+        }
     (void)hs;
 #else
     (void)per_thread;
+    // The records of a source go in after its search; a record only ever
+    // concerns its own source's pairs, so no search of the phase sees
+    // another's.
+    uint64_t runs = 0;
     std::vector<std::pair<uint64_t, uint32_t>> recs;
     for (uint32_t s : sources) {
         recs.clear();
         search(s, hs, recs);
-        for (const auto& [k, v] : recs) dist[k] = v;
+        for (const auto& [k, v] : recs) {
+            if (k == ~uint64_t(0)) ++runs;
+            else dist[k] = v;
+        }
     }
 #endif
+    if (searched) *searched += runs;
     return sources.size();
+}
+
+// The (s, v) pairs a phase with these middles needs, v in N_out(u) for an
+// out-neighbour u of s among the middles, v != s; sorted, no repeats.
+std::vector<uint64_t> phase_pairs(const Overlay& g, const std::vector<char>& middle,
+                                  const std::vector<uint32_t>& middle_list) {
+    std::vector<uint64_t> pairs;
+    for (uint32_t u : middle_list)
+        for (const auto& [s, w1] : g.in[u])
+            for (const auto& [v, w2] : g.out[u])
+                if (v != s) pairs.push_back(pair_key(s, v));
+    std::sort(pairs.begin(), pairs.end());
+    pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+    (void)middle;
+    return pairs;
 }
 
 struct Shortcut {
@@ -418,6 +468,7 @@ struct CH {
     std::vector<std::array<int64_t, 14>> trace;
     // Overlay edges deleted by the pruning of Alg. 3: (round, s, v, w).
     std::vector<std::array<uint32_t, 4>> pruned;
+    uint64_t searches = 0;  // witness searches run (sources with a target to search)
 };
 
 }  // namespace
@@ -487,7 +538,7 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
            const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t seed,
            bool want_trace = false, const Replay* replay = nullptr,
            uint64_t cmax = ~uint64_t(0), uint64_t ball = ~uint64_t(0), uint64_t theta = 0,
-           bool prune = false) {
+           bool prune = false, uint64_t memo_limit = 0) {
     Overlay g;
     load(g, n, off, tgt, w);
     ch.ed_last.assign(n, 0);
@@ -508,6 +559,7 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
     wit.ball = ball;
     wit.theta = theta;
     wit.prune = prune;
+    wit.memo = memo_limit > 0;
     Searcher hs(n);
     std::unordered_map<uint64_t, uint32_t> dist;
     std::vector<Searcher>* per_thread = nullptr;
@@ -542,7 +594,7 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
 
         // Step 1: LocalSearch for the affected set.
         for (uint32_t u : Ae) inA[u] = 1;
-        st[ST_SCORE_SOURCES] = local_search(g, inA, Ae, wit, hs, dist, per_thread);
+        st[ST_SCORE_SOURCES] = local_search(g, inA, Ae, wit, hs, dist, per_thread, &ch.searches);
 
         // Pruning (Alg. 3, last step): an overlay edge (s, v) heavier than the
         // witness distance just recorded for (s, v) is deleted. That distance
@@ -552,10 +604,9 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
         // lighter edges. All searches of the step see the overlay as it was
         // before any deletion; Score and the rest of the round see it after.
         if (prune) {
-            std::vector<std::pair<uint64_t, uint32_t>> recs(dist.begin(), dist.end());
-            std::sort(recs.begin(), recs.end());
-            for (const auto& [key, d] : recs) {
+            for (uint64_t key : phase_pairs(g, inA, Ae)) {
                 const uint32_t s = uint32_t(key >> 32), v = uint32_t(key);
+                const uint32_t d = dist.at(key);
                 auto it = g.out[s].find(v);
                 if (it == g.out[s].end() || !(it->second > d)) continue;
                 ch.pruned.push_back({r, s, v, it->second});
@@ -618,7 +669,7 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
         // Step 4: Contract. Witness distances for the candidates of V_F on
         // the same overlay.
         for (uint32_t u : F) inF[u] = 1;
-        st[ST_CONTRACT_SOURCES] = local_search(g, inF, F, wit, hs, dist, per_thread);
+        st[ST_CONTRACT_SOURCES] = local_search(g, inF, F, wit, hs, dist, per_thread, &ch.searches);
 
         std::map<std::pair<uint32_t, uint32_t>, std::pair<uint32_t, uint32_t>> best;
         for (uint32_t u : F) {
@@ -693,6 +744,10 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
         st[ST_VO_AFTER] = live;
         st[ST_EO_AFTER] = live_edges;
         ch.stats.push_back(st);
+        // Memoised distances are cleared lazily: only at the end of a round
+        // that leaves more than memo_limit of them (the paper clears its
+        // table once a constant fraction of it is full).
+        if (wit.memo && dist.size() > memo_limit) dist.clear();
         A.swap(nextA);
     }
 
@@ -829,7 +884,7 @@ int orc_build2(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
                const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t tie_seed,
                int want_trace, uint64_t nreplay, const uint32_t* rp_round, const uint32_t* rp_u,
                const int32_t* rp_p, uint64_t cmax, uint64_t ball, uint64_t theta, int prune,
-               orc_ch** out) {
+               uint64_t memo_limit, orc_ch** out) {
     // the settled-vertex cap replaces the hop-limited search, ball bound included
     if (!out || !validate(n, m, off, tgt, w) || tie_mode > 1 || (theta && ball != ~uint64_t(0)))
         return ORC_EINVAL;
@@ -838,7 +893,7 @@ int orc_build2(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
     orc_ch* h = new orc_ch();
     try {
         build(h->ch, n, off, tgt, w, H, tie_mode, tie_seed, want_trace != 0,
-              nreplay ? &rp : nullptr, cmax, ball, theta, prune != 0);
+              nreplay ? &rp : nullptr, cmax, ball, theta, prune != 0, memo_limit);
     } catch (const std::exception&) {
         delete h;
         return ORC_EINVAL;
@@ -848,6 +903,7 @@ int orc_build2(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
 }
 
 uint64_t orc_num_pruned(const orc_ch* h) { return h->ch.pruned.size(); }
+uint64_t orc_searches(const orc_ch* h) { return h->ch.searches; }
 void orc_get_pruned(const orc_ch* h, uint32_t* out4) {
     size_t i = 0;
     for (const auto& row : h->ch.pruned)

@@ -159,9 +159,24 @@ def _settled_distances(gr, s, theta):
     return out
 
 
-def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=False):
+def _ball_labels(gr, s, H, bound, ball):
+    """Labels below `bound` of a hop-synchronous search from s: those of
+    level H, or with a ball bound those of the first level at which more than
+    `ball` vertices hold one; INF elsewhere."""
+    lab = np.where(np.arange(gr.n) == s, 0, INF).astype(np.int64)
+    for h in range(1, H + 1):
+        dist_h = O.hop_limited(gr, h, s).astype(np.int64)
+        lab = np.where(dist_h < bound, dist_h, INF)
+        if ball is not None and int((lab != INF).sum()) > ball:
+            break
+    return lab
+
+
+def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=False, memo=0):
     och = O.build_ch(g, H, tie, tie_seed=seed, cmax=cmax, ball=O.CMAX_ALL if ball is None else ball,
-                     theta=theta, prune=prune)
+                     theta=theta, prune=prune, memo=memo)
+    memo_d = {}
+    searches = [0]
     n = g.n
     off, tgt, w = O.normalize(g)
     edges = {}
@@ -221,13 +236,42 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=Fals
                 dh[keyd] = lab if lab is not None else np.where(np.arange(n) == v1, 0, INF)
             return int(dh[keyd][v2])
 
+        def fill(middles):
+            # the searches of one phase: a source with a candidate target
+            # searches once; with memoisation only for targets whose pair has
+            # no recorded distance, and the value recorded is the label its
+            # search held (labels at or above the heaviest weight the search
+            # must decide are dropped), INF if none
+            for s in sorted(set().union(*(set(inn[u]) for u in middles))):
+                cands = [(c1 + c2, v) for u, c1 in out[s].items() if u in middles
+                         for v, c2 in out[u].items() if v != s and not (memo and (s, v) in memo_d)]
+                if not cands:
+                    continue
+                searches[0] += 1
+                if not memo:
+                    continue
+                new = {v for _, v in cands}
+                if theta:
+                    lab = _settled_distances(gr, s, theta)
+                else:
+                    bound = max(c for c, _ in cands)
+                    if prune and ball is None:
+                        bound = max([bound] + [live[(s, v)] for v in new if (s, v) in live])
+                    lab = _ball_labels(gr, s, H, bound, ball)
+                for v in new:
+                    memo_d[(s, v)] = int(lab[v])
+
+        def dm(v1, v2, middles):
+            return memo_d[(v1, v2)] if memo else d(v1, v2, middles)
+
         # rescoring of the affected set (Alg. 3, 4) under the candidate bound:
         # every witness distance of the step on the overlay of the round start
         for u in A:
             eligible[u] = len(inn[u]) * len(out[u]) <= cmax
         middles = {u for u in A if eligible[u]}
         score_sources = set().union(*(set(inn[u]) for u in middles))
-        score_d = {(v1, v2): d(v1, v2, middles) for u in middles
+        fill(middles)
+        score_d = {(v1, v2): dm(v1, v2, middles) for u in middles
                    for v1 in inn[u] for v2 in out[u] if v1 != v2}
         if prune:
             # Alg. 3's pruning: overlay edges heavier than their pair's
@@ -256,6 +300,7 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=Fals
         # contraction (Alg. 6): candidates, witness test on the overlay as it
         # stands now, merge, insertion
         middles = set(F)
+        fill(middles)
         best, cand, keep_n = {}, 0, 0
         for u in F:
             for v1 in inn[u]:
@@ -264,7 +309,7 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=Fals
                         continue
                     cand += 1
                     via = inn[u][v1] + out[u][v2]
-                    if via < INF and via <= d(v1, v2, middles):
+                    if via < INF and via <= dm(v1, v2, middles):
                         keep_n += 1
                         best[(v1, v2)] = min(best.get((v1, v2), (INF + 1, n)), (via, u))
         inserted = {(v1, v2, wv, via) for (v1, v2), (wv, via) in best.items()
@@ -281,9 +326,12 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=Fals
                len(inserted), int(alive.sum()), live_after]
         assert och.stats[r].tolist() == row, (r, och.stats[r].tolist(), row)
         A = {x for x in nextA if alive[x]}
+        if memo and len(memo_d) > memo:
+            memo_d.clear()
         r += 1
     assert och.rounds == r
     assert och.pruned.tolist() == [list(p) for p in pruned]
+    assert och.searches == searches[0]
     return och
 
 
@@ -339,3 +387,23 @@ def test_every_round_rederived_with_pruning_and_a_core():
                   prune=True)
         _rederive(I.random_digraph(70, 300, 1, 20, seed=63 + seed), 5, O.TIE_ID, cmax=9, theta=6,
                   prune=True)
+
+
+@pytest.mark.parametrize("name,g", [(n, g) for n, g in small_families()
+                                    if n in ("digraph0", "digraph5", "sparse1", "sparse4", "grid8",
+                                             "grid10u", "geo150", "geo120s", "rmat8", "chain30",
+                                             "star9", "complete6")],
+                         ids=lambda x: x if isinstance(x, str) else "")
+@pytest.mark.parametrize("H,theta,ball,prune,memo", [
+    (5, 0, None, False, 1 << 40), (2, 0, None, False, 1 << 40), (5, 0, None, True, 1 << 40),
+    (5, 0, None, False, 40), (3, 0, 3, False, 1 << 40), (3, 0, 3, True, 25),
+    (5, 3, None, False, 1 << 40), (5, 6, None, True, 30), (0, 0, None, True, 1 << 40)])
+def test_every_round_rederived_with_memoisation(name, g, H, theta, ball, prune, memo):
+    _rederive(g, H, O.TIE_HASHED, seed=11, ball=ball, theta=theta, prune=prune, memo=memo)
+
+
+def test_every_round_rederived_with_memoisation_and_a_core():
+    for seed in range(3):
+        _rederive(I.random_digraph(70, 300, 1, 20, seed=70 + seed), 5, O.TIE_HASHED, cmax=9,
+                  prune=True, memo=1 << 40)
+        _rederive(I.random_digraph(70, 300, 1, 20, seed=73 + seed), 3, O.TIE_ID, cmax=9, memo=50)

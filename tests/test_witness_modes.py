@@ -1,7 +1,7 @@
 """Oracle pins for Alg. 3 as the paper writes it (no GPU): the witness search
 capped at theta settled vertices, the pruning of overlay edges heavier than
-their pair's witness distance, and the one-to-all query (PHAST, which the
-paper cites for SSSP on a CH).
+their pair's witness distance, the memoised distance map kept across rounds,
+and the one-to-all query (PHAST, which the paper cites for SSSP on a CH).
 
 Pins, none of which goes through the oracle's own search code:
   * theta = 1 settles only the source, so every candidate pair is kept: the
@@ -13,6 +13,8 @@ Pins, none of which goes through the oracle's own search code:
     (scipy's Dijkstra), so pruning never deletes a needed edge.
   * one-to-all rows equal scipy's all-pairs Dijkstra, with or without a core,
     a ball bound, a settled cap or pruning.
+  * with hop limit 0 or theta = 1 every recorded value is INF, so
+    memoisation cannot change a decision: the same hierarchy.
   * every query is exact in every mode.
 Round-by-round re-derivations of both modes are in test_trace_pins.py."""
 import numpy as np
@@ -53,6 +55,27 @@ def test_theta_unbounded_equals_exact_hop_limit(name, g):
     _same(O.build_ch(g, 3, theta=g.n, cmax=6), O.build_ch(g, H, cmax=6))
 
 
+@pytest.mark.parametrize("name,g", FAMILIES, ids=[n for n, _ in FAMILIES])
+def test_memo_changes_nothing_where_every_value_is_inf(name, g):
+    # hop limit 0 and theta = 1 record INF for every pair, so reusing a value
+    # decides exactly as a fresh search would: the same hierarchy, and never
+    # more searches
+    for kw in (dict(hop_limit=0), dict(hop_limit=5, theta=1)):
+        a = O.build_ch(g, **kw)
+        b = O.build_ch(g, memo=1 << 40, **kw)
+        _same(a, b)
+        assert b.searches <= a.searches
+
+
+def test_memo_halves_the_searches_on_a_geometric_graph():
+    g = I.geometric_knn_graph(5000, seed=21)
+    a = O.build_ch(g, 5)
+    b = O.build_ch(g, 5, memo=1 << 40)
+    assert b.searches < 0.7 * a.searches
+    s, t = I.random_pairs(g.n, 3000, seed=22)
+    assert np.array_equal(b.query(s, t), O.dijkstra_pairs(g, s, t))
+
+
 def test_theta_and_ball_are_exclusive():
     g = I.random_digraph(10, 30, 1, 5, seed=1)
     with pytest.raises(ValueError):
@@ -60,7 +83,8 @@ def test_theta_and_ball_are_exclusive():
 
 
 MODES = [dict(), dict(prune=True), dict(theta=3), dict(theta=3, prune=True),
-         dict(ball=2, prune=True), dict(cmax=4, prune=True), dict(cmax=4, theta=8)]
+         dict(ball=2, prune=True), dict(cmax=4, prune=True), dict(cmax=4, theta=8),
+         dict(memo=1 << 40), dict(memo=30, prune=True), dict(memo=1 << 40, theta=4, cmax=4)]
 
 
 @pytest.mark.parametrize("mode", MODES, ids=[",".join(f"{k}={v}" for k, v in m.items()) or "plain"
