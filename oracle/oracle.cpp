@@ -27,7 +27,7 @@
 //           upward set, surviving in x out pairs become shortcuts, u and its
 //           edges leave the overlay.
 //   Sec. 4  duplicate shortcuts (u-c1-v and u-c2-v) keep the smallest weight.
-//   Sec. 4  Postprocess: vertices ordered by level, then by score.
+//   Sec. 3.5 Postprocess: vertices ordered by level, then by score.
 //   Sec. 5  Query: upward search from s on the upward edges, upward search
 //           from t on the reversed downward edges, answer = min over meeting
 //           vertices of d_s(v) + d_t(v).

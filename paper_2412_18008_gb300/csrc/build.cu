@@ -5,7 +5,7 @@
 // source), Alg. 4 (Score = edge difference), Alg. 5 (Select = strict local
 // minimum of the score, ties by label), Alg. 6 (Contract), Sec. 4 (overlay in
 // CSR form, duplicate shortcuts keep the minimum weight) and the
-// Postprocess paragraph of Sec. 4 (vertices ranked by level, then score).
+// Postprocessing of Sec. 3.5 (vertices ranked by level, then score).
 //
 // GPU design (one round = the steps below, one host synchronisation):
 //   1 score_prep     A_r: P[u] = -(|N_in|+|N_out|); sources N_in(A_r) listed

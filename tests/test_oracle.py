@@ -291,7 +291,7 @@ def test_chain_one_shortcut_per_interior_contraction(bidirectional, tie):
     else:
         inner = (ups == 1) & (dns == 1)
         assert len(ch.shortcuts) == int(inner.sum())
-    # hashed tie-break contracts a constant fraction per round (Sec. 6.5)
+    # hashed tie-break contracts a constant fraction per round (Sec. 6.4)
     if tie == O.TIE_HASHED:
         assert ch.rounds < 60
 
@@ -338,7 +338,7 @@ def test_sampled_queries_on_grid_workload():
     assert np.array_equal(ch.query(s, t), O.dijkstra_pairs(g, s, t))
     # the grid keeps the largest component: everything is reachable
     assert (ch.query(s, t) != INF).all()
-    # >99% of the vertices go in the first rounds on road-like inputs (Sec. 4.3)
+    # >99% of the vertices go in the first rounds on road-like inputs (Sec. 3.3)
     frac = np.cumsum(ch.stats[:, 2]) / g.n
     assert frac[min(40, len(frac) - 1)] > 0.99
 
