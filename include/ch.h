@@ -232,6 +232,20 @@ int ch_query_status(ch_t *ch, void *stream);
 int ch_query_one_to_many(ch_t *ch, uint32_t s, const uint32_t *dst, uint64_t k,
                          uint32_t *dist_out, void *stream);
 
+/* One-to-all distances (the PHAST scheme the paper cites for single-source
+ * distances on a CH, Sec. 5): for each of the k sources src[i],
+ * dist_out[i * n + v] = length of a shortest path src[i] -> v in the input
+ * graph, for every vertex v (0xFFFFFFFF if unreachable). src (uint32[k]) and
+ * dist_out (uint32[k * n], row-major, caller-owned) are DEVICE pointers; the
+ * work is enqueued on `stream`. The sweeps run over the rank order, 16
+ * sources at a time, in library-owned scratch of 64 bytes per vertex, so
+ * calls on one handle must not overlap on the GPU. A hierarchy with a core
+ * iterates the core on the host's command, so the call then waits for
+ * `stream` once per core pass. Ids >= n are reported by ch_query_status as
+ * for ch_query_batch (that source's row is left all 0xFFFFFFFF). k = 0 is a
+ * no-op. */
+int ch_one_to_all(ch_t *ch, const uint32_t *src, uint64_t k, uint32_t *dist_out, void *stream);
+
 /* Saves a built hierarchy to `path` (binary, little-endian; everything
  * ch_query_batch, ch_export and ch_get_stats use, not learned-priority
  * traces) and loads one back onto the current device. CH_EINVAL on I/O

@@ -149,9 +149,10 @@ def load(build_if_missing: bool = True):
                                       C.POINTER(TuneRowT), C.POINTER(C.c_uint32)]
     lib.ch_build_autotune.restype = C.c_int
     lib.ch_query_one_to_many.argtypes = [P, C.c_uint32, P, C.c_uint64, P, P]
+    lib.ch_one_to_all.argtypes = [P, P, C.c_uint64, P, P]
     lib.ch_save.argtypes = [P, C.c_char_p]
     lib.ch_load.argtypes = [C.c_char_p, C.POINTER(P)]
-    for f in ("ch_query_one_to_many", "ch_save", "ch_load"):
+    for f in ("ch_query_one_to_many", "ch_one_to_all", "ch_save", "ch_load"):
         getattr(lib, f).restype = C.c_int
     lib.ch_set_query_config.argtypes = [P, C.POINTER(QueryConfigT)]
     lib.ch_get_query_config.argtypes = [P, C.POINTER(QueryConfigT)]
@@ -348,6 +349,17 @@ class CH:
         out = torch.empty_like(dst)
         _check(load().ch_query_one_to_many(self._h, int(s), dst.data_ptr(), dst.numel(),
                                            out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def one_to_all(self, src, stream=None):
+        """Distances from each source of the CUDA tensor ``src`` (int32 view
+        of uint32 ids) to every vertex: an int32 tensor [len(src), n] holding
+        uint32 bit patterns, asynchronous on ``stream``."""
+        import torch
+        n = self.stats()["n"]
+        out = torch.empty((src.numel(), n), dtype=torch.int32, device=src.device)
+        _check(load().ch_one_to_all(self._h, src.data_ptr(), src.numel(), out.data_ptr(),
+                                    _stream_ptr(stream)))
         return out
 
     # -- saving and loading -------------------------------------------------

@@ -256,6 +256,14 @@ int ch_query_one_to_many(ch_t *ch, uint32_t s, const uint32_t *dst, uint64_t k, 
     return guarded([&] { query_one_to_many(ch, s, dst, k, dist_out, static_cast<cudaStream_t>(stream)); });
 }
 
+int ch_one_to_all(ch_t *ch, const uint32_t *src, uint64_t k, uint32_t *dist_out, void *stream) {
+    if (!ch || (k && (!src || !dist_out))) {
+        g_last_error = "null argument";
+        return CH_EINVAL;
+    }
+    return guarded([&] { one_to_all(ch, src, k, dist_out, static_cast<cudaStream_t>(stream)); });
+}
+
 int ch_save(const ch_t *ch, const char *path) {
     if (!ch || !path) {
         g_last_error = "null argument";

@@ -69,6 +69,12 @@ struct ch_s {
     uint32_t q_slots = 0;
     uint64_t q_ovf_cap = 0;
     gbch::DevBuf<uint32_t> q_src_fill;  // repeated source of one-to-many queries
+
+    // One-to-all scratch: interleaved labels of a batch of sources, level
+    // boundaries, the core pass's change flag.
+    gbch::DevBuf<uint32_t> phast_d;
+    gbch::DevBuf<uint32_t> phast_lv;
+    gbch::DevBuf<uint32_t> phast_flag;
 };
 
 namespace gbch {
@@ -104,6 +110,9 @@ void save_hierarchy(const ch_s *h, const char *path);
 ch_s *load_hierarchy(const char *path);
 void query_one_to_many(ch_s *h, uint32_t s, const uint32_t *dst, uint64_t k, uint32_t *dist_out,
                        cudaStream_t st);
+
+// One-to-all distances for k sources (phast.cu).
+void one_to_all(ch_s *h, const uint32_t *src, uint64_t k, uint32_t *dist_out, cudaStream_t st);
 
 // Query server (serve.cu).
 ch_server_s *server_new();
