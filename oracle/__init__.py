@@ -62,9 +62,11 @@ def _load(threads: bool = False):
         lib.orc_build.restype = C.c_int
         lib.orc_free.argtypes = [P]
         lib.orc_build2.argtypes = [u32, u64, P, P, P, u32, u32, u32, C.c_int, u64, P, P, P,
-                                   u64, u64, u64, C.c_int, u64, C.POINTER(P)]
+                                   u64, u64, u64, C.c_int, u64, u64, C.POINTER(P)]
         lib.orc_searches.argtypes = [P]
         lib.orc_searches.restype = u64
+        lib.orc_witness_work.argtypes = [P]
+        lib.orc_witness_work.restype = u64
         lib.orc_num_pruned.argtypes = [P]
         lib.orc_num_pruned.restype = u64
         lib.orc_get_pruned.argtypes = [P, P]
@@ -180,7 +182,7 @@ CMAX_ALL = (1 << 64) - 1
 def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int = 0,
              trace: bool = False, replay=None, cmax: int = CMAX_ALL,
              ball: int = CMAX_ALL, threads: bool = False, theta: int = 0,
-             prune: bool = False, memo: int = 0) -> OracleCH:
+             prune: bool = False, memo: int = 0, level_work: int = CMAX_ALL) -> OracleCH:
     """Run the oracle's round algorithm on graph ``g`` (see ``oracle.cpp``).
 
     ``trace`` records the learned-priority features of every rescoring
@@ -198,7 +200,10 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
     keeps the witness distances across phases and rounds (pairs already
     recorded are not searched again) and clears them at the end of a round
     that leaves more than ``memo`` of them; ``OracleCH.searches`` counts the
-    witness searches run. ``threads`` runs
+    witness searches run. ``level_work`` bounds a hop-limited search's work:
+    a level from the second on whose frontier has more out-edges in total is
+    not run (``OracleCH.witness_work`` sums the frontier out-edges of the
+    levels run). ``threads`` runs
     the -DORACLE_THREADS build (witness searches on all host threads; the
     same result).
     """
@@ -214,7 +219,7 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
         rpv = np.ascontiguousarray(replay[2], np.int32)
     rc = lib.orc_build2(*args, hop_limit, tie_break, tie_seed & 0xFFFFFFFF, int(trace),
                         rr.size, _p(rr), _p(ru), _p(rpv), int(cmax), int(ball), int(theta),
-                        int(bool(prune)), int(memo), C.byref(h))
+                        int(bool(prune)), int(memo), int(level_work), C.byref(h))
     if rc != 0:
         raise ValueError(f"oracle rejected the graph or parameters (status {rc})")
     n = g.n
@@ -257,6 +262,7 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
     och.labels = labels
     och.pruned = pruned
     och.searches = int(lib.orc_searches(h))
+    och.witness_work = int(lib.orc_witness_work(h))
     return och
 
 

@@ -44,6 +44,12 @@
 //     and d_h replaces d_H (still an upper bound on a real walk, so the
 //     distances stay exact; only more shortcuts may be kept). Unbounded by
 //     default.
+//   * Level-work bound (optional): a hop-limited search does not run a
+//     level, from the second on, whose frontier (the vertices whose label
+//     dropped in the level before) has more out-edges in total than the
+//     bound; the labels of the level before are its result. Like the ball
+//     bound it only drops witnesses, so distances stay exact. It keeps
+//     searches from expanding hubs of power-law graphs.
 //   * Settled-vertex cap (optional, theta > 0): the search of Alg. 3 as
 //     written, a Dijkstra from the source that stops when all its targets or
 //     theta vertices are settled; an unsettled target's distance is INF.
@@ -204,28 +210,41 @@ void load(Overlay& g, uint32_t n, const uint64_t* off, const uint32_t* tgt,
 // level re-relaxes all edges out of every vertex reached so far using the
 // previous level's values, exactly as the recurrence reads.
 struct HopSearch {
-    std::vector<uint32_t> prev, cur;
+    std::vector<uint32_t> prev, cur, mark;
     std::vector<char> seen;
-    std::vector<uint32_t> reached;
+    std::vector<uint32_t> reached, front, next;
+    uint64_t work = 0;  // out-edges of the frontier vertices of every level run, summed
 
-    explicit HopSearch(uint32_t n) : prev(n, INF), cur(n, INF), seen(n, 0) {}
+    explicit HopSearch(uint32_t n) : prev(n, INF), cur(n, INF), mark(n, 0), seen(n, 0) {}
 
     // Levels 1..H of a hop-synchronous search from s that keeps only labels
     // below `bound` (a walk at or above the bound cannot decide a candidate:
     // keep(via, d) holds for every via <= bound whenever d >= bound). After
     // each level, if more than `ball` vertices (s included) hold a label, the
-    // search stops there and the labels of that level are its result.
+    // search stops there and the labels of that level are its result. The
+    // frontier of a level is s (level 1) or the vertices whose label dropped
+    // in the level before; only their out-edges can lower a label. With a
+    // finite `level_work`, a level from the second on whose frontier has
+    // more than that many out-edges in total is not run, and the labels of
+    // the level before are the result.
     void run(const std::vector<Adj>& out, uint32_t s, uint32_t H, uint32_t bound = INF,
-             uint64_t ball = ~uint64_t(0)) {
+             uint64_t ball = ~uint64_t(0), uint64_t level_work = ~uint64_t(0)) {
         for (uint32_t x : reached) {
             prev[x] = cur[x] = INF;
             seen[x] = 0;
+            mark[x] = 0;
         }
         reached.clear();
         prev[s] = cur[s] = 0;
         seen[s] = 1;
         reached.push_back(s);
+        front.assign(1, s);
         for (uint32_t k = 1; k <= H; ++k) {
+            uint64_t wk = 0;
+            for (uint32_t x : front) wk += out[x].size();
+            if (k >= 2 && wk > level_work) break;
+            work += wk;
+            next.clear();
             size_t R = reached.size();
             for (size_t i = 0; i < R; ++i) {
                 uint32_t x = reached[i];
@@ -238,10 +257,15 @@ struct HopSearch {
                             seen[y] = 1;
                             reached.push_back(y);
                         }
+                        if (mark[y] != k) {
+                            mark[y] = k;
+                            next.push_back(y);
+                        }
                     }
                 }
             }
             for (uint32_t x : reached) prev[x] = cur[x];
+            front.swap(next);
             if (reached.size() > ball) break;
         }
     }
@@ -318,6 +342,7 @@ struct Searcher {
 struct Witness {
     uint32_t H = 0;
     uint64_t ball = ~uint64_t(0);
+    uint64_t level_work = ~uint64_t(0);
     uint64_t theta = 0;
     bool prune = false;  // the recorded distances also decide edge deletions
     bool memo = false;   // the distance map persists across phases and rounds
@@ -379,7 +404,7 @@ uint64_t local_search(const Overlay& g, const std::vector<char>& middle,
             // candidate bound is part of the definition and stays.
             const bool unbounded = wit.ball == ~uint64_t(0);
             h.hop.run(g.out, s, wit.H, unbounded && wit.prune ? std::max(bound, direct) : bound,
-                      wit.ball);
+                      wit.ball, wit.level_work);
             for (uint32_t v : targets) outp.push_back({pair_key(s, v), h.hop.dist(v)});
         }
     };
@@ -469,6 +494,7 @@ struct CH {
     // Overlay edges deleted by the pruning of Alg. 3: (round, s, v, w).
     std::vector<std::array<uint32_t, 4>> pruned;
     uint64_t searches = 0;  // witness searches run (sources with a target to search)
+    uint64_t witness_work = 0;  // hop-limited searches: frontier out-edges of the levels run
 };
 
 }  // namespace
@@ -538,7 +564,7 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
            const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t seed,
            bool want_trace = false, const Replay* replay = nullptr,
            uint64_t cmax = ~uint64_t(0), uint64_t ball = ~uint64_t(0), uint64_t theta = 0,
-           bool prune = false, uint64_t memo_limit = 0) {
+           bool prune = false, uint64_t memo_limit = 0, uint64_t level_work = ~uint64_t(0)) {
     Overlay g;
     load(g, n, off, tgt, w);
     ch.ed_last.assign(n, 0);
@@ -560,6 +586,7 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
     wit.theta = theta;
     wit.prune = prune;
     wit.memo = memo_limit > 0;
+    wit.level_work = level_work;
     Searcher hs(n);
     std::unordered_map<uint64_t, uint32_t> dist;
     std::vector<Searcher>* per_thread = nullptr;
@@ -570,6 +597,17 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
     per_thread = &hs_pool;
 #endif
 
+    // the frontier work of the searches so far, collected from every searcher
+    auto take_work = [&]() {
+        uint64_t w = hs.hop.work;
+        hs.hop.work = 0;
+        if (per_thread)
+            for (auto& t : *per_thread) {
+                w += t.hop.work;
+                t.hop.work = 0;
+            }
+        return w;
+    };
     uint64_t live = n;
     uint64_t live_edges = 0;
     for (uint32_t u = 0; u < n; ++u) live_edges += g.out[u].size();
@@ -595,6 +633,7 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
         // Step 1: LocalSearch for the affected set.
         for (uint32_t u : Ae) inA[u] = 1;
         st[ST_SCORE_SOURCES] = local_search(g, inA, Ae, wit, hs, dist, per_thread, &ch.searches);
+        ch.witness_work += take_work();
 
         // Pruning (Alg. 3, last step): an overlay edge (s, v) heavier than the
         // witness distance just recorded for (s, v) is deleted. That distance
@@ -670,6 +709,7 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
         // the same overlay.
         for (uint32_t u : F) inF[u] = 1;
         st[ST_CONTRACT_SOURCES] = local_search(g, inF, F, wit, hs, dist, per_thread, &ch.searches);
+        ch.witness_work += take_work();
 
         std::map<std::pair<uint32_t, uint32_t>, std::pair<uint32_t, uint32_t>> best;
         for (uint32_t u : F) {
@@ -884,7 +924,7 @@ int orc_build2(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
                const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t tie_seed,
                int want_trace, uint64_t nreplay, const uint32_t* rp_round, const uint32_t* rp_u,
                const int32_t* rp_p, uint64_t cmax, uint64_t ball, uint64_t theta, int prune,
-               uint64_t memo_limit, orc_ch** out) {
+               uint64_t memo_limit, uint64_t level_work, orc_ch** out) {
     // the settled-vertex cap replaces the hop-limited search, ball bound included
     if (!out || !validate(n, m, off, tgt, w) || tie_mode > 1 || (theta && ball != ~uint64_t(0)))
         return ORC_EINVAL;
@@ -893,7 +933,7 @@ int orc_build2(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
     orc_ch* h = new orc_ch();
     try {
         build(h->ch, n, off, tgt, w, H, tie_mode, tie_seed, want_trace != 0,
-              nreplay ? &rp : nullptr, cmax, ball, theta, prune != 0, memo_limit);
+              nreplay ? &rp : nullptr, cmax, ball, theta, prune != 0, memo_limit, level_work);
     } catch (const std::exception&) {
         delete h;
         return ORC_EINVAL;
@@ -904,6 +944,7 @@ int orc_build2(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
 
 uint64_t orc_num_pruned(const orc_ch* h) { return h->ch.pruned.size(); }
 uint64_t orc_searches(const orc_ch* h) { return h->ch.searches; }
+uint64_t orc_witness_work(const orc_ch* h) { return h->ch.witness_work; }
 void orc_get_pruned(const orc_ch* h, uint32_t* out4) {
     size_t i = 0;
     for (const auto& row : h->ch.pruned)

@@ -1,6 +1,6 @@
 """Property tests over random small digraphs (no GPU): for any hop limit,
-tie-break, candidate bound, witness ball bound, settled-vertex cap, pruning
-and memoisation setting, every CH query and every one-to-all row equals the true
+tie-break, candidate bound, witness ball bound, level-work bound, settled-
+vertex cap, pruning and memoisation setting, every CH query and every one-to-all row equals the true
 distance, and every round re-derives from the definitions."""
 import numpy as np
 import pytest
@@ -27,16 +27,17 @@ def _case(draw):
     theta = 0 if ball is not None else draw(st.sampled_from([0, 0, 1, 2, 4, 9]))
     prune = draw(st.booleans())
     memo = draw(st.sampled_from([0, 0, 5, 1 << 40]))
+    level_work = None if theta else draw(st.sampled_from([None, None, 0, 3, 12]))
     return (I.random_digraph(n, m, 1, wmax, seed=seed), H, tie, seed & 0xFFFF, cmax, ball, theta,
-            prune, memo)
+            prune, memo, level_work)
 
 
 @hyp.settings(max_examples=200, deadline=None, derandomize=True)
 @hyp.given(_case())
 def test_random_digraphs(case):
-    g, H, tie, seed, cmax, ball, theta, prune, memo = case
+    g, H, tie, seed, cmax, ball, theta, prune, memo, level_work = case
     och = _rederive(g, H, tie, seed=seed, cmax=cmax, ball=ball, theta=theta, prune=prune,
-                    memo=memo)
+                    memo=memo, level_work=level_work)
     s, t = np.meshgrid(np.arange(g.n), np.arange(g.n), indexing="ij")
     d = och.query(s.ravel().astype(np.uint32), t.ravel().astype(np.uint32))
     truth = all_pairs_truth(g)

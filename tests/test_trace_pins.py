@@ -159,24 +159,43 @@ def _settled_distances(gr, s, theta):
     return out
 
 
-def _ball_labels(gr, s, H, bound, ball):
+def _ball_labels(gr, s, H, bound, ball, level_work=None):
     """Labels below `bound` of a hop-synchronous search from s: those of
     level H, or with a ball bound those of the first level at which more than
-    `ball` vertices hold one; INF elsewhere."""
+    `ball` vertices hold one, or with a level-work bound those of the last
+    level before one whose frontier (the vertices whose label dropped in the
+    level before) has more than `level_work` out-edges; INF elsewhere."""
+    return _ball_search(gr, s, H, bound, ball, level_work)[0]
+
+
+def _ball_search(gr, s, H, bound, ball, level_work=None):
+    """(_ball_labels's labels, the frontier out-edges of the levels run)."""
+    outdeg = np.diff(gr.offsets.astype(np.int64))
     lab = np.where(np.arange(gr.n) == s, 0, INF).astype(np.int64)
+    front = np.array([s])
+    work = 0
     for h in range(1, H + 1):
+        wk = int(outdeg[front].sum())
+        if level_work is not None and h >= 2 and wk > level_work:
+            break
+        work += wk
         dist_h = O.hop_limited(gr, h, s).astype(np.int64)
-        lab = np.where(dist_h < bound, dist_h, INF)
+        new = np.where(dist_h < bound, dist_h, INF)
+        front = np.flatnonzero(new < lab)
+        lab = new
         if ball is not None and int((lab != INF).sum()) > ball:
             break
-    return lab
+    return lab, work
 
 
-def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=False, memo=0):
+def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=False, memo=0,
+              level_work=None):
     och = O.build_ch(g, H, tie, tie_seed=seed, cmax=cmax, ball=O.CMAX_ALL if ball is None else ball,
-                     theta=theta, prune=prune, memo=memo)
+                     theta=theta, prune=prune, memo=memo,
+                     level_work=O.CMAX_ALL if level_work is None else level_work)
     memo_d = {}
     searches = [0]
+    work = [0]
     n = g.n
     off, tgt, w = O.normalize(g)
     edges = {}
@@ -219,21 +238,18 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=Fals
                 if v1 not in dh:
                     dh[v1] = _settled_distances(gr, v1, theta)
                 return int(dh[v1][v2])
-            if ball is None:
+            if ball is None and level_work is None:
                 if v1 not in dh:
                     dh[v1] = O.hop_limited(gr, H, v1)
                 return int(dh[v1][v2])
-            bound = max([c1 + c2 for u, c1 in out[v1].items() if u in middles
-                         for x, c2 in out[u].items() if x != v1], default=0)
+            cands = [(c1 + c2, x) for u, c1 in out[v1].items() if u in middles
+                     for x, c2 in out[u].items() if x != v1]
+            bound = max([c for c, _ in cands], default=0)
+            if prune and ball is None:
+                bound = max([bound] + [live[(v1, x)] for _, x in cands if (v1, x) in live])
             keyd = (v1, bound)
             if keyd not in dh:
-                lab = None
-                for h in range(1, H + 1):
-                    dist_h = O.hop_limited(gr, h, v1)
-                    lab = np.where(dist_h.astype(np.int64) < bound, dist_h, INF)
-                    if int((lab != INF).sum()) > ball:
-                        break
-                dh[keyd] = lab if lab is not None else np.where(np.arange(n) == v1, 0, INF)
+                dh[keyd] = _ball_labels(gr, v1, H, bound, ball, level_work)
             return int(dh[keyd][v2])
 
         def fill(middles):
@@ -248,8 +264,6 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=Fals
                 if not cands:
                     continue
                 searches[0] += 1
-                if not memo:
-                    continue
                 new = {v for _, v in cands}
                 if theta:
                     lab = _settled_distances(gr, s, theta)
@@ -257,9 +271,11 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=Fals
                     bound = max(c for c, _ in cands)
                     if prune and ball is None:
                         bound = max([bound] + [live[(s, v)] for v in new if (s, v) in live])
-                    lab = _ball_labels(gr, s, H, bound, ball)
-                for v in new:
-                    memo_d[(s, v)] = int(lab[v])
+                    lab, wk = _ball_search(gr, s, H, bound, ball, level_work)
+                    work[0] += wk
+                if memo:
+                    for v in new:
+                        memo_d[(s, v)] = int(lab[v])
 
         def dm(v1, v2, middles):
             return memo_d[(v1, v2)] if memo else d(v1, v2, middles)
@@ -332,6 +348,7 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=Fals
     assert och.rounds == r
     assert och.pruned.tolist() == [list(p) for p in pruned]
     assert och.searches == searches[0]
+    assert och.witness_work == work[0]
     return och
 
 
@@ -407,3 +424,14 @@ def test_every_round_rederived_with_memoisation_and_a_core():
         _rederive(I.random_digraph(70, 300, 1, 20, seed=70 + seed), 5, O.TIE_HASHED, cmax=9,
                   prune=True, memo=1 << 40)
         _rederive(I.random_digraph(70, 300, 1, 20, seed=73 + seed), 3, O.TIE_ID, cmax=9, memo=50)
+
+
+@pytest.mark.parametrize("name,g", [(n, g) for n, g in small_families()
+                                    if n in ("digraph0", "digraph2", "sparse3", "grid8", "geo150",
+                                             "rmat8", "star9", "complete6")],
+                         ids=lambda x: x if isinstance(x, str) else "")
+@pytest.mark.parametrize("H,lw,ball,prune,memo", [
+    (3, 0, None, False, 0), (3, 4, None, False, 0), (5, 12, None, False, 0), (5, 40, None, True, 0),
+    (4, 12, 5, False, 0), (4, 8, None, False, 1 << 40), (5, 20, 6, True, 40)])
+def test_every_round_rederived_with_a_level_work_bound(name, g, H, lw, ball, prune, memo):
+    _rederive(g, H, O.TIE_HASHED, seed=13, ball=ball, prune=prune, memo=memo, level_work=lw)

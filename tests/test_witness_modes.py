@@ -15,6 +15,8 @@ Pins, none of which goes through the oracle's own search code:
     a ball bound, a settled cap or pruning.
   * with hop limit 0 or theta = 1 every recorded value is INF, so
     memoisation cannot change a decision: the same hierarchy.
+  * a level-work bound of 0 leaves level 1 alone: the hierarchy of hop
+    limit 1.
   * every query is exact in every mode.
 Round-by-round re-derivations of both modes are in test_trace_pins.py."""
 import numpy as np
@@ -76,6 +78,25 @@ def test_memo_halves_the_searches_on_a_geometric_graph():
     assert np.array_equal(b.query(s, t), O.dijkstra_pairs(g, s, t))
 
 
+@pytest.mark.parametrize("name,g", FAMILIES, ids=[n for n, _ in FAMILIES])
+def test_level_work_zero_equals_hop_limit_one(name, g):
+    # with no out-edge allowed past the first level a search runs level 1
+    # alone (a second level whose frontier has no out-edge lowers nothing)
+    _same(O.build_ch(g, 5, level_work=0), O.build_ch(g, 1))
+    _same(O.build_ch(g, 4, level_work=0, cmax=6), O.build_ch(g, 1, cmax=6))
+
+
+def test_level_work_bound_cuts_the_work_on_rmat():
+    g = I.rmat_graph(scale=10, nsamples=16 << 10, wmax=1000, seed=8)
+    a = O.build_ch(g, 2, cmax=256, ball=256)
+    b = O.build_ch(g, 2, cmax=256, ball=256, level_work=1024)
+    assert b.witness_work * 5 < a.witness_work
+    s, t = I.random_pairs(g.n, 2000, seed=9)
+    want = O.dijkstra_pairs(g, s, t)
+    assert np.array_equal(a.query(s, t), want)
+    assert np.array_equal(b.query(s, t), want)
+
+
 def test_theta_and_ball_are_exclusive():
     g = I.random_digraph(10, 30, 1, 5, seed=1)
     with pytest.raises(ValueError):
@@ -84,7 +105,8 @@ def test_theta_and_ball_are_exclusive():
 
 MODES = [dict(), dict(prune=True), dict(theta=3), dict(theta=3, prune=True),
          dict(ball=2, prune=True), dict(cmax=4, prune=True), dict(cmax=4, theta=8),
-         dict(memo=1 << 40), dict(memo=30, prune=True), dict(memo=1 << 40, theta=4, cmax=4)]
+         dict(memo=1 << 40), dict(memo=30, prune=True), dict(memo=1 << 40, theta=4, cmax=4),
+         dict(level_work=6), dict(level_work=10, prune=True, memo=1 << 40, cmax=4)]
 
 
 @pytest.mark.parametrize("mode", MODES, ids=[",".join(f"{k}={v}" for k, v in m.items()) or "plain"
