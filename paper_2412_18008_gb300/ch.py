@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -211,6 +212,9 @@ class CH:
 
     def __init__(self, handle: C.c_void_p):
         self._h = handle
+        # servers and captured graphs whose device work reads this handle's
+        # memory; close() ends them first
+        self._deps = weakref.WeakSet()
 
     # -- construction -----------------------------------------------------
     @staticmethod
@@ -405,7 +409,9 @@ class CH:
         h = C.c_void_p()
         _check(load().ch_query_graph_create(self._h, src.data_ptr(), dst.data_ptr(), src.numel(),
                                             out.data_ptr(), C.byref(h)))
-        return QueryGraph(h, (src, dst, out), self)
+        g = QueryGraph(h, (src, dst, out), self)
+        self._deps.add(g)
+        return g
 
     # -- introspection ----------------------------------------------------
     def stats(self) -> dict:
@@ -453,9 +459,23 @@ class CH:
         return dict(rows=rows, prio=prio, labels=labels)
 
     def close(self):
-        if self._h:
-            load().ch_free(self._h)
-            self._h = None
+        """Stop this hierarchy's servers and free its captured graphs, then
+        free the hierarchy. If a server does not stop, its kernel may still
+        read the hierarchy, so the hierarchy's memory is left allocated for
+        the rest of the process and the error is raised."""
+        if not self._h:
+            return
+        for dep in list(self._deps):
+            try:
+                if isinstance(dep, Server):
+                    dep.stop()
+                else:
+                    dep.close()
+            except Exception:
+                self._h = None  # never freed: device work may still use it
+                raise
+        h, self._h = self._h, None
+        load().ch_free(h)
 
     def __enter__(self):
         return self
@@ -508,6 +528,7 @@ class Server:
         p = ServerParamsT(blocks, ring, pool, idle_ms, 0)
         self._h = C.c_void_p()
         _check(load().ch_server_start(ch._h, C.byref(p), C.byref(self._h)))
+        ch._deps.add(self)
 
     @property
     def blocks(self) -> int:
