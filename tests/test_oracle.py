@@ -49,8 +49,12 @@ def test_golden_examples(name):
     tie = O.TIE_ID if spec.get("tie_break") == "id" else O.TIE_HASHED
     ch = O.build_ch(spec["graph"], spec["hop_limit"], tie, cmax=spec.get("cmax", O.CMAX_ALL),
                     ball=spec.get("ball", O.CMAX_ALL), theta=spec.get("theta", 0),
-                    prune=bool(spec.get("prune", 0)))
+                    prune=bool(spec.get("prune", 0)), level_work=spec.get("level_work", O.CMAX_ALL))
     assert sorted(map(tuple, ch.pruned.tolist())) == sorted(spec.get("pruned", []))
+    if "expect_searches" in spec:
+        assert ch.searches == spec["expect_searches"]
+    if "expect_witness_work" in spec:
+        assert ch.witness_work == spec["expect_witness_work"]
     assert ch.rounds == spec["expect_rounds"]
     if "expect_stats" in spec:  # every round's counters, row after row
         assert ch.stats.ravel().tolist() == spec["expect_stats"]
