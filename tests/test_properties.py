@@ -16,7 +16,7 @@ st = pytest.importorskip("hypothesis.strategies")
 
 @st.composite
 def _case(draw):
-    n = draw(st.integers(1, 24))
+    n = draw(st.integers(1, 40))
     m = draw(st.integers(0, 4 * n))
     seed = draw(st.integers(0, 2**31 - 1))
     wmax = draw(st.sampled_from([1, 3, 30, 1000]))
@@ -32,7 +32,7 @@ def _case(draw):
             prune, memo, level_work)
 
 
-@hyp.settings(max_examples=200, deadline=None, derandomize=True)
+@hyp.settings(max_examples=400, deadline=None, derandomize=True)
 @hyp.given(_case())
 def test_random_digraphs(case):
     g, H, tie, seed, cmax, ball, theta, prune, memo, level_work = case
