@@ -1,7 +1,8 @@
 """Property tests over random small digraphs (no GPU): for any hop limit,
 tie-break, candidate bound, witness ball bound, level-work bound, settled-
-vertex cap, pruning and memoisation setting, every CH query and every one-to-all row equals the true
-distance, and every round re-derives from the definitions."""
+vertex cap, pruning and memoisation setting, every CH query and every
+one-to-all row equals the true distance, and every round re-derives from the
+definitions."""
 import numpy as np
 import pytest
 
