@@ -313,6 +313,10 @@ def _rederive(g, H, tie, seed=0, cmax=O.CMAX_ALL, ball=None, theta=0, prune=Fals
             assert (level[core] == r).all() and och.rounds == r
             break
         assert sorted(F) == np.flatnonzero(level == r).tolist(), r
+        # Alg. 5's invariants: V_F is independent, and the live eligible
+        # vertex of least key is always in it (so every round makes progress)
+        assert not any(v in set(F) for u in F for v in set(inn[u]) | set(out[u]))
+        assert min((u for u in np.flatnonzero(alive).tolist() if eligible[u]), key=key) in F
         # contraction (Alg. 6): candidates, witness test on the overlay as it
         # stands now, merge, insertion
         middles = set(F)
