@@ -434,3 +434,49 @@ def test_threaded_build_is_identical(name, g, cmax, ball):
     s, t = np.meshgrid(np.arange(g.n), np.arange(g.n), indexing="ij")
     s, t = s.ravel(), t.ravel()
     assert np.array_equal(a.query(s, t), b.query(s, t))
+
+
+# ---------------------------------------------------------------------------
+# Bidirectional trees: every shortest path is the unique tree path
+# ---------------------------------------------------------------------------
+
+def _random_tree(n, seed, wmax=30):
+    rng = np.random.default_rng(seed)
+    label = rng.permutation(n)
+    parent = [int(rng.integers(0, i)) for i in range(1, n)]
+    w = rng.integers(1, wmax + 1, n - 1)
+    edges = []
+    for i, (p, c) in enumerate(zip(parent, range(1, n))):
+        edges += [(label[p], label[c], int(w[i])), (label[c], label[p], int(w[i]))]
+    return from_edges(n, edges)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tree_shortcuts_follow_tree_paths(seed):
+    """With exact witnesses (H >= n) on a bidirectional tree, contracting x
+    keeps (a, x, b) exactly when x lies on the tree path from a to b, with
+    weight dist(a, b); it is inserted when (a, b) is not yet an overlay edge.
+    Replaying the oracle's contraction order with that rule alone (no witness
+    search) must give its shortcut log."""
+    n = 40
+    g = _random_tree(n, seed)
+    truth = all_pairs_truth(g).astype(np.int64)
+    och = O.build_ch(g, n)
+    adj = {(a, b) for a, bs in _adj(g).items() for b in bs}
+    alive = np.ones(n, bool)
+    want = set()
+    for r in range(och.rounds):
+        F = np.flatnonzero(och.level == r).tolist()
+        new = set()
+        for x in F:
+            nb = {b for (a, b) in adj if a == x and alive[b]}
+            for a in nb:
+                for b in nb:
+                    if a != b and truth[a, x] + truth[x, b] == truth[a, b] and (a, b) not in adj:
+                        new.add((r, a, b, int(truth[a, b]), x))
+        want |= new
+        adj |= {(a, b) for _, a, b, _, _ in new}
+        alive[F] = False
+        adj = {(a, b) for (a, b) in adj if alive[a] and alive[b]}
+    assert set(map(tuple, och.shortcuts.tolist())) == want
+    assert np.array_equal(och.one_to_all(np.arange(n)).astype(np.int64), truth)
