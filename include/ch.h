@@ -463,6 +463,15 @@ int ch_server_stop(ch_server_t *sv);
 
 void ch_free(ch_t *ch);
 
+/* Failure injection for tests of the error paths (not part of the method).
+ * After ch_debug_fail_alloc(k) with k >= 0, the library's device
+ * allocations succeed k more times; the next one fails as if the device were
+ * out of memory (the call in progress returns CH_ENOMEM and releases what it
+ * had allocated), and later allocations succeed again. A negative k turns
+ * the injection off. Returns the previous setting (-1 when it was off).
+ * Process-wide; makes no CUDA call. */
+int64_t ch_debug_fail_alloc(int64_t after);
+
 const char *ch_last_error(void);
 
 /* Library version string, e.g. "gb300-ch 0.1 sm_103a". */

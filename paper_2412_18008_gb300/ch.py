@@ -171,6 +171,8 @@ def load(build_if_missing: bool = True):
     lib.ch_last_error.restype = C.c_char_p
     lib.ch_version.restype = C.c_char_p
     lib.ch_kernel_launches.restype = C.c_uint64
+    lib.ch_debug_fail_alloc.argtypes = [C.c_int64]
+    lib.ch_debug_fail_alloc.restype = C.c_int64
     _lib = lib
     return lib
 
@@ -645,3 +647,10 @@ def version() -> str:
 def kernel_launches() -> int:
     """CUDA kernels libch.so has launched in this process."""
     return int(load().ch_kernel_launches())
+
+
+def debug_fail_alloc(after: int) -> int:
+    """Failure injection (ch_debug_fail_alloc): the library's device
+    allocation after the next ``after`` ones fails with CH_ENOMEM, once; a
+    negative value turns it off. Returns the previous setting."""
+    return int(load().ch_debug_fail_alloc(int(after)))

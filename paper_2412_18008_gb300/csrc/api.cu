@@ -14,6 +14,14 @@ namespace gbch {
 namespace {
 thread_local std::string g_last_error;
 std::atomic<uint64_t> g_launches{0};
+// Allocations left before the injected failure; negative = off.
+std::atomic<int64_t> g_alloc_countdown{-1};
+}
+
+bool inject_alloc_failure() {
+    if (g_alloc_countdown.load(std::memory_order_relaxed) < 0) return false;
+    // the allocation that takes the count from 0 to -1 fails; later ones do not
+    return g_alloc_countdown.fetch_sub(1, std::memory_order_relaxed) == 0;
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -68,6 +76,10 @@ const char *ch_last_error(void) { return g_last_error.c_str(); }
 const char *ch_version(void) { return "gb300-ch 0.1 sm_103a"; }
 
 uint64_t ch_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int64_t ch_debug_fail_alloc(int64_t after) {
+    return g_alloc_countdown.exchange(after < 0 ? -1 : after, std::memory_order_relaxed);
+}
 
 void ch_default_params(ch_params_t *p) {
     if (!p) return;

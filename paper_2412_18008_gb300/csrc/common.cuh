@@ -51,6 +51,10 @@ void kernel_launch_add(int64_t d);
 // Device memory owned by the library
 // ---------------------------------------------------------------------------
 
+// Failure injection for the error paths (ch_debug_fail_alloc): true when
+// this allocation is the one chosen to fail. Off unless armed.
+bool inject_alloc_failure();
+
 template <class T>
 struct DevBuf {
     T *ptr = nullptr;
@@ -83,6 +87,9 @@ struct DevBuf {
     void alloc(size_t n) {
         release();
         if (n == 0) n = 1;
+        if (inject_alloc_failure())
+            throw Error{CH_ENOMEM, "injected failure of a " + std::to_string(n * sizeof(T)) +
+                                       "-byte device allocation"};
         cudaError_t e = cudaMalloc(&ptr, n * sizeof(T));
         if (e != cudaSuccess) {
             cudaGetLastError();
