@@ -110,7 +110,21 @@ typedef struct {
  *              at which more than θ vertices (the source included) hold one;
  *              the distances of that level replace d_H. Still upper bounds
  *              on real walks, so distances stay exact (only more shortcuts
- *              may be kept). 0 = no bound (the default). */
+ *              may be kept). 0 = no bound (the default).
+ *   witness_memo_limit  nonzero: witness distances are memoised across
+ *              phases and rounds (Alg. 3's dist map, Sec. 4.2). A source
+ *              searches only for targets whose pair has no recorded
+ *              distance, keeping labels below its new targets' heaviest
+ *              candidate weight; a source with none is not searched. The
+ *              value recorded is the label the search held, else INF.
+ *              Decisions read the map. The map is cleared after any round
+ *              that leaves more than this many pairs in it. Every recorded
+ *              value is the weight of a real walk (or INF), so distances
+ *              stay exact. The map takes 12 bytes per slot; it keeps at
+ *              least twice (its pairs + 8 per input edge) slots, growing
+ *              between rounds, and a round that overfills it fails with
+ *              CH_ENOMEM.
+ *              0 = off (the default). */
 typedef struct {
     uint32_t hop_limit;
     uint32_t priority;
@@ -122,7 +136,7 @@ typedef struct {
     int32_t trace;
     uint32_t witness_route_deg;
     uint32_t witness_ball_limit;
-    uint32_t reserved;
+    uint32_t witness_memo_limit;
 } ch_params_t;
 
 /* Training parameters of ch_mlp_train (Adam, mean squared error). */

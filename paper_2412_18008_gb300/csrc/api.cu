@@ -94,7 +94,7 @@ void ch_default_params(ch_params_t *p) {
     p->trace = 0;
     p->witness_route_deg = 0;
     p->witness_ball_limit = 0;
-    p->reserved = 0;
+    p->witness_memo_limit = 0;
 }
 
 int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out) {

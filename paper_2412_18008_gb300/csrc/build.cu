@@ -52,6 +52,7 @@ constexpr uint32_t ERR_INPUT = 1u;
 constexpr uint32_t ERR_REC_OVERFLOW = 2u;
 constexpr uint32_t ERR_CH_OVERFLOW = 4u;
 constexpr uint32_t ERR_BOUND = 8u;  // an index check failed; the access was skipped
+constexpr uint32_t ERR_MAP_FULL = 16u;  // the memoised-distance map has no free slot
 
 constexpr int MODE_SCORE = 0;
 constexpr int MODE_PRUNE = 1;
@@ -73,6 +74,7 @@ struct Ctl {
     unsigned long long wit_sources, wit_fallback, wit_vertices, wit_edges, wit_middles,
         wit_midedges, wit_block;
     unsigned long long trace_valid;  // trace rows of eligible rescorings
+    unsigned long long dm_count;     // keys in the memoised-distance map since its last clear
 };
 
 struct Dev {
@@ -114,8 +116,86 @@ constexpr uint32_t MEMO_MAX_OUT = 64;
 constexpr int32_t P_INELIGIBLE = 2147483646;  // INT32_MAX - 1
 constexpr uint32_t AMARK_NONE = 0xFFFFFFFFu;   // never a round index
 
+// Memoised witness distances across phases and rounds (Alg. 3's dist map):
+// open addressing on 64-bit keys (s << 32 | v) with linear probing, the
+// distance in a parallel array. Only the source s touches keys (s, .), and it
+// inserts them only after all of its decisions of the phase are made, so a
+// key a search finds was written, with its value, by an earlier launch. Keys
+// are never removed between two clears, so a probe that reaches an empty
+// slot before its key proves the key absent.
+constexpr unsigned long long DMAP_EMPTY = ~0ull;
+// An insertion never places a key further than this from its home slot (it
+// reports the map full instead), so a lookup may stop there too.
+constexpr unsigned long long DMAP_MAXPROBE = 4096;
+
+struct DMap {
+    unsigned long long *keys;
+    uint32_t *vals;
+    unsigned long long mask;  // capacity - 1; the capacity is a power of two
+    unsigned long long *count;
+};
+
+__device__ __forceinline__ unsigned long long dmap_key(uint32_t s, uint32_t v) {
+    return ((unsigned long long)s << 32) | v;
+}
+
+// SplitMix64's output finaliser (Steele, Lea and Flood, OOPSLA 2014) spreads
+// the keys over the slots.
+__device__ __forceinline__ unsigned long long dmap_hash(unsigned long long x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    x ^= x >> 31;
+    return x;
+}
+
+__device__ __forceinline__ bool dmap_get(const DMap &m, unsigned long long key, uint32_t *val) {
+    unsigned long long i = dmap_hash(key) & m.mask;
+    for (unsigned long long p = 0; p < DMAP_MAXPROBE && p <= m.mask; ++p) {
+        const unsigned long long k = m.keys[i];
+        if (k == key) {
+            *val = m.vals[i];
+            return true;
+        }
+        if (k == DMAP_EMPTY) return false;
+        i = (i + 1) & m.mask;
+    }
+    return false;
+}
+
+// Records key -> val unless the key is present: 1 = inserted, 0 = present,
+// -1 = no free slot.
+__device__ __forceinline__ int dmap_put(const DMap &m, unsigned long long key, uint32_t val) {
+    unsigned long long i = dmap_hash(key) & m.mask;
+    for (unsigned long long p = 0; p < DMAP_MAXPROBE && p <= m.mask; ++p) {
+        unsigned long long k = m.keys[i];
+        if (k == key) return 0;
+        if (k == DMAP_EMPTY) {
+            k = atomicCAS(&m.keys[i], DMAP_EMPTY, key);
+            if (k == DMAP_EMPTY) {
+                m.vals[i] = val;
+                return 1;
+            }
+            if (k == key) return 0;
+        }
+        i = (i + 1) & m.mask;
+    }
+    return -1;
+}
+
+// Moves every key of `from` into the larger map `to` (the count is unchanged).
+__global__ void k_dmap_rehash(DMap from, DMap to, Ctl *ctl) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i <= from.mask;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = from.keys[i];
+        if (k != DMAP_EMPTY && dmap_put(to, k, from.vals[i]) < 0) atomicOr(&ctl->err, ERR_MAP_FULL);
+    }
+}
+
 struct WArgs {
     Dev d;
+    DMap dm;                 // memoised distances (witness kernels instantiated with XM)
     const uint32_t *S;       // source list
     const uint32_t *nS;      // its length (device)
     uint32_t *work;          // dynamic work counter
@@ -381,7 +461,7 @@ __device__ __forceinline__ uint32_t ht_find(const uint32_t *keys, int bits, uint
     return EMPTY;
 }
 
-template <int MODE>
+template <int MODE, bool XM>
 __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
     __shared__ WarpSmem smem[WIT_WARPS];
     WarpSmem &w = smem[threadIdx.x >> 5];
@@ -393,6 +473,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
     const bool route_all = nS <= a.route_all;
     unsigned long long c_src = 0, c_vert = 0, c_edge = 0, c_mid = 0, c_midedge = 0;
     unsigned long long c_cand = 0, c_kept = 0, c_merged = 0, c_ins = 0, c_new = 0;
+    unsigned long long c_dm = 0;  // keys added to the memoised-distance map
 
     while (true) {
         uint32_t i = 0;
@@ -427,6 +508,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         // contracted middle has its score-phase decisions memoised.
         uint32_t bound = 0;
         bool memo_all = MODE == MODE_PRUNE && d.memo;
+        bool any = false;  // XM: a candidate exists (the bound covers new targets only)
         for (uint32_t c0 = 0; c0 < sd; c0 += 32) {
             const uint32_t j = c0 + lane;
             const bool valid = j < sd;
@@ -449,7 +531,12 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                 const uint32_t ex_o = __shfl_sync(FULL, excl, o);
                 if (idx < total) {
                     const uint2 e2 = d.out_adj[ub_o + (idx - ex_o)];
-                    if (e2.x != s) bound = max(bound, sat_add(w1, e2.y));
+                    if (e2.x != s) {
+                        uint32_t known;
+                        if constexpr (XM) any = true;
+                        if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &known)))
+                            bound = max(bound, sat_add(w1, e2.y));
+                    }
                 }
             }
         }
@@ -458,7 +545,10 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
             continue;
         }
-        if (bound == 0) {  // no candidate pair from this source
+        bool no_cand;
+        if constexpr (XM) no_cand = !__any_sync(FULL, any);
+        else no_cand = bound == 0;
+        if (no_cand) {  // no candidate pair from this source
             c_src += (lane == 0);
             c_mid += l_mid;
             c_midedge += l_midedge;
@@ -468,7 +558,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         // Phase 1: hop-limited Bellman-Ford from s, levels 1..H, each level
         // relaxing from the previous level's values (frontier snapshots);
         // skipped when the decisions are memoised.
-        if (!memo_all) {
+        if (!memo_all && !(XM && bound == 0)) {
         for (uint32_t t = lane; t < WIT_T; t += 32) {
             w.key[t] = EMPTY;
             w.val[t] = INF;
@@ -601,8 +691,11 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                         if (MODE == MODE_PRUNE && memo_all) {
                             keepit = (mw_o >> kj) & 1ull;
                         } else {
-                            const uint32_t slot = ht_find(w.key, WIT_TBITS, e2.x);
-                            const uint32_t dh = slot == EMPTY ? INF : w.val[slot];
+                            uint32_t dh;
+                            if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &dh))) {
+                                const uint32_t slot = ht_find(w.key, WIT_TBITS, e2.x);
+                                dh = slot == EMPTY ? INF : w.val[slot];
+                            }
                             keepit = via != INF && via <= dh;
                         }
                         if (MODE == MODE_SCORE && keepit && mk_o)
@@ -672,6 +765,43 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             if (lane == 0) d.new_out[s] = tot_new;
             __syncwarp();
         }
+        // Phase 3 (memoised distances): the targets this search found new
+        // get their labels (INF when none), now that all of the source's
+        // decisions are made.
+        if constexpr (XM) {
+            if (bound != 0) {
+                bool full = false;
+                for (uint32_t c0 = 0; c0 < sd; c0 += 32) {
+                    const uint32_t j = c0 + lane;
+                    const bool valid = j < sd;
+                    const uint2 e = valid ? d.out_adj[sb + j] : make_uint2(0, 0);
+                    const bool mid = valid && id_ok(d, e.x) && is_middle<MODE>(d, e.x, r);
+                    uint32_t cnt = mid ? d.out_deg[e.x] : 0;
+                    const uint64_t ub = mid ? d.out_beg[e.x] : 0;
+                    if (mid && !out_list_ok(d, ub, cnt)) cnt = 0;
+                    const uint32_t incl = warp_incl_scan(cnt);
+                    const uint32_t total = __shfl_sync(FULL, incl, 31);
+                    const uint32_t excl = incl - cnt;
+                    for (uint32_t b = 0; b < total; b += 32) {
+                        const uint32_t idx = b + lane;
+                        const uint32_t o = warp_owner(excl, idx);
+                        const uint64_t ub_o = __shfl_sync(FULL, ub, o);
+                        const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                        if (idx < total) {
+                            const uint2 e2 = d.out_adj[ub_o + (idx - ex_o)];
+                            if (e2.x != s) {
+                                const uint32_t slot = ht_find(w.key, WIT_TBITS, e2.x);
+                                const int put = dmap_put(a.dm, dmap_key(s, e2.x),
+                                                         slot == EMPTY ? INF : w.val[slot]);
+                                full |= put < 0;
+                                c_dm += put > 0;
+                            }
+                        }
+                    }
+                }
+                if (full) atomicOr(&ctl->err, ERR_MAP_FULL);
+            }
+        }
         c_src += (lane == 0);
         c_vert += l_vert;
         c_edge += l_edge;
@@ -688,8 +818,10 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
     }
     FOLD64(c_vert) FOLD64(c_edge) FOLD64(c_mid) FOLD64(c_midedge) FOLD64(c_cand)
     FOLD64(c_kept) FOLD64(c_merged) FOLD64(c_ins) FOLD64(c_new)
+    if constexpr (XM) FOLD64(c_dm)
 #undef FOLD64
     if (lane == 0) {
+        if constexpr (XM) atomicAdd(a.dm.count, c_dm);
         atomicAdd(&ctl->wit_sources, c_src);
         atomicAdd(&ctl->wit_vertices, c_vert);
         atomicAdd(&ctl->wit_edges, c_edge);
@@ -728,9 +860,10 @@ struct BlkSmem {
     uint32_t cntw[WB_THREADS / 32][32];
     uint32_t nf[2];
     uint32_t item, ovf, bound, nnew, nkeys, memo_ok;
+    uint32_t any;  // memoised-distance mode: the source has a candidate
 };
 
-template <int MODE>
+template <int MODE, bool XM>
 __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
     extern __shared__ __align__(16) unsigned char wb_raw[];
     BlkSmem &b = *reinterpret_cast<BlkSmem *>(wb_raw);
@@ -742,6 +875,7 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
     const uint32_t nIn = ctl->nOvf;
     unsigned long long c_src = 0, c_vert = 0, c_edge = 0, c_mid = 0, c_midedge = 0;
     unsigned long long c_cand = 0, c_kept = 0, c_merged = 0, c_ins = 0, c_new = 0;
+    unsigned long long c_dm = 0;  // keys added to the memoised-distance map
     while (true) {
         __syncthreads();
         if (tid == 0) b.item = atomicAdd(&ctl->work3, 1u);
@@ -779,6 +913,7 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             b.ovf = 0;
             b.nnew = 0;
             b.memo_ok = MODE == MODE_PRUNE && d.memo;
+            if constexpr (XM) b.any = 0;
         }
         __syncthreads();
         // Phase 0: heaviest candidate weight of the source, and whether every
@@ -794,14 +929,22 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             l_midedge += ud;
             for (uint32_t jj = 0; jj < ud; ++jj) {
                 const uint2 e2 = d.out_adj[ub + jj];
-                if (e2.x != s) lb = max(lb, sat_add(e.y, e2.y));
+                if (e2.x != s) {
+                    uint32_t known;
+                    if constexpr (XM) b.any = 1;
+                    if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &known)))
+                        lb = max(lb, sat_add(e.y, e2.y));
+                }
             }
         }
         if (lb) atomicMax(&b.bound, lb);
         __syncthreads();
         const uint32_t bound = b.bound;
         const bool memo_all = b.memo_ok != 0;
-        if (bound == 0) {
+        bool no_cand;
+        if constexpr (XM) no_cand = b.any == 0;
+        else no_cand = bound == 0;
+        if (no_cand) {
             c_src += (tid == 0);
             c_mid += l_mid;
             c_midedge += l_midedge;
@@ -819,7 +962,7 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
         // level relaxing from the previous level's values (snapshots);
         // skipped when the decisions are memoised.
         uint32_t cur = 0;
-        for (uint32_t lvl = 1; lvl <= d.H && !memo_all; ++lvl) {
+        for (uint32_t lvl = 1; lvl <= d.H && !memo_all && !(XM && bound == 0); ++lvl) {
             __syncthreads();
             const uint32_t nfront = b.nf[cur];
             const uint32_t ovf = b.ovf;
@@ -917,8 +1060,11 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
                 if (MODE == MODE_PRUNE && memo_all) {
                     keepit = (mw_o >> kj) & 1ull;
                 } else {
-                    const uint32_t slot = ht_find(b.key, WB_TBITS, e2.x);
-                    const uint32_t dh = slot == EMPTY ? INF : b.val[slot];
+                    uint32_t dh;
+                    if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &dh))) {
+                        const uint32_t slot = ht_find(b.key, WB_TBITS, e2.x);
+                        dh = slot == EMPTY ? INF : b.val[slot];
+                    }
                     keepit = via != INF && via <= dh;
                 }
                 if (MODE == MODE_SCORE && keepit && mk_o) atomicOr(&d.emask[sb + c0 + o], 1ull << kj);
@@ -984,6 +1130,41 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             c_kept += l_kept;
             c_new += l_new;
         }
+        // Phase 3 (memoised distances): the targets this search found new
+        // get their labels (INF when none), now that all of the source's
+        // decisions are made. The next source's table reset waits for the
+        // barrier at the top of the loop.
+        if constexpr (XM) {
+            if (bound != 0) {
+                bool full = false;
+                for (uint32_t c0 = warp * 32; c0 < sd; c0 += nwarps * 32) {
+                    const uint32_t j = c0 + lane;
+                    const bool valid = j < sd;
+                    const uint2 e = valid ? d.out_adj[sb + j] : make_uint2(0, 0);
+                    const bool mid = valid && id_ok(d, e.x) && is_middle<MODE>(d, e.x, r);
+                    uint32_t cnt = mid ? d.out_deg[e.x] : 0;
+                    const uint64_t ub = mid ? d.out_beg[e.x] : 0;
+                    if (mid && !out_list_ok(d, ub, cnt)) cnt = 0;
+                    const uint32_t incl = warp_incl_scan(cnt);
+                    const uint32_t total = __shfl_sync(FULL, incl, 31);
+                    const uint32_t excl = incl - cnt;
+                    for (uint32_t base = 0; base < total; base += 32) {
+                        const uint32_t idx = base + lane;
+                        const uint32_t o = warp_owner(excl, idx);
+                        const uint64_t ub_o = __shfl_sync(FULL, ub, o);
+                        const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                        if (idx >= total) continue;
+                        const uint2 e2 = d.out_adj[ub_o + (idx - ex_o)];
+                        if (e2.x == s) continue;
+                        const uint32_t slot = ht_find(b.key, WB_TBITS, e2.x);
+                        const int put = dmap_put(a.dm, dmap_key(s, e2.x), slot == EMPTY ? INF : b.val[slot]);
+                        full |= put < 0;
+                        c_dm += put > 0;
+                    }
+                }
+                if (full) atomicOr(&ctl->err, ERR_MAP_FULL);
+            }
+        }
         c_src += (tid == 0);
         c_vert += l_vert;
         c_edge += l_edge;
@@ -998,8 +1179,10 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
     }
     FOLD64(c_src) FOLD64(c_vert) FOLD64(c_edge) FOLD64(c_mid) FOLD64(c_midedge) FOLD64(c_cand)
     FOLD64(c_kept) FOLD64(c_merged) FOLD64(c_ins) FOLD64(c_new)
+    if constexpr (XM) FOLD64(c_dm)
 #undef FOLD64
     if (lane == 0) {
+        if constexpr (XM) atomicAdd(a.dm.count, c_dm);
         atomicAdd(&ctl->wit_block, c_src);
         atomicAdd(&ctl->wit_vertices, c_vert);
         atomicAdd(&ctl->wit_edges, c_edge);
@@ -1017,7 +1200,7 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
 
 // Same search for the sources whose ball overflowed shared memory: one block
 // per slot of dense per-vertex arrays in global memory (no capacity limit).
-template <int MODE>
+template <int MODE, bool XM>
 __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
     const Dev d = a.d;
     Ctl *ctl = d.ctl;
@@ -1069,7 +1252,9 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             uint32_t bmax = 0;
             for (uint32_t jj = 0; jj < ud; ++jj) {
                 const uint2 e2 = d.out_adj[ub + jj];
-                if (e2.x != s) bmax = max(bmax, sat_add(e.y, e2.y));
+                uint32_t known;
+                if (e2.x != s && !(XM && dmap_get(a.dm, dmap_key(s, e2.x), &known)))
+                    bmax = max(bmax, sat_add(e.y, e2.y));
             }
             atomicMax(&s_bound, bmax);
         }
@@ -1149,7 +1334,8 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
                 if (MODE == MODE_PRUNE && memo_all) {
                     keepit = (mword >> jj) & 1ull;
                 } else {
-                    const uint32_t dh = dist[e2.x];
+                    uint32_t dh;
+                    if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &dh))) dh = dist[e2.x];
                     keepit = via != INF && via <= dh;
                 }
                 if (MODE == MODE_SCORE && keepit && mk) rec_mask |= 1ull << jj;
@@ -1204,6 +1390,29 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
                 atomicAdd(&ctl->inserted, s_cnt[2]);
                 atomicAdd(&ctl->newEdges, s_cnt[3]);
                 d.new_out[s] = (uint32_t)s_cnt[3];
+            }
+        }
+        // Phase 3 (memoised distances): the targets this search found new
+        // get their labels (INF when none), before the labels are reset.
+        if constexpr (XM) {
+            if (bound != 0) {
+                unsigned long long l_dm = 0;
+                bool full = false;
+                for (uint32_t j = tid; j < sd; j += blockDim.x) {
+                    const uint2 e = d.out_adj[sb + j];
+                    if (!id_ok(d, e.x) || !is_middle<MODE>(d, e.x, r)) continue;
+                    const uint64_t ub = d.out_beg[e.x];
+                    const uint32_t ud = out_list_ok(d, ub, d.out_deg[e.x]) ? d.out_deg[e.x] : 0;
+                    for (uint32_t jj = 0; jj < ud; ++jj) {
+                        const uint2 e2 = d.out_adj[ub + jj];
+                        if (e2.x == s || !id_ok(d, e2.x)) continue;
+                        const int put = dmap_put(a.dm, dmap_key(s, e2.x), dist[e2.x]);
+                        full |= put < 0;
+                        l_dm += put > 0;
+                    }
+                }
+                if (full) atomicOr(&ctl->err, ERR_MAP_FULL);
+                if (l_dm) atomicAdd(a.dm.count, l_dm);
             }
         }
         __syncthreads();
@@ -1743,6 +1952,12 @@ struct Builder {
     DevBuf<uint32_t> dn32;
     DevBuf<unsigned long long> dn64;
     Dense dense{};
+    // memoised witness distances across rounds (witness_memo_limit > 0)
+    DevBuf<unsigned long long> dm_keys;
+    DevBuf<uint32_t> dm_vals;
+    DMap dm{};
+    uint64_t dm_limit = 0;
+    void dmap_reserve(uint64_t keys);
     int sms = 152;
     EventPool pool;
     std::vector<Span> spans;
@@ -1764,6 +1979,8 @@ struct Builder {
         CH_CUDA_TRY(cudaStreamSynchronize(st));
         if (hctl->err & ERR_INPUT) throw Error{CH_EINVAL, "graph has a malformed offset, id or weight"};
         if (hctl->err & ERR_BOUND) throw Error{CH_ECUDA, "internal index check failed"};
+        if (hctl->err & ERR_MAP_FULL)
+            throw Error{CH_ENOMEM, "the memoised witness-distance map is full (witness_memo_limit)"};
         if (hctl->err) throw Error{CH_ECUDA, "internal capacity error " + std::to_string(hctl->err)};
     }
 
@@ -1773,6 +1990,8 @@ struct Builder {
     void postprocess();
     template <int MODE>
     void witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_max, uint32_t r);
+    template <int MODE, bool XM>
+    void launch_witness(const WArgs &a, int blocks);
 };
 
 #define CTL_OFF(field) offsetof(Ctl, field)
@@ -1897,16 +2116,53 @@ void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_ma
     a.rec_cap = rec.count;
     a.route_all = (uint32_t)blk_blocks * 2;
     a.route_deg = route_deg;
+    a.dm = dm;
     cudaEvent_t e0 = start();
     const int blocks = grid_for((uint64_t)nS_max, WIT_WARPS, sms * 8);
-    k_witness<MODE><<<blocks, WIT_WARPS * 32, 0, st>>>(a);
-    CH_CHECK_LAUNCH();
-    k_witness_block<MODE><<<blk_blocks, WB_THREADS, sizeof(BlkSmem), st>>>(a);
-    CH_CHECK_LAUNCH();
-    k_witness_dense<MODE><<<dense.nslots, 256, 0, st>>>(a, dense);
-    CH_CHECK_LAUNCH();
+    if (dm_limit) launch_witness<MODE, true>(a, blocks);
+    else launch_witness<MODE, false>(a, blocks);
     mark(&h->t_witness_ms, e0, 5);
     h->witness_launches += 3;
+}
+
+// The three tiers of one phase, in order (each takes the sources the one
+// before it could not hold).
+template <int MODE, bool XM>
+void Builder::launch_witness(const WArgs &a, int blocks) {
+    k_witness<MODE, XM><<<blocks, WIT_WARPS * 32, 0, st>>>(a);
+    CH_CHECK_LAUNCH();
+    k_witness_block<MODE, XM><<<blk_blocks, WB_THREADS, sizeof(BlkSmem), st>>>(a);
+    CH_CHECK_LAUNCH();
+    k_witness_dense<MODE, XM><<<dense.nslots, 256, 0, st>>>(a, dense);
+    CH_CHECK_LAUNCH();
+}
+
+// Keeps the memoised-distance map at most half full with `keys` keys plus one
+// round's new keys (at most one per candidate pair of the round, taken as 8
+// per input edge), growing it by a rehash into a map at least twice as large.
+// A round that still overfills it fails with CH_ENOMEM.
+void Builder::dmap_reserve(uint64_t keys) {
+    const uint64_t want = 2 * (keys + 8 * h->m_input + 1024);
+    if (dm_keys.count >= want) return;
+    uint64_t cap = std::max<uint64_t>(1024, dm_keys.count * 2);
+    while (cap < want) cap <<= 1;
+    DevBuf<unsigned long long> nk;
+    DevBuf<uint32_t> nv;
+    nk.alloc(cap);
+    nv.alloc(cap);
+    nk.fill_ff(st);
+    DMap to = dm;
+    to.keys = nk.ptr;
+    to.vals = nv.ptr;
+    to.mask = cap - 1;
+    if (dm_keys.count) {
+        k_dmap_rehash<<<grid_for(dm_keys.count, 256, sms * 8), 256, 0, st>>>(dm, to, ctl.ptr);
+        CH_CHECK_LAUNCH();
+    }
+    CH_CUDA_TRY(cudaStreamSynchronize(st));
+    dm_keys = std::move(nk);
+    dm_vals = std::move(nv);
+    dm = to;
 }
 
 void Builder::emit_core(uint32_t r, uint32_t nVO, uint64_t live_edges) {
@@ -2087,6 +2343,15 @@ void Builder::run_rounds() {
         if (c2.nRec > rec.count) throw Error{CH_ECUDA, "internal: record overflow"};
         log_count += c2.nRec;
         nA = nAnext;
+        // memoised distances are cleared lazily: only after a round that
+        // leaves more keys than the limit; otherwise the map keeps room for
+        // another round's keys
+        if (dm_limit && c2.dm_count > dm_limit) {
+            CH_CUDA_TRY(cudaMemsetAsync(dm_keys.ptr, 0xFF, dm_keys.count * sizeof(unsigned long long), st));
+            CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->dm_count, 0, sizeof(unsigned long long), st));
+        } else if (dm_limit) {
+            dmap_reserve(c2.dm_count);
+        }
     }
     h->n_shortcuts = log_count;
     h->witness_bytes = 0;
@@ -2201,12 +2466,18 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     for (auto *l : {&b.VO, &b.VO2, &b.A, &b.Anext, &b.S, &b.S2, &b.F, &b.ovf, &b.ovf2}) l->alloc(n);
     {
         const int smem = (int)sizeof(BlkSmem);
-        CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_SCORE>,
+        CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_SCORE, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_PRUNE>,
+        CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_PRUNE, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        if (p->witness_memo_limit) {
+            CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_SCORE, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_PRUNE, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        }
         int per_sm = 0;
-        CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_witness_block<MODE_PRUNE>,
+        CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_witness_block<MODE_PRUNE, false>,
                                                                   WB_THREADS, smem));
         b.blk_blocks = b.sms * std::max(1, per_sm);
     }
@@ -2309,8 +2580,14 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     d.inel = b.inel.ptr;
     d.ball = p->witness_ball_limit ? p->witness_ball_limit : 0xFFFFFFFFu;
     // memoised in-round decisions need both phases to decide alike, which a
-    // ball bound (cut levels depend on each phase's own weight bound) breaks
-    d.memo = p->witness_ball_limit == 0;
+    // ball bound (cut levels depend on each phase's own weight bound) breaks;
+    // the memoised distances across rounds replace them
+    d.memo = p->witness_ball_limit == 0 && p->witness_memo_limit == 0;
+    if (p->witness_memo_limit) {
+        b.dm.count = &b.ctl.ptr->dm_count;
+        b.dm_limit = p->witness_memo_limit;
+        b.dmap_reserve(0);
+    }
     b.emask.alloc(b.out_adj.count);
     d.emask = b.emask.ptr;
     d.kround = b.kround.ptr;
