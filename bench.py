@@ -119,6 +119,9 @@ def parse():
     ap.add_argument("--witness-ball", type=int, default=None,
                     help="witness ball bound: stop a search after the first hop level that "
                          "reaches more than this many vertices (default: none)")
+    ap.add_argument("--memo", type=int, default=None,
+                    help="memoise witness distances across rounds, clearing the map after a "
+                         "round that leaves more pairs than this (default: off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
@@ -207,7 +210,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_sample_build(workload: str, hop_limit: int, cmax, ball=None, threads: bool = False):
+def cpu_sample_build(workload: str, hop_limit: int, cmax, ball=None, threads: bool = False,
+                     memo=None):
     """Oracle build on a sample graph of the same family, scaled linearly
     (by vertex count) to the full workload. Returns (scaled_s, raw_s,
     threads used, sample vertices). threads: the -DORACLE_THREADS build,
@@ -216,7 +220,7 @@ def cpu_sample_build(workload: str, hop_limit: int, cmax, ball=None, threads: bo
     g = make_graph(workload, sample=True)
     t0 = time.perf_counter()
     O.build_ch(g, hop_limit, cmax=O.CMAX_ALL if cmax is None else cmax,
-               ball=O.CMAX_ALL if ball is None else ball, threads=threads)
+               ball=O.CMAX_ALL if ball is None else ball, threads=threads, memo=memo or 0)
     raw = time.perf_counter() - t0
     return raw * (WORKLOADS[workload][0] / g.n), raw, (os.cpu_count() or 1) if threads else 1, g.n
 
@@ -233,11 +237,11 @@ def run_reference(args):
     g = make_graph(args.workload, sample=True)
     sample_n = g.n
     for _ in range(args.warmup):
-        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball)
+        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball, memo=args.memo or 0)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball)
+        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball, memo=args.memo or 0)
         times.append(time.perf_counter() - t0)
     scale = n / sample_n
     value = statistics.mean(times) * scale
@@ -479,7 +483,7 @@ def main():
     def step():
         h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
                         hop_limit=args.hop_limit, stream=stream, max_candidates_per_vertex=args.cmax,
-                        witness_ball_limit=args.witness_ball)
+                        witness_ball_limit=args.witness_ball, witness_memo_limit=args.memo)
         if qcfg is not None:
             h.set_query_config(*qcfg)
         if not args.build_only:
@@ -514,7 +518,8 @@ def main():
             e0.record(stream)
             h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
                             hop_limit=args.hop_limit, stream=stream,
-                            max_candidates_per_vertex=args.cmax, witness_ball_limit=args.witness_ball)
+                            max_candidates_per_vertex=args.cmax, witness_ball_limit=args.witness_ball,
+                            witness_memo_limit=args.memo)
             if qcfg is not None:
                 h.set_query_config(*qcfg)
             e1.record(stream)
@@ -618,7 +623,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             hh = ch.CH.build(g, hop_limit=args.hop_limit, max_candidates_per_vertex=args.cmax,
-                             witness_ball_limit=args.witness_ball)
+                             witness_ball_limit=args.witness_ball, witness_memo_limit=args.memo)
             if qcfg is not None:
                 hh.set_query_config(*qcfg)
             t1 = time.perf_counter()
@@ -635,14 +640,15 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         scaled, raw, cores, sn = cpu_sample_build(args.workload, args.hop_limit, args.cmax,
-                                                  args.witness_ball)
+                                                  args.witness_ball, memo=args.memo)
         cpu = {"value": scaled, "unit": "s", "cores": cores, "kind": "oracle",
                "sample": f"oracle build of a {sn}-vertex graph of the same family "
                          f"({raw:.2f} s, one thread), scaled linearly by vertex count to {n}"}
         # the same oracle with its witness searches on every host thread
         # (identical result; the rest of each round stays sequential)
         mt_scaled, mt_raw, mt_cores, _ = cpu_sample_build(args.workload, args.hop_limit, args.cmax,
-                                                          args.witness_ball, threads=True)
+                                                          args.witness_ball, threads=True,
+                                                          memo=args.memo)
         cpu["threaded"] = {"value": mt_scaled, "unit": "s", "cores": mt_cores,
                            "sample": f"same sample, -DORACLE_THREADS build ({mt_raw:.2f} s)"}
 
@@ -654,6 +660,7 @@ def main():
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": args.workload, "vertices": n, "edges": int(g.m),
                        "cmax": args.cmax, "witness_ball": args.witness_ball,
+                       "witness_memo": args.memo,
                        "core_vertices": stats["core_vertices"],
                        "queries": nq, "hop_limit": args.hop_limit,
                        "parallelism": f"replicas{world}",
