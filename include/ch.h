@@ -124,7 +124,14 @@ typedef struct {
  *              least twice (its pairs + 8 per input edge) slots, growing
  *              between rounds, and a round that overfills it fails with
  *              CH_ENOMEM.
- *              0 = off (the default). */
+ *              0 = off (the default).
+ *   witness_level_work  W, a bound on a hop-limited witness search's work
+ *              (not in the paper; for power-law graphs): a hop level from
+ *              the second on whose frontier (the vertices whose label
+ *              dropped in the level before) has more than W out-edges in
+ *              total is not run, and the labels of the level before are the
+ *              result. Still upper bounds on real walks, so distances stay
+ *              exact. 0 = no bound (the default). */
 typedef struct {
     uint32_t hop_limit;
     uint32_t priority;
@@ -137,6 +144,8 @@ typedef struct {
     uint32_t witness_route_deg;
     uint32_t witness_ball_limit;
     uint32_t witness_memo_limit;
+    uint32_t witness_level_work;
+    uint32_t reserved;  /* 0 */
 } ch_params_t;
 
 /* Training parameters of ch_mlp_train (Adam, mean squared error). */

@@ -57,6 +57,12 @@ constexpr uint32_t ERR_MAP_FULL = 16u;  // the memoised-distance map has no free
 constexpr int MODE_SCORE = 0;
 constexpr int MODE_PRUNE = 1;
 
+// Optional witness-search features, instantiated separately so that the
+// plain kernels stay as they are: memoised distances across rounds, and the
+// bound on a hop level's frontier out-edges.
+constexpr int F_XM = 1;
+constexpr int F_LW = 2;
+
 // Shared-memory search state of one warp.
 constexpr int WIT_WARPS = 4;       // warps per block
 constexpr int WIT_TBITS = 8;       // hash table of 2^8 vertices
@@ -210,6 +216,9 @@ struct WArgs {
     // warp each, so per-source latency decides), and any source whose
     // middles' out-degrees sum above route_deg (its ball would overflow).
     uint32_t route_all, route_deg;
+    // F_LW: a hop level from the second on whose frontier has more
+    // out-edges than this is not run
+    unsigned long long level_work;
 };
 
 struct Dense {
@@ -461,8 +470,9 @@ __device__ __forceinline__ uint32_t ht_find(const uint32_t *keys, int bits, uint
     return EMPTY;
 }
 
-template <int MODE, bool XM>
+template <int MODE, int FEAT>
 __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
+    constexpr bool XM = (FEAT & F_XM) != 0, LW = (FEAT & F_LW) != 0;
     __shared__ WarpSmem smem[WIT_WARPS];
     WarpSmem &w = smem[threadIdx.x >> 5];
     const uint32_t lane = lane_id();
@@ -579,6 +589,14 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         bool overflowed = false;
         uint32_t cur = 0;
         for (uint32_t lvl = 1; lvl <= d.H && nfront > 0 && nkeys <= d.ball; ++lvl) {
+            if constexpr (LW) {
+                if (lvl >= 2) {
+                    unsigned long long wk = 0;
+                    for (uint32_t f = lane; f < nfront; f += 32) wk += d.out_deg[w.key[w.front[cur][f].x]];
+                    for (int o = 16; o > 0; o >>= 1) wk += __shfl_xor_sync(FULL, wk, o);
+                    if (wk > a.level_work) break;
+                }
+            }
             const uint32_t nxt = cur ^ 1u;
             if (lane == 0) w.nf[nxt] = 0;
             __syncwarp();
@@ -861,10 +879,12 @@ struct BlkSmem {
     uint32_t nf[2];
     uint32_t item, ovf, bound, nnew, nkeys, memo_ok;
     uint32_t any;  // memoised-distance mode: the source has a candidate
+    unsigned long long lwork;  // F_LW: out-edges of the next level's frontier
 };
 
-template <int MODE, bool XM>
+template <int MODE, int FEAT>
 __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
+    constexpr bool XM = (FEAT & F_XM) != 0, LW = (FEAT & F_LW) != 0;
     extern __shared__ __align__(16) unsigned char wb_raw[];
     BlkSmem &b = *reinterpret_cast<BlkSmem *>(wb_raw);
     const Dev d = a.d;
@@ -967,10 +987,17 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             const uint32_t nfront = b.nf[cur];
             const uint32_t ovf = b.ovf;
             const uint32_t nkeys = b.nkeys;
+            unsigned long long lwork = 0;
+            if constexpr (LW) lwork = b.lwork;
             __syncthreads();
             if (ovf || nfront == 0 || nkeys > d.ball) break;
+            if constexpr (LW)
+                if (lvl >= 2 && lwork > a.level_work) break;
             const uint32_t nxt = cur ^ 1u;
-            if (tid == 0) b.nf[nxt] = 0;
+            if (tid == 0) {
+                b.nf[nxt] = 0;
+                if constexpr (LW) b.lwork = 0;
+            }
             __syncthreads();
             for (uint32_t f0 = warp * 32; f0 < nfront; f0 += nwarps * 32) {
                 const uint32_t fi = f0 + lane;
@@ -1015,7 +1042,13 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             }
             __syncthreads();
             const uint32_t nn = min(b.nf[nxt], (uint32_t)WB_FC);
-            for (uint32_t p = tid; p < nn; p += blockDim.x) b.front[nxt][p].y = b.val[b.front[nxt][p].x];
+            unsigned long long lw = 0;
+            for (uint32_t p = tid; p < nn; p += blockDim.x) {
+                b.front[nxt][p].y = b.val[b.front[nxt][p].x];
+                if constexpr (LW) lw += d.out_deg[b.key[b.front[nxt][p].x]];
+            }
+            if constexpr (LW)
+                if (lw) atomicAdd(&b.lwork, lw);
             cur = nxt;
         }
         __syncthreads();
@@ -1200,8 +1233,9 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
 
 // Same search for the sources whose ball overflowed shared memory: one block
 // per slot of dense per-vertex arrays in global memory (no capacity limit).
-template <int MODE, bool XM>
+template <int MODE, int FEAT>
 __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
+    constexpr bool XM = (FEAT & F_XM) != 0, LW = (FEAT & F_LW) != 0;
     const Dev d = a.d;
     Ctl *ctl = d.ctl;
     const uint32_t n = d.n;
@@ -1212,6 +1246,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
     uint32_t *mt = dn.mt + base, *direct = dn.direct + base;
     unsigned long long *merge = dn.merge + base;
     __shared__ uint32_t s_item, s_bound, s_nt, s_nm, s_nf[2], s_memo;
+    __shared__ unsigned long long s_lw;  // F_LW: out-edges of the next level's frontier
     __shared__ unsigned long long s_cnt[5];
     const uint32_t tid = threadIdx.x;
     const uint32_t nOvf = ctl->nOvf2;
@@ -1266,7 +1301,10 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
         for (uint32_t lvl = 1; lvl <= d.H && bound > 0 && !memo_all; ++lvl) {
             const uint32_t nf = s_nf[(lvl - 1) & 1];
             __syncthreads();
-            if (tid == 0) s_nf[lvl & 1] = 0;
+            if (tid == 0) {
+                s_nf[lvl & 1] = 0;
+                if constexpr (LW) s_lw = 0;
+            }
             __syncthreads();
             // each warp takes 32 frontier entries and spreads their out-edges
             // over its lanes
@@ -1298,7 +1336,13 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             }
             __syncthreads();
             const uint32_t nn = s_nf[lvl & 1];
-            for (uint32_t p = tid; p < nn; p += blockDim.x) nxd[p] = dist[nx[p]];
+            unsigned long long lw = 0;
+            for (uint32_t p = tid; p < nn; p += blockDim.x) {
+                nxd[p] = dist[nx[p]];
+                if constexpr (LW) lw += d.out_deg[nx[p]];
+            }
+            if constexpr (LW)
+                if (lw) atomicAdd(&s_lw, lw);
             __syncthreads();
             uint32_t *t1 = cur, *t2 = curd;
             cur = nx;
@@ -1306,6 +1350,9 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             nx = t1;
             nxd = t2;
             if (nn == 0 || s_nt > d.ball) break;  // s_nt: vertices holding a label
+            // the next level (the second or later) would expand too much
+            if constexpr (LW)
+                if (s_lw > a.level_work) break;
         }
         // the source's direct edges, for the existing-edge test
         if (MODE == MODE_PRUNE) {
@@ -1990,8 +2037,9 @@ struct Builder {
     void postprocess();
     template <int MODE>
     void witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_max, uint32_t r);
-    template <int MODE, bool XM>
+    template <int MODE, int FEAT>
     void launch_witness(const WArgs &a, int blocks);
+    unsigned long long level_work = ~0ull;  // F_LW bound; all ones = off
 };
 
 #define CTL_OFF(field) offsetof(Ctl, field)
@@ -2117,23 +2165,29 @@ void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_ma
     a.route_all = (uint32_t)blk_blocks * 2;
     a.route_deg = route_deg;
     a.dm = dm;
+    a.level_work = level_work;
     cudaEvent_t e0 = start();
     const int blocks = grid_for((uint64_t)nS_max, WIT_WARPS, sms * 8);
-    if (dm_limit) launch_witness<MODE, true>(a, blocks);
-    else launch_witness<MODE, false>(a, blocks);
+    const int feat = (dm_limit ? F_XM : 0) | (level_work != ~0ull ? F_LW : 0);
+    switch (feat) {
+        case 0: launch_witness<MODE, 0>(a, blocks); break;
+        case F_XM: launch_witness<MODE, F_XM>(a, blocks); break;
+        case F_LW: launch_witness<MODE, F_LW>(a, blocks); break;
+        default: launch_witness<MODE, F_XM | F_LW>(a, blocks); break;
+    }
     mark(&h->t_witness_ms, e0, 5);
     h->witness_launches += 3;
 }
 
 // The three tiers of one phase, in order (each takes the sources the one
 // before it could not hold).
-template <int MODE, bool XM>
+template <int MODE, int FEAT>
 void Builder::launch_witness(const WArgs &a, int blocks) {
-    k_witness<MODE, XM><<<blocks, WIT_WARPS * 32, 0, st>>>(a);
+    k_witness<MODE, FEAT><<<blocks, WIT_WARPS * 32, 0, st>>>(a);
     CH_CHECK_LAUNCH();
-    k_witness_block<MODE, XM><<<blk_blocks, WB_THREADS, sizeof(BlkSmem), st>>>(a);
+    k_witness_block<MODE, FEAT><<<blk_blocks, WB_THREADS, sizeof(BlkSmem), st>>>(a);
     CH_CHECK_LAUNCH();
-    k_witness_dense<MODE, XM><<<dense.nslots, 256, 0, st>>>(a, dense);
+    k_witness_dense<MODE, FEAT><<<dense.nslots, 256, 0, st>>>(a, dense);
     CH_CHECK_LAUNCH();
 }
 
@@ -2466,18 +2520,21 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     for (auto *l : {&b.VO, &b.VO2, &b.A, &b.Anext, &b.S, &b.S2, &b.F, &b.ovf, &b.ovf2}) l->alloc(n);
     {
         const int smem = (int)sizeof(BlkSmem);
-        CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_SCORE, false>,
+        CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_SCORE, 0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_PRUNE, false>,
+        CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_PRUNE, 0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        if (p->witness_memo_limit) {
-            CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_SCORE, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_PRUNE, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        }
+        const int feat = (p->witness_memo_limit ? F_XM : 0) | (p->witness_level_work ? F_LW : 0);
+        auto set_smem = [&](auto score_kernel, auto prune_kernel) {
+            CH_CUDA_TRY(cudaFuncSetAttribute(score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            CH_CUDA_TRY(cudaFuncSetAttribute(prune_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        };
+        if (feat == F_XM) set_smem(k_witness_block<MODE_SCORE, F_XM>, k_witness_block<MODE_PRUNE, F_XM>);
+        if (feat == F_LW) set_smem(k_witness_block<MODE_SCORE, F_LW>, k_witness_block<MODE_PRUNE, F_LW>);
+        if (feat == (F_XM | F_LW))
+            set_smem(k_witness_block<MODE_SCORE, F_XM | F_LW>, k_witness_block<MODE_PRUNE, F_XM | F_LW>);
         int per_sm = 0;
-        CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_witness_block<MODE_PRUNE, false>,
+        CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_witness_block<MODE_PRUNE, 0>,
                                                                   WB_THREADS, smem));
         b.blk_blocks = b.sms * std::max(1, per_sm);
     }
@@ -2583,6 +2640,7 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     // ball bound (cut levels depend on each phase's own weight bound) breaks;
     // the memoised distances across rounds replace them
     d.memo = p->witness_ball_limit == 0 && p->witness_memo_limit == 0;
+    if (p->witness_level_work) b.level_work = p->witness_level_work;
     if (p->witness_memo_limit) {
         b.dm.count = &b.ctl.ptr->dm_count;
         b.dm_limit = p->witness_memo_limit;

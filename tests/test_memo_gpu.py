@@ -1,8 +1,9 @@
-"""Memoised witness distances across rounds on the GPU (witness_memo_limit)
-against the oracle run with the same limit: levels, scores, ranks, shortcut
-logs, E_up, E_down and every round's counters bit for bit, and exact
-queries. The oracle's memo mode is pinned in test_trace_pins.py (its own map,
-bound and clearing rule) and test_witness_modes.py."""
+"""Memoised witness distances across rounds (witness_memo_limit) and the
+level-work bound (witness_level_work) on the GPU, against the oracle run with
+the same settings: levels, scores, ranks, shortcut logs, E_up, E_down and
+every round's counters bit for bit, and exact queries. Both oracle modes are
+pinned in test_trace_pins.py (the test's own map, bound, clearing rule,
+frontier and work sums) and test_witness_modes.py."""
 import numpy as np
 import pytest
 
@@ -12,7 +13,7 @@ from tests.graphs import all_pairs_truth, small_families
 from tests.test_gpu_parity import assert_same_hierarchy
 
 pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="the memoised-distance kernels are written but have not yet run on a GPU")]
+              pytest.mark.skip(reason="the memo and level-work kernels are written but have not yet run on a GPU")]
 
 
 def _ch():
@@ -59,3 +60,33 @@ def test_dense_graph_tiers_and_rmat_core():
         assert_same_hierarchy(gch, och)
         s, t = I.random_pairs(g.n, 3000, seed=153)
         assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))
+
+
+# ---------------------------------------------------------------------------
+# Level-work bound (witness_level_work), alone and with memoised distances
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("H,lw,limit,ball", [(3, 4, None, None), (5, 12, None, None),
+                                             (5, 40, 1 << 30, None), (4, 12, None, 5),
+                                             (5, 20, 30, 6)])
+@pytest.mark.parametrize("name,g", FAMILIES, ids=[n for n, _ in FAMILIES])
+def test_level_work_small_families(name, g, H, lw, limit, ball):
+    och = O.build_ch(g, H, ball=O.CMAX_ALL if ball is None else ball, memo=limit or 0,
+                     level_work=lw)
+    gch = _ch().CH.build(g, hop_limit=H, witness_ball_limit=ball, witness_memo_limit=limit,
+                         witness_level_work=lw)
+    assert_same_hierarchy(gch, och)
+    s, t = np.meshgrid(np.arange(g.n), np.arange(g.n), indexing="ij")
+    d = gch.query(s.ravel().astype(np.uint32), t.ravel().astype(np.uint32))
+    assert np.array_equal(d.astype(np.uint64).reshape(g.n, g.n), all_pairs_truth(g))
+
+
+@pytest.mark.parametrize("lw,limit", [(1024, None), (256, 1 << 30)])
+def test_level_work_on_rmat_with_a_core(lw, limit):
+    g = I.rmat_graph(scale=12, nsamples=1 << 16, wmax=1000, seed=154)
+    och = O.build_ch(g, 2, cmax=256, ball=256, memo=limit or 0, level_work=lw)
+    gch = _ch().CH.build(g, hop_limit=2, max_candidates_per_vertex=256, witness_ball_limit=256,
+                         witness_memo_limit=limit, witness_level_work=lw)
+    assert_same_hierarchy(gch, och)
+    s, t = I.random_pairs(g.n, 3000, seed=155)
+    assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))
