@@ -122,6 +122,9 @@ def parse():
     ap.add_argument("--memo", type=int, default=None,
                     help="memoise witness distances across rounds, clearing the map after a "
                          "round that leaves more pairs than this (default: off)")
+    ap.add_argument("--level-work", type=int, default=None,
+                    help="skip a witness hop level (from the second on) whose frontier has more "
+                         "out-edges than this (default: off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
@@ -211,7 +214,7 @@ class ClockSampler:
 
 
 def cpu_sample_build(workload: str, hop_limit: int, cmax, ball=None, threads: bool = False,
-                     memo=None):
+                     memo=None, level_work=None):
     """Oracle build on a sample graph of the same family, scaled linearly
     (by vertex count) to the full workload. Returns (scaled_s, raw_s,
     threads used, sample vertices). threads: the -DORACLE_THREADS build,
@@ -220,7 +223,8 @@ def cpu_sample_build(workload: str, hop_limit: int, cmax, ball=None, threads: bo
     g = make_graph(workload, sample=True)
     t0 = time.perf_counter()
     O.build_ch(g, hop_limit, cmax=O.CMAX_ALL if cmax is None else cmax,
-               ball=O.CMAX_ALL if ball is None else ball, threads=threads, memo=memo or 0)
+               ball=O.CMAX_ALL if ball is None else ball, threads=threads, memo=memo or 0,
+               level_work=O.CMAX_ALL if level_work is None else level_work)
     raw = time.perf_counter() - t0
     return raw * (WORKLOADS[workload][0] / g.n), raw, (os.cpu_count() or 1) if threads else 1, g.n
 
@@ -237,11 +241,13 @@ def run_reference(args):
     g = make_graph(args.workload, sample=True)
     sample_n = g.n
     for _ in range(args.warmup):
-        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball, memo=args.memo or 0)
+        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball, memo=args.memo or 0,
+                   level_work=O.CMAX_ALL if args.level_work is None else args.level_work)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball, memo=args.memo or 0)
+        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball, memo=args.memo or 0,
+                   level_work=O.CMAX_ALL if args.level_work is None else args.level_work)
         times.append(time.perf_counter() - t0)
     scale = n / sample_n
     value = statistics.mean(times) * scale
@@ -483,7 +489,8 @@ def main():
     def step():
         h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
                         hop_limit=args.hop_limit, stream=stream, max_candidates_per_vertex=args.cmax,
-                        witness_ball_limit=args.witness_ball, witness_memo_limit=args.memo)
+                        witness_ball_limit=args.witness_ball, witness_memo_limit=args.memo,
+                        witness_level_work=args.level_work)
         if qcfg is not None:
             h.set_query_config(*qcfg)
         if not args.build_only:
@@ -519,7 +526,7 @@ def main():
             h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
                             hop_limit=args.hop_limit, stream=stream,
                             max_candidates_per_vertex=args.cmax, witness_ball_limit=args.witness_ball,
-                            witness_memo_limit=args.memo)
+                            witness_memo_limit=args.memo, witness_level_work=args.level_work)
             if qcfg is not None:
                 h.set_query_config(*qcfg)
             e1.record(stream)
@@ -623,7 +630,8 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             hh = ch.CH.build(g, hop_limit=args.hop_limit, max_candidates_per_vertex=args.cmax,
-                             witness_ball_limit=args.witness_ball, witness_memo_limit=args.memo)
+                             witness_ball_limit=args.witness_ball, witness_memo_limit=args.memo,
+                        witness_level_work=args.level_work)
             if qcfg is not None:
                 hh.set_query_config(*qcfg)
             t1 = time.perf_counter()
@@ -640,7 +648,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         scaled, raw, cores, sn = cpu_sample_build(args.workload, args.hop_limit, args.cmax,
-                                                  args.witness_ball, memo=args.memo)
+                                                  args.witness_ball, memo=args.memo,
+                                                  level_work=args.level_work)
         cpu = {"value": scaled, "unit": "s", "cores": cores, "kind": "oracle",
                "sample": f"oracle build of a {sn}-vertex graph of the same family "
                          f"({raw:.2f} s, one thread), scaled linearly by vertex count to {n}"}
@@ -648,7 +657,7 @@ def main():
         # (identical result; the rest of each round stays sequential)
         mt_scaled, mt_raw, mt_cores, _ = cpu_sample_build(args.workload, args.hop_limit, args.cmax,
                                                           args.witness_ball, threads=True,
-                                                          memo=args.memo)
+                                                          memo=args.memo, level_work=args.level_work)
         cpu["threaded"] = {"value": mt_scaled, "unit": "s", "cores": mt_cores,
                            "sample": f"same sample, -DORACLE_THREADS build ({mt_raw:.2f} s)"}
 
@@ -660,7 +669,7 @@ def main():
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": args.workload, "vertices": n, "edges": int(g.m),
                        "cmax": args.cmax, "witness_ball": args.witness_ball,
-                       "witness_memo": args.memo,
+                       "witness_memo": args.memo, "witness_level_work": args.level_work,
                        "core_vertices": stats["core_vertices"],
                        "queries": nq, "hop_limit": args.hop_limit,
                        "parallelism": f"replicas{world}",
