@@ -631,7 +631,7 @@ def main():
             t0 = time.perf_counter()
             hh = ch.CH.build(g, hop_limit=args.hop_limit, max_candidates_per_vertex=args.cmax,
                              witness_ball_limit=args.witness_ball, witness_memo_limit=args.memo,
-                        witness_level_work=args.level_work)
+                             witness_level_work=args.level_work)
             if qcfg is not None:
                 hh.set_query_config(*qcfg)
             t1 = time.perf_counter()
