@@ -131,7 +131,15 @@ typedef struct {
  *              dropped in the level before) has more than W out-edges in
  *              total is not run, and the labels of the level before are the
  *              result. Still upper bounds on real walks, so distances stay
- *              exact. 0 = no bound (the default). */
+ *              exact. 0 = no bound (the default).
+ *   witness_prune  nonzero: after each round's rescoring searches, every
+ *              overlay edge (s, v) heavier than the distance recorded for a
+ *              pair (s, v) of those searches is deleted (Alg. 3's last step),
+ *              and the scores are taken on the pruned overlay. The searches'
+ *              label bound then also covers the direct edges (s, v) to their
+ *              new targets (without a ball bound). A pruned edge lies on no
+ *              shortest path, so distances stay exact. Uses the distance map
+ *              of witness_memo_limit (held for one phase when that is 0). */
 typedef struct {
     uint32_t hop_limit;
     uint32_t priority;
@@ -145,7 +153,7 @@ typedef struct {
     uint32_t witness_ball_limit;
     uint32_t witness_memo_limit;
     uint32_t witness_level_work;
-    uint32_t reserved;  /* 0 */
+    uint32_t witness_prune;
 } ch_params_t;
 
 /* Training parameters of ch_mlp_train (Adam, mean squared error). */

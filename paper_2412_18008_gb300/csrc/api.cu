@@ -96,7 +96,7 @@ void ch_default_params(ch_params_t *p) {
     p->witness_ball_limit = 0;
     p->witness_memo_limit = 0;
     p->witness_level_work = 0;
-    p->reserved = 0;
+    p->witness_prune = 0;
 }
 
 int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out) {

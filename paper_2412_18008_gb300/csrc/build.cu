@@ -62,6 +62,20 @@ constexpr int MODE_PRUNE = 1;
 // bound on a hop level's frontier out-edges.
 constexpr int F_XM = 1;
 constexpr int F_LW = 2;
+// Pruning of overlay edges heavier than their pair's witness distance: the
+// searches' label bound also covers the direct edges (s, v) to new targets
+// (without a ball bound), so the recorded value decides the deletion. Needs
+// F_XM (the recorded values live in the memoised-distance map).
+constexpr int F_PR = 4;
+
+// Weight of the overlay edge (s, v) from s's out-list, INF if none.
+__device__ __forceinline__ uint32_t direct_weight(const uint2 *out_adj, uint64_t sb, uint32_t sd, uint32_t v) {
+    for (uint32_t j = 0; j < sd; ++j) {
+        const uint2 e = out_adj[sb + j];
+        if (e.x == v) return e.y;
+    }
+    return INF;
+}
 
 // Shared-memory search state of one warp.
 constexpr int WIT_WARPS = 4;       // warps per block
@@ -81,6 +95,8 @@ struct Ctl {
         wit_midedges, wit_block;
     unsigned long long trace_valid;  // trace rows of eligible rescorings
     unsigned long long dm_count;     // keys in the memoised-distance map since its last clear
+    unsigned long long pruned;       // overlay edges pruned this round
+    uint32_t nDirty, pad2;           // vertices whose lists hold pruned entries
 };
 
 struct Dev {
@@ -472,7 +488,7 @@ __device__ __forceinline__ uint32_t ht_find(const uint32_t *keys, int bits, uint
 
 template <int MODE, int FEAT>
 __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
-    constexpr bool XM = (FEAT & F_XM) != 0, LW = (FEAT & F_LW) != 0;
+    constexpr bool XM = (FEAT & F_XM) != 0, LW = (FEAT & F_LW) != 0, PR = (FEAT & F_PR) != 0;
     __shared__ WarpSmem smem[WIT_WARPS];
     WarpSmem &w = smem[threadIdx.x >> 5];
     const uint32_t lane = lane_id();
@@ -519,6 +535,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         uint32_t bound = 0;
         bool memo_all = MODE == MODE_PRUNE && d.memo;
         bool any = false;  // XM: a candidate exists (the bound covers new targets only)
+        uint32_t direct = 0;  // PR: heaviest overlay edge (s, v) to a new target v
         for (uint32_t c0 = 0; c0 < sd; c0 += 32) {
             const uint32_t j = c0 + lane;
             const bool valid = j < sd;
@@ -544,13 +561,23 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                     if (e2.x != s) {
                         uint32_t known;
                         if constexpr (XM) any = true;
-                        if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &known)))
+                        if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &known))) {
                             bound = max(bound, sat_add(w1, e2.y));
+                            if constexpr (PR) {
+                                const uint32_t dw = direct_weight(d.out_adj, sb, sd, e2.x);
+                                if (dw != INF) direct = max(direct, dw);
+                            }
+                        }
                     }
                 }
             }
         }
         bound = warp_max(bound);
+        // the search's label bound (PR without a ball bound: the direct
+        // edges to new targets too)
+        uint32_t sbound = bound;
+        if constexpr (PR)
+            if (d.ball == 0xFFFFFFFFu) sbound = max(bound, warp_max(direct));
         if (warp_sum((uint32_t)l_midedge) > a.route_deg) {
             if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
             continue;
@@ -624,7 +651,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                     if (idx < total) {
                         const uint2 e = d.out_adj[xb_o + (idx - ex_o)];
                         const uint32_t nd = sat_add(dx_o, e.y);
-                        if (nd < bound && id_ok(d, e.x)) {
+                        if (nd < sbound && id_ok(d, e.x)) {
                             bool created = false;
                             const uint32_t slot = ht_insert(w.key, WIT_TBITS, e.x, &created);
                             l_created += created;
@@ -880,11 +907,12 @@ struct BlkSmem {
     uint32_t item, ovf, bound, nnew, nkeys, memo_ok;
     uint32_t any;  // memoised-distance mode: the source has a candidate
     unsigned long long lwork;  // F_LW: out-edges of the next level's frontier
+    uint32_t direct;           // F_PR: heaviest overlay edge (s, v) to a new target v
 };
 
 template <int MODE, int FEAT>
 __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
-    constexpr bool XM = (FEAT & F_XM) != 0, LW = (FEAT & F_LW) != 0;
+    constexpr bool XM = (FEAT & F_XM) != 0, LW = (FEAT & F_LW) != 0, PR = (FEAT & F_PR) != 0;
     extern __shared__ __align__(16) unsigned char wb_raw[];
     BlkSmem &b = *reinterpret_cast<BlkSmem *>(wb_raw);
     const Dev d = a.d;
@@ -934,6 +962,7 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             b.nnew = 0;
             b.memo_ok = MODE == MODE_PRUNE && d.memo;
             if constexpr (XM) b.any = 0;
+            if constexpr (PR) b.direct = 0;
         }
         __syncthreads();
         // Phase 0: heaviest candidate weight of the source, and whether every
@@ -952,14 +981,22 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
                 if (e2.x != s) {
                     uint32_t known;
                     if constexpr (XM) b.any = 1;
-                    if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &known)))
+                    if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &known))) {
                         lb = max(lb, sat_add(e.y, e2.y));
+                        if constexpr (PR) {
+                            const uint32_t dw = direct_weight(d.out_adj, sb, sd, e2.x);
+                            if (dw != INF) atomicMax(&b.direct, dw);
+                        }
+                    }
                 }
             }
         }
         if (lb) atomicMax(&b.bound, lb);
         __syncthreads();
         const uint32_t bound = b.bound;
+        uint32_t sbound = bound;  // the search's label bound
+        if constexpr (PR)
+            if (d.ball == 0xFFFFFFFFu) sbound = max(bound, b.direct);
         const bool memo_all = b.memo_ok != 0;
         bool no_cand;
         if constexpr (XM) no_cand = b.any == 0;
@@ -1024,7 +1061,7 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
                     if (idx >= total) continue;
                     const uint2 e = d.out_adj[xb_o + (idx - ex_o)];
                     const uint32_t nd = sat_add(dx_o, e.y);
-                    if (nd >= bound || !id_ok(d, e.x)) continue;
+                    if (nd >= sbound || !id_ok(d, e.x)) continue;
                     bool created = false;
                     const uint32_t slot = ht_insert(b.key, WB_TBITS, e.x, &created);
                     if (created) atomicAdd(&b.nkeys, 1u);
@@ -1235,7 +1272,7 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
 // per slot of dense per-vertex arrays in global memory (no capacity limit).
 template <int MODE, int FEAT>
 __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
-    constexpr bool XM = (FEAT & F_XM) != 0, LW = (FEAT & F_LW) != 0;
+    constexpr bool XM = (FEAT & F_XM) != 0, LW = (FEAT & F_LW) != 0, PR = (FEAT & F_PR) != 0;
     const Dev d = a.d;
     Ctl *ctl = d.ctl;
     const uint32_t n = d.n;
@@ -1247,6 +1284,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
     unsigned long long *merge = dn.merge + base;
     __shared__ uint32_t s_item, s_bound, s_nt, s_nm, s_nf[2], s_memo;
     __shared__ unsigned long long s_lw;  // F_LW: out-edges of the next level's frontier
+    __shared__ uint32_t s_direct;        // F_PR: heaviest overlay edge (s, v) to a new target v
     __shared__ unsigned long long s_cnt[5];
     const uint32_t tid = threadIdx.x;
     const uint32_t nOvf = ctl->nOvf2;
@@ -1276,6 +1314,14 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             fa[0] = s;
             fda[0] = 0;
             atomicAdd(&ctl->wit_fallback, 1ull);
+            if constexpr (PR) s_direct = 0;
+        }
+        if constexpr (PR) {
+            // the source's direct edges, for the widened label bound
+            for (uint32_t j = tid; j < sd; j += blockDim.x) {
+                const uint2 e = d.out_adj[sb + j];
+                if (e.x < n) direct[e.x] = e.y;
+            }
         }
         __syncthreads();
         for (uint32_t j = tid; j < sd; j += blockDim.x) {
@@ -1288,13 +1334,19 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             for (uint32_t jj = 0; jj < ud; ++jj) {
                 const uint2 e2 = d.out_adj[ub + jj];
                 uint32_t known;
-                if (e2.x != s && !(XM && dmap_get(a.dm, dmap_key(s, e2.x), &known)))
+                if (e2.x != s && !(XM && dmap_get(a.dm, dmap_key(s, e2.x), &known))) {
                     bmax = max(bmax, sat_add(e.y, e2.y));
+                    if constexpr (PR)
+                        if (e2.x < n && direct[e2.x] != INF) atomicMax(&s_direct, direct[e2.x]);
+                }
             }
             atomicMax(&s_bound, bmax);
         }
         __syncthreads();
         const uint32_t bound = s_bound;
+        uint32_t sbound = bound;  // the search's label bound
+        if constexpr (PR)
+            if (d.ball == 0xFFFFFFFFu) sbound = max(bound, s_direct);
         const bool memo_all = s_memo != 0;  // decisions memoised: no search
         uint32_t *cur = fa, *curd = fda, *nx = fb, *nxd = fdb;
         const uint32_t lane = lane_id(), warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -1326,7 +1378,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
                     if (idx >= total) continue;
                     const uint2 e = d.out_adj[xb_o + (idx - ex_o)];
                     const uint32_t nd = sat_add(dx_o, e.y);
-                    if (nd >= bound || !id_ok(d, e.x)) continue;
+                    if (nd >= sbound || !id_ok(d, e.x)) continue;
                     const uint32_t old = atomicMin(&dist[e.x], nd);
                     if (nd < old) {
                         if (old == INF) touched[atomicAdd(&s_nt, 1u)] = e.x;
@@ -1469,7 +1521,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             dist[v] = INF;
             fst[v] = 0;
         }
-        if (MODE == MODE_PRUNE)
+        if (MODE == MODE_PRUNE || PR)
             for (uint32_t j = tid; j < sd; j += blockDim.x) {
                 const uint2 e = d.out_adj[sb + j];
                 if (e.x < n) direct[e.x] = INF;
@@ -1743,6 +1795,162 @@ __device__ __forceinline__ uint32_t warp_compact_list(const Dev &d, uint2 *adj, 
     return k;
 }
 
+// --------------------------------------------------------------------------
+// Pruning of overlay edges (Alg. 3's last step), after the rescoring searches
+// --------------------------------------------------------------------------
+
+constexpr uint32_t TOMB = 0xFFFFFFFFu;  // a pruned adjacency entry (fails id_ok)
+
+// One warp per rescoring source s: every pair (s, v) of the step (v in
+// N_out(u), u an affected out-neighbour of s, v != s) whose overlay edge
+// weighs more than the distance recorded for (s, v) has that edge's weight
+// set to 0 (weights are at least 1). Only ids are read while the pairs are
+// enumerated, so marking changes no other warp's enumeration; a pair reached
+// through several middles is marked once.
+__global__ void k_prune_find(Dev d, DMap dm, const uint32_t *S, const uint32_t *nS_dev, uint32_t r) {
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nS = *nS_dev;
+    Ctl *ctl = d.ctl;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nS; i += nwarps) {
+        const uint32_t s = S[i];
+        if (!id_ok(d, s)) continue;
+        const uint64_t sb = d.out_beg[s];
+        const uint32_t sd = d.out_deg[s];
+        if (!out_list_ok(d, sb, sd)) continue;
+        bool miss = false;
+        for (uint32_t c0 = 0; c0 < sd; c0 += 32) {
+            const uint32_t j = c0 + lane;
+            const bool valid = j < sd;
+            const uint2 e = valid ? d.out_adj[sb + j] : make_uint2(0, 0);
+            const bool mid = valid && id_ok(d, e.x) && is_middle<MODE_SCORE>(d, e.x, r);
+            uint32_t cnt = mid ? d.out_deg[e.x] : 0;
+            const uint64_t ub = mid ? d.out_beg[e.x] : 0;
+            if (mid && !out_list_ok(d, ub, cnt)) cnt = 0;
+            const uint32_t incl = warp_incl_scan(cnt);
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            const uint32_t excl = incl - cnt;
+            for (uint32_t b = 0; b < total; b += 32) {
+                const uint32_t idx = b + lane;
+                const uint32_t o = warp_owner(excl, idx);
+                const uint64_t ub_o = __shfl_sync(FULL, ub, o);
+                const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                if (idx >= total) continue;
+                const uint32_t v = d.out_adj[ub_o + (idx - ex_o)].x;
+                if (v == s || !id_ok(d, v)) continue;
+                uint32_t dv;
+                if (!dmap_get(dm, dmap_key(s, v), &dv)) {
+                    miss = true;  // every pair of the step was recorded
+                    continue;
+                }
+                for (uint32_t jj = 0; jj < sd; ++jj) {
+                    const uint2 se = d.out_adj[sb + jj];
+                    if (se.x != v) continue;
+                    if (se.y > dv) atomicCAS(&d.out_adj[sb + jj].y, se.y, 0u);
+                    break;
+                }
+            }
+        }
+        if (__any_sync(FULL, miss) && lane == 0) atomicOr(&ctl->err, ERR_BOUND);
+    }
+}
+
+// One warp per rescoring source s: each out-entry marked by k_prune_find
+// and its in-entry twin become tombstones; s and the edge's head are listed
+// (once each) for compaction.
+__global__ void k_prune_apply(Dev d, const uint32_t *S, const uint32_t *nS_dev, uint32_t *dirty,
+                              uint32_t *pmark, uint32_t stamp) {
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nS = *nS_dev;
+    Ctl *ctl = d.ctl;
+    unsigned long long l_pruned = 0;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nS; i += nwarps) {
+        const uint32_t s = S[i];
+        if (!id_ok(d, s)) continue;
+        const uint64_t sb = d.out_beg[s];
+        const uint32_t sd = d.out_deg[s];
+        if (!out_list_ok(d, sb, sd)) continue;
+        bool any = false;
+        for (uint32_t j = lane; j < sd; j += 32) {
+            const uint2 e = d.out_adj[sb + j];
+            if (e.y != 0 || !id_ok(d, e.x)) continue;
+            const uint32_t v = e.x;
+            d.out_adj[sb + j].x = TOMB;
+            const uint64_t ib = d.in_beg[v];
+            const uint32_t id = d.in_deg[v];
+            if (in_list_ok(d, ib, id))
+                for (uint32_t k = 0; k < id; ++k)
+                    if (d.in_adj[ib + k].x == s) {
+                        d.in_adj[ib + k].x = TOMB;
+                        break;
+                    }
+            ++l_pruned;
+            any = true;
+            if (atomicExch(&pmark[v], stamp) != stamp) dirty[atomicAdd(&ctl->nDirty, 1u)] = v;
+        }
+        if (__any_sync(FULL, any) && lane == 0 && atomicExch(&pmark[s], stamp) != stamp)
+            dirty[atomicAdd(&ctl->nDirty, 1u)] = s;
+    }
+    for (int o = 16; o > 0; o >>= 1) l_pruned += __shfl_xor_sync(FULL, l_pruned, o);
+    if (lane == 0 && l_pruned) atomicAdd(&ctl->pruned, l_pruned);
+}
+
+// One warp per listed vertex: drop the tombstones from its out- and in-lists
+// (at this point of a round no vertex carries the round's level, so the
+// shared compaction drops nothing else).
+__global__ void k_compact_dirty(Dev d, const uint32_t *X, const uint32_t *nX_dev, uint32_t r) {
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nX = *nX_dev;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nX; i += nwarps) {
+        const uint32_t x = X[i];
+        if (!id_ok(d, x)) continue;
+        const uint64_t ob = d.out_beg[x], ib = d.in_beg[x];
+        const uint32_t od = d.out_deg[x], id = d.in_deg[x];
+        if (out_list_ok(d, ob, od)) {
+            const uint32_t k = warp_compact_list(d, d.out_adj, ob, od, r);
+            if (lane == 0) d.out_deg[x] = k;
+        }
+        if (in_list_ok(d, ib, id)) {
+            const uint32_t k = warp_compact_list(d, d.in_adj, ib, id, r);
+            if (lane == 0) d.in_deg[x] = k;
+        }
+    }
+}
+
+// One warp per rescored vertex u (eligible): its score on the pruned overlay
+// from the recorded distances, P[u] = #{(v1, v2) kept} - (|N_in| + |N_out|).
+__global__ void k_score_map(Dev d, DMap dm, const uint32_t *A, uint32_t nA, uint32_t r) {
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nA; i += nwarps) {
+        const uint32_t u = A[i];
+        if (!id_ok(d, u) || d.amark[u] != r) continue;
+        const uint64_t ob = d.out_beg[u], ib = d.in_beg[u];
+        const uint32_t od = d.out_deg[u], id = d.in_deg[u];
+        if (!out_list_ok(d, ob, od) || !in_list_ok(d, ib, id)) continue;
+        uint32_t kept = 0;
+        bool miss = false;
+        const uint64_t pairs = (uint64_t)od * id;
+        for (uint64_t q = lane; q < pairs; q += 32) {
+            const uint2 e1 = d.in_adj[ib + q / od];
+            const uint2 e2 = d.out_adj[ob + q % od];
+            if (e1.x == e2.x) continue;
+            const uint32_t via = sat_add(e1.y, e2.y);
+            uint32_t dv;
+            if (!dmap_get(dm, dmap_key(e1.x, e2.x), &dv)) {
+                miss = true;
+                continue;
+            }
+            kept += via != INF && via <= dv;
+        }
+        kept = warp_sum(kept);
+        if (__any_sync(FULL, miss) && lane == 0) atomicOr(&d.ctl->err, ERR_BOUND);
+        if (lane == 0) d.P[u] = (int32_t)kept - (int32_t)(od + id);
+    }
+}
+
 // One warp per affected vertex x: drop this round's contracted vertices from
 // its out- and in-lists.
 __global__ void k_compact_lists(Dev d, const uint32_t *X, uint32_t nX, uint32_t r) {
@@ -2004,6 +2212,10 @@ struct Builder {
     DevBuf<uint32_t> dm_vals;
     DMap dm{};
     uint64_t dm_limit = 0;
+    bool xm = false;              // the map is in use (memoisation or pruning)
+    bool prune = false;           // overlay-edge pruning after the rescoring searches
+    bool dm_phase_clear = false;  // pruning without memoisation: the map holds one phase
+    DevBuf<uint32_t> pmark, dirty;
     void dmap_reserve(uint64_t keys);
     int sms = 152;
     EventPool pool;
@@ -2166,14 +2378,21 @@ void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_ma
     a.route_deg = route_deg;
     a.dm = dm;
     a.level_work = level_work;
+    if (dm_phase_clear) {
+        CH_CUDA_TRY(cudaMemsetAsync(dm_keys.ptr, 0xFF, dm_keys.count * sizeof(unsigned long long), st));
+        CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->dm_count, 0, sizeof(unsigned long long), st));
+    }
     cudaEvent_t e0 = start();
     const int blocks = grid_for((uint64_t)nS_max, WIT_WARPS, sms * 8);
-    const int feat = (dm_limit ? F_XM : 0) | (level_work != ~0ull ? F_LW : 0);
+    const int feat = (xm ? F_XM : 0) | (level_work != ~0ull ? F_LW : 0) | (prune ? F_PR : 0);
     switch (feat) {
         case 0: launch_witness<MODE, 0>(a, blocks); break;
         case F_XM: launch_witness<MODE, F_XM>(a, blocks); break;
         case F_LW: launch_witness<MODE, F_LW>(a, blocks); break;
-        default: launch_witness<MODE, F_XM | F_LW>(a, blocks); break;
+        case F_XM | F_LW: launch_witness<MODE, F_XM | F_LW>(a, blocks); break;
+        case F_XM | F_PR: launch_witness<MODE, F_XM | F_PR>(a, blocks); break;
+        case F_XM | F_LW | F_PR: launch_witness<MODE, F_XM | F_LW | F_PR>(a, blocks); break;
+        default: throw Error{CH_EINVAL, "internal: unsupported witness feature set"};
     }
     mark(&h->t_witness_ms, e0, 5);
     h->witness_launches += 3;
@@ -2252,6 +2471,7 @@ void Builder::run_rounds() {
         // reset per-round counters
         CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->nS, 0, 4 * 6, st));  // nS nS2 nF nAnext nOvf nRec
         CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->candBound, 0, 8 * 4, st));
+        if (prune) CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->pruned, 0, 8 + 4, st));  // pruned, nDirty
         // 1-2: score the affected set
         cudaEvent_t e0 = start();
         const uint32_t sstamp = 2 * r + 1, cstamp = 2 * r + 2;
@@ -2260,6 +2480,18 @@ void Builder::run_rounds() {
                                                                                     S.ptr, r);
             CH_CHECK_LAUNCH();
             witness<MODE_SCORE>(S.ptr, &ctl.ptr->nS, nA * 4 + 32 > n ? n : nA * 4 + 32, r);
+            if (prune) {
+                // Alg. 3's pruning, then the scores on the pruned overlay from
+                // the recorded distances
+                k_prune_find<<<sms * 8, 256, 0, st>>>(d, dm, S.ptr, &ctl.ptr->nS, r);
+                CH_CHECK_LAUNCH();
+                k_prune_apply<<<sms * 8, 256, 0, st>>>(d, S.ptr, &ctl.ptr->nS, dirty.ptr, pmark.ptr, r + 1);
+                CH_CHECK_LAUNCH();
+                k_compact_dirty<<<sms * 8, 256, 0, st>>>(d, dirty.ptr, &ctl.ptr->nDirty, r);
+                CH_CHECK_LAUNCH();
+                k_score_map<<<grid_for((uint64_t)nA * 32, 256, sms * 8), 256, 0, st>>>(d, dm, A.ptr, nA, r);
+                CH_CHECK_LAUNCH();
+            }
             if (tracing || learned) {
                 if (tracing && trace.count < (trace_count + nA) * 14) {
                     const uint64_t want = std::max<uint64_t>(trace_count + nA, trace.count / 14 * 2);
@@ -2391,7 +2623,7 @@ void Builder::run_rounds() {
         st_row[7] = c2.inserted;
         nVO -= nF;
         st_row[8] = nVO;
-        live_edges = live_edges - c.degFout - c.degFin + c2.newEdges;
+        live_edges = live_edges - c.degFout - c.degFin + c2.newEdges - c.pruned;
         st_row[9] = live_edges;
         h->round_stats.push_back(st_row);
         if (c2.nRec > rec.count) throw Error{CH_ECUDA, "internal: record overflow"};
@@ -2524,7 +2756,8 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_PRUNE, 0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        const int feat = (p->witness_memo_limit ? F_XM : 0) | (p->witness_level_work ? F_LW : 0);
+        const int feat = (p->witness_memo_limit || p->witness_prune ? F_XM : 0) |
+                         (p->witness_level_work ? F_LW : 0) | (p->witness_prune ? F_PR : 0);
         auto set_smem = [&](auto score_kernel, auto prune_kernel) {
             CH_CUDA_TRY(cudaFuncSetAttribute(score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             CH_CUDA_TRY(cudaFuncSetAttribute(prune_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -2533,6 +2766,11 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
         if (feat == F_LW) set_smem(k_witness_block<MODE_SCORE, F_LW>, k_witness_block<MODE_PRUNE, F_LW>);
         if (feat == (F_XM | F_LW))
             set_smem(k_witness_block<MODE_SCORE, F_XM | F_LW>, k_witness_block<MODE_PRUNE, F_XM | F_LW>);
+        if (feat == (F_XM | F_PR))
+            set_smem(k_witness_block<MODE_SCORE, F_XM | F_PR>, k_witness_block<MODE_PRUNE, F_XM | F_PR>);
+        if (feat == (F_XM | F_LW | F_PR))
+            set_smem(k_witness_block<MODE_SCORE, F_XM | F_LW | F_PR>,
+                     k_witness_block<MODE_PRUNE, F_XM | F_LW | F_PR>);
         int per_sm = 0;
         CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_witness_block<MODE_PRUNE, 0>,
                                                                   WB_THREADS, smem));
@@ -2639,12 +2877,20 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     // memoised in-round decisions need both phases to decide alike, which a
     // ball bound (cut levels depend on each phase's own weight bound) breaks;
     // the memoised distances across rounds replace them
-    d.memo = p->witness_ball_limit == 0 && p->witness_memo_limit == 0;
+    d.memo = p->witness_ball_limit == 0 && p->witness_memo_limit == 0 && p->witness_prune == 0;
     if (p->witness_level_work) b.level_work = p->witness_level_work;
-    if (p->witness_memo_limit) {
+    if (p->witness_memo_limit || p->witness_prune) {
+        b.xm = true;
         b.dm.count = &b.ctl.ptr->dm_count;
         b.dm_limit = p->witness_memo_limit;
+        b.dm_phase_clear = p->witness_memo_limit == 0;
         b.dmap_reserve(0);
+    }
+    if (p->witness_prune) {
+        b.prune = true;
+        b.pmark.alloc(n);
+        b.pmark.zero(b.st);
+        b.dirty.alloc(n);
     }
     b.emask.alloc(b.out_adj.count);
     d.emask = b.emask.ptr;

@@ -1,9 +1,10 @@
-"""Memoised witness distances across rounds (witness_memo_limit) and the
-level-work bound (witness_level_work) on the GPU, against the oracle run with
+"""Memoised witness distances across rounds (witness_memo_limit), the
+level-work bound (witness_level_work) and the pruning of overlay edges
+(witness_prune) on the GPU, against the oracle run with
 the same settings: levels, scores, ranks, shortcut logs, E_up, E_down and
-every round's counters bit for bit, and exact queries. Both oracle modes are
+every round's counters bit for bit, and exact queries. The oracle modes are
 pinned in test_trace_pins.py (the test's own map, bound, clearing rule,
-frontier and work sums) and test_witness_modes.py."""
+frontier and work sums, deletion log) and test_witness_modes.py."""
 import numpy as np
 import pytest
 
@@ -13,7 +14,7 @@ from tests.graphs import all_pairs_truth, small_families
 from tests.test_gpu_parity import assert_same_hierarchy
 
 pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="the memo and level-work kernels are written but have not yet run on a GPU")]
+              pytest.mark.skip(reason="the memo, level-work and pruning kernels are written but have not yet run on a GPU")]
 
 
 def _ch():
@@ -89,4 +90,36 @@ def test_level_work_on_rmat_with_a_core(lw, limit):
                          witness_memo_limit=limit, witness_level_work=lw)
     assert_same_hierarchy(gch, och)
     s, t = I.random_pairs(g.n, 3000, seed=155)
+    assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))
+
+
+# ---------------------------------------------------------------------------
+# Pruning of overlay edges (witness_prune), with and without memoisation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("H,limit,ball,cmax", [(5, None, None, None), (2, None, None, None),
+                                               (5, 1 << 30, None, None), (4, 30, None, None),
+                                               (4, None, 3, None), (5, 1 << 30, None, 6)])
+@pytest.mark.parametrize("name,g", FAMILIES, ids=[n for n, _ in FAMILIES])
+def test_prune_small_families(name, g, H, limit, ball, cmax):
+    och = O.build_ch(g, H, ball=O.CMAX_ALL if ball is None else ball,
+                     cmax=O.CMAX_ALL if cmax is None else cmax, memo=limit or 0, prune=True)
+    gch = _ch().CH.build(g, hop_limit=H, witness_ball_limit=ball, max_candidates_per_vertex=cmax,
+                         witness_memo_limit=limit, witness_prune=True)
+    assert_same_hierarchy(gch, och)
+    s, t = np.meshgrid(np.arange(g.n), np.arange(g.n), indexing="ij")
+    d = gch.query(s.ravel().astype(np.uint32), t.ravel().astype(np.uint32))
+    assert np.array_equal(d.astype(np.uint64).reshape(g.n, g.n), all_pairs_truth(g))
+
+
+@pytest.mark.parametrize("H,limit,lw", [(2, None, None), (5, 1 << 30, None), (5, 1 << 30, 64)])
+def test_prune_geometric(H, limit, lw):
+    g = I.geometric_knn_graph(20_000, seed=156)
+    och = O.build_ch(g, H, memo=limit or 0, prune=True,
+                     level_work=O.CMAX_ALL if lw is None else lw)
+    assert och.pruned.shape[0] > 0
+    gch = _ch().CH.build(g, hop_limit=H, witness_memo_limit=limit, witness_prune=True,
+                         witness_level_work=lw)
+    assert_same_hierarchy(gch, och)
+    s, t = I.random_pairs(g.n, 5000, seed=157)
     assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))
