@@ -139,7 +139,13 @@ typedef struct {
  *              label bound then also covers the direct edges (s, v) to their
  *              new targets (without a ball bound). A pruned edge lies on no
  *              shortest path, so distances stay exact. Uses the distance map
- *              of witness_memo_limit (held for one phase when that is 0). */
+ *              of witness_memo_limit (held for one phase when that is 0).
+ *   witness_settle_cap  θ > 0: the witness search is Alg. 3's own, a
+ *              Dijkstra from the source that stops once its targets or θ
+ *              vertices (the source included) are settled, equal labels
+ *              settled in id order; an unsettled target's distance is INF.
+ *              hop_limit and witness_level_work do not apply, and a ball
+ *              bound is an error (CH_EINVAL). 0 = the hop-limited search. */
 typedef struct {
     uint32_t hop_limit;
     uint32_t priority;
@@ -154,6 +160,8 @@ typedef struct {
     uint32_t witness_memo_limit;
     uint32_t witness_level_work;
     uint32_t witness_prune;
+    uint32_t witness_settle_cap;
+    uint32_t reserved;  /* 0 */
 } ch_params_t;
 
 /* Training parameters of ch_mlp_train (Adam, mean squared error). */

@@ -54,7 +54,8 @@ class ParamsT(C.Structure):
                 ("stream", C.c_void_p), ("mlp_weights", C.c_void_p), ("trace", C.c_int32),
                 ("witness_route_deg", C.c_uint32), ("witness_ball_limit", C.c_uint32),
                 ("witness_memo_limit", C.c_uint32), ("witness_level_work", C.c_uint32),
-                ("witness_prune", C.c_uint32)]
+                ("witness_prune", C.c_uint32), ("witness_settle_cap", C.c_uint32),
+                ("reserved", C.c_uint32)]
 
 
 class TuneRowT(C.Structure):
@@ -224,7 +225,7 @@ class CH:
     def _marshal(graph, n, offsets, targets, weights, hop_limit, tie_break, tie_seed, stream,
                  mlp_weights, trace, max_candidates_per_vertex, witness_route_deg,
                  witness_ball_limit=None, witness_memo_limit=None, witness_level_work=None,
-                 witness_prune=False):
+                 witness_prune=False, witness_settle_cap=None):
         if graph is not None:
             n, offsets, targets, weights = graph.n, graph.offsets, graph.targets, graph.weights
         g = GraphT()
@@ -261,6 +262,7 @@ class CH:
         p.witness_memo_limit = 0 if witness_memo_limit is None else int(witness_memo_limit)
         p.witness_level_work = 0 if witness_level_work is None else int(witness_level_work)
         p.witness_prune = int(bool(witness_prune))
+        p.witness_settle_cap = 0 if witness_settle_cap is None else int(witness_settle_cap)
         if max_candidates_per_vertex is not None:
             p.max_candidates_per_vertex = int(max_candidates_per_vertex)
         if mlp_weights is not None:
@@ -279,7 +281,8 @@ class CH:
               max_candidates_per_vertex: int | None = None, witness_route_deg: int = 0,
               witness_ball_limit: int | None = None,
               witness_memo_limit: int | None = None,
-              witness_level_work: int | None = None, witness_prune: bool = False) -> "CH":
+              witness_level_work: int | None = None, witness_prune: bool = False,
+              witness_settle_cap: int | None = None) -> "CH":
         """ch_build on a graph given as an ``inputs.Graph`` / NumPy CSR (host
         memory) or as CUDA tensors ``offsets`` (int64), ``targets`` and
         ``weights`` (int32 views of uint32 values) in device memory.
@@ -292,11 +295,13 @@ class CH:
         ``witness_level_work`` skips a hop level (from the second on) whose
         frontier has more out-edges than that; None = off. ``witness_prune``
         deletes overlay edges heavier than their pair's witness distance
-        after each round's rescoring searches."""
+        after each round's rescoring searches. ``witness_settle_cap`` (θ)
+        replaces the hop-limited search by Alg. 3's Dijkstra capped at θ
+        settled vertices; None = off."""
         g, p, keep = cls._marshal(graph, n, offsets, targets, weights, hop_limit, tie_break,
                                   tie_seed, stream, mlp_weights, trace, max_candidates_per_vertex,
                                   witness_route_deg, witness_ball_limit, witness_memo_limit,
-                                  witness_level_work, witness_prune)
+                                  witness_level_work, witness_prune, witness_settle_cap)
         h = C.c_void_p()
         _check(load().ch_build(C.byref(g), C.byref(p), C.byref(h)))
         del keep

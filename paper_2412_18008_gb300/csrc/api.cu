@@ -97,6 +97,8 @@ void ch_default_params(ch_params_t *p) {
     p->witness_memo_limit = 0;
     p->witness_level_work = 0;
     p->witness_prune = 0;
+    p->witness_settle_cap = 0;
+    p->reserved = 0;
 }
 
 int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out) {
@@ -117,6 +119,10 @@ int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out) {
     }
     if (p.tie_break > CH_TIE_ID) {
         g_last_error = "unknown tie_break";
+        return CH_EINVAL;
+    }
+    if (p.witness_settle_cap && p.witness_ball_limit) {
+        g_last_error = "the settled-vertex cap replaces the hop-limited search and its ball bound";
         return CH_EINVAL;
     }
     if (g->n == 0xFFFFFFFFu) {

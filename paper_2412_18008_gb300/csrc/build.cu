@@ -67,6 +67,11 @@ constexpr int F_LW = 2;
 // (without a ball bound), so the recorded value decides the deletion. Needs
 // F_XM (the recorded values live in the memoised-distance map).
 constexpr int F_PR = 4;
+// Alg. 3's search itself: a Dijkstra from the source that stops once its new
+// targets or theta vertices are settled, equal labels settled in id order.
+// Replaces the hop-limited search; the block tier is skipped (its sources go
+// to the global-memory tier).
+constexpr int F_TH = 8;
 
 // Weight of the overlay edge (s, v) from s's out-list, INF if none.
 __device__ __forceinline__ uint32_t direct_weight(const uint2 *out_adj, uint64_t sb, uint32_t sd, uint32_t v) {
@@ -235,6 +240,7 @@ struct WArgs {
     // F_LW: a hop level from the second on whose frontier has more
     // out-edges than this is not run
     unsigned long long level_work;
+    uint32_t theta;  // F_TH: settled-vertex cap
 };
 
 struct Dense {
@@ -489,6 +495,7 @@ __device__ __forceinline__ uint32_t ht_find(const uint32_t *keys, int bits, uint
 template <int MODE, int FEAT>
 __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
     constexpr bool XM = (FEAT & F_XM) != 0, LW = (FEAT & F_LW) != 0, PR = (FEAT & F_PR) != 0;
+    constexpr bool TH = (FEAT & F_TH) != 0;
     __shared__ WarpSmem smem[WIT_WARPS];
     WarpSmem &w = smem[threadIdx.x >> 5];
     const uint32_t lane = lane_id();
@@ -511,8 +518,16 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             if (lane == 0) atomicOr(&ctl->err, ERR_BOUND);
             continue;
         }
+        // where a source this tier cannot hold goes next (the settled-vertex
+        // cap has no block tier)
+        auto hand_on = [&]() {
+            if (lane == 0) {
+                if constexpr (TH) a.ovf2[atomicAdd(&ctl->nOvf2, 1u)] = s;
+                else a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
+            }
+        };
         if (route_all) {
-            if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
+            hand_on();
             continue;
         }
         const uint64_t sb = d.out_beg[s];
@@ -579,7 +594,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         if constexpr (PR)
             if (d.ball == 0xFFFFFFFFu) sbound = max(bound, warp_max(direct));
         if (warp_sum((uint32_t)l_midedge) > a.route_deg) {
-            if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
+            hand_on();
             continue;
         }
         bool no_cand;
@@ -592,6 +607,106 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             continue;
         }
 
+        // Phase 1 with the settled-vertex cap: the new targets are flagged
+        // in the table (bit 1 of fst), then each step settles the unsettled
+        // vertex of least (label, id) (bit 0) and relaxes its out-edges,
+        // until every new target or theta vertices are settled.
+        if constexpr (TH) {
+            if (!(XM && bound == 0)) {
+                for (uint32_t t = lane; t < WIT_T; t += 32) {
+                    w.key[t] = EMPTY;
+                    w.val[t] = INF;
+                    w.fst[t] = 0;
+                }
+                __syncwarp();
+                if (lane == 0) w.val[ht_insert(w.key, WIT_TBITS, s)] = 0;
+                __syncwarp();
+                bool t_ovf = false;
+                uint32_t l_targets = 0;
+                for (uint32_t c0 = 0; c0 < sd; c0 += 32) {
+                    const uint32_t j = c0 + lane;
+                    const bool valid = j < sd;
+                    const uint2 e = valid ? d.out_adj[sb + j] : make_uint2(0, 0);
+                    const bool mid = valid && id_ok(d, e.x) && is_middle<MODE>(d, e.x, r);
+                    uint32_t cnt = mid ? d.out_deg[e.x] : 0;
+                    const uint64_t ub = mid ? d.out_beg[e.x] : 0;
+                    if (mid && !out_list_ok(d, ub, cnt)) cnt = 0;
+                    const uint32_t incl = warp_incl_scan(cnt);
+                    const uint32_t total = __shfl_sync(FULL, incl, 31);
+                    const uint32_t excl = incl - cnt;
+                    for (uint32_t b = 0; b < total; b += 32) {
+                        const uint32_t idx = b + lane;
+                        const uint32_t o = warp_owner(excl, idx);
+                        const uint64_t ub_o = __shfl_sync(FULL, ub, o);
+                        const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                        if (idx >= total) continue;
+                        const uint32_t v2 = d.out_adj[ub_o + (idx - ex_o)].x;
+                        uint32_t known;
+                        if (v2 == s || !id_ok(d, v2) || (XM && dmap_get(a.dm, dmap_key(s, v2), &known)))
+                            continue;
+                        const uint32_t slot = ht_insert(w.key, WIT_TBITS, v2);
+                        if (slot == EMPTY) t_ovf = true;
+                        else if ((atomicOr(&w.fst[slot], 2u) & 2u) == 0) ++l_targets;
+                    }
+                }
+                uint32_t remaining = warp_sum(l_targets);
+                t_ovf = __any_sync(FULL, t_ovf);
+                uint32_t settled = 0;
+                while (!t_ovf && remaining > 0 && settled < a.theta) {
+                    __syncwarp();
+                    unsigned long long best = ~0ull;
+                    uint32_t bslot = 0;
+                    for (uint32_t t = lane; t < WIT_T; t += 32) {
+                        const uint32_t k = w.key[t];
+                        if (k == EMPTY || (w.fst[t] & 1u) || w.val[t] == INF) continue;
+                        const unsigned long long c = ((unsigned long long)w.val[t] << 32) | k;
+                        if (c < best) {
+                            best = c;
+                            bslot = t;
+                        }
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long ob = __shfl_xor_sync(FULL, best, o);
+                        const uint32_t os = __shfl_xor_sync(FULL, bslot, o);
+                        if (ob < best) {
+                            best = ob;
+                            bslot = os;
+                        }
+                    }
+                    if (best == ~0ull) break;  // nothing reachable left
+                    const uint32_t x = (uint32_t)best, dx = (uint32_t)(best >> 32);
+                    ++settled;
+                    remaining -= (w.fst[bslot] & 2u) ? 1u : 0u;
+                    __syncwarp();
+                    if (lane == 0) w.fst[bslot] |= 1u;
+                    if (remaining == 0 || settled >= a.theta) break;
+                    const uint64_t xb = d.out_beg[x];
+                    uint32_t xd = d.out_deg[x];
+                    if (!out_list_ok(d, xb, xd)) xd = 0;
+                    l_vert += (lane == 0);
+                    l_edge += (lane == 0) ? xd : 0;
+                    bool ovf_here = false;
+                    for (uint32_t j = lane; j < xd; j += 32) {
+                        const uint2 e = d.out_adj[xb + j];
+                        if (!id_ok(d, e.x)) continue;
+                        const uint32_t nd = sat_add(dx, e.y);
+                        if (nd == INF) continue;
+                        const uint32_t slot = ht_insert(w.key, WIT_TBITS, e.x);
+                        if (slot == EMPTY) {
+                            ovf_here = true;
+                            continue;
+                        }
+                        if (!(w.fst[slot] & 1u)) atomicMin(&w.val[slot], nd);
+                    }
+                    t_ovf = __any_sync(FULL, ovf_here);
+                }
+                __syncwarp();
+                if (t_ovf) {
+                    hand_on();
+                    continue;
+                }
+            }
+        } else {
         // Phase 1: hop-limited Bellman-Ford from s, levels 1..H, each level
         // relaxing from the previous level's values (frontier snapshots);
         // skipped when the decisions are memoised.
@@ -689,6 +804,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
             continue;
         }
         }  // Phase 1
+        }  // hop-limited search
 
         // Phase 2: decisions for every candidate (s, u, v2).
         if (MODE == MODE_PRUNE) {
@@ -740,6 +856,8 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                             if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &dh))) {
                                 const uint32_t slot = ht_find(w.key, WIT_TBITS, e2.x);
                                 dh = slot == EMPTY ? INF : w.val[slot];
+                                if constexpr (TH)  // an unsettled target counts as INF
+                                    if (slot != EMPTY && !(w.fst[slot] & 1u)) dh = INF;
                             }
                             keepit = via != INF && via <= dh;
                         }
@@ -766,7 +884,7 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         if (MODE == MODE_PRUNE) {
             __syncwarp();
             if (__any_sync(FULL, mover)) {
-                if (lane == 0) a.ovf[atomicAdd(&ctl->nOvf, 1u)] = s;
+                hand_on();
                 continue;
             }
             c_cand += l_cand;
@@ -836,8 +954,10 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
                             const uint2 e2 = d.out_adj[ub_o + (idx - ex_o)];
                             if (e2.x != s) {
                                 const uint32_t slot = ht_find(w.key, WIT_TBITS, e2.x);
-                                const int put = dmap_put(a.dm, dmap_key(s, e2.x),
-                                                         slot == EMPTY ? INF : w.val[slot]);
+                                uint32_t dv = slot == EMPTY ? INF : w.val[slot];
+                                if constexpr (TH)
+                                    if (slot != EMPTY && !(w.fst[slot] & 1u)) dv = INF;
+                                const int put = dmap_put(a.dm, dmap_key(s, e2.x), dv);
                                 full |= put < 0;
                                 c_dm += put > 0;
                             }
@@ -1273,6 +1393,7 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
 template <int MODE, int FEAT>
 __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
     constexpr bool XM = (FEAT & F_XM) != 0, LW = (FEAT & F_LW) != 0, PR = (FEAT & F_PR) != 0;
+    constexpr bool TH = (FEAT & F_TH) != 0;
     const Dev d = a.d;
     Ctl *ctl = d.ctl;
     const uint32_t n = d.n;
@@ -1285,6 +1406,8 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
     __shared__ uint32_t s_item, s_bound, s_nt, s_nm, s_nf[2], s_memo;
     __shared__ unsigned long long s_lw;  // F_LW: out-edges of the next level's frontier
     __shared__ uint32_t s_direct;        // F_PR: heaviest overlay edge (s, v) to a new target v
+    __shared__ uint32_t s_rem, s_settled;  // F_TH: new targets not yet settled, vertices settled
+    __shared__ unsigned long long s_best;  // F_TH: least (label, id) of an unsettled vertex
     __shared__ unsigned long long s_cnt[5];
     const uint32_t tid = threadIdx.x;
     const uint32_t nOvf = ctl->nOvf2;
@@ -1350,6 +1473,68 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
         const bool memo_all = s_memo != 0;  // decisions memoised: no search
         uint32_t *cur = fa, *curd = fda, *nx = fb, *nxd = fdb;
         const uint32_t lane = lane_id(), warp = tid >> 5, nwarps = blockDim.x >> 5;
+        // Alg. 3's search with the settled-vertex cap: bit 1 of fst flags a
+        // new target, bit 0 a settled vertex; each step settles the
+        // unsettled vertex of least (label, id) among those reached.
+        if constexpr (TH) {
+            if (bound > 0) {
+                if (tid == 0) {
+                    s_rem = 0;
+                    s_settled = 0;
+                }
+                __syncthreads();
+                for (uint32_t j = tid; j < sd; j += blockDim.x) {
+                    const uint2 e = d.out_adj[sb + j];
+                    if (!id_ok(d, e.x) || !is_middle<MODE>(d, e.x, r)) continue;
+                    const uint64_t ub = d.out_beg[e.x];
+                    const uint32_t ud = out_list_ok(d, ub, d.out_deg[e.x]) ? d.out_deg[e.x] : 0;
+                    for (uint32_t jj = 0; jj < ud; ++jj) {
+                        const uint32_t v2 = d.out_adj[ub + jj].x;
+                        uint32_t known;
+                        if (v2 == s || !id_ok(d, v2) || (XM && dmap_get(a.dm, dmap_key(s, v2), &known)))
+                            continue;
+                        if ((atomicOr(&fst[v2], 2u) & 2u) == 0) atomicAdd(&s_rem, 1u);
+                    }
+                }
+                while (true) {
+                    __syncthreads();
+                    if (tid == 0) s_best = ~0ull;
+                    __syncthreads();
+                    if (s_rem == 0 || s_settled >= a.theta) break;  // read by all between barriers
+                    const uint32_t nt = s_nt;
+                    unsigned long long best = ~0ull;
+                    for (uint32_t p = tid; p < nt; p += blockDim.x) {
+                        const uint32_t v = touched[p];
+                        if ((fst[v] & 1u) || dist[v] == INF) continue;
+                        best = min(best, ((unsigned long long)dist[v] << 32) | v);
+                    }
+                    if (best != ~0ull) atomicMin(&s_best, best);
+                    __syncthreads();
+                    const unsigned long long b = s_best;
+                    if (b == ~0ull) break;  // nothing reachable left
+                    const uint32_t x = (uint32_t)b, dx = (uint32_t)(b >> 32);
+                    __syncthreads();
+                    if (tid == 0) {
+                        fst[x] |= 1u;
+                        ++s_settled;
+                        if (fst[x] & 2u) --s_rem;
+                    }
+                    __syncthreads();
+                    if (s_rem == 0 || s_settled >= a.theta) break;
+                    const uint64_t xb = d.out_beg[x];
+                    const uint32_t xd = out_list_ok(d, xb, d.out_deg[x]) ? d.out_deg[x] : 0;
+                    for (uint32_t j = tid; j < xd; j += blockDim.x) {
+                        const uint2 e = d.out_adj[xb + j];
+                        if (!id_ok(d, e.x) || (fst[e.x] & 1u)) continue;
+                        const uint32_t nd = sat_add(dx, e.y);
+                        if (nd == INF) continue;
+                        const uint32_t old = atomicMin(&dist[e.x], nd);
+                        if (old == INF && nd < INF) touched[atomicAdd(&s_nt, 1u)] = e.x;
+                    }
+                }
+                __syncthreads();
+            }
+        } else {
         for (uint32_t lvl = 1; lvl <= d.H && bound > 0 && !memo_all; ++lvl) {
             const uint32_t nf = s_nf[(lvl - 1) & 1];
             __syncthreads();
@@ -1406,6 +1591,7 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
             if constexpr (LW)
                 if (s_lw > a.level_work) break;
         }
+        }  // hop-limited search
         // the source's direct edges, for the existing-edge test
         if (MODE == MODE_PRUNE) {
             for (uint32_t j = tid; j < sd; j += blockDim.x) {
@@ -1434,7 +1620,11 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
                     keepit = (mword >> jj) & 1ull;
                 } else {
                     uint32_t dh;
-                    if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &dh))) dh = dist[e2.x];
+                    if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &dh))) {
+                        dh = dist[e2.x];
+                        if constexpr (TH)  // an unsettled target counts as INF
+                            if (!(fst[e2.x] & 1u)) dh = INF;
+                    }
                     keepit = via != INF && via <= dh;
                 }
                 if (MODE == MODE_SCORE && keepit && mk) rec_mask |= 1ull << jj;
@@ -1505,7 +1695,10 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
                     for (uint32_t jj = 0; jj < ud; ++jj) {
                         const uint2 e2 = d.out_adj[ub + jj];
                         if (e2.x == s || !id_ok(d, e2.x)) continue;
-                        const int put = dmap_put(a.dm, dmap_key(s, e2.x), dist[e2.x]);
+                        uint32_t dv = dist[e2.x];
+                        if constexpr (TH)
+                            if (!(fst[e2.x] & 1u)) dv = INF;
+                        const int put = dmap_put(a.dm, dmap_key(s, e2.x), dv);
                         full |= put < 0;
                         l_dm += put > 0;
                     }
@@ -1526,6 +1719,19 @@ __global__ void __launch_bounds__(256) k_witness_dense(WArgs a, Dense dn) {
                 const uint2 e = d.out_adj[sb + j];
                 if (e.x < n) direct[e.x] = INF;
             }
+        if constexpr (TH) {
+            // targets never reached are not in the touched list: clear their flags
+            for (uint32_t j = tid; j < sd; j += blockDim.x) {
+                const uint2 e = d.out_adj[sb + j];
+                if (!id_ok(d, e.x) || !is_middle<MODE>(d, e.x, r)) continue;
+                const uint64_t ub = d.out_beg[e.x];
+                const uint32_t ud = out_list_ok(d, ub, d.out_deg[e.x]) ? d.out_deg[e.x] : 0;
+                for (uint32_t jj = 0; jj < ud; ++jj) {
+                    const uint32_t v2 = d.out_adj[ub + jj].x;
+                    if (v2 < n) fst[v2] = 0;
+                }
+            }
+        }
     }
 }
 
@@ -2252,6 +2458,7 @@ struct Builder {
     template <int MODE, int FEAT>
     void launch_witness(const WArgs &a, int blocks);
     unsigned long long level_work = ~0ull;  // F_LW bound; all ones = off
+    uint32_t theta = 0;                     // F_TH settled-vertex cap; 0 = off
 };
 
 #define CTL_OFF(field) offsetof(Ctl, field)
@@ -2378,13 +2585,15 @@ void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_ma
     a.route_deg = route_deg;
     a.dm = dm;
     a.level_work = level_work;
+    a.theta = theta;
     if (dm_phase_clear) {
         CH_CUDA_TRY(cudaMemsetAsync(dm_keys.ptr, 0xFF, dm_keys.count * sizeof(unsigned long long), st));
         CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->dm_count, 0, sizeof(unsigned long long), st));
     }
     cudaEvent_t e0 = start();
     const int blocks = grid_for((uint64_t)nS_max, WIT_WARPS, sms * 8);
-    const int feat = (xm ? F_XM : 0) | (level_work != ~0ull ? F_LW : 0) | (prune ? F_PR : 0);
+    const int feat = (xm ? F_XM : 0) | (level_work != ~0ull && !theta ? F_LW : 0) | (prune ? F_PR : 0) |
+                     (theta ? F_TH : 0);
     switch (feat) {
         case 0: launch_witness<MODE, 0>(a, blocks); break;
         case F_XM: launch_witness<MODE, F_XM>(a, blocks); break;
@@ -2392,6 +2601,9 @@ void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_ma
         case F_XM | F_LW: launch_witness<MODE, F_XM | F_LW>(a, blocks); break;
         case F_XM | F_PR: launch_witness<MODE, F_XM | F_PR>(a, blocks); break;
         case F_XM | F_LW | F_PR: launch_witness<MODE, F_XM | F_LW | F_PR>(a, blocks); break;
+        case F_TH: launch_witness<MODE, F_TH>(a, blocks); break;
+        case F_TH | F_XM: launch_witness<MODE, F_TH | F_XM>(a, blocks); break;
+        case F_TH | F_XM | F_PR: launch_witness<MODE, F_TH | F_XM | F_PR>(a, blocks); break;
         default: throw Error{CH_EINVAL, "internal: unsupported witness feature set"};
     }
     mark(&h->t_witness_ms, e0, 5);
@@ -2757,7 +2969,8 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
         CH_CUDA_TRY(cudaFuncSetAttribute(k_witness_block<MODE_PRUNE, 0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         const int feat = (p->witness_memo_limit || p->witness_prune ? F_XM : 0) |
-                         (p->witness_level_work ? F_LW : 0) | (p->witness_prune ? F_PR : 0);
+                         (p->witness_level_work && !p->witness_settle_cap ? F_LW : 0) |
+                         (p->witness_prune ? F_PR : 0) | (p->witness_settle_cap ? F_TH : 0);
         auto set_smem = [&](auto score_kernel, auto prune_kernel) {
             CH_CUDA_TRY(cudaFuncSetAttribute(score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             CH_CUDA_TRY(cudaFuncSetAttribute(prune_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -2771,6 +2984,12 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
         if (feat == (F_XM | F_LW | F_PR))
             set_smem(k_witness_block<MODE_SCORE, F_XM | F_LW | F_PR>,
                      k_witness_block<MODE_PRUNE, F_XM | F_LW | F_PR>);
+        if (feat == F_TH) set_smem(k_witness_block<MODE_SCORE, F_TH>, k_witness_block<MODE_PRUNE, F_TH>);
+        if (feat == (F_TH | F_XM))
+            set_smem(k_witness_block<MODE_SCORE, F_TH | F_XM>, k_witness_block<MODE_PRUNE, F_TH | F_XM>);
+        if (feat == (F_TH | F_XM | F_PR))
+            set_smem(k_witness_block<MODE_SCORE, F_TH | F_XM | F_PR>,
+                     k_witness_block<MODE_PRUNE, F_TH | F_XM | F_PR>);
         int per_sm = 0;
         CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_witness_block<MODE_PRUNE, 0>,
                                                                   WB_THREADS, smem));
@@ -2879,6 +3098,7 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     // the memoised distances across rounds replace them
     d.memo = p->witness_ball_limit == 0 && p->witness_memo_limit == 0 && p->witness_prune == 0;
     if (p->witness_level_work) b.level_work = p->witness_level_work;
+    b.theta = p->witness_settle_cap;
     if (p->witness_memo_limit || p->witness_prune) {
         b.xm = true;
         b.dm.count = &b.ctl.ptr->dm_count;

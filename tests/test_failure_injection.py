@@ -76,3 +76,14 @@ def test_query_allocation_failure_leaves_the_handle_usable():
             assert np.array_equal(got, want)
         ch.debug_fail_alloc(-1)
         assert np.array_equal(h.query(s, t), want)
+
+
+def test_settled_cap_with_a_ball_bound_is_rejected_before_any_cuda_call():
+    # ch_build checks its parameters first; the settled-vertex cap replaces
+    # the hop-limited search, so a ball bound beside it is an error
+    ch = _ch()
+    g = I.grid_graph(8, 8, 0.1, 1, 20, seed=3)
+    with pytest.raises(ch.CHError) as ei:
+        ch.CH.build(g, hop_limit=5, witness_settle_cap=4, witness_ball_limit=3)
+    assert ei.value.code == ch.CH_EINVAL
+    assert "settled-vertex cap" in str(ei.value)

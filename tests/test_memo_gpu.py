@@ -1,6 +1,7 @@
 """Memoised witness distances across rounds (witness_memo_limit), the
-level-work bound (witness_level_work) and the pruning of overlay edges
-(witness_prune) on the GPU, against the oracle run with
+level-work bound (witness_level_work), the pruning of overlay edges
+(witness_prune) and Alg. 3's settled-vertex cap (witness_settle_cap) on the
+GPU, against the oracle run with
 the same settings: levels, scores, ranks, shortcut logs, E_up, E_down and
 every round's counters bit for bit, and exact queries. The oracle modes are
 pinned in test_trace_pins.py (the test's own map, bound, clearing rule,
@@ -14,7 +15,7 @@ from tests.graphs import all_pairs_truth, small_families
 from tests.test_gpu_parity import assert_same_hierarchy
 
 pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="the memo, level-work and pruning kernels are written but have not yet run on a GPU")]
+              pytest.mark.skip(reason="the memo, level-work, pruning and settled-cap kernels are written but have not yet run on a GPU")]
 
 
 def _ch():
@@ -123,3 +124,37 @@ def test_prune_geometric(H, limit, lw):
     assert_same_hierarchy(gch, och)
     s, t = I.random_pairs(g.n, 5000, seed=157)
     assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))
+
+
+# ---------------------------------------------------------------------------
+# Alg. 3's settled-vertex cap (witness_settle_cap), alone and with memo and
+# pruning
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("theta,limit,prune,cmax", [(1, None, False, None), (3, None, False, None),
+                                                    (20, None, False, None), (10**6, None, False, None),
+                                                    (8, 1 << 30, False, None), (8, 30, True, None),
+                                                    (6, 1 << 30, False, 6)])
+@pytest.mark.parametrize("name,g", FAMILIES, ids=[n for n, _ in FAMILIES])
+def test_settled_cap_small_families(name, g, theta, limit, prune, cmax):
+    och = O.build_ch(g, 5, theta=theta, memo=limit or 0, prune=prune,
+                     cmax=O.CMAX_ALL if cmax is None else cmax)
+    gch = _ch().CH.build(g, hop_limit=5, witness_settle_cap=theta, witness_memo_limit=limit,
+                         witness_prune=prune, max_candidates_per_vertex=cmax)
+    assert_same_hierarchy(gch, och)
+    s, t = np.meshgrid(np.arange(g.n), np.arange(g.n), indexing="ij")
+    d = gch.query(s.ravel().astype(np.uint32), t.ravel().astype(np.uint32))
+    assert np.array_equal(d.astype(np.uint64).reshape(g.n, g.n), all_pairs_truth(g))
+
+
+@pytest.mark.parametrize("theta", [50, 400])
+def test_settled_cap_geometric_and_dense(theta):
+    # 400 settled vertices outgrow a warp's 256-slot table: the global-memory tier
+    for g in (I.geometric_knn_graph(20_000, seed=158),
+              I.random_digraph(1500, 9000, 1, 1000, seed=159, allow_loops=False)):
+        och = O.build_ch(g, 5, theta=theta)
+        gch = _ch().CH.build(g, hop_limit=5, witness_settle_cap=theta)
+        assert_same_hierarchy(gch, och)
+        s, t = I.random_pairs(g.n, 3000, seed=160)
+        assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))
+
