@@ -127,6 +127,9 @@ def parse():
                          "out-edges than this (default: off)")
     ap.add_argument("--prune", action="store_true",
                     help="prune overlay edges heavier than their pair's witness distance")
+    ap.add_argument("--theta", type=int, default=None,
+                    help="Alg. 3's witness search: a Dijkstra capped at this many settled "
+                         "vertices, in place of the hop-limited search (default: off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
@@ -216,7 +219,7 @@ class ClockSampler:
 
 
 def cpu_sample_build(workload: str, hop_limit: int, cmax, ball=None, threads: bool = False,
-                     memo=None, level_work=None, prune=False):
+                     memo=None, level_work=None, prune=False, theta=None):
     """Oracle build on a sample graph of the same family, scaled linearly
     (by vertex count) to the full workload. Returns (scaled_s, raw_s,
     threads used, sample vertices). threads: the -DORACLE_THREADS build,
@@ -226,7 +229,8 @@ def cpu_sample_build(workload: str, hop_limit: int, cmax, ball=None, threads: bo
     t0 = time.perf_counter()
     O.build_ch(g, hop_limit, cmax=O.CMAX_ALL if cmax is None else cmax,
                ball=O.CMAX_ALL if ball is None else ball, threads=threads, memo=memo or 0,
-               level_work=O.CMAX_ALL if level_work is None else level_work, prune=prune)
+               level_work=O.CMAX_ALL if level_work is None else level_work, prune=prune,
+               theta=theta or 0)
     raw = time.perf_counter() - t0
     return raw * (WORKLOADS[workload][0] / g.n), raw, (os.cpu_count() or 1) if threads else 1, g.n
 
@@ -245,13 +249,13 @@ def run_reference(args):
     for _ in range(args.warmup):
         O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball, memo=args.memo or 0,
                    level_work=O.CMAX_ALL if args.level_work is None else args.level_work,
-                   prune=args.prune)
+                   prune=args.prune, theta=args.theta or 0)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
         O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball, memo=args.memo or 0,
                    level_work=O.CMAX_ALL if args.level_work is None else args.level_work,
-                   prune=args.prune)
+                   prune=args.prune, theta=args.theta or 0)
         times.append(time.perf_counter() - t0)
     scale = n / sample_n
     value = statistics.mean(times) * scale
@@ -494,7 +498,8 @@ def main():
         h = ch.CH.build(n=n, offsets=off_d, targets=tgt_d, weights=w_d,
                         hop_limit=args.hop_limit, stream=stream, max_candidates_per_vertex=args.cmax,
                         witness_ball_limit=args.witness_ball, witness_memo_limit=args.memo,
-                        witness_level_work=args.level_work, witness_prune=args.prune)
+                        witness_level_work=args.level_work, witness_prune=args.prune,
+                        witness_settle_cap=args.theta)
         if qcfg is not None:
             h.set_query_config(*qcfg)
         if not args.build_only:
@@ -531,7 +536,8 @@ def main():
                             hop_limit=args.hop_limit, stream=stream,
                             max_candidates_per_vertex=args.cmax, witness_ball_limit=args.witness_ball,
                             witness_memo_limit=args.memo, witness_level_work=args.level_work,
-                            witness_prune=args.prune)
+                            witness_prune=args.prune,
+                            witness_settle_cap=args.theta)
             if qcfg is not None:
                 h.set_query_config(*qcfg)
             e1.record(stream)
@@ -636,7 +642,8 @@ def main():
             t0 = time.perf_counter()
             hh = ch.CH.build(g, hop_limit=args.hop_limit, max_candidates_per_vertex=args.cmax,
                              witness_ball_limit=args.witness_ball, witness_memo_limit=args.memo,
-                             witness_level_work=args.level_work, witness_prune=args.prune)
+                             witness_level_work=args.level_work, witness_prune=args.prune,
+                             witness_settle_cap=args.theta)
             if qcfg is not None:
                 hh.set_query_config(*qcfg)
             t1 = time.perf_counter()
@@ -654,7 +661,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         scaled, raw, cores, sn = cpu_sample_build(args.workload, args.hop_limit, args.cmax,
                                                   args.witness_ball, memo=args.memo,
-                                                  level_work=args.level_work, prune=args.prune)
+                                                  level_work=args.level_work, prune=args.prune,
+                                                  theta=args.theta)
         cpu = {"value": scaled, "unit": "s", "cores": cores, "kind": "oracle",
                "sample": f"oracle build of a {sn}-vertex graph of the same family "
                          f"({raw:.2f} s, one thread), scaled linearly by vertex count to {n}"}
@@ -663,7 +671,7 @@ def main():
         mt_scaled, mt_raw, mt_cores, _ = cpu_sample_build(args.workload, args.hop_limit, args.cmax,
                                                           args.witness_ball, threads=True,
                                                           memo=args.memo, level_work=args.level_work,
-                                                          prune=args.prune)
+                                                          prune=args.prune, theta=args.theta)
         cpu["threaded"] = {"value": mt_scaled, "unit": "s", "cores": mt_cores,
                            "sample": f"same sample, -DORACLE_THREADS build ({mt_raw:.2f} s)"}
 
@@ -676,7 +684,7 @@ def main():
             "config": {"workload": args.workload, "vertices": n, "edges": int(g.m),
                        "cmax": args.cmax, "witness_ball": args.witness_ball,
                        "witness_memo": args.memo, "witness_level_work": args.level_work,
-                       "witness_prune": args.prune,
+                       "witness_prune": args.prune, "witness_settle_cap": args.theta,
                        "core_vertices": stats["core_vertices"],
                        "queries": nq, "hop_limit": args.hop_limit,
                        "parallelism": f"replicas{world}",
