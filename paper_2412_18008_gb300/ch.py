@@ -313,23 +313,41 @@ class CH:
                        offsets=None, targets=None, weights=None, tie_break: int = CH_TIE_HASHED,
                        tie_seed: int = 0, stream=None, mlp_weights=None,
                        max_candidates_per_vertex: int | None = None,
-                       witness_ball_limit: int | None = None):
+                       witness_ball_limit: int | None = None, level_works=(None,)):
         """ch_build_autotune: builds once per (hop limit, routing threshold),
-        keeps the cheapest. Returns (CH, rows as dicts, chosen index)."""
-        g, p, keep = cls._marshal(graph, n, offsets, targets, weights, 5, tie_break, tie_seed,
-                                  stream, mlp_weights, False, max_candidates_per_vertex, 0,
-                                  witness_ball_limit)
+        keeps the cheapest. ``level_works`` adds the witness level-work bound
+        as a third dimension (one ch_build_autotune call per value; None =
+        no bound). Returns (CH, rows as dicts with their ``level_work``,
+        chosen index)."""
         hl = np.ascontiguousarray(hop_limits, dtype=np.uint32)
         rd = np.ascontiguousarray(route_degs, dtype=np.uint32)
-        rows = (TuneRowT * (hl.size * rd.size))()
-        chosen = C.c_uint32()
-        h = C.c_void_p()
-        _check(load().ch_build_autotune(C.byref(g), C.byref(p), _hp(hl), hl.size, _hp(rd), rd.size,
-                                        sample, float(queries_per_build), C.byref(h), rows,
-                                        C.byref(chosen)))
-        del keep
-        out = [{f: getattr(r, f) for f, _ in TuneRowT._fields_} for r in rows]
-        return cls(h), out, int(chosen.value)
+        best, out, best_i = None, [], 0
+        for lw in level_works:
+            g, p, keep = cls._marshal(graph, n, offsets, targets, weights, 5, tie_break, tie_seed,
+                                      stream, mlp_weights, False, max_candidates_per_vertex, 0,
+                                      witness_ball_limit, None, lw)
+            rows = (TuneRowT * (hl.size * rd.size))()
+            chosen = C.c_uint32()
+            h = C.c_void_p()
+            rc = load().ch_build_autotune(C.byref(g), C.byref(p), _hp(hl), hl.size, _hp(rd), rd.size,
+                                          sample, float(queries_per_build), C.byref(h), rows,
+                                          C.byref(chosen))
+            del keep
+            if rc != CH_OK:
+                if best is not None:
+                    best.close()
+                _check(rc)
+            base = len(out)
+            out += [dict({f: getattr(r, f) for f, _ in TuneRowT._fields_}, level_work=lw) for r in rows]
+            k = base + int(chosen.value)
+            cand = cls(h)
+            if best is None or out[k]["cost"] < out[best_i]["cost"]:
+                if best is not None:
+                    best.close()
+                best, best_i = cand, k
+            else:
+                cand.close()
+        return best, out, best_i
 
     # -- queries ----------------------------------------------------------
     def query(self, src, dst, want_settled: bool = False, stream=None):
