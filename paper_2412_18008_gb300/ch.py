@@ -188,6 +188,12 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
+def _need_cuda_ids(t, name: str):
+    """The device entry points take contiguous 32-bit CUDA tensors of ids."""
+    if not _is_torch(t) or not t.is_cuda or not t.is_contiguous() or t.element_size() != 4:
+        raise ValueError(f"{name} must be a contiguous 32-bit CUDA tensor of vertex ids")
+
+
 def _host(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
@@ -389,6 +395,7 @@ class CH:
         """Distances from s to every target of the CUDA tensor ``dst``
         (int32 view of uint32 ids), asynchronous on ``stream``."""
         import torch
+        _need_cuda_ids(dst, "dst")
         out = torch.empty_like(dst)
         _check(load().ch_query_one_to_many(self._h, int(s), dst.data_ptr(), dst.numel(),
                                            out.data_ptr(), _stream_ptr(stream)))
@@ -399,6 +406,7 @@ class CH:
         of uint32 ids) to every vertex: an int32 tensor [len(src), n] holding
         uint32 bit patterns, asynchronous on ``stream``."""
         import torch
+        _need_cuda_ids(src, "src")
         n = self.stats()["n"]
         out = torch.empty((src.numel(), n), dtype=torch.int32, device=src.device)
         _check(load().ch_one_to_all(self._h, src.data_ptr(), src.numel(), out.data_ptr(),

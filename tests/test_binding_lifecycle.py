@@ -114,3 +114,18 @@ def test_build_autotune_keeps_the_cheapest_over_level_work_values(monkeypatch):
     h2, rows2, k2 = ch.CH.build_autotune(g, hop_limits=(2, 5), route_degs=(64,))
     assert rec2.calls == 1 and k2 == 1 and rows2[1]["level_work"] is None and h2._h.value == 1001
     h2.close()
+
+
+def test_device_entry_points_reject_host_arrays():
+    import numpy as np
+    h = ch.CH.__new__(ch.CH)
+    h._h = None
+    with pytest.raises(ValueError):
+        h.one_to_all(np.zeros(3, np.uint32))
+    with pytest.raises(ValueError):
+        h.query_one_to_many(0, np.zeros(3, np.uint32))
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        h.one_to_all(torch.zeros(3, dtype=torch.int32))  # a CPU tensor
+    with pytest.raises(ValueError):
+        h.one_to_all(torch.zeros(3, dtype=torch.int64))
