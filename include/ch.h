@@ -131,7 +131,9 @@ typedef struct {
  *              dropped in the level before) has more than W out-edges in
  *              total is not run, and the labels of the level before are the
  *              result. Still upper bounds on real walks, so distances stay
- *              exact. 0 = no bound (the default).
+ *              exact. 0 = no bound (the default). A bound of 0 itself would
+ *              leave only the first hop level, which is the search of
+ *              hop_limit = 1: pass that instead.
  *   witness_prune  nonzero: after each round's rescoring searches, every
  *              overlay edge (s, v) heavier than the distance recorded for a
  *              pair (s, v) of those searches is deleted (Alg. 3's last step),
@@ -254,8 +256,10 @@ int ch_query_batch_host(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint
  * device share the array, which keeps the last call's contents (the call
  * clears the counters it needs): calls whose work overlaps on the GPU race
  * on it, so serialise them (one stream, or events), across handles too.
- * Errors: CH_ERANGE when k > CH_STATIC_QUERY_MAX; ids >= n are reported by
- * ch_query_status as for ch_query_batch. */
+ * The hierarchy's device must be the current device (the scratch address is
+ * resolved per current device). Errors: CH_ERANGE when
+ * k > CH_STATIC_QUERY_MAX; CH_EINVAL when another device is current; ids >= n
+ * are reported by ch_query_status as for ch_query_batch. */
 int ch_query_batch_static(ch_t *ch, const uint32_t *src, const uint32_t *dst, uint64_t k,
                           uint32_t *dist_out, void *stream);
 
@@ -438,6 +442,15 @@ int ch_mlp_train(const int64_t *rows, const float *labels, uint64_t n,
                  const ch_train_params_t *tp, float *weights_io, float *loss_out,
                  float *grad_out, void *stream);
 
+/* Training targets of trace rows on the device (not in the paper; the
+ * learned priority's label): y_out[r] = sign(x) * log2(1 + |x|) with
+ * x = edge difference + 2 * hierarchy depth of row r (its features 4 and 6),
+ * the same transform the features get. The network learns this score; the
+ * transform is monotone, so the priority it gives orders vertices as the
+ * score does. rows (n x 14 int64) and y_out (n floats) are DEVICE pointers;
+ * asynchronous on `stream`. */
+int ch_mlp_targets(const int64_t *rows, uint64_t n, float *y_out, void *stream);
+
 /* MLP outputs for trace rows on the device (the inference the learned
  * priority runs, before scaling by 1024): rows (n x 14 int64, device),
  * weights (host, CH_MLP_NPARAM floats), y_out (device, n floats). */
@@ -456,8 +469,13 @@ int ch_mlp_forward(const float *weights, const int64_t *rows, uint64_t n, float 
  * ring holds `ring` requests; ch_server_submit returns CH_EAGAIN when
  * either is full (poll completed requests, then retry). Each answer equals
  * what ch_query_batch returns for the same pair. The kernel's idle wait is
- * bounded by idle_ms: after that long without a request it ends, and later
- * submits return CH_ETIMEOUT. The handle `ch` must outlive the server. */
+ * bounded by idle_ms: after that long without a published request it ends
+ * (its blocks take only published work, so nothing is lost), and the next
+ * submit, poll or replay launches it again. Calls that synchronise the
+ * whole device (cudaFree, cudaDeviceSynchronize, ch_free of any hierarchy,
+ * ...) wait for the running loop, so in the same process they return only
+ * after it has ended at the idle limit; keep them out of serving windows or
+ * choose a short idle_ms. The handle `ch` must outlive the server. */
 typedef struct {
     uint32_t blocks;   /* blocks of the device loop; 0 = as many as are resident at once */
     uint32_t ring;     /* requests in flight at most */
@@ -472,6 +490,12 @@ int ch_server_start(ch_t *ch, const ch_server_params_t *params, ch_server_t **ou
 
 /* Number of blocks the device loop runs (after the default is resolved). */
 uint32_t ch_server_blocks(const ch_server_t *sv);
+
+/* 1 while the device loop's kernel runs, 0 when it has ended at the idle
+ * limit (or the server was stopped); the next submit, poll or replay
+ * launches it again. CH_ECUDA (with the loop's state in ch_last_error) if
+ * it ended on a failed check. */
+int ch_server_running(ch_server_t *sv);
 
 /* Copies the k targets (host memory) and publishes the request; *ticket
  * identifies it for ch_server_poll. */
@@ -497,7 +521,8 @@ int ch_server_replay(ch_server_t *sv, uint64_t nreq, const uint32_t *src, const 
 
 /* Stops the device loop once every published request is served (a bounded
  * wait) and frees the server. Returns CH_ECUDA if an index or capacity
- * check failed in the device loop during the server's life. */
+ * check failed in the device loop during the server's life, or a published
+ * entry never matched its request. */
 int ch_server_stop(ch_server_t *sv);
 
 void ch_free(ch_t *ch);

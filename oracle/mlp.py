@@ -39,6 +39,15 @@ def transform(f):
     return (np.sign(f) * np.log2(1.0 + np.abs(f))).astype(np.float32).astype(np.float64)
 
 
+def targets(rows):
+    """Training target of trace rows (round, vertex, 12 features): the
+    transformed score x = edge difference + 2 * hierarchy depth, features 4
+    and 6 of the row (the learned-priority label reading), float64 of the
+    float32 value."""
+    r = np.asarray(rows, dtype=np.int64)
+    return transform(r[:, 2 + 4] + 2 * r[:, 2 + 6])
+
+
 def bf16(x):
     """Round to the nearest bfloat16 value (ties to even), returned as float64."""
     a = np.asarray(x, dtype=np.float32)

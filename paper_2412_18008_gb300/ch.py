@@ -135,7 +135,8 @@ def load(build_if_missing: bool = True):
     lib.ch_export_trace.argtypes = [P, P, P, P]
     lib.ch_mlp_train.argtypes = [P, P, C.c_uint64, C.POINTER(TrainT), P, P, P, P]
     lib.ch_mlp_forward.argtypes = [P, P, C.c_uint64, P, P]
-    for f in ("ch_export_trace", "ch_mlp_train", "ch_mlp_forward"):
+    lib.ch_mlp_targets.argtypes = [P, C.c_uint64, P, P]
+    for f in ("ch_export_trace", "ch_mlp_train", "ch_mlp_forward", "ch_mlp_targets"):
         getattr(lib, f).restype = C.c_int
     lib.ch_server_start.argtypes = [P, C.POINTER(ServerParamsT), C.POINTER(P)]
     lib.ch_server_submit.argtypes = [P, C.c_uint32, P, C.c_uint32, C.POINTER(C.c_uint64)]
@@ -144,6 +145,8 @@ def load(build_if_missing: bool = True):
     lib.ch_server_stop.argtypes = [P]
     lib.ch_server_blocks.argtypes = [P]
     lib.ch_server_blocks.restype = C.c_uint32
+    lib.ch_server_running.argtypes = [P]
+    lib.ch_server_running.restype = C.c_int
     for f in ("ch_server_start", "ch_server_submit", "ch_server_poll", "ch_server_replay",
               "ch_server_stop"):
         getattr(lib, f).restype = C.c_int
@@ -258,6 +261,10 @@ class CH:
             g.on_device = 0
             st = C.c_void_p(None) if stream is None else _stream_ptr(stream)
         p = default_params()
+        # a level-work bound of 0 leaves only the first hop level, which is
+        # the search of hop limit 1; the ABI's 0 means "no bound"
+        if witness_level_work is not None and int(witness_level_work) == 0:
+            hop_limit, witness_level_work = min(int(hop_limit), 1), None
         p.hop_limit = hop_limit
         p.tie_break = tie_break
         p.tie_seed = tie_seed & 0xFFFFFFFF
@@ -299,7 +306,8 @@ class CH:
         ``witness_memo_limit`` memoises witness distances across rounds and
         clears them after a round that leaves more pairs; None = off.
         ``witness_level_work`` skips a hop level (from the second on) whose
-        frontier has more out-edges than that; None = off. ``witness_prune``
+        frontier has more out-edges than that (0 runs the first level only,
+        as hop limit 1 does); None = off. ``witness_prune``
         deletes overlay edges heavier than their pair's witness distance
         after each round's rescoring searches. ``witness_settle_cap`` (θ)
         replaces the hop-limited search by Alg. 3's Dijkstra capped at θ
@@ -325,10 +333,12 @@ class CH:
         as a third dimension (one ch_build_autotune call per value; None =
         no bound). Returns (CH, rows as dicts with their ``level_work``,
         chosen index)."""
-        hl = np.ascontiguousarray(hop_limits, dtype=np.uint32)
         rd = np.ascontiguousarray(route_degs, dtype=np.uint32)
         best, out, best_i = None, [], 0
         for lw in level_works:
+            # level work 0 is the search of hop limit 1 (see _marshal)
+            hl = (np.unique(np.minimum(np.ascontiguousarray(hop_limits, dtype=np.uint32), 1))
+                  if lw is not None and int(lw) == 0 else np.ascontiguousarray(hop_limits, dtype=np.uint32))
             g, p, keep = cls._marshal(graph, n, offsets, targets, weights, 5, tie_break, tie_seed,
                                       stream, mlp_weights, False, max_candidates_per_vertex, 0,
                                       witness_ball_limit, None, lw)
@@ -570,7 +580,7 @@ class Server:
     """Query server (continuous batching) over a built hierarchy."""
 
     def __init__(self, ch: CH, blocks: int = 0, ring: int = 1 << 14, pool: int = 1 << 22,
-                 idle_ms: int = 5000):
+                 idle_ms: int = 1000):
         self._ch = ch
         p = ServerParamsT(blocks, ring, pool, idle_ms, 0)
         self._h = C.c_void_p()
@@ -581,6 +591,15 @@ class Server:
     def blocks(self) -> int:
         """Blocks of the device loop."""
         return int(load().ch_server_blocks(self._h))
+
+    def running(self) -> bool:
+        """ch_server_running: whether the device loop's kernel runs now (it
+        ends after idle_ms without requests and is launched again by the next
+        submit or poll)."""
+        rc = load().ch_server_running(self._h)
+        if rc < 0:
+            _check(rc)
+        return rc == 1
 
     def submit(self, s: int, targets) -> int | None:
         """Ticket of the published request, or None when the server is full."""
@@ -635,16 +654,23 @@ class Server:
             pass
 
 
-def training_labels(rows) -> np.ndarray:
-    """Target of each trace row (float32): sign(x) * log2(1 + |x|) of the
-    score x = edge difference + 2 * hierarchy depth at that rescoring. The
-    network learns this score from the 12 (equally transformed) features;
-    the transform is monotone, so the learned priority orders vertices as
-    the score does. On road-like graphs the score yields shallower
-    hierarchies with smaller search spaces than the edge difference alone."""
-    rows = np.asarray(rows)
-    x = (rows[:, 2 + 4] + 2 * rows[:, 2 + 6]).astype(np.float64)
-    return (np.sign(x) * np.log2(1.0 + np.abs(x))).astype(np.float32)
+def training_labels(rows, stream=None) -> np.ndarray:
+    """ch_mlp_targets: the training target of each trace row (float32),
+    computed on the device from the row's edge difference and hierarchy
+    depth. ``rows`` is a host int64 array [n, 14] or a CUDA tensor; the
+    result is a host array for host input, else a CUDA tensor."""
+    import torch
+    on_host = not isinstance(rows, torch.Tensor)
+    d = torch.from_numpy(np.ascontiguousarray(rows, dtype=np.int64)).cuda() if on_host else rows
+    if d.dtype != torch.int64 or d.dim() != 2 or d.shape[1] != 14 or not d.is_cuda:
+        raise ValueError("rows must be an int64 [n, 14] array")
+    d = d.contiguous()
+    y = torch.empty(d.shape[0], dtype=torch.float32, device=d.device)
+    _check(load().ch_mlp_targets(d.data_ptr(), d.shape[0], y.data_ptr(), _stream_ptr(stream)))
+    if on_host:
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return y.cpu().numpy()
+    return y
 
 
 def mlp_init(seed: int = 0, scale: float = 0.3) -> np.ndarray:

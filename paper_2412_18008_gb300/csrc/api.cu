@@ -559,6 +559,16 @@ int ch_mlp_train(const int64_t *rows, const float *labels, uint64_t n, const ch_
     });
 }
 
+int ch_mlp_targets(const int64_t *rows, uint64_t n, float *y_out, void *stream) {
+    if (n && (!rows || !y_out)) {
+        g_last_error = "bad target arguments";
+        return CH_EINVAL;
+    }
+    return guarded([&] {
+        mlp_targets(reinterpret_cast<const long long *>(rows), n, y_out, (cudaStream_t)stream);
+    });
+}
+
 int ch_mlp_forward(const float *weights, const int64_t *rows, uint64_t n, float *y_out,
                    void *stream) {
     if (!weights || (n && (!rows || !y_out))) {
@@ -599,6 +609,16 @@ int ch_server_start(ch_t *ch, const ch_server_params_t *params, ch_server_t **ou
 
 uint32_t ch_server_blocks(const ch_server_t *sv) { return sv ? server_blocks(sv) : 0; }
 
+int ch_server_running(ch_server_t *sv) {
+    if (!sv) {
+        g_last_error = "no server";
+        return CH_EINVAL;
+    }
+    int r = 0;
+    const int rc = guarded([&] { r = server_running(sv); });
+    return rc != CH_OK ? rc : r;
+}
+
 int ch_server_submit(ch_server_t *sv, uint32_t s, const uint32_t *targets, uint32_t k,
                      uint64_t *ticket) {
     if (!sv || !targets || !ticket || k == 0) {
@@ -609,7 +629,6 @@ int ch_server_submit(ch_server_t *sv, uint32_t s, const uint32_t *targets, uint3
     const int g = guarded([&] { rc = server_submit(sv, s, targets, k, ticket); });
     if (g != CH_OK) return g;
     if (rc == CH_EAGAIN) g_last_error = "server full";
-    if (rc == CH_ETIMEOUT) g_last_error = "server kernel has ended (idle limit)";
     return rc;
 }
 
@@ -648,6 +667,10 @@ int ch_server_stop(ch_server_t *sv) {
     if (rc != CH_OK) return rc;
     if (status & 2u) {
         g_last_error = "index or capacity check failed in the server loop";
+        return CH_ECUDA;
+    }
+    if (status & 4u) {
+        g_last_error = "a published pool entry never matched its request in the server loop";
         return CH_ECUDA;
     }
     return CH_OK;

@@ -123,6 +123,8 @@ bool server_poll(ch_server_s *sv, uint64_t ticket, uint32_t *out, uint64_t *dev_
 int server_stop(ch_server_s *sv, uint32_t *status);
 void server_free(ch_server_s *sv);
 uint32_t server_blocks(const ch_server_s *sv);
+std::string server_state(ch_server_s *sv);
+int server_running(ch_server_s *sv);
 void server_replay(ch_server_s *sv, uint64_t nreq, const uint32_t *src, const uint32_t *k,
                    const uint64_t *toff, const uint32_t *targets, const uint64_t *arrival_ns,
                    uint32_t *answers, uint64_t *latency_ns, uint64_t *service_ns, double limit_s);

@@ -288,7 +288,22 @@ __global__ void k_rows_to_x(const long long *rows, uint64_t n, float *x) {
     }
 }
 
+// Training target of trace rows: the transformed score
+// x = edge difference + 2 * hierarchy depth (features 4 and 6).
+__global__ void k_targets(const long long *rows, uint64_t n, float *y) {
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
+         r += (uint64_t)gridDim.x * blockDim.x)
+        y[r] = feature_transform(rows[r * 14 + 2 + 4] + 2 * rows[r * 14 + 2 + 6]);
+}
+
 }  // namespace
+
+void mlp_targets(const long long *rows, uint64_t n, float *y, cudaStream_t st) {
+    if (n == 0) return;
+    const uint64_t blocks = std::min<uint64_t>((n + 255) / 256, (uint64_t)device_sm_count() * 8);
+    k_targets<<<(unsigned)blocks, 256, 0, st>>>(rows, n, y);
+    CH_CHECK_LAUNCH();
+}
 
 // ---------------------------------------------------------------------------
 

@@ -32,6 +32,10 @@ struct MlpDevice {
 // x[r] = transformed features of trace rows (round, vertex, 12 features).
 void rows_to_features(const long long *rows, uint64_t n, float *x, cudaStream_t st);
 
+// y[r] = training target of trace row r: sign(x) * log2(1 + |x|) of
+// x = edge difference + 2 * hierarchy depth at that rescoring.
+void mlp_targets(const long long *rows, uint64_t n, float *y, cudaStream_t st);
+
 // Adam training (or, with epochs = 0, the gradient of the first batch).
 void mlp_train(const long long *rows, const float *labels, uint64_t n, const ch_train_params_t *tp,
                float *weights_io, float *loss_out, float *grad_out, cudaStream_t st);

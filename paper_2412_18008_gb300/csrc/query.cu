@@ -580,6 +580,10 @@ void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint6
     if (k > CH_STATIC_QUERY_MAX)
         throw Error{CH_ERANGE, "batch larger than CH_STATIC_QUERY_MAX queries"};
     if (k == 0) return;
+    int dev = 0;
+    CH_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != h->device)
+        throw Error{CH_EINVAL, "the current device is not the hierarchy's device"};
     uint32_t *scratch = static_scratch();
     const size_t sn = (size_t)h->q_slots * std::max<uint32_t>(h->n, 1);
     QDense dn;

@@ -26,7 +26,9 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <new>
 #include <thread>
 
@@ -59,15 +61,36 @@ struct SvArgs {
     unsigned long long *t_begin, *t_end;  // mapped ring: device time (ns)
     uint32_t ring;
     uint64_t pool;
-    unsigned long long *claimed;  // device: next pool position to take
+    unsigned long long *claimed;  // device: pool positions taken so far (all published)
     uint32_t *finished;           // device: targets served per ring slot
-    uint32_t *closing;            // device: set once a block reached the idle limit
-    unsigned *status;             // device: 1 = idle limit reached, 2 = index or capacity check failed
+    uint32_t *closing;            // device: epoch of the launch a block closed
+    uint32_t epoch;               // this launch (1, 2, ...)
+    unsigned *status;             // device: SV_IDLE | QERR_BOUND | SV_UNMATCHED
+    unsigned long long *diag;     // device: the first failure (SvDiag layout)
     unsigned long long idle_ns;
     // per-block fallback tables (global memory)
     uint32_t tbits;               // table of 2^tbits slots
     uint32_t fcap;                // frontier capacity
     uint32_t *key, *df, *db, *fst, *front, *touched;
+};
+
+// Status bits of the device loop (QERR_BOUND = 2 is an index check).
+constexpr unsigned SV_IDLE = 1u;       // a launch ended after the idle limit without a published position
+constexpr unsigned SV_UNMATCHED = 4u;  // a published entry never matched its descriptor
+
+// What the loop saw when it gave up, for the host's messages: the first
+// idle exit (words [0, DG_ERR)) and the last failure (words [DG_ERR, 2 DG_ERR)).
+enum SvDiag : int {
+    DG_CODE = 0,  // SV_IDLE or SV_UNMATCHED (0: none)
+    DG_POS,       // idle: the claim counter; failure: the position taken
+    DG_PUB,       // the published count last read
+    DG_CLAIMED,   // idle: the launch epoch; failure: the claim counter
+    DG_ITEM,      // failure: the entry's ticket + 1
+    DG_SEQ,       // failure: the descriptor's ticket
+    DG_DPOS,      // failure: the descriptor's first position
+    DG_DK,        // failure: the descriptor's target count
+    DG_ERR,       // offset of the failure record
+    DG_WORDS = 2 * DG_ERR
 };
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -281,75 +304,99 @@ __global__ void __launch_bounds__(QB_THREADS) k_serve(SvArgs a) {
     t.fcap = a.fcap;
     while (true) {
         __syncthreads();
-        // thread 0 takes the next pool position and waits (boundedly) until
-        // the host has published it
+        // Thread 0 takes the next published pool position. A position is
+        // taken only once the host has published it, so a block that gives
+        // up waiting holds nothing: after the idle limit the first block to
+        // reach it closes this launch, every block leaves at its next look,
+        // and what is published later waits for the host to launch the loop
+        // again.
         if (tid == 0) {
             s_go = 0;
-            if (!*(volatile uint32_t *)a.closing) {
-                const unsigned long long pos = atomicAdd(a.claimed, 1ull);
-                const unsigned long long t0 = globaltimer();
-                unsigned sleep_ns = 256;
-                while (true) {
-                    if (ld_acquire_sys(&a.ctl->published) > pos) {
+            const unsigned long long t0 = globaltimer();
+            unsigned sleep_ns = 256;
+            unsigned long long pos = 0;
+            while (true) {
+                if (*(volatile uint32_t *)a.closing == a.epoch) break;
+                const unsigned long long pub = ld_acquire_sys(&a.ctl->published);
+                const unsigned long long c = *(volatile unsigned long long *)a.claimed;
+                if (c < pub) {
+                    if (atomicCAS(a.claimed, c, c + 1ull) == c) {
+                        pos = c;
                         s_go = 1;
                         break;
                     }
-                    // stop is set after the last publication: look again first
-                    if (ld_acquire_sys(&a.ctl->stop)) {
-                        s_go = ld_acquire_sys(&a.ctl->published) > pos;
-                        break;
-                    }
-                    if (*(volatile uint32_t *)a.closing) break;
-                    if (globaltimer() - t0 > a.idle_ns) {
-                        atomicOr(a.status, 1u);
-                        atomicExch(a.closing, 1u);
-                        break;
-                    }
-                    __nanosleep(sleep_ns);
-                    sleep_ns = min(2u * sleep_ns, 8192u);
+                    continue;  // another block took it: look again at once
                 }
-                if (s_go) {
-                    // The entry names its request (ticket + 1); the request's
-                    // descriptor must carry that ticket and cover this
-                    // position. Both were written before the publication, so
-                    // they match at once; the bounded re-read only guards
-                    // against seeing them late.
-                    const uint64_t e = pos % a.pool;
-                    const unsigned long long t1 = globaltimer();
-                    s_go = 2;  // skip the entry unless it validates
-                    while (true) {
-                        const uint32_t v = ld_sys(a.item_req + e);
-                        if (v != 0) {
-                            const uint32_t slot = (v - 1) % a.ring;
-                            const SvDesc *d = a.desc + slot;
-                            const uint64_t dseq = ld_sys(&d->seq), dpos = ld_sys(&d->pos);
-                            const uint32_t dk = ld_sys(&d->k);
-                            if ((uint32_t)(dseq + 1) == v && dpos <= pos && pos < dpos + dk) {
-                                s_src = ld_sys(&d->s);
-                                s_k = dk;
-                                s_seq = dseq;
-                                s_first = dpos == pos;
-                                s_tgt = ld_sys(a.targets + e);
-                                s_slot = slot;
-                                s_e = e;
-                                if (s_first) a.t_begin[slot] = globaltimer();
-                                s_go = 1;
-                                break;
-                            }
-                        }
-                        if (globaltimer() - t1 > 1000000000ull) {  // 1 s: report and skip
-                            atomicOr(a.status, QERR_BOUND);
+                // stop is set after the last publication: look again first
+                if (ld_acquire_sys(&a.ctl->stop)) {
+                    if (*(volatile unsigned long long *)a.claimed < ld_acquire_sys(&a.ctl->published)) continue;
+                    break;
+                }
+                if (globaltimer() - t0 > a.idle_ns) {
+                    if (atomicCAS(&a.diag[DG_CODE], 0ull, (unsigned long long)SV_IDLE) == 0ull) {
+                        a.diag[DG_POS] = c;
+                        a.diag[DG_PUB] = pub;
+                        a.diag[DG_CLAIMED] = a.epoch;
+                    }
+                    atomicOr(a.status, SV_IDLE);
+                    atomicExch(a.closing, a.epoch);
+                    break;
+                }
+                __nanosleep(sleep_ns);
+                sleep_ns = min(2u * sleep_ns, 8192u);
+            }
+            if (s_go) {
+                // The entry names its request (ticket + 1); the request's
+                // descriptor must carry that ticket and cover this position.
+                // Both were written before the publication, so they match at
+                // once; the re-read only guards against seeing them late. A
+                // taken position is never dropped: a block that cannot match
+                // it within the idle limit records what it saw and fails the
+                // loop, which the host reports.
+                const uint64_t e = pos % a.pool;
+                const unsigned long long t1 = globaltimer();
+                uint32_t v = 0, dk = 0;
+                uint64_t dseq = 0, dpos = 0;
+                while (true) {
+                    v = ld_sys(a.item_req + e);
+                    if (v != 0) {
+                        const uint32_t slot = (v - 1) % a.ring;
+                        const SvDesc *d = a.desc + slot;
+                        dseq = ld_sys(&d->seq);
+                        dpos = ld_sys(&d->pos);
+                        dk = ld_sys(&d->k);
+                        if ((uint32_t)(dseq + 1) == v && dpos <= pos && pos < dpos + dk) {
+                            s_src = ld_sys(&d->s);
+                            s_k = dk;
+                            s_seq = dseq;
+                            s_first = dpos == pos;
+                            s_tgt = ld_sys(a.targets + e);
+                            s_slot = slot;
+                            s_e = e;
+                            if (s_first) a.t_begin[slot] = globaltimer();
                             break;
                         }
-                        __nanosleep(256);
                     }
+                    if (globaltimer() - t1 > a.idle_ns) {
+                        a.diag[DG_ERR + DG_CODE] = SV_UNMATCHED;
+                        a.diag[DG_ERR + DG_POS] = pos;
+                        a.diag[DG_ERR + DG_PUB] = ld_sys(&a.ctl->published);
+                        a.diag[DG_ERR + DG_CLAIMED] = *(volatile unsigned long long *)a.claimed;
+                        a.diag[DG_ERR + DG_ITEM] = v;
+                        a.diag[DG_ERR + DG_SEQ] = dseq;
+                        a.diag[DG_ERR + DG_DPOS] = dpos;
+                        a.diag[DG_ERR + DG_DK] = dk;
+                        atomicOr(a.status, SV_UNMATCHED);
+                        atomicExch(a.closing, a.epoch);
+                        s_go = 0;
+                        break;
+                    }
+                    __nanosleep(256);
                 }
             }
         }
         __syncthreads();
-        const uint32_t go = s_go;
-        if (!go) break;
-        if (go != 1) continue;
+        if (!s_go) break;
         const uint32_t s = s_src, tv = s_tgt;
         uint32_t ans = INF;
         if (s < g.n && tv < g.n) {
@@ -420,15 +467,29 @@ struct ch_server_s {
     gbch::DevBuf<unsigned long long> claimed;
     gbch::DevBuf<uint32_t> finished, closing;
     gbch::DevBuf<unsigned> status;
+    gbch::DevBuf<unsigned long long> diag;
     // host-side ring and pool state
     uint64_t next_seq = 0, retired = 0, pool_head = 0, pool_tail = 0;
     std::vector<uint64_t> slot_pos;
     std::vector<uint32_t> slot_k;
     std::vector<char> consumed;
     bool running = false;
+    // the loop's launch: kernel, block size and arguments; a launch that
+    // ended at the idle limit is launched again (next epoch) when needed
+    gbch::SvArgs args{};
+    void (*kern)(gbch::SvArgs) = nullptr;
+    int threads = 0;
+    uint32_t launches = 0;
 };
 
 namespace gbch {
+
+// Launches the device loop for the next epoch.
+void server_launch(ch_server_s *sv) {
+    sv->args.epoch = ++sv->launches;
+    sv->kern<<<sv->nblocks, sv->threads, sizeof(QBSmem<12>), sv->st>>>(sv->args);
+    CH_CHECK_LAUNCH();
+}
 
 void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     sv->h = h;
@@ -475,6 +536,8 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     sv->closing.zero(sv->st);
     sv->status.alloc(1);
     sv->status.zero(sv->st);
+    sv->diag.alloc(DG_WORDS);
+    sv->diag.zero(sv->st);
     SvArgs a{};
     a.q.n = h->n;
     a.q.n_up = (uint32_t)h->n_up;
@@ -499,6 +562,7 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     a.finished = sv->finished.ptr;
     a.closing = sv->closing.ptr;
     a.status = sv->status.ptr;
+    a.diag = sv->diag.ptr;
     a.idle_ns = sv->idle_ns;
     a.tbits = tbits;
     a.fcap = (uint32_t)fcap;
@@ -508,8 +572,10 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     a.fst = base + 3 * T * NB;
     a.touched = base + 4 * T * NB;
     a.front = base + 5 * T * NB;
-    kern<<<sv->nblocks, threads, sizeof(QBSmem<12>), sv->st>>>(a);
-    CH_CHECK_LAUNCH();
+    sv->args = a;
+    sv->kern = kern;
+    sv->threads = threads;
+    server_launch(sv);
     sv->running = true;
 }
 
@@ -531,19 +597,71 @@ void pool_span(uint64_t P, uint64_t pos, uint64_t n, F &&f) {
     if (n1 < n) f(0, n1, n - n1);
 }
 
+// The loop's status word (device), read on the legacy stream, which does not
+// wait for the loop's non-blocking stream.
+unsigned server_status_word(ch_server_s *sv) {
+    unsigned st = 0;
+    CH_CUDA_TRY(cudaMemcpy(&st, sv->status.ptr, sizeof st, cudaMemcpyDeviceToHost));
+    return st;
+}
+
+// The loop's status word and records, with the host's ring and pool
+// counters, as one line for messages.
+std::string server_state(ch_server_s *sv) {
+    unsigned st = 0;
+    unsigned long long dg[DG_WORDS] = {};
+    if (cudaMemcpy(&st, sv->status.ptr, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(dg, sv->diag.ptr, sizeof dg, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return "device status unreadable";
+    }
+    const unsigned long long *e = dg + DG_ERR;
+    char buf[640];
+    std::snprintf(buf, sizeof buf,
+                  "device status %u (1 idle exit, 2 index check, 4 unmatched entry); launches %u; "
+                  "first idle exit: taken %llu published %llu epoch %llu; "
+                  "failure: code %llu pos %llu published %llu taken %llu entry %llu desc seq %llu pos %llu k %llu; "
+                  "host: next ticket %llu retired %llu pool head %llu tail %llu published %llu",
+                  st, sv->launches, dg[DG_POS], dg[DG_PUB], dg[DG_CLAIMED], e[DG_CODE], e[DG_POS], e[DG_PUB],
+                  e[DG_CLAIMED], e[DG_ITEM], e[DG_SEQ], e[DG_DPOS], e[DG_DK],
+                  (unsigned long long)sv->next_seq, (unsigned long long)sv->retired,
+                  (unsigned long long)sv->pool_head, (unsigned long long)sv->pool_tail,
+                  (unsigned long long)sv->ctl.h->published);
+    return buf;
+}
+
+// True while the loop's kernel runs.
+bool server_alive(ch_server_s *sv) {
+    const cudaError_t e = cudaStreamQuery(sv->st);
+    if (e == cudaErrorNotReady) return true;
+    if (e != cudaSuccess) throw Error{CH_ECUDA, std::string("server kernel: ") + cudaGetErrorString(e)};
+    return false;
+}
+
+// Makes sure the loop runs: a launch that ended at the idle limit is
+// launched again (its blocks held no position, so nothing was lost and the
+// device counters carry over). A launch that ended on a failed check is an
+// error, reported with the loop's state.
+void server_resume(ch_server_s *sv) {
+    if (server_alive(sv)) return;
+    const unsigned st = server_status_word(sv);
+    if (st & ~SV_IDLE) throw Error{CH_ECUDA, "server loop failed; " + server_state(sv)};
+    server_launch(sv);
+}
+
 int server_submit(ch_server_s *sv, uint32_t s, const uint32_t *targets, uint32_t k, uint64_t *ticket) {
     if (!sv->running) return CH_EINVAL;
     if (k == 0) return CH_EINVAL;
     if (sv->next_seq - sv->retired >= sv->ring) {
-        // full: make sure the kernel is still serving before asking to retry
-        const cudaError_t e = cudaStreamQuery(sv->st);
-        if (e == cudaSuccess) return CH_ETIMEOUT;
-        if (e != cudaErrorNotReady) throw Error{CH_ECUDA, cudaGetErrorString(e)};
+        server_resume(sv);  // full: the loop must be serving before the caller retries
         return CH_EAGAIN;
     }
     if (k > sv->pool) return CH_EINVAL;
     uint64_t pos = 0;
-    if (!pool_reserve(sv, k, pos)) return CH_EAGAIN;
+    if (!pool_reserve(sv, k, pos)) {
+        server_resume(sv);
+        return CH_EAGAIN;
+    }
     const uint64_t seq = sv->next_seq;
     const uint32_t slot = (uint32_t)(seq % sv->ring);
     pool_span(sv->pool, pos, k, [&](uint64_t e, uint64_t j, uint64_t n) {
@@ -560,13 +678,17 @@ int server_submit(ch_server_s *sv, uint32_t s, const uint32_t *targets, uint32_t
     std::atomic_thread_fence(std::memory_order_seq_cst);
     sv->next_seq = seq + 1;
     *ticket = seq;
+    server_resume(sv);
     return CH_OK;
 }
 
 bool server_poll(ch_server_s *sv, uint64_t ticket, uint32_t *out, uint64_t *dev_ns) {
     const uint32_t slot = (uint32_t)(ticket % sv->ring);
     if (ticket < sv->retired || ticket >= sv->next_seq) throw Error{CH_EINVAL, "unknown ticket"};
-    if (*(volatile uint32_t *)&sv->done.h[slot] != (uint32_t)(ticket + 1)) return false;
+    if (*(volatile uint32_t *)&sv->done.h[slot] != (uint32_t)(ticket + 1)) {
+        server_resume(sv);  // not served yet: the loop must be running
+        return false;
+    }
     std::atomic_thread_fence(std::memory_order_acquire);
     if (out)
         pool_span(sv->pool, sv->slot_pos[slot], sv->slot_k[slot], [&](uint64_t e, uint64_t j, uint64_t n) {
@@ -587,6 +709,9 @@ int server_stop(ch_server_s *sv, uint32_t *status) {
     if (!sv->running) return CH_OK;
     *(volatile uint32_t *)&sv->ctl.h->stop = 1;
     std::atomic_thread_fence(std::memory_order_seq_cst);
+    // a launch that ended idle is launched once more, so that what was
+    // published since is served; with stop set it ends once nothing is left
+    if (!server_alive(sv) && server_status_word(sv) == SV_IDLE) server_launch(sv);
     // bounded wait: the kernel ends once no request is left, or at the idle limit
     const auto t0 = std::chrono::steady_clock::now();
     const double limit_s = (double)sv->idle_ns * 1e-9 + 30.0;
@@ -599,18 +724,18 @@ int server_stop(ch_server_s *sv, uint32_t *status) {
         std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     sv->running = false;
-    CH_CUDA_TRY(cudaMemcpy(status, sv->status.ptr, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    *status = server_status_word(sv);
     return CH_OK;
 }
 
-bool server_alive(ch_server_s *sv) {
-    const cudaError_t e = cudaStreamQuery(sv->st);
-    if (e == cudaErrorNotReady) return true;
-    if (e != cudaSuccess) throw Error{CH_ECUDA, cudaGetErrorString(e)};
-    return false;
-}
-
 uint32_t server_blocks(const ch_server_s *sv) { return sv->nblocks; }
+
+int server_running(ch_server_s *sv) {
+    if (!sv->running) return 0;
+    if (server_alive(sv)) return 1;
+    if (server_status_word(sv) & ~SV_IDLE) throw Error{CH_ECUDA, "server loop failed; " + server_state(sv)};
+    return 0;
+}
 
 ch_server_s *server_new() { return new (std::nothrow) ch_server_s(); }
 void server_delete(ch_server_s *sv) { delete sv; }
@@ -644,7 +769,7 @@ void server_replay(ch_server_s *sv, uint64_t nreq, const uint32_t *src, const ui
         while (next < nreq && arrival_ns[next] <= now_ns()) {
             const int rc = server_submit(sv, src[next], targets + toff[next], k[next], &ticket[next]);
             if (rc == CH_EAGAIN) break;
-            if (rc != CH_OK) throw Error{rc, "server stopped serving during the replay"};
+            if (rc != CH_OK) throw Error{rc, "server refused a request during the replay; " + server_state(sv)};
             inflight.push_back(next);
             ++next;
         }
@@ -663,8 +788,8 @@ void server_replay(ch_server_s *sv, uint64_t nreq, const uint32_t *src, const ui
         }
         inflight.resize(w);
         if (std::chrono::duration<double>(clk::now() - t0).count() > limit_s)
-            throw Error{CH_ETIMEOUT, "replay exceeded its time limit"};
-        if (!server_alive(sv)) throw Error{CH_ETIMEOUT, "server kernel ended during the replay"};
+            throw Error{CH_ETIMEOUT, "replay exceeded its time limit; " + server_state(sv)};
+        server_resume(sv);
     }
 }
 

@@ -43,6 +43,120 @@ def test_reference_gradient_matches_finite_differences():
         assert abs(fd - g[i]) <= 1e-5 + 1e-3 * abs(g[i]), (i, fd, g[i])
 
 
+U_BF16 = 2.0 ** -7   # one BF16 unit, relative to the value (8 significant bits)
+U_F32 = 2.0 ** -24
+
+
+def _gamma(k):
+    """Relative error bound of a k-term float32 sum (or dot product)."""
+    return k * U_F32 / (1.0 - k * U_F32)
+
+
+def grad_error_bound(w, X, labels):
+    """Per-element bound on |g - g_ref| between a float32 implementation of
+    the MLP's loss gradient that rounds as the inference does (inputs, W1, W2
+    and the first hidden layer to BF16) and the float64 reference
+    M.loss_and_grad. First-order propagation of (a) float32 rounding of every
+    sum and (b) one BF16 unit of every first-hidden-layer value (its
+    pre-activation may round to the other neighbour), through the forward
+    pass and back; a ReLU whose input lies within its error of 0 may switch,
+    which adds the whole upstream term."""
+    W1, b1, W2, b2, W3, b3 = M.split(w)
+    q = M.bf16
+    x, W1q, W2q = q(X), q(W1), q(W2)
+    n = X.shape[0]
+    labels = np.asarray(labels, np.float64)
+    z1 = x @ W1q + b1
+    e_z1 = _gamma(M.NIN + 1) * (np.abs(x) @ np.abs(W1q) + np.abs(b1))
+    a1 = np.maximum(z1, 0.0)
+    h1 = q(a1)
+    d_h1 = np.where(z1 + e_z1 > 0, e_z1 + U_BF16 * (a1 + e_z1), 0.0)
+    m1, u1 = h1 > 0, np.abs(z1) <= e_z1
+    z2 = h1 @ W2q + b2
+    e_z2 = _gamma(M.NH + 1) * (np.abs(h1) @ np.abs(W2q) + np.abs(b2)) + d_h1 @ np.abs(W2q)
+    h2 = np.maximum(z2, 0.0)
+    d_h2 = np.where(z2 + e_z2 > 0, e_z2, 0.0)
+    m2, u2 = h2 > 0, np.abs(z2) <= e_z2
+    y = h2 @ W3 + b3
+    e_y = _gamma(M.NH + 1) * (np.abs(h2) @ np.abs(W3) + abs(b3)) + d_h2 @ np.abs(W3)
+    dy = 2.0 * (y - labels) / n
+    d_dy = 2.0 * (e_y + 2 * U_F32 * (np.abs(y) + np.abs(labels))) / n + 2 * U_F32 * np.abs(dy)
+    G = _gamma(n)
+    ady = np.abs(dy)
+    b_gW3 = d_h2.T @ ady + np.abs(h2).T @ d_dy + d_h2.T @ d_dy + G * (np.abs(h2).T @ ady)
+    b_gb3 = d_dy.sum() + G * ady.sum()
+    ag2 = np.abs(np.outer(dy, W3))
+    g2 = ag2 * m2
+    d_g2 = np.outer(d_dy, np.abs(W3)) * (m2 | u2) + u2 * ag2 + U_F32 * ag2
+    b_gW2 = d_h1.T @ g2 + np.abs(h1).T @ d_g2 + d_h1.T @ d_g2 + G * (np.abs(h1).T @ g2)
+    b_gb2 = d_g2.sum(0) + G * g2.sum(0)
+    pre1 = np.abs(np.outer(dy, W3) * m2) @ np.abs(W2q).T
+    e_pre1 = d_g2 @ np.abs(W2q).T + _gamma(M.NH) * pre1
+    d_g1 = e_pre1 * (m1 | u1) + u1 * pre1
+    ag1 = pre1 * m1
+    b_gW1 = np.abs(x).T @ d_g1 + G * (np.abs(x).T @ ag1)
+    b_gb1 = d_g1.sum(0) + G * ag1.sum(0)
+    return M.join(b_gW1, b_gb1, b_gW2, b_gb2, b_gW3, b_gb3)
+
+
+def _float32_grad(w, X, labels, mistake=None):
+    """The gradient computed in float32 with the inference's BF16 roundings
+    (a CPU stand-in for the GPU's arithmetic); `mistake` plants one error."""
+    f = np.float32
+    W1, b1, W2, b2, W3, b3 = (np.asarray(a, f) for a in M.split(w))
+    q = lambda a: M.bf16(a).astype(f)
+    x = q(X)
+    h1 = q(np.maximum(x @ q(W1) + b1, f(0)))
+    h2 = np.maximum(h1 @ q(W2) + b2, f(0))
+    y = h2 @ W3 + f(b3)
+    n = X.shape[0]
+    dy = (f(2) * (y - np.asarray(labels, f)) / f(n)).astype(f)
+    gW3, gb3 = h2.T @ dy, dy.sum(dtype=f)
+    g2 = np.outer(dy, W3) * (h2 > 0)
+    gW2, gb2 = h1.T @ g2, g2.sum(0)
+    g1 = (g2 @ q(W2).T) * (h1 > 0)
+    if mistake == "transposed W2":
+        g1 = (g2 @ q(W2)) * (h1 > 0)
+    gW1, gb1 = x.T @ g1, g1.sum(0)
+    if mistake == "b3 sign":
+        gb3 = -gb3
+    if mistake == "W3 from h1":
+        gW3 = h1.T @ dy
+    if mistake == "b2 dropped mask":
+        gb2 = np.outer(dy, W3).sum(0)
+    return M.join(gW1, gb1, gW2, gb2, gW3, gb3)
+
+
+def _trace_batch(n_rows=3000, seed=52):
+    och = O.build_ch(I.geometric_knn_graph(4_000, seed=seed), 5, trace=True)
+    rows = och.trace[:n_rows]
+    return M.transform(rows[:, 2:]), M.targets(rows).astype(np.float32)
+
+
+def test_gradient_bound_holds_for_float32_and_catches_mistakes():
+    X, lab = _trace_batch()
+    w = M.init_weights(3)
+    _, g_ref = M.loss_and_grad(w, X, lab.astype(np.float64))
+    bound = grad_error_bound(w, X, lab)
+    g32 = _float32_grad(w, X, lab).astype(np.float64)
+    assert (np.abs(g32 - g_ref) <= bound).all()
+    # the bound is tight enough to matter: below a tenth of |g| for most
+    assert np.median(bound / np.maximum(np.abs(g_ref), 1e-30)) < 0.1
+    for mistake in ("transposed W2", "b3 sign", "W3 from h1", "b2 dropped mask"):
+        bad = _float32_grad(w, X, lab, mistake).astype(np.float64)
+        assert (np.abs(bad - g_ref) > bound).any(), mistake
+
+
+def test_training_target_closed_forms():
+    # rows (round, vertex, S, |N_in|, |N_out|, |N|, ED, cn, depth, ...):
+    # the target is sign(x) * log2(1 + |x|) of x = ED + 2 * depth
+    rows = np.zeros((5, 14), np.int64)
+    rows[:, 2 + 4] = [0, 3, -7, 1, -2]   # edge difference
+    rows[:, 2 + 6] = [0, 2, 0, 7, 1]     # hierarchy depth
+    # x = 0, 7, -7, 15, 0
+    assert M.targets(rows).tolist() == [0.0, 3.0, -3.0, 4.0, 0.0]
+
+
 def test_round0_trace_features_recomputed():
     g = I.random_digraph(60, 200, 1, 20, seed=9)
     och = O.build_ch(g, 5, trace=True)
@@ -104,6 +218,20 @@ def _train_data(graphs):
 
 
 @gpu
+def test_training_targets_match_oracle():
+    torch = _torch()
+    och = O.build_ch(I.geometric_knn_graph(5_000, seed=50), 5, trace=True)
+    rows = och.trace
+    got = _ch().training_labels(rows)
+    want = M.targets(rows).astype(np.float32)
+    # both round log2 of the same integer to float32; allow one float32 unit
+    assert np.allclose(got, want, rtol=2.0 ** -23, atol=0)
+    # device input gives a device result, asynchronous on the stream
+    d = _ch().training_labels(torch.from_numpy(rows).cuda())
+    assert np.array_equal(d.cpu().numpy(), got)
+
+
+@gpu
 def test_mlp_forward_and_gradient_match_cpu_reference():
     torch = _torch()
     ch = _ch()
@@ -122,7 +250,10 @@ def test_mlp_forward_and_gradient_match_cpu_reference():
     grad, loss = ch.mlp_train(drows, dl, dw, epochs=0, batch=rows.shape[0])
     L_ref, g_ref = M.loss_and_grad(w, X, labels.astype(np.float64))
     g = grad.cpu().numpy().astype(np.float64)
-    assert np.linalg.norm(g - g_ref) <= 1e-2 * np.linalg.norm(g_ref)
+    # element by element, within the bound BF16 and float32 rounding allow
+    bound = grad_error_bound(w, X, labels)
+    bad = np.nonzero(np.abs(g - g_ref) > bound)[0]
+    assert bad.size == 0, (bad[:10], g[bad[:10]], g_ref[bad[:10]], bound[bad[:10]])
     assert abs(loss[0] - L_ref) <= 1e-3 * L_ref
 
 

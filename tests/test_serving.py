@@ -77,13 +77,38 @@ def test_admission_by_memory_and_ring(built):
     assert np.array_equal(ans, _expected(gch, src, ks, targets))
 
 
-def test_idle_limit_ends_the_loop(built):
+def test_idle_limit_ends_the_loop_and_a_request_resumes_it(built):
     g, gch = built
     ch = _ch()
     sv = ch.Server(gch, blocks=8, ring=64, pool=4096, idle_ms=200)
     time.sleep(1.0)
-    with pytest.raises(ch.CHError) as ei:
-        for _ in range(200):  # the ring fills only if the loop were still serving
-            sv.submit(0, [1])
-    assert ei.value.code == ch.CH_ETIMEOUT
+    assert not sv.running()  # ended at the idle limit, holding no work
+    tk = sv.submit(5, [1, 2, 3])
+    res = None
+    t0 = time.time()
+    while res is None and time.time() - t0 < 30:
+        res = sv.poll(tk, 3)
+    assert res is not None
+    assert np.array_equal(res, gch.query(np.full(3, 5, np.uint32), np.array([1, 2, 3], np.uint32)))
     sv.stop()
+
+
+def test_device_wide_synchronisation_during_serving(built):
+    """A device-wide synchronisation (cudaDeviceSynchronize, or the cudaFree
+    of another hierarchy) waits for the running loop, which ends at its idle
+    limit; requests submitted afterwards are served by a new launch, and
+    every answer equals the batch query's."""
+    torch = pytest.importorskip("torch")
+    g, gch = built
+    ch = _ch()
+    other = ch.CH.build(I.grid_graph(8, 8, 0.0, 1, 5, seed=3), hop_limit=5)
+    src, ks, targets = I.request_mix(g.n, 60, seed=76, one_to_many=0.5)
+    cut = int(ks[:30].sum())
+    zeros = np.zeros(30, np.uint64)
+    with ch.Server(gch, blocks=16, ring=64, pool=4096, idle_ms=300) as sv:
+        first, _, _ = sv.replay(src[:30], ks[:30], targets[:cut], zeros)
+        torch.cuda.synchronize()  # returns once the loop has ended
+        assert not sv.running()
+        other.close()
+        rest, _, _ = sv.replay(src[30:], ks[30:], targets[cut:], zeros)
+    assert np.array_equal(np.concatenate([first, rest]), _expected(gch, src, ks, targets))
