@@ -1979,8 +1979,11 @@ __global__ void k_emit_ch(Dev d, const uint32_t *F, uint32_t nF, uint2 *ch_up, u
     }
 }
 
-// Stable in-place removal of this round's contracted vertices from a list,
-// by one warp (32 entries per step; writes never pass the reads).
+constexpr uint32_t TOMB = 0xFFFFFFFFu;  // a pruned adjacency entry (never a vertex id)
+
+// Stable in-place removal, by one warp, of this round's contracted vertices
+// and of pruned entries (tombstones) from a list (32 entries per step;
+// writes never pass the reads).
 __device__ __forceinline__ uint32_t warp_compact_list(const Dev &d, uint2 *adj, uint64_t b, uint32_t dg,
                                                       uint32_t r) {
     const uint32_t lane = lane_id();
@@ -1991,7 +1994,7 @@ __device__ __forceinline__ uint32_t warp_compact_list(const Dev &d, uint2 *adj, 
         bool keep = false;
         if (j < dg) {
             e = adj[b + j];
-            keep = id_ok(d, e.x) && d.level[e.x] != r;
+            keep = e.x != TOMB && id_ok(d, e.x) && d.level[e.x] != r;
         }
         const uint32_t m = __ballot_sync(FULL, keep);
         if (keep) adj[b + k + __popc(m & ((1u << lane) - 1u))] = e;
@@ -2004,8 +2007,6 @@ __device__ __forceinline__ uint32_t warp_compact_list(const Dev &d, uint2 *adj, 
 // --------------------------------------------------------------------------
 // Pruning of overlay edges (Alg. 3's last step), after the rescoring searches
 // --------------------------------------------------------------------------
-
-constexpr uint32_t TOMB = 0xFFFFFFFFu;  // a pruned adjacency entry (fails id_ok)
 
 // One warp per rescoring source s: every pair (s, v) of the step (v in
 // N_out(u), u an affected out-neighbour of s, v != s) whose overlay edge

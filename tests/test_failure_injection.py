@@ -24,7 +24,6 @@ def test_setting_and_reset_make_no_cuda_call():
 
 
 @pytest.mark.gpu
-@pytest.mark.skip(reason="the injection hook is written but has not yet run on a GPU")
 def test_every_build_allocation_can_fail_cleanly():
     import torch
     from tests.test_gpu_parity import assert_same_hierarchy
@@ -59,7 +58,6 @@ def test_every_build_allocation_can_fail_cleanly():
 
 
 @pytest.mark.gpu
-@pytest.mark.skip(reason="the injection hook is written but has not yet run on a GPU")
 def test_query_allocation_failure_leaves_the_handle_usable():
     ch = _ch()
     g = I.grid_graph(20, 20, 0.1, 1, 20, seed=142)

@@ -57,12 +57,14 @@ def assert_same_queries(gch, och, s, t):
 @pytest.mark.parametrize("name", golden_names())
 def test_golden_examples(name):
     spec = load_golden(name)
-    if spec.get("theta") or spec.get("prune") or "level_work" in spec:
-        pytest.skip("the settled-vertex cap, pruning and the level-work bound have not yet run on a GPU")
     tie = 1 if spec.get("tie_break") == "id" else 0
     g = ch_mod().CH.build(spec["graph"], hop_limit=spec["hop_limit"], tie_break=tie,
                           max_candidates_per_vertex=spec.get("cmax"),
-                          witness_ball_limit=spec.get("ball"))
+                          witness_ball_limit=spec.get("ball"),
+                          witness_memo_limit=spec.get("memo"),
+                          witness_level_work=spec.get("level_work"),
+                          witness_prune=bool(spec.get("prune")),
+                          witness_settle_cap=spec.get("theta"))
     ex = g.export()
     assert ex["level"].tolist() == spec["expect_level"]
     assert ex["priority"].tolist() == spec["expect_priority"]

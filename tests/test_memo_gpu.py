@@ -14,8 +14,7 @@ from paper_2412_18008_gb300 import inputs as I
 from tests.graphs import all_pairs_truth, small_families
 from tests.test_gpu_parity import assert_same_hierarchy
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="the memo, level-work, pruning and settled-cap kernels are written but have not yet run on a GPU")]
+pytestmark = pytest.mark.gpu
 
 
 def _ch():

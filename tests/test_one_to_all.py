@@ -10,8 +10,7 @@ import oracle as O
 from paper_2412_18008_gb300 import inputs as I
 from tests.graphs import all_pairs_truth, small_families
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="ch_one_to_all is written but has not yet run on a GPU")]
+pytestmark = pytest.mark.gpu
 
 
 def _ch():
