@@ -132,6 +132,8 @@ def parse():
                          "vertices, in place of the hop-limited search (default: off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the learned-priority (1M) and 16M serving records of the default line")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default query kernel configuration")
     ap.add_argument("--build-only", action="store_true",
@@ -218,64 +220,119 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_sample_build(workload: str, hop_limit: int, cmax, ball=None, threads: bool = False,
-                     memo=None, level_work=None, prune=False, theta=None):
-    """Oracle build on a sample graph of the same family, scaled linearly
-    (by vertex count) to the full workload. Returns (scaled_s, raw_s,
-    threads used, sample vertices). threads: the -DORACLE_THREADS build,
-    whose witness searches run on every host thread."""
+def host_info():
+    """Host cores and CPU model (from /proc/cpuinfo: 'model name' on x86,
+    implementer/part ids on Arm)."""
+    import platform
+    info = {"nproc": os.cpu_count(), "machine": platform.machine()}
+    model = None
+    try:
+        fields = {}
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k, v = k.strip().lower(), v.strip()
+                if k in ("model name", "cpu implementer", "cpu part") and k not in fields:
+                    fields[k] = v
+        model = fields.get("model name") or (
+            f"implementer {fields.get('cpu implementer')} part {fields.get('cpu part')}"
+            if fields else None)
+    except OSError:
+        pass
+    info["cpu_model"] = model
+    return info
+
+
+def oracle_sample_sizes(workload: str):
+    """Two sample graphs of the workload's family (the smaller first): the
+    oracle is timed on both and the time extrapolated to the workload along
+    the power law through the two points."""
+    n = WORKLOADS[workload][0]
+    if workload.startswith("rmat"):
+        return [(1 << sc, lambda sc=sc: I.rmat_graph(scale=sc, nsamples=16 << sc, wmax=1000, seed=7))
+                for sc in (11, 12)]
+    return [(k, lambda k=k: I.geometric_knn_graph(k, seed=7)) for k in (min(n, 100_000), min(n, 200_000))]
+
+
+def oracle_build_s(g, args, threads=False):
     import oracle as O
-    g = make_graph(workload, sample=True)
     t0 = time.perf_counter()
-    O.build_ch(g, hop_limit, cmax=O.CMAX_ALL if cmax is None else cmax,
-               ball=O.CMAX_ALL if ball is None else ball, threads=threads, memo=memo or 0,
-               level_work=O.CMAX_ALL if level_work is None else level_work, prune=prune,
-               theta=theta or 0)
-    raw = time.perf_counter() - t0
-    return raw * (WORKLOADS[workload][0] / g.n), raw, (os.cpu_count() or 1) if threads else 1, g.n
+    O.build_ch(g, args.hop_limit, cmax=O.CMAX_ALL if args.cmax is None else args.cmax,
+               ball=O.CMAX_ALL if args.witness_ball is None else args.witness_ball, threads=threads,
+               memo=args.memo or 0,
+               level_work=O.CMAX_ALL if args.level_work is None else args.level_work,
+               prune=args.prune, theta=args.theta or 0)
+    return time.perf_counter() - t0
+
+
+def power_law(n1, t1, n2, t2, n):
+    """t(n) through (n1, t1) and (n2, t2) on t = a * n^b; returns (t(n), b)."""
+    b = float(np.log(t2 / t1) / np.log(n2 / n1)) if n2 != n1 and t1 > 0 and t2 > 0 else 1.0
+    return t2 * (n / n2) ** b, b
+
+
+def cpu_baseline_record(args):
+    """The oracle (one thread, then its -DORACLE_THREADS build) on the two
+    sample graphs of the family, extrapolated to the workload's size."""
+    n = WORKLOADS[args.workload][0]
+    (n1, g1f), (n2, g2f) = oracle_sample_sizes(args.workload)
+    g1, g2 = g1f(), g2f()
+    oracle_build_s(I.geometric_knn_graph(2000, seed=7), args)  # load + warm
+    rec = {}
+    for threads in (False, True):
+        t1 = oracle_build_s(g1, args, threads)
+        t2 = oracle_build_s(g2, args, threads)
+        est, b = power_law(n1, t1, n2, t2, n)
+        rec[threads] = (est, b, t1, t2)
+    est, b, t1, t2 = rec[False]
+    hi = host_info()
+    cpu = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+           "sample": f"oracle builds of {n1}- and {n2}-vertex graphs of the same family "
+                     f"({t1:.2f} s and {t2:.2f} s, one thread), extrapolated to {n} vertices along "
+                     f"the power law through them (exponent {b:.2f})",
+           "host": hi}
+    est, b, t1, t2 = rec[True]
+    cpu["threaded"] = {"value": est, "unit": "s", "cores": hi["nproc"],
+                       "sample": f"same samples, -DORACLE_THREADS build ({t1:.2f} s and {t2:.2f} s), "
+                                 f"exponent {b:.2f}"}
+    return cpu
 
 
 def run_reference(args):
-    n, gseed, qseed, nq = WORKLOADS[args.workload]
+    """The oracle as the reference arm: the warm-up steps build the smaller
+    sample graph, the timed steps the larger one (one host thread each);
+    value = the timed mean extrapolated to the workload along the power law
+    through the two means. ms_per_step is the timed step as run."""
+    n = WORKLOADS[args.workload][0]
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle as O
-    cmax = O.CMAX_ALL if args.cmax is None else args.cmax
-    ball = O.CMAX_ALL if args.witness_ball is None else args.witness_ball
-    O.build_ch(I.geometric_knn_graph(2000, seed=7), args.hop_limit)  # load + warm
-    g = make_graph(args.workload, sample=True)
-    sample_n = g.n
-    for _ in range(args.warmup):
-        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball, memo=args.memo or 0,
-                   level_work=O.CMAX_ALL if args.level_work is None else args.level_work,
-                   prune=args.prune, theta=args.theta or 0)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        O.build_ch(g, args.hop_limit, cmax=cmax, ball=ball, memo=args.memo or 0,
-                   level_work=O.CMAX_ALL if args.level_work is None else args.level_work,
-                   prune=args.prune, theta=args.theta or 0)
-        times.append(time.perf_counter() - t0)
-    scale = n / sample_n
-    value = statistics.mean(times) * scale
+    (n1, g1f), (n2, g2f) = oracle_sample_sizes(args.workload)
+    g1, g2 = g1f(), g2f()
+    oracle_build_s(I.geometric_knn_graph(2000, seed=7), args)  # load + warm
+    warm = [oracle_build_s(g1, args) for _ in range(max(1, args.warmup))]
+    times = [oracle_build_s(g2, args) for _ in range(args.steps)]
+    t1, t2 = statistics.mean(warm), statistics.mean(times)
+    value, b = power_law(n1, t1, n2, t2, n)
+    hi = host_info()
+    sample = (f"timed steps: oracle build of a {n2}-vertex graph of the same family ({args.workload}), "
+              f"one thread, mean {t2:.2f} s; warm-up steps: {n1} vertices, mean {t1:.2f} s; value "
+              f"extrapolated to {n} vertices along the power law through the two (exponent {b:.2f})")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": value * 1000, "higher_is_better": False, "scaling": "weak",
+        "ms_per_step": t2 * 1000, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": args.workload, "vertices": n, "hop_limit": args.hop_limit,
-                   "cmax": args.cmax},
-        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": f"oracle build of a {sample_n}-vertex graph of the same "
-                                   f"family ({args.workload}), mean of {args.steps} runs, scaled "
-                                   f"linearly by vertex count to {n} vertices"},
+                   "cmax": args.cmax, "sample_vertices": n2},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": hi},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def compare_learned(args):
+def compare_learned(args, steps=None, warmup=None):
     """Learned priority vs edge difference (one JSON line). geo1M: trained on
     traces of 20 seeded 256K-vertex graphs of the family, compared on a
     held-out 1M graph (seed 5). rmat2M: trained on traces of seeded 2^17-vertex
@@ -285,6 +342,8 @@ def compare_learned(args):
     import torch
     from paper_2412_18008_gb300 import ch
     dev = torch.device("cuda", 0)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     rmat = args.workload.startswith("rmat")
     cmax = args.cmax
     hop_limit, route_deg, tune_rows = args.hop_limit, 0, None
@@ -336,7 +395,7 @@ def compare_learned(args):
     answers = {}
     for name, mw in (("edge_difference", None), ("learned", weights)):
         times = []
-        for k in range(args.warmup + args.steps):
+        for k in range(warmup + steps):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -345,9 +404,9 @@ def compare_learned(args):
                             witness_route_deg=route_deg, witness_ball_limit=ball)
             e1.record()
             torch.cuda.synchronize()
-            if k >= args.warmup:
+            if k >= warmup:
                 times.append(e0.elapsed_time(e1))
-            if k + 1 < args.warmup + args.steps:
+            if k + 1 < warmup + steps:
                 h.close()
         st = h.stats()
         d, sett = h.query(ds[:n_ss], dt[:n_ss], want_settled=True)
@@ -378,24 +437,25 @@ def compare_learned(args):
         "queries_compared": nq_cmp,
         "train_loss_per_epoch": [float(x) for x in loss],
         "trace_seconds": t_traces, "train_seconds": t_train,
-        "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 MLP / u32 graph",
+        "steps": steps, "warmup": warmup, "dtype": "bf16 MLP / u32 graph",
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
-def serve_bench(args):
-    """Serving: one JSON line with throughput and latency percentiles."""
+def serve_bench(args, workload=None, nreq=None):
+    """Serving: throughput and latency percentiles (a dict for one JSON line)."""
     import torch
     from paper_2412_18008_gb300 import ch
     dev = torch.device("cuda", 0)
-    if args.serve_workload == "geo16M":
+    workload = args.serve_workload if workload is None else workload
+    if workload == "geo16M":
         n, gseed = 16_000_000, 6
     else:
         n, gseed = 1_000_000, 3
     g = I.geometric_knn_graph(n, seed=gseed)
     h = ch.CH.build(g, hop_limit=args.hop_limit)
     st = h.stats()
-    nreq = args.serve_requests
+    nreq = args.serve_requests if nreq is None else nreq
     src, ks, tg = I.request_mix(n, nreq, seed=7)
     expected = h.query(np.repeat(src, ks), tg)
 
@@ -446,13 +506,14 @@ def serve_bench(args):
     line = {
         "metric": "served queries: requests/s and p50/p99 latency, continuous batching vs one "
                   "batch call per request",
-        "config": {"workload": f"{args.serve_workload}-serve", "vertices": n, "edges": int(g.m),
+        "config": {"workload": f"{workload}-serve", "vertices": n, "edges": int(g.m),
                    "requests": nreq, "mean_targets_per_request": float(ks.mean()),
                    "one_to_many_fraction": 0.2, "targets_max": 1024,
                    "server_blocks": nblocks, "build_s": st["build_ms"] / 1e3},
         "results": out, "dtype": "u32", "data": "synthetic",
     }
-    print(json.dumps(line), flush=True)
+    h.close()
+    return line
 
 
 def main():
@@ -461,10 +522,10 @@ def main():
         run_reference(args)
         return
     if args.serve:
-        serve_bench(args)
+        print(json.dumps(serve_bench(args)), flush=True)
         return
     if args.compare_learned:
-        compare_learned(args)
+        print(json.dumps(compare_learned(args)), flush=True)
         return
     import torch
     import torch.distributed as dist
@@ -659,21 +720,25 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        scaled, raw, cores, sn = cpu_sample_build(args.workload, args.hop_limit, args.cmax,
-                                                  args.witness_ball, memo=args.memo,
-                                                  level_work=args.level_work, prune=args.prune,
-                                                  theta=args.theta)
-        cpu = {"value": scaled, "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": f"oracle build of a {sn}-vertex graph of the same family "
-                         f"({raw:.2f} s, one thread), scaled linearly by vertex count to {n}"}
-        # the same oracle with its witness searches on every host thread
-        # (identical result; the rest of each round stays sequential)
-        mt_scaled, mt_raw, mt_cores, _ = cpu_sample_build(args.workload, args.hop_limit, args.cmax,
-                                                          args.witness_ball, threads=True,
-                                                          memo=args.memo, level_work=args.level_work,
-                                                          prune=args.prune, theta=args.theta)
-        cpu["threaded"] = {"value": mt_scaled, "unit": "s", "cores": mt_cores,
-                           "sample": f"same sample, -DORACLE_THREADS build ({mt_raw:.2f} s)"}
+        cpu = cpu_baseline_record(args)
+
+    # the other workloads of the method, measured in the same run: the
+    # learned priority against the edge difference (1M, trained on 20
+    # 256K-vertex graphs) and the server on the 16M-vertex graph
+    configs = None
+    if rank == 0 and world == 1 and not args.no_configs and args.workload == "geo1M":
+        h_last.close()
+        handles = []
+        configs = {}
+        for name, fn in (("learned_geo1M", lambda: compare_learned(args, steps=3, warmup=1)),
+                         ("serve_geo16M", lambda: serve_bench(args, "geo16M", 20_000))):
+            t0 = time.perf_counter()
+            try:
+                configs[name] = fn()
+            except Exception as e:  # a side record must not cost the line
+                configs[name] = {"error": repr(e)[:300]}
+            configs[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+            ch.trim_memory()
 
     if rank == 0:
         line = {
@@ -699,13 +764,15 @@ def main():
             "round_profile": round_profile,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "configs": configs,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks,
             "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)
-    h_last.close()
+    if configs is None:
+        h_last.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -525,7 +525,18 @@ int ch_server_replay(ch_server_t *sv, uint64_t nreq, const uint32_t *src, const 
  * entry never matched its request. */
 int ch_server_stop(ch_server_t *sv);
 
+/* Frees the hierarchy. Waits for the device first (no work that reads the
+ * hierarchy may still be in flight; a running server of another hierarchy
+ * delays it until that loop ends at its idle limit). The memory goes back
+ * to the library's device-memory cache. */
 void ch_free(ch_t *ch);
+
+/* Device memory: the library keeps the blocks of freed buffers (hierarchies,
+ * build and query temporaries) in a per-device cache and reuses them, so
+ * repeated builds allocate nothing from CUDA. ch_trim_memory waits for the
+ * current device and returns that device's cached blocks to CUDA; it
+ * returns the bytes released. */
+size_t ch_trim_memory(void);
 
 /* Failure injection for tests of the error paths (not part of the method).
  * After ch_debug_fail_alloc(k) with k >= 0, the library's device

@@ -1033,8 +1033,21 @@ void orc_get_down(const orc_ch* h, uint32_t* out3) {
 
 void orc_query_batch(const orc_ch* h, uint64_t k, const uint32_t* s, const uint32_t* t,
                      uint32_t* out, uint64_t* settled) {
+#ifdef ORACLE_THREADS
+    // Threaded build: pairs are split over host threads; each answer depends
+    // on its pair alone, so the output is the sequential one.
+    const uint64_t nt = std::max(1u, std::thread::hardware_concurrency());
+    std::vector<std::thread> pool;
+    for (uint64_t th = 0; th < nt; ++th)
+        pool.emplace_back([&, th] {
+            for (uint64_t i = th; i < k; i += nt)
+                out[i] = query(h->ch, s[i], t[i], settled ? settled + i : nullptr);
+        });
+    for (auto& x : pool) x.join();
+#else
     for (uint64_t i = 0; i < k; ++i)
         out[i] = query(h->ch, s[i], t[i], settled ? settled + i : nullptr);
+#endif
 }
 
 // Scores of every vertex of the input graph as round 0 computes them.

@@ -176,6 +176,7 @@ def load(build_if_missing: bool = True):
     lib.ch_last_error.restype = C.c_char_p
     lib.ch_version.restype = C.c_char_p
     lib.ch_kernel_launches.restype = C.c_uint64
+    lib.ch_trim_memory.restype = C.c_size_t
     lib.ch_debug_fail_alloc.argtypes = [C.c_int64]
     lib.ch_debug_fail_alloc.restype = C.c_int64
     _lib = lib
@@ -718,6 +719,12 @@ def version() -> str:
 def kernel_launches() -> int:
     """CUDA kernels libch.so has launched in this process."""
     return int(load().ch_kernel_launches())
+
+
+def trim_memory() -> int:
+    """ch_trim_memory: waits for the current device and returns the library's
+    cached device blocks to CUDA; the bytes released."""
+    return int(load().ch_trim_memory())
 
 
 def debug_fail_alloc(after: int) -> int:

@@ -676,6 +676,19 @@ int ch_server_stop(ch_server_t *sv) {
     return CH_OK;
 }
 
-void ch_free(ch_t *ch) { delete ch; }
+void ch_free(ch_t *ch) {
+    if (!ch) return;
+    // the hierarchy's memory goes back to the library's cache: no work that
+    // reads it may still be in flight
+    cudaDeviceSynchronize();
+    cudaGetLastError();
+    delete ch;
+}
+
+size_t ch_trim_memory(void) {
+    size_t b = 0;
+    guarded([&] { b = dev_trim(); });
+    return b;
+}
 
 }  // extern "C"

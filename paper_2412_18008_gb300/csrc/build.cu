@@ -102,6 +102,11 @@ struct Ctl {
     unsigned long long dm_count;     // keys in the memoised-distance map since its last clear
     unsigned long long pruned;       // overlay edges pruned this round
     uint32_t nDirty, pad2;           // vertices whose lists hold pruned entries
+    // shortcut log entries so far (device-side, so that k_insert needs no
+    // host value), and the contraction counters of the last finished round,
+    // copied by k_round_end for the host's next read
+    unsigned long long log_tail;
+    unsigned long long s_cand, s_kept, s_merged, s_inserted, s_newEdges, s_nRec, s_dm_count;
 };
 
 struct Dev {
@@ -2232,9 +2237,23 @@ __global__ void k_advance_tails(Ctl *ctl) {
     ctl->in_tail += ctl->relocIn;
 }
 
+// End of a round's contraction: its counters are kept for the host's next
+// read, and the shortcut log advances past the round's records.
+__global__ void k_round_end(Ctl *ctl) {
+    ctl->s_cand = ctl->cand;
+    ctl->s_kept = ctl->kept;
+    ctl->s_merged = ctl->merged;
+    ctl->s_inserted = ctl->inserted;
+    ctl->s_newEdges = ctl->newEdges;
+    ctl->s_nRec = ctl->nRec;
+    ctl->s_dm_count = ctl->dm_count;
+    ctl->log_tail += ctl->nRec;
+}
+
 __global__ void k_insert(Dev d, const uint4 *rec, const uint8_t *flag, uint32_t r,
-                         uint4 *log, uint32_t *log_round, uint64_t log_base) {
+                         uint4 *log, uint32_t *log_round) {
     const uint32_t nRec = d.ctl->nRec;
+    const uint64_t log_base = d.ctl->log_tail;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nRec;
          i += gridDim.x * blockDim.x) {
         const uint4 c = rec[i];  // (v1, v2, w, via)
@@ -2370,7 +2389,7 @@ struct Span {
 
 struct Builder {
     ch_s *h;
-    cudaStream_t st;
+    cudaStream_t st = nullptr;
     uint32_t n;
     uint64_t m_in;
     Dev d{};
@@ -2429,6 +2448,9 @@ struct Builder {
     std::vector<Span> spans;
 
     int cur_round = -1;
+    // The build's buffers go back to the library's cache when the builder is
+    // destroyed; on an error path its kernels may still be running.
+    ~Builder() { cudaStreamSynchronize(st); }
     void mark(double *acc, cudaEvent_t a, int phase = -1) {
         cudaEvent_t b = pool.get();
         CH_CUDA_TRY(cudaEventRecord(b, st));
@@ -2678,6 +2700,26 @@ void Builder::run_rounds() {
     CH_CUDA_TRY(cudaMemcpyAsync(&ctl.ptr->nVO, &hctl->nVO, 4, cudaMemcpyHostToDevice, st));
     uint32_t nA = n, nVO = n;
     uint64_t live_edges = h->m_input;
+    // The statistics row of a round is finished at the next read of the
+    // control block, which also brings the round's contraction counters
+    // (k_round_end): one host synchronisation per round.
+    bool pending = false;
+    std::array<uint64_t, CH_NSTAT> row{};
+    uint64_t row_drop = 0;  // live edges the pending round removed (its V_F's and pruned ones)
+    auto finish_row = [&]() {
+        if (!pending) return;
+        const Ctl &c = *hctl;
+        row[4] = c.s_cand;
+        row[5] = c.s_kept;
+        row[6] = c.s_merged;
+        row[7] = c.s_inserted;
+        live_edges = live_edges - row_drop + c.s_newEdges;
+        row[9] = live_edges;
+        h->round_stats.push_back(row);
+        if (c.s_nRec > rec.count) throw Error{CH_ECUDA, "internal: record overflow"};
+        log_count = c.log_tail;
+        pending = false;
+    };
     for (uint32_t r = 0; nVO > 0; ++r) {
         if (r > 0x7FFFFFF0u) throw Error{CH_ERANGE, "too many rounds"};
         cur_round = (int)r;
@@ -2740,6 +2782,7 @@ void Builder::run_rounds() {
         CH_CHECK_LAUNCH();
         mark(&h->t_prep_ms, e0, 2);
         sync_ctl();
+        finish_row();  // the round before
         const Ctl c = *hctl;
         const uint32_t nF = c.nF, nS2 = c.nS2, nAnext = c.nAnext;
         if (nF == 0) {
@@ -2813,7 +2856,9 @@ void Builder::run_rounds() {
         }
         const uint64_t rec_bound = std::max<uint64_t>(cb, 1);
         k_insert<<<grid_for(rec_bound, 256, sms * 8), 256, 0, st>>>(
-            d, rec.ptr, rec_flag.ptr, r, log.ptr, log_round.ptr, log_count);
+            d, rec.ptr, rec_flag.ptr, r, log.ptr, log_round.ptr);
+        CH_CHECK_LAUNCH();
+        k_round_end<<<1, 1, 0, st>>>(ctl.ptr);
         CH_CHECK_LAUNCH();
         compact_alive(VO.ptr, &ctl.ptr->nVO, nVO, level.ptr, VO2.ptr, &ctl.ptr->nVO2, tmp.ptr,
                       scan32.ptr, st);
@@ -2821,36 +2866,37 @@ void Builder::run_rounds() {
         CH_CUDA_TRY(cudaMemcpyAsync(&ctl.ptr->nVO, &ctl.ptr->nVO2, 4, cudaMemcpyDeviceToDevice, st));
         std::swap(A, Anext);
         mark(&h->t_update_ms, e0, 4);
-        // read this round's contraction counters (one more sync per round
-        // keeps the bookkeeping simple; the next round needs nothing from it)
-        sync_ctl();
-        const Ctl c2 = *hctl;
-        std::array<uint64_t, CH_NSTAT> st_row{};
-        st_row[0] = nA;
-        st_row[1] = c.nS;
-        st_row[2] = nF;
-        st_row[3] = nS2;
-        st_row[4] = c2.cand;
-        st_row[5] = c2.kept;
-        st_row[6] = c2.merged;
-        st_row[7] = c2.inserted;
+        // this round's row: what is known now; its contraction counters
+        // arrive with the next read of the control block
+        row = {};
+        row[0] = nA;
+        row[1] = c.nS;
+        row[2] = nF;
+        row[3] = nS2;
         nVO -= nF;
-        st_row[8] = nVO;
-        live_edges = live_edges - c.degFout - c.degFin + c2.newEdges - c.pruned;
-        st_row[9] = live_edges;
-        h->round_stats.push_back(st_row);
-        if (c2.nRec > rec.count) throw Error{CH_ECUDA, "internal: record overflow"};
-        log_count += c2.nRec;
+        row[8] = nVO;
+        row_drop = c.degFout + c.degFin + c.pruned;
+        pending = true;
         nA = nAnext;
-        // memoised distances are cleared lazily: only after a round that
-        // leaves more keys than the limit; otherwise the map keeps room for
-        // another round's keys
-        if (dm_limit && c2.dm_count > dm_limit) {
-            CH_CUDA_TRY(cudaMemsetAsync(dm_keys.ptr, 0xFF, dm_keys.count * sizeof(unsigned long long), st));
-            CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->dm_count, 0, sizeof(unsigned long long), st));
-        } else if (dm_limit) {
-            dmap_reserve(c2.dm_count);
+        if (dm_limit) {
+            // memoised distances are cleared lazily: only after a round that
+            // leaves more keys than the limit; otherwise the map keeps room
+            // for another round's keys. The decision needs this round's
+            // count before the next round's searches.
+            sync_ctl();
+            const uint64_t dm_count = hctl->s_dm_count;
+            finish_row();
+            if (dm_count > dm_limit) {
+                CH_CUDA_TRY(cudaMemsetAsync(dm_keys.ptr, 0xFF, dm_keys.count * sizeof(unsigned long long), st));
+                CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->dm_count, 0, sizeof(unsigned long long), st));
+            } else {
+                dmap_reserve(dm_count);
+            }
         }
+    }
+    if (pending) {
+        sync_ctl();
+        finish_row();
     }
     h->n_shortcuts = log_count;
     h->witness_bytes = 0;
@@ -3095,9 +3141,11 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     d.inel = b.inel.ptr;
     d.ball = p->witness_ball_limit ? p->witness_ball_limit : 0xFFFFFFFFu;
     // memoised in-round decisions need both phases to decide alike, which a
-    // ball bound (cut levels depend on each phase's own weight bound) breaks;
-    // the memoised distances across rounds replace them
-    d.memo = p->witness_ball_limit == 0 && p->witness_memo_limit == 0 && p->witness_prune == 0;
+    // ball bound or a level-work bound breaks (their cut levels depend on
+    // each phase's own weight bound, through the labels it keeps); the
+    // memoised distances across rounds replace them
+    d.memo = p->witness_ball_limit == 0 && p->witness_memo_limit == 0 && p->witness_prune == 0 &&
+             (p->witness_level_work == 0 || p->witness_settle_cap != 0);
     if (p->witness_level_work) b.level_work = p->witness_level_work;
     b.theta = p->witness_settle_cap;
     if (p->witness_memo_limit || p->witness_prune) {

@@ -6,6 +6,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <exception>
 #include <string>
 #include <vector>
 
@@ -55,48 +56,68 @@ void kernel_launch_add(int64_t d);
 // this allocation is the one chosen to fail. Off unless armed.
 bool inject_alloc_failure();
 
+// The library's device allocator (alloc.cu): blocks come from a per-device
+// cache of freed blocks in size classes, else from cudaMalloc. *got receives
+// the block's class size, which dev_release needs. A block may be released
+// only once the device no longer uses it. dev_trim waits for the device and
+// frees the cached blocks of the current device (returns their bytes).
+void *dev_alloc(size_t bytes, size_t *got);
+void dev_release(void *p, size_t cls);
+size_t dev_trim();
+
+// A device array owned by the library (memory from dev_alloc). Releasing it
+// (destruction, alloc, move-assignment) hands the block back to the cache,
+// so the device must be done with it by then.
 template <class T>
 struct DevBuf {
     T *ptr = nullptr;
     size_t count = 0;
+    size_t cls = 0;  // class size of the block
 
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
-    DevBuf(DevBuf &&o) noexcept : ptr(o.ptr), count(o.count) {
+    DevBuf(DevBuf &&o) noexcept : ptr(o.ptr), count(o.count), cls(o.cls) {
         o.ptr = nullptr;
         o.count = 0;
+        o.cls = 0;
     }
     DevBuf &operator=(DevBuf &&o) noexcept {
         if (this != &o) {
             release();
             ptr = o.ptr;
             count = o.count;
+            cls = o.cls;
             o.ptr = nullptr;
             o.count = 0;
+            o.cls = 0;
         }
         return *this;
     }
-    ~DevBuf() { release(); }
+    // Destroyed while an exception unwinds, the array may still be in use by
+    // work the failed call had enqueued: wait for the device first.
+    ~DevBuf() {
+        if (ptr && std::uncaught_exceptions() > 0) cudaDeviceSynchronize();
+        release();
+    }
 
     void release() {
-        if (ptr) cudaFree(ptr);
+        if (ptr) dev_release(ptr, cls);
         ptr = nullptr;
         count = 0;
+        cls = 0;
     }
+    // (Re)allocates n elements. An array that held memory before may still
+    // be read by work in flight on any stream: the device is waited for
+    // before its block goes back to the cache.
     void alloc(size_t n) {
+        if (ptr) cudaDeviceSynchronize();
         release();
         if (n == 0) n = 1;
         if (inject_alloc_failure())
             throw Error{CH_ENOMEM, "injected failure of a " + std::to_string(n * sizeof(T)) +
                                        "-byte device allocation"};
-        cudaError_t e = cudaMalloc(&ptr, n * sizeof(T));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            ptr = nullptr;
-            throw Error{CH_ENOMEM, "cudaMalloc of " + std::to_string(n * sizeof(T)) +
-                                       " bytes failed: " + cudaGetErrorString(e)};
-        }
+        ptr = static_cast<T *>(dev_alloc(n * sizeof(T), &cls));
         count = n;
     }
     // Grow to at least n elements keeping the first `keep` elements.

@@ -745,7 +745,12 @@ void server_free(ch_server_s *sv) {
         uint32_t st = 0;
         server_stop(sv, &st);
     }
-    if (sv->st) cudaStreamDestroy(sv->st);
+    // the loop's buffers go back to the library's cache: wait for the
+    // kernel (it ends at its idle limit at the latest)
+    if (sv->st) {
+        cudaStreamSynchronize(sv->st);
+        cudaStreamDestroy(sv->st);
+    }
 }
 
 // Replays a request schedule against the server: request i is submitted at

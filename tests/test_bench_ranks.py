@@ -42,3 +42,16 @@ def test_two_ranks_take_the_maximum():
 def test_single_rank_is_a_no_op():
     import bench
     assert bench.max_over_ranks([1, 2.5], 1, None) == [1.0, 2.5]
+
+
+def test_power_law_extrapolation_is_exact_on_a_power_law():
+    import bench
+    t = lambda n: 2e-9 * n ** 1.5
+    est, b = bench.power_law(100_000, t(100_000), 200_000, t(200_000), 1_000_000)
+    assert abs(b - 1.5) < 1e-12 and abs(est - t(1_000_000)) < 1e-9 * t(1_000_000)
+
+
+def test_host_info_names_cores_and_cpu():
+    import bench
+    hi = bench.host_info()
+    assert hi["nproc"] == os.cpu_count() and hi["machine"]

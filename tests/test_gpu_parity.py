@@ -109,11 +109,14 @@ def test_geometric_full_parity(n, seed):
 
 def test_full_size_road_like_graph():
     """The 1M-vertex geometric workload, built in the configuration the
-    benchmark times: the whole hierarchy is compared with the oracle's, the
-    1M-query batch on sampled answers (oracle CH query and Dijkstra)."""
+    benchmark times: the whole hierarchy is compared with the oracle's, and
+    every answer of the 1M-query batch with the oracle's CH query (its
+    threaded build, whose output equals the sequential one), sampled
+    answers and search-space sizes also with Dijkstra and the sequential
+    query."""
     g = I.geometric_knn_graph(1_000_000, seed=3)
     gch = gpu_build(g, 5)
-    och = O.build_ch(g, 5)
+    och = O.build_ch(g, 5, threads=True)
     assert_same_hierarchy(gch, och)
     s, t = I.random_pairs(g.n, 1_000_000, seed=4)
     ds = torch.from_numpy(s.view(np.int32)).cuda()
@@ -123,6 +126,7 @@ def test_full_size_road_like_graph():
     gch.query_status()
     d = out.cpu().numpy().view(np.uint32)
     st = settled.cpu().numpy().view(np.uint32)
+    assert np.array_equal(d, och.query(s, t)), "answers differ from the oracle's"
     idx = np.random.default_rng(0).choice(g.n, 4000, replace=False)
     od, ost = och.query(s[idx], t[idx], want_settled=True)
     assert np.array_equal(d[idx], od)

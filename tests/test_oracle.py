@@ -433,7 +433,9 @@ def test_threaded_build_is_identical(name, g, cmax, ball):
         assert np.array_equal(getattr(a, f), getattr(b, f)), f
     s, t = np.meshgrid(np.arange(g.n), np.arange(g.n), indexing="ij")
     s, t = s.ravel(), t.ravel()
-    assert np.array_equal(a.query(s, t), b.query(s, t))
+    da, sa = a.query(s, t, want_settled=True)
+    db, sb = b.query(s, t, want_settled=True)  # pairs split over host threads
+    assert np.array_equal(da, db) and np.array_equal(sa, sb)
 
 
 # ---------------------------------------------------------------------------
