@@ -56,6 +56,12 @@ extern "C" {
  * (it is a feature). Any priority yields a hierarchy with exact distances. */
 #define CH_PRIO_EDGE_DIFF 0u
 #define CH_PRIO_LEARNED 1u
+/* CH_PRIO_COMPOSITE: the combination Sec. 3.2 names (edge difference,
+ * vertex degree, hop distance, hierarchy depth; no weights given), read as
+ * 4 * ED + (|N_in| + |N_out|) + 8 * depth, clamped to +-2^30, where depth is
+ * 1 + the largest depth among contracted neighbours (0 if none). Hop counts
+ * per overlay edge are not kept, so the hop-distance term is left out. */
+#define CH_PRIO_COMPOSITE 2u
 
 /* MLP parameters, FP32, in this order: W1[12][64] (input-major), b1[64],
  * W2[64][64] (input-major), b2[64], W3[64], b3. */
@@ -84,7 +90,7 @@ typedef struct {
  *              (Alg. 3, 4, 6 with a hop bound in place of the unstated
  *              settled-vertex bound). Any H >= 0 yields exact distances;
  *              default 5.
- *   priority   CH_PRIO_EDGE_DIFF.
+ *   priority   CH_PRIO_EDGE_DIFF (default), CH_PRIO_LEARNED or CH_PRIO_COMPOSITE.
  *   tie_break  CH_TIE_HASHED (default) or CH_TIE_ID; tie_seed feeds the hash.
  *   max_candidates_per_vertex  Cmax: a rescored vertex u with
  *              |N_in(u)| * |N_out(u)| > Cmax is not eligible (not scored,

@@ -62,7 +62,7 @@ def _load(threads: bool = False):
         lib.orc_build.restype = C.c_int
         lib.orc_free.argtypes = [P]
         lib.orc_build2.argtypes = [u32, u64, P, P, P, u32, u32, u32, C.c_int, u64, P, P, P,
-                                   u64, u64, u64, C.c_int, u64, u64, C.POINTER(P)]
+                                   u64, u64, u64, C.c_int, u64, u64, C.c_int, C.POINTER(P)]
         lib.orc_searches.argtypes = [P]
         lib.orc_searches.restype = u64
         lib.orc_witness_work.argtypes = [P]
@@ -182,7 +182,8 @@ CMAX_ALL = (1 << 64) - 1
 def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int = 0,
              trace: bool = False, replay=None, cmax: int = CMAX_ALL,
              ball: int = CMAX_ALL, threads: bool = False, theta: int = 0,
-             prune: bool = False, memo: int = 0, level_work: int = CMAX_ALL) -> OracleCH:
+             prune: bool = False, memo: int = 0, level_work: int = CMAX_ALL,
+             composite: bool = False) -> OracleCH:
     """Run the oracle's round algorithm on graph ``g`` (see ``oracle.cpp``).
 
     ``trace`` records the learned-priority features of every rescoring
@@ -203,7 +204,9 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
     witness searches run. ``level_work`` bounds a hop-limited search's work:
     a level from the second on whose frontier has more out-edges in total is
     not run (``OracleCH.witness_work`` sums the frontier out-edges of the
-    levels run). ``threads`` runs
+    levels run). ``composite`` scores by 4 * edge difference + (|N_in| +
+    |N_out|) + 8 * hierarchy depth (clamped to +-2^30) instead of the edge
+    difference. ``threads`` runs
     the -DORACLE_THREADS build (witness searches on all host threads; the
     same result).
     """
@@ -219,7 +222,8 @@ def build_ch(g, hop_limit: int = 5, tie_break: int = TIE_HASHED, tie_seed: int =
         rpv = np.ascontiguousarray(replay[2], np.int32)
     rc = lib.orc_build2(*args, hop_limit, tie_break, tie_seed & 0xFFFFFFFF, int(trace),
                         rr.size, _p(rr), _p(ru), _p(rpv), int(cmax), int(ball), int(theta),
-                        int(bool(prune)), int(memo), int(level_work), C.byref(h))
+                        int(bool(prune)), int(memo), int(level_work), int(bool(composite)),
+                        C.byref(h))
     if rc != 0:
         raise ValueError(f"oracle rejected the graph or parameters (status {rc})")
     n = g.n

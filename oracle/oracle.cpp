@@ -560,11 +560,23 @@ using Replay = std::map<std::pair<uint32_t, uint32_t>, int32_t>;
 
 constexpr int32_t P_INELIGIBLE = 2147483646;  // INT32_MAX - 1
 
+// The composite score (Sec. 3.2 names edge difference, vertex degree, hop
+// distance and hierarchy depth, without weights): 4 * ED + (|N_in| + |N_out|)
+// + 8 * depth, the edge difference weighted highest and depth at twice its
+// weight, clamped to +-2^30. Hop counts per overlay edge are not kept, so
+// the hop-distance term is left out.
+int32_t composite_score(int32_t ed, size_t n_in, size_t n_out, int32_t depth) {
+    int64_t p = 4 * int64_t(ed) + int64_t(n_in) + int64_t(n_out) + 8 * int64_t(depth);
+    p = std::min<int64_t>(std::max<int64_t>(p, -(int64_t(1) << 30)), int64_t(1) << 30);
+    return int32_t(p);
+}
+
 void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
            const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t seed,
            bool want_trace = false, const Replay* replay = nullptr,
            uint64_t cmax = ~uint64_t(0), uint64_t ball = ~uint64_t(0), uint64_t theta = 0,
-           bool prune = false, uint64_t memo_limit = 0, uint64_t level_work = ~uint64_t(0)) {
+           bool prune = false, uint64_t memo_limit = 0, uint64_t level_work = ~uint64_t(0),
+           bool composite = false) {
     Overlay g;
     load(g, n, off, tgt, w);
     ch.ed_last.assign(n, 0);
@@ -673,6 +685,8 @@ void build(CH& ch, uint32_t n, const uint64_t* off, const uint32_t* tgt,
                 auto it = replay->find({r, u});
                 if (it == replay->end()) throw std::runtime_error("replay has no priority");
                 ch.P[u] = it->second;
+            } else if (composite) {
+                ch.P[u] = composite_score(ed, g.in[u].size(), g.out[u].size(), ch.depth[u]);
             } else {
                 ch.P[u] = ed;
             }
@@ -924,7 +938,7 @@ int orc_build2(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
                const uint32_t* w, uint32_t H, uint32_t tie_mode, uint32_t tie_seed,
                int want_trace, uint64_t nreplay, const uint32_t* rp_round, const uint32_t* rp_u,
                const int32_t* rp_p, uint64_t cmax, uint64_t ball, uint64_t theta, int prune,
-               uint64_t memo_limit, uint64_t level_work, orc_ch** out) {
+               uint64_t memo_limit, uint64_t level_work, int composite, orc_ch** out) {
     // the settled-vertex cap replaces the hop-limited search, ball bound included
     if (!out || !validate(n, m, off, tgt, w) || tie_mode > 1 || (theta && ball != ~uint64_t(0)))
         return ORC_EINVAL;
@@ -933,7 +947,8 @@ int orc_build2(uint32_t n, uint64_t m, const uint64_t* off, const uint32_t* tgt,
     orc_ch* h = new orc_ch();
     try {
         build(h->ch, n, off, tgt, w, H, tie_mode, tie_seed, want_trace != 0,
-              nreplay ? &rp : nullptr, cmax, ball, theta, prune != 0, memo_limit, level_work);
+              nreplay ? &rp : nullptr, cmax, ball, theta, prune != 0, memo_limit, level_work,
+              composite != 0);
     } catch (const std::exception&) {
         delete h;
         return ORC_EINVAL;

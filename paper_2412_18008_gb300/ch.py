@@ -27,6 +27,7 @@ CH_TIE_HASHED = 0
 CH_TIE_ID = 1
 CH_PRIO_EDGE_DIFF = 0
 CH_PRIO_LEARNED = 1
+CH_PRIO_COMPOSITE = 2
 CH_MLP_NPARAM = 5057
 CH_NFEAT = 12
 CH_NSTAT = 10
@@ -235,7 +236,7 @@ class CH:
     def _marshal(graph, n, offsets, targets, weights, hop_limit, tie_break, tie_seed, stream,
                  mlp_weights, trace, max_candidates_per_vertex, witness_route_deg,
                  witness_ball_limit=None, witness_memo_limit=None, witness_level_work=None,
-                 witness_prune=False, witness_settle_cap=None):
+                 witness_prune=False, witness_settle_cap=None, composite=False):
         if graph is not None:
             n, offsets, targets, weights = graph.n, graph.offsets, graph.targets, graph.weights
         g = GraphT()
@@ -285,6 +286,10 @@ class CH:
                 raise ValueError(f"mlp_weights needs {CH_MLP_NPARAM} floats")
             keep.append(wts)
             p.priority = CH_PRIO_LEARNED
+        if composite:
+            if mlp_weights is not None:
+                raise ValueError("composite and learned priorities exclude each other")
+            p.priority = CH_PRIO_COMPOSITE
             p.mlp_weights = wts.ctypes.data_as(C.c_void_p)
         return g, p, keep
 
@@ -296,7 +301,7 @@ class CH:
               witness_ball_limit: int | None = None,
               witness_memo_limit: int | None = None,
               witness_level_work: int | None = None, witness_prune: bool = False,
-              witness_settle_cap: int | None = None) -> "CH":
+              witness_settle_cap: int | None = None, composite: bool = False) -> "CH":
         """ch_build on a graph given as an ``inputs.Graph`` / NumPy CSR (host
         memory) or as CUDA tensors ``offsets`` (int64), ``targets`` and
         ``weights`` (int32 views of uint32 values) in device memory.
@@ -312,11 +317,12 @@ class CH:
         deletes overlay edges heavier than their pair's witness distance
         after each round's rescoring searches. ``witness_settle_cap`` (θ)
         replaces the hop-limited search by Alg. 3's Dijkstra capped at θ
-        settled vertices; None = off."""
+        settled vertices; None = off. ``composite`` scores vertices by
+        CH_PRIO_COMPOSITE (4 * edge difference + degree + 8 * depth)."""
         g, p, keep = cls._marshal(graph, n, offsets, targets, weights, hop_limit, tie_break,
                                   tie_seed, stream, mlp_weights, trace, max_candidates_per_vertex,
                                   witness_route_deg, witness_ball_limit, witness_memo_limit,
-                                  witness_level_work, witness_prune, witness_settle_cap)
+                                  witness_level_work, witness_prune, witness_settle_cap, composite)
         h = C.c_void_p()
         _check(load().ch_build(C.byref(g), C.byref(p), C.byref(h)))
         del keep

@@ -109,7 +109,8 @@ int ch_build(const ch_graph_t *g, const ch_params_t *params, ch_t **out) {
     ch_params_t p;
     if (params) p = *params;
     else ch_default_params(&p);
-    if (p.priority != CH_PRIO_EDGE_DIFF && p.priority != CH_PRIO_LEARNED) {
+    if (p.priority != CH_PRIO_EDGE_DIFF && p.priority != CH_PRIO_LEARNED &&
+        p.priority != CH_PRIO_COMPOSITE) {
         g_last_error = "unsupported priority mode";
         return CH_EINVAL;
     }

@@ -1822,6 +1822,20 @@ __global__ void k_apply_learned(Dev d, const uint32_t *A, uint32_t nA, const flo
     }
 }
 
+// CH_PRIO_COMPOSITE: P[u] = 4 * ED + (|N_in| + |N_out|) + 8 * depth,
+// clamped to +-2^30, for the eligible rescored vertices (P holds the edge
+// difference on entry).
+__global__ void k_composite(Dev d, const uint32_t *A, uint32_t nA) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nA;
+         i += gridDim.x * blockDim.x) {
+        const uint32_t u = A[i];
+        if (!id_ok(d, u) || d.inel[u]) continue;
+        long long p = 4ll * d.P[u] + (long long)d.in_deg[u] + (long long)d.out_deg[u] + 8ll * d.depth[u];
+        p = p < -(1ll << 30) ? -(1ll << 30) : (p > (1ll << 30) ? (1ll << 30) : p);
+        d.P[u] = (int32_t)p;
+    }
+}
+
 __global__ void k_log_priority(const Dev d, const uint32_t *A, uint32_t nA, int32_t *log) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nA;
          i += gridDim.x * blockDim.x) {
@@ -2426,7 +2440,7 @@ struct Builder {
     DevBuf<long long> trace;     // 14 int64 per rescoring
     DevBuf<int32_t> trace_prio;  // priority per rescoring
     uint64_t trace_count = 0;
-    bool tracing = false, learned = false;
+    bool tracing = false, learned = false, composite = false;
     MlpDevice mlp;
     DevBuf<float> fx, fy;
     // dense fallback
@@ -2747,7 +2761,7 @@ void Builder::run_rounds() {
                 k_score_map<<<grid_for((uint64_t)nA * 32, 256, sms * 8), 256, 0, st>>>(d, dm, A.ptr, nA, r);
                 CH_CHECK_LAUNCH();
             }
-            if (tracing || learned) {
+            if (tracing || learned || composite) {
                 if (tracing && trace.count < (trace_count + nA) * 14) {
                     const uint64_t want = std::max<uint64_t>(trace_count + nA, trace.count / 14 * 2);
                     trace.grow(want * 14, trace_count * 14, st);
@@ -2756,13 +2770,19 @@ void Builder::run_rounds() {
                 long long *rows = tracing ? trace.ptr + trace_count * 14 : nullptr;
                 int32_t *plog = tracing ? trace_prio.ptr + trace_count : nullptr;
                 const int ga = grid_for(nA, 256, sms * 8);
-                k_features<<<ga, 256, 0, st>>>(d, A.ptr, nA, r, rows, learned ? fx.ptr : nullptr);
-                CH_CHECK_LAUNCH();
+                if (tracing || learned) {
+                    k_features<<<ga, 256, 0, st>>>(d, A.ptr, nA, r, rows, learned ? fx.ptr : nullptr);
+                    CH_CHECK_LAUNCH();
+                }
                 if (learned) {
                     mlp.infer(fx.ptr, nA, fy.ptr, st);
                     k_apply_learned<<<ga, 256, 0, st>>>(d, A.ptr, nA, fy.ptr, plog);
                     CH_CHECK_LAUNCH();
-                } else if (plog) {
+                } else if (composite) {
+                    k_composite<<<ga, 256, 0, st>>>(d, A.ptr, nA);
+                    CH_CHECK_LAUNCH();
+                }
+                if (!learned && plog) {
                     k_log_priority<<<ga, 256, 0, st>>>(d, A.ptr, nA, plog);
                     CH_CHECK_LAUNCH();
                 }
@@ -3099,6 +3119,7 @@ void build_hierarchy(ch_s *h, const ch_graph_t *g, const ch_params_t *p) {
     b.label.zero(b.st);
     b.tracing = p->trace != 0;
     b.learned = p->priority == CH_PRIO_LEARNED;
+    b.composite = p->priority == CH_PRIO_COMPOSITE;
     if (b.learned) {
         b.mlp.load(p->mlp_weights, b.st);
         b.fx.alloc((size_t)n * 16);

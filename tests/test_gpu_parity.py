@@ -64,7 +64,8 @@ def test_golden_examples(name):
                           witness_memo_limit=spec.get("memo"),
                           witness_level_work=spec.get("level_work"),
                           witness_prune=bool(spec.get("prune")),
-                          witness_settle_cap=spec.get("theta"))
+                          witness_settle_cap=spec.get("theta"),
+                          composite=bool(spec.get("composite")))
     ex = g.export()
     assert ex["level"].tolist() == spec["expect_level"]
     assert ex["priority"].tolist() == spec["expect_priority"]

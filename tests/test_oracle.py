@@ -49,7 +49,8 @@ def test_golden_examples(name):
     tie = O.TIE_ID if spec.get("tie_break") == "id" else O.TIE_HASHED
     ch = O.build_ch(spec["graph"], spec["hop_limit"], tie, cmax=spec.get("cmax", O.CMAX_ALL),
                     ball=spec.get("ball", O.CMAX_ALL), theta=spec.get("theta", 0),
-                    prune=bool(spec.get("prune", 0)), level_work=spec.get("level_work", O.CMAX_ALL))
+                    prune=bool(spec.get("prune", 0)), level_work=spec.get("level_work", O.CMAX_ALL),
+                    composite=bool(spec.get("composite", 0)))
     assert sorted(map(tuple, ch.pruned.tolist())) == sorted(spec.get("pruned", []))
     if "expect_searches" in spec:
         assert ch.searches == spec["expect_searches"]
