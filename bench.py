@@ -334,6 +334,84 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def modes_record(args, g, off, tgt, wt, s_d, t_d, stream, steps=2, warmup=1):
+    """The method's other construction modes on the same graph and GPU:
+    memoised witness distances across rounds (Alg. 3's dist), with overlay
+    pruning, Alg. 3's settled-vertex cap, the composite priority; build
+    seconds (CUDA events), shortcuts, rounds, witness searches, mean search
+    space and queries/s on the first 100K pairs of the batch, whose answers
+    must equal the plain build's. Then one-to-all distances (PHAST sweeps)
+    on the plain hierarchy: 64 sources, microseconds per source and the
+    sweeps' algorithmic HBM bytes."""
+    import torch
+    from paper_2412_18008_gb300 import ch
+    nq = min(100_000, s_d.numel())
+    ds, dt = s_d[:nq], t_d[:nq]
+    modes = [("plain", {}), ("memo", {"witness_memo_limit": 1 << 30}),
+             ("memo_prune", {"witness_memo_limit": 1 << 30, "witness_prune": True}),
+             ("settle_cap_100", {"witness_settle_cap": 100}),
+             ("composite", {"composite": True})]
+    out, ref = {}, None
+    for name, kw in modes:
+        times = []
+        for k in range(warmup + steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = ch.CH.build(n=g.n, offsets=off, targets=tgt, weights=wt, hop_limit=args.hop_limit,
+                            stream=stream, **kw)
+            e1.record(stream)
+            stream.synchronize()
+            if k >= warmup:
+                times.append(e0.elapsed_time(e1))
+            if k + 1 < warmup + steps:
+                h.close()
+        st = h.stats()
+        h.set_query_config(1, 256, 1, 1)
+        d, sett = h.query(ds, dt, want_settled=True, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.query(ds, dt, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        d = d.cpu().numpy()
+        if ref is None:
+            ref = d
+        out[name] = {"build_s": statistics.mean(times) / 1e3, "shortcuts": st["shortcuts"],
+                     "rounds": st["rounds"], "witness_searches": st["witness_sources"],
+                     "witness_ms": st["witness_ms"],
+                     "mean_search_space": float(sett.cpu().numpy().view(np.uint32).mean()),
+                     "queries_per_s": nq / (e0.elapsed_time(e1) * 1e-3),
+                     "answers_equal_plain": bool(np.array_equal(d, ref))}
+        if name == "plain":
+            # one-to-all on the plain hierarchy: 4 passes of 16 sources
+            src = s_d[:64]
+            h.one_to_all(src, stream=stream)  # warm
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = h.one_to_all(src, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            h.query_status(stream)
+            ms = e0.elapsed_time(e1)
+            # algorithmic bytes per pass of 16 sources: per vertex and sweep a
+            # 64-B label row read and written, per CH edge 8 B plus a 64-B row,
+            # per vertex 64 B read and 64 B written by the output pass
+            m_ch = st["up_edges"] + st["down_edges"]
+            bytes_pass = 2 * 128 * g.n + 72 * m_ch + 128 * g.n
+            peak, _ = load_peaks()
+            gbs = 4 * bytes_pass / (ms * 1e-3) / 1e9
+            # spot check against the query kernel: the distances of pairs
+            # (source, target) read from the rows equal the batch's answers
+            tt = t_d[:64].long()
+            row_d = res[torch.arange(64, device=res.device), tt].cpu().numpy()
+            out["one_to_all"] = {"sources": 64, "ms": ms, "us_per_source": ms * 1e3 / 64,
+                                 "achieved_gbs": gbs, "hbm_frac": gbs / peak,
+                                 "matches_pair_queries": bool(np.array_equal(row_d, ref[:64]))}
+        h.close()
+    return out
+
+
 def compare_learned(args, steps=None, warmup=None):
     """Learned priority vs edge difference (one JSON line). geo1M: trained on
     traces of 20 seeded 256K-vertex graphs of the family, compared on a
@@ -732,7 +810,8 @@ def main():
         h_last.close()
         handles = []
         configs = {}
-        for name, fn in (("learned_geo1M", lambda: compare_learned(args, steps=3, warmup=1)),
+        for name, fn in (("modes_geo1M", lambda: modes_record(args, g, off_d, tgt_d, w_d, s_d, t_d, stream)),
+                         ("learned_geo1M", lambda: compare_learned(args, steps=3, warmup=1)),
                          ("serve_geo16M", lambda: serve_bench(args, "geo16M", 20_000))):
             t0 = time.perf_counter()
             try:

@@ -182,7 +182,9 @@ def geometric_knn_graph(n: int, k: int = 3, oneway_frac: float = 0.05,
     src = np.repeat(np.arange(n, dtype=np.int64), nbr.shape[1])
     dst = nbr.ravel()
     lo, hi = np.minimum(src, dst), np.maximum(src, dst)
-    key = np.unique(lo * n + hi)
+    key = np.sort(lo * n + hi)  # sorted distinct keys (np.unique's result, faster)
+    if key.size:
+        key = key[np.concatenate([[True], key[1:] != key[:-1]])]
     a, b = key // n, key % n
     E = a.size
     f = np.asarray(speeds, dtype=np.float64)[rng.integers(0, len(speeds), size=E)]
@@ -199,7 +201,13 @@ def geometric_knn_graph(n: int, k: int = 3, oneway_frac: float = 0.05,
     s = np.concatenate([a[fwd], b[bwd]])
     t = np.concatenate([b[fwd], a[bwd]])
     ww = np.concatenate([w[fwd], w[bwd]])
-    return csr_from_edges(n, s, t, ww)
+    # (s, t) pairs are distinct here, so ordering by s * n + t is the
+    # (src, dst, w) order csr_from_edges would produce
+    order = np.argsort(s * n + t, kind="stable")
+    s, t, ww = s[order], t[order], ww[order]
+    offsets = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(np.bincount(s, minlength=n), out=offsets[1:])
+    return Graph(n, offsets, t.astype(np.uint32), ww.astype(np.uint32))
 
 
 # ---------------------------------------------------------------------------
