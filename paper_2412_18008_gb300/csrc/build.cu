@@ -449,7 +449,7 @@ __global__ void k_score_prep(Dev d, const uint32_t *A, uint32_t nA, uint32_t sta
 // Steps 2 and 5: witness searches, one warp per source
 // --------------------------------------------------------------------------
 
-struct WarpSmem {
+struct __align__(16) WarpSmem {
     uint32_t key[WIT_T];
     uint32_t val[WIT_T];
     uint32_t fst[WIT_T];
@@ -716,10 +716,14 @@ __global__ void __launch_bounds__(WIT_WARPS * 32) k_witness(WArgs a) {
         // relaxing from the previous level's values (frontier snapshots);
         // skipped when the decisions are memoised.
         if (!memo_all && !(XM && bound == 0)) {
-        for (uint32_t t = lane; t < WIT_T; t += 32) {
-            w.key[t] = EMPTY;
-            w.val[t] = INF;
-            w.fst[t] = 0;
+        {
+            uint4 *k4 = reinterpret_cast<uint4 *>(w.key), *v4 = reinterpret_cast<uint4 *>(w.val),
+                  *f4 = reinterpret_cast<uint4 *>(w.fst);
+            for (uint32_t t = lane; t < WIT_T / 4; t += 32) {
+                k4[t] = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
+                v4[t] = make_uint4(INF, INF, INF, INF);
+                f4[t] = make_uint4(0, 0, 0, 0);
+            }
         }
         __syncwarp();
         if (lane == 0) {
@@ -1020,7 +1024,7 @@ constexpr int WB_FC = 2048;
 constexpr int WB_MBITS = 11;
 constexpr int WB_M = 1 << WB_MBITS;
 
-struct BlkSmem {
+struct __align__(16) BlkSmem {
     uint32_t key[WB_T];
     uint32_t val[WB_T];
     uint32_t fst[WB_T];
@@ -1071,16 +1075,6 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             continue;
         }
         unsigned long long l_vert = 0, l_edge = 0, l_mid = 0, l_midedge = 0, l_cand = 0, l_kept = 0;
-        for (uint32_t t = tid; t < (uint32_t)WB_T; t += blockDim.x) {
-            b.key[t] = EMPTY;
-            b.val[t] = INF;
-            b.fst[t] = 0;
-        }
-        if (MODE == MODE_PRUNE)
-            for (uint32_t t = tid; t < (uint32_t)WB_M; t += blockDim.x) {
-                b.mkey[t] = EMPTY;
-                b.mval[t] = ~0ull;
-            }
         if (tid == 0) {
             b.bound = 0;
             b.ovf = 0;
@@ -1091,27 +1085,40 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
         }
         __syncthreads();
         // Phase 0: heaviest candidate weight of the source, and whether every
-        // contracted middle has its score-phase decisions memoised.
+        // contracted middle has its score-phase decisions memoised. Each warp
+        // takes 32 of the source's out-edges and spreads their middles'
+        // out-lists over its lanes.
         uint32_t lb = 0;
-        for (uint32_t j = tid; j < sd; j += blockDim.x) {
-            const uint2 e = d.out_adj[sb + j];
-            if (!id_ok(d, e.x) || !is_middle<MODE>(d, e.x, r)) continue;
-            if (MODE == MODE_PRUNE && d.kround[e.x] != r + 1) b.memo_ok = 0;
-            const uint64_t ub = d.out_beg[e.x];
-            const uint32_t ud = out_list_ok(d, ub, d.out_deg[e.x]) ? d.out_deg[e.x] : 0;
-            ++l_mid;
-            l_midedge += ud;
-            for (uint32_t jj = 0; jj < ud; ++jj) {
-                const uint2 e2 = d.out_adj[ub + jj];
-                if (e2.x != s) {
-                    uint32_t known;
-                    if constexpr (XM) b.any = 1;
-                    if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &known))) {
-                        lb = max(lb, sat_add(e.y, e2.y));
-                        if constexpr (PR) {
-                            const uint32_t dw = direct_weight(d.out_adj, sb, sd, e2.x);
-                            if (dw != INF) atomicMax(&b.direct, dw);
-                        }
+        for (uint32_t c0 = warp * 32; c0 < sd; c0 += nwarps * 32) {
+            const uint32_t j = c0 + lane;
+            const bool valid = j < sd;
+            const uint2 e = valid ? d.out_adj[sb + j] : make_uint2(0, 0);
+            const bool mid = valid && id_ok(d, e.x) && is_middle<MODE>(d, e.x, r);
+            if (MODE == MODE_PRUNE && mid && d.kround[e.x] != r + 1) b.memo_ok = 0;
+            uint32_t cnt = mid ? d.out_deg[e.x] : 0;
+            const uint64_t ub = mid ? d.out_beg[e.x] : 0;
+            if (mid && !out_list_ok(d, ub, cnt)) cnt = 0;
+            l_mid += mid;
+            l_midedge += cnt;
+            const uint32_t incl = warp_incl_scan(cnt);
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            const uint32_t excl = incl - cnt;
+            for (uint32_t base = 0; base < total; base += 32) {
+                const uint32_t idx = base + lane;
+                const uint32_t o = warp_owner(excl, idx);
+                const uint64_t ub_o = __shfl_sync(FULL, ub, o);
+                const uint32_t w1 = __shfl_sync(FULL, e.y, o);
+                const uint32_t ex_o = __shfl_sync(FULL, excl, o);
+                if (idx >= total) continue;
+                const uint2 e2 = d.out_adj[ub_o + (idx - ex_o)];
+                if (e2.x == s) continue;
+                uint32_t known;
+                if constexpr (XM) b.any = 1;
+                if (!(XM && dmap_get(a.dm, dmap_key(s, e2.x), &known))) {
+                    lb = max(lb, sat_add(w1, e2.y));
+                    if constexpr (PR) {
+                        const uint32_t dw = direct_weight(d.out_adj, sb, sd, e2.x);
+                        if (dw != INF) atomicMax(&b.direct, dw);
                     }
                 }
             }
@@ -1132,6 +1139,26 @@ __global__ void __launch_bounds__(WB_THREADS) k_witness_block(WArgs a) {
             c_midedge += l_midedge;
             continue;
         }
+        // Empty the tables this source uses (16-byte stores): the search's
+        // only when it runs, the merge table in the contraction phase.
+        const bool searches = !memo_all && !(XM && bound == 0);
+        if (searches) {
+            uint4 *k4 = reinterpret_cast<uint4 *>(b.key), *v4 = reinterpret_cast<uint4 *>(b.val),
+                  *f4 = reinterpret_cast<uint4 *>(b.fst);
+            for (uint32_t t = tid; t < (uint32_t)WB_T / 4; t += blockDim.x) {
+                k4[t] = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
+                v4[t] = make_uint4(INF, INF, INF, INF);
+                f4[t] = make_uint4(0, 0, 0, 0);
+            }
+        }
+        if (MODE == MODE_PRUNE) {
+            uint4 *m4 = reinterpret_cast<uint4 *>(b.mkey);
+            ulonglong2 *mv2 = reinterpret_cast<ulonglong2 *>(b.mval);
+            for (uint32_t t = tid; t < (uint32_t)WB_M / 4; t += blockDim.x)
+                m4[t] = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
+            for (uint32_t t = tid; t < (uint32_t)WB_M / 2; t += blockDim.x) mv2[t] = make_ulonglong2(~0ull, ~0ull);
+        }
+        __syncthreads();
         if (tid == 0 && !memo_all) {
             const uint32_t h = ht_insert(b.key, WB_TBITS, s);
             b.val[h] = 0;
@@ -2246,14 +2273,35 @@ __global__ void k_relocate(Dev d, const uint32_t *X, uint32_t nX, const uint64_t
     }
 }
 
-__global__ void k_advance_tails(Ctl *ctl) {
-    ctl->out_tail += ctl->relocOut;
-    ctl->in_tail += ctl->relocIn;
+
+// Start of a round: its counters, and the score phase's witness work
+// counters, start from zero.
+__global__ void k_round_begin(Ctl *ctl) {
+    ctl->nS = ctl->nS2 = ctl->nF = ctl->nAnext = ctl->nOvf = ctl->nRec = 0;
+    ctl->candBound = ctl->degFout = ctl->degFin = ctl->degAnext = 0;
+    ctl->pruned = 0;
+    ctl->nDirty = 0;
+    ctl->work = ctl->work2 = ctl->work3 = ctl->nOvf2 = 0;
 }
 
-// End of a round's contraction: its counters are kept for the host's next
-// read, and the shortcut log advances past the round's records.
-__global__ void k_round_end(Ctl *ctl) {
+// Start of a round's contraction phase: its counters and its witness work
+// counters start from zero.
+__global__ void k_contract_begin(Ctl *ctl) {
+    ctl->cand = ctl->kept = ctl->merged = ctl->inserted = ctl->newEdges = 0;
+    ctl->nOvf = 0;
+    ctl->work = ctl->work2 = ctl->work3 = ctl->nOvf2 = 0;
+}
+
+// End of a round: the arena tails pass the lists relocated this round (when
+// any were), the next round's live count takes the compacted one, the
+// round's contraction counters are kept for the host's next read, and the
+// shortcut log advances past the round's records.
+__global__ void k_round_end(Ctl *ctl, int advance_tails) {
+    if (advance_tails) {
+        ctl->out_tail += ctl->relocOut;
+        ctl->in_tail += ctl->relocIn;
+    }
+    ctl->nVO = ctl->nVO2;
     ctl->s_cand = ctl->cand;
     ctl->s_kept = ctl->kept;
     ctl->s_merged = ctl->merged;
@@ -2605,8 +2653,8 @@ void Builder::normalise(const ch_graph_t *g) {
 
 template <int MODE>
 void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_max, uint32_t r) {
-    CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->nOvf, 0, 4, st));
-    CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->work, 0, 16, st));  // work, work2, work3, nOvf2
+    // the tiers' work counters (work, work2, work3, nOvf, nOvf2) are zeroed
+    // by k_round_begin / k_contract_begin before each phase
     WArgs a;
     a.d = d;
     a.S = Sl;
@@ -2738,9 +2786,8 @@ void Builder::run_rounds() {
         if (r > 0x7FFFFFF0u) throw Error{CH_ERANGE, "too many rounds"};
         cur_round = (int)r;
         // reset per-round counters
-        CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->nS, 0, 4 * 6, st));  // nS nS2 nF nAnext nOvf nRec
-        CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->candBound, 0, 8 * 4, st));
-        if (prune) CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->pruned, 0, 8 + 4, st));  // pruned, nDirty
+        k_round_begin<<<1, 1, 0, st>>>(ctl.ptr);
+        CH_CHECK_LAUNCH();
         // 1-2: score the affected set
         cudaEvent_t e0 = start();
         const uint32_t sstamp = 2 * r + 1, cstamp = 2 * r + 2;
@@ -2846,7 +2893,8 @@ void Builder::run_rounds() {
             d.out_arena = out_adj.count;
             d.in_arena = in_adj.count;
         }
-        CH_CUDA_TRY(cudaMemsetAsync(&ctl.ptr->cand, 0, 8 * 5, st));
+        k_contract_begin<<<1, 1, 0, st>>>(ctl.ptr);
+        CH_CHECK_LAUNCH();
         // 5: witness searches for V_F's candidates
         e0 = start();
         if (nS2) witness<MODE_PRUNE>(S2.ptr, &ctl.ptr->nS2, nS2, r);
@@ -2871,19 +2919,16 @@ void Builder::run_rounds() {
             k_relocate<<<gw, 256, 0, st>>>(d, Anext.ptr, nAnext, reqO.ptr, posO.ptr, reqI.ptr,
                                            posI.ptr);
             CH_CHECK_LAUNCH();
-            k_advance_tails<<<1, 1, 0, st>>>(ctl.ptr);
-            CH_CHECK_LAUNCH();
         }
         const uint64_t rec_bound = std::max<uint64_t>(cb, 1);
         k_insert<<<grid_for(rec_bound, 256, sms * 8), 256, 0, st>>>(
             d, rec.ptr, rec_flag.ptr, r, log.ptr, log_round.ptr);
         CH_CHECK_LAUNCH();
-        k_round_end<<<1, 1, 0, st>>>(ctl.ptr);
-        CH_CHECK_LAUNCH();
         compact_alive(VO.ptr, &ctl.ptr->nVO, nVO, level.ptr, VO2.ptr, &ctl.ptr->nVO2, tmp.ptr,
                       scan32.ptr, st);
         std::swap(VO, VO2);
-        CH_CUDA_TRY(cudaMemcpyAsync(&ctl.ptr->nVO, &ctl.ptr->nVO2, 4, cudaMemcpyDeviceToDevice, st));
+        k_round_end<<<1, 1, 0, st>>>(ctl.ptr, nAnext ? 1 : 0);
+        CH_CHECK_LAUNCH();
         std::swap(A, Anext);
         mark(&h->t_update_ms, e0, 4);
         // this round's row: what is known now; its contraction counters
