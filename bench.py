@@ -158,6 +158,24 @@ def parse():
     return ap.parse_args()
 
 
+def l2_read_gbs(dev, mbytes: int = 48, reps: int = 50) -> float:
+    """L2 read bandwidth, measured: a float32 sum over a buffer that stays
+    in the 129 MB L2 (warmed first), timed with CUDA events. A lower bound
+    of the L2 peak (the reduction also has to issue its arithmetic)."""
+    import torch
+    x = torch.ones(mbytes * (1 << 20) // 4, dtype=torch.float32, device=dev)
+    for _ in range(5):
+        x.sum()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        x.sum()
+    e1.record()
+    torch.cuda.synchronize()
+    return reps * x.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:

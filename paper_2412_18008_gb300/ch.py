@@ -286,11 +286,11 @@ class CH:
                 raise ValueError(f"mlp_weights needs {CH_MLP_NPARAM} floats")
             keep.append(wts)
             p.priority = CH_PRIO_LEARNED
+            p.mlp_weights = wts.ctypes.data_as(C.c_void_p)
         if composite:
             if mlp_weights is not None:
                 raise ValueError("composite and learned priorities exclude each other")
             p.priority = CH_PRIO_COMPOSITE
-            p.mlp_weights = wts.ctypes.data_as(C.c_void_p)
         return g, p, keep
 
     @classmethod

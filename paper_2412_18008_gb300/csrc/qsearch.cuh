@@ -247,75 +247,41 @@ __device__ bool block_search(QBSmem<TB> &q, const QArgs &a, QStat &stat) {
                     const uint32_t stotal = __shfl_sync(FULL, sincl, 31);
                     const uint32_t sexcl = sincl - scnt;
                     bool stalled = false;
-                    // the edge of this lane in the chunk at `base` (loads of
-                    // the next chunk overlap the probes of the current one)
-                    auto fetch_stall = [&](uint32_t base, uint2 &e, uint32_t &odx, uint32_t &odir) {
+                    for (uint32_t base = 0; base < stotal; base += 32) {
                         const uint32_t e0 = base + lane;
                         const uint32_t o = warp_owner(sexcl, e0);
                         const uint32_t osb = __shfl_sync(FULL, sb, o);
                         const uint32_t oex = __shfl_sync(FULL, sexcl, o);
-                        odx = __shfl_sync(FULL, dx, o);
-                        odir = __shfl_sync(FULL, ent, o) >> 31;
-                        const bool v = e0 < stotal;
-                        if (v) e = (odir ? a.up_adj : a.dn_adj)[osb + (e0 - oex)];
-                        return v;
-                    };
-                    uint2 se_c = make_uint2(0, 0);
-                    uint32_t sdx_c = 0, sdir_c = 0;
-                    bool sv_c = stotal > 0 && fetch_stall(0, se_c, sdx_c, sdir_c);
-                    for (uint32_t base = 0; base < stotal; base += 32) {
-                        uint2 se_n = make_uint2(0, 0);
-                        uint32_t sdx_n = 0, sdir_n = 0;
-                        bool sv_n = false;
-                        if (base + 32 < stotal) sv_n = fetch_stall(base + 32, se_n, sdx_n, sdir_n);
+                        const uint32_t odx = __shfl_sync(FULL, dx, o);
+                        const uint32_t odir = __shfl_sync(FULL, ent, o) >> 31;
                         bool st = false;
-                        if (sv_c) {
+                        if (e0 < stotal) {
                             ++stat.edges;
-                            const uint32_t ys = se_c.x < a.n ? qb_find<TB>(q.key, se_c.x) : EMPTY;
-                            if (ys != EMPTY) st = sat_add(sdir_c ? q.db[ys] : q.df[ys], se_c.y) < sdx_c;
+                            const uint2 e = (odir ? a.up_adj : a.dn_adj)[osb + (e0 - oex)];
+                            const uint32_t ys = e.x < a.n ? qb_find<TB>(q.key, e.x) : EMPTY;
+                            if (ys != EMPTY) st = sat_add(odir ? q.db[ys] : q.df[ys], e.y) < odx;
                         }
                         const uint32_t B = __ballot_sync(FULL, st);
                         const uint32_t lo = max(sexcl, base), hi = min(sexcl + scnt, base + 32);
                         if (hi > lo && (B & qb_lane_range(lo - base, hi - base))) stalled = true;
-                        se_c = se_n;
-                        sdx_c = sdx_n;
-                        sdir_c = sdir_n;
-                        sv_c = sv_n;
                     }
                     if (stalled) cnt = 0;
                 }
                 const uint32_t incl = warp_incl_scan(cnt);
                 const uint32_t total = __shfl_sync(FULL, incl, 31);
                 const uint32_t excl = incl - cnt;
-                // as above: the next chunk's edge loads overlap this chunk's
-                // relaxations
-                auto fetch = [&](uint32_t base, uint2 &e, uint32_t &odx, uint32_t &odir) {
+                for (uint32_t base = 0; base < total; base += 32) {
                     const uint32_t e0 = base + lane;
                     const uint32_t o = warp_owner(excl, e0);
                     const uint32_t ob = __shfl_sync(FULL, b, o);
                     const uint32_t oex = __shfl_sync(FULL, excl, o);
-                    odx = __shfl_sync(FULL, dx, o);
-                    odir = __shfl_sync(FULL, ent, o) >> 31;
-                    const bool v = e0 < total;
-                    if (v) e = (odir ? a.dn_adj : a.up_adj)[ob + (e0 - oex)];
-                    return v;
-                };
-                uint2 e_c = make_uint2(0, 0);
-                uint32_t dx_c = 0, dir_c = 0;
-                bool v_c = total > 0 && fetch(0, e_c, dx_c, dir_c);
-                for (uint32_t base = 0; base < total; base += 32) {
-                    uint2 e_n = make_uint2(0, 0);
-                    uint32_t dx_n = 0, dir_n = 0;
-                    bool v_n = false;
-                    if (base + 32 < total) v_n = fetch(base + 32, e_n, dx_n, dir_n);
-                    if (v_c) {
+                    const uint32_t odx = __shfl_sync(FULL, dx, o);
+                    const uint32_t odir = __shfl_sync(FULL, ent, o) >> 31;
+                    if (e0 < total) {
                         ++stat.edges;
-                        qb_relax<PRUNE, TB>(q, a, dir_c, e_c, dx_c, lvl, nxt_cnt, next_front);
+                        const uint2 e = (odir ? a.dn_adj : a.up_adj)[ob + (e0 - oex)];
+                        qb_relax<PRUNE, TB>(q, a, odir, e, odx, lvl, nxt_cnt, next_front);
                     }
-                    e_c = e_n;
-                    dx_c = dx_n;
-                    dir_c = dir_n;
-                    v_c = v_n;
                 }
             }
         } else {

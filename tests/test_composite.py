@@ -78,3 +78,17 @@ def test_gpu_equals_oracle_on_a_geometric_graph_with_trace():
     assert [composite_of_row(r) for r in tr["rows"]] == tr["prio"].tolist()
     s, t = I.random_pairs(g.n, 4000, seed=64)
     assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))
+
+
+def test_binding_marshals_the_priority_modes():
+    from paper_2412_18008_gb300 import ch
+    g = I.grid_graph(4, 4, 0.0, 1, 5, seed=1)
+    args = (g, None, None, None, None, 5, ch.CH_TIE_HASHED, 0, None)
+    _, p, _ = ch.CH._marshal(*args, None, False, None, 0, composite=True)
+    assert p.priority == ch.CH_PRIO_COMPOSITE and not p.mlp_weights
+    _, p, keep = ch.CH._marshal(*args, ch.mlp_init(1), False, None, 0)
+    assert p.priority == ch.CH_PRIO_LEARNED and p.mlp_weights
+    _, p, _ = ch.CH._marshal(*args, None, False, None, 0)
+    assert p.priority == ch.CH_PRIO_EDGE_DIFF
+    with pytest.raises(ValueError):
+        ch.CH._marshal(*args, ch.mlp_init(1), False, None, 0, composite=True)

@@ -146,14 +146,21 @@ def test_settled_cap_small_families(name, g, theta, limit, prune, cmax):
     assert np.array_equal(d.astype(np.uint64).reshape(g.n, g.n), all_pairs_truth(g))
 
 
-@pytest.mark.parametrize("theta", [50, 400])
-def test_settled_cap_geometric_and_dense(theta):
-    # 400 settled vertices outgrow a warp's 256-slot table: the global-memory tier
-    for g in (I.geometric_knn_graph(20_000, seed=158),
-              I.random_digraph(1500, 9000, 1, 1000, seed=159, allow_loops=False)):
-        och = O.build_ch(g, 5, theta=theta)
-        gch = _ch().CH.build(g, hop_limit=5, witness_settle_cap=theta)
-        assert_same_hierarchy(gch, och)
-        s, t = I.random_pairs(g.n, 3000, seed=160)
-        assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))
+def _settle_cap_cases():
+    geo = lambda: I.geometric_knn_graph(20_000, seed=158)
+    # 400 settled vertices outgrow a warp's 256-slot table: the global-memory
+    # tier. (A small cap on this dense digraph lets the overlay fill in: at
+    # theta = 50 the oracle alone needs a minute for 600 vertices.)
+    dense = lambda: I.random_digraph(600, 3600, 1, 1000, seed=159, allow_loops=False)
+    return [("geo20K", geo, 50), ("geo20K", geo, 400), ("dense600", dense, 400)]
+
+
+@pytest.mark.parametrize("name,make,theta", _settle_cap_cases(), ids=lambda v: str(v) if not callable(v) else "")
+def test_settled_cap_geometric_and_dense(name, make, theta):
+    g = make()
+    och = O.build_ch(g, 5, theta=theta)
+    gch = _ch().CH.build(g, hop_limit=5, witness_settle_cap=theta)
+    assert_same_hierarchy(gch, och)
+    s, t = I.random_pairs(g.n, 3000, seed=160)
+    assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))
 
