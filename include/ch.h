@@ -405,6 +405,22 @@ int ch_get_round_stats(const ch_t *ch, uint64_t *out, uint32_t max_rounds);
 #define CH_NTIME 6u
 int ch_get_round_times(const ch_t *ch, double *out, uint32_t max_rounds);
 
+/* Core distance table (the partial hierarchy of Sec. 3: a candidate bound
+ * max_candidates_per_vertex leaves a core; its queries are the paper's
+ * core-aware queries). Computes, for every pair of core vertices, the
+ * shortest-path distance between them (one search per core vertex inside
+ * the core, on the device) and keeps it with the hierarchy: core_size^2
+ * uint32 in device memory. From then on ch_query_batch and
+ * ch_query_batch_static stop both upward searches at the core's vertices
+ * and join them through the table, min over core entries c1 of s's search
+ * and c2 of t's of d_s(c1) + table(c1, c2) + d_t(c2), besides the meetings
+ * below the core; answers are unchanged, search spaces smaller (a query
+ * with more than one tile of core entries in either direction falls back
+ * to the search inside the core). Synchronous on `stream`. Errors:
+ * CH_ERANGE when core_size^2 * 4 > max_bytes (nothing is kept); a handle
+ * without a core keeps no table. The table is not saved by ch_save. */
+int ch_core_table(ch_t *ch, uint64_t max_bytes, void *stream);
+
 /* Copies the hierarchy to HOST buffers; any pointer may be NULL to skip it.
  *   level[n]    round in which each vertex was contracted
  *   priority[n] its score (int32) when it was contracted

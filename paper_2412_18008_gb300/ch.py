@@ -137,6 +137,8 @@ def load(build_if_missing: bool = True):
     lib.ch_mlp_train.argtypes = [P, P, C.c_uint64, C.POINTER(TrainT), P, P, P, P]
     lib.ch_mlp_forward.argtypes = [P, P, C.c_uint64, P, P]
     lib.ch_mlp_targets.argtypes = [P, C.c_uint64, P, P]
+    lib.ch_core_table.argtypes = [P, C.c_uint64, P]
+    lib.ch_core_table.restype = C.c_int
     for f in ("ch_export_trace", "ch_mlp_train", "ch_mlp_forward", "ch_mlp_targets"):
         getattr(lib, f).restype = C.c_int
     lib.ch_server_start.argtypes = [P, C.POINTER(ServerParamsT), C.POINTER(P)]
@@ -429,6 +431,12 @@ class CH:
         _check(load().ch_one_to_all(self._h, src.data_ptr(), src.numel(), out.data_ptr(),
                                     _stream_ptr(stream)))
         return out
+
+    def core_table(self, max_bytes: int = 16 << 30, stream=None):
+        """ch_core_table: the core's all-pairs distance table; queries then
+        join their upward searches through it instead of searching inside
+        the core."""
+        _check(load().ch_core_table(self._h, int(max_bytes), _stream_ptr(stream)))
 
     # -- saving and loading -------------------------------------------------
     def save(self, path: str):

@@ -560,6 +560,14 @@ int ch_mlp_train(const int64_t *rows, const float *labels, uint64_t n, const ch_
     });
 }
 
+int ch_core_table(ch_t *ch, uint64_t max_bytes, void *stream) {
+    if (!ch) {
+        g_last_error = "null handle";
+        return CH_EINVAL;
+    }
+    return guarded([&] { core_table(ch, max_bytes, (cudaStream_t)stream); });
+}
+
 int ch_mlp_targets(const int64_t *rows, uint64_t n, float *y_out, void *stream) {
     if (n && (!rows || !y_out)) {
         g_last_error = "bad target arguments";

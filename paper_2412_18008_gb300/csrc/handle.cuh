@@ -75,6 +75,12 @@ struct ch_s {
     gbch::DevBuf<uint32_t> phast_d;
     gbch::DevBuf<uint32_t> phast_lv;
     gbch::DevBuf<uint32_t> phast_flag;
+
+    // Core distance table (ch_core_table): core_n x core_n shortest-path
+    // distances between the core vertices, which are the ranks
+    // [core_lo, n); empty when none was built (core_lo = n).
+    gbch::DevBuf<uint32_t> core_tab;
+    uint32_t core_lo = 0, core_n = 0;
 };
 
 namespace gbch {
@@ -110,6 +116,9 @@ void save_hierarchy(const ch_s *h, const char *path);
 ch_s *load_hierarchy(const char *path);
 void query_one_to_many(ch_s *h, uint32_t s, const uint32_t *dst, uint64_t k, uint32_t *dist_out,
                        cudaStream_t st);
+
+// Core distance table (core.cu); CH_ERANGE when it would exceed max_bytes.
+void core_table(ch_s *h, uint64_t max_bytes, cudaStream_t st);
 
 // One-to-all distances for k sources (phast.cu).
 void one_to_all(ch_s *h, const uint32_t *src, uint64_t k, uint32_t *dist_out, cudaStream_t st);

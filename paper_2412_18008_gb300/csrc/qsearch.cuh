@@ -64,6 +64,11 @@ struct QArgs {
     uint32_t *ovf;
     uint32_t *err;
     unsigned long long *stats;  // [0] expansions, [1] edges scanned (or null)
+    // Core distance table (or null): the searches do not expand the core's
+    // vertices (ranks >= core_lo) and join through core_tab (core_n x
+    // core_n distances) instead.
+    const uint32_t *core_tab = nullptr;
+    uint32_t core_lo = 0, core_n = 0;
 };
 
 template <int TB>
@@ -167,6 +172,7 @@ __device__ __forceinline__ void qb_entry(const QBSmem<TB> &q, const QArgs &a, bo
     cnt = 0;
     if (xok && b <= e_end && e_end <= n_edges) cnt = e_end - b;
     else if (xok) atomicOr(a.err, QERR_BOUND);
+    if (a.core_tab && x >= a.core_lo) cnt = 0;  // a core vertex: joined through the table
     dx = cnt ? (dir ? q.db[slot] : q.df[slot]) : INF;
 }
 
@@ -364,12 +370,48 @@ __device__ bool block_query(QBSmem<TB> &q, const QArgs &a, uint32_t rs, uint32_t
         q.cnt3[1] = 0;
         q.cnt3[2] = 0;
     }
-    const bool ok = block_search<PRUNE, WARP, TB, STALL>(q, a, stat);
+    bool ok = block_search<PRUNE, WARP, TB, STALL>(q, a, stat);
     // q.mu only steered pruning; the answer is the least meeting sum.
     __syncthreads();
-    if (tid == 0) q.mu = INF;
+    if (tid == 0) {
+        q.mu = INF;
+        q.cnt3[0] = 0;
+        q.cnt3[1] = 0;
+    }
     __syncthreads();
     uint32_t mu = INF, cnt = 0;
+    if (a.core_tab && ok) {
+        // Core entries of the two searches (their slots, in the two
+        // frontier arrays, free now), then the least
+        // d_s(c1) + table(c1, c2) + d_t(c2) over every pair.
+        constexpr uint32_t FC = QBSmem<TB>::FC;
+        for (uint32_t j = tid; j < QBSmem<TB>::T; j += blockDim.x) {
+            const uint32_t k = q.key[j];
+            if (k == EMPTY || k < a.core_lo || k >= a.n) continue;
+            if (q.df[j] != INF) {
+                const uint32_t p = atomicAdd(&q.cnt3[0], 1u);
+                if (p < FC) q.front[0][p] = j;
+            }
+            if (q.db[j] != INF) {
+                const uint32_t p = atomicAdd(&q.cnt3[1], 1u);
+                if (p < FC) q.front[1][p] = j;
+            }
+        }
+        __syncthreads();
+        const uint32_t nf = q.cnt3[0], nb = q.cnt3[1];
+        if (nf > FC || nb > FC) {
+            ok = false;  // too many core entries: redone by the full search
+        } else {
+            const uint64_t pairs = (uint64_t)nf * nb;
+            for (uint64_t p = tid; p < pairs; p += blockDim.x) {
+                const uint32_t sf = q.front[0][p / nb], sb = q.front[1][p % nb];
+                const uint32_t cf = q.key[sf] - a.core_lo, cb = q.key[sb] - a.core_lo;
+                const uint32_t dcc = a.core_tab[(uint64_t)cf * a.core_n + cb];
+                mu = min(mu, sat_add(sat_add(q.df[sf], dcc), q.db[sb]));
+            }
+        }
+        __syncthreads();
+    }
     for (uint32_t j = tid; j < QBSmem<TB>::T; j += blockDim.x) {
         const uint32_t f = q.df[j], g = q.db[j];
         mu = min(mu, sat_add(f, g));

@@ -312,6 +312,9 @@ void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
         a.stats = h->q_stats.ptr;
         a.in_list = nullptr;
         a.in_cnt = 0;
+        a.core_tab = h->core_n ? h->core_tab.ptr : nullptr;
+        a.core_lo = h->core_lo;
+        a.core_n = h->core_n;
         CH_CUDA_TRY(cudaMemsetAsync(h->qwork.ptr, 0, 8 * sizeof(uint32_t), st));
         // Pruned searches unless the caller asked for search-space sizes,
         // which are defined by the exhaustive upward searches.
@@ -616,6 +619,9 @@ void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint6
     a.ovf_cnt = 2;
     a.err = h->qerr.ptr;
     a.stats = h->q_stats.ptr;
+    a.core_tab = h->core_n ? h->core_tab.ptr : nullptr;
+    a.core_lo = h->core_lo;
+    a.core_n = h->core_n;
     // the counters keep the previous call's values: clear them
     CH_CUDA_TRY(cudaMemsetAsync(scratch, 0, kStaticScratchHead * sizeof(uint32_t), st));
     // one block-kernel pass (large tables): the scratch holds one list

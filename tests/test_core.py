@@ -152,3 +152,60 @@ def test_hub_sources_use_the_global_memory_tier(cmax, ball):
     assert_same_hierarchy(gch, och)
     s, t = I.random_pairs(g.n, 3000, seed=101)
     assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))
+
+
+# ---------------------------------------------------------------------------
+# Core distance table (ch_core_table): queries join their upward searches
+# through the core's all-pairs distances instead of searching inside it
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("cmax", [0, 4, 12])
+@pytest.mark.parametrize("name,g", FAMILIES, ids=[n for n, _ in FAMILIES])
+def test_core_table_answers_every_pair(name, g, cmax):
+    gch = _ch().CH.build(g, hop_limit=5, max_candidates_per_vertex=cmax)
+    gch.core_table()
+    s, t = np.meshgrid(np.arange(g.n), np.arange(g.n), indexing="ij")
+    s, t = s.ravel().astype(np.uint32), t.ravel().astype(np.uint32)
+    truth = all_pairs_truth(g)
+    d = gch.query(s, t)
+    assert np.array_equal(d.astype(np.uint64).reshape(g.n, g.n), truth)
+    for cfg in _ch().QUERY_CONFIGS:
+        gch.set_query_config(*cfg)
+        assert np.array_equal(gch.query(s, t).astype(np.uint64).reshape(g.n, g.n), truth), cfg
+
+
+@pytest.mark.parametrize("cmax", [16, 256])
+def test_core_table_on_rmat(cmax):
+    g = I.rmat_graph(scale=12, nsamples=1 << 15, wmax=1000, seed=91)
+    och = O.build_ch(g, 5, cmax=cmax)
+    core = np.nonzero(och.level == och.rounds)[0].astype(np.uint32)
+    gch = _ch().CH.build(g, hop_limit=5, max_candidates_per_vertex=cmax)
+    s, t = I.random_pairs(g.n, 3000, seed=92)
+    _, full = gch.query(s, t, want_settled=True)
+    gch.core_table()
+    # between core vertices a query reads the table itself
+    rng = np.random.default_rng(93)
+    cs = core[rng.integers(0, core.size, 2000)]
+    ct = core[rng.integers(0, core.size, 2000)]
+    assert np.array_equal(gch.query(cs, ct), O.dijkstra_pairs(g, cs, ct))
+    d, joined = gch.query(s, t, want_settled=True)
+    assert np.array_equal(d, O.dijkstra_pairs(g, s, t))
+    for cfg in _ch().QUERY_CONFIGS:
+        gch.set_query_config(*cfg)
+        assert np.array_equal(gch.query(s, t), d), cfg
+    # the searches stop at the core: fewer labels than the search inside it
+    assert joined.mean() < full.mean()
+
+
+def test_core_table_byte_limit():
+    g = I.rmat_graph(scale=10, nsamples=1 << 13, wmax=100, seed=94)
+    gch = _ch().CH.build(g, hop_limit=3, max_candidates_per_vertex=16)
+    core = gch.stats()["core_vertices"]
+    assert core > 10
+    with pytest.raises(_ch().CHError) as ei:
+        gch.core_table(max_bytes=4 * core * core - 1)
+    assert ei.value.code == _ch().CH_ERANGE
+    s, t = I.random_pairs(g.n, 2000, seed=95)
+    assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))  # no table: the full search
+    gch.core_table(max_bytes=4 * core * core)
+    assert np.array_equal(gch.query(s, t), O.dijkstra_pairs(g, s, t))
