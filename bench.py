@@ -402,7 +402,7 @@ def modes_record(args, g, off, tgt, wt, s_d, t_d, stream, steps=2, warmup=1):
                      "queries_per_s": nq / (e0.elapsed_time(e1) * 1e-3),
                      "answers_equal_plain": bool(np.array_equal(d, ref))}
         if name == "plain":
-            # one-to-all on the plain hierarchy: 4 passes of 16 sources
+            # one-to-all on the plain hierarchy: one pass of 64 sources
             src = s_d[:64]
             h.one_to_all(src, stream=stream)  # warm
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -412,13 +412,14 @@ def modes_record(args, g, off, tgt, wt, s_d, t_d, stream, steps=2, warmup=1):
             stream.synchronize()
             h.query_status(stream)
             ms = e0.elapsed_time(e1)
-            # algorithmic bytes per pass of 16 sources: per vertex and sweep a
-            # 64-B label row read and written, per CH edge 8 B plus a 64-B row,
-            # per vertex 64 B read and 64 B written by the output pass
+            # algorithmic bytes of one pass of 64 sources: per vertex and
+            # sweep a 256-B label row read and written, per CH edge 8 B plus
+            # a 256-B row, per vertex 256 B read and 256 B written by the
+            # output pass
             m_ch = st["up_edges"] + st["down_edges"]
-            bytes_pass = 2 * 128 * g.n + 72 * m_ch + 128 * g.n
+            bytes_pass = 2 * 512 * g.n + 264 * m_ch + 512 * g.n
             peak, _ = load_peaks()
-            gbs = 4 * bytes_pass / (ms * 1e-3) / 1e9
+            gbs = bytes_pass / (ms * 1e-3) / 1e9
             # spot check against the query kernel: the distances of pairs
             # (source, target) read from the rows equal the batch's answers
             tt = t_d[:64].long()

@@ -18,19 +18,21 @@
 //             edges (x, u); x lies in a higher level, so d(x) is final. No
 //             atomics: each vertex is written by its own thread.
 //
-// Layout: the labels of PK = 16 sources are interleaved per vertex in rank
-// order, D[r * PK + i], so the 16 threads that serve one vertex read and
-// write one 64-byte row and every gather along an edge is one coalesced
-// 64-byte segment. Levels with more than TAIL_MAX vertices get a launch
+// Layout: the labels of PK = 64 sources are interleaved per vertex in rank
+// order, D[r * PK + i], so the 64 threads that serve one vertex read and
+// write one 256-byte row and every gather along an edge is one coalesced
+// 256-byte segment. A pass costs a chain of dependent level steps whatever
+// its width, so the wider pass spreads that latency over more sources.
+// Levels with more than TAIL_MAX vertices get a launch
 // each; the run of smaller levels at the top of the hierarchy (where levels
 // hold a handful of vertices) is walked by one block with a barrier between
 // levels. The result leaves D through one permuting pass, out[i * n + v] =
 // D[rank[v] * PK + i].
 //
 // Algorithmic bytes per batch of PK sources, both sweeps: the label rows
-// (64 B read and 64 B written per vertex and sweep), 8 B per E_up / E_down
-// entry plus a 64-B label row per entry, and the offsets; then 64 B read and
-// 4 B * PK written per vertex for the output.
+// (4 * PK B read and written per vertex and sweep), 8 B per E_up / E_down
+// entry plus a 4 * PK-B label row per entry, and the offsets; then 4 * PK B
+// read and 4 * PK B written per vertex for the output.
 
 #include <algorithm>
 #include <vector>
@@ -40,7 +42,7 @@
 namespace gbch {
 namespace {
 
-constexpr uint32_t PK = 16;            // sources per pass (labels interleaved per vertex)
+constexpr uint32_t PK = 64;            // sources per pass (labels interleaved per vertex)
 constexpr uint32_t TAIL_MAX = 512;     // largest level the one-block tail walks
 constexpr int TAIL_THREADS = 1024;
 constexpr uint32_t PERR_RANGE = 1u;    // a source id >= n (same bit as the query kernels)
@@ -156,18 +158,13 @@ __global__ void k_phast_out(const uint32_t *D, const uint32_t *rank, uint32_t n,
             continue;
         }
         const uint4 *row = reinterpret_cast<const uint4 *>(D + (uint64_t)r * PK);
-        uint32_t lab[PK];
-#pragma unroll
-        for (uint32_t q = 0; q < PK / 4; ++q) {
+        for (uint32_t q = 0; q < PK / 4 && 4 * q < nsrc; ++q) {
             const uint4 x = row[q];
-            lab[4 * q] = x.x;
-            lab[4 * q + 1] = x.y;
-            lab[4 * q + 2] = x.z;
-            lab[4 * q + 3] = x.w;
-        }
+            const uint32_t lab[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-        for (uint32_t i = 0; i < PK; ++i)
-            if (i < nsrc) out[(uint64_t)i * n + v] = lab[i];
+            for (uint32_t j = 0; j < 4; ++j)
+                if (4 * q + j < nsrc) out[(uint64_t)(4 * q + j) * n + v] = lab[j];
+        }
     }
 }
 
@@ -204,7 +201,7 @@ void one_to_all(ch_s *h, const uint32_t *src, uint64_t k, uint32_t *dist_out, cu
     for (uint64_t b = 0; b < k; b += PK) {
         const uint32_t nsrc = (uint32_t)std::min<uint64_t>(PK, k - b);
         CH_CUDA_TRY(cudaMemsetAsync(D, 0xFF, (size_t)n * PK * sizeof(uint32_t), st));
-        k_phast_seed<<<1, 32, 0, st>>>(D, src + b, nsrc, h->rank.ptr, n, err);
+        k_phast_seed<<<1, PK, 0, st>>>(D, src + b, nsrc, h->rank.ptr, n, err);
         CH_CHECK_LAUNCH();
         // upward: big levels one launch each, the small top levels in one
         // block, then the core to its fixpoint

@@ -1,7 +1,7 @@
 """One-to-all distances on the GPU (ch_one_to_all, the PHAST sweeps) against
 the oracle's one-to-all, which is pinned to scipy's all-pairs Dijkstra in
 test_witness_modes.py: every row bit for bit, with and without a core, for
-ragged source batches (the kernel runs 16 sources at a time), on a loaded
+ragged source batches (the kernel runs 64 sources at a time), on a loaded
 hierarchy, and with an out-of-range source."""
 import numpy as np
 import pytest
@@ -40,7 +40,7 @@ def test_small_families_all_sources(name, g, cmax):
     assert np.array_equal(got, och.one_to_all(np.arange(g.n)))
 
 
-@pytest.mark.parametrize("k", [1, 15, 16, 17, 40])
+@pytest.mark.parametrize("k", [1, 15, 16, 17, 63, 64, 65, 150])
 def test_geometric_ragged_batches(k):
     g = I.geometric_knn_graph(20_000, seed=131)
     h = _ch().CH.build(g, hop_limit=5)
