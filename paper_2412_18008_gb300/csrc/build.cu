@@ -1936,17 +1936,17 @@ __global__ void k_contract_prep(Dev d, const uint32_t *F, uint32_t src_stamp, ui
     const uint32_t nF = d.ctl->nF;
     const uint32_t lane = lane_id();
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    // the warp's sums over its vertices, added to the totals once at the end
+    unsigned long long w_cand = 0, w_out = 0, w_in = 0, w_aff = 0;
     for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nF; i += nwarps) {
         const uint32_t u = F[i];
         if (!id_ok(d, u)) continue;
         const uint64_t ob = d.out_beg[u], ib = d.in_beg[u];
         const uint32_t od = out_list_ok(d, ob, d.out_deg[u]) ? d.out_deg[u] : 0;
         const uint32_t id = in_list_ok(d, ib, d.in_deg[u]) ? d.in_deg[u] : 0;
-        if (lane == 0) {
-            atomicAdd(&d.ctl->candBound, (unsigned long long)od * id);
-            atomicAdd(&d.ctl->degFout, (unsigned long long)od);
-            atomicAdd(&d.ctl->degFin, (unsigned long long)id);
-        }
+        w_cand += (unsigned long long)od * id;
+        w_out += od;
+        w_in += id;
         unsigned long long deg_sum = 0;
         for (uint32_t j0 = 0; j0 < id + od; j0 += 32) {
             const uint32_t j = j0 + lane;
@@ -1965,9 +1965,17 @@ __global__ void k_contract_prep(Dev d, const uint32_t *F, uint32_t src_stamp, ui
             const uint32_t pa = warp_append(aff, &d.ctl->nAnext);
             if (aff) Anext[pa] = x;
         }
+        w_aff += deg_sum;  // lane-local; folded over the warp at the end
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) deg_sum += __shfl_xor_sync(FULL, deg_sum, o);
-        if (lane == 0 && deg_sum) atomicAdd(&d.ctl->degAnext, deg_sum);
+    for (int o = 16; o > 0; o >>= 1) w_aff += __shfl_xor_sync(FULL, w_aff, o);
+    if (lane == 0) {
+        if (w_aff) atomicAdd(&d.ctl->degAnext, w_aff);
+        if (w_out + w_in) {
+            atomicAdd(&d.ctl->candBound, w_cand);
+            atomicAdd(&d.ctl->degFout, w_out);
+            atomicAdd(&d.ctl->degFin, w_in);
+        }
     }
 }
 
