@@ -66,7 +66,11 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) of the k_query_block launches of the full 1M
 # query batch (first pass + overflow redo), from an ncu capture of the
 # current kernel on this workload (set to None when the kernel changes).
-QUERY_TRAFFIC_PER_LAUNCH = 85_268_000
+QUERY_TRAFFIC_PER_LAUNCH = None
+# L2 bytes per query of that kernel in that configuration (lts__t_sectors *
+# 32 over a 200K-query pass of the same workload; L2 traffic is per-query
+# work, so it scales with the queries of a batch).
+QUERY_L2_BYTES_PER_QUERY = 397_587
 
 
 def max_over_ranks(values, world: int, device):
@@ -770,6 +774,15 @@ def main():
     else:
         # with stalling each expansion also reads the other CSR's two offsets
         stall = bool(qcfg[3]) if qcfg else False
+        default_cfg = qcfg is None or tuple(qcfg) == (1, 256, 1, 1)
+        l2_record = None
+        if args.workload == "geo1M" and default_cfg:
+            l2_peak = l2_read_gbs(dev)
+            l2_gbs = QUERY_L2_BYTES_PER_QUERY * nq / (mean_query * 1e-3) / 1e9
+            l2_record = {"bytes_per_query": QUERY_L2_BYTES_PER_QUERY, "achieved": round(l2_gbs, 1),
+                         "peak": round(l2_peak, 1), "unit": "GB/s", "frac": round(l2_gbs / l2_peak, 4),
+                         "peak_source": "measured: float32 sum over a 48 MB L2-resident buffer",
+                         "bytes_source": "ncu lts__t_sectors of a 200K-query pass, per query"}
         q_bytes = (20 if stall else 12) * q_exp + 8 * q_edges + 20 * nq
         q_gbs = q_bytes / (mean_query * 1e-3) / 1e9
         roofline = {
@@ -788,6 +801,7 @@ def main():
                              "small_tables_first": bool(qcfg[2]) if qcfg else None,
                              "stall_on_demand": bool(qcfg[3]) if qcfg else None,
                              "autotune_ms": [round(float(x), 3) for x in tune_ms] if tune_ms is not None else None},
+            "l2": l2_record,
             "witness": {"achieved": round(wit_gbs, 1), "frac": round(wit_gbs / peak, 4),
                         "share_of_build": round(stats["witness_ms"] / mean_build, 3) if mean_build else None},
         }
