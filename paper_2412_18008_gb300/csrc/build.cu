@@ -101,7 +101,8 @@ struct Ctl {
     unsigned long long trace_valid;  // trace rows of eligible rescorings
     unsigned long long dm_count;     // keys in the memoised-distance map since its last clear
     unsigned long long pruned;       // overlay edges pruned this round
-    uint32_t nDirty, pad2;           // vertices whose lists hold pruned entries
+    uint32_t nDirty;                 // vertices whose lists hold pruned entries
+    uint32_t longRows;               // rank-ordered CSR rows left for the radix sort
     // shortcut log entries so far (device-side, so that k_insert needs no
     // host value), and the contraction counters of the last finished round,
     // copied by k_round_end for the host's next read
@@ -2386,6 +2387,30 @@ __global__ void k_ranked_deg(const uint32_t *perm, uint32_t n, const uint32_t *d
     if (blockIdx.x == 0 && threadIdx.x == 0) rdeg[n] = 0;
 }
 
+constexpr uint32_t RANKED_SORT_MAX = 64;  // longest row a thread insertion-sorts
+
+// Keys of every entry of a rank-ordered CSR for the radix sort of its rows:
+// row << 32 | target rank (one warp per row), the weight as the value.
+__global__ void k_row_keys(const uint32_t *off, uint32_t n, const uint2 *adj, uint64_t *keys, uint32_t *vals) {
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
+        const uint32_t b = off[i], e = off[i + 1];
+        for (uint32_t j = b + lane; j < e; j += 32) {
+            const uint2 a = adj[j];
+            keys[j] = ((uint64_t)i << 32) | a.x;
+            vals[j] = a.y;
+        }
+    }
+}
+
+// The sorted keys back into the CSR's (target rank, weight) entries.
+__global__ void k_row_unpack(const uint64_t *keys, const uint32_t *vals, uint64_t m, uint2 *adj) {
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < m;
+         j += (uint64_t)gridDim.x * blockDim.x)
+        adj[j] = make_uint2((uint32_t)keys[j], vals[j]);
+}
+
 __global__ void k_ranked_fill(const uint32_t *perm, const uint32_t *rank, uint32_t n,
                               const uint64_t *beg, const uint32_t *deg, const uint2 *src,
                               uint64_t src_count, const uint32_t *off, uint64_t dst_count,
@@ -2412,7 +2437,13 @@ __global__ void k_ranked_fill(const uint32_t *perm, const uint32_t *rank, uint32
             }
             out[j] = make_uint2(rank[e.x], e.y);
         }
-        // insertion sort by target rank: the list order becomes canonical
+        // rows are sorted by target rank, which makes the list order
+        // canonical: short rows here (insertion sort), longer ones by the
+        // radix sort of the whole CSR that a set flag asks for
+        if (dg > RANKED_SORT_MAX) {
+            ctl->longRows = 1;
+            continue;
+        }
         for (uint32_t j = 1; j < dg; ++j) {
             const uint2 t = out[j];
             uint32_t k = j;
@@ -3016,6 +3047,32 @@ void Builder::postprocess() {
         CH_CHECK_LAUNCH();
     }
     sync_ctl();
+    if (hctl->longRows) {
+        // some row is longer than a thread sorts: sort every row of both
+        // CSRs at once by (row, target rank)
+        std::vector<int> rd;
+        append_digits(rd, 0, bits_for(n));
+        append_digits(rd, 32, bits_for(n));
+        for (int dir = 0; dir < 2; ++dir) {
+            DevBuf<uint32_t> &off = dir == 0 ? h->up_off : h->dn_off;
+            DevBuf<uint2> &adj = dir == 0 ? h->up_adj : h->dn_adj;
+            const uint64_t m = dir == 0 ? n_up : n_dn;
+            if (m < 2) continue;
+            DevBuf<uint64_t> k1, k2;
+            DevBuf<uint32_t> v1, v2;
+            k1.alloc(m);
+            k2.alloc(m);
+            v1.alloc(m);
+            v2.alloc(m);
+            k_row_keys<<<grid_for((uint64_t)n * 32, 256, sms * 8), 256, 0, st>>>(off.ptr, n, adj.ptr, k1.ptr,
+                                                                                 v1.ptr);
+            CH_CHECK_LAUNCH();
+            radix_sort_pairs(k1.ptr, v1.ptr, k2.ptr, v2.ptr, m, rd, st);
+            k_row_unpack<<<grid_for(m, 256, sms * 8), 256, 0, st>>>(k1.ptr, v1.ptr, m, adj.ptr);
+            CH_CHECK_LAUNCH();
+            CH_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+    }
 }
 
 }  // namespace
