@@ -435,6 +435,54 @@ def modes_record(args, g, off, tgt, wt, s_d, t_d, stream, steps=2, warmup=1):
     return out
 
 
+def rmat_record(args, steps=2, warmup=1, nq=50):
+    """Config 5's stress graph (RMAT, 2^21 vertices, 2^25 edge samples) with
+    a finite candidate bound and the core it leaves: build seconds (CUDA
+    events), rounds, core, shortcuts, witness time, and queries/s of a small
+    batch, whose searches cover the core; a few answers against Dijkstra."""
+    import torch
+    import oracle as O
+    from paper_2412_18008_gb300 import ch
+    dev = torch.device("cuda", 0)
+    g = make_graph("rmat2M")
+    kw = dict(hop_limit=2, max_candidates_per_vertex=256, witness_ball_limit=256,
+              witness_level_work=1024, witness_memo_limit=1 << 30)
+    off = torch.from_numpy(g.offsets.view(np.int64)).to(dev)
+    tgt = torch.from_numpy(g.targets.view(np.int32)).to(dev)
+    wt = torch.from_numpy(g.weights.view(np.int32)).to(dev)
+    times = []
+    for k in range(warmup + steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h = ch.CH.build(n=g.n, offsets=off, targets=tgt, weights=wt, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= warmup:
+            times.append(e0.elapsed_time(e1))
+        if k + 1 < warmup + steps:
+            h.close()
+    st = h.stats()
+    s_h, t_h = I.random_pairs(g.n, nq, seed=9)
+    ds = torch.from_numpy(s_h.view(np.int32)).to(dev)
+    dt = torch.from_numpy(t_h.view(np.int32)).to(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    d = h.query(ds, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    got = d.cpu().numpy().view(np.uint32)
+    h.close()
+    return {"workload": "rmat2M", "vertices": g.n, "edge_samples": int(g.m),
+            "params": {"hop_limit": 2, "cmax": 256, "witness_ball": 256, "witness_level_work": 1024,
+                       "witness_memo": 1 << 30},
+            "build_s": statistics.mean(times) / 1e3, "rounds": st["rounds"],
+            "core_vertices": st["core_vertices"], "shortcuts": st["shortcuts"],
+            "witness_ms": st["witness_ms"], "queries": nq,
+            "queries_per_s": nq / (e0.elapsed_time(e1) * 1e-3),
+            "answers_equal_dijkstra_5": bool(np.array_equal(got[:5], O.dijkstra_pairs(g, s_h[:5], t_h[:5])))}
+
+
 def compare_learned(args, steps=None, warmup=None):
     """Learned priority vs edge difference (one JSON line). geo1M: trained on
     traces of 20 seeded 256K-vertex graphs of the family, compared on a
@@ -845,6 +893,7 @@ def main():
         configs = {}
         for name, fn in (("modes_geo1M", lambda: modes_record(args, g, off_d, tgt_d, w_d, s_d, t_d, stream)),
                          ("learned_geo1M", lambda: compare_learned(args, steps=3, warmup=1)),
+                         ("rmat2M", lambda: rmat_record(args)),
                          ("serve_geo16M", lambda: serve_bench(args, "geo16M", 20_000))):
             t0 = time.perf_counter()
             try:
