@@ -239,7 +239,7 @@ struct WArgs {
     uint8_t *rec_flag;       // PRUNE: 1 = lowers an existing edge
     uint64_t rec_cap;
     // Routing to the block tier without a warp attempt: every source when
-    // the phase has at most route_all sources (8 times the block tier's
+    // the phase has at most route_all sources (16 times the block tier's
     // grid: with that few sources per-source latency decides, and a block
     // finishes a source sooner than a warp), and any source whose middles'
     // out-degrees sum above route_deg (its ball would overflow).
@@ -2706,7 +2706,7 @@ void Builder::witness(const uint32_t *Sl, const uint32_t *nS_dev, uint32_t nS_ma
     a.rec = rec.ptr;
     a.rec_flag = rec_flag.ptr;
     a.rec_cap = rec.count;
-    a.route_all = (uint32_t)blk_blocks * 8;
+    a.route_all = (uint32_t)blk_blocks * 16;
     a.route_deg = route_deg;
     a.dm = dm;
     a.level_work = level_work;
