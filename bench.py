@@ -67,9 +67,11 @@ L2_BYTES = 129 * 1024 * 1024
 # query batch (first pass + overflow redo), from an ncu capture of the
 # current kernel on this workload (set to None when the kernel changes).
 QUERY_TRAFFIC_PER_LAUNCH = None
-# L2 bytes per query of that kernel in that configuration (lts__t_sectors *
-# 32 over a 200K-query pass of the same workload; L2 traffic is per-query
-# work, so it scales with the queries of a batch).
+# L2 bytes per query of that kernel in the configuration named (layout,
+# threads, small_first, stall, delta) (lts__t_sectors * 32 over a
+# 200K-query pass of the same workload; L2 traffic is per-query work, so it
+# scales with the queries of a batch).
+QUERY_L2_CONFIG = (1, 256, 1, 1, 0)
 QUERY_L2_BYTES_PER_QUERY = 397_587
 
 
@@ -389,7 +391,6 @@ def modes_record(args, g, off, tgt, wt, s_d, t_d, stream, steps=2, warmup=1):
             if k + 1 < warmup + steps:
                 h.close()
         st = h.stats()
-        h.set_query_config(1, 256, 1, 1)
         d, sett = h.query(ds, dt, want_settled=True, stream=stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -822,9 +823,8 @@ def main():
     else:
         # with stalling each expansion also reads the other CSR's two offsets
         stall = bool(qcfg[3]) if qcfg else False
-        default_cfg = qcfg is None or tuple(qcfg) == (1, 256, 1, 1)
         l2_record = None
-        if args.workload == "geo1M" and default_cfg:
+        if args.workload == "geo1M" and qcfg is not None and tuple(qcfg) == QUERY_L2_CONFIG:
             l2_peak = l2_read_gbs(dev)
             l2_gbs = QUERY_L2_BYTES_PER_QUERY * nq / (mean_query * 1e-3) / 1e9
             l2_record = {"bytes_per_query": QUERY_L2_BYTES_PER_QUERY, "achieved": round(l2_gbs, 1),
@@ -840,7 +840,7 @@ def main():
             # the captured traffic belongs to this workload in the default
             # configuration (warp layout, 256 threads, small tables, stalling)
             "traffic": (QUERY_TRAFFIC_PER_LAUNCH if args.workload == "geo1M" and nq == 1_000_000
-                        and (qcfg is None or tuple(qcfg) == (1, 256, 1, 1)) else None),
+                        and qcfg is not None and tuple(qcfg) == QUERY_L2_CONFIG else None),
             "peak_source": peak_src, "bytes_per_launch": q_bytes, "ms_per_launch": mean_query,
             "launch": "one batch = the small-table pass + its overflow redo (two launches)",
             "expansions_per_query": q_exp / nq, "edges_per_query": q_edges / nq,
@@ -848,6 +848,7 @@ def main():
                              "threads": qcfg[1] if qcfg else None,
                              "small_tables_first": bool(qcfg[2]) if qcfg else None,
                              "stall_on_demand": bool(qcfg[3]) if qcfg else None,
+                             "delta": qcfg[4] if qcfg else None,
                              "autotune_ms": [round(float(x), 3) for x in tune_ms] if tune_ms is not None else None},
             "l2": l2_record,
             "witness": {"achieved": round(wit_gbs, 1), "frac": round(wit_gbs / peak, 4),

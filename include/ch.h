@@ -318,8 +318,15 @@ int ch_load(const char *path, ch_t **out);
  * arrays. stall = 1 (warp layout only) skips expanding a vertex whose label
  * a reached higher neighbour already beats through one edge ("stall on
  * demand"; it applies to pruned searches, not to those that report search-
- * space sizes). Every configuration gives the same answers and search-space
- * sizes. */
+ * space sizes). delta > 0 (with stall = 1 only, so for pruned searches)
+ * orders each search's levels like delta-stepping: a level expands only the
+ * queued vertices whose label is at most the least queued label of their
+ * direction plus delta, and keeps the others queued, so fewer vertices are
+ * expanded again after a later improvement; delta = 0 expands every queued
+ * vertex. A built or loaded hierarchy starts with the warp layout, 256
+ * threads, small_first 1, stall 1 and delta = 128 x its weight scale (the
+ * median weight of 1024 evenly spaced E_up edges). Every configuration
+ * gives the same answers and search-space sizes. */
 #define CH_QUERY_BLOCK_FLAT 0u
 #define CH_QUERY_WARP_FLAT 1u
 typedef struct {
@@ -327,6 +334,7 @@ typedef struct {
     uint32_t threads;
     uint32_t small_first;
     uint32_t stall;
+    uint32_t delta;
 } ch_query_config_t;
 
 int ch_set_query_config(ch_t *ch, const ch_query_config_t *cfg);  /* CH_EINVAL on other values */
@@ -334,11 +342,14 @@ int ch_get_query_config(const ch_t *ch, ch_query_config_t *cfg);
 
 /* Times each configuration on `sample` seeded uniform random queries (a
  * warm-up run, then one run timed with CUDA events on `stream`) and keeps
- * the fastest for the handle. ms_out (or NULL) receives the 12 times: index
- * 4 * small_first + 2 * (layout == WARP_FLAT) + (threads == 256) without
- * stalling, then 8 + 2 * small_first + (threads == 256) for the warp layout
- * with stalling; chosen (or NULL) the configuration kept. Waits for
- * `stream`. */
+ * the fastest for the handle. ms_out (or NULL) receives the
+ * CH_QUERY_AUTOTUNE_CONFIGS times: index 4 * small_first +
+ * 2 * (layout == WARP_FLAT) + (threads == 256) without stalling or delta;
+ * then 8 + 2 * small_first + (threads == 256) for the warp layout with
+ * stalling and no delta; then 12, 13, 14 for the warp layout, 256 threads,
+ * small_first 1, stalling, and delta = 64, 128, 256 x the weight scale.
+ * chosen (or NULL) receives the configuration kept. Waits for `stream`. */
+#define CH_QUERY_AUTOTUNE_CONFIGS 15
 int ch_query_autotune(ch_t *ch, uint64_t sample, uint32_t seed, void *stream,
                       ch_query_config_t *chosen, double *ms_out);
 

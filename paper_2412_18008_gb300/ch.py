@@ -67,15 +67,18 @@ class TuneRowT(C.Structure):
 
 class QueryConfigT(C.Structure):
     _fields_ = [("layout", C.c_uint32), ("threads", C.c_uint32), ("small_first", C.c_uint32),
-                ("stall", C.c_uint32)]
+                ("stall", C.c_uint32), ("delta", C.c_uint32)]
 
 
 CH_QUERY_BLOCK_FLAT = 0
 CH_QUERY_WARP_FLAT = 1
 # (layout, threads, small_first, stall) in the autotuner's order
-QUERY_CONFIGS = (tuple((lay, thr, sf, 0) for sf in (0, 1) for lay in (CH_QUERY_BLOCK_FLAT, CH_QUERY_WARP_FLAT)
-                       for thr in (128, 256)) +
-                 tuple((CH_QUERY_WARP_FLAT, thr, sf, 1) for sf in (0, 1) for thr in (128, 256)))
+# The autotuner's candidates as (layout, threads, small_first, stall,
+# delta in weight scales), in its timing order; delta = 0 is off.
+QUERY_CONFIGS = (tuple((lay, thr, sf, 0, 0) for sf in (0, 1)
+                       for lay in (CH_QUERY_BLOCK_FLAT, CH_QUERY_WARP_FLAT) for thr in (128, 256)) +
+                 tuple((CH_QUERY_WARP_FLAT, thr, sf, 1, 0) for sf in (0, 1) for thr in (128, 256)) +
+                 tuple((CH_QUERY_WARP_FLAT, 256, 1, 1, mult) for mult in (64, 128, 256)))
 
 
 class ServerParamsT(C.Structure):
@@ -449,24 +452,26 @@ class CH:
         return cls(h)
 
     # -- query configuration, autotuning, work, graphs ----------------------
-    def set_query_config(self, layout: int, threads: int, small_first: int = 0, stall: int = 0):
+    def set_query_config(self, layout: int, threads: int, small_first: int = 0, stall: int = 0,
+                         delta: int = 0):
         _check(load().ch_set_query_config(self._h, C.byref(QueryConfigT(layout, threads, small_first,
-                                                                        stall))))
+                                                                        stall, delta))))
 
-    def query_config(self) -> tuple[int, int, int, int]:
+    def query_config(self) -> tuple[int, int, int, int, int]:
+        """(layout, threads, small_first, stall, delta); delta in weight units."""
         c = QueryConfigT()
         _check(load().ch_get_query_config(self._h, C.byref(c)))
-        return c.layout, c.threads, c.small_first, c.stall
+        return c.layout, c.threads, c.small_first, c.stall, c.delta
 
     def autotune_queries(self, sample: int = 1 << 16, seed: int = 1, stream=None):
         """Time every query configuration on ``sample`` random queries and keep
-        the fastest. Returns (chosen (layout, threads, small_first, stall), ms
-        per configuration in QUERY_CONFIGS order)."""
+        the fastest. Returns (chosen (layout, threads, small_first, stall,
+        delta), ms per configuration in QUERY_CONFIGS order)."""
         c = QueryConfigT()
-        ms = np.zeros(12, np.float64)
+        ms = np.zeros(len(QUERY_CONFIGS), np.float64)
         _check(load().ch_query_autotune(self._h, sample, seed, _stream_ptr(stream), C.byref(c),
                                         _hp(ms)))
-        return (c.layout, c.threads, c.small_first, c.stall), ms
+        return (c.layout, c.threads, c.small_first, c.stall, c.delta), ms
 
     def query_work(self, stream=None) -> tuple[int, int]:
         """(expansions, edges scanned) of the query searches since the last call."""

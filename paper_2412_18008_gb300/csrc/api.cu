@@ -309,7 +309,7 @@ int ch_set_query_config(ch_t *ch, const ch_query_config_t *cfg) {
         g_last_error = "null argument";
         return CH_EINVAL;
     }
-    return guarded([&] { query_set_config(ch, cfg->layout, cfg->threads, cfg->small_first, cfg->stall); });
+    return guarded([&] { query_set_config(ch, cfg->layout, cfg->threads, cfg->small_first, cfg->stall, cfg->delta); });
 }
 
 int ch_get_query_config(const ch_t *ch, ch_query_config_t *cfg) {
@@ -321,6 +321,7 @@ int ch_get_query_config(const ch_t *ch, ch_query_config_t *cfg) {
     cfg->threads = ch->q_threads;
     cfg->small_first = ch->q_small_first;
     cfg->stall = ch->q_stall;
+    cfg->delta = ch->q_delta;
     return CH_OK;
 }
 

@@ -66,6 +66,8 @@ struct ch_s {
     uint32_t q_threads = 256;
     uint32_t q_small_first = 1;  // first pass on 2^11-slot tables
     uint32_t q_stall = 1;        // stall on demand (warp layout, pruned searches)
+    uint32_t q_delta = 0;        // delta-stepping bucket width (warp layout; 0: off)
+    uint32_t q_wscale = 1;       // weight scale: median of sampled E_up weights
     uint32_t q_slots = 0;
     uint64_t q_ovf_cap = 0;
     gbch::DevBuf<uint32_t> q_src_fill;  // repeated source of one-to-many queries
@@ -100,7 +102,8 @@ void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint6
                         uint32_t *dist_out, cudaStream_t st);
 
 // Query configuration, autotuning, work counters, graphs (query.cu).
-void query_set_config(ch_s *h, uint32_t layout, uint32_t threads, uint32_t small_first, uint32_t stall);
+void query_set_config(ch_s *h, uint32_t layout, uint32_t threads, uint32_t small_first, uint32_t stall,
+                      uint32_t delta);
 void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch_query_config_t *chosen,
                     double *ms_out);
 void query_work(ch_s *h, cudaStream_t st, uint64_t out[2]);

@@ -20,7 +20,8 @@ constexpr int QB_THREADS = 256;  // threads per query block, at most
 // bitmaps that keep a slot from being queued twice in one level and
 // direction (one bitmap per level parity, the idle one cleared during the
 // level), a double-buffered frontier holding both directions' entries
-// (slot | dir<<31) and a triple-buffered frontier counter (see block_search).
+// (slot | dir<<31), and a triple-buffered frontier counter and pair of
+// least queued labels (see block_search).
 template <int TB>
 struct QBSmem {
     static constexpr uint32_t T = 1u << TB;   // table slots
@@ -41,6 +42,7 @@ struct QBSmem {
     uint32_t t_ent[QB_THREADS];
     uint32_t wtot[QB_THREADS / 32 + 1];
     uint32_t cnt3[3];
+    uint32_t lmin3[3][2];  // least label queued per level (mod 3) and direction
     uint32_t item, ovf, mu, cnt, ss, st;
 };
 
@@ -69,6 +71,10 @@ struct QArgs {
     // core_n distances) instead.
     const uint32_t *core_tab = nullptr;
     uint32_t core_lo = 0, core_n = 0;
+    // Bucket width of delta-stepping levels (the DELTA kernels): a level
+    // expands only the entries whose label is at most the least queued
+    // label of their direction plus delta and keeps the rest queued.
+    uint32_t delta = INF;
 };
 
 template <int TB>
@@ -124,9 +130,13 @@ struct QStat {
 
 // Relaxes one edge e = (y, w) of a vertex labelled dx in direction dir.
 // Returns nothing; records an overflow in q.ovf, an index error in a.err.
-template <bool PRUNE, int TB>
+// With TRACK, lmf / lmb keep the least new forward / backward label this
+// thread has set in the level (every vertex whose label drops is queued for
+// the next level).
+template <bool PRUNE, int TB, bool TRACK = false>
 __device__ __forceinline__ void qb_relax(QBSmem<TB> &q, const QArgs &a, uint32_t dir, uint2 e, uint32_t dx,
-                                         uint32_t lvl, uint32_t nxt_cnt, uint32_t *next_front) {
+                                         uint32_t lvl, uint32_t nxt_cnt, uint32_t *next_front, uint32_t &lmf,
+                                         uint32_t &lmb) {
     const uint32_t nd = sat_add(dx, e.y);
     if (e.x >= a.n) {
         atomicOr(a.err, QERR_BOUND);
@@ -142,6 +152,10 @@ __device__ __forceinline__ void qb_relax(QBSmem<TB> &q, const QArgs &a, uint32_t
     uint32_t *dist = dir ? q.db : q.df;
     const uint32_t old = atomicMin(&dist[ys], nd);
     if (nd >= old) return;
+    if (TRACK) {
+        if (dir) lmb = min(lmb, nd);
+        else lmf = min(lmf, nd);
+    }
     if (PRUNE) {
         const uint32_t other = dir ? q.df[ys] : q.db[ys];
         if (other != INF) atomicMin(&q.mu, sat_add(nd, other));
@@ -193,14 +207,25 @@ __device__ __forceinline__ void qb_entry(const QBSmem<TB> &q, const QArgs &a, bo
 //    over its lanes (warp scan, owner found by shuffles); no barrier inside
 //    a level.
 //
-// Barrier discipline: the frontier counter of level k lives in cnt3[k % 3];
-// thread 0 clears the counter of level k + 2 during level k, when no thread
-// reads it any more. Each level reads its frontier size and the overflow
+// DELTA (warp-flattened, pruned searches) orders the levels like
+// delta-stepping: a level expands only the entries within a.delta of their
+// direction's least queued label and keeps the others queued, so fewer
+// vertices are expanded again after a later improvement; an entry whose
+// label is not below the best meeting sum is dropped (every relaxation from
+// it would be skipped). The least queued label of each direction is
+// expanded every level and new labels exceed it, so the least label grows
+// every level and the search ends.
+//
+// Barrier discipline: the frontier counter of level k lives in cnt3[k % 3],
+// and (DELTA) the least labels queued for it in lmin3[k % 3]; thread 0
+// clears both for level k + 2 during level k, when no thread reads them any
+// more. Each level reads its frontier size and the overflow
 // flag right after a barrier that follows every write to them: the barrier
 // at the top of the level (warp-flattened; block-flattened at level 1) or
 // the barrier that ends the previous level's last tile (block-flattened).
-template <bool PRUNE, bool WARP, int TB, bool STALL>
+template <bool PRUNE, bool WARP, int TB, bool STALL, bool DELTA = false>
 __device__ bool block_search(QBSmem<TB> &q, const QArgs &a, QStat &stat) {
+    static_assert(!DELTA || (PRUNE && WARP), "delta-stepping levels: pruned warp-flattened searches");
     constexpr uint32_t FC = QBSmem<TB>::FC, CW = QBSmem<TB>::CW;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
@@ -215,18 +240,52 @@ __device__ bool block_search(QBSmem<TB> &q, const QArgs &a, QStat &stat) {
             if (tid == 0) atomicOr(a.err, QERR_BOUND);
             return false;
         }
-        if (tid == 0) q.cnt3[(lvl + 1) % 3] = 0;
+        uint32_t thr_f = INF, thr_b = INF;  // DELTA: this level's label thresholds
+        if (DELTA) {
+            thr_f = sat_add(q.lmin3[(lvl - 1) % 3][0], a.delta);
+            thr_b = sat_add(q.lmin3[(lvl - 1) % 3][1], a.delta);
+        }
+        if (tid == 0) {
+            q.cnt3[(lvl + 1) % 3] = 0;
+            if (DELTA) q.lmin3[(lvl + 1) % 3][0] = q.lmin3[(lvl + 1) % 3][1] = INF;
+        }
         // the bitmap of the other parity was last used two levels ago and is
         // next used one level from now
         for (uint32_t j = tid; j < 2u * CW; j += blockDim.x) (&q.claim[(lvl + 1) & 1u][0][0])[j] = 0;
         const uint32_t nxt_cnt = lvl % 3;
         uint32_t *next_front = q.front[cur ^ 1u];
+        uint32_t lmf = INF, lmb = INF;  // DELTA: least labels this thread queues
         if (WARP) {
             const uint32_t stride = blockDim.x;
             for (uint32_t p0 = 0; p0 < nfront; p0 += stride) {
                 const uint32_t fi = p0 + warp + nwarps * lane;
-                const bool fv = fi < nfront && fi < FC;
+                bool fv = fi < nfront && fi < FC;
                 const uint32_t ent = fv ? q.front[cur][fi] : 0;
+                if (DELTA) {
+                    // keep an entry above its direction's threshold queued
+                    // (warp-aggregated push); drop one that cannot improve
+                    // the meeting sum
+                    const uint32_t edir = ent >> 31, eslot = ent & 0x7FFFFFFFu;
+                    const bool sok = fv && eslot < QBSmem<TB>::T;
+                    const uint32_t lab = sok ? (edir ? q.db[eslot] : q.df[eslot]) : INF;
+                    const bool drop = sok && lab >= q.mu;
+                    const bool keep = sok && !drop && lab > (edir ? thr_b : thr_f);
+                    const bool won = keep && qb_claim(q, eslot, edir, lvl);
+                    const uint32_t m = __ballot_sync(FULL, won);
+                    if (m) {
+                        const uint32_t leader = __ffs(m) - 1;
+                        uint32_t p = 0;
+                        if (lane == leader) p = atomicAdd(&q.cnt3[nxt_cnt], (uint32_t)__popc(m));
+                        p = __shfl_sync(FULL, p, leader) + __popc(m & ((1u << lane) - 1u));
+                        if (won) {
+                            if (p < FC) next_front[p] = ent;
+                            else q.ovf = 1;
+                            if (edir) lmb = min(lmb, lab);
+                            else lmf = min(lmf, lab);
+                        }
+                    }
+                    if (keep || drop) fv = false;
+                }
                 uint32_t b, cnt, dx;
                 qb_entry(q, a, fv, ent, b, cnt, dx);
                 stat.exp += cnt ? 1u : 0u;
@@ -286,8 +345,21 @@ __device__ bool block_search(QBSmem<TB> &q, const QArgs &a, QStat &stat) {
                     if (e0 < total) {
                         ++stat.edges;
                         const uint2 e = (odir ? a.dn_adj : a.up_adj)[ob + (e0 - oex)];
-                        qb_relax<PRUNE, TB>(q, a, odir, e, odx, lvl, nxt_cnt, next_front);
+                        qb_relax<PRUNE, TB, DELTA>(q, a, odir, e, odx, lvl, nxt_cnt, next_front, lmf, lmb);
                     }
+                }
+            }
+            if (DELTA) {
+                // the least labels queued for the next level, one atomic per
+                // warp and direction
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    lmf = min(lmf, __shfl_xor_sync(FULL, lmf, o));
+                    lmb = min(lmb, __shfl_xor_sync(FULL, lmb, o));
+                }
+                if (lane == 0) {
+                    if (lmf != INF) atomicMin(&q.lmin3[nxt_cnt][0], lmf);
+                    if (lmb != INF) atomicMin(&q.lmin3[nxt_cnt][1], lmb);
                 }
             }
         } else {
@@ -324,7 +396,7 @@ __device__ bool block_search(QBSmem<TB> &q, const QArgs &a, QStat &stat) {
                     ++stat.edges;
                     const uint32_t odir = q.t_ent[lo] >> 31;
                     const uint2 e = (odir ? a.dn_adj : a.up_adj)[q.t_beg[lo] + (e0 - q.t_excl[lo])];
-                    qb_relax<PRUNE, TB>(q, a, odir, e, q.t_dx[lo], lvl, nxt_cnt, next_front);
+                    qb_relax<PRUNE, TB>(q, a, odir, e, q.t_dx[lo], lvl, nxt_cnt, next_front, lmf, lmb);
                 }
                 __syncthreads();
             }
@@ -351,7 +423,7 @@ __device__ __forceinline__ void qb_clear(QBSmem<TB> &q) {
 // overflowed the table or the frontier (the caller redoes the query
 // elsewhere); otherwise mu and cnt hold, in every thread, the least meeting
 // sum and the number of labels set. Every thread of the block must call it.
-template <bool PRUNE, bool WARP, int TB, bool STALL = false>
+template <bool PRUNE, bool WARP, int TB, bool STALL = false, bool DELTA = false>
 __device__ bool block_query(QBSmem<TB> &q, const QArgs &a, uint32_t rs, uint32_t rt, uint32_t &mu_out,
                             uint32_t &cnt_out, QStat &stat) {
     const uint32_t tid = threadIdx.x;
@@ -369,8 +441,12 @@ __device__ bool block_query(QBSmem<TB> &q, const QArgs &a, uint32_t rs, uint32_t
         q.cnt3[0] = 2;
         q.cnt3[1] = 0;
         q.cnt3[2] = 0;
+        if (DELTA) {
+            q.lmin3[0][0] = q.lmin3[0][1] = 0;  // the two roots
+            q.lmin3[1][0] = q.lmin3[1][1] = INF;
+        }
     }
-    bool ok = block_search<PRUNE, WARP, TB, STALL>(q, a, stat);
+    bool ok = block_search<PRUNE, WARP, TB, STALL, DELTA>(q, a, stat);
     // q.mu only steered pruning; the answer is the least meeting sum.
     __syncthreads();
     if (tid == 0) {

@@ -27,8 +27,10 @@ namespace {
 
 constexpr uint64_t Q_CHUNK = 1u << 22;  // queries per launch pair
 
-template <bool PRUNE, bool WARP, int TB, bool STALL>
-__global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
+// (The delta-stepping variant is held to the others' register budget, so
+// that six 2^11-slot blocks stay resident per SM.)
+template <bool PRUNE, bool WARP, int TB, bool STALL, bool DELTA = false>
+__global__ void __launch_bounds__(QB_THREADS, DELTA ? 6 : 1) k_query_block(QArgs a) {
     extern __shared__ __align__(16) unsigned char qb_raw[];
     QBSmem<TB> &q = *reinterpret_cast<QBSmem<TB> *>(qb_raw);
     const uint32_t tid = threadIdx.x;
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_block(QArgs a) {
             continue;
         }
         uint32_t mu, cnt;
-        if (!block_query<PRUNE, WARP, TB, STALL>(q, a, rs, rt, mu, cnt, stat)) {
+        if (!block_query<PRUNE, WARP, TB, STALL, DELTA>(q, a, rs, rt, mu, cnt, stat)) {
             if (tid == 0) a.ovf[atomicAdd(&a.work[a.ovf_cnt], 1u)] = i;
             continue;
         }
@@ -195,23 +197,25 @@ __global__ void __launch_bounds__(256) k_query_dense(QArgs a, QDense dn) {
 }
 
 // Resident blocks per SM of each block-kernel configuration
-// [table bits == 11][block-flat, warp-flat, warp-flat with stalling]
-// [threads == 256], resolved once.
-int g_qb_bps[2][3][2] = {{{-1, -1}, {-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}, {-1, -1}}};
+// [table bits == 11][block-flat, warp-flat, warp-flat with stalling,
+// the same with delta-stepping levels][threads == 256], resolved once.
+int g_qb_bps[2][4][2] = {{{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}}};
 
 template <int TB>
 void qb_resolve(int s) {
     const int smem = (int)sizeof(QBSmem<TB>);
+    CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true, true, TB, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true, false, TB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<false, false, TB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true, true, TB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<false, true, TB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CH_CUDA_TRY(cudaFuncSetAttribute(k_query_block<true, true, TB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    for (int l = 0; l < 3; ++l)
+    for (int l = 0; l < 4; ++l)
         for (int t = 0; t < 2; ++t) {
             int b = 0;
             const int threads = t ? 256 : 128;
-            if (l == 2) CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, true, TB, true>, threads, smem));
+            if (l == 3) CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, true, TB, true, true>, threads, smem));
+            else if (l == 2) CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, true, TB, true>, threads, smem));
             else if (l == 1) CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, true, TB, false>, threads, smem));
             else CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_query_block<true, false, TB, false>, threads, smem));
             g_qb_bps[s][l][t] = std::max(1, b);
@@ -225,10 +229,12 @@ void qb_resolve_occupancy() {
 }
 
 template <int TB>
-void launch_tb(const QArgs &a, bool prune, bool warp, bool stall, int blocks, int threads, cudaStream_t st) {
+void launch_tb(const QArgs &a, bool prune, bool warp, bool stall, bool delta, int blocks, int threads,
+               cudaStream_t st) {
     const size_t smem = sizeof(QBSmem<TB>);
     if (warp) {
-        if (prune && stall) k_query_block<true, true, TB, true><<<blocks, threads, smem, st>>>(a);
+        if (prune && stall && delta) k_query_block<true, true, TB, true, true><<<blocks, threads, smem, st>>>(a);
+        else if (prune && stall) k_query_block<true, true, TB, true><<<blocks, threads, smem, st>>>(a);
         else if (prune) k_query_block<true, true, TB, false><<<blocks, threads, smem, st>>>(a);
         else k_query_block<false, true, TB, false><<<blocks, threads, smem, st>>>(a);
     } else {
@@ -241,18 +247,36 @@ void launch_tb(const QArgs &a, bool prune, bool warp, bool stall, int blocks, in
 // Launches one block-kernel pass in the handle's layout and block size: a
 // persistent grid of as many blocks as are resident at once (no more than
 // the items), with 2^11-slot tables when small is set, else 2^12. Stall on
-// demand applies to pruned searches in the warp layout only.
+// demand applies to pruned searches in the warp layout only, and
+// delta-stepping levels to those with stalling.
 void launch_query_block(const ch_s *h, const QArgs &a, bool prune, bool small, uint64_t items,
                         cudaStream_t st) {
     const bool warp = h->q_layout == CH_QUERY_WARP_FLAT;
     const bool stall = warp && prune && h->q_stall;
-    const int l = stall ? 2 : (warp ? 1 : 0);
+    const bool delta = stall && h->q_delta != 0;
+    const int l = delta ? 3 : (stall ? 2 : (warp ? 1 : 0));
     const int t = h->q_threads == 256 ? 1 : 0;
     const int threads = t ? 256 : 128;
     const int blocks = (int)std::max<uint64_t>(
         1, std::min<uint64_t>(items, (uint64_t)device_sm_count() * g_qb_bps[small ? 1 : 0][l][t]));
-    if (small) launch_tb<11>(a, prune, warp, stall, blocks, threads, st);
-    else launch_tb<12>(a, prune, warp, stall, blocks, threads, st);
+    if (small) launch_tb<11>(a, prune, warp, stall, delta, blocks, threads, st);
+    else launch_tb<12>(a, prune, warp, stall, delta, blocks, threads, st);
+}
+
+// Weights of `cnt` evenly spaced entries of an adjacency array.
+__global__ void k_sample_weights(const uint2 *adj, uint64_t m, uint32_t *out, uint32_t cnt) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) out[i] = adj[(uint64_t)i * m / cnt].y;
+}
+
+constexpr uint32_t WSCALE_SAMPLE = 1024;
+constexpr uint32_t DELTA_DEFAULT_MULT = 128;         // default delta, in weight scales
+constexpr uint32_t DELTA_TUNE_MULT[3] = {64, 128, 256};  // autotuner candidates 12-14
+
+// mult x the weight scale, at least 1 and below INF.
+uint32_t delta_of(const ch_s *h, uint32_t mult) {
+    const uint64_t d = (uint64_t)mult * h->q_wscale;
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(d, INF - 1));
 }
 
 }  // namespace
@@ -276,6 +300,20 @@ void query_init(ch_s *h) {
     h->q_stats.alloc(2);
     h->q_stats.zero(0);
     qb_resolve_occupancy();
+    // weight scale of the hierarchy (the median of sampled E_up weights) and
+    // the default delta
+    h->q_wscale = 1;
+    if (h->n_up > 0) {
+        DevBuf<uint32_t> wb;
+        wb.alloc(WSCALE_SAMPLE);
+        k_sample_weights<<<(WSCALE_SAMPLE + 255) / 256, 256>>>(h->up_adj.ptr, h->n_up, wb.ptr, WSCALE_SAMPLE);
+        CH_CHECK_LAUNCH();
+        std::vector<uint32_t> w(WSCALE_SAMPLE);
+        CH_CUDA_TRY(cudaMemcpy(w.data(), wb.ptr, WSCALE_SAMPLE * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        std::nth_element(w.begin(), w.begin() + WSCALE_SAMPLE / 2, w.end());
+        h->q_wscale = std::max<uint32_t>(1, w[WSCALE_SAMPLE / 2]);
+    }
+    h->q_delta = delta_of(h, DELTA_DEFAULT_MULT);
     CH_CUDA_TRY(cudaDeviceSynchronize());
 }
 
@@ -315,6 +353,7 @@ void query_batch(ch_s *h, const uint32_t *src, const uint32_t *dst, uint64_t k,
         a.core_tab = h->core_n ? h->core_tab.ptr : nullptr;
         a.core_lo = h->core_lo;
         a.core_n = h->core_n;
+        a.delta = h->q_delta ? h->q_delta : INF;
         CH_CUDA_TRY(cudaMemsetAsync(h->qwork.ptr, 0, 8 * sizeof(uint32_t), st));
         // Pruned searches unless the caller asked for search-space sizes,
         // which are defined by the exhaustive upward searches.
@@ -359,15 +398,19 @@ __global__ void k_sample_pairs(uint32_t *s, uint32_t *t, uint64_t k, uint32_t n,
 
 }  // namespace
 
-void query_set_config(ch_s *h, uint32_t layout, uint32_t threads, uint32_t small_first, uint32_t stall) {
+void query_set_config(ch_s *h, uint32_t layout, uint32_t threads, uint32_t small_first, uint32_t stall,
+                      uint32_t delta) {
     if ((layout != CH_QUERY_BLOCK_FLAT && layout != CH_QUERY_WARP_FLAT) || (threads != 128 && threads != 256) ||
-        small_first > 1 || stall > 1 || (stall && layout != CH_QUERY_WARP_FLAT))
+        small_first > 1 || stall > 1 || (stall && layout != CH_QUERY_WARP_FLAT) || (delta && !stall) ||
+        delta == INF)
         throw Error{CH_EINVAL, "query configuration: layout BLOCK_FLAT or WARP_FLAT, threads 128 or 256, "
-                               "small_first 0 or 1, stall 0 or 1 (WARP_FLAT only)"};
+                               "small_first 0 or 1, stall 0 or 1 (WARP_FLAT only), delta below 2^32 - 1 "
+                               "(with stall 1 only when not 0)"};
     h->q_layout = layout;
     h->q_threads = threads;
     h->q_small_first = small_first;
     h->q_stall = stall;
+    h->q_delta = delta;
 }
 
 void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch_query_config_t *chosen,
@@ -379,23 +422,27 @@ void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch
     k_sample_pairs<<<grid_for(sample, 256, device_sm_count() * 4), 256, 0, st>>>(s, t, sample, h->n, seed);
     CH_CHECK_LAUNCH();
     const uint32_t keep_l = h->q_layout, keep_t = h->q_threads, keep_s = h->q_small_first,
-                   keep_st = h->q_stall;
+                   keep_st = h->q_stall, keep_d = h->q_delta;
     cudaEvent_t e0, e1;
     CH_CUDA_TRY(cudaEventCreate(&e0));
     CH_CUDA_TRY(cudaEventCreate(&e1));
     // candidates 0-7: 4 * small_first + 2 * warp layout + (threads == 256);
-    // 8-11: warp layout with stalling, 8 + 2 * small_first + (threads == 256)
+    // 8-11: warp layout with stalling, 8 + 2 * small_first + (threads == 256);
+    // 12-14: warp layout, 256 threads, small tables first, stalling, delta
+    // at three multiples of the weight scale
     auto apply = [&](int i) {
         if (i < 8)
             query_set_config(h, (i & 2) ? CH_QUERY_WARP_FLAT : CH_QUERY_BLOCK_FLAT, (i & 1) ? 256 : 128,
-                             (i & 4) ? 1 : 0, 0);
+                             (i & 4) ? 1 : 0, 0, 0);
+        else if (i < 12)
+            query_set_config(h, CH_QUERY_WARP_FLAT, (i & 1) ? 256 : 128, (i & 2) ? 1 : 0, 1, 0);
         else
-            query_set_config(h, CH_QUERY_WARP_FLAT, (i & 1) ? 256 : 128, (i & 2) ? 1 : 0, 1);
+            query_set_config(h, CH_QUERY_WARP_FLAT, 256, 1, 1, delta_of(h, DELTA_TUNE_MULT[i - 12]));
     };
     double best = 0;
     int best_i = -1;
     try {
-        for (int i = 0; i < 12; ++i) {
+        for (int i = 0; i < CH_QUERY_AUTOTUNE_CONFIGS; ++i) {
             apply(i);
             query_batch(h, s, t, sample, out, nullptr, st);  // warm-up
             CH_CUDA_TRY(cudaEventRecord(e0, st));
@@ -415,6 +462,7 @@ void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch
         h->q_threads = keep_t;
         h->q_small_first = keep_s;
         h->q_stall = keep_st;
+        h->q_delta = keep_d;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         throw;
@@ -427,6 +475,7 @@ void query_autotune(ch_s *h, uint64_t sample, uint32_t seed, cudaStream_t st, ch
         chosen->threads = h->q_threads;
         chosen->small_first = h->q_small_first;
         chosen->stall = h->q_stall;
+        chosen->delta = h->q_delta;
     }
     // the sample's work is not the caller's: clear the counters
     CH_CUDA_TRY(cudaMemsetAsync(h->q_stats.ptr, 0, 2 * sizeof(unsigned long long), st));
@@ -622,6 +671,7 @@ void query_batch_static(ch_s *h, const uint32_t *src, const uint32_t *dst, uint6
     a.core_tab = h->core_n ? h->core_tab.ptr : nullptr;
     a.core_lo = h->core_lo;
     a.core_n = h->core_n;
+    a.delta = h->q_delta ? h->q_delta : INF;
     // the counters keep the previous call's values: clear them
     CH_CUDA_TRY(cudaMemsetAsync(scratch, 0, kStaticScratchHead * sizeof(uint32_t), st));
     // one block-kernel pass (large tables): the scratch holds one list

@@ -281,7 +281,7 @@ __device__ uint32_t sv_query(const SvArgs &a, const Tab &t, uint32_t rs, uint32_
     return res;
 }
 
-template <bool WARP, bool STALL>
+template <bool WARP, bool STALL, bool DELTA = false>
 __global__ void __launch_bounds__(QB_THREADS) k_serve(SvArgs a) {
     extern __shared__ __align__(16) unsigned char qb_raw[];
     QBSmem<12> &q = *reinterpret_cast<QBSmem<12> *>(qb_raw);
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_serve(SvArgs a) {
             const uint32_t rs = g.rank[s], rt = g.rank[tv];
             if (rs < g.n && rt < g.n) {
                 uint32_t cnt;
-                if (!block_query<true, WARP, 12, STALL>(q, g, rs, rt, ans, cnt, stat))
+                if (!block_query<true, WARP, 12, STALL, DELTA>(q, g, rs, rt, ans, cnt, stat))
                     ans = sv_query(a, t, rs, rt, q.cnt3, &q.ovf, &q.mu, &q.cnt);
             } else if (tid == 0) {
                 atomicOr(a.status, QERR_BOUND);
@@ -500,7 +500,9 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     // the handle's query configuration (layout and block size)
     const bool warp = h->q_layout == CH_QUERY_WARP_FLAT;
     const int threads = (int)h->q_threads;
-    auto kern = warp ? (h->q_stall ? k_serve<true, true> : k_serve<true, false>) : k_serve<false, false>;
+    auto kern = warp ? (h->q_stall ? (h->q_delta ? k_serve<true, true, true> : k_serve<true, true>)
+                                   : k_serve<true, false>)
+                     : k_serve<false, false>;
     CH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(QBSmem<12>)));
     int per_sm = 0;
     CH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sizeof(QBSmem<12>)));
@@ -548,6 +550,7 @@ void server_start(ch_server_s *sv, ch_s *h, const ch_server_params_t *p) {
     a.q.up_adj = h->up_adj.ptr;
     a.q.dn_adj = h->dn_adj.ptr;
     a.q.err = sv->status.ptr;
+    a.q.delta = h->q_delta ? h->q_delta : INF;
     a.ctl = sv->ctl.d;
     a.desc = sv->desc.d;
     a.item_req = sv->item_req.d;

@@ -139,7 +139,9 @@ def test_full_size_road_like_graph():
     assert (st >= 2 - same).all()
     # the pruned searches the benchmark times, in both table tiers and both
     # layouts, answer every pair of the batch as the exhaustive ones do
-    for cfg in ((1, 256, 0, 0), (1, 256, 1, 0), (0, 256, 1, 0), (1, 256, 1, 1)):
+    default = gch.query_config()
+    assert default[:4] == (1, 256, 1, 1) and default[4] > 0
+    for cfg in ((1, 256, 0, 0, 0), (1, 256, 1, 0, 0), (0, 256, 1, 0, 0), (1, 256, 1, 1, 0), default):
         gch.set_query_config(*cfg)
         dp = gch.query(ds, dt)
         torch.cuda.synchronize()

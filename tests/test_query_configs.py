@@ -26,8 +26,14 @@ def geo():
     return g, _ch().CH.build(g, hop_limit=5), O.build_ch(g, 5)
 
 
-@pytest.mark.parametrize("cfg", [(lay, thr, sf, 0) for sf in (0, 1) for lay in (0, 1) for thr in (128, 256)]
-                         + [(1, thr, sf, 1) for sf in (0, 1) for thr in (128, 256)])
+# every fixed configuration, then delta-stepping from a bucket width of one
+# weight unit (nearly one label value per level: the most deferral) to one
+# far above the labels (no deferral), in both table tiers and block sizes
+DELTA_CASES = [(1, 256, 1, 1, d) for d in (1, 3, 64, 1000, 1 << 30)] + [(1, 128, 0, 1, d) for d in (1, 50)]
+
+
+@pytest.mark.parametrize("cfg", [(lay, thr, sf, 0, 0) for sf in (0, 1) for lay in (0, 1) for thr in (128, 256)]
+                         + [(1, thr, sf, 1, 0) for sf in (0, 1) for thr in (128, 256)] + DELTA_CASES)
 def test_every_configuration_gives_the_oracle_answers(geo, cfg):
     g, gch, och = geo
     gch.set_query_config(*cfg)
@@ -48,7 +54,7 @@ def test_configurations_on_a_dense_random_digraph():
     och = O.build_ch(g, 4)
     s, t = I.random_pairs(g.n, 5000, seed=84)
     want = och.query(s, t)
-    for cfg in _ch().QUERY_CONFIGS:
+    for cfg in _ch().QUERY_CONFIGS + tuple(DELTA_CASES):
         gch.set_query_config(*cfg)
         assert np.array_equal(gch.query(s, t), want), cfg
 
@@ -57,8 +63,8 @@ def test_invalid_configuration_is_rejected(geo):
     ch = _ch()
     _, gch, _ = geo
     before = gch.query_config()
-    for cfg in ((2, 256, 0, 0), (0, 64, 0, 0), (1, 512, 0, 0), (1, 256, 2, 0), (0, 256, 0, 1),
-                (1, 256, 0, 2)):
+    for cfg in ((2, 256, 0, 0, 0), (0, 64, 0, 0, 0), (1, 512, 0, 0, 0), (1, 256, 2, 0, 0), (0, 256, 0, 1, 0),
+                (1, 256, 0, 2, 0), (0, 256, 0, 0, 5), (1, 256, 1, 0, 5), (1, 256, 1, 1, 0xFFFFFFFF)):
         with pytest.raises(ch.CHError) as ei:
             gch.set_query_config(*cfg)
         assert ei.value.code == ch.CH_EINVAL
@@ -68,9 +74,14 @@ def test_invalid_configuration_is_rejected(geo):
 def test_autotune_keeps_a_configuration_and_the_answers(geo):
     g, gch, och = geo
     cfg, ms = gch.autotune_queries(sample=8192, seed=3)
-    assert cfg in _ch().QUERY_CONFIGS and (ms > 0).all()
+    assert ms.size == len(_ch().QUERY_CONFIGS) and (ms > 0).all()
     assert gch.query_config() == cfg
-    assert ms[_ch().QUERY_CONFIGS.index(cfg)] == ms.min()
+    # the fastest candidate was kept; its delta is its multiple of the
+    # hierarchy's weight scale
+    best = _ch().QUERY_CONFIGS[int(ms.argmin())]
+    assert cfg[:4] == best[:4] and (cfg[4] == 0) == (best[4] == 0)
+    if best[4]:
+        assert cfg[4] % best[4] == 0
     s, t = I.random_pairs(g.n, 5000, seed=85)
     assert np.array_equal(gch.query(s, t), och.query(s, t))
 
@@ -92,7 +103,7 @@ def test_work_counters(geo):
     assert gch.query_work() == (0, 0)  # cleared by the read
 
 
-@pytest.mark.parametrize("cfg", [(1, 256, 0, 0), (1, 256, 1, 0), (1, 256, 1, 1)])
+@pytest.mark.parametrize("cfg", [(1, 256, 0, 0, 0), (1, 256, 1, 0, 0), (1, 256, 1, 1, 0), (1, 256, 1, 1, 40)])
 def test_graph_replay_matches_batch_calls(geo, cfg):
     torch = _torch()
     g, gch, och = geo
