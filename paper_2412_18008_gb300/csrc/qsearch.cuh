@@ -190,6 +190,40 @@ __device__ __forceinline__ void qb_entry(const QBSmem<TB> &q, const QArgs &a, bo
     dx = cnt ? (dir ? q.db[slot] : q.df[slot]) : INF;
 }
 
+// qb_entry plus the stall test's edge range: the offsets of the entry's
+// vertex in both CSRs, loaded together before any check, so that they cost
+// one round trip to L2 instead of two. sb / se: the other CSR's range
+// (0, 0 when cnt = 0).
+template <int TB>
+__device__ __forceinline__ void qb_entry_both(const QBSmem<TB> &q, const QArgs &a, bool fv, uint32_t ent,
+                                              uint32_t &b, uint32_t &cnt, uint32_t &dx, uint32_t &sb,
+                                              uint32_t &se) {
+    const uint32_t dir = ent >> 31;
+    const uint32_t slot = ent & 0x7FFFFFFFu;
+    const bool sok = fv && slot < QBSmem<TB>::T;
+    const uint32_t x = sok ? q.key[slot] : 0;
+    const bool xok = sok && x < a.n;
+    const uint32_t *off = dir ? a.dn_off : a.up_off;
+    const uint32_t *soff = dir ? a.up_off : a.dn_off;
+    uint32_t e_end = 0;
+    b = sb = se = 0;
+    if (xok) {
+        b = off[x];
+        e_end = off[x + 1];
+        sb = soff[x];
+        se = soff[x + 1];
+    }
+    if (fv && !sok) atomicOr(a.err, QERR_BOUND);
+    if (sok && !xok) atomicOr(a.err, QERR_BOUND);
+    const uint32_t n_edges = dir ? a.n_dn : a.n_up;
+    cnt = 0;
+    if (xok && b <= e_end && e_end <= n_edges) cnt = e_end - b;
+    else if (xok) atomicOr(a.err, QERR_BOUND);
+    if (a.core_tab && x >= a.core_lo) cnt = 0;  // a core vertex: joined through the table
+    dx = cnt ? (dir ? q.db[slot] : q.df[slot]) : INF;
+    if (!cnt) sb = se = 0;
+}
+
 // Both upward searches at once, label-correcting over the rank DAG: the
 // frontier holds forward (E_up) and backward (reversed E_down) entries,
 // each level relaxes the out-edges of every queued vertex with its current
@@ -286,8 +320,9 @@ __device__ bool block_search(QBSmem<TB> &q, const QArgs &a, QStat &stat) {
                     }
                     if (keep || drop) fv = false;
                 }
-                uint32_t b, cnt, dx;
-                qb_entry(q, a, fv, ent, b, cnt, dx);
+                uint32_t b, cnt, dx, psb = 0, pse = 0;
+                if (DELTA) qb_entry_both(q, a, fv, ent, b, cnt, dx, psb, pse);
+                else qb_entry(q, a, fv, ent, b, cnt, dx);
                 stat.exp += cnt ? 1u : 0u;
                 if (STALL) {
                     // Stall on demand: the entry's vertex x is not expanded
@@ -300,11 +335,11 @@ __device__ bool block_search(QBSmem<TB> &q, const QArgs &a, QStat &stat) {
                     // and a later improvement queues x again.
                     const uint32_t dir = ent >> 31;
                     const uint32_t slot = ent & 0x7FFFFFFFu;
-                    const uint32_t x = cnt ? q.key[slot] : 0;
+                    const uint32_t x = (cnt && !DELTA) ? q.key[slot] : 0;
                     const uint32_t *soff = dir ? a.up_off : a.dn_off;
                     const uint32_t s_edges = dir ? a.n_up : a.n_dn;
-                    const uint32_t sb = cnt ? soff[x] : 0;
-                    const uint32_t se = cnt ? soff[x + 1] : 0;
+                    const uint32_t sb = DELTA ? psb : (cnt ? soff[x] : 0);
+                    const uint32_t se = DELTA ? pse : (cnt ? soff[x + 1] : 0);
                     uint32_t scnt = 0;
                     if (cnt && sb <= se && se <= s_edges) scnt = se - sb;
                     else if (cnt) atomicOr(a.err, QERR_BOUND);

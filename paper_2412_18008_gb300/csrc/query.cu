@@ -27,10 +27,10 @@ namespace {
 
 constexpr uint64_t Q_CHUNK = 1u << 22;  // queries per launch pair
 
-// (The delta-stepping variant is held to the others' register budget, so
-// that six 2^11-slot blocks stay resident per SM.)
+// (The stalling variants are held to six resident blocks per SM, about 40
+// registers a thread, so that six 2^11-slot blocks fit an SM.)
 template <bool PRUNE, bool WARP, int TB, bool STALL, bool DELTA = false>
-__global__ void __launch_bounds__(QB_THREADS, DELTA ? 6 : 1) k_query_block(QArgs a) {
+__global__ void __launch_bounds__(QB_THREADS, (STALL || DELTA) ? 6 : 1) k_query_block(QArgs a) {
     extern __shared__ __align__(16) unsigned char qb_raw[];
     QBSmem<TB> &q = *reinterpret_cast<QBSmem<TB> *>(qb_raw);
     const uint32_t tid = threadIdx.x;
