@@ -325,8 +325,9 @@ int ch_load(const char *path, ch_t **out);
  * expanded again after a later improvement; delta = 0 expands every queued
  * vertex. A built or loaded hierarchy starts with the warp layout, 256
  * threads, small_first 1, stall 1 and delta = 128 x its weight scale (the
- * median weight of 1024 evenly spaced E_up edges). Every configuration
- * gives the same answers and search-space sizes. */
+ * median weight of 1024 evenly spaced E_up edges; delta = 0 when it has a
+ * core, whose searches outgrow the shared tables anyway). Every
+ * configuration gives the same answers and search-space sizes. */
 #define CH_QUERY_BLOCK_FLAT 0u
 #define CH_QUERY_WARP_FLAT 1u
 typedef struct {

@@ -313,7 +313,10 @@ void query_init(ch_s *h) {
         std::nth_element(w.begin(), w.begin() + WSCALE_SAMPLE / 2, w.end());
         h->q_wscale = std::max<uint32_t>(1, w[WSCALE_SAMPLE / 2]);
     }
-    h->q_delta = delta_of(h, DELTA_DEFAULT_MULT);
+    // Without delta when the hierarchy has a core: its queries search the
+    // core, outgrow the shared tables and are redone on the dense kernel;
+    // delta-stepping levels only delay that overflow.
+    h->q_delta = h->core_size ? 0 : delta_of(h, DELTA_DEFAULT_MULT);
     CH_CUDA_TRY(cudaDeviceSynchronize());
 }
 

@@ -47,6 +47,7 @@ def test_rmat_with_a_core(cmax):
     assert_same_hierarchy(gch, och)
     core = int((och.level == och.rounds).sum())
     assert core > 0 and gch.stats()["core_vertices"] == core
+    assert gch.query_config()[4] == 0  # no delta-stepping levels by default with a core
     s, t = I.random_pairs(g.n, 3000, seed=92)
     d = assert_same_queries(gch, och, s, t)
     assert np.array_equal(d, O.dijkstra_pairs(g, s, t))
