@@ -71,8 +71,8 @@ QUERY_TRAFFIC_PER_LAUNCH = None
 # threads, small_first, stall, delta) (lts__t_sectors * 32 over a
 # 200K-query pass of the same workload; L2 traffic is per-query work, so it
 # scales with the queries of a batch).
-QUERY_L2_CONFIG = (1, 256, 1, 1, 0)
-QUERY_L2_BYTES_PER_QUERY = 397_587
+QUERY_L2_CONFIG = (1, 256, 1, 1, 256)
+QUERY_L2_BYTES_PER_QUERY = 217_501
 
 
 def max_over_ranks(values, world: int, device):
