@@ -73,6 +73,27 @@ def test_struct_layouts_match_header():
     assert sizes[7] == ch.ServerParamsT.idle_ms.offset
 
 
+def test_autotune_candidates_match_the_header():
+    # the binding's candidate list has the header's length and its order:
+    # 4 * small_first + 2 * warp layout + (threads == 256) without stalling,
+    # then the stalling warp layout, then the delta candidates
+    from paper_2412_18008_gb300 import ch
+    text = open(HEADER).read()
+    n = int(re.search(r"#define CH_QUERY_AUTOTUNE_CONFIGS (\d+)", text).group(1))
+    assert len(ch.QUERY_CONFIGS) == n
+    for i, (lay, thr, sf, stall, delta) in enumerate(ch.QUERY_CONFIGS[:8]):
+        assert i == 4 * sf + 2 * lay + (thr == 256) and stall == 0 and delta == 0
+    for i, (lay, thr, sf, stall, delta) in enumerate(ch.QUERY_CONFIGS[8:12]):
+        assert i == 2 * sf + (thr == 256) and lay == ch.CH_QUERY_WARP_FLAT and stall == 1 and delta == 0
+    tail = ch.QUERY_CONFIGS[12:]
+    assert all(c[:4] == (ch.CH_QUERY_WARP_FLAT, 256, 1, 1) and c[4] > 0 for c in tail)
+    mults = re.search(r"delta = ([\d, ]+) x the weight scale", " ".join(text.split())).group(1)
+    assert [c[4] for c in tail] == [int(x) for x in mults.split(",")]
+    src = open(os.path.join(os.path.dirname(HEADER), "..", "paper_2412_18008_gb300", "csrc", "query.cu")).read()
+    lib_mults = re.search(r"DELTA_TUNE_MULT\[\d+\] = \{([\d, ]+)\}", src).group(1)
+    assert [c[4] for c in tail] == [int(x) for x in lib_mults.split(",")]
+
+
 def test_no_cpu_fallback_in_product_package():
     pkg = os.path.join(os.path.dirname(HEADER), "..", "paper_2412_18008_gb300")
     for root, _, files in os.walk(pkg):
