@@ -97,7 +97,7 @@ void core_table(ch_s *h, uint64_t max_bytes, cudaStream_t st) {
     h->core_n = 0;
     h->core_lo = h->n;
     if (C == 0) return;
-    if (C >= (1ull << 32) || C * C * 4 > max_bytes)
+    if (C >= (1ull << 32) || C > max_bytes / 4 / C)  // C^2 * 4 > max_bytes, without overflow
         throw Error{CH_ERANGE, "core distance table of " + std::to_string(C) + "^2 entries exceeds the byte limit"};
     const uint32_t n = h->n;
     const uint32_t core_lo = (uint32_t)(n - C);
