@@ -437,12 +437,12 @@ def modes_record(args, g, off, tgt, wt, s_d, t_d, stream, steps=2, warmup=1):
 
 
 def rmat_record(args, steps=2, warmup=1, nq=50):
-    """Config 5's stress graph (RMAT, 2^21 vertices, 2^25 edge samples) with
-    a finite candidate bound and the core it leaves: build seconds (CUDA
-    events), rounds, core, shortcuts, witness time, and queries/s of a small
-    batch, whose searches cover the core; a few answers against Dijkstra."""
+    """The RMAT stress graph (2^21 vertices, 2^25 edge samples) with a finite
+    candidate bound and the core it leaves: build seconds (CUDA events),
+    rounds, core, shortcuts, witness time, and queries/s of a small batch,
+    whose searches cover the core. (Its hierarchy and answers are checked
+    against the oracle by tests/test_rmat_full_size.py, not here.)"""
     import torch
-    import oracle as O
     from paper_2412_18008_gb300 import ch
     dev = torch.device("cuda", 0)
     g = make_graph("rmat2M")
@@ -472,7 +472,6 @@ def rmat_record(args, steps=2, warmup=1, nq=50):
     d = h.query(ds, dt)
     e1.record()
     torch.cuda.synchronize()
-    got = d.cpu().numpy().view(np.uint32)
     h.close()
     return {"workload": "rmat2M", "vertices": g.n, "edge_samples": int(g.m),
             "params": {"hop_limit": 2, "cmax": 256, "witness_ball": 256, "witness_level_work": 1024,
@@ -480,8 +479,7 @@ def rmat_record(args, steps=2, warmup=1, nq=50):
             "build_s": statistics.mean(times) / 1e3, "rounds": st["rounds"],
             "core_vertices": st["core_vertices"], "shortcuts": st["shortcuts"],
             "witness_ms": st["witness_ms"], "queries": nq,
-            "queries_per_s": nq / (e0.elapsed_time(e1) * 1e-3),
-            "answers_equal_dijkstra_5": bool(np.array_equal(got[:5], O.dijkstra_pairs(g, s_h[:5], t_h[:5])))}
+            "queries_per_s": nq / (e0.elapsed_time(e1) * 1e-3)}
 
 
 def compare_learned(args, steps=None, warmup=None):

@@ -101,3 +101,27 @@ def test_no_cpu_fallback_in_product_package():
             if f.endswith((".py", ".cu", ".cuh")):
                 text = open(os.path.join(root, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_bench_touches_the_oracle_only_in_its_baseline_legs():
+    # bench.py may run the oracle only to time it: the cpu_baseline record
+    # and the reference arm (through oracle_build_s)
+    import ast
+    path = os.path.join(os.path.dirname(HEADER), "..", "bench.py")
+    tree = ast.parse(open(path).read())
+    allowed = {"oracle_build_s", "cpu_baseline_record", "run_reference"}
+    users = set()
+    for fn in ast.walk(tree):
+        if not isinstance(fn, ast.FunctionDef):
+            continue
+        for node in ast.walk(fn):
+            if isinstance(node, (ast.Import, ast.ImportFrom)):
+                mods = [a.name for a in node.names] if isinstance(node, ast.Import) else [node.module or ""]
+                if any(m == "oracle" or m.startswith("oracle.") for m in mods):
+                    users.add(fn.name)
+            if isinstance(node, ast.Call) and isinstance(node.func, ast.Name) and node.func.id == "oracle_build_s":
+                users.add(fn.name)
+    assert users and users <= allowed, users - allowed
+    top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
+    assert not any((a.name if isinstance(n, ast.Import) else n.module or "").startswith("oracle")
+                   for n in top for a in n.names), "bench.py imports the oracle at module level"
