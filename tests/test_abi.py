@@ -125,3 +125,14 @@ def test_bench_touches_the_oracle_only_in_its_baseline_legs():
     top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
     assert not any((a.name if isinstance(n, ast.Import) else n.module or "").startswith("oracle")
                    for n in top for a in n.names), "bench.py imports the oracle at module level"
+
+
+def test_device_code_has_no_trap_or_device_assert():
+    # failures inside kernels are reported through error words the host
+    # reads, never by trapping the GPU
+    csrc = os.path.join(os.path.dirname(HEADER), "..", "paper_2412_18008_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            text = re.sub(r"//[^\n]*|/\*.*?\*/", "", open(os.path.join(csrc, f)).read(), flags=re.S)
+            assert "__trap" not in text and "brkpt" not in text, f
+            assert not re.search(r"(?<![\w_])assert\s*\(", text), f
